@@ -1,0 +1,748 @@
+/*
+ * bab_oracle.c -- plain, slow FP64 CPU oracle for the bounding hot path of
+ * BaB-ND (branch-and-bound planning over neural dynamics, arXiv 2412.09584).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker, not the product: only
+ * the test suite, the package's smoke() check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or helper with the
+ * CUDA library (paper_2412_09584_gb300/csrc), and the CUDA library never calls it.
+ *
+ * Everything is written as straight loops in double precision, in the order
+ * the paper states the method, so that each function can be checked against
+ * the paper by eye:
+ *
+ *   oracle_objective      Section 3 "Formulation", Eq. (trajop): the H-step
+ *                         unrolled dynamics x_{t+1} = x_t + f(x_t, u_t) and the
+ *                         summed cost, flattened to f(u) with d = kH.
+ *   oracle_rollout        Section 3.3 (batch_search) with uniform sampling: the
+ *                         best sampled objective of each box, an upper bound.
+ *   oracle_ibp            interval bound propagation of the pre-activation
+ *                         bounds (the intermediate bounds Lemma 1 needs).
+ *   oracle_crown          Appendix B.1: Lemma 1 (ReLU relaxation), Theorem 1
+ *                         (backward propagation of a linear lower bound) and
+ *                         Theorem 2 (concretization) in box form.
+ *   oracle_alpha_grad     d(lower bound)/d(alpha) for the free lower slopes of
+ *                         Lemma 1, by a forward pass of the relaxed network.
+ *   oracle_adam_ascent    projected Adam ascent on alpha.
+ *   oracle_prune_branch   Section 3 overview (prune when lower > incumbent),
+ *                         Section 3.1 batch_pick_out and batch_split (bisection
+ *                         of the widest dimension).
+ *
+ * Layout conventions (these are the public conventions of the library too):
+ *   network: L linear layers, dims[0] = s + k, dims[L] = s; params holds, for
+ *            l = 1..L in order, W_l as a row-major dims[l] x dims[l-1] matrix
+ *            followed by b_l (dims[l]).  ReLU follows layers 1..L-1.
+ *   actions: u is t-major, u[t*k + j], t = 0..H-1 (Section 3, flattening).
+ *   hidden : per time step the hidden pre-activations of layers 1..L-1 are
+ *            concatenated (sumh values); per-box arrays are [H][sumh].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_LAYERS 16
+#define ORC_MAX_WIDTH 1024
+
+typedef struct {
+    int L;
+    int dims[ORC_MAX_LAYERS + 1];
+    const double *W[ORC_MAX_LAYERS + 1];
+    const double *b[ORC_MAX_LAYERS + 1];
+    int hoff[ORC_MAX_LAYERS + 1]; /* offset of hidden layer l in the [sumh] vector */
+    int sumh;
+    int s, k;
+} onet;
+
+/* Returns 0 on success, -1 if the shapes are outside the oracle's limits. */
+static int onet_init(onet *N, int L, const int *dims, const double *params, int s, int k)
+{
+    if (L < 1 || L > ORC_MAX_LAYERS || dims[0] != s + k || dims[L] != s) return -1;
+    N->L = L;
+    N->s = s;
+    N->k = k;
+    size_t off = 0;
+    int h = 0;
+    for (int l = 0; l <= L; ++l) {
+        if (dims[l] < 1 || dims[l] > ORC_MAX_WIDTH) return -1;
+        N->dims[l] = dims[l];
+    }
+    for (int l = 1; l <= L; ++l) {
+        N->W[l] = params + off;
+        off += (size_t)dims[l] * dims[l - 1];
+        N->b[l] = params + off;
+        off += dims[l];
+        N->hoff[l] = h;
+        if (l < L) h += dims[l];
+    }
+    N->sumh = h;
+    return 0;
+}
+
+int oracle_param_count(int L, const int *dims)
+{
+    int n = 0;
+    for (int l = 1; l <= L; ++l) n += dims[l] * dims[l - 1] + dims[l];
+    return n;
+}
+
+int oracle_sumh(int L, const int *dims)
+{
+    int h = 0;
+    for (int l = 1; l < L; ++l) h += dims[l];
+    return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Objective (Section 3, Eq. trajop)                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One step of the residual dynamics x_{t+1} = x_t + N([x_t; u_t]) with N the
+ * ReLU MLP.  pre (nullable) receives the hidden pre-activations (sumh values).
+ */
+static void step_forward(const onet *N, const double *x, const double *u, double *xnext, double *pre)
+{
+    double a[ORC_MAX_WIDTH], z[ORC_MAX_WIDTH];
+    for (int i = 0; i < N->s; ++i) a[i] = x[i];
+    for (int j = 0; j < N->k; ++j) a[N->s + j] = u[j];
+    for (int l = 1; l <= N->L; ++l) {
+        int no = N->dims[l], ni = N->dims[l - 1];
+        for (int r = 0; r < no; ++r) {
+            double acc = N->b[l][r];
+            for (int c = 0; c < ni; ++c) acc += N->W[l][(size_t)r * ni + c] * a[c];
+            z[r] = acc;
+        }
+        if (l < N->L) {
+            for (int r = 0; r < no; ++r) {
+                if (pre) pre[N->hoff[l] + r] = z[r];
+                a[r] = z[r] > 0.0 ? z[r] : 0.0;
+            }
+        }
+    }
+    for (int i = 0; i < N->s; ++i) xnext[i] = x[i] + z[i];
+}
+
+/*
+ * f(u) = sum_{t=1..H} ||x_t - goal||^2 + rho * sum_{t=0..H-1} ||u_t||^2.
+ * traj (nullable) receives x_0..x_H ([H+1][s]); pre (nullable) the hidden
+ * pre-activations of every step ([H][sumh]).
+ */
+double oracle_objective(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                        const double *x0, const double *goal, const double *u, double *traj, double *pre)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return NAN;
+    double x[ORC_MAX_WIDTH], xn[ORC_MAX_WIDTH];
+    for (int i = 0; i < s; ++i) x[i] = x0[i];
+    if (traj) memcpy(traj, x0, sizeof(double) * s);
+    double f = 0.0;
+    for (int t = 0; t < H; ++t) {
+        const double *ut = u + (size_t)t * k;
+        step_forward(&N, x, ut, xn, pre ? pre + (size_t)t * N.sumh : NULL);
+        for (int j = 0; j < k; ++j) f += rho * ut[j] * ut[j];
+        for (int i = 0; i < s; ++i) {
+            double e = xn[i] - goal[i];
+            f += e * e;
+            x[i] = xn[i];
+        }
+        if (traj) memcpy(traj + (size_t)(t + 1) * s, x, sizeof(double) * s);
+    }
+    return f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampled search (Section 3.3) with a counter-based generator               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014): add the golden-ratio
+ * increment, then two xor-shift-multiply rounds and a final xor-shift.
+ */
+uint64_t oracle_splitmix64(uint64_t state)
+{
+    uint64_t z = state + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/*
+ * The uniform draw of sample m, coordinate j, of the box with identifier id:
+ * chained SplitMix64 over (seed, id, m, j), top 24 bits as r in [0, 1), and
+ * the sample u = lo + (hi - lo) * r formed in FP32 with one rounding per
+ * operation (no fused multiply-add), so that every implementation that follows
+ * this definition draws bit-identical samples.
+ */
+float oracle_sample(uint64_t seed, uint64_t id, uint32_t m, uint32_t j, float lo, float hi)
+{
+    uint64_t h = oracle_splitmix64(seed ^ oracle_splitmix64(id));
+    h = oracle_splitmix64(h ^ ((uint64_t)m << 32 | (uint64_t)j));
+    float r = (float)(h >> 40) * (1.0f / 16777216.0f);
+    volatile float w = hi - lo;
+    volatile float step = w * r;
+    volatile float u = lo + step;
+    return u;
+}
+
+/*
+ * For each box i: draw M samples, evaluate f in FP64, and return the minimum
+ * (ub[i]) with its argmin sample (best_u, [n][d]) and index (best_m).  Ties
+ * go to the lowest m.
+ */
+int oracle_rollout(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                   const double *x0, const double *goal, int n, const float *lo, const float *hi,
+                   const uint64_t *id, int M, uint64_t seed, double *ub, float *best_u, int *best_m)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    int d = k * H;
+    double *u = (double *)malloc(sizeof(double) * d);
+    float *uf = (float *)malloc(sizeof(float) * d);
+    for (int i = 0; i < n; ++i) {
+        double best = INFINITY;
+        int bm = -1;
+        for (int m = 0; m < M; ++m) {
+            for (int j = 0; j < d; ++j) {
+                uf[j] = oracle_sample(seed, id[i], (uint32_t)m, (uint32_t)j, lo[(size_t)i * d + j],
+                                      hi[(size_t)i * d + j]);
+                u[j] = uf[j];
+            }
+            double f = oracle_objective(L, dims, params, s, k, H, rho, x0, goal, u, NULL, NULL);
+            if (f < best || bm < 0) {
+                best = f;
+                bm = m;
+                if (best_u) memcpy(best_u + (size_t)i * d, uf, sizeof(float) * d);
+            }
+        }
+        ub[i] = best;
+        if (best_m) best_m[i] = bm;
+    }
+    free(u);
+    free(uf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interval bound propagation (intermediate bounds)                          */
+/* ------------------------------------------------------------------------ */
+
+/* min over s in [lo, hi] of s^2 */
+static double sq_min(double lo, double hi)
+{
+    if (lo <= 0.0 && hi >= 0.0) return 0.0;
+    return lo > 0.0 ? lo * lo : hi * hi;
+}
+
+/*
+ * Interval bounds of one box through the unrolled dynamics.  Each layer maps
+ * an input interval, in centre/radius form (c, r), to c' = W c + b and
+ * r' = |W| r; the ReLU clamps both ends at zero; the next state interval is
+ * the sum of the current state interval and the network output interval.
+ * x_0 is known exactly.  Outputs per box: pre_lo/pre_hi [H][sumh], x_lo/x_hi
+ * [H+1][s] (all nullable), and the interval lower bound of the objective.
+ */
+static double ibp_box(const onet *N, int H, double rho, const double *x0, const double *goal, const double *lo,
+                      const double *hi, double *pre_lo, double *pre_hi, double *x_lo, double *x_hi)
+{
+    int s = N->s, k = N->k;
+    double xl[ORC_MAX_WIDTH], xu[ORC_MAX_WIDTH];
+    double c[ORC_MAX_WIDTH], r[ORC_MAX_WIDTH], cn[ORC_MAX_WIDTH], rn[ORC_MAX_WIDTH];
+    double zl[ORC_MAX_WIDTH], zu[ORC_MAX_WIDTH];
+    for (int i = 0; i < s; ++i) xl[i] = xu[i] = x0[i];
+    if (x_lo) for (int i = 0; i < s; ++i) x_lo[i] = x_hi[i] = x0[i];
+    double lb = 0.0;
+    for (int t = 0; t < H; ++t) {
+        for (int i = 0; i < s; ++i) {
+            c[i] = 0.5 * (xl[i] + xu[i]);
+            r[i] = 0.5 * (xu[i] - xl[i]);
+        }
+        for (int j = 0; j < k; ++j) {
+            double a = lo[t * k + j], bb = hi[t * k + j];
+            c[s + j] = 0.5 * (a + bb);
+            r[s + j] = 0.5 * (bb - a);
+            lb += rho * sq_min(a, bb);
+        }
+        for (int l = 1; l <= N->L; ++l) {
+            int no = N->dims[l], ni = N->dims[l - 1];
+            for (int q = 0; q < no; ++q) {
+                double cc = N->b[l][q], rr = 0.0;
+                for (int p = 0; p < ni; ++p) {
+                    double w = N->W[l][(size_t)q * ni + p];
+                    cc += w * c[p];
+                    rr += fabs(w) * r[p];
+                }
+                cn[q] = cc;
+                rn[q] = rr;
+                zl[q] = cc - rr;
+                zu[q] = cc + rr;
+            }
+            if (l < N->L) {
+                for (int q = 0; q < no; ++q) {
+                    if (pre_lo) {
+                        pre_lo[(size_t)t * N->sumh + N->hoff[l] + q] = zl[q];
+                        pre_hi[(size_t)t * N->sumh + N->hoff[l] + q] = zu[q];
+                    }
+                    double al = zl[q] > 0.0 ? zl[q] : 0.0;
+                    double au = zu[q] > 0.0 ? zu[q] : 0.0;
+                    c[q] = 0.5 * (al + au);
+                    r[q] = 0.5 * (au - al);
+                }
+            }
+        }
+        (void)cn;
+        (void)rn;
+        for (int i = 0; i < s; ++i) {
+            xl[i] += zl[i];
+            xu[i] += zu[i];
+            lb += sq_min(xl[i] - goal[i], xu[i] - goal[i]);
+        }
+        if (x_lo) {
+            for (int i = 0; i < s; ++i) {
+                x_lo[(size_t)(t + 1) * s + i] = xl[i];
+                x_hi[(size_t)(t + 1) * s + i] = xu[i];
+            }
+        }
+    }
+    return lb;
+}
+
+int oracle_ibp(int L, const int *dims, const double *params, int s, int k, int H, double rho, const double *x0,
+               const double *goal, int n, const double *lo, const double *hi, double *pre_lo, double *pre_hi,
+               double *x_lo, double *x_hi, double *lb_ibp)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    int d = k * H;
+    for (int i = 0; i < n; ++i) {
+        double v = ibp_box(&N, H, rho, x0, goal, lo + (size_t)i * d, hi + (size_t)i * d,
+                           pre_lo ? pre_lo + (size_t)i * H * N.sumh : NULL,
+                           pre_hi ? pre_hi + (size_t)i * H * N.sumh : NULL,
+                           x_lo ? x_lo + (size_t)i * (H + 1) * s : NULL,
+                           x_hi ? x_hi + (size_t)i * (H + 1) * s : NULL);
+        if (lb_ibp) lb_ibp[i] = v;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Relaxations                                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Tangent lower bound of s^2 at m: s^2 >= 2 m s - m^2 (exact at s = m).
+ * Chord upper bound of s^2 on [L, U]: s^2 <= (L + U) s - L U (exact at L, U).
+ */
+double oracle_sq_tangent(double m, double s) { return 2.0 * m * s - m * m; }
+double oracle_sq_chord(double L, double U, double s) { return (L + U) * s - L * U; }
+
+/*
+ * Lemma 1 for one neuron with pre-activation bounds [l, u]: the slope D and
+ * intercept c of the lower (which = 0) or upper (which = 1) linear bound of
+ * ReLU.  Active iff l >= 0, inactive iff u <= 0, otherwise unstable; the lower
+ * bound of an unstable neuron is alpha * z (intercept 0) and the upper bound
+ * is the chord u (z - l) / (u - l).
+ */
+void oracle_relu_relax(double l, double u, double alpha, int which, double *D, double *c)
+{
+    if (l >= 0.0) {
+        *D = 1.0;
+        *c = 0.0;
+    } else if (u <= 0.0) {
+        *D = 0.0;
+        *c = 0.0;
+    } else if (which == 0) {
+        *D = alpha;
+        *c = 0.0;
+    } else {
+        *D = u / (u - l);
+        *c = -u * l / (u - l);
+    }
+}
+
+/* The adaptive lower slope of an unstable neuron: 1 if u >= -l, else 0. */
+static double adaptive_alpha(double l, double u) { return u >= -l ? 1.0 : 0.0; }
+
+/* min over u in [lo, hi] of mu u + rho u^2, with its minimiser. */
+static double quad_min(double mu, double rho, double lo, double hi, double *arg)
+{
+    double u;
+    if (rho > 0.0) {
+        u = -mu / (2.0 * rho);
+        if (u < lo) u = lo;
+        if (u > hi) u = hi;
+    } else {
+        u = mu >= 0.0 ? lo : hi;
+    }
+    *arg = u;
+    return mu * u + rho * u * u;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CROWN backward bound (Appendix B.1, Lemma 1 / Theorem 1 / Theorem 2)      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double lb;          /* concretized lower bound */
+    double lin_const;   /* f(u) >= lin_const + mu . u + rho ||u||^2 on the box */
+} crown_out;
+
+/*
+ * The bound of one box.  The cost term ||x_t - g||^2 (t >= 1) is bounded below
+ * by its tangent at the midpoint m of the interval of s = x_{t,i} - g_i, which
+ * turns the objective into a linear function of x_1..x_H plus the exact
+ * rho ||u||^2.  The coefficient lam of x_{t+1} is then carried backward through
+ * step t: lam . x_{t+1} = lam . x_t + lam . N([x_t; u_t]), and lam . N is
+ * bounded below by Theorem 1 (last layer: A = lam; then, per hidden layer
+ * from the top: relax each ReLU by Lemma 1, choosing the lower bound where the
+ * coefficient is >= 0 and the upper bound where it is < 0, then multiply by
+ * W_l), which leaves coefficients on x_t and u_t.  x_0 is a constant.
+ * Theorem 2 in box form concretizes the remaining function of u.
+ *
+ * alpha (nullable, [H][sumh]) gives the lower slopes; NULL means adaptive.
+ * Outputs (all nullable): mu [d] (coefficients of u), ustar [d] (concretizing
+ * point), A_pre [H][sumh] (the coefficient of each ReLU output before its
+ * relaxation), and tangent coefficients atan [H+1][s] (row 0 unused).
+ */
+static crown_out crown_box(const onet *N, int H, double rho, const double *x0, const double *goal,
+                           const double *lo, const double *hi, const double *pre_lo, const double *pre_hi,
+                           const double *x_lo, const double *x_hi, const double *alpha, double *mu,
+                           double *ustar, double *A_pre, double *atan)
+{
+    int s = N->s, k = N->k, L = N->L, sumh = N->sumh;
+    double lam[ORC_MAX_WIDTH], A[ORC_MAX_WIDTH], An[ORC_MAX_WIDTH];
+    double cst = 0.0;
+    double *mu_loc = (double *)malloc(sizeof(double) * k * H);
+
+    /* tangent coefficients a_{t,i} = 2 m and constants -2 m g - m^2 */
+    double *a = (double *)calloc((size_t)(H + 1) * s, sizeof(double));
+    for (int t = 1; t <= H; ++t) {
+        for (int i = 0; i < s; ++i) {
+            double Ls = x_lo[(size_t)t * s + i] - goal[i];
+            double Us = x_hi[(size_t)t * s + i] - goal[i];
+            double m = 0.5 * (Ls + Us);
+            a[(size_t)t * s + i] = 2.0 * m;
+            cst += -2.0 * m * goal[i] - m * m;
+        }
+    }
+    for (int i = 0; i < s; ++i) lam[i] = a[(size_t)H * s + i];
+
+    for (int t = H - 1; t >= 0; --t) {
+        /* last linear layer: A = lam on z_L */
+        int nL = N->dims[L], nLm = N->dims[L - 1];
+        for (int q = 0; q < nL; ++q) A[q] = lam[q];
+        for (int q = 0; q < nL; ++q) cst += A[q] * N->b[L][q];
+        for (int p = 0; p < nLm; ++p) {
+            double acc = 0.0;
+            for (int q = 0; q < nL; ++q) acc += A[q] * N->W[L][(size_t)q * nLm + p];
+            An[p] = acc;
+        }
+        for (int p = 0; p < nLm; ++p) A[p] = An[p];
+        /* hidden layers l = L-1 .. 1 */
+        for (int l = L - 1; l >= 1; --l) {
+            int no = N->dims[l], ni = N->dims[l - 1];
+            for (int q = 0; q < no; ++q) {
+                size_t idx = (size_t)t * sumh + N->hoff[l] + q;
+                double zl = pre_lo[idx], zu = pre_hi[idx];
+                double al = alpha ? alpha[idx] : adaptive_alpha(zl, zu);
+                double D, c;
+                if (A_pre) A_pre[idx] = A[q];
+                oracle_relu_relax(zl, zu, al, A[q] >= 0.0 ? 0 : 1, &D, &c);
+                cst += A[q] * c;
+                A[q] *= D;
+            }
+            for (int q = 0; q < no; ++q) cst += A[q] * N->b[l][q];
+            for (int p = 0; p < ni; ++p) {
+                double acc = 0.0;
+                for (int q = 0; q < no; ++q) acc += A[q] * N->W[l][(size_t)q * ni + p];
+                An[p] = acc;
+            }
+            for (int p = 0; p < ni; ++p) A[p] = An[p];
+        }
+        /* A is now on [x_t; u_t] */
+        for (int j = 0; j < k; ++j) mu_loc[t * k + j] = A[s + j];
+        for (int i = 0; i < s; ++i) lam[i] = lam[i] + A[i] + (t >= 1 ? a[(size_t)t * s + i] : 0.0);
+    }
+    for (int i = 0; i < s; ++i) cst += lam[i] * x0[i];
+
+    double lb = cst;
+    for (int j = 0; j < k * H; ++j) {
+        double arg;
+        lb += quad_min(mu_loc[j], rho, lo[j], hi[j], &arg);
+        if (ustar) ustar[j] = arg;
+        if (mu) mu[j] = mu_loc[j];
+    }
+    if (atan) memcpy(atan, a, sizeof(double) * (size_t)(H + 1) * s);
+    free(a);
+    free(mu_loc);
+    crown_out o = {lb, cst};
+    return o;
+}
+
+/*
+ * CROWN lower bound of each box, with IBP intermediate bounds.  Outputs (all
+ * but lb nullable): lb [n], lin_coef [n][d] and lin_const [n] such that
+ * f(u) >= lin_const + lin_coef . u + rho ||u||^2 on the box, ustar [n][d],
+ * A_pre [n][H][sumh].
+ */
+int oracle_crown(int L, const int *dims, const double *params, int s, int k, int H, double rho, const double *x0,
+                 const double *goal, int n, const double *lo, const double *hi, const double *alpha, double *lb,
+                 double *lin_coef, double *lin_const, double *ustar, double *A_pre)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    int d = k * H;
+    size_t nh = (size_t)H * N.sumh, nx = (size_t)(H + 1) * s;
+    double *pl = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *pu = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *xl = (double *)malloc(sizeof(double) * nx);
+    double *xu = (double *)malloc(sizeof(double) * nx);
+    for (int i = 0; i < n; ++i) {
+        const double *bl = lo + (size_t)i * d, *bh = hi + (size_t)i * d;
+        ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, alpha ? alpha + (size_t)i * nh : NULL,
+                                lin_coef ? lin_coef + (size_t)i * d : NULL, ustar ? ustar + (size_t)i * d : NULL,
+                                A_pre ? A_pre + (size_t)i * nh : NULL, NULL);
+        lb[i] = o.lb;
+        if (lin_const) lin_const[i] = o.lin_const;
+    }
+    free(pl);
+    free(pu);
+    free(xl);
+    free(xu);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the bound with respect to alpha                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The backward pass of crown_box is a back-substitution through the "relaxed
+ * network": every ReLU replaced by the linear bound Lemma 1 selected for it.
+ * Its final linear function of u therefore equals the relaxed network's
+ * objective (tangent-linearised cost plus rho ||u||^2), and the bound is that
+ * objective at the concretizing point u*.  With the selections fixed, the
+ * bound depends on a lower slope alpha_j only through the term
+ * A_j * alpha_j * z_j, where A_j >= 0 is the coefficient of the ReLU output and
+ * z_j the neuron's pre-activation in the relaxed network at u*.  Hence
+ *   dLB/dalpha_j = A_j * z~_j(u*)   (unstable neurons whose lower bound was
+ *                                    selected), 0 otherwise.
+ * relaxed_obj (nullable) receives the relaxed network's objective at u*, which
+ * must equal lb.
+ */
+int oracle_alpha_grad(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                      const double *x0, const double *goal, int n, const double *lo, const double *hi,
+                      const double *alpha, double *lb, double *grad_alpha, double *relaxed_obj)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    int d = k * H, sumh = N.sumh;
+    size_t nh = (size_t)H * sumh, nx = (size_t)(H + 1) * s;
+    double *pl = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *pu = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *Ap = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *xl = (double *)malloc(sizeof(double) * nx);
+    double *xu = (double *)malloc(sizeof(double) * nx);
+    double *at = (double *)malloc(sizeof(double) * nx);
+    double *us = (double *)malloc(sizeof(double) * d);
+    for (int i = 0; i < n; ++i) {
+        const double *bl = lo + (size_t)i * d, *bh = hi + (size_t)i * d;
+        const double *al = alpha ? alpha + (size_t)i * nh : NULL;
+        double *g = grad_alpha + (size_t)i * nh;
+        ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, NULL, us, Ap, at);
+        lb[i] = o.lb;
+
+        /* forward pass of the relaxed network from x_0 and u* */
+        double x[ORC_MAX_WIDTH], a[ORC_MAX_WIDTH], z[ORC_MAX_WIDTH];
+        double obj = 0.0;
+        for (int q = 0; q < s; ++q) x[q] = x0[q];
+        for (int t = 0; t < H; ++t) {
+            for (int q = 0; q < s; ++q) a[q] = x[q];
+            for (int j = 0; j < k; ++j) {
+                a[s + j] = us[t * k + j];
+                obj += rho * us[t * k + j] * us[t * k + j];
+            }
+            for (int l = 1; l <= L; ++l) {
+                int no = N.dims[l], ni = N.dims[l - 1];
+                for (int r = 0; r < no; ++r) {
+                    double acc = N.b[l][r];
+                    for (int c = 0; c < ni; ++c) acc += N.W[l][(size_t)r * ni + c] * a[c];
+                    z[r] = acc;
+                }
+                if (l < L) {
+                    for (int r = 0; r < no; ++r) {
+                        size_t idx = (size_t)t * sumh + N.hoff[l] + r;
+                        double zl = pl[idx], zu = pu[idx];
+                        double alj = al ? al[idx] : adaptive_alpha(zl, zu);
+                        int lower = Ap[idx] >= 0.0;
+                        double D, c;
+                        oracle_relu_relax(zl, zu, alj, lower ? 0 : 1, &D, &c);
+                        g[idx] = (zl < 0.0 && zu > 0.0 && lower) ? Ap[idx] * z[r] : 0.0;
+                        a[r] = D * z[r] + c;
+                    }
+                }
+            }
+            for (int q = 0; q < s; ++q) {
+                x[q] += z[q];
+                double m = 0.5 * at[(size_t)(t + 1) * s + q];
+                obj += 2.0 * m * (x[q] - goal[q]) - m * m;
+            }
+        }
+        if (relaxed_obj) relaxed_obj[i] = obj;
+    }
+    free(pl);
+    free(pu);
+    free(Ap);
+    free(xl);
+    free(xu);
+    free(at);
+    free(us);
+    return 0;
+}
+
+/*
+ * One projected Adam ascent step (Kingma and Ba, 2015, Algorithm 1, with the
+ * update sign flipped to ascend), then clamp to [clamp_lo, clamp_hi].  step
+ * counts from 1.
+ */
+void oracle_adam_ascent(int count, double *param, double *m, double *v, const double *grad, int step, double lr,
+                        double beta1, double beta2, double eps, double clamp_lo, double clamp_hi)
+{
+    double bc1 = 1.0 - pow(beta1, step), bc2 = 1.0 - pow(beta2, step);
+    for (int i = 0; i < count; ++i) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+        double mh = m[i] / bc1, vh = v[i] / bc2;
+        double p = param[i] + lr * mh / (sqrt(vh) + eps);
+        if (p < clamp_lo) p = clamp_lo;
+        if (p > clamp_hi) p = clamp_hi;
+        param[i] = p;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Prune, pick out, split (Section 3 overview, Section 3.1, Algorithm 2)     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    float key;
+    uint64_t id;
+    int row;
+} okey;
+
+static int okey_cmp(const void *pa, const void *pb)
+{
+    const okey *a = (const okey *)pa, *b = (const okey *)pb;
+    /* NaN keys order last */
+    int an = isnan(a->key), bn = isnan(b->key);
+    if (an != bn) return an - bn;
+    if (!an && a->key < b->key) return -1;
+    if (!an && a->key > b->key) return 1;
+    if (a->id < b->id) return -1;
+    if (a->id > b->id) return 1;
+    return 0;
+}
+
+/*
+ * One prune-and-branch pass over a pool of n boxes.
+ *  1. Prune (Section 3 overview, Algorithm 2): drop box i iff
+ *     (double) lb[i] > inc_val; a NaN bound is kept.  keep[i] in {0,1}.
+ *  2. Pick out up to n_pick survivors (Section 3.1): if there are at most
+ *     n_pick survivors all are picked; otherwise the ceil(eta * n_pick) with
+ *     smallest (ub, id) are picked first, and the rest of the quota is filled
+ *     by smallest (lb, id) among the others.
+ *  3. Split each picked box (Section 3.1) on its widest dimension, lowest
+ *     index on ties, at mid = 0.5f * (lo + hi) in FP32: child 2p is the lower
+ *     half, child 2p + 1 the upper half; ids 2 id and 2 id + 1; both inherit
+ *     the parent's lb and ub.
+ * Output rows: the 2 P children (picked boxes in pool order), then the R
+ * unpicked survivors in pool order.  Returns 0, or -1 if a picked id is too
+ * deep to split (id >= 2^63).
+ */
+int oracle_prune_branch(int n, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                        const uint64_t *id, double inc_val, int n_pick, double eta, float *out_lo, float *out_hi,
+                        float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep, int *n_children, int *n_rest)
+{
+    int *surv = (int *)malloc(sizeof(int) * (n ? n : 1));
+    uint8_t *picked = (uint8_t *)calloc(n ? n : 1, 1);
+    int ns = 0;
+    for (int i = 0; i < n; ++i) {
+        int kp = !((double)lb[i] > inc_val);
+        keep[i] = (uint8_t)kp;
+        if (kp) surv[ns++] = i;
+    }
+    if (ns <= n_pick) {
+        for (int q = 0; q < ns; ++q) picked[surv[q]] = 1;
+    } else {
+        int n1 = (int)ceil(eta * n_pick);
+        if (n1 > n_pick) n1 = n_pick;
+        okey *ks = (okey *)malloc(sizeof(okey) * ns);
+        for (int q = 0; q < ns; ++q) {
+            ks[q].key = ub[surv[q]];
+            ks[q].id = id[surv[q]];
+            ks[q].row = surv[q];
+        }
+        qsort(ks, ns, sizeof(okey), okey_cmp);
+        for (int q = 0; q < n1; ++q) picked[ks[q].row] = 1;
+        int m = 0;
+        for (int q = 0; q < ns; ++q) {
+            if (picked[surv[q]]) continue;
+            ks[m].key = lb[surv[q]];
+            ks[m].id = id[surv[q]];
+            ks[m].row = surv[q];
+            ++m;
+        }
+        qsort(ks, m, sizeof(okey), okey_cmp);
+        for (int q = 0; q < n_pick - n1 && q < m; ++q) picked[ks[q].row] = 1;
+        free(ks);
+    }
+    int P = 0, err = 0;
+    for (int q = 0; q < ns; ++q) {
+        int i = surv[q];
+        if (!picked[i]) continue;
+        const float *pl = lo + (size_t)i * d, *ph = hi + (size_t)i * d;
+        int js = 0;
+        float wbest = ph[0] - pl[0];
+        for (int j = 1; j < d; ++j) {
+            float w = ph[j] - pl[j];
+            if (w > wbest) {
+                wbest = w;
+                js = j;
+            }
+        }
+        volatile float sum = pl[js] + ph[js];
+        volatile float mid = 0.5f * sum;
+        if (id[i] >> 63) err = -1;
+        for (int c = 0; c < 2; ++c) {
+            size_t o = (size_t)(2 * P + c);
+            memcpy(out_lo + o * d, pl, sizeof(float) * d);
+            memcpy(out_hi + o * d, ph, sizeof(float) * d);
+            if (c == 0) out_hi[o * d + js] = mid;
+            else out_lo[o * d + js] = mid;
+            out_id[o] = 2 * id[i] + (uint64_t)c;
+            out_lb[o] = lb[i];
+            out_ub[o] = ub[i];
+        }
+        ++P;
+    }
+    int R = 0;
+    for (int q = 0; q < ns; ++q) {
+        int i = surv[q];
+        if (picked[i]) continue;
+        size_t o = (size_t)(2 * P + R);
+        memcpy(out_lo + o * d, lo + (size_t)i * d, sizeof(float) * d);
+        memcpy(out_hi + o * d, hi + (size_t)i * d, sizeof(float) * d);
+        out_id[o] = id[i];
+        out_lb[o] = lb[i];
+        out_ub[o] = ub[i];
+        ++R;
+    }
+    *n_children = 2 * P;
+    *n_rest = R;
+    free(surv);
+    free(picked);
+    return err;
+}

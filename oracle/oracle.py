@@ -1,0 +1,326 @@
+"""Python face of the FP64 CPU oracle (``bab_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the checker for the CUDA library:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it.  It shares no code with the CUDA path.
+
+Each function converts its numpy inputs to the C layout (float64 for real
+inputs; the FP32 boxes stay FP32 where the method fixes FP32 arithmetic, i.e.
+the sample draw and the bisection midpoint) and calls the C routine.  The
+citations are to arXiv 2412.09584 (BaB-ND):
+
+* ``objective``     Section 3, Eq. (trajop)
+* ``rollout``       Section 3.3 (batch_search, uniform samples)
+* ``ibp``           interval intermediate bounds used by Lemma 1
+* ``crown``         Appendix B.1, Lemma 1, Theorem 1, Theorem 2 (box form)
+* ``alpha_grad``    gradient of the Theorem 1/2 bound in the Lemma 1 slopes
+* ``adam_ascent``   projected Adam on the slopes
+* ``prune_branch``  Section 3 overview (Pruner), Section 3.1 (pick out, split)
+* ``bab``           Algorithm 2 (search, bound, incumbent, prune, pick, split)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bab_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_float_p = ctypes.POINTER(ctypes.c_float)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_u64_p = ctypes.POINTER(ctypes.c_uint64)
+_c_u8_p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (strict IEEE double, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               _SRC, "-o", _LIB + ".tmp", "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.oracle_objective.restype = ctypes.c_double
+        L.oracle_splitmix64.restype = ctypes.c_uint64
+        L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
+        L.oracle_sample.restype = ctypes.c_float
+        L.oracle_sample.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                    ctypes.c_float, ctypes.c_float]
+        L.oracle_sq_tangent.restype = ctypes.c_double
+        L.oracle_sq_tangent.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.oracle_sq_chord.restype = ctypes.c_double
+        L.oracle_sq_chord.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.oracle_relu_relax.restype = None
+        L.oracle_relu_relax.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        _c_double_p, _c_double_p]
+        L.oracle_adam_ascent.restype = None
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_c_double_p)
+
+
+def _f(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_c_float_p)
+
+
+def _optd(a):
+    if a is None:
+        return None, None
+    return _d(a)
+
+
+class Net:
+    """Network shape and packed parameters (W_1, b_1, ..., W_L, b_L)."""
+
+    def __init__(self, dims, params, s, k):
+        self.dims = np.ascontiguousarray(dims, dtype=np.int32)
+        self.L = len(dims) - 1
+        self.params = np.ascontiguousarray(params, dtype=np.float64)
+        self.s, self.k = int(s), int(k)
+        self.sumh = int(sum(dims[1:-1]))
+
+    def cargs(self):
+        return (ctypes.c_int(self.L), self.dims.ctypes.data_as(_c_int_p), self.params.ctypes.data_as(_c_double_p),
+                ctypes.c_int(self.s), ctypes.c_int(self.k))
+
+
+def net_of(problem) -> Net:
+    return Net(problem["dims"], problem["params"], problem["s"], problem["k"])
+
+
+def _prob(problem):
+    net = net_of(problem)
+    x0, px0 = _d(problem["x0"])
+    g, pg = _d(problem["goal"])
+    return net, (x0, g), (ctypes.c_int(int(problem["H"])), ctypes.c_double(float(problem["rho"])), px0, pg)
+
+
+def objective(problem, u, with_traj=False):
+    """f(u) in FP64 (Section 3, Eq. trajop); optionally the trajectory and hidden pre-activations."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    u, pu = _d(u)
+    H = int(problem["H"])
+    traj = np.zeros((H + 1, net.s)) if with_traj else None
+    pre = np.zeros((H, max(net.sumh, 1))) if with_traj else None
+    f = lib().oracle_objective(*net.cargs(), cH, crho, px0, pg, pu,
+                               traj.ctypes.data_as(_c_double_p) if with_traj else None,
+                               pre.ctypes.data_as(_c_double_p) if with_traj else None)
+    if with_traj:
+        return f, traj, pre[:, :net.sumh]
+    return f
+
+
+def sample(seed, box_id, m, j, lo, hi):
+    return lib().oracle_sample(seed, box_id, m, j, lo, hi)
+
+
+def rollout(problem, lo, hi, ids, samples, seed):
+    """Best of `samples` uniform samples per box (Section 3.3): (ub FP64, best_u FP32, best_m)."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _f(lo)
+    hi, phi = _f(hi)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    n, d = lo.shape
+    ub = np.zeros(n)
+    best_u = np.zeros((n, d), dtype=np.float32)
+    best_m = np.zeros(n, dtype=np.int32)
+    rc = lib().oracle_rollout(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi,
+                              ids.ctypes.data_as(_c_u64_p), ctypes.c_int(samples), ctypes.c_uint64(seed),
+                              ub.ctypes.data_as(_c_double_p), best_u.ctypes.data_as(_c_float_p),
+                              best_m.ctypes.data_as(_c_int_p))
+    assert rc == 0
+    return ub, best_u, best_m
+
+
+def ibp(problem, lo, hi):
+    """Interval bounds: (lb_ibp [n], pre_lo/pre_hi [n,H,sumh], x_lo/x_hi [n,H+1,s])."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _d(lo)
+    hi, phi = _d(hi)
+    n = lo.shape[0]
+    H = int(problem["H"])
+    pl = np.zeros((n, H, max(net.sumh, 1)))
+    pu = np.zeros_like(pl)
+    xl = np.zeros((n, H + 1, net.s))
+    xu = np.zeros_like(xl)
+    lb = np.zeros(n)
+    rc = lib().oracle_ibp(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi,
+                          pl.ctypes.data_as(_c_double_p), pu.ctypes.data_as(_c_double_p),
+                          xl.ctypes.data_as(_c_double_p), xu.ctypes.data_as(_c_double_p),
+                          lb.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return lb, pl[:, :, :net.sumh], pu[:, :, :net.sumh], xl, xu
+
+
+def crown(problem, lo, hi, alpha=None):
+    """CROWN bound per box (Appendix B.1): dict with lb, lin_coef, lin_const, ustar, A_pre."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _d(lo)
+    hi, phi = _d(hi)
+    n, d = lo.shape
+    H = int(problem["H"])
+    alpha_a, palpha = _optd(alpha)
+    lb = np.zeros(n)
+    mu = np.zeros((n, d))
+    cst = np.zeros(n)
+    us = np.zeros((n, d))
+    Ap = np.zeros((n, H, max(net.sumh, 1)))
+    rc = lib().oracle_crown(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi, palpha,
+                            lb.ctypes.data_as(_c_double_p), mu.ctypes.data_as(_c_double_p),
+                            cst.ctypes.data_as(_c_double_p), us.ctypes.data_as(_c_double_p),
+                            Ap.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return {"lb": lb, "lin_coef": mu, "lin_const": cst, "ustar": us, "A_pre": Ap[:, :, :net.sumh]}
+
+
+def alpha_grad(problem, lo, hi, alpha=None):
+    """(lb, dlb/dalpha [n,H,sumh], relaxed-network objective at u*) per box."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _d(lo)
+    hi, phi = _d(hi)
+    n, d = lo.shape
+    H = int(problem["H"])
+    alpha_a, palpha = _optd(alpha)
+    lb = np.zeros(n)
+    g = np.zeros((n, H, max(net.sumh, 1)))
+    robj = np.zeros(n)
+    rc = lib().oracle_alpha_grad(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi, palpha,
+                                 lb.ctypes.data_as(_c_double_p), g.ctypes.data_as(_c_double_p),
+                                 robj.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return lb, g[:, :, :net.sumh], robj
+
+
+def adaptive_alpha(problem, lo, hi):
+    """The adaptive lower slopes (1 where u >= -l, else 0) of every neuron, from the oracle's IBP bounds."""
+    _, pl, pu, _, _ = ibp(problem, lo, hi)
+    return np.where(pu >= -pl, 1.0, 0.0)
+
+
+def adam_ascent(param, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, clamp=(0.0, 1.0)):
+    """One projected Adam ascent step, in place on float64 arrays."""
+    for a in (param, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    lib().oracle_adam_ascent(ctypes.c_int(param.size), param.ctypes.data_as(_c_double_p),
+                             m.ctypes.data_as(_c_double_p), v.ctypes.data_as(_c_double_p),
+                             grad.ctypes.data_as(_c_double_p), ctypes.c_int(step), ctypes.c_double(lr),
+                             ctypes.c_double(beta1), ctypes.c_double(beta2), ctypes.c_double(eps),
+                             ctypes.c_double(clamp[0]), ctypes.c_double(clamp[1]))
+
+
+def alpha_optimize(problem, lo, hi, steps, lr, alpha0=None):
+    """`steps` rounds of (bound and gradient at alpha, keep the best bound, Adam ascent step)."""
+    alpha = adaptive_alpha(problem, lo, hi) if alpha0 is None else np.array(alpha0, dtype=np.float64)
+    alpha = np.ascontiguousarray(alpha)
+    m = np.zeros_like(alpha)
+    v = np.zeros_like(alpha)
+    best = np.full(alpha.shape[0], -np.inf)
+    for step in range(1, steps + 1):
+        lb, g, _ = alpha_grad(problem, lo, hi, alpha)
+        best = np.maximum(best, lb)
+        adam_ascent(alpha, m, v, g, step, lr)
+    return best, alpha, m, v
+
+
+def relu_relax(l, u, alpha, which):
+    D = ctypes.c_double()
+    c = ctypes.c_double()
+    lib().oracle_relu_relax(l, u, alpha, which, ctypes.byref(D), ctypes.byref(c))
+    return D.value, c.value
+
+
+def sq_tangent(m, s):
+    return lib().oracle_sq_tangent(m, s)
+
+
+def sq_chord(L, U, s):
+    return lib().oracle_sq_chord(L, U, s)
+
+
+def prune_branch(lo, hi, lb, ub, ids, inc_val, n_pick, eta=0.75):
+    """Prune, pick out, bisect (see bab_oracle.c). Returns dict of outputs."""
+    lo, plo = _f(lo)
+    hi, phi = _f(hi)
+    lb, plb = _f(lb)
+    ub, pub = _f(ub)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    n, d = lo.shape
+    cap = 2 * n + 1
+    out_lo = np.zeros((cap, d), dtype=np.float32)
+    out_hi = np.zeros_like(out_lo)
+    out_lb = np.zeros(cap, dtype=np.float32)
+    out_ub = np.zeros(cap, dtype=np.float32)
+    out_id = np.zeros(cap, dtype=np.uint64)
+    keep = np.zeros(max(n, 1), dtype=np.uint8)
+    nc = ctypes.c_int()
+    nr = ctypes.c_int()
+    rc = lib().oracle_prune_branch(ctypes.c_int(n), ctypes.c_int(d), plo, phi, plb, pub,
+                                   ids.ctypes.data_as(_c_u64_p), ctypes.c_double(inc_val), ctypes.c_int(n_pick),
+                                   ctypes.c_double(eta), out_lo.ctypes.data_as(_c_float_p),
+                                   out_hi.ctypes.data_as(_c_float_p), out_lb.ctypes.data_as(_c_float_p),
+                                   out_ub.ctypes.data_as(_c_float_p), out_id.ctypes.data_as(_c_u64_p),
+                                   keep.ctypes.data_as(_c_u8_p), ctypes.byref(nc), ctypes.byref(nr))
+    m = nc.value + nr.value
+    return {"rc": rc, "keep": keep[:n], "n_children": nc.value, "n_rest": nr.value, "lo": out_lo[:m],
+            "hi": out_hi[:m], "lb": out_lb[:m], "ub": out_ub[:m], "id": out_id[:m]}
+
+
+def bab(problem, lo, hi, ids, iters, n_pick, samples, seed, alpha_steps=0, alpha_lr=0.1, eta=0.75):
+    """Algorithm 2 on the host: search and bound the initial boxes, then per iteration prune the pool
+    against the incumbent, pick out and split, search and bound the children, update the incumbent.
+
+    Returns (inc_val, inc_u, history) where history holds one dict per iteration."""
+    lo = np.asarray(lo, dtype=np.float32)
+    hi = np.asarray(hi, dtype=np.float32)
+    ids = np.asarray(ids, dtype=np.uint64)
+    inc_val, inc_u = np.inf, None
+
+    def search_and_bound(lo, hi, ids):
+        nonlocal inc_val, inc_u
+        ub, bu, _ = rollout(problem, lo, hi, ids, samples, seed)
+        if alpha_steps > 0:
+            lb, *_ = alpha_optimize(problem, lo, hi, alpha_steps, alpha_lr)
+        else:
+            lb = crown(problem, lo, hi)["lb"]
+        if len(ub):
+            i = int(np.argmin(ub))
+            if ub[i] < inc_val:
+                inc_val, inc_u = float(ub[i]), bu[i].copy()
+        return lb.astype(np.float32), ub.astype(np.float32)
+
+    lb, ub = search_and_bound(lo, hi, ids)
+    hist = []
+    for it in range(iters):
+        out = prune_branch(lo, hi, lb, ub, ids, inc_val, n_pick, eta)
+        nc = out["n_children"]
+        lo, hi, ids = out["lo"], out["hi"], out["id"]
+        lb, ub = out["lb"].copy(), out["ub"].copy()
+        if nc:
+            clb, cub = search_and_bound(lo[:nc], hi[:nc], ids[:nc])
+            lb[:nc], ub[:nc] = clb, cub
+        live_lb = float(np.min(lb)) if len(lb) else np.inf
+        hist.append({"iter": it, "pool": len(lb), "children": nc, "pruned": int((out["keep"] == 0).sum()),
+                     "inc_val": inc_val, "global_lb": live_lb})
+        if len(lb) == 0:
+            break
+    return inc_val, inc_u, hist

@@ -1,0 +1,530 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+test vectors, hand-worked examples (tests/golden), closed forms, vertex brute
+force, dense grids, finite differences, or an independent library routine.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2412_09584_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def hand_problem():
+    g = json.load(open(os.path.join(GOLDEN, "hand_crown.json")))
+    n = g["network"]
+    layers = [(np.array(n["W1"]), np.array(n["b1"])), (np.array(n["W2"]), np.array(n["b2"]))]
+    p = dict(dims=n["dims"], params=W.pack_params(layers), x0=np.array(g["x0"], dtype=np.float32),
+             goal=np.array(g["goal"], dtype=np.float32), H=g["H"], rho=g["rho"], s=1, k=1)
+    return p, g
+
+
+def scaled_problem(s, k, hidden, H, rho, seed, scale=1.0, bias_shift=None):
+    """A random problem; scale multiplies the weights, bias_shift (per hidden layer) is added to biases."""
+    p = W.make_problem(s, k, hidden, H, rho, seed, weight_scale=scale)
+    layers = W.unpack_params(p)
+    if bias_shift is not None:
+        layers = [(Wl, bl + (bias_shift[i] if i < len(layers) - 1 else 0.0)) for i, (Wl, bl) in enumerate(layers)]
+    p["params"] = W.pack_params([(Wl.astype(np.float64), bl.astype(np.float64)) for Wl, bl in layers])
+    return p
+
+
+# --------------------------------------------------------------------------
+# Counter-based sampler: SplitMix64 published reference sequence
+# --------------------------------------------------------------------------
+
+def test_splitmix64_reference_sequence(oracle):
+    # Reference outputs of SplitMix64 seeded with 1234567 (the test vector
+    # published with the generator's reference C implementation).
+    expect = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+              16408922859458223821]
+    gamma = 0x9E3779B97F4A7C15
+    x = 1234567
+    got = []
+    for _ in range(5):
+        got.append(oracle.lib().oracle_splitmix64(x))
+        x = (x + gamma) % (1 << 64)
+    assert got == expect
+
+
+def test_samples_fp32_formula_and_range(oracle):
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        lo = np.float32(rng.uniform(-1, 0.5))
+        hi = np.float32(lo + rng.uniform(0, 1))
+        u = oracle.sample(11, 12345, int(rng.integers(0, 4096)), int(rng.integers(0, 160)), lo, hi)
+        assert lo <= u <= hi
+    # the draw is r = (top 24 bits) / 2^24 of the chained hash; u = lo + (hi-lo)*r in FP32
+    sm = oracle.lib().oracle_splitmix64
+    seed, bid, m, j = 5, 77, 3, 9
+    h = sm(seed ^ sm(bid))
+    h = sm(h ^ ((m << 32) | j))
+    r = np.float32(h >> 40) * np.float32(1.0 / 16777216.0)
+    lo, hi = np.float32(-0.75), np.float32(0.5)
+    assert oracle.sample(seed, bid, m, j, lo, hi) == np.float32(lo + np.float32(np.float32(hi - lo) * r))
+    # zero-width interval returns the point
+    assert oracle.sample(1, 2, 3, 4, np.float32(0.25), np.float32(0.25)) == np.float32(0.25)
+
+
+# --------------------------------------------------------------------------
+# Objective (Section 3, Eq. trajop)
+# --------------------------------------------------------------------------
+
+def test_objective_hand_example(oracle):
+    p, g = hand_problem()
+    for pt in g["objective_points"]:
+        assert oracle.objective(p, np.array(pt["u"])) == pytest.approx(pt["f"], rel=1e-14)
+
+
+def test_objective_all_active_closed_form(oracle):
+    """All ReLUs active: the dynamics are affine, x_{t+1} = (I + Wx) x_t + Wu u_t + c, and f is a quadratic
+    evaluated here by plain matrix algebra."""
+    s, k, H, rho = 3, 2, 4, 0.05
+    rng = np.random.default_rng(9)
+    # layer 1 biased far positive; layer 2 has nonnegative weights and bias, so every ReLU is active
+    layers = [(rng.normal(size=(8, s + k)), np.full(8, 50.0)),
+              (rng.uniform(0, 0.1, size=(8, 8)), np.full(8, 1.0)),
+              (0.01 * rng.normal(size=(s, 8)), 0.1 * rng.normal(size=s))]
+    p = dict(dims=[s + k, 8, 8, s], params=W.pack_params(layers), x0=rng.normal(size=s).astype(np.float32),
+             goal=rng.normal(size=s).astype(np.float32), H=H, rho=rho, s=s, k=k)
+    layers = [(Wl.astype(np.float64), bl.astype(np.float64)) for Wl, bl in W.unpack_params(p)]
+    Weff = np.eye(s + k)
+    beff = np.zeros(s + k)
+    for Wl, bl in layers:
+        beff = Wl @ beff + bl
+        Weff = Wl @ Weff
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        u = rng.uniform(-1, 1, size=k * H)
+        x = p["x0"].astype(np.float64)
+        f = 0.0
+        for t in range(H):
+            ut = u[t * k:(t + 1) * k]
+            x = x + Weff[:, :s] @ x + Weff[:, s:] @ ut + beff
+            f += np.sum((x - p["goal"]) ** 2) + rho * np.sum(ut ** 2)
+        fo, traj, pre = oracle.objective(p, u, with_traj=True)
+        assert (pre > 0).all()
+        assert fo == pytest.approx(f, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Rollout (Section 3.3)
+# --------------------------------------------------------------------------
+
+def test_rollout_is_min_over_its_samples(oracle):
+    p = scaled_problem(4, 2, [16, 16], 3, 0.01, seed=2, scale=1.0)
+    lo, hi, ids = W.random_boxes(6, 5, seed=4, min_width=0.1, max_width=1.0)
+    M, seed = 40, 99
+    ub, best_u, best_m = oracle.rollout(p, lo, hi, ids, M, seed)
+    for i in range(5):
+        vals = []
+        for m in range(M):
+            u = np.array([oracle.sample(seed, int(ids[i]), m, j, lo[i, j], hi[i, j]) for j in range(6)],
+                         dtype=np.float32)
+            assert (u >= lo[i]).all() and (u <= hi[i]).all()
+            vals.append(oracle.objective(p, u.astype(np.float64)))
+        assert ub[i] == min(vals)
+        assert best_m[i] == int(np.argmin(vals))
+        assert oracle.objective(p, best_u[i].astype(np.float64)) == ub[i]
+
+
+def test_rollout_zero_width_box(oracle):
+    p = W.config_problem("tiny", 1)
+    lo, hi, ids = W.random_boxes(10, 3, seed=1, min_width=0.0, max_width=0.0)
+    ub, best_u, _ = oracle.rollout(p, lo, hi, ids, 8, 1)
+    for i in range(3):
+        assert (best_u[i] == lo[i]).all()
+        assert ub[i] == oracle.objective(p, lo[i].astype(np.float64))
+
+
+# --------------------------------------------------------------------------
+# IBP intermediate bounds
+# --------------------------------------------------------------------------
+
+def test_ibp_contains_sampled_trajectories(oracle):
+    p = scaled_problem(4, 2, [16, 16], 4, 0.01, seed=8, scale=1.0)
+    lo, hi, ids = W.random_boxes(8, 6, seed=9, min_width=0.05, max_width=1.5)
+    lb, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    rng = np.random.default_rng(1)
+    for i in range(6):
+        for _ in range(300):
+            u = lo[i] + rng.uniform(size=8) * (hi[i] - lo[i])
+            f, traj, pre = oracle.objective(p, u, with_traj=True)
+            assert (pre >= pl[i] - 1e-12).all() and (pre <= pu[i] + 1e-12).all()
+            assert (traj >= xl[i] - 1e-12).all() and (traj <= xu[i] + 1e-12).all()
+            assert lb[i] <= f + 1e-12
+
+
+def test_ibp_zero_width_box_is_forward_pass(oracle):
+    p = W.config_problem("tiny", 3)
+    lo, hi, _ = W.random_boxes(10, 2, seed=2, min_width=0.0, max_width=0.0)
+    lb, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    for i in range(2):
+        f, traj, pre = oracle.objective(p, lo[i].astype(np.float64), with_traj=True)
+        np.testing.assert_allclose(pl[i], pre, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(pu[i], pre, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(xl[i], traj, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(xu[i], traj, rtol=0, atol=1e-13)
+        assert lb[i] == pytest.approx(f, rel=1e-13)
+
+
+def test_ibp_single_affine_layer_exact_range(oracle):
+    """With no hidden layer and H=1, each coordinate of x_1 is affine in u, so the interval bound is the exact
+    range, which vertex enumeration gives."""
+    s, k = 3, 6
+    p = scaled_problem(s, k, [], 1, 0.0, seed=12, scale=1.0)
+    lo, hi, _ = W.random_boxes(k, 4, seed=13, min_width=0.1, max_width=1.2)
+    lb, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    for i in range(4):
+        vals = []
+        for bits in itertools.product([0, 1], repeat=k):
+            u = np.where(np.array(bits) == 1, hi[i], lo[i]).astype(np.float64)
+            _, traj, _ = oracle.objective(p, u, with_traj=True)
+            vals.append(traj[1])
+        vals = np.array(vals)
+        np.testing.assert_allclose(xl[i, 1], vals.min(axis=0), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(xu[i, 1], vals.max(axis=0), rtol=1e-12, atol=1e-12)
+
+
+def test_ibp_hand_example(oracle):
+    p, g = hand_problem()
+    lo = np.array([g["box"]["lo"]], dtype=np.float32)
+    hi = np.array([g["box"]["hi"]], dtype=np.float32)
+    lb, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    e = g["ibp"]
+    assert pl[0, 0, 0] == e["pre_lo"] and pu[0, 0, 0] == e["pre_hi"]
+    assert xl[0, 1, 0] == e["x1_lo"] and xu[0, 1, 0] == e["x1_hi"]
+    assert lb[0] == pytest.approx(e["lb_ibp"], rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Relaxations: tangent / chord of s^2, Lemma 1
+# --------------------------------------------------------------------------
+
+def test_square_tangent_and_chord(oracle):
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        L = rng.uniform(-3, 3)
+        U = L + rng.uniform(0, 4)
+        m = 0.5 * (L + U)
+        assert oracle.sq_tangent(m, m) == pytest.approx(m * m, abs=1e-14)
+        assert oracle.sq_chord(L, U, L) == pytest.approx(L * L, abs=1e-12)
+        assert oracle.sq_chord(L, U, U) == pytest.approx(U * U, abs=1e-12)
+        for sv in np.linspace(L, U, 41):
+            assert oracle.sq_tangent(m, sv) <= sv * sv + 1e-12
+            assert oracle.sq_chord(L, U, sv) >= sv * sv - 1e-12
+
+
+def test_relu_relaxation_lemma1(oracle):
+    cases = [(-2.0, 3.0), (-3.0, 1.0), (0.5, 2.0), (0.0, 1.0), (-2.0, -0.5), (-1.0, 0.0)]
+    for l, u in cases:
+        zs = np.linspace(l, u, 101)
+        for a in (0.0, 0.3, 1.0):
+            Dl, cl = oracle.relu_relax(l, u, a, 0)
+            Du, cu = oracle.relu_relax(l, u, a, 1)
+            relu = np.maximum(zs, 0)
+            assert (Dl * zs + cl <= relu + 1e-12).all()
+            assert (Du * zs + cu >= relu - 1e-12).all()
+        if l < 0 < u:
+            Du, cu = oracle.relu_relax(l, u, 0.5, 1)
+            assert Du * l + cu == pytest.approx(0.0, abs=1e-12)       # chord touches at l
+            assert Du * u + cu == pytest.approx(u, abs=1e-12)         # and at u
+            assert oracle.relu_relax(l, u, 0.3, 0) == (0.3, 0.0)
+        elif l >= 0:
+            assert oracle.relu_relax(l, u, 0.3, 0) == (1.0, 0.0) == oracle.relu_relax(l, u, 0.3, 1)
+        else:
+            assert oracle.relu_relax(l, u, 0.3, 0) == (0.0, 0.0) == oracle.relu_relax(l, u, 0.3, 1)
+
+
+# --------------------------------------------------------------------------
+# CROWN bound (Appendix B.1)
+# --------------------------------------------------------------------------
+
+def test_crown_hand_example(oracle):
+    p, g = hand_problem()
+    lo = np.array([g["box"]["lo"]], dtype=np.float32)
+    hi = np.array([g["box"]["hi"]], dtype=np.float32)
+    r = oracle.crown(p, lo, hi)
+    e = g["crown_adaptive"]
+    assert r["lb"][0] == pytest.approx(e["lb"], rel=1e-14)
+    assert r["lin_coef"][0, 0] == pytest.approx(e["lin_coef"][0], rel=1e-14)
+    assert r["lin_const"][0] == pytest.approx(e["lin_const"], rel=1e-14)
+    assert r["ustar"][0, 0] == e["ustar"][0]
+    r0 = oracle.crown(p, lo, hi, alpha=np.zeros((1, 1, 1)))
+    assert r0["lb"][0] == pytest.approx(g["crown_alpha0"]["lb"], rel=1e-14)
+    lb, grad, _ = oracle.alpha_grad(p, lo, hi, alpha=np.ones((1, 1, 1)))
+    assert grad[0, 0, 0] == pytest.approx(g["alpha_grad_at_1"]["grad"], rel=1e-14)
+
+
+def test_crown_zero_width_box_equals_objective(oracle):
+    for name, seed in (("tiny", 4), ("pushing", 5)):
+        p = W.config_problem(name, seed)
+        d = p["k"] * p["H"]
+        lo, hi, _ = W.random_boxes(d, 2, seed=seed, min_width=0.0, max_width=0.0)
+        r = oracle.crown(p, lo, hi)
+        for i in range(2):
+            f = oracle.objective(p, lo[i].astype(np.float64))
+            assert r["lb"][i] == pytest.approx(f, rel=1e-11)
+
+
+def test_crown_sound_on_dense_grid_tiny_boxes(oracle):
+    """3^10 grid points inside each of two small boxes of the tiny workload (scaled-up weights so that ReLUs
+    are unstable); the bound must not exceed any of them."""
+    p = scaled_problem(4, 2, [32, 32], 5, 0.0, seed=21, scale=3.0)
+    lo, hi, _ = W.random_boxes(10, 2, seed=22, min_width=0.02, max_width=0.08)
+    r = oracle.crown(p, lo, hi)
+    _, pl, pu, _, _ = oracle.ibp(p, lo, hi)
+    assert ((pl < 0) & (pu > 0)).sum() > 0, "test needs unstable neurons"
+    for i in range(2):
+        axes = [np.linspace(lo[i, j], hi[i, j], 3) for j in range(10)]
+        fmin = np.inf
+        for pt in itertools.product(*axes):
+            fmin = min(fmin, oracle.objective(p, np.array(pt)))
+        assert r["lb"][i] <= fmin + 1e-12
+
+
+def test_crown_sound_random_points_large_boxes(oracle):
+    p = scaled_problem(8, 2, [64, 64, 64], 6, 0.01, seed=23, scale=2.0)
+    lo, hi, _ = W.random_boxes(12, 4, seed=24, min_width=0.5, max_width=2.0)
+    r = oracle.crown(p, lo, hi)
+    lbi = oracle.ibp(p, lo, hi)[0]
+    rng = np.random.default_rng(2)
+    for i in range(4):
+        for _ in range(400):
+            u = lo[i] + rng.uniform(size=12) * (hi[i] - lo[i])
+            f = oracle.objective(p, u)
+            assert r["lb"][i] <= f + 1e-10
+            assert lbi[i] <= f + 1e-10
+        # the linear function itself is below f at every sample
+        for _ in range(50):
+            u = lo[i] + rng.uniform(size=12) * (hi[i] - lo[i])
+            lin = r["lin_const"][i] + r["lin_coef"][i] @ u + p["rho"] * np.sum(u * u)
+            assert lin <= oracle.objective(p, u) + 1e-10
+            assert lin >= r["lb"][i] - 1e-10
+
+
+def _tangent_linear_objective(oracle, p, lo, hi, u):
+    """sum_t sum_i [2 m (x_t,i(u) - g_i) - m^2] + rho ||u||^2, the objective with each square replaced by its
+    tangent at the midpoint m of its interval bound, evaluated through the true forward pass."""
+    _, _, _, xl, xu = oracle.ibp(p, lo[None], hi[None])
+    f, traj, _ = oracle.objective(p, u, with_traj=True)
+    m = 0.5 * ((xl[0] - p["goal"]) + (xu[0] - p["goal"]))
+    val = 0.0
+    for t in range(1, p["H"] + 1):
+        val += np.sum(2 * m[t] * (traj[t] - p["goal"]) - m[t] ** 2)
+    return val + p["rho"] * np.sum(u * u)
+
+
+def stable_problem(s, k, H, seed, frac_active1, frac_active2):
+    """A network whose ReLUs are all stable for |x|, |u| of order 1: layer-1 biases are +-50, layer-2 weights
+    are nonnegative with biases +1 (active) or -1000 (inactive), and the output layer is small."""
+    rng = np.random.default_rng(seed)
+    b1 = np.where(rng.uniform(size=12) < frac_active1, 50.0, -50.0)
+    b2 = np.where(rng.uniform(size=12) < frac_active2, 1.0, -1000.0)
+    layers = [(rng.normal(size=(12, s + k)), b1), (rng.uniform(0, 0.1, size=(12, 12)), b2),
+              (0.05 * rng.normal(size=(s, 12)), 0.1 * rng.normal(size=s))]
+    return dict(dims=[s + k, 12, 12, s], params=W.pack_params(layers), x0=rng.normal(size=s).astype(np.float32),
+                goal=rng.normal(size=s).astype(np.float32), H=H, rho=0.0, s=s, k=k)
+
+
+@pytest.mark.parametrize("fracs", [(1.0, 1.0), (0.5, 1.0), (0.6, 0.5)])
+def test_crown_stable_network_gives_exact_linear_bound(oracle, fracs):
+    """With every ReLU stable on the box the network is affine there, so the bound's linear function must
+    equal the tangent-linearised objective at every point, and (rho = 0) its minimum over the box is the
+    minimum over the 2^d vertices."""
+    s, k, H = 3, 2, 4
+    p = stable_problem(s, k, H, 31, *fracs)
+    lo, hi, _ = W.random_boxes(k * H, 2, seed=32, min_width=0.2, max_width=1.0)
+    _, pl, pu, _, _ = oracle.ibp(p, lo, hi)
+    assert not ((pl < 0) & (pu > 0)).any()
+    r = oracle.crown(p, lo, hi)
+    rng = np.random.default_rng(5)
+    for i in range(2):
+        for _ in range(20):
+            u = lo[i] + rng.uniform(size=k * H) * (hi[i] - lo[i])
+            lin = r["lin_const"][i] + r["lin_coef"][i] @ u
+            ref = _tangent_linear_objective(oracle, p, lo[i], hi[i], u)
+            assert lin == pytest.approx(ref, rel=1e-11, abs=1e-11)
+        best = np.inf
+        for bits in itertools.product([0, 1], repeat=k * H):
+            u = np.where(np.array(bits) == 1, hi[i], lo[i]).astype(np.float64)
+            best = min(best, _tangent_linear_objective(oracle, p, lo[i], hi[i], u))
+        assert r["lb"][i] == pytest.approx(best, rel=1e-11, abs=1e-11)
+
+
+def test_crown_any_alpha_is_sound_and_relaxed_identity(oracle):
+    p = scaled_problem(4, 2, [32, 32], 5, 0.01, seed=41, scale=3.0)
+    lo, hi, _ = W.random_boxes(10, 3, seed=42, min_width=0.1, max_width=0.6)
+    rng = np.random.default_rng(6)
+    alpha = rng.uniform(0, 1, size=(3, 5, 64))
+    lb, g, robj = oracle.alpha_grad(p, lo, hi, alpha)
+    np.testing.assert_allclose(robj, lb, rtol=1e-12, atol=1e-12)
+    for i in range(3):
+        for _ in range(200):
+            u = lo[i] + rng.uniform(size=10) * (hi[i] - lo[i])
+            assert lb[i] <= oracle.objective(p, u) + 1e-10
+
+
+# --------------------------------------------------------------------------
+# alpha gradient: central finite differences
+# --------------------------------------------------------------------------
+
+def test_alpha_gradient_central_fd(oracle):
+    # weights and box sized so that the bound is O(1): the stencil difference is then far above FP64 rounding
+    p = scaled_problem(4, 2, [32, 32], 5, 0.01, seed=51, scale=0.3)
+    lo, hi, _ = W.random_boxes(10, 4, seed=52, min_width=0.5, max_width=1.0)
+    rng = np.random.default_rng(7)
+    alpha = rng.uniform(0.05, 0.95, size=(4, 5, 64))
+    lb, g, _ = oracle.alpha_grad(p, lo, hi, alpha)
+    Ap = oracle.crown(p, lo, hi, alpha)["A_pre"]
+    _, pl, pu, _, _ = oracle.ibp(p, lo, hi)
+    unstable = (pl < 0) & (pu > 0)
+    # zero gradient where the slope is unused: stable neurons, or upper bound selected
+    assert (g[~unstable] == 0).all()
+    assert (g[unstable & (Ap < 0)] == 0).all()
+    cand = np.argwhere(unstable & (Ap > 0))
+    assert len(cand) >= 16
+    eps = 1e-4
+    checked = 0
+    for c in cand[rng.permutation(len(cand))]:
+        i, t, j = c
+        ap, am = alpha.copy(), alpha.copy()
+        ap[i, t, j] += eps
+        am[i, t, j] -= eps
+        rp = oracle.crown(p, lo[i:i + 1], hi[i:i + 1], ap[i:i + 1])
+        rm = oracle.crown(p, lo[i:i + 1], hi[i:i + 1], am[i:i + 1])
+        if not (np.sign(rp["A_pre"]) == np.sign(rm["A_pre"])).all() or \
+                not (np.sign(rp["A_pre"]) == np.sign(Ap[i:i + 1])).all():
+            continue  # a relaxation selection flips inside the stencil: kink, skip
+        clamp_p = (rp["ustar"] == lo[i:i + 1]) | (rp["ustar"] == hi[i:i + 1])
+        clamp_m = (rm["ustar"] == lo[i:i + 1]) | (rm["ustar"] == hi[i:i + 1])
+        if not (clamp_p == clamp_m).all():
+            continue  # the concretizing point changes face inside the stencil: kink, skip
+        fp, fm = rp["lb"][0], rm["lb"][0]
+        fd = (fp - fm) / (2 * eps)
+        assert g[i, t, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+        checked += 1
+        if checked == 16:
+            break
+    assert checked == 16
+
+
+# --------------------------------------------------------------------------
+# Adam (independent library implementation)
+# --------------------------------------------------------------------------
+
+def test_adam_matches_torch_maximize_with_clamp(oracle):
+    import torch
+    rng = np.random.default_rng(8)
+    x0 = rng.uniform(0, 1, size=50)
+    p_t = torch.tensor(x0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p_t], lr=0.1, betas=(0.9, 0.999), eps=1e-8, maximize=True)
+    param = x0.copy()
+    m = np.zeros(50)
+    v = np.zeros(50)
+    for step in range(1, 21):
+        g = rng.normal(size=50)
+        p_t.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        with torch.no_grad():
+            p_t.clamp_(0.0, 1.0)
+        oracle.adam_ascent(param, m, v, g, step, 0.1)
+        np.testing.assert_allclose(param, p_t.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Prune / pick out / split (Section 3 overview, Section 3.1)
+# --------------------------------------------------------------------------
+
+def test_prune_branch_hand_cases(oracle):
+    d = 3
+    lo = np.array([[-1, -1, -1], [0, -1, -1], [-1, 0, -1], [0, 0, -1], [-0.5, -1, 0]], dtype=np.float32)
+    hi = np.array([[0, 1, 1], [1, 1, 1], [1, 1, 0], [1, 1, 0], [0, 0, 1]], dtype=np.float32)
+    ids = np.array([8, 9, 10, 11, 12], dtype=np.uint64)
+    lb = np.array([1.0, 5.0, np.nan, 3.0, 3.0], dtype=np.float32)
+    ub = np.array([2.0, 6.0, 9.0, 4.0, 3.5], dtype=np.float32)
+    # inc 3.0: box 1 pruned (5 > 3); NaN kept; lb == inc kept (strict comparison)
+    r = oracle.prune_branch(lo, hi, lb, ub, ids, 3.0, n_pick=8)
+    assert list(r["keep"]) == [1, 0, 1, 1, 1]
+    assert r["n_children"] == 8 and r["n_rest"] == 0
+    # box 0 widths (1,2,2): dim 1 (lowest index among the widest); mid 0
+    np.testing.assert_array_equal(r["lo"][0], [-1, -1, -1]); np.testing.assert_array_equal(r["hi"][0], [0, 0, 1])
+    np.testing.assert_array_equal(r["lo"][1], [-1, 0, -1]); np.testing.assert_array_equal(r["hi"][1], [0, 1, 1])
+    assert list(r["id"][:2]) == [16, 17]
+    # box 2 widths (2,1,1): dim 0 at 0
+    np.testing.assert_array_equal(r["hi"][2], [0, 1, 0]); np.testing.assert_array_equal(r["lo"][3], [0, 0, -1])
+    # box 4 widths (0.5,1,1): dim 1 at -0.5
+    np.testing.assert_array_equal(r["hi"][6], [0, -0.5, 1]); np.testing.assert_array_equal(r["lo"][7], [-0.5, -0.5, 0])
+    assert list(r["id"]) == [16, 17, 20, 21, 22, 23, 24, 25]
+    assert list(r["lb"][:2]) == [1.0, 1.0]
+
+    # pick-out over capacity: n_pick=2, eta=0.75 -> ceil(1.5)=2 by (ub, id): boxes 0 (ub 2) and 4 (ub 3.5)
+    r = oracle.prune_branch(lo, hi, lb, ub, ids, 3.0, n_pick=2)
+    assert r["n_children"] == 4 and r["n_rest"] == 2
+    assert list(r["id"]) == [16, 17, 24, 25, 10, 11]
+    # n_pick=3, eta=0.5 -> 2 by ub (boxes 0, 4), then 1 by (lb, id) among {2 (NaN), 3 (lb 3)} -> box 3
+    r = oracle.prune_branch(lo, hi, lb, ub, ids, 3.0, n_pick=3, eta=0.5)
+    assert list(r["id"]) == [16, 17, 22, 23, 24, 25, 10]
+    # ub ties are broken by id
+    ub2 = np.array([2.0, 6.0, 2.0, 2.0, 2.0], dtype=np.float32)
+    r = oracle.prune_branch(lo, hi, lb, ub2, ids, 100.0, n_pick=1, eta=1.0)
+    assert list(r["id"]) == [16, 17, 9, 10, 11, 12]
+
+
+def test_prune_branch_edge_cases(oracle):
+    d = 2
+    lo = np.zeros((0, d), dtype=np.float32)
+    r = oracle.prune_branch(lo, lo, np.zeros(0, np.float32), np.zeros(0, np.float32), np.zeros(0, np.uint64),
+                            1.0, n_pick=4)
+    assert r["n_children"] == 0 and r["n_rest"] == 0
+    lo = np.array([[-1, -1], [0, 0]], dtype=np.float32)
+    hi = np.array([[1, 1], [1, 1]], dtype=np.float32)
+    r = oracle.prune_branch(lo, hi, np.array([5, 6], np.float32), np.array([7, 8], np.float32),
+                            np.array([2, 3], np.uint64), 1.0, n_pick=4)
+    assert list(r["keep"]) == [0, 0] and r["n_children"] == 0 and r["n_rest"] == 0
+    # too deep to split
+    r = oracle.prune_branch(lo[:1], hi[:1], np.array([0], np.float32), np.array([1], np.float32),
+                            np.array([1 << 63], np.uint64), 1.0, n_pick=4)
+    assert r["rc"] == -1
+
+
+def test_grid_boxes_match_repeated_bisection(oracle):
+    """The generator's initial grid equals what repeated widest-dimension bisection of [-1,1]^d produces."""
+    d, levels = 10, 6
+    lo = np.full((1, d), -1, np.float32)
+    hi = np.full((1, d), 1, np.float32)
+    ids = np.array([1], np.uint64)
+    for _ in range(levels):
+        n = len(ids)
+        r = oracle.prune_branch(lo, hi, np.zeros(n, np.float32), np.zeros(n, np.float32), ids, np.inf, n_pick=n)
+        lo, hi, ids = r["lo"], r["hi"], r["id"]
+    glo, ghi, gid = W.grid_boxes(d, levels)
+    order = np.argsort(ids)
+    gorder = np.argsort(gid)
+    np.testing.assert_array_equal(ids[order], gid[gorder])
+    np.testing.assert_array_equal(lo[order], glo[gorder])
+    np.testing.assert_array_equal(hi[order], ghi[gorder])
+
+
+# --------------------------------------------------------------------------
+# BaB end to end: brute force on a 2-D problem
+# --------------------------------------------------------------------------
+
+def test_bab_end_to_end_against_grid(oracle):
+    p = scaled_problem(2, 2, [16, 16], 1, 0.0, seed=61, scale=4.0)
+    grid = np.linspace(-1, 1, 401)
+    fgrid = min(oracle.objective(p, np.array([a, b])) for a in grid for b in grid)
+    lo = np.array([[-1, -1]], np.float32)
+    hi = np.array([[1, 1]], np.float32)
+    inc, inc_u, hist = oracle.bab(p, lo, hi, np.array([1], np.uint64), iters=25, n_pick=8, samples=16, seed=3)
+    assert oracle.objective(p, inc_u.astype(np.float64)) == inc
+    for h in hist:
+        assert h["global_lb"] <= min(fgrid, inc) + 1e-12 or h["pool"] == 0
+    # grid resolution 0.005; the objective's slope is O(10): allow 0.05 + 1e-6
+    assert inc <= fgrid + 0.05
