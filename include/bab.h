@@ -1,0 +1,238 @@
+/*
+ * bab.h -- C ABI of libbab, a GB300 (sm_103a) library for the data-parallel
+ * bounding hot path of BaB-ND: branch-and-bound planning over a learned
+ * residual ReLU-MLP dynamics model (arXiv 2412.09584).
+ *
+ * The planning problem (Section 3, "Formulation", Eq. trajop) is
+ *
+ *     min_u f(u),  f(u) = sum_{t=1..H} ||x_t - g||^2 + rho sum_{t=0..H-1} ||u_t||^2,
+ *     x_{t+1} = x_t + N([x_t; u_t]),  x_0 known,  u in C = [lo, hi] subset R^d, d = kH,
+ *
+ * where N is an L-layer ReLU MLP (ReLU after layers 1..L-1) with input size
+ * s + k (state first) and output size s.  A "box" (subdomain C_i, Section 3
+ * overview) is a pair of rows lo[d], hi[d]; actions are flattened t-major,
+ * u[t*k + j].  Branch-and-bound (Algorithm 2) repeatedly searches boxes for
+ * good plans (upper bounds), bounds them from below, prunes boxes whose lower
+ * bound exceeds the incumbent, and bisects the survivors.
+ *
+ * Conventions shared by every call:
+ *   - Return value: BAB_OK (0) or a negative BAB_ERR_* code; bab_last_error()
+ *     describes the last failure of a context.  No exception crosses the ABI.
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous and
+ *     row-major, unless the comment says "host".  They must stay valid until
+ *     the work queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is queued on it asynchronously; a call returns
+ *     before the work finishes.  A context must not be used from two host
+ *     threads at once.
+ *   - Row counts: `n` (host) is the number of boxes.  Where `d_n` is non-NULL
+ *     it points to a device int holding the live count (<= n), read by the
+ *     kernels, so that a call can be captured in a CUDA graph while the count
+ *     changes between replays; `n` then only sizes the launch.
+ *   - Scratch: the context owns its scratch device memory and grows it with
+ *     cudaMalloc on demand.  Make the first call with the largest sizes before
+ *     capturing a graph.
+ *   - Network layout (same as the oracle's): params packs, for l = 1..L,
+ *     W_l row-major [dims[l]][dims[l-1]] followed by b_l [dims[l]].
+ *   - Hidden-neuron arrays (pre-activation bounds, alpha, Adam moments) are
+ *     [n][H][sumh] with sumh = dims[1] + ... + dims[L-1]; per time step the
+ *     hidden layers are concatenated in order.
+ */
+#ifndef BAB_H
+#define BAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BAB_OK 0
+#define BAB_ERR_INVALID_ARG (-1)
+#define BAB_ERR_SHAPE (-2)
+#define BAB_ERR_CUDA (-3)
+#define BAB_ERR_OOM (-4)
+#define BAB_ERR_TIMEOUT (-5)
+#define BAB_ERR_NUMERIC (-6)
+#define BAB_ERR_UNSUPPORTED (-7)
+
+/* Arithmetic of the dense products. */
+#define BAB_PREC_FP32 0    /* FP32 on CUDA cores (round-to-nearest FMA chains) */
+#define BAB_PREC_BF16X3 1  /* tcgen05 tensor cores, 3-term BF16 split operands, FP32 accumulate */
+#define BAB_PREC_BF16 2    /* tcgen05 tensor cores, BF16 operands, FP32 accumulate (rollouts only) */
+
+/* Split rules of bab_prune_branch. */
+#define BAB_SPLIT_WIDEST 0 /* bisect the widest coordinate (Section 3.1), lowest index on ties */
+
+/* Limits of this build. */
+#define BAB_MAX_LAYERS 8
+#define BAB_MAX_WIDTH 256
+
+typedef struct bab_ctx bab_ctx;
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int bab_version(void);
+
+/*
+ * Load the dynamics network f_dyn (Section 3, Formulation; Appendix B.1,
+ * "Definition": z_l = W_l a_{l-1} + b_l, a_l = ReLU(z_l) for l < L) and create a
+ * context on the current CUDA device.
+ *   out        receives the new context (host pointer to a host pointer).
+ *   n_layers   L, 1 <= L <= BAB_MAX_LAYERS.
+ *   dims       host int[L+1]; dims[0] = state_dim + action_dim, dims[L] =
+ *              state_dim, every width <= BAB_MAX_WIDTH.
+ *   params     HOST float array packed as described above; copied, so the
+ *              caller may free it on return.
+ *   flags      reserved, pass 0.
+ * Errors: BAB_ERR_INVALID_ARG (null pointer, flags), BAB_ERR_SHAPE (dims),
+ * BAB_ERR_NUMERIC (a non-finite parameter), BAB_ERR_OOM, BAB_ERR_CUDA.
+ */
+int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float *params, int state_dim,
+                      int action_dim, unsigned flags);
+
+/* Free a context and its device memory (synchronises the device first). */
+int bab_destroy(bab_ctx *ctx);
+
+/* Message of the last failure of ctx (empty string if none); valid until the next call on ctx. */
+const char *bab_last_error(const bab_ctx *ctx);
+
+/*
+ * Sampled search (Section 3.3, batch_search, with uniform sampling): for each
+ * box i < n draw `samples` action sequences u^m uniformly in the box, roll the
+ * dynamics out for H steps and keep the best objective:
+ *     ub[i] = min_m f(u^m),  best_u[i] = argmin (lowest m on ties).
+ * Sample m, coordinate j of box i is u = lo + (hi - lo) * r, formed in FP32
+ * without fused multiply-add, with r the top 24 bits of a SplitMix64 chain
+ * over (seed, id[i], m, j) divided by 2^24:
+ *     h = sm64(seed ^ sm64(id)),  h = sm64(h ^ (m << 32 | j)),  r = (h >> 40) / 2^24,
+ * where sm64 is the SplitMix64 output function (Steele, Lea and Flood, 2014).
+ *   x0, goal   device float[s]; horizon H >= 1; rho >= 0.
+ *   lo, hi     device float[n][d], d = k * H; id device uint64[n] (distinct).
+ *   samples    M >= 1.  precision: BAB_PREC_FP32, BAB_PREC_BF16X3 or BAB_PREC_BF16.
+ *   ub         device float[n]; best_u device float[n][d] (nullable).
+ *   inc_val, inc_u (both nullable, device double[1], float[d]): the incumbent
+ *              of Algorithm 2 (lines 10-11).  If given, the box with the
+ *              smallest ub (lowest index on ties) has its best_u re-evaluated
+ *              in FP64 on the GPU, and if that value is below *inc_val the
+ *              pair (*inc_val, inc_u) is replaced by it.  Requires best_u.
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE (H, n, samples, d), BAB_ERR_UNSUPPORTED
+ * (precision not built for this network), BAB_ERR_CUDA.
+ */
+int bab_rollout(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
+                int precision, float *ub, float *best_u, double *inc_val, float *inc_u, void *stream);
+
+/*
+ * Interval bound propagation through the unrolled dynamics: the intermediate
+ * (pre-activation) bounds that Lemma 1 (Appendix B.1) needs, in outward-rounded
+ * FP32 so that they contain the exact interval bounds.  Per layer the input
+ * interval [a_lo, a_hi] maps to [z_lo, z_hi] with z_lo = W+ a_lo + W- a_hi + b
+ * (rounded down) and z_hi = W+ a_hi + W- a_lo + b (rounded up); ReLU clamps
+ * both ends; x_{t+1} lies in [x_t] + [z_L].
+ *   lb_ibp     device float[n] (nullable): interval lower bound of f.
+ *   pre_lo, pre_hi  device float[n][H][sumh] (nullable, both or neither).
+ *   x_lo, x_hi device float[n][H+1][s] (nullable, both or neither).
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_CUDA.
+ */
+int bab_bound_ibp(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                  const float *hi, int n, const int *d_n, float *lb_ibp, float *pre_lo, float *pre_hi, float *x_lo,
+                  float *x_hi, void *stream);
+
+/*
+ * Sound CROWN lower bound of f over each box (Appendix B.1: Lemma 1, Theorem
+ * 1, Theorem 2 in box form), with interval intermediate bounds.  Each square
+ * ||x_t - g||^2 is bounded below by its tangent at the midpoint of its
+ * interval, the resulting linear function of the states is propagated
+ * backward through the unrolled network (lower ReLU bound where the
+ * coefficient is >= 0, upper where < 0), and the final function of u,
+ * lin_const + mu . u + rho ||u||^2, is minimised exactly over the box.
+ * lb[i] is that minimum MINUS margin[i], an a-posteriori bound on the FP32
+ * rounding error of the whole computation, so lb[i] <= the exact CROWN bound
+ * <= min_box f.
+ *   alpha      device float[n][H][sumh] (nullable): lower slopes of unstable
+ *              ReLUs, each in [0, 1]; NULL selects the adaptive slope
+ *              (1 if u >= -l, else 0).
+ *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3.
+ *   lb         device float[n]; margin device float[n] (nullable).
+ *   lin_coef   device float[n][d] (nullable): mu; lin_const device float[n]
+ *              (nullable): the constant (before the margin).
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_UNSUPPORTED, BAB_ERR_OOM, BAB_ERR_CUDA.
+ */
+int bab_bound_crown(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                    const float *hi, int n, const int *d_n, const float *alpha, int precision, float *lb,
+                    float *margin, float *lin_coef, float *lin_const, void *stream);
+
+/*
+ * One step of alpha-CROWN: the free lower slopes alpha of Lemma 1 are raised
+ * by projected Adam ascent on the sum of the boxes' bounds.  The step
+ *   1. computes the bound at alpha (as bab_bound_crown, margin subtracted)
+ *      and its gradient dLB/dalpha_j = A_j z~_j(u*) for unstable neurons whose
+ *      lower bound is selected (A_j >= 0 the coefficient of the ReLU output, z~
+ *      the pre-activation of the relaxed network at the concretizing point
+ *      u*), 0 elsewhere;
+ *   2. lb_best[i] = max(lb_best[i], lb[i]) (every alpha gives a valid bound);
+ *   3. Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with `step`,
+ *      counting from 1) ascent on alpha with learning rate lr, then clamps
+ *      alpha to [0, 1].
+ *   alpha, adam_m, adam_v  device float[n][H][sumh], updated in place
+ *              (m, v start at 0; alpha typically at the adaptive slopes).
+ *   lb         device float[n] (nullable): bound at the incoming alpha.
+ *   lb_best    device float[n] (nullable): running maximum, updated.
+ *   grad_alpha device float[n][H][sumh] (nullable): the gradient.
+ * Errors: as bab_bound_crown.
+ */
+int bab_alpha_step(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                   const float *hi, int n, const int *d_n, float *alpha, float *adam_m, float *adam_v, int step,
+                   float lr, float *lb, float *lb_best, float *grad_alpha, void *stream);
+
+/*
+ * The adaptive lower slopes of every hidden neuron (1 where u >= -l, else 0,
+ * with the interval bounds of bab_bound_ibp), to start alpha optimisation.
+ *   alpha      device float[n][H][sumh], written.
+ */
+int bab_alpha_init(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                   const float *hi, int n, const int *d_n, float *alpha, void *stream);
+
+/*
+ * Prune, pick out and split one pool of n boxes (Algorithm 2: Pruner, then
+ * batch_pick_out and batch_split of Section 3.1).
+ *   1. Prune: box i is dropped iff (double)lb[i] > *inc_val (strict; a NaN
+ *      bound is kept).  keep[i] = 1 if kept.
+ *   2. Pick out up to n_pick survivors: all of them if there are at most
+ *      n_pick; otherwise the ceil(eta * n_pick) smallest by (ub, id), then the
+ *      rest of the quota by smallest (lb, id) among the others.
+ *   3. Split each picked box on its widest coordinate (lowest index on ties)
+ *      at mid = 0.5f * (lo + hi) in FP32: child 2p is the lower half, child
+ *      2p + 1 the upper half, ids 2 id and 2 id + 1, lb and ub inherited.
+ * Output rows: the 2P children (picked boxes in pool order) followed by the R
+ * unpicked survivors in pool order.  d_counts (device int[3]) receives
+ * {2P, R, 2P + R}: pass d_counts (children) or d_counts + 2 (whole pool) as
+ * the `d_n` of the next calls to chain an iteration without a host sync.
+ * Everything is integer or exact FP32 work: results are bit-identical run to
+ * run.
+ *   d          box dimension; lo, hi device float[n][d]; lb, ub float[n]; id uint64[n] (distinct).
+ *   inc_val    device double[1].
+ *   n_pick >= 0, 0 <= eta <= 1, split_rule BAB_SPLIT_WIDEST.
+ *   cap_out    rows available in the outputs; must be >= n + n_pick.
+ *   out_*      device arrays of cap_out rows; keep device uint8[n].
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE (cap_out too small), BAB_ERR_CUDA.
+ * A picked box whose id is >= 2^63 cannot be split; the call then records
+ * BAB_ERR_SHAPE in the context's device status (see bab_status).
+ */
+int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                     const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
+                     int split_rule, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
+                     uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream);
+
+/*
+ * Synchronise `stream` and return the sticky device-side status of ctx (0 or
+ * a BAB_ERR_* code recorded by a kernel), then clear it.
+ */
+int bab_status(bab_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BAB_H */

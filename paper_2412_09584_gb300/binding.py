@@ -1,0 +1,181 @@
+"""Thin Python binding of libbab (include/bab.h), same names as the C entry points.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays are torch CUDA tensors (device memory and streams come from
+PyTorch); the binding checks dtype, device and contiguity, passes raw
+pointers and the current CUDA stream, and raises BabError on a nonzero status.
+If libbab.so is missing the import fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbab.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "bab.h")
+
+BAB_OK = 0
+ERRORS = {-1: "BAB_ERR_INVALID_ARG", -2: "BAB_ERR_SHAPE", -3: "BAB_ERR_CUDA", -4: "BAB_ERR_OOM",
+          -5: "BAB_ERR_TIMEOUT", -6: "BAB_ERR_NUMERIC", -7: "BAB_ERR_UNSUPPORTED"}
+PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
+SPLIT_WIDEST = 0
+
+
+class BabError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+
+
+def header_symbols():
+    """Names of the functions declared in include/bab.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(bab_\w+)\s*\(", text, re.M)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libbab.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_2412_09584_gb300.build_lib.build()")
+    L = ctypes.CDLL(path)
+    L.bab_version.restype = _I
+    L.bab_load_dynamics.argtypes = [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _I, _I,
+                                    ctypes.c_uint]
+    L.bab_destroy.argtypes = [_P]
+    L.bab_last_error.argtypes = [_P]
+    L.bab_last_error.restype = ctypes.c_char_p
+    L.bab_status.argtypes = [_P, _P]
+    L.bab_rollout.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _P, _P, _P, _P, _P]
+    L.bab_bound_ibp.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]
+    L.bab_bound_crown.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P]
+    L.bab_alpha_init.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
+    L.bab_alpha_step.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _I, _F, _P, _P, _P, _P]
+    L.bab_prune_branch.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _I, _P, _P, _P, _P, _P, _P, _P,
+                                   _P]
+    _lib = L
+    return L
+
+
+def _ptr(t, dtype=None, name="array", allow_none=True):
+    if t is None:
+        if not allow_none:
+            raise ValueError(f"{name} is required")
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is torch.uint64 and t.dtype == torch.int64:
+        dtype = torch.int64  # box identifiers: the same 64 bits either way
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _check(ctx, rc):
+    if rc != BAB_OK:
+        raise BabError(rc, load().bab_last_error(ctx).decode())
+
+
+def bab_version():
+    return load().bab_version()
+
+
+def bab_load_dynamics(dims, params, state_dim, action_dim, flags=0):
+    """Create a context from host parameters (packed W_1, b_1, ..., W_L, b_L). Returns an opaque handle."""
+    L = load()
+    dims_a = (_I * len(dims))(*[int(x) for x in dims])
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    out = _P()
+    rc = L.bab_load_dynamics(ctypes.byref(out), len(dims) - 1, dims_a, p.ctypes.data_as(ctypes.POINTER(_F)),
+                             int(state_dim), int(action_dim), int(flags))
+    if rc != BAB_OK:
+        raise BabError(rc, "bab_load_dynamics failed")
+    return out.value
+
+
+def bab_destroy(ctx):
+    load().bab_destroy(ctx)
+
+
+def bab_status(ctx, stream=None):
+    return load().bab_status(ctx, _stream(stream))
+
+
+def bab_rollout(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, seed, precision, ub, best_u=None,
+                inc_val=None, inc_u=None, d_n=None, stream=None):
+    f32, u64 = torch.float32, torch.uint64
+    rc = load().bab_rollout(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                            _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, u64, "id"), int(n),
+                            _ptr(d_n, torch.int32, "d_n"), int(samples), ctypes.c_uint64(int(seed)), int(precision),
+                            _ptr(ub, f32, "ub"), _ptr(best_u, f32, "best_u"), _ptr(inc_val, torch.float64, "inc_val"),
+                            _ptr(inc_u, f32, "inc_u"), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_bound_ibp(ctx, x0, goal, horizon, rho, lo, hi, n, lb_ibp=None, pre_lo=None, pre_hi=None, x_lo=None,
+                  x_hi=None, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_bound_ibp(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
+                              _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), _ptr(lb_ibp, f32), _ptr(pre_lo, f32),
+                              _ptr(pre_hi, f32), _ptr(x_lo, f32), _ptr(x_hi, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_bound_crown(ctx, x0, goal, horizon, rho, lo, hi, n, lb, alpha=None, precision=PREC_FP32, margin=None,
+                    lin_coef=None, lin_const=None, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_bound_crown(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
+                                _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), _ptr(alpha, f32), int(precision),
+                                _ptr(lb, f32), _ptr(margin, f32), _ptr(lin_coef, f32), _ptr(lin_const, f32),
+                                _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_alpha_init(ctx, x0, goal, horizon, rho, lo, hi, n, alpha, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_alpha_init(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
+                               _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), _ptr(alpha, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_alpha_step(ctx, x0, goal, horizon, rho, lo, hi, n, alpha, adam_m, adam_v, step, lr, lb=None, lb_best=None,
+                   grad_alpha=None, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_alpha_step(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
+                               _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), _ptr(alpha, f32), _ptr(adam_m, f32),
+                               _ptr(adam_v, f32), int(step), float(lr), _ptr(lb, f32), _ptr(lb_best, f32),
+                               _ptr(grad_alpha, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_prune_branch(ctx, d, lo, hi, lb, ub, ids, n, inc_val, n_pick, eta, cap_out, out_lo, out_hi, out_lb, out_ub,
+                     out_id, keep, d_counts, split_rule=SPLIT_WIDEST, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_prune_branch(ctx, int(d), _ptr(lo, f32), _ptr(hi, f32), _ptr(lb, f32), _ptr(ub, f32),
+                                 _ptr(ids, torch.uint64), int(n), _ptr(d_n, torch.int32),
+                                 _ptr(inc_val, torch.float64), int(n_pick), float(eta), int(split_rule), int(cap_out),
+                                 _ptr(out_lo, f32), _ptr(out_hi, f32), _ptr(out_lb, f32), _ptr(out_ub, f32),
+                                 _ptr(out_id, torch.uint64), _ptr(keep, torch.uint8), _ptr(d_counts, torch.int32),
+                                 _stream(stream))
+    _check(ctx, rc)

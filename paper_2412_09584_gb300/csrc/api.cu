@@ -1,0 +1,426 @@
+// api.cu -- the extern "C" entry points of libbab (declared in include/bab.h):
+// argument checks, the context (network images, scratch, device status), and
+// the kernel launches of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "bab_internal.cuh"
+#include "kernels.cuh"
+
+using namespace bab;
+
+struct bab_ctx {
+    int device = 0;
+    int num_sms = 1;
+    NetDesc net{};
+    float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int *d_status = nullptr;
+    char err[512] = {0};
+};
+
+namespace {
+
+int fail(bab_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(bab_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? BAB_ERR_OOM : BAB_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Grow the context scratch to at least `bytes` (synchronises the device when it reallocates).
+int ensure_scratch(bab_ctx *c, size_t bytes)
+{
+    if (bytes <= c->scratch_bytes) return BAB_OK;
+    size_t want = bytes + bytes / 4 + (1u << 20);
+    if (c->scratch) {
+        cudaDeviceSynchronize();
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->scratch, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(c, e, "scratch allocation");
+    }
+    c->scratch_bytes = want;
+    return BAB_OK;
+}
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+size_t bound_scratch_bytes(const NetDesc &N, int n, int H, int d, bool alpha)
+{
+    size_t nh = (size_t)n * H * N.sumh, nx = (size_t)n * (H + 1) * N.s, ns = (size_t)n * H * (N.sumh + N.s);
+    size_t f = 2 * nh + 2 * nx + ns + (alpha ? (2 * nh + (size_t)n * d + 2 * (size_t)n) : 0);
+    return f * sizeof(float) + 16 * 256;
+}
+
+int check_problem(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                  int n)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!x0 || !goal) return fail(c, BAB_ERR_INVALID_ARG, "x0 and goal are required");
+    if (H < 1 || H > (1 << 20)) return fail(c, BAB_ERR_SHAPE, "horizon %d out of range", H);
+    if (n < 0) return fail(c, BAB_ERR_SHAPE, "n = %d < 0", n);
+    if (n > 0 && (!lo || !hi)) return fail(c, BAB_ERR_INVALID_ARG, "lo and hi are required");
+    if (!(rho >= 0.f) || !std::isfinite(rho)) return fail(c, BAB_ERR_INVALID_ARG, "rho must be finite and >= 0");
+    long long d = (long long)c->net.k * H;
+    if (d > (1 << 24)) return fail(c, BAB_ERR_SHAPE, "action dimension k*H too large");
+    return BAB_OK;
+}
+
+BoundArgs make_bound_args(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                          const float *hi, int n, const int *d_n)
+{
+    BoundArgs a{};
+    a.net = c->net;
+    a.fwd = c->d_fwd;
+    a.bwd = c->d_bwd;
+    a.x0 = x0;
+    a.goal = goal;
+    a.lo = lo;
+    a.hi = hi;
+    a.n = n;
+    a.d_n = d_n;
+    a.H = H;
+    a.d = c->net.k * H;
+    a.rho = rho;
+    a.status = c->d_status;
+    return a;
+}
+
+// IBP into the scratch (or the caller's arrays); fills the interval fields of `a`.
+int run_ibp(bab_ctx *c, BoundArgs &a, Carver &cv, float *pre_lo, float *pre_hi, float *x_lo, float *x_hi,
+            float *lb_ibp, cudaStream_t st)
+{
+    const NetDesc &N = c->net;
+    size_t nh = (size_t)a.n * a.H * N.sumh, nx = (size_t)a.n * (a.H + 1) * N.s;
+    a.pre_lo = pre_lo ? pre_lo : cv.take<float>(nh);
+    a.pre_hi = pre_hi ? pre_hi : cv.take<float>(nh);
+    a.x_lo = x_lo ? x_lo : cv.take<float>(nx);
+    a.x_hi = x_hi ? x_hi : cv.take<float>(nx);
+    a.S = cv.take<float>((size_t)a.n * a.H * (N.sumh + N.s));
+    a.lb_ibp = lb_ibp;
+    cudaError_t e = launch_ibp(a, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "interval bounds kernel");
+    return BAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bab_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float *params, int state_dim, int action_dim,
+                      unsigned flags)
+{
+    if (!out || !dims || !params) return BAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (flags != 0) return BAB_ERR_INVALID_ARG;
+    if (n_layers < 1 || n_layers > kMaxLayers) return BAB_ERR_SHAPE;
+    if (state_dim < 1 || action_dim < 1 || dims[0] != state_dim + action_dim || dims[n_layers] != state_dim)
+        return BAB_ERR_SHAPE;
+    for (int l = 0; l <= n_layers; ++l)
+        if (dims[l] < 1 || dims[l] > kMaxWidth) return BAB_ERR_SHAPE;
+
+    bab_ctx *c = new bab_ctx();
+    NetDesc &N = c->net;
+    N.L = n_layers;
+    N.s = state_dim;
+    N.k = action_dim;
+    int maxw = 0, h = 0, raw = 0, img = 0;
+    for (int l = 0; l <= n_layers; ++l) {
+        N.dims[l] = dims[l];
+        maxw = dims[l] > maxw ? dims[l] : maxw;
+    }
+    N.maxw_p = pad4(maxw);
+    for (int l = 1; l <= n_layers; ++l) {
+        N.hoff[l] = h;
+        if (l < n_layers) h += dims[l];
+        N.raw_w[l] = raw;
+        raw += dims[l] * dims[l - 1];
+        N.raw_b[l] = raw;
+        raw += dims[l];
+        const int Kp = pad4(dims[l - 1]), Np = pad4(dims[l]);
+        N.fwd_w[l] = N.bwd_w[l] = img;
+        img += Kp * Np;
+        N.fwd_b[l] = N.bwd_b[l] = img;
+        img += Np;
+    }
+    N.sumh = h;
+    N.raw_floats = raw;
+    N.img_floats = img;
+    for (int i = 0; i < raw; ++i)
+        if (!std::isfinite(params[i])) {
+            delete c;
+            return BAB_ERR_NUMERIC;
+        }
+
+    std::vector<float> fwd(img, 0.f), bwd(img, 0.f);
+    for (int l = 1; l <= n_layers; ++l) {
+        const int no = dims[l], ni = dims[l - 1], Kp = pad4(ni), Np = pad4(no);
+        const float *W = params + N.raw_w[l], *b = params + N.raw_b[l];
+        for (int q = 0; q < no; ++q)
+            for (int p = 0; p < ni; ++p) {
+                fwd[N.fwd_w[l] + p * Np + q] = W[q * ni + p];  // Wt [Kp][Np]
+                bwd[N.bwd_w[l] + q * Kp + p] = W[q * ni + p];  // W  [Np][Kp]
+            }
+        for (int q = 0; q < no; ++q) fwd[N.fwd_b[l] + q] = bwd[N.bwd_b[l] + q] = b[q];
+    }
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_raw, sizeof(float) * raw);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_fwd, sizeof(float) * img);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bwd, sizeof(float) * img);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_raw, params, sizeof(float) * raw, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_fwd, fwd.data(), sizeof(float) * img, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_bwd, bwd.data(), sizeof(float) * img, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        int code = e == cudaErrorMemoryAllocation ? BAB_ERR_OOM : BAB_ERR_CUDA;
+        cudaGetLastError();
+        bab_destroy(c);
+        return code;
+    }
+    *out = c;
+    return BAB_OK;
+}
+
+int bab_destroy(bab_ctx *c)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(c->d_raw);
+    cudaFree(c->d_fwd);
+    cudaFree(c->d_bwd);
+    cudaFree(c->scratch);
+    cudaFree(c->d_status);
+    delete c;
+    return BAB_OK;
+}
+
+const char *bab_last_error(const bab_ctx *c) { return c ? c->err : "null context"; }
+
+int bab_status(bab_ctx *c, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    return v;
+}
+
+int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
+                float *best_u, double *inc_val, float *inc_u, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (samples < 1) return fail(c, BAB_ERR_SHAPE, "samples must be >= 1");
+    if (n > 0 && (!id || !ub)) return fail(c, BAB_ERR_INVALID_ARG, "id and ub are required");
+    if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
+    if (inc_val && !best_u) return fail(c, BAB_ERR_INVALID_ARG, "the incumbent update needs best_u");
+    if (precision != BAB_PREC_FP32) return fail(c, BAB_ERR_UNSUPPORTED, "rollout precision %d not available", precision);
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, (size_t)n * sizeof(unsigned long long) + 256);
+    if (rc) return rc;
+    RolloutArgs a{};
+    a.net = c->net;
+    a.fwd = c->d_fwd;
+    a.raw = c->d_raw;
+    a.x0 = x0;
+    a.goal = goal;
+    a.lo = lo;
+    a.hi = hi;
+    a.id = id;
+    a.n = n;
+    a.d_n = d_n;
+    a.H = H;
+    a.M = samples;
+    a.d = c->net.k * H;
+    a.rho = rho;
+    a.seed = seed;
+    a.keys = reinterpret_cast<unsigned long long *>(c->scratch);
+    a.ub = ub;
+    a.best_u = best_u;
+    a.inc_val = inc_val;
+    a.inc_u = inc_u;
+    a.status = c->d_status;
+    cudaError_t e = launch_rollout_fp32(a, c->num_sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "rollout kernels");
+    return BAB_OK;
+}
+
+int bab_bound_ibp(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                  int n, const int *d_n, float *lb_ibp, float *pre_lo, float *pre_hi, float *x_lo, float *x_hi,
+                  void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if ((pre_lo == nullptr) != (pre_hi == nullptr) || (x_lo == nullptr) != (x_hi == nullptr))
+        return fail(c, BAB_ERR_INVALID_ARG, "bound arrays come in lo/hi pairs");
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, false));
+    if (rc) return rc;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    return run_ibp(c, a, cv, pre_lo, pre_hi, x_lo, x_hi, lb_ibp, (cudaStream_t)stream);
+}
+
+int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                    int n, const int *d_n, const float *alpha, int precision, float *lb, float *margin,
+                    float *lin_coef, float *lin_const, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
+    if (precision != BAB_PREC_FP32) return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, false));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    a.alpha = alpha;
+    a.lb = lb;
+    a.margin = margin;
+    a.lin_coef = lin_coef;
+    a.lin_const = lin_const;
+    cudaError_t e = launch_crown(a, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
+    return BAB_OK;
+}
+
+int bab_alpha_init(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                   int n, const int *d_n, float *alpha, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && !alpha) return fail(c, BAB_ERR_INVALID_ARG, "alpha is required");
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, false));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    a.alpha = alpha;
+    cudaError_t e = launch_alpha_init(a, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha init kernel");
+    return BAB_OK;
+}
+
+int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                   int n, const int *d_n, float *alpha, float *adam_m, float *adam_v, int step, float lr, float *lb,
+                   float *lb_best, float *grad_alpha, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && (!alpha || !adam_m || !adam_v)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, m and v are required");
+    if (step < 1) return fail(c, BAB_ERR_INVALID_ARG, "step counts from 1");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
+    if (n == 0) return BAB_OK;
+    const int d = c->net.k * H;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, d, true));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    const size_t nh = (size_t)n * H * c->net.sumh;
+    a.alpha = alpha;
+    a.A_pre = cv.take<float>(nh);
+    a.ustar = cv.take<float>((size_t)n * d);
+    a.grad_alpha = grad_alpha ? grad_alpha : cv.take<float>(nh);
+    a.lb = lb ? lb : cv.take<float>(n);
+    a.lb_best = lb_best;
+    cudaError_t e = launch_crown(a, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
+    e = launch_alpha_fwd(a, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha adjoint kernel");
+    const double bc1 = 1.0 - std::pow(0.9, step), bc2 = 1.0 - std::pow(0.999, step);
+    e = launch_adam(alpha, adam_m, adam_v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Adam kernel");
+    return BAB_OK;
+}
+
+int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                     const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
+                     int split_rule, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
+                     uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (d < 1 || n < 0 || n_pick < 0) return fail(c, BAB_ERR_SHAPE, "bad d, n or n_pick");
+    if (!(eta >= 0.f && eta <= 1.f)) return fail(c, BAB_ERR_INVALID_ARG, "eta must be in [0, 1]");
+    if (split_rule != BAB_SPLIT_WIDEST) return fail(c, BAB_ERR_UNSUPPORTED, "split rule %d", split_rule);
+    if (!inc_val || !d_counts) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and d_counts are required");
+    if (n > 0 && (!lo || !hi || !lb || !ub || !id || !keep || !out_lo || !out_hi || !out_lb || !out_ub || !out_id))
+        return fail(c, BAB_ERR_INVALID_ARG, "null array");
+    if ((long long)cap_out < (long long)n + n_pick) return fail(c, BAB_ERR_SHAPE, "cap_out must be >= n + n_pick");
+    int rc = ensure_scratch(c, (size_t)(n > 0 ? n : 1) * sizeof(int) + 256);
+    if (rc) return rc;
+    BranchArgs a{};
+    a.d = d;
+    a.n = n;
+    a.d_n = d_n;
+    a.lo = lo;
+    a.hi = hi;
+    a.lb = lb;
+    a.ub = ub;
+    a.id = id;
+    a.inc_val = inc_val;
+    a.n_pick = n_pick;
+    int n1 = (int)std::ceil((double)eta * n_pick);
+    a.n1 = n1 > n_pick ? n_pick : n1;
+    a.out_lo = out_lo;
+    a.out_hi = out_hi;
+    a.out_lb = out_lb;
+    a.out_ub = out_ub;
+    a.out_id = out_id;
+    a.keep = keep;
+    a.d_counts = d_counts;
+    a.dest = reinterpret_cast<int *>(c->scratch);
+    a.status = c->d_status;
+    cudaError_t e = launch_prune_branch(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prune/branch kernels");
+    return BAB_OK;
+}
+
+}  // extern "C"

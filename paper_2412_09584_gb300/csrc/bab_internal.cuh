@@ -1,0 +1,127 @@
+// bab_internal.cuh -- device-side types and helpers shared by the libbab kernels.
+//
+// Network images.  The context keeps the dynamics network N (Section 3,
+// Formulation; Appendix B.1, Definition) in three device layouts, every
+// segment padded to a multiple of 4 floats (16 bytes) so that rows can be
+// moved as float4:
+//   raw : as loaded, W_l row-major [d_l][d_{l-1}] then b_l      (FP64 re-score)
+//   fwd : per layer Wt_l [Kp][Np] (= W_l^T, zero padded), then b_l [Np]
+//         (forward products a_l = W_l a_{l-1} + b_l over a tile of rows)
+//   bwd : per layer W_l [Np][Kp] (zero padded), then b_l [Np]
+//         (backward products A <- A W_l over a tile of rows)
+// with Kp = pad4(d_{l-1}), Np = pad4(d_l).  The input layer's activation row
+// is [x (s) | u (k) | 0 ...].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bab.h"
+
+namespace bab {
+
+constexpr int kMaxLayers = BAB_MAX_LAYERS;
+constexpr int kMaxWidth = BAB_MAX_WIDTH;
+
+__host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
+
+struct NetDesc {
+    int L, s, k, sumh, maxw_p;                // maxw_p = pad4(max width)
+    int dims[kMaxLayers + 1];
+    int hoff[kMaxLayers + 1];                 // offset of hidden layer l in the [sumh] vector
+    int raw_w[kMaxLayers + 1], raw_b[kMaxLayers + 1];
+    int fwd_w[kMaxLayers + 1], fwd_b[kMaxLayers + 1];
+    int bwd_w[kMaxLayers + 1], bwd_b[kMaxLayers + 1];
+    int img_floats;                           // floats in the fwd (= bwd) image
+    int raw_floats;
+};
+
+// ---------------------------------------------------------------------------
+// Counter-based sampling: SplitMix64 output function (Steele, Lea and Flood,
+// OOPSLA 2014), chained over (seed, box id, sample index m, coordinate j).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ uint64_t box_hash(uint64_t seed, uint64_t id) { return splitmix64(seed ^ splitmix64(id)); }
+
+// u = lo + (hi - lo) * r in FP32, one rounding per operation (no contraction).
+__device__ __forceinline__ float draw_sample(uint64_t hbox, uint32_t m, uint32_t j, float lo, float hi)
+{
+    uint64_t h = splitmix64(hbox ^ (((uint64_t)m << 32) | (uint64_t)j));
+    float r = __fmul_rn(__ull2float_rn(h >> 40), 5.9604644775390625e-08f);  // 2^-24, exact
+    return __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), r));
+}
+
+// Order-preserving map of a float to uint32 (NaN canonicalised to the top).
+__device__ __forceinline__ uint32_t float_order(float f)
+{
+    if (f != f) return 0xFFFFFFFFu;
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float float_unorder(uint32_t k)
+{
+    if (k == 0xFFFFFFFFu) return __int_as_float(0x7FC00000);
+    uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    return __uint_as_float(b);
+}
+
+// gamma_n = n u / (1 - n u), u = 2^-24: the classical bound on the relative
+// error of an n-term FP32 sum or dot product in any order (Higham, "Accuracy
+// and Stability of Numerical Algorithms", 2nd ed., Section 3.1), rounded up.
+__host__ __device__ __forceinline__ float gamma_fp32(int n)
+{
+    const double u = 5.9604644775390625e-08;
+    double g = n * u / (1.0 - n * u);
+    return (float)(g * (1.0 + 1e-6));
+}
+
+__device__ __forceinline__ int live_count(int n, const int *d_n)
+{
+    if (!d_n) return n;
+    int v = *d_n;
+    return v < n ? (v < 0 ? 0 : v) : n;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+// Sum with every addition rounded up: an upper bound of the exact sum of
+// nonnegative terms.
+__device__ __forceinline__ float warp_sum_ru(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_sum_rd(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
+// min over s in [lo, hi] of s^2, rounded down.
+__device__ __forceinline__ float sq_min_rd(float lo, float hi)
+{
+    if (lo > 0.f) return __fmul_rd(lo, lo);
+    if (hi < 0.f) return __fmul_rd(hi, hi);
+    return 0.f;
+}
+
+// Device status codes written by kernels (sticky, first error wins).
+__device__ __forceinline__ void set_status(int *status, int code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace bab

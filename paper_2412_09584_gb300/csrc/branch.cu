@@ -1,0 +1,261 @@
+// branch.cu -- Pruner, batch_pick_out and batch_split of Algorithm 2
+// (Section 3 overview and Section 3.1), bit-exact and deterministic.
+//
+//   k_branch_plan   one CTA: the FP64 prune test, the pick-out selection (exact
+//                   k-th smallest of the composite keys (order(ub), id) and
+//                   (order(lb), id) by 8-bit radix selection), and the stable
+//                   ranks of picked and unpicked survivors (warp ballots).
+//   k_branch_write  one warp per pool row: the widest coordinate (warp
+//                   argmax, lowest index on ties), the FP32 midpoint, and the
+//                   coalesced writes of two children or of the unpicked row.
+#include "bab_internal.cuh"
+#include "kernels.cuh"
+
+namespace bab {
+
+constexpr int kPlanThreads = 1024;
+constexpr int kPickFlag = 1 << 30;
+
+struct Thresh {
+    uint32_t key;
+    uint64_t id;
+    bool none;  // nothing selected
+};
+
+__device__ __forceinline__ bool le_thresh(uint32_t key, uint64_t id, const Thresh &T)
+{
+    return !T.none && (key < T.key || (key == T.key && id <= T.id));
+}
+
+__device__ __forceinline__ uint32_t row_key(const float *v, int i) { return float_order(v[i]); }
+
+// 96-bit composite digit `pass` (0 = most significant byte of the key).
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, uint64_t id, int pass)
+{
+    return pass < 4 ? (key >> (24 - 8 * pass)) & 0xFFu : (uint32_t)(id >> (56 - 8 * (pass - 4))) & 0xFFu;
+}
+
+__device__ __forceinline__ bool prefix_match(uint32_t key, uint64_t id, uint32_t pk, uint64_t pid, int pass)
+{
+    if (pass == 0) return true;
+    if (pass <= 4) {
+        const int sh = 32 - 8 * pass;
+        return sh == 0 ? key == pk : (key >> sh) == (pk >> sh);
+    }
+    if (key != pk) return false;
+    const int sh = 64 - 8 * (pass - 4);
+    return (id >> sh) == (pid >> sh);
+}
+
+// The kth smallest (1-based) composite key among the rows accepted by `filt`.
+template <typename Filt>
+__device__ Thresh radix_select(int n, const float *val, const uint64_t *ids, Filt filt, int kth, unsigned *hist,
+                               uint32_t *sh_pk, uint64_t *sh_pid, int *sh_rem, int *sh_done)
+{
+    Thresh T;
+    T.none = kth <= 0;
+    if (T.none) return T;
+    if (threadIdx.x == 0) {
+        *sh_pk = 0;
+        *sh_pid = 0;
+        *sh_rem = kth;
+        *sh_done = 0;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 12; ++pass) {
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t pk = *sh_pk;
+        const uint64_t pid = *sh_pid;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            if (!filt(i)) continue;
+            const uint32_t key = row_key(val, i);
+            const uint64_t id = ids[i];
+            if (prefix_match(key, id, pk, pid, pass)) atomicAdd(&hist[digit_of(key, id, pass)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int rem = *sh_rem;
+            unsigned cum = 0;
+            int D = 255;
+            for (int b = 0; b < 256; ++b) {
+                if (cum + hist[b] >= (unsigned)rem) {
+                    D = b;
+                    break;
+                }
+                cum += hist[b];
+            }
+            rem -= (int)cum;
+            if (pass < 4) {
+                *sh_pk = pk | ((uint32_t)D << (24 - 8 * pass));
+            } else {
+                *sh_pid = pid | ((uint64_t)D << (56 - 8 * (pass - 4)));
+            }
+            *sh_rem = rem;
+            // key resolved and every row with that key is needed: take all ties
+            if (pass == 3 && hist[D] == (unsigned)rem) {
+                *sh_pid = ~0ull;
+                *sh_done = 1;
+            }
+        }
+        __syncthreads();
+        if (*sh_done) break;
+    }
+    T.key = *sh_pk;
+    T.id = *sh_pid;
+    __syncthreads();
+    return T;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
+{
+    __shared__ unsigned hist[256];
+    __shared__ uint32_t sh_pk;
+    __shared__ uint64_t sh_pid;
+    __shared__ int sh_rem, sh_done;
+    __shared__ int wsum[2][kPlanThreads / 32];
+    __shared__ int red[kPlanThreads / 32];
+    const int n = live_count(a.n, a.d_n);
+    const double inc = *a.inc_val;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // prune (strict, in FP64; a NaN bound is kept)
+    int cnt = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint8_t k = !((double)a.lb[i] > inc);
+        a.keep[i] = k;
+        cnt += k;
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    if (lane == 0) red[warp] = cnt;
+    __syncthreads();
+    int ns = 0;
+    for (int w = 0; w < kPlanThreads / 32; ++w) ns += red[w];
+    __syncthreads();
+
+    const bool all = ns <= a.n_pick;
+    Thresh T1, T2;
+    T1.none = T2.none = true;
+    if (!all) {
+        const uint8_t *keep = a.keep;
+        T1 = radix_select(n, a.ub, a.id, [&](int i) { return keep[i] != 0; }, a.n1, hist, &sh_pk, &sh_pid, &sh_rem,
+                          &sh_done);
+        const float *ub = a.ub;
+        const uint64_t *ids = a.id;
+        T2 = radix_select(
+            n, a.lb, a.id,
+            [&](int i) { return keep[i] != 0 && !le_thresh(float_order(ub[i]), ids[i], T1); }, a.n_pick - a.n1, hist,
+            &sh_pk, &sh_pid, &sh_rem, &sh_done);
+    }
+
+    // stable ranks of picked and unpicked survivors
+    int base_p = 0, base_r = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        bool kp = false, pk = false;
+        if (i < n) {
+            kp = a.keep[i] != 0;
+            pk = kp && (all || le_thresh(float_order(a.ub[i]), a.id[i], T1) ||
+                        le_thresh(float_order(a.lb[i]), a.id[i], T2));
+        }
+        const bool rs = kp && !pk;
+        const unsigned bp = __ballot_sync(0xFFFFFFFFu, pk), br = __ballot_sync(0xFFFFFFFFu, rs);
+        if (lane == 0) {
+            wsum[0][warp] = __popc(bp);
+            wsum[1][warp] = __popc(br);
+        }
+        __syncthreads();
+        int op = 0, orr = 0, tp = 0, tr = 0;
+        for (int w = 0; w < kPlanThreads / 32; ++w) {
+            if (w < warp) {
+                op += wsum[0][w];
+                orr += wsum[1][w];
+            }
+            tp += wsum[0][w];
+            tr += wsum[1][w];
+        }
+        if (i < n) {
+            if (pk) a.dest[i] = (base_p + op + __popc(bp & lt)) | kPickFlag;
+            else if (rs) a.dest[i] = base_r + orr + __popc(br & lt);
+            else a.dest[i] = -1;
+        }
+        base_p += tp;
+        base_r += tr;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.d_counts[0] = 2 * base_p;
+        a.d_counts[1] = base_r;
+        a.d_counts[2] = 2 * base_p + base_r;
+    }
+}
+
+__global__ void k_branch_write(BranchArgs a)
+{
+    const int n = live_count(a.n, a.d_n);
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    const int dst = a.dest[row];
+    if (dst < 0) return;
+    const int d = a.d;
+    const float *lo = a.lo + (size_t)row * d, *hi = a.hi + (size_t)row * d;
+    const uint64_t id = a.id[row];
+    if (!(dst & kPickFlag)) {
+        const size_t o = (size_t)a.d_counts[0] + dst;
+        for (int j = lane; j < d; j += 32) {
+            a.out_lo[o * d + j] = lo[j];
+            a.out_hi[o * d + j] = hi[j];
+        }
+        if (lane == 0) {
+            a.out_id[o] = id;
+            a.out_lb[o] = a.lb[row];
+            a.out_ub[o] = a.ub[row];
+        }
+        return;
+    }
+    // widest coordinate, lowest index on ties
+    float wb = -1.f;
+    int jb = 0x7FFFFFFF;
+    for (int j = lane; j < d; j += 32) {
+        const float w = __fsub_rn(hi[j], lo[j]);
+        if (w > wb) {
+            wb = w;
+            jb = j;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w2 = __shfl_xor_sync(0xFFFFFFFFu, wb, o);
+        const int j2 = __shfl_xor_sync(0xFFFFFFFFu, jb, o);
+        if (w2 > wb || (w2 == wb && j2 < jb)) {
+            wb = w2;
+            jb = j2;
+        }
+    }
+    const float mid = __fmul_rn(0.5f, __fadd_rn(lo[jb], hi[jb]));
+    const size_t o0 = 2 * (size_t)(dst & ~kPickFlag);
+    for (int j = lane; j < d; j += 32) {
+        const float l = lo[j], h = hi[j];
+        a.out_lo[o0 * d + j] = l;
+        a.out_hi[o0 * d + j] = (j == jb) ? mid : h;
+        a.out_lo[(o0 + 1) * d + j] = (j == jb) ? mid : l;
+        a.out_hi[(o0 + 1) * d + j] = h;
+    }
+    if (lane == 0) {
+        if (id >> 63) set_status(a.status, BAB_ERR_SHAPE);
+        a.out_id[o0] = 2 * id;
+        a.out_id[o0 + 1] = 2 * id + 1;
+        a.out_lb[o0] = a.out_lb[o0 + 1] = a.lb[row];
+        a.out_ub[o0] = a.out_ub[o0 + 1] = a.ub[row];
+    }
+}
+
+cudaError_t launch_prune_branch(const BranchArgs &a, cudaStream_t st)
+{
+    k_branch_plan<<<1, kPlanThreads, 0, st>>>(a);
+    if (a.n > 0) k_branch_write<<<(a.n + 7) / 8, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace bab

@@ -1,0 +1,152 @@
+// kernels.cuh -- argument blocks, the shared register-blocked dense product,
+// and the host launchers of the libbab kernels.
+#pragma once
+
+#include "bab_internal.cuh"
+
+namespace bab {
+
+struct RolloutArgs {
+    NetDesc net;
+    const float *fwd;   // forward image (device)
+    const float *raw;   // raw parameters (device), for the FP64 re-score
+    const float *x0, *goal, *lo, *hi;
+    const uint64_t *id;
+    int n;
+    const int *d_n;
+    int H, M, d;
+    float rho;
+    uint64_t seed;
+    unsigned long long *keys;  // [n] scratch
+    float *ub, *best_u;
+    double *inc_val;
+    float *inc_u;
+    int *status;
+};
+
+struct BoundArgs {
+    NetDesc net;
+    const float *fwd, *bwd;
+    const float *x0, *goal, *lo, *hi;
+    int n;
+    const int *d_n;
+    int H, d;
+    float rho;
+    // interval bounds (written by k_ibp, read by k_crown / k_alpha_fwd)
+    float *pre_lo, *pre_hi;  // [n][H][sumh]
+    float *x_lo, *x_hi;      // [n][H+1][s]
+    float *S;                // [n][H][sumh + s]: per row of each layer, sum_j |W_kj| max|a_j| over the input box
+    float *lb_ibp;           // [n] (nullable)
+    // CROWN
+    const float *alpha;      // [n][H][sumh] (nullable: adaptive)
+    float *A_pre;            // [n][H][sumh] (nullable): coefficient of each ReLU output before relaxation
+    float *lb, *margin, *lin_coef, *lin_const;
+    float *ustar;            // [n][d] (nullable)
+    float *lb_best;          // [n] (nullable): running max
+    // alpha
+    float *grad_alpha;       // [n][H][sumh]
+    int *status;
+};
+
+// out[r][c] = act(sum_k in[r][k] * B[k][c] + bias[c]) for r < R, c < Np, where
+// B is [Kp][Np] row-major (a forward image Wt_l, or a backward image W_l).
+// Kp % 4 == 0 and Np % 4 == 0; bias may be null.
+template <int R, int NT, int TR, int TN>
+__device__ __forceinline__ void dense_rows(const float *__restrict__ in, int ldi, const float *__restrict__ B,
+                                           const float *__restrict__ bias, int Kp, int Np, float *__restrict__ out,
+                                           int ldo, bool relu)
+{
+    const int ngc = (Np + TN - 1) / TN;
+    const int items = (R / TR) * ngc;
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int cg = it % ngc, rg = it / ngc;
+        const int c0 = cg * TN, r0 = rg * TR;
+        float acc[TR][TN];
+        float bv[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = (bias && c0 + j < Np) ? bias[c0 + j] : 0.f;
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = bv[j];
+        const bool full = (c0 + TN <= Np);
+        for (int k = 0; k < Kp; k += 4) {
+            float4 xv[TR];
+#pragma unroll
+            for (int i = 0; i < TR; ++i) xv[i] = *reinterpret_cast<const float4 *>(in + (r0 + i) * ldi + k);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float w[TN];
+                const float *wr = B + (size_t)(k + kk) * Np + c0;
+                if (full) {
+#pragma unroll
+                    for (int j = 0; j < TN; j += 4) {
+                        float4 q = *reinterpret_cast<const float4 *>(wr + j);
+                        w[j] = q.x;
+                        w[j + 1] = q.y;
+                        w[j + 2] = q.z;
+                        w[j + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) w[j] = (c0 + j < Np) ? wr[j] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < TR; ++i) {
+                    const float xs = kk == 0 ? xv[i].x : kk == 1 ? xv[i].y : kk == 2 ? xv[i].z : xv[i].w;
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(xs, w[j], acc[i][j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                if (c0 + j < Np) {
+                    const float v = acc[i][j];
+                    out[(r0 + i) * ldo + c0 + j] = relu ? fmaxf(v, 0.f) : v;
+                }
+    }
+}
+
+// Picks the register block so that the tile's items cover the threads.
+template <int R, int NT>
+__device__ __forceinline__ void dense_rows_auto(const float *in, int ldi, const float *B, const float *bias, int Kp,
+                                                int Np, float *out, int ldo, bool relu)
+{
+    if (R >= 4 && (R / 4) * ((Np + 7) / 8) >= NT / 2)
+        dense_rows<R, NT, (R >= 4 ? 4 : 1), 8>(in, ldi, B, bias, Kp, Np, out, ldo, relu);
+    else if (R >= 2 && (R / 2) * ((Np + 3) / 4) >= NT / 2)
+        dense_rows<R, NT, (R >= 2 ? 2 : 1), 4>(in, ldi, B, bias, Kp, Np, out, ldo, relu);
+    else
+        dense_rows<R, NT, 1, 4>(in, ldi, B, bias, Kp, Np, out, ldo, relu);
+}
+
+// host launchers (return the first CUDA error)
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_ibp(const BoundArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
+cudaError_t launch_adam(float *alpha, float *m, float *v, const float *grad, long long count, float lr, float bc1,
+                        float bc2, cudaStream_t st);
+
+struct BranchArgs {
+    int d, n;
+    const int *d_n;
+    const float *lo, *hi, *lb, *ub;
+    const uint64_t *id;
+    const double *inc_val;
+    int n_pick;
+    int n1;  // ceil(eta * n_pick), clamped to n_pick
+    float *out_lo, *out_hi, *out_lb, *out_ub;
+    uint64_t *out_id;
+    uint8_t *keep;
+    int *d_counts;
+    int *dest;     // [n] scratch: destination code per row
+    int *status;
+};
+cudaError_t launch_prune_branch(const BranchArgs &a, cudaStream_t st);
+
+}  // namespace bab

@@ -1,0 +1,253 @@
+// rollout.cu -- sampled search (Section 3.3, batch_search with uniform samples)
+// and the FP64 incumbent re-score (Algorithm 2, lines 10-11).
+//
+// k_rollout_fp32: a persistent kernel.  A tile is R samples of one box; a CTA
+// keeps the whole forward network image in shared memory for all H steps and
+// all of its tiles, and carries the R states x_t and running costs in shared
+// memory.  Per step it draws u_t (counter-based, so nothing is read from
+// memory), runs the L dense layers as register-blocked FP32 products over the
+// tile, adds the residual, and reduces the per-row cost with warp shuffles.
+// A tile's best (f, m) is folded into its box with a 64-bit atomicMin on
+// (order(f) << 32 | m), which keeps the lowest m among equal values.
+#include "bab_internal.cuh"
+#include "kernels.cuh"
+
+namespace bab {
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
+
+template <int R, int NT, bool WSMEM>
+__global__ void __launch_bounds__(NT, 1) k_rollout_fp32(RolloutArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, L = N.L, d = a.d;
+    const int ld = N.maxw_p;
+    const float *img = a.fwd;
+    float *p = sm;
+    if (WSMEM) {
+        for (int i = threadIdx.x; i < N.img_floats / 4; i += NT)
+            smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
+        img = sm;
+        p += N.img_floats;
+    }
+    float *act0 = p; p += R * ld;
+    float *act1 = p; p += R * ld;
+    float *xs = p; p += R * pad4(s);
+    float *us = p; p += R * pad4(k);
+    float *blo = p; p += pad4(d);
+    float *bhi = p; p += pad4(d);
+    float *cost = p; p += R;
+    float *goal = p; p += pad4(s);
+    __shared__ unsigned long long red[NT / 32];
+    for (int i = threadIdx.x; i < s; i += NT) goal[i] = a.goal[i];
+
+    const int nlive = live_count(a.n, a.d_n);
+    const int tpb = (a.M + R - 1) / R;
+    const long long ntiles = (long long)nlive * tpb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Kp1 = pad4(s + k);
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int box = (int)(tile / tpb);
+        const int m0 = (int)(tile % tpb) * R;
+        __syncthreads();  // previous tile fully consumed
+        for (int j = threadIdx.x; j < d; j += NT) {
+            blo[j] = a.lo[(size_t)box * d + j];
+            bhi[j] = a.hi[(size_t)box * d + j];
+        }
+        for (int i = threadIdx.x; i < R * s; i += NT) xs[(i / s) * pad4(s) + i % s] = a.x0[i % s];
+        for (int r = threadIdx.x; r < R; r += NT) cost[r] = 0.f;
+        const uint64_t hb = box_hash(a.seed, a.id[box]);
+        __syncthreads();
+        for (int t = 0; t < a.H; ++t) {
+            // input rows [x_t | u_t | 0]
+            for (int i = threadIdx.x; i < R * Kp1; i += NT) {
+                const int r = i / Kp1, c = i % Kp1;
+                float v;
+                if (c < s) {
+                    v = xs[r * pad4(s) + c];
+                } else if (c < s + k) {
+                    const int j = t * k + (c - s);
+                    v = draw_sample(hb, (uint32_t)(m0 + r), (uint32_t)j, blo[j], bhi[j]);
+                    us[r * pad4(k) + (c - s)] = v;
+                } else {
+                    v = 0.f;
+                }
+                act0[r * ld + c] = v;
+            }
+            __syncthreads();
+            float *in = act0, *out = act1;
+            for (int l = 1; l <= L; ++l) {
+                const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]);
+                dense_rows_auto<R, NT>(in, ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, out, ld, l < L);
+                __syncthreads();
+                float *tmp = in; in = out; out = tmp;
+            }
+            // `in` holds the network output: residual step and per-row cost (one warp per row)
+            for (int r = warp; r < R; r += NT / 32) {
+                float c = 0.f;
+                for (int i = lane; i < s; i += 32) {
+                    const float x = xs[r * pad4(s) + i] + in[r * ld + i];
+                    xs[r * pad4(s) + i] = x;
+                    const float e = x - goal[i];
+                    c = fmaf(e, e, c);
+                }
+                for (int j = lane; j < k; j += 32) {
+                    const float u = us[r * pad4(k) + j];
+                    c = fmaf(a.rho * u, u, c);
+                }
+                c = warp_sum(c);
+                if (lane == 0) cost[r] += c;
+            }
+            __syncthreads();
+        }
+        // best (f, m) of the tile
+        unsigned long long best = ~0ull;
+        for (int r = threadIdx.x; r < R; r += NT)
+            if (m0 + r < a.M) best = umin64(best, ((unsigned long long)float_order(cost[r]) << 32) | (unsigned)(m0 + r));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+        if (lane == 0) red[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = red[0];
+            for (int w = 1; w < NT / 32; ++w) b = umin64(b, red[w]);
+            atomicMin(&a.keys[box], b);
+        }
+    }
+}
+
+__global__ void k_fill_u64(unsigned long long *p, int n, unsigned long long v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// ub[i] and best_u[i] from the packed per-box minimum; the argmin sample is re-drawn.
+__global__ void k_rollout_finalize(RolloutArgs a)
+{
+    const int nlive = live_count(a.n, a.d_n);
+    const int box = blockIdx.x;
+    if (box >= nlive) return;
+    const unsigned long long key = a.keys[box];
+    const uint32_t m = (uint32_t)(key & 0xFFFFFFFFu);
+    if (threadIdx.x == 0) a.ub[box] = float_unorder((uint32_t)(key >> 32));
+    if (!a.best_u) return;
+    const uint64_t hb = box_hash(a.seed, a.id[box]);
+    for (int j = threadIdx.x; j < a.d; j += blockDim.x)
+        a.best_u[(size_t)box * a.d + j] =
+            draw_sample(hb, m, (uint32_t)j, a.lo[(size_t)box * a.d + j], a.hi[(size_t)box * a.d + j]);
+}
+
+// Incumbent update: the box with the smallest ub (lowest index on ties) has its
+// best_u re-evaluated in FP64; if the value beats *inc_val, it becomes the incumbent.
+__global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
+{
+    const NetDesc &N = a.net;
+    const int nlive = live_count(a.n, a.d_n);
+    __shared__ unsigned long long red[8];
+    __shared__ double act[2][kMaxWidth + 4];
+    __shared__ double xs[kMaxWidth];
+    __shared__ double f_sh;
+    __shared__ int row_sh;
+    unsigned long long best = ~0ull;
+    for (int i = threadIdx.x; i < nlive; i += blockDim.x)
+        best = umin64(best, ((unsigned long long)float_order(a.ub[i]) << 32) | (unsigned)i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = red[0];
+        for (int w = 1; w < 8; ++w) b = umin64(b, red[w]);
+        row_sh = (b == ~0ull) ? -1 : (int)(b & 0xFFFFFFFFu);
+        f_sh = 0.0;
+    }
+    __syncthreads();
+    const int row = row_sh;
+    if (row < 0) return;
+    const float *u = a.best_u + (size_t)row * a.d;
+    const int s = N.s, k = N.k;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = (double)a.x0[i];
+    __syncthreads();
+    for (int t = 0; t < a.H; ++t) {
+        for (int c = threadIdx.x; c < s + k; c += blockDim.x)
+            act[0][c] = c < s ? xs[c] : (double)u[t * k + (c - s)];
+        __syncthreads();
+        int cur = 0;
+        for (int l = 1; l <= N.L; ++l) {
+            const int no = N.dims[l], ni = N.dims[l - 1];
+            const float *W = a.raw + N.raw_w[l];
+            const float *b = a.raw + N.raw_b[l];
+            for (int q = threadIdx.x; q < no; q += blockDim.x) {
+                double acc = (double)b[q];
+                for (int c = 0; c < ni; ++c) acc = fma((double)W[(size_t)q * ni + c], act[cur][c], acc);
+                act[cur ^ 1][q] = (l < N.L && acc < 0.0) ? 0.0 : acc;
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        if (threadIdx.x == 0) {
+            double f = f_sh;
+            for (int i = 0; i < s; ++i) {
+                xs[i] += act[cur][i];
+                const double e = xs[i] - (double)a.goal[i];
+                f += e * e;
+            }
+            for (int j = 0; j < k; ++j) {
+                const double uu = (double)u[t * k + j];
+                f += (double)a.rho * uu * uu;
+            }
+            f_sh = f;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) row_sh = (f_sh < *a.inc_val) ? 1 : 0;
+    __syncthreads();
+    if (row_sh) {
+        for (int j = threadIdx.x; j < a.d; j += blockDim.x) a.inc_u[j] = u[j];
+        if (threadIdx.x == 0) *a.inc_val = f_sh;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static size_t rollout_smem_bytes(const NetDesc &N, int R, int d, bool wsmem)
+{
+    size_t f = (wsmem ? (size_t)N.img_floats : 0) + 2 * (size_t)R * N.maxw_p + (size_t)R * pad4(N.s) +
+               (size_t)R * pad4(N.k) + 2 * (size_t)pad4(d) + R + pad4(N.s);
+    return f * sizeof(float);
+}
+
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t st)
+{
+    constexpr int R = 64, NT = 256;
+    int dev;
+    cudaGetDevice(&dev);
+    int max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t budget = (size_t)max_optin - 1024;  // room for static shared memory
+    bool wsmem = rollout_smem_bytes(a.net, R, a.d, true) <= budget;
+    size_t smem = rollout_smem_bytes(a.net, R, a.d, wsmem);
+    if (smem > budget) return cudaErrorInvalidConfiguration;
+    if (a.n <= 0) return cudaSuccess;
+    k_fill_u64<<<(a.n + 255) / 256, 256, 0, st>>>(a.keys, a.n, ~0ull);
+    long long ntiles = (long long)a.n * ((a.M + R - 1) / R);
+    int grid = (int)(ntiles < (long long)num_sms ? ntiles : num_sms);
+    if (grid < 1) grid = 1;
+    if (wsmem) {
+        cudaFuncSetAttribute(k_rollout_fp32<R, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rollout_fp32<R, NT, true><<<grid, NT, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_rollout_fp32<R, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rollout_fp32<R, NT, false><<<grid, NT, smem, st>>>(a);
+    }
+    if (a.n > 0) k_rollout_finalize<<<a.n, 128, 0, st>>>(a);
+    if (a.inc_val && a.n > 0) k_incumbent_fp64<<<1, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace bab
