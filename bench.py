@@ -37,6 +37,7 @@ WORKLOAD = "pushing"
 N_PICK = 2048          # parents per iteration -> 4096 children bounded per iteration (--boxes changes it)
 SEED = 2024
 METRIC = "CROWN subdomain-bounds/s & rollout-steps/s at H=20"
+PRECISION = "bf16x3"   # rollout arithmetic (--precision)
 
 
 def workload_config():
@@ -44,7 +45,10 @@ def workload_config():
     c = W.CONFIGS[WORKLOAD]
     return {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
                         "rho=0.01, 4096 children bounded per iteration (2048 picked, widest-dim bisection), "
-                        "1024 uniform rollouts per child, FP32",
+                        "1024 uniform rollouts per child",
+            "rollout_arithmetic": {"fp32": "FP32 CUDA cores", "bf16x3": "tcgen05, 3-term BF16 split, FP32 accumulate",
+                                   "bf16": "tcgen05, BF16 operands, FP32 accumulate, FP32 re-score"}[PRECISION],
+            "bound_arithmetic": "FP32 CUDA cores, outward-rounded intervals, margin-corrected CROWN",
             "boxes_per_step": 2 * N_PICK, "samples_per_box": c["samples"], "H": c["H"],
             "initial_pool": "4096-box grid over [-1,1]^40", "l2": "flushed between steps (256 MiB write)"}
 
@@ -106,6 +110,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     """Dense FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -130,7 +137,7 @@ class BabIteration:
         f = dict(device=device, dtype=torch.float32)
         self.x0 = torch.as_tensor(self.p["x0"]).to(**f)
         self.goal = torch.as_tensor(self.p["goal"]).to(**f)
-        lo, hi, ids = W.grid_boxes(self.d, c["grid_dims"])
+        lo, hi, ids = W.grid_boxes(self.d, int(np.log2(self.nb)))  # 4096 boxes = the 12-level grid
         self.cap = 4096 + 64 * N_PICK  # enough for 60+ iterations of pool growth
         self.pool = [self._alloc(), self._alloc()]
         self.cur = 0
@@ -166,7 +173,7 @@ class BabIteration:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
         B.bab_rollout(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
-                      self.seed, B.PREC_FP32, P["ub"], self.best_u, self.inc_val, self.inc_u, d_n=d_n)
+                      self.seed, PRECISIONS[PRECISION], P["ub"], self.best_u, self.inc_val, self.inc_u, d_n=d_n)
         if time_rollout:
             e1.record()
             e2 = torch.cuda.Event(enable_timing=True)
@@ -244,20 +251,31 @@ def run_ours(args):
     flops_roll = 2.0 * it.nb * it.M * it.H * macs
     roll_avg = statistics.mean(roll_ms) / 1e3
     achieved = flops_roll / roll_avg / 1e12
-    peak = fp32_alu_peak_tflops(2070.0)
+    if PRECISION == "fp32":
+        roof = {"kernel": "k_rollout_fp32 (bab_rollout)", "bound": "alu", "peak": fp32_alu_peak_tflops(2070.0),
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz max SM clock"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        pk = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"kernel": "k_rollout_tc (bab_rollout)", "bound": "tensor", "peak": pk,
+                "peak_note": ("of measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "of fallback") +
+                             "; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe "
+                             "executes " + ("3x that (3-term BF16 split)" if PRECISION == "bf16x3" else
+                                            "the same (BF16 operands)") + " plus padding to multiples of 16"}
+    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": None})
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": "subdomain-bounds/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random network, start and goal)",
+           "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16"}[PRECISION],
+           "data": "synthetic (seeded random network, start and goal)",
            "config": dict(workload_config(), parallelism=f"independent problems x{ws}" if ws > 1 else "single GPU"),
            "rollout_steps_per_s": rsteps,
            "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound_crown": statistics.mean(crown_ms)},
            "crown_subdomain_bounds_per_s_kernel_only": it.nb / (statistics.mean(crown_ms) / 1e3),
            "incumbent_fp64": inc,
-           "roofline": {"kernel": "k_rollout_fp32 (bab_rollout)", "bound": "alu", "achieved": achieved,
-                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_note": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz max SM clock"},
+           "roofline": roof,
            "clocks": clocks, "e2e": e2e, "gpu_launches": it.launches_per_step * args.steps}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
@@ -383,6 +401,7 @@ def run_reference(args):
 
 
 def main():
+    global N_PICK, PRECISION
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -390,11 +409,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default=PRECISION,
+                    help="rollout arithmetic: fp32 (CUDA cores), bf16x3 (tcgen05, 3-term split), bf16 (tcgen05)")
     ap.add_argument("--boxes", type=int, default=2 * N_PICK,
                     help="children bounded per iteration; smaller values make small cases for profiler captures")
     args = ap.parse_args()
-    global N_PICK
     N_PICK = args.boxes // 2
+    PRECISION = args.precision
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

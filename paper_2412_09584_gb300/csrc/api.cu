@@ -15,8 +15,11 @@ using namespace bab;
 struct bab_ctx {
     int device = 0;
     int num_sms = 1;
+    int max_smem = 0;
     NetDesc net{};
     float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
+    uint8_t *d_tc = nullptr;
+    float *d_tc_bias = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int *d_status = nullptr;
@@ -24,6 +27,67 @@ struct bab_ctx {
 };
 
 namespace {
+
+uint16_t bf16_rn_host(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7FFFFFFFu) > 0x7F800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_to_f32_host(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Tensor-core layout of the network (see NetDesc) and its BF16 hi/lo image.
+void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, std::vector<float> &bias)
+{
+    const int L = N.L;
+    bool ok = N.s <= 32 && pad16(N.s + N.k) <= 64;
+    for (int l = 1; l < L; ++l) ok = ok && (N.dims[l] % 32 == 0);
+    int hi = 0, dcols = 16, acols = 8, bo = 0;
+    for (int l = 1; l <= L; ++l) {
+        N.tc_K[l] = pad16(N.dims[l - 1]);
+        N.tc_N[l] = pad16(N.dims[l]);
+        N.tc_hi[l] = hi;
+        hi += ((N.tc_K[l] + 63) / 64) * N.tc_N[l] * 128;
+        N.tc_boff[l] = bo;
+        bo += N.tc_N[l];
+        dcols = N.tc_N[l] > dcols ? N.tc_N[l] : dcols;
+        acols = N.tc_K[l] / 2 > acols ? N.tc_K[l] / 2 : acols;
+    }
+    for (int l = 1; l <= L; ++l) N.tc_lo[l] = hi + N.tc_hi[l];
+    N.tc_bytes_hi = hi;
+    N.tc_bytes = 2 * hi;
+    N.tc_bias_floats = bo;
+    N.tc_dcols = dcols;
+    N.tc_acols = acols;
+    N.tc_ok = ok ? 1 : 0;
+    img.assign((size_t)N.tc_bytes, 0);
+    bias.assign((size_t)bo, 0.f);
+    for (int l = 1; l <= L; ++l) {
+        const int no = N.dims[l], ni = N.dims[l - 1], Nl = N.tc_N[l];
+        const float *W = params + N.raw_w[l], *b = params + N.raw_b[l];
+        for (int n = 0; n < no; ++n) {
+            bias[N.tc_boff[l] + n] = b[n];
+            for (int kk = 0; kk < ni; ++kk) {
+                const float w = W[(size_t)n * ni + kk];
+                const uint16_t h = bf16_rn_host(w);
+                const uint16_t lo = bf16_rn_host(w - bf16_to_f32_host(h));
+                const int kb = kk / 64, within = kk % 64;
+                const size_t off = (size_t)kb * Nl * 128 + (size_t)n * 128 + (size_t)((((within * 2) / 16) ^ (n % 8)) * 16) +
+                                   (size_t)((within * 2) % 16);
+                std::memcpy(&img[N.tc_hi[l] + off], &h, 2);
+                std::memcpy(&img[N.tc_lo[l] + off], &lo, 2);
+            }
+        }
+    }
+}
 
 int fail(bab_ctx *c, int code, const char *fmt, ...)
 {
@@ -195,8 +259,17 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
             }
         for (int q = 0; q < no; ++q) fwd[N.fwd_b[l] + q] = bwd[N.bwd_b[l] + q] = b[q];
     }
+    std::vector<uint8_t> tc_img;
+    std::vector<float> tc_bias;
+    build_tc_image(N, params, tc_img, tc_bias);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tc, tc_img.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_bias, sizeof(float) * tc_bias.size());
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_tc, tc_img.data(), tc_img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_tc_bias, tc_bias.data(), sizeof(float) * tc_bias.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_raw, sizeof(float) * raw);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_fwd, sizeof(float) * img);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_bwd, sizeof(float) * img);
@@ -222,6 +295,8 @@ int bab_destroy(bab_ctx *c)
     cudaFree(c->d_raw);
     cudaFree(c->d_fwd);
     cudaFree(c->d_bwd);
+    cudaFree(c->d_tc);
+    cudaFree(c->d_tc_bias);
     cudaFree(c->scratch);
     cudaFree(c->d_status);
     delete c;
@@ -252,7 +327,12 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     if (n > 0 && (!id || !ub)) return fail(c, BAB_ERR_INVALID_ARG, "id and ub are required");
     if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
     if (inc_val && !best_u) return fail(c, BAB_ERR_INVALID_ARG, "the incumbent update needs best_u");
-    if (precision != BAB_PREC_FP32) return fail(c, BAB_ERR_UNSUPPORTED, "rollout precision %d not available", precision);
+    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3 && precision != BAB_PREC_BF16)
+        return fail(c, BAB_ERR_INVALID_ARG, "unknown precision %d", precision);
+    const int split = precision == BAB_PREC_BF16X3 ? 3 : 1;
+    if (precision != BAB_PREC_FP32 && !rollout_tc_supported(c->net, split, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout needs hidden widths that are multiples of 32, "
+                                            "s <= 32, s + k <= 64 and a weight image that fits in shared memory");
     if (n == 0) return BAB_OK;
     rc = ensure_scratch(c, (size_t)n * sizeof(unsigned long long) + 256);
     if (rc) return rc;
@@ -278,7 +358,11 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     a.inc_val = inc_val;
     a.inc_u = inc_u;
     a.status = c->d_status;
-    cudaError_t e = launch_rollout_fp32(a, c->num_sms, (cudaStream_t)stream);
+    a.tc_img = c->d_tc;
+    a.tc_bias = c->d_tc_bias;
+    a.tc_bytes = c->net.tc_bytes;
+    cudaError_t e = precision == BAB_PREC_FP32 ? launch_rollout_fp32(a, c->num_sms, (cudaStream_t)stream)
+                                               : launch_rollout_tc(a, split, c->num_sms, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "rollout kernels");
     return BAB_OK;
 }

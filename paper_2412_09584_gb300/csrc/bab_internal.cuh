@@ -34,7 +34,18 @@ struct NetDesc {
     int bwd_w[kMaxLayers + 1], bwd_b[kMaxLayers + 1];
     int img_floats;                           // floats in the fwd (= bwd) image
     int raw_floats;
+    // tensor-core image: per layer the BF16 hi halves of W_l (N_l x K_l, 128-byte
+    // swizzled K-major), all layers first, then the lo halves; N_l = pad16(d_l),
+    // K_l = pad16(d_{l-1}); FP32 biases padded to N_l
+    int tc_ok;
+    int tc_K[kMaxLayers + 1], tc_N[kMaxLayers + 1];
+    int tc_hi[kMaxLayers + 1], tc_lo[kMaxLayers + 1];  // byte offsets in the image
+    int tc_boff[kMaxLayers + 1];                       // float offsets in the bias vector
+    int tc_bytes, tc_bytes_hi, tc_bias_floats;
+    int tc_dcols, tc_acols;                            // TMEM columns: accumulator, A operand
 };
+
+__host__ __device__ constexpr int pad16(int x) { return (x + 15) & ~15; }
 
 // ---------------------------------------------------------------------------
 // Counter-based sampling: SplitMix64 output function (Steele, Lea and Flood,

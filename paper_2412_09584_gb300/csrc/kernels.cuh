@@ -22,6 +22,11 @@ struct RolloutArgs {
     double *inc_val;
     float *inc_u;
     int *status;
+    // tensor-core path
+    const uint8_t *tc_img;
+    const float *tc_bias;
+    int tc_bytes;        // bytes of the image the kernel loads (hi only for BF16)
+    uint32_t tmem_cols;
 };
 
 struct BoundArgs {
@@ -125,6 +130,11 @@ __device__ __forceinline__ void dense_rows_auto(const float *in, int ldi, const 
 
 // host launchers (return the first CUDA error)
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_rollout_tc(RolloutArgs a, int split, int num_sms, cudaStream_t st);
+bool rollout_tc_supported(const NetDesc &N, int split, int max_smem);
+void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st);
+void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st);
+void launch_incumbent(const RolloutArgs &a, cudaStream_t st);
 cudaError_t launch_ibp(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);

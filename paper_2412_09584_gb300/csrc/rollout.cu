@@ -234,7 +234,7 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t 
     size_t smem = rollout_smem_bytes(a.net, R, a.d, wsmem);
     if (smem > budget) return cudaErrorInvalidConfiguration;
     if (a.n <= 0) return cudaSuccess;
-    k_fill_u64<<<(a.n + 255) / 256, 256, 0, st>>>(a.keys, a.n, ~0ull);
+    k_fill_keys(a.keys, a.n, st);
     long long ntiles = (long long)a.n * ((a.M + R - 1) / R);
     int grid = (int)(ntiles < (long long)num_sms ? ntiles : num_sms);
     if (grid < 1) grid = 1;
@@ -245,9 +245,24 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t 
         cudaFuncSetAttribute(k_rollout_fp32<R, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rollout_fp32<R, NT, false><<<grid, NT, smem, st>>>(a);
     }
-    if (a.n > 0) k_rollout_finalize<<<a.n, 128, 0, st>>>(a);
-    if (a.inc_val && a.n > 0) k_incumbent_fp64<<<1, 256, 0, st>>>(a);
+    launch_rollout_finalize(a, st);
+    if (a.inc_val) launch_incumbent(a, st);
     return cudaGetLastError();
+}
+
+void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st)
+{
+    if (n > 0) k_fill_u64<<<(n + 255) / 256, 256, 0, st>>>(keys, n, ~0ull);
+}
+
+void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st)
+{
+    if (a.n > 0) k_rollout_finalize<<<a.n, 128, 0, st>>>(a);
+}
+
+void launch_incumbent(const RolloutArgs &a, cudaStream_t st)
+{
+    if (a.n > 0) k_incumbent_fp64<<<1, 256, 0, st>>>(a);
 }
 
 }  // namespace bab

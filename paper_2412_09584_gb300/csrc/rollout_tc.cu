@@ -1,0 +1,433 @@
+// rollout_tc.cu -- sampled search (Section 3.3) on tcgen05 tensor cores.
+//
+// A tile is M = 128 samples of one box (one sample per TMEM lane).  A CTA is
+// persistent and runs NSLOT tiles at once, ping-ponging the tensor core
+// between them:
+//
+//   warps 4s .. 4s+3 (slot s): the epilogue of slot s.  Thread r of the slot
+//     owns sample row r: it keeps the state x_t and the running cost in
+//     registers, draws u_t (counter-based), writes the input row [x_t|u_t|0]
+//     to TMEM as the A operand of layer 1, and after each layer reads the FP32
+//     accumulator row from TMEM, adds the bias, applies ReLU and writes the
+//     next layer's A operand back to TMEM (as BF16, or as a BF16 hi/lo pair
+//     for the 3-term split); after the last layer it adds the residual and
+//     the step cost.  No shared memory is touched per layer.
+//   warp 4*NSLOT: allocates TMEM, loads the weight image into shared memory
+//     once with the bulk copy engine, and issues every layer's MMAs
+//     (M=128, N = layer width, K = 16 per instruction) for the slots in
+//     turn, signalling completion on per-slot mbarriers.
+//
+// Precision: SPLIT = 3 computes each product as a_hi b_hi + a_hi b_lo +
+// a_lo b_hi with BF16 halves of the FP32 operands and FP32 accumulation
+// (about 2^-16 relative per product); SPLIT = 1 uses BF16 operands only.
+// Samples are drawn exactly as in the FP32 path (bit-identical u).
+//
+// Every mbarrier wait is bounded in time; on a time-out the kernel records
+// BAB_ERR_TIMEOUT, stops issuing work, waits (bounded) for its MMAs, frees
+// its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "bab_internal.cuh"
+#include "kernels.cuh"
+#include "tc_ptx.cuh"
+
+namespace bab {
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr int kKMax = 8;                          // action dimension limit of this kernel
+
+__device__ __forceinline__ uint32_t pack2(uint32_t lo16, uint32_t hi16) { return lo16 | (hi16 << 16); }
+
+__device__ __forceinline__ uint32_t bf16_rn(float f) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+
+// hi = bf16(v), lo = bf16(v - hi)
+__device__ __forceinline__ void split_bf16(float v, uint32_t &hi, uint32_t &lo)
+{
+    hi = bf16_rn(v);
+    lo = bf16_rn(v - __uint_as_float(hi << 16));
+}
+
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t phase, volatile int *abort)
+{
+    bool ok = tc::mbar_wait(bar, phase, abort, kWaitLimitNs);
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
+__device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
+{
+    set_status(status, BAB_ERR_TIMEOUT);
+    *abort = 1;
+}
+
+}  // namespace
+
+// SP: padded state width of the last layer (16 or 32).
+template <int NSLOT, int SPLIT, int SP>
+__global__ void __launch_bounds__(NSLOT * 128 + 32, 1) k_rollout_tc(RolloutArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float *bias = reinterpret_cast<float *>(wimg + a.tc_bytes);
+    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const NetDesc &N = a.net;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mma_warp = NSLOT * 4;
+    const int L = N.L, s = N.s, k = N.k;
+    volatile int *abort = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        tc::mbar_init(&bar_w, 1);
+        for (int i = 0; i < NSLOT; ++i) {
+            tc::mbar_init(&bar_a[i], 128);
+            tc::mbar_init(&bar_d[i], 1);
+        }
+        tc::mbar_init_fence();
+    }
+    if (warp == mma_warp) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+    for (int i = threadIdx.x; i < N.tc_bias_floats; i += blockDim.x) bias[i] = a.tc_bias[i];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == mma_warp * 32) {
+        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)a.tc_bytes);
+        constexpr uint32_t kChunk = 32768;
+        for (uint32_t off = 0; off < (uint32_t)a.tc_bytes; off += kChunk) {
+            const uint32_t sz = min(kChunk, (uint32_t)a.tc_bytes - off);
+            tc::bulk_g2s(wimg + off, a.tc_img + off, sz, &bar_w);
+        }
+    }
+    if (!warp_wait(&bar_w, 0, abort) && lane == 0) raise_abort(a.status, abort);
+
+    const int nlive = live_count(a.n, a.d_n);
+    const int tpb = (a.M + 127) / 128;
+    const long long ntiles = (long long)nlive * tpb;
+    const long long G = (long long)gridDim.x * NSLOT;
+    const uint32_t tb = tmem_base;
+    const int Dc = N.tc_dcols, Ac = N.tc_acols;
+    const int slot_cols = Dc + (SPLIT == 3 ? 2 : 1) * Ac;
+
+    if (warp < mma_warp) {
+        // ------------------------------- epilogue -------------------------------
+        const int slot = warp >> 2;
+        const int r = 32 * (warp & 3) + lane;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        const uint32_t dcol = tb + lane_off + slot * slot_cols;
+        const uint32_t acol_h = dcol + Dc, acol_l = acol_h + Ac;
+        const int K1 = N.tc_K[1];
+        uint32_t phD = 0;
+        float g[SP], x0v[SP];
+#pragma unroll
+        for (int i = 0; i < SP; ++i) {
+            g[i] = i < s ? a.goal[i] : 0.f;
+            x0v[i] = i < s ? a.x0[i] : 0.f;
+        }
+        for (long long tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
+            const int box = (int)(tile / tpb);
+            const int m = (int)(tile % tpb) * 128 + r;
+            const uint64_t hb = box_hash(a.seed, a.id[box]);
+            const float *blo = a.lo + (size_t)box * a.d, *bhi = a.hi + (size_t)box * a.d;
+            float x[SP];
+#pragma unroll
+            for (int i = 0; i < SP; ++i) x[i] = x0v[i];
+            float cost = 0.f;
+            bool ok = true;
+            for (int t = 0; t < a.H && ok; ++t) {
+                // layer-1 input row [x_t | u_t | 0], K1 <= 64 BF16 values
+                float u[kKMax];
+#pragma unroll
+                for (int j = 0; j < kKMax; ++j) {
+                    if (j < k) {
+                        const int jj = t * k + j;
+                        u[j] = draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj));
+                        cost = fmaf(a.rho * u[j], u[j], cost);
+                    } else {
+                        u[j] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int c16 = 0; c16 < 4; ++c16) {
+                    if (c16 * 16 >= K1) break;
+                    uint32_t ph[8], pl[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        uint32_t h2[2], l2[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int i = c16 * 16 + 2 * q + e;
+                            float v = 0.f;
+#pragma unroll
+                            for (int ii = 0; ii < SP; ++ii)
+                                if (ii == i && ii < s) v = x[ii];
+#pragma unroll
+                            for (int j = 0; j < kKMax; ++j)
+                                if (i == s + j && j < k) v = u[j];
+                            if (SPLIT == 3) split_bf16(v, h2[e], l2[e]);
+                            else h2[e] = bf16_rn(v), l2[e] = 0;
+                        }
+                        ph[q] = pack2(h2[0], h2[1]);
+                        pl[q] = pack2(l2[0], l2[1]);
+                    }
+                    tc::tmem_st8(acol_h + c16 * 8, ph);
+                    if (SPLIT == 3) tc::tmem_st8(acol_l + c16 * 8, pl);
+                }
+                tc::tmem_wait_st();
+                tc::fence_before_sync();
+                tc::mbar_arrive(&bar_a[slot]);
+                for (int l = 1; l <= L; ++l) {
+                    if (!warp_wait(&bar_d[slot], phD, abort)) {
+                        if (lane == 0) raise_abort(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    phD ^= 1;
+                    tc::fence_after_sync();
+                    const float *bl = bias + N.tc_boff[l];
+                    if (l < L) {
+                        const int Nl = N.tc_N[l];
+                        for (int c0 = 0; c0 < Nl; c0 += 32) {
+                            uint32_t v[32];
+                            tc::tmem_ld32(dcol + c0, v);
+                            tc::tmem_wait_ld();
+                            uint32_t ph[16], pl[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                uint32_t h2[2], l2[2];
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    const float z = fmaxf(__uint_as_float(v[2 * q + e]) + bl[c0 + 2 * q + e], 0.f);
+                                    if (SPLIT == 3) split_bf16(z, h2[e], l2[e]);
+                                    else h2[e] = bf16_rn(z), l2[e] = 0;
+                                }
+                                ph[q] = pack2(h2[0], h2[1]);
+                                pl[q] = pack2(l2[0], l2[1]);
+                            }
+                            tc::tmem_st16(acol_h + c0 / 2, ph);
+                            if (SPLIT == 3) tc::tmem_st16(acol_l + c0 / 2, pl);
+                        }
+                        tc::tmem_wait_st();
+                        tc::fence_before_sync();
+                        tc::mbar_arrive(&bar_a[slot]);
+                    } else {
+                        float dx[SP];
+                        if (SP == 16) {
+                            uint32_t v[16];
+                            tc::tmem_ld16(dcol, v);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) dx[i % SP] = __uint_as_float(v[i]);
+                        } else {
+                            uint32_t v[32];
+                            tc::tmem_ld32(dcol, v);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < SP; ++i) dx[i] = __uint_as_float(v[i % 32]);
+                        }
+                        float c = 0.f;
+#pragma unroll
+                        for (int i = 0; i < SP; ++i) {
+                            if (i < s) {
+                                x[i] = x[i] + (dx[i] + bl[i]);
+                                const float e = x[i] - g[i];
+                                c = fmaf(e, e, c);
+                            }
+                        }
+                        cost += c;
+                    }
+                }
+            }
+            if (!ok) break;
+            // best (f, m) of the warp's 32 rows
+            unsigned long long key =
+                (m < a.M) ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+                key = other < key ? other : key;
+            }
+            if (lane == 0 && key != ~0ull) atomicMin(&a.keys[box], key);
+        }
+    } else if (lane == 0) {
+        // ------------------------------- MMA issuer -------------------------------
+        long long left[NSLOT];
+        int lcur[NSLOT];
+        uint32_t phA[NSLOT], ncommit[NSLOT];
+        for (int sl = 0; sl < NSLOT; ++sl) {
+            const long long gi = (long long)blockIdx.x * NSLOT + sl;
+            const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
+            left[sl] = cnt * a.H * L;
+            lcur[sl] = 1;
+            phA[sl] = 0;
+            ncommit[sl] = 0;
+        }
+        bool any = true;
+        while (any && !*abort) {
+            any = false;
+            for (int sl = 0; sl < NSLOT; ++sl) {
+                if (left[sl] == 0) continue;
+                any = true;
+                if (!tc::mbar_wait(&bar_a[sl], phA[sl], abort, kWaitLimitNs)) {
+                    raise_abort(a.status, abort);
+                    break;
+                }
+                phA[sl] ^= 1;
+                tc::fence_after_sync();
+                const int l = lcur[sl];
+                const int Kl = N.tc_K[l], Nl = N.tc_N[l];
+                const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
+                const uint32_t dcol = tb + sl * slot_cols;
+                const uint32_t ah = dcol + Dc, al = ah + Ac;
+                const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
+                for (int ks = 0; ks < Kl / 16; ++ks) {
+                    const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
+                    const uint64_t dh = tc::desc_sw128(bh + boff);
+                    tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                    if (SPLIT == 3) {
+                        tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
+                        tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                    }
+                }
+                tc::mma_commit(&bar_d[sl]);
+                ++ncommit[sl];
+                lcur[sl] = (l == L) ? 1 : l + 1;
+                --left[sl];
+            }
+        }
+        if (*abort) {
+            // let every issued MMA finish before the TMEM is released
+            for (int sl = 0; sl < NSLOT; ++sl)
+                if (ncommit[sl]) {
+                    volatile int never = 0;
+                    tc::mbar_wait(&bar_d[sl], (ncommit[sl] - 1) & 1, &never, kWaitLimitNs);
+                }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == mma_warp) {
+        __syncwarp();
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tb, a.tmem_cols);
+    }
+}
+
+// Per box: ub and best_u from the packed minimum; in BF16 mode the chosen
+// sample is re-scored in FP32 on CUDA cores (one CTA per box).
+__global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
+{
+    const NetDesc &N = a.net;
+    const int box = blockIdx.x;
+    if (box >= live_count(a.n, a.d_n)) return;
+    __shared__ float act[2][kMaxWidth + 4];
+    __shared__ float xs[kMaxWidth];
+    __shared__ float f_sh;
+    const unsigned long long key = a.keys[box];
+    const uint32_t m = (uint32_t)(key & 0xFFFFFFFFu);
+    const uint64_t hb = box_hash(a.seed, a.id[box]);
+    const int s = N.s, k = N.k, d = a.d;
+    const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
+    for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = a.x0[i];
+    if (threadIdx.x == 0) f_sh = 0.f;
+    __syncthreads();
+    for (int t = 0; t < a.H; ++t) {
+        for (int c = threadIdx.x; c < s + k; c += blockDim.x)
+            act[0][c] = c < s ? xs[c] : draw_sample(hb, m, (uint32_t)(t * k + c - s), blo[t * k + c - s], bhi[t * k + c - s]);
+        __syncthreads();
+        int cur = 0;
+        for (int l = 1; l <= N.L; ++l) {
+            const int no = N.dims[l], ni = N.dims[l - 1];
+            const float *W = a.raw + N.raw_w[l];
+            const float *b = a.raw + N.raw_b[l];
+            for (int q = threadIdx.x; q < no; q += blockDim.x) {
+                float acc = b[q];
+                for (int c = 0; c < ni; ++c) acc = fmaf(W[(size_t)q * ni + c], act[cur][c], acc);
+                act[cur ^ 1][q] = (l < N.L) ? fmaxf(acc, 0.f) : acc;
+            }
+            __syncthreads();
+            cur ^= 1;
+        }
+        if (threadIdx.x == 0) {
+            float f = f_sh;
+            for (int j = 0; j < k; ++j) {
+                const float u = draw_sample(hb, m, (uint32_t)(t * k + j), blo[t * k + j], bhi[t * k + j]);
+                f = fmaf(a.rho * u, u, f);
+            }
+            float c = 0.f;
+            for (int i = 0; i < s; ++i) {
+                xs[i] = xs[i] + act[cur][i];
+                const float e = xs[i] - a.goal[i];
+                c = fmaf(e, e, c);
+            }
+            f_sh = f + c;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ub[box] = f_sh;
+    if (a.best_u)
+        for (int j = threadIdx.x; j < d; j += blockDim.x)
+            a.best_u[(size_t)box * d + j] = draw_sample(hb, m, (uint32_t)j, blo[j], bhi[j]);
+}
+
+template <int NSLOT, int SPLIT, int SP>
+static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_rollout_tc<NSLOT, SPLIT, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_rollout_tc<NSLOT, SPLIT, SP><<<grid, NSLOT * 128 + 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Tensor-core variant available for this network and precision?
+bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
+{
+    if (!N.tc_ok || N.s > 32 || N.k > kKMax || N.tc_K[1] > 64) return false;
+    const size_t img = split == 3 ? N.tc_bytes : N.tc_bytes_hi;
+    return img + N.tc_bias_floats * 4 + 1024 + 2048 <= (size_t)max_smem;
+}
+
+cudaError_t launch_rollout_tc(RolloutArgs a, int split, int num_sms, cudaStream_t st)
+{
+    const NetDesc &N = a.net;
+    if (a.n <= 0) return cudaSuccess;
+    // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
+    const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols;
+    const int nslot = (2 * slot_cols <= 512) ? 2 : 1;
+    int cols = 32;
+    while (cols < nslot * slot_cols) cols *= 2;
+    if (cols > 512) return cudaErrorInvalidConfiguration;
+    a.tmem_cols = (uint32_t)cols;
+    if (split == 1) {
+        // BF16 only: the weight image is the hi halves, laid out contiguously first
+        a.tc_bytes = N.tc_bytes_hi;
+    }
+    const size_t smem = a.tc_bytes + (size_t)N.tc_bias_floats * 4 + 1024;
+    const long long ntiles = (long long)a.n * ((a.M + 127) / 128);
+    int grid = (int)((ntiles + nslot - 1) / nslot);
+    grid = grid < num_sms ? grid : num_sms;
+    k_fill_keys(a.keys, a.n, st);
+    cudaError_t e;
+    const int SPv = N.tc_N[N.L];
+    if (SPv != 16 && SPv != 32) return cudaErrorInvalidConfiguration;
+    if (nslot == 2) {
+        if (split == 3) e = SPv == 16 ? launch_tc_variant<2, 3, 16>(a, grid, smem, st) : launch_tc_variant<2, 3, 32>(a, grid, smem, st);
+        else e = SPv == 16 ? launch_tc_variant<2, 1, 16>(a, grid, smem, st) : launch_tc_variant<2, 1, 32>(a, grid, smem, st);
+    } else {
+        if (split == 3) e = SPv == 16 ? launch_tc_variant<1, 3, 16>(a, grid, smem, st) : launch_tc_variant<1, 3, 32>(a, grid, smem, st);
+        else e = SPv == 16 ? launch_tc_variant<1, 1, 16>(a, grid, smem, st) : launch_tc_variant<1, 1, 32>(a, grid, smem, st);
+    }
+    if (e != cudaSuccess) return e;
+    if (split == 1) {
+        k_rescore_fp32<<<a.n, 256, 0, st>>>(a);
+    } else {
+        launch_rollout_finalize(a, st);
+    }
+    if (a.inc_val) launch_incumbent(a, st);
+    return cudaGetLastError();
+}
+
+}  // namespace bab

@@ -283,3 +283,51 @@ def test_pushing_full_size_sampled(oracle, gp):
     # properties at every box: bounds below the sampled objective, finite margins
     assert np.all(c["lb"] <= r["ub"]) and np.all(np.isfinite(c["margin"]))
     assert r["inc_val"] == pytest.approx(oracle.objective(p, r["inc_u"].astype(np.float64)), rel=1e-10)
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# tensor-core rollouts (tcgen05): 3-term BF16 split and plain BF16 with an FP32 re-score
+# ----------------------------------------------------------------------------------------------------------------
+
+REL_BF16X3 = 1e-5   # three BF16 partial products per FP32 product: about 2^-16 relative each, FP32 accumulation
+
+
+def test_tc_samples_bit_identical(oracle, gp):
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem("pushing", 7)
+    lo, hi, ids = W.dyadic_boxes(40, 9, seed=7, max_depth=3)
+    g = gp(p)
+    for prec in (B.PREC_BF16X3, B.PREC_BF16):
+        r = g.rollout(lo, hi, ids, M=1, seed=31, precision=prec)
+        _, bu_o, _ = oracle.rollout(p, lo, hi, ids, 1, 31)
+        assert np.array_equal(r["best_u"].view(np.uint32), bu_o.view(np.uint32))
+
+
+@pytest.mark.parametrize("name,M", [("pushing", 256), ("pushing", 300), ("tiny", 256), ("tiny", 77)])
+def test_tc_bf16x3_rollout_matches_oracle(oracle, gp, name, M):
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem(name, 8)
+    d = p["k"] * p["H"]
+    lo, hi, ids = W.dyadic_boxes(d, 10, seed=8, max_depth=3)
+    g = gp(p)
+    r = g.rollout(lo, hi, ids, M=M, seed=12, precision=B.PREC_BF16X3, incumbent=True)
+    ub_o, _, _ = oracle.rollout(p, lo, hi, ids, M, 12)
+    np.testing.assert_allclose(r["ub"], ub_o, rtol=REL_BF16X3, atol=0)
+    f_best = np.array([oracle.objective(p, u.astype(np.float64)) for u in r["best_u"]])
+    assert np.all(f_best <= ub_o * (1 + 2 * REL_BF16X3))
+    assert r["inc_val"] == pytest.approx(oracle.objective(p, r["inc_u"].astype(np.float64)), rel=1e-10)
+
+
+def test_tc_bf16_rollout_rescored(oracle, gp):
+    """BF16 operands pick each box's best sample; its value is then re-scored in FP32, so ub equals the objective
+    of the returned plan to FP32 accuracy and is close to the best sampled value."""
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem("pushing", 9)
+    lo, hi, ids = W.dyadic_boxes(40, 10, seed=9, max_depth=3)
+    g = gp(p)
+    r = g.rollout(lo, hi, ids, M=256, seed=13, precision=B.PREC_BF16, incumbent=True)
+    ub_o, _, _ = oracle.rollout(p, lo, hi, ids, 256, 13)
+    f_best = np.array([oracle.objective(p, u.astype(np.float64)) for u in r["best_u"]])
+    np.testing.assert_allclose(r["ub"], f_best, rtol=REL)
+    assert np.all(f_best >= ub_o * (1 - 1e-12))
+    np.testing.assert_allclose(r["ub"], ub_o, rtol=1e-2)
