@@ -4,18 +4,19 @@
 // persistent and runs NSLOT tiles at once, ping-ponging the tensor core
 // between them:
 //
-//   warps 4s .. 4s+3 (slot s): the epilogue of slot s.  Thread r of the slot
-//     owns sample row r: it keeps the state x_t and the running cost in
-//     registers, draws u_t (counter-based), writes the input row [x_t|u_t|0]
-//     to TMEM as the A operand of layer 1, and after each layer reads the FP32
-//     accumulator row from TMEM, adds the bias, applies ReLU and writes the
-//     next layer's A operand back to TMEM (as BF16, or as a BF16 hi/lo pair
-//     for the 3-term split); after the last layer it adds the residual and
-//     the step cost.  No shared memory is touched per layer.
-//   warp 4*NSLOT: allocates TMEM, loads the weight image into shared memory
-//     once with the bulk copy engine, and issues every layer's MMAs
-//     (M=128, N = layer width, K = 16 per instruction) for the slots in
-//     turn, signalling completion on per-slot mbarriers.
+//   warps 8s .. 8s+7 (slot s): the epilogue of slot s.  Thread r of warps
+//     8s .. 8s+3 owns sample row r: it keeps the state x_t and the running
+//     cost in registers, draws u_t (counter-based), writes the input row
+//     [x_t|u_t|0] to TMEM as the A operand of layer 1, and after the last
+//     layer adds the residual and the step cost.  After each hidden layer the
+//     warp pair of a lane quadrant reads the FP32 accumulator row from TMEM
+//     (one half of the columns each), adds the bias, applies ReLU and writes
+//     the next layer's A operand back to TMEM (as BF16, or as a BF16 hi/lo
+//     pair for the 3-term split).  No shared memory is written per layer.
+//   warps 8*NSLOT + s: issue every layer's MMAs of slot s (M=128, N = layer
+//     width, K = 16 per instruction), signalling completion on the slot's
+//     mbarrier; the first of them allocates TMEM and loads the weight image
+//     into shared memory once with the bulk copy engine.
 //
 // Precision: SPLIT = 3 computes each product as a_hi b_hi + a_hi b_lo +
 // a_lo b_hi with BF16 halves of the FP32 operands and FP32 accumulation
@@ -37,16 +38,20 @@ namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 constexpr int kKMax = 8;                          // action dimension limit of this kernel
+constexpr int kEpiWarps = 8;                      // epilogue warps per tile slot (2 per TMEM lane quadrant)
 
-__device__ __forceinline__ uint32_t pack2(uint32_t lo16, uint32_t hi16) { return lo16 | (hi16 << 16); }
-
-__device__ __forceinline__ uint32_t bf16_rn(float f) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f)); }
-
-// hi = bf16(v), lo = bf16(v - hi)
-__device__ __forceinline__ void split_bf16(float v, uint32_t &hi, uint32_t &lo)
+// (a, b) -> packed BF16 pair, a in the low half, round to nearest even
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
-    hi = bf16_rn(v);
-    lo = bf16_rn(v - __uint_as_float(hi << 16));
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// hi = bf16(v), lo = bf16(v - hi), for a pair of values
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    hi = pack_bf16x2(a, b);
+    lo = pack_bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xFFFF0000u));
 }
 
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t phase, volatile int *abort)
@@ -65,17 +70,19 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 
 // SP: padded state width of the last layer (16 or 32).
 template <int NSLOT, int SPLIT, int SP>
-__global__ void __launch_bounds__(NSLOT * 128 + 32, 1) k_rollout_tc(RolloutArgs a)
+__global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tc(RolloutArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
+    const NetDesc &N = a.net;
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float *bias = reinterpret_cast<float *>(wimg + a.tc_bytes);
+    float *goal_s = bias + N.tc_bias_floats;
+    float *x0_s = goal_s + SP;
     __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    const NetDesc &N = a.net;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mma_warp = NSLOT * 4;
+    const int mma_warp = NSLOT * kEpiWarps;
     const int L = N.L, s = N.s, k = N.k;
     volatile int *abort = &abort_flag;
 
@@ -83,13 +90,17 @@ __global__ void __launch_bounds__(NSLOT * 128 + 32, 1) k_rollout_tc(RolloutArgs 
         abort_flag = 0;
         tc::mbar_init(&bar_w, 1);
         for (int i = 0; i < NSLOT; ++i) {
-            tc::mbar_init(&bar_a[i], 128);
+            tc::mbar_init(&bar_a[i], kEpiWarps);
             tc::mbar_init(&bar_d[i], 1);
         }
         tc::mbar_init_fence();
     }
     if (warp == mma_warp) tc::tmem_alloc(&tmem_base, a.tmem_cols);
     for (int i = threadIdx.x; i < N.tc_bias_floats; i += blockDim.x) bias[i] = a.tc_bias[i];
+    for (int i = threadIdx.x; i < SP; i += blockDim.x) {
+        goal_s[i] = i < s ? a.goal[i] : 0.f;
+        x0_s[i] = i < s ? a.x0[i] : 0.f;
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -113,19 +124,18 @@ __global__ void __launch_bounds__(NSLOT * 128 + 32, 1) k_rollout_tc(RolloutArgs 
 
     if (warp < mma_warp) {
         // ------------------------------- epilogue -------------------------------
-        const int slot = warp >> 2;
-        const int r = 32 * (warp & 3) + lane;
-        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        // Slot `slot` has 8 warps; warps q and q + 4 share TMEM lane quadrant q
+        // (rows 32q .. 32q + 31).  The primary warp (q < 4) owns the rows' state;
+        // for hidden layers whose width is a multiple of 64 the two warps of a
+        // quadrant split the columns.
+        const int slot = warp / kEpiWarps, qw = warp % kEpiWarps, quad = qw & 3;
+        const bool primary = qw < 4;
+        const int r = 32 * quad + lane;
+        const uint32_t lane_off = (uint32_t)(32 * quad) << 16;
         const uint32_t dcol = tb + lane_off + slot * slot_cols;
         const uint32_t acol_h = dcol + Dc, acol_l = acol_h + Ac;
         const int K1 = N.tc_K[1];
         uint32_t phD = 0;
-        float g[SP], x0v[SP];
-#pragma unroll
-        for (int i = 0; i < SP; ++i) {
-            g[i] = i < s ? a.goal[i] : 0.f;
-            x0v[i] = i < s ? a.x0[i] : 0.f;
-        }
         for (long long tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
             const int box = (int)(tile / tpb);
             const int m = (int)(tile % tpb) * 128 + r;
@@ -133,51 +143,53 @@ __global__ void __launch_bounds__(NSLOT * 128 + 32, 1) k_rollout_tc(RolloutArgs 
             const float *blo = a.lo + (size_t)box * a.d, *bhi = a.hi + (size_t)box * a.d;
             float x[SP];
 #pragma unroll
-            for (int i = 0; i < SP; ++i) x[i] = x0v[i];
+            for (int i = 0; i < SP; ++i) x[i] = x0_s[i];
             float cost = 0.f;
             bool ok = true;
             for (int t = 0; t < a.H && ok; ++t) {
-                // layer-1 input row [x_t | u_t | 0], K1 <= 64 BF16 values
-                float u[kKMax];
+                if (primary) {
+                    // layer-1 input row [x_t | u_t | 0], K1 <= 64 BF16 values
+                    float u[kKMax];
 #pragma unroll
-                for (int j = 0; j < kKMax; ++j) {
-                    if (j < k) {
-                        const int jj = t * k + j;
-                        u[j] = draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj));
-                        cost = fmaf(a.rho * u[j], u[j], cost);
-                    } else {
-                        u[j] = 0.f;
-                    }
-                }
-#pragma unroll
-                for (int c16 = 0; c16 < 4; ++c16) {
-                    if (c16 * 16 >= K1) break;
-                    uint32_t ph[8], pl[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        uint32_t h2[2], l2[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int i = c16 * 16 + 2 * q + e;
-                            float v = 0.f;
-#pragma unroll
-                            for (int ii = 0; ii < SP; ++ii)
-                                if (ii == i && ii < s) v = x[ii];
-#pragma unroll
-                            for (int j = 0; j < kKMax; ++j)
-                                if (i == s + j && j < k) v = u[j];
-                            if (SPLIT == 3) split_bf16(v, h2[e], l2[e]);
-                            else h2[e] = bf16_rn(v), l2[e] = 0;
+                    for (int j = 0; j < kKMax; ++j) {
+                        if (j < k) {
+                            const int jj = t * k + j;
+                            u[j] = draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj));
+                            cost = fmaf(a.rho * u[j], u[j], cost);
+                        } else {
+                            u[j] = 0.f;
                         }
-                        ph[q] = pack2(h2[0], h2[1]);
-                        pl[q] = pack2(l2[0], l2[1]);
                     }
-                    tc::tmem_st8(acol_h + c16 * 8, ph);
-                    if (SPLIT == 3) tc::tmem_st8(acol_l + c16 * 8, pl);
+#pragma unroll
+                    for (int c16 = 0; c16 < 4; ++c16) {
+                        if (c16 * 16 >= K1) break;
+                        uint32_t ph[8], pl[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            float v2[2];
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const int i = c16 * 16 + 2 * q + e;
+                                float v = 0.f;
+#pragma unroll
+                                for (int ii = 0; ii < SP; ++ii)
+                                    if (ii == i && ii < s) v = x[ii];
+#pragma unroll
+                                for (int j = 0; j < kKMax; ++j)
+                                    if (i == s + j && j < k) v = u[j];
+                                v2[e] = v;
+                            }
+                            if (SPLIT == 3) split2(v2[0], v2[1], ph[q], pl[q]);
+                            else ph[q] = pack_bf16x2(v2[0], v2[1]);
+                        }
+                        tc::tmem_st8(acol_h + c16 * 8, ph);
+                        if (SPLIT == 3) tc::tmem_st8(acol_l + c16 * 8, pl);
+                    }
+                    tc::tmem_wait_st();
                 }
-                tc::tmem_wait_st();
                 tc::fence_before_sync();
-                tc::mbar_arrive(&bar_a[slot]);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bar_a[slot]);
                 for (int l = 1; l <= L; ++l) {
                     if (!warp_wait(&bar_d[slot], phD, abort)) {
                         if (lane == 0) raise_abort(a.status, abort);
@@ -187,123 +199,126 @@ __global__ void __launch_bounds__(NSLOT * 128 + 32, 1) k_rollout_tc(RolloutArgs 
                     phD ^= 1;
                     tc::fence_after_sync();
                     const float *bl = bias + N.tc_boff[l];
-                    if (l < L) {
-                        const int Nl = N.tc_N[l];
-                        for (int c0 = 0; c0 < Nl; c0 += 32) {
+                    const int Nl = N.tc_N[l];
+                    const bool split_cols = (Nl % 64 == 0);
+                    int c_beg = 0, c_end = Nl;
+                    if (split_cols) {
+                        c_beg = primary ? 0 : Nl / 2;
+                        c_end = c_beg + Nl / 2;
+                    } else if (!primary) {
+                        c_end = 0;
+                    }
+                    if (l == L) {
+                        // network output: residual step and step cost (the primary warps own the rows)
+                        if (primary) {
+                            float dx[SP];
+                            if (SP == 16) {
+                                uint32_t v[16];
+                                tc::tmem_ld16(dcol, v);
+                                tc::tmem_wait_ld();
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) dx[i % SP] = __uint_as_float(v[i]);
+                            } else {
+                                uint32_t v[32];
+                                tc::tmem_ld32(dcol, v);
+                                tc::tmem_wait_ld();
+#pragma unroll
+                                for (int i = 0; i < SP; ++i) dx[i] = __uint_as_float(v[i % 32]);
+                            }
+                            float c = 0.f;
+#pragma unroll
+                            for (int i = 0; i < SP; ++i) {
+                                if (i < s) {
+                                    x[i] = x[i] + (dx[i] + bl[i]);
+                                    const float e = x[i] - goal_s[i];
+                                    c = fmaf(e, e, c);
+                                }
+                            }
+                            cost += c;
+                        }
+                    } else {
+                        for (int c0 = c_beg; c0 < c_end; c0 += 32) {
                             uint32_t v[32];
                             tc::tmem_ld32(dcol + c0, v);
                             tc::tmem_wait_ld();
+                            const float4 *b4 = reinterpret_cast<const float4 *>(bl + c0);
                             uint32_t ph[16], pl[16];
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                uint32_t h2[2], l2[2];
-#pragma unroll
-                                for (int e = 0; e < 2; ++e) {
-                                    const float z = fmaxf(__uint_as_float(v[2 * q + e]) + bl[c0 + 2 * q + e], 0.f);
-                                    if (SPLIT == 3) split_bf16(z, h2[e], l2[e]);
-                                    else h2[e] = bf16_rn(z), l2[e] = 0;
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 bb = b4[q];
+                                const float z0 = fmaxf(__uint_as_float(v[4 * q + 0]) + bb.x, 0.f);
+                                const float z1 = fmaxf(__uint_as_float(v[4 * q + 1]) + bb.y, 0.f);
+                                const float z2 = fmaxf(__uint_as_float(v[4 * q + 2]) + bb.z, 0.f);
+                                const float z3 = fmaxf(__uint_as_float(v[4 * q + 3]) + bb.w, 0.f);
+                                if (SPLIT == 3) {
+                                    split2(z0, z1, ph[2 * q], pl[2 * q]);
+                                    split2(z2, z3, ph[2 * q + 1], pl[2 * q + 1]);
+                                } else {
+                                    ph[2 * q] = pack_bf16x2(z0, z1);
+                                    ph[2 * q + 1] = pack_bf16x2(z2, z3);
                                 }
-                                ph[q] = pack2(h2[0], h2[1]);
-                                pl[q] = pack2(l2[0], l2[1]);
                             }
                             tc::tmem_st16(acol_h + c0 / 2, ph);
                             if (SPLIT == 3) tc::tmem_st16(acol_l + c0 / 2, pl);
                         }
                         tc::tmem_wait_st();
                         tc::fence_before_sync();
-                        tc::mbar_arrive(&bar_a[slot]);
-                    } else {
-                        float dx[SP];
-                        if (SP == 16) {
-                            uint32_t v[16];
-                            tc::tmem_ld16(dcol, v);
-                            tc::tmem_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) dx[i % SP] = __uint_as_float(v[i]);
-                        } else {
-                            uint32_t v[32];
-                            tc::tmem_ld32(dcol, v);
-                            tc::tmem_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < SP; ++i) dx[i] = __uint_as_float(v[i % 32]);
-                        }
-                        float c = 0.f;
-#pragma unroll
-                        for (int i = 0; i < SP; ++i) {
-                            if (i < s) {
-                                x[i] = x[i] + (dx[i] + bl[i]);
-                                const float e = x[i] - g[i];
-                                c = fmaf(e, e, c);
-                            }
-                        }
-                        cost += c;
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&bar_a[slot]);
                     }
                 }
             }
             if (!ok) break;
-            // best (f, m) of the warp's 32 rows
-            unsigned long long key =
-                (m < a.M) ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
+            if (primary) {
+                // best (f, m) of the warp's 32 rows
+                unsigned long long key =
+                    (m < a.M) ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
-                key = other < key ? other : key;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+                    key = other < key ? other : key;
+                }
+                if (lane == 0 && key != ~0ull) atomicMin(&a.keys[box], key);
             }
-            if (lane == 0 && key != ~0ull) atomicMin(&a.keys[box], key);
         }
     } else if (lane == 0) {
-        // ------------------------------- MMA issuer -------------------------------
-        long long left[NSLOT];
-        int lcur[NSLOT];
-        uint32_t phA[NSLOT], ncommit[NSLOT];
-        for (int sl = 0; sl < NSLOT; ++sl) {
-            const long long gi = (long long)blockIdx.x * NSLOT + sl;
-            const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
-            left[sl] = cnt * a.H * L;
-            lcur[sl] = 1;
-            phA[sl] = 0;
-            ncommit[sl] = 0;
-        }
-        bool any = true;
-        while (any && !*abort) {
-            any = false;
-            for (int sl = 0; sl < NSLOT; ++sl) {
-                if (left[sl] == 0) continue;
-                any = true;
-                if (!tc::mbar_wait(&bar_a[sl], phA[sl], abort, kWaitLimitNs)) {
-                    raise_abort(a.status, abort);
-                    break;
-                }
-                phA[sl] ^= 1;
-                tc::fence_after_sync();
-                const int l = lcur[sl];
-                const int Kl = N.tc_K[l], Nl = N.tc_N[l];
-                const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
-                const uint32_t dcol = tb + sl * slot_cols;
-                const uint32_t ah = dcol + Dc, al = ah + Ac;
-                const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
-                for (int ks = 0; ks < Kl / 16; ++ks) {
-                    const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
-                    const uint64_t dh = tc::desc_sw128(bh + boff);
-                    tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
-                    if (SPLIT == 3) {
-                        tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
-                        tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
-                    }
-                }
-                tc::mma_commit(&bar_d[sl]);
-                ++ncommit[sl];
-                lcur[sl] = (l == L) ? 1 : l + 1;
-                --left[sl];
+        // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
+        const int sl = warp - mma_warp;
+        const long long gi = (long long)blockIdx.x * NSLOT + sl;
+        const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
+        long long left = cnt * a.H * L;
+        int l = 1;
+        uint32_t phA = 0, ncommit = 0;
+        const uint32_t dcol = tb + sl * slot_cols;
+        const uint32_t ah = dcol + Dc, al = ah + Ac;
+        while (left > 0 && !*abort) {
+            if (!tc::mbar_wait(&bar_a[sl], phA, abort, kWaitLimitNs)) {
+                raise_abort(a.status, abort);
+                break;
             }
-        }
-        if (*abort) {
-            // let every issued MMA finish before the TMEM is released
-            for (int sl = 0; sl < NSLOT; ++sl)
-                if (ncommit[sl]) {
-                    volatile int never = 0;
-                    tc::mbar_wait(&bar_d[sl], (ncommit[sl] - 1) & 1, &never, kWaitLimitNs);
+            phA ^= 1;
+            tc::fence_after_sync();
+            const int Kl = N.tc_K[l], Nl = N.tc_N[l];
+            const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
+            const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
+            for (int ks = 0; ks < Kl / 16; ++ks) {
+                const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
+                const uint64_t dh = tc::desc_sw128(bh + boff);
+                tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                if (SPLIT == 3) {
+                    tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
+                    tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
                 }
+            }
+            tc::mma_commit(&bar_d[sl]);
+            ++ncommit;
+            l = (l == L) ? 1 : l + 1;
+            --left;
+        }
+        if (*abort && ncommit) {
+            // let every issued MMA finish before the TMEM is released
+            volatile int never = 0;
+            tc::mbar_wait(&bar_d[sl], (ncommit - 1) & 1, &never, kWaitLimitNs);
         }
     }
     tc::fence_before_sync();
@@ -378,16 +393,24 @@ static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem
     cudaError_t e = cudaFuncSetAttribute(k_rollout_tc<NSLOT, SPLIT, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_rollout_tc<NSLOT, SPLIT, SP><<<grid, NSLOT * 128 + 32, smem, st>>>(a);
+    k_rollout_tc<NSLOT, SPLIT, SP><<<grid, NSLOT * (kEpiWarps + 1) * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 // Tensor-core variant available for this network and precision?
+static size_t rollout_tc_smem(const NetDesc &N, int split, int nslot)
+{
+    const int SP = N.tc_N[N.L];
+    const size_t img = split == 3 ? N.tc_bytes : N.tc_bytes_hi;
+    (void)nslot;
+    const size_t floats = (size_t)N.tc_bias_floats + 2 * SP;
+    return img + floats * 4 + 1024;
+}
+
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
 {
-    if (!N.tc_ok || N.s > 32 || N.k > kKMax || N.tc_K[1] > 64) return false;
-    const size_t img = split == 3 ? N.tc_bytes : N.tc_bytes_hi;
-    return img + N.tc_bias_floats * 4 + 1024 + 2048 <= (size_t)max_smem;
+    if (!N.tc_ok || N.L < 2 || N.s > 32 || N.k > kKMax || N.tc_K[1] > 64) return false;
+    return rollout_tc_smem(N, split, 2) + 1024 <= (size_t)max_smem;
 }
 
 cudaError_t launch_rollout_tc(RolloutArgs a, int split, int num_sms, cudaStream_t st)
@@ -405,7 +428,7 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int num_sms, cudaStream_
         // BF16 only: the weight image is the hi halves, laid out contiguously first
         a.tc_bytes = N.tc_bytes_hi;
     }
-    const size_t smem = a.tc_bytes + (size_t)N.tc_bias_floats * 4 + 1024;
+    const size_t smem = rollout_tc_smem(N, split, nslot);
     const long long ntiles = (long long)a.n * ((a.M + 127) / 128);
     int grid = (int)((ntiles + nslot - 1) / nslot);
     grid = grid < num_sms ? grid : num_sms;
