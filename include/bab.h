@@ -231,6 +231,41 @@ int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, cons
  */
 int bab_status(bab_ctx *ctx, void *stream);
 
+/* Size of the fixed device working area of bab_bound_crown_static. */
+#define BAB_STATIC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * bab_bound_crown without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant of the CROWN bound above.
+ *
+ * It is for callers that may not call cudaMalloc (or cudaFree, which also
+ * synchronises the device) when they need a bound: for example a plugin
+ * whose enqueue step runs inside a host framework that owns all device
+ * memory, or a real-time planning loop that must not allocate once it runs.
+ * It takes no context (creating one allocates).  The network comes as a
+ * DEVICE pointer in the layout of bab_load_dynamics, and all working memory
+ * (padded weight images, interval bounds, rounding-error helpers) lives in
+ * one fixed array of BAB_STATIC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads the library keeps until the process exits.
+ *   n_layers, dims (HOST int[L+1]), state_dim, action_dim: as bab_load_dynamics.
+ *   params     DEVICE float array, packed W_1, b_1, ..., W_L, b_L (caller-owned).
+ *   x0, goal, horizon, rho, lo, hi, n: as bab_bound_crown (adaptive slopes,
+ *              FP32 arithmetic; d_n is not supported).
+ *   lb, margin device float[n] (margin nullable): as bab_bound_crown.
+ * The call needs 4 * (2 * image + n * H * (3 * sumh + s) + 2 * n * (H + 1) * s)
+ * bytes (image = the padded network, about the parameter count); if that
+ * exceeds BAB_STATIC_SCRATCH_BYTES it returns BAB_ERR_SHAPE before any
+ * device work.  The first call on a device (with that device current) looks
+ * up the array's device address once; make that first call before any stream
+ * capture.  All calls share the one array, so calls whose GPU work overlaps
+ * (on different streams or host threads) race: order them on one stream.
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_UNSUPPORTED (device
+ * index >= 64), BAB_ERR_CUDA.  There is no context, so no bab_last_error.
+ */
+int bab_bound_crown_static(int n_layers, const int *dims, const float *params, int state_dim, int action_dim,
+                           const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                           const float *hi, int n, float *lb, float *margin, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
     L.bab_alpha_step.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _I, _F, _P, _P, _P, _P]
     L.bab_prune_branch.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _I, _P, _P, _P, _P, _P, _P, _P,
                                    _P]
+    L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
     _lib = L
     return L
 
@@ -179,3 +180,15 @@ def bab_prune_branch(ctx, d, lo, hi, lb, ub, ids, n, inc_val, n_pick, eta, cap_o
                                  _ptr(out_id, torch.uint64), _ptr(keep, torch.uint8), _ptr(d_counts, torch.int32),
                                  _stream(stream))
     _check(ctx, rc)
+
+
+def bab_bound_crown_static(dims, params, state_dim, action_dim, x0, goal, horizon, rho, lo, hi, n, lb, margin=None,
+                           stream=None):
+    """The CROWN bound without device allocation (no context): `params` is a CUDA tensor holding the packed
+    network; returns the library's status code instead of raising, so callers can test for BAB_ERR_SHAPE."""
+    f32 = torch.float32
+    dims_a = (_I * len(dims))(*[int(x) for x in dims])
+    return load().bab_bound_crown_static(len(dims) - 1, dims_a, _ptr(params, f32, "params"), int(state_dim),
+                                         int(action_dim), _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho),
+                                         _ptr(lo, f32), _ptr(hi, f32), int(n), _ptr(lb, f32), _ptr(margin, f32),
+                                         _stream(stream))
