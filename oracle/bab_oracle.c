@@ -386,6 +386,7 @@ static double quad_min(double mu, double rho, double lo, double hi, double *arg)
 typedef struct {
     double lb;          /* concretized lower bound */
     double lin_const;   /* f(u) >= lin_const + mu . u + rho ||u||^2 on the box */
+    double scale;       /* sum of |each term added into the bound|: the magnitude rounding errors scale with */
 } crown_out;
 
 /*
@@ -412,7 +413,7 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
 {
     int s = N->s, k = N->k, L = N->L, sumh = N->sumh;
     double lam[ORC_MAX_WIDTH], A[ORC_MAX_WIDTH], An[ORC_MAX_WIDTH];
-    double cst = 0.0;
+    double cst = 0.0, cabs = 0.0;
     double *mu_loc = (double *)malloc(sizeof(double) * k * H);
 
     /* tangent coefficients a_{t,i} = 2 m and constants -2 m g - m^2 */
@@ -424,6 +425,7 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
             double m = 0.5 * (Ls + Us);
             a[(size_t)t * s + i] = 2.0 * m;
             cst += -2.0 * m * goal[i] - m * m;
+            cabs += fabs(2.0 * m * goal[i]) + m * m;
         }
     }
     for (int i = 0; i < s; ++i) lam[i] = a[(size_t)H * s + i];
@@ -432,7 +434,10 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
         /* last linear layer: A = lam on z_L */
         int nL = N->dims[L], nLm = N->dims[L - 1];
         for (int q = 0; q < nL; ++q) A[q] = lam[q];
-        for (int q = 0; q < nL; ++q) cst += A[q] * N->b[L][q];
+        for (int q = 0; q < nL; ++q) {
+            cst += A[q] * N->b[L][q];
+            cabs += fabs(A[q] * N->b[L][q]);
+        }
         for (int p = 0; p < nLm; ++p) {
             double acc = 0.0;
             for (int q = 0; q < nL; ++q) acc += A[q] * N->W[L][(size_t)q * nLm + p];
@@ -450,9 +455,13 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
                 if (A_pre) A_pre[idx] = A[q];
                 oracle_relu_relax(zl, zu, al, A[q] >= 0.0 ? 0 : 1, &D, &c);
                 cst += A[q] * c;
+                cabs += fabs(A[q] * c);
                 A[q] *= D;
             }
-            for (int q = 0; q < no; ++q) cst += A[q] * N->b[l][q];
+            for (int q = 0; q < no; ++q) {
+                cst += A[q] * N->b[l][q];
+                cabs += fabs(A[q] * N->b[l][q]);
+            }
             for (int p = 0; p < ni; ++p) {
                 double acc = 0.0;
                 for (int q = 0; q < no; ++q) acc += A[q] * N->W[l][(size_t)q * ni + p];
@@ -464,19 +473,24 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
         for (int j = 0; j < k; ++j) mu_loc[t * k + j] = A[s + j];
         for (int i = 0; i < s; ++i) lam[i] = lam[i] + A[i] + (t >= 1 ? a[(size_t)t * s + i] : 0.0);
     }
-    for (int i = 0; i < s; ++i) cst += lam[i] * x0[i];
+    for (int i = 0; i < s; ++i) {
+        cst += lam[i] * x0[i];
+        cabs += fabs(lam[i] * x0[i]);
+    }
 
     double lb = cst;
     for (int j = 0; j < k * H; ++j) {
         double arg;
-        lb += quad_min(mu_loc[j], rho, lo[j], hi[j], &arg);
+        double v = quad_min(mu_loc[j], rho, lo[j], hi[j], &arg);
+        lb += v;
+        cabs += fabs(v);
         if (ustar) ustar[j] = arg;
         if (mu) mu[j] = mu_loc[j];
     }
     if (atan) memcpy(atan, a, sizeof(double) * (size_t)(H + 1) * s);
     free(a);
     free(mu_loc);
-    crown_out o = {lb, cst};
+    crown_out o = {lb, cst, cabs};
     return o;
 }
 
@@ -484,11 +498,14 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
  * CROWN lower bound of each box, with IBP intermediate bounds.  Outputs (all
  * but lb nullable): lb [n], lin_coef [n][d] and lin_const [n] such that
  * f(u) >= lin_const + lin_coef . u + rho ||u||^2 on the box, ustar [n][d],
- * A_pre [n][H][sumh].
+ * A_pre [n][H][sumh], and scale [n]: the sum of the absolute values of every
+ * term added into the bound (tangent constants, A.b, A.c, lam.x0 and the
+ * concretized terms), the magnitude that rounding errors of any evaluation
+ * order scale with; tests use it as the tolerance scale.
  */
 int oracle_crown(int L, const int *dims, const double *params, int s, int k, int H, double rho, const double *x0,
                  const double *goal, int n, const double *lo, const double *hi, const double *alpha, double *lb,
-                 double *lin_coef, double *lin_const, double *ustar, double *A_pre)
+                 double *lin_coef, double *lin_const, double *ustar, double *A_pre, double *scale)
 {
     onet N;
     if (onet_init(&N, L, dims, params, s, k)) return -1;
@@ -506,6 +523,7 @@ int oracle_crown(int L, const int *dims, const double *params, int s, int k, int
                                 A_pre ? A_pre + (size_t)i * nh : NULL, NULL);
         lb[i] = o.lb;
         if (lin_const) lin_const[i] = o.lin_const;
+        if (scale) scale[i] = o.scale;
     }
     free(pl);
     free(pu);

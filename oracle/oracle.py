@@ -184,12 +184,14 @@ def crown(problem, lo, hi, alpha=None):
     cst = np.zeros(n)
     us = np.zeros((n, d))
     Ap = np.zeros((n, H, max(net.sumh, 1)))
+    scale = np.zeros(n)
     rc = lib().oracle_crown(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi, palpha,
                             lb.ctypes.data_as(_c_double_p), mu.ctypes.data_as(_c_double_p),
                             cst.ctypes.data_as(_c_double_p), us.ctypes.data_as(_c_double_p),
-                            Ap.ctypes.data_as(_c_double_p))
+                            Ap.ctypes.data_as(_c_double_p), scale.ctypes.data_as(_c_double_p))
     assert rc == 0
-    return {"lb": lb, "lin_coef": mu, "lin_const": cst, "ustar": us, "A_pre": Ap[:, :, :net.sumh]}
+    return {"lb": lb, "lin_coef": mu, "lin_const": cst, "ustar": us, "A_pre": Ap[:, :, :net.sumh],
+            "scale": scale}
 
 
 def alpha_grad(problem, lo, hi, alpha=None):

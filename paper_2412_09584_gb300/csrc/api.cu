@@ -18,7 +18,7 @@ struct bab_ctx {
     int max_smem = 0;
     NetDesc net{};
     float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
-    uint8_t *d_tc = nullptr;
+    uint8_t *d_tc = nullptr, *d_tcb = nullptr;
     float *d_tc_bias = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -86,6 +86,41 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
                 std::memcpy(&img[N.tc_lo[l] + off], &lo, 2);
             }
         }
+    }
+}
+
+// Backward tensor-core image: B_l = W_l^T (rows n < d_{l-1}, K = d_l), BF16 hi then lo, 128-byte swizzled.
+void build_tcb_image(NetDesc &N, const float *params, std::vector<uint8_t> &img)
+{
+    const int L = N.L;
+    int hi = 0, dcols = 16, acols = 8;
+    for (int l = 1; l <= L; ++l) {
+        N.tcb_K[l] = pad16(N.dims[l]);
+        N.tcb_N[l] = pad16(N.dims[l - 1]);
+        N.tcb_hi[l] = hi;
+        hi += ((N.tcb_K[l] + 63) / 64) * N.tcb_N[l] * 128;
+        dcols = N.tcb_N[l] > dcols ? N.tcb_N[l] : dcols;
+        acols = N.tcb_K[l] / 2 > acols ? N.tcb_K[l] / 2 : acols;
+    }
+    for (int l = 1; l <= L; ++l) N.tcb_lo[l] = hi + N.tcb_hi[l];
+    N.tcb_bytes = 2 * hi;
+    N.tcb_dcols = dcols;
+    N.tcb_acols = acols;
+    img.assign((size_t)N.tcb_bytes, 0);
+    for (int l = 1; l <= L; ++l) {
+        const int no = N.dims[l], ni = N.dims[l - 1], Nl = N.tcb_N[l];
+        const float *W = params + N.raw_w[l];
+        for (int n = 0; n < ni; ++n)
+            for (int kk = 0; kk < no; ++kk) {
+                const float w = W[(size_t)kk * ni + n];
+                const uint16_t h = bf16_rn_host(w);
+                const uint16_t lo = bf16_rn_host(w - bf16_to_f32_host(h));
+                const int kb = kk / 64, within = kk % 64;
+                const size_t off = (size_t)kb * Nl * 128 + (size_t)n * 128 +
+                                   (size_t)((((within * 2) / 16) ^ (n % 8)) * 16) + (size_t)((within * 2) % 16);
+                std::memcpy(&img[N.tcb_hi[l] + off], &h, 2);
+                std::memcpy(&img[N.tcb_lo[l] + off], &lo, 2);
+            }
     }
 }
 
@@ -262,10 +297,14 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
     std::vector<uint8_t> tc_img;
     std::vector<float> tc_bias;
     build_tc_image(N, params, tc_img, tc_bias);
+    std::vector<uint8_t> tcb_img;
+    build_tcb_image(N, params, tcb_img);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tc, tc_img.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tcb, tcb_img.size());
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_tcb, tcb_img.data(), tcb_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_bias, sizeof(float) * tc_bias.size());
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tc, tc_img.data(), tc_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -296,6 +335,7 @@ int bab_destroy(bab_ctx *c)
     cudaFree(c->d_fwd);
     cudaFree(c->d_bwd);
     cudaFree(c->d_tc);
+    cudaFree(c->d_tcb);
     cudaFree(c->d_tc_bias);
     cudaFree(c->scratch);
     cudaFree(c->d_status);
@@ -390,9 +430,14 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
     if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
-    if (precision != BAB_PREC_FP32) return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
+    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
+        return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
+    const bool tc = precision == BAB_PREC_BF16X3;
+    if (tc && !crown_tc_supported(c->net, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN needs hidden widths that are multiples of 32, "
+                                            "s <= 32, s + k <= 48 and a weight image that fits in shared memory");
     if (n == 0) return BAB_OK;
-    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, false));
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, tc));
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
@@ -404,7 +449,15 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
     a.margin = margin;
     a.lin_coef = lin_coef;
     a.lin_const = lin_const;
-    cudaError_t e = launch_crown(a, c->num_sms, st);
+    cudaError_t e;
+    if (tc) {
+        a.tcb_img = c->d_tcb;
+        a.tc_bias = c->d_tc_bias;
+        a.mu = lin_coef ? lin_coef : cv.take<float>((size_t)n * a.d);
+        e = launch_crown_tc(a, c->num_sms, st);
+    } else {
+        e = launch_crown(a, c->num_sms, st);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
     return BAB_OK;
 }

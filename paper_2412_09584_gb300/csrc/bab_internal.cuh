@@ -43,6 +43,11 @@ struct NetDesc {
     int tc_boff[kMaxLayers + 1];                       // float offsets in the bias vector
     int tc_bytes, tc_bytes_hi, tc_bias_floats;
     int tc_dcols, tc_acols;                            // TMEM columns: accumulator, A operand
+    // backward tensor-core image: per layer B = W_l^T as pad16(d_{l-1}) rows of pad16(d_l)
+    // (the product A' W_l over a tile of boxes), hi halves of all layers, then lo halves
+    int tcb_K[kMaxLayers + 1], tcb_N[kMaxLayers + 1];
+    int tcb_hi[kMaxLayers + 1], tcb_lo[kMaxLayers + 1];
+    int tcb_bytes, tcb_dcols, tcb_acols;
 };
 
 __host__ __device__ constexpr int pad16(int x) { return (x + 15) & ~15; }
@@ -127,6 +132,29 @@ __device__ __forceinline__ float sq_min_rd(float lo, float hi)
     if (lo > 0.f) return __fmul_rd(lo, lo);
     if (hi < 0.f) return __fmul_rd(hi, hi);
     return 0.f;
+}
+
+// Lemma 1 (Appendix B.1) with outward rounding: slope D and intercept c of
+// the selected linear bound of ReLU on [zl, zu] for coefficient A (the lower
+// bound where A >= 0, the upper where A < 0).  The upper chord is replaced by
+// a line that lies above it on [zl, zu]: slope rounded up, intercept -D zl
+// rounded up.
+__device__ __forceinline__ void relax_select(float zl, float zu, float A, float alpha_j, bool has_alpha, float &D,
+                                             float &c)
+{
+    if (zl >= 0.f) {
+        D = 1.f;
+        c = 0.f;
+    } else if (zu <= 0.f) {
+        D = 0.f;
+        c = 0.f;
+    } else if (A >= 0.f) {
+        D = has_alpha ? alpha_j : (zu >= -zl ? 1.f : 0.f);
+        c = 0.f;
+    } else {
+        D = __fdiv_ru(zu, __fsub_rd(zu, zl));
+        c = __fmul_ru(D, -zl);
+    }
 }
 
 // Device status codes written by kernels (sticky, first error wins).

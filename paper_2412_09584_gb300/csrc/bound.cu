@@ -220,30 +220,6 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
             if (box0 + r < nlive) a.lb_ibp[box0 + r] = lbacc[r];
 }
 
-// ---------------------------------------------------------------------------
-// Lemma 1 with outward rounding: slope D and intercept c of the selected
-// linear bound of ReLU on [zl, zu] for coefficient A (lower if A >= 0).
-// The upper chord is replaced by a line that lies above it on [zl, zu]:
-// slope rounded up, intercept -D zl rounded up.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void relax_select(float zl, float zu, float A, float alpha_j, bool has_alpha, float &D,
-                                             float &c)
-{
-    if (zl >= 0.f) {
-        D = 1.f;
-        c = 0.f;
-    } else if (zu <= 0.f) {
-        D = 0.f;
-        c = 0.f;
-    } else if (A >= 0.f) {
-        D = has_alpha ? alpha_j : (zu >= -zl ? 1.f : 0.f);
-        c = 0.f;
-    } else {
-        D = __fdiv_ru(zu, __fsub_rd(zu, zl));
-        c = __fmul_ru(D, -zl);
-    }
-}
-
 template <bool WSMEM>
 __global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
 {

@@ -1,0 +1,432 @@
+// bound_tc.cu -- backward CROWN (Appendix B.1, Theorem 1) with the per-layer
+// products A' W_l on tcgen05 tensor cores, 3-term BF16 split, FP32 accumulate.
+//
+// A tile is 128 boxes, one box per TMEM lane.  Per time step t = H-1 .. 0 the
+// coefficient row of each box runs backward through the network:
+//
+//   lam (coefficient of x_{t+1})  --x W_L^T-->  coefficient on a_{L-1}
+//   relax (Lemma 1)               --x W_{L-1}^T--> ...  --x W_1^T-->  [x_t | u_t]
+//
+// Each product is an MMA chain D[box][j] = sum_k A'[box][k] W_l[k][j] with A'
+// (the relaxed coefficients, BF16 hi/lo) in TMEM and W_l^T (BF16 hi/lo) in
+// shared memory, loaded once by the bulk copy engine.  The epilogue warps read
+// the FP32 accumulator rows from TMEM, apply Lemma 1 with the interval bounds
+// of bab_bound_ibp (outward-rounded slope and intercept), add the constant
+// terms rounded down, accumulate the rounding-error margin rounded up, and
+// write the next A' back to TMEM.  The margin for a split product is
+// (3.1 * 2^-16 + gamma_K) sum_k |A'_k| S_k: the BF16 hi/lo representation of
+// both operands and the dropped lo*lo term cost at most 3.1 * 2^-16 of
+// |A'_k| |W_kj| per term, and gamma_K (unit 2^-23, allowing a truncating
+// accumulator) covers the FP32 sum; S_k = sum_j |W_kj| max|a_j| comes from IBP.
+//
+// Warp roles are those of k_rollout_tc: per slot 8 epilogue warps (primary
+// and helper of each TMEM lane quadrant, splitting the columns of hidden
+// layers) and one MMA issuer warp.  Every wait is bounded in time.
+#include <cuda_bf16.h>
+
+#include "bab_internal.cuh"
+#include "kernels.cuh"
+#include "tc_ptx.cuh"
+
+namespace bab {
+
+namespace {
+
+constexpr uint64_t kWaitNs = 2000000000ull;
+constexpr int kEpi = 8;
+constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20)
+
+__device__ __forceinline__ float gamma_tc(int K)
+{
+    // split error of one product term plus the FP32 accumulation of K terms
+    const double u = 1.1920928955078125e-07;  // 2^-23
+    return (float)(3.1 * 1.52587890625e-05 + K * u / (1.0 - K * u)) * 1.000001f;
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    hi = pack2(a, b);
+    lo = pack2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xFFFF0000u));
+}
+
+__device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t phase, volatile int *abort)
+{
+    return __all_sync(0xFFFFFFFFu, tc::mbar_wait(bar, phase, abort, kWaitNs));
+}
+__device__ __forceinline__ void abort_all(int *status, volatile int *abort)
+{
+    set_status(status, BAB_ERR_TIMEOUT);
+    *abort = 1;
+}
+
+// tangent of s^2 at the midpoint of the interval of s = x - g (outward-rounded ends)
+__device__ __forceinline__ void tangent(float xl, float xu, float g, float &coef, float &cterm)
+{
+    const float Ls = __fsub_rd(xl, g), Us = __fsub_ru(xu, g);
+    const float m = 0.5f * (Ls + Us);
+    coef = 2.f * m;
+    cterm = __fmaf_rd(-coef, g, -__fmul_ru(m, m));
+}
+
+}  // namespace
+
+// SP: padded state width (16 or 32); KP1: padded width of [x | u] (<= 64)
+template <int NSLOT, int SP>
+__global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const NetDesc &N = a.net;
+    uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float *bias = reinterpret_cast<float *>(wimg + N.tcb_bytes);
+    float *pair = bias + N.tc_bias_floats;  // [NSLOT][128][2]: helper warps' (constant, margin) partials
+    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_p[NSLOT * 4];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mma_warp = NSLOT * kEpi;
+    const int L = N.L, s = N.s, k = N.k, H = a.H, d = a.d, sumh = N.sumh, sw = N.sumh + N.s;
+    volatile int *abort = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        tc::mbar_init(&bar_w, 1);
+        for (int i = 0; i < NSLOT; ++i) {
+            tc::mbar_init(&bar_a[i], kEpi);
+            tc::mbar_init(&bar_d[i], 1);
+            for (int q = 0; q < 4; ++q) tc::mbar_init(&bar_p[i * 4 + q], 1);
+        }
+        tc::mbar_init_fence();
+    }
+    if (warp == mma_warp) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+    for (int i = threadIdx.x; i < N.tc_bias_floats; i += blockDim.x) bias[i] = a.tc_bias[i];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == mma_warp * 32) {
+        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
+        for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
+            tc::bulk_g2s(wimg + off, a.tcb_img + off, min(32768u, (uint32_t)N.tcb_bytes - off), &bar_w);
+    }
+    if (!wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
+
+    const int nlive = live_count(a.n, a.d_n);
+    const int ntiles = (nlive + 127) / 128;
+    const int G = gridDim.x * NSLOT;
+    const uint32_t tb = tmem_base;
+    const int Dc = N.tcb_dcols, Ac = N.tcb_acols;
+    const int slot_cols = Dc + 2 * Ac;
+    const bool has_alpha = a.alpha != nullptr;
+
+    if (warp < mma_warp) {
+        const int slot = warp / kEpi, qw = warp % kEpi, quad = qw & 3;
+        const bool primary = qw < 4;
+        const int r = 32 * quad + lane;
+        const uint32_t dcol = tb + ((uint32_t)(32 * quad) << 16) + slot * slot_cols;
+        const uint32_t acol_h = dcol + Dc, acol_l = acol_h + Ac;
+        uint32_t phD = 0, phP = 0;
+        for (int tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
+            const int box = tile * 128 + r;
+            const bool valid = box < nlive;
+            float lam[SP];
+            float cst = 0.f, mg = 0.f;  // constant (rounded down), margin (rounded up): this warp's share
+            bool ok = true;
+            if (primary) {
+                // tangent of ||x_H - g||^2
+#pragma unroll
+                for (int i = 0; i < SP; ++i) {
+                    lam[i] = 0.f;
+                    if (i < s && valid) {
+                        const size_t xi = ((size_t)box * (H + 1) + H) * s + i;
+                        float cf, ct;
+                        tangent(a.x_lo[xi], a.x_hi[xi], a.goal[i], cf, ct);
+                        lam[i] = cf;
+                        cst = __fadd_rd(cst, ct);
+                    }
+                }
+            }
+            for (int t = H - 1; t >= 0 && ok; --t) {
+                const size_t rowb = ((size_t)box * H + t);
+                // ---- last layer: A = lam on z_L; constant lam . b_L; product lam W_L^T ----
+                if (primary) {
+                    const float *bL = bias + N.tc_boff[L];
+                    float e = 0.f;
+                    uint32_t ph[8], pl[8];
+#pragma unroll
+                    for (int c16 = 0; c16 < SP / 16; ++c16) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int i0 = c16 * 16 + 2 * q;
+                            const float v0 = (i0 < s) ? lam[i0] : 0.f, v1 = (i0 + 1 < s) ? lam[i0 + 1] : 0.f;
+                            split2(v0, v1, ph[q], pl[q]);
+                        }
+                        tc::tmem_st8(acol_h + c16 * 8, ph);
+                        tc::tmem_st8(acol_l + c16 * 8, pl);
+                    }
+#pragma unroll
+                    for (int i = 0; i < SP; ++i)
+                        if (i < s && valid) {
+                            cst = __fmaf_rd(lam[i], bL[i], cst);
+                            e = __fmaf_ru(fabsf(lam[i]), a.S[rowb * sw + sumh + i], e);
+                        }
+                    mg = __fmaf_ru(gamma_tc(N.tcb_K[L]), e, mg);
+                    tc::tmem_wait_st();
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bar_a[slot]);
+                // ---- hidden layers l = L-1 .. 1: relax the coefficient on a_l, product with W_l^T ----
+                for (int l = L - 1; l >= 1; --l) {
+                    if (!wwait(&bar_d[slot], phD, abort)) {
+                        if (lane == 0) abort_all(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    phD ^= 1;
+                    tc::fence_after_sync();
+                    const int dl = N.dims[l];
+                    const int c_beg = primary ? 0 : dl / 2, c_end = (dl % 64 == 0) ? c_beg + dl / 2 : (primary ? dl : 0);
+                    const float *bl = bias + N.tc_boff[l];
+                    const float gK = gamma_tc(N.tcb_K[l]);
+                    float eg = 0.f, er = 0.f;
+                    for (int c0 = c_beg; c0 < c_end; c0 += 32) {
+                        uint32_t v[32];
+                        tc::tmem_ld32(dcol + c0, v);
+                        tc::tmem_wait_ld();
+                        const size_t ib = rowb * sumh + N.hoff[l] + c0;
+                        uint32_t ph[16], pl[16];
+#pragma unroll
+                        for (int q4 = 0; q4 < 8; ++q4) {
+                            float4 zl4 = make_float4(0.f, 0.f, 0.f, 0.f), zu4 = zl4, al4 = zl4;
+                            if (valid) {
+                                zl4 = *reinterpret_cast<const float4 *>(a.pre_lo + ib + 4 * q4);
+                                zu4 = *reinterpret_cast<const float4 *>(a.pre_hi + ib + 4 * q4);
+                                if (has_alpha) al4 = *reinterpret_cast<const float4 *>(a.alpha + ib + 4 * q4);
+                            }
+                            const float zlv[4] = {zl4.x, zl4.y, zl4.z, zl4.w}, zuv[4] = {zu4.x, zu4.y, zu4.z, zu4.w};
+                            const float alv[4] = {al4.x, al4.y, al4.z, al4.w};
+                            float ap[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int j = 4 * q4 + e;
+                                const float A = valid ? __uint_as_float(v[j]) : 0.f;
+                                float D, c;
+                                relax_select(zlv[e], zuv[e], A, alv[e], has_alpha, D, c);
+                                const float Ap = A * D;
+                                ap[e] = Ap;
+                                if (valid) {
+                                    if (a.A_pre) a.A_pre[ib + j] = A;
+                                    cst = __fmaf_rd(A, c, cst);
+                                    cst = __fmaf_rd(Ap, bl[c0 + j], cst);
+                                    eg = __fmaf_ru(fabsf(Ap), a.S[rowb * sw + N.hoff[l] + c0 + j], eg);
+                                    if (D != 0.f && D != 1.f) er = __fmaf_ru(fabsf(Ap), fmaxf(-zlv[e], zuv[e]), er);
+                                }
+                            }
+                            split2(ap[0], ap[1], ph[2 * q4], pl[2 * q4]);
+                            split2(ap[2], ap[3], ph[2 * q4 + 1], pl[2 * q4 + 1]);
+                        }
+                        tc::tmem_st16(acol_h + c0 / 2, ph);
+                        tc::tmem_st16(acol_l + c0 / 2, pl);
+                    }
+                    mg = __fadd_ru(mg, __fmaf_ru(gK, eg, __fmul_ru(kTwoU, er)));
+                    tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bar_a[slot]);
+                }
+                if (!ok) break;
+                // ---- coefficient on [x_t | u_t]: mu_t, and lam <- lam + A_x (+ tangent of x_t) ----
+                if (!wwait(&bar_d[slot], phD, abort)) {
+                    if (lane == 0) abort_all(a.status, abort);
+                    ok = false;
+                    break;
+                }
+                phD ^= 1;
+                tc::fence_after_sync();
+                if (primary) {
+                    float ax[SP + 16];
+                    const int K1 = N.tcb_N[1];
+#pragma unroll
+                    for (int c16 = 0; c16 < (SP + 16) / 16; ++c16) {
+                        if (c16 * 16 >= K1) break;
+                        uint32_t v[16];
+                        tc::tmem_ld16(dcol + c16 * 16, v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) ax[c16 * 16 + j] = __uint_as_float(v[j]);
+                    }
+                    if (valid) {
+#pragma unroll
+                        for (int j = 0; j < SP + 16; ++j)
+                            if (j >= s && j < s + k) a.mu[(size_t)box * d + t * k + (j - s)] = ax[j];
+                    }
+                    float e = 0.f;
+#pragma unroll
+                    for (int i = 0; i < SP; ++i) {
+                        if (i < s) {
+                            float aa = 0.f, B;
+                            if (t >= 1 && valid) {
+                                const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
+                                const float xl = a.x_lo[xi], xu = a.x_hi[xi];
+                                float ct;
+                                tangent(xl, xu, a.goal[i], aa, ct);
+                                cst = __fadd_rd(cst, ct);
+                                B = fmaxf(fabsf(xl), fabsf(xu));
+                            } else {
+                                B = fabsf(a.x0[i]);
+                            }
+                            const float lo_ = lam[i], Ax = ax[i];
+                            lam[i] = (lo_ + Ax) + aa;
+                            const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
+                            e = __fmaf_ru(__fmul_ru(kTwoU, mag), B, e);
+                        }
+                    }
+                    if (valid) mg = __fadd_ru(mg, e);
+                }
+            }
+            if (!ok) break;
+            // ---- combine with the helper's share, concretize (Theorem 2, box form), write ----
+            float *pp = pair + ((size_t)slot * 128 + r) * 2;
+            if (!primary) {
+                pp[0] = cst;
+                pp[1] = mg;
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bar_p[slot * 4 + quad]);
+            } else {
+                if (!wwait(&bar_p[slot * 4 + quad], phP, abort)) {
+                    if (lane == 0) abort_all(a.status, abort);
+                    break;
+                }
+                phP ^= 1;
+                cst = __fadd_rd(cst, pp[0]);
+                mg = __fadd_ru(mg, pp[1]);
+                if (valid) {
+                    float c = 0.f, vsum = 0.f, e = 0.f;
+#pragma unroll
+                    for (int i = 0; i < SP; ++i)
+                        if (i < s) c = __fmaf_rd(lam[i], a.x0[i], c);
+                    c = __fadd_rd(cst, c);
+                    for (int j = 0; j < d; ++j) {
+                        const float m_ = a.mu[(size_t)box * d + j];
+                        const float lo = a.lo[(size_t)box * d + j], hi = a.hi[(size_t)box * d + j];
+                        float us, vj;
+                        if (a.rho > 0.f) {
+                            const float uc = -m_ / (2.f * a.rho);
+                            if (uc >= lo && uc <= hi) {
+                                us = uc;
+                                vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * a.rho);
+                            } else {
+                                us = uc < lo ? lo : hi;
+                                vj = __fmaf_rd(m_, us, __fmul_rd(a.rho, __fmul_rd(us, us)));
+                                const float du = __fmul_ru(kTwoU, fabsf(uc));
+                                e = __fmaf_ru(__fmul_ru(a.rho, du), du, e);
+                            }
+                        } else {
+                            us = m_ >= 0.f ? lo : hi;
+                            vj = __fmul_rd(m_, us);
+                        }
+                        vsum = __fadd_rd(vsum, vj);
+                        if (a.ustar) a.ustar[(size_t)box * d + j] = us;
+                        if (a.lin_coef && a.lin_coef != a.mu) a.lin_coef[(size_t)box * d + j] = m_;
+                    }
+                    const float raw = __fadd_rd(c, vsum);
+                    const float marg = __fadd_ru(mg, e);
+                    const float lbv = __fsub_rd(raw, marg);
+                    a.lb[box] = lbv;
+                    if (a.margin) a.margin[box] = marg;
+                    if (a.lin_const) a.lin_const[box] = c;
+                    if (a.lb_best) a.lb_best[box] = fmaxf(a.lb_best[box], lbv);
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
+        const int sl = warp - mma_warp;
+        const int gi = blockIdx.x * NSLOT + sl;
+        const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
+        long long left = cnt * H * L;
+        int l = L;
+        uint32_t phA = 0, ncommit = 0;
+        const uint32_t dcol = tb + sl * slot_cols;
+        const uint32_t ah = dcol + Dc, al = ah + Ac;
+        while (left > 0 && !*abort) {
+            if (!tc::mbar_wait(&bar_a[sl], phA, abort, kWaitNs)) {
+                abort_all(a.status, abort);
+                break;
+            }
+            phA ^= 1;
+            tc::fence_after_sync();
+            const int Kl = N.tcb_K[l], Nl = N.tcb_N[l];
+            const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
+            const uint32_t bh = tc::smem_u32(wimg + N.tcb_hi[l]), blo = tc::smem_u32(wimg + N.tcb_lo[l]);
+            for (int ks = 0; ks < Kl / 16; ++ks) {
+                const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
+                const uint64_t dh = tc::desc_sw128(bh + boff);
+                tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
+                tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+            }
+            tc::mma_commit(&bar_d[sl]);
+            ++ncommit;
+            l = (l == 1) ? L : l - 1;
+            --left;
+        }
+        if (*abort && ncommit) {
+            volatile int never = 0;
+            tc::mbar_wait(&bar_d[sl], (ncommit - 1) & 1, &never, kWaitNs);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == mma_warp) {
+        __syncwarp();
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tb, a.tmem_cols);
+    }
+}
+
+static size_t crown_tc_smem(const NetDesc &N, int nslot)
+{
+    return (size_t)N.tcb_bytes + (size_t)N.tc_bias_floats * 4 + (size_t)nslot * 128 * 2 * 4 + 1024;
+}
+
+bool crown_tc_supported(const NetDesc &N, int max_smem)
+{
+    if (!N.tc_ok || N.L < 2 || N.s > 32 || pad16(N.s + N.k) > 48) return false;
+    return crown_tc_smem(N, 2) + 1024 <= (size_t)max_smem;
+}
+
+template <int NSLOT, int SP>
+static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_crown_tc<NSLOT, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_crown_tc<NSLOT, SP><<<grid, NSLOT * (kEpi + 1) * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crown_tc(BoundArgs a, int num_sms, cudaStream_t st)
+{
+    const NetDesc &N = a.net;
+    if (a.n <= 0) return cudaSuccess;
+    const int slot_cols = N.tcb_dcols + 2 * N.tcb_acols;
+    const int ntiles = (a.n + 127) / 128;
+    const int nslot = (ntiles > num_sms && 2 * slot_cols <= 512) ? 2 : 1;
+    int cols = 32;
+    while (cols < nslot * slot_cols) cols *= 2;
+    if (cols > 512) return cudaErrorInvalidConfiguration;
+    a.tmem_cols = (uint32_t)cols;
+    const size_t smem = crown_tc_smem(N, nslot);
+    int grid = (ntiles + nslot - 1) / nslot;
+    grid = grid < num_sms ? grid : num_sms;
+    const int SP = pad16(N.s);
+    if (SP != 16 && SP != 32) return cudaErrorInvalidConfiguration;
+    if (nslot == 2) return SP == 16 ? launch_variant<2, 16>(a, grid, smem, st) : launch_variant<2, 32>(a, grid, smem, st);
+    return SP == 16 ? launch_variant<1, 16>(a, grid, smem, st) : launch_variant<1, 32>(a, grid, smem, st);
+}
+
+}  // namespace bab

@@ -51,6 +51,11 @@ struct BoundArgs {
     // alpha
     float *grad_alpha;       // [n][H][sumh]
     int *status;
+    // tensor-core CROWN
+    const uint8_t *tcb_img;  // backward image (W_l^T, BF16 hi then lo)
+    const float *tc_bias;    // biases padded to multiples of 16 (offsets tc_boff)
+    float *mu;               // [n][d] coefficients of u (lin_coef or scratch)
+    uint32_t tmem_cols;
 };
 
 // out[r][c] = act(sum_k in[r][k] * B[k][c] + bias[c]) for r < R, c < Np, where
@@ -137,6 +142,8 @@ void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st);
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st);
 cudaError_t launch_ibp(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_crown_tc(BoundArgs a, int num_sms, cudaStream_t st);
+bool crown_tc_supported(const NetDesc &N, int max_smem);
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
 cudaError_t launch_adam(float *alpha, float *m, float *v, const float *grad, long long count, float lr, float bc1,

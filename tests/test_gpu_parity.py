@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 oracle, on the same seeded inputs.
 
-Tolerances: FP32 results must lie within 1e-5 relative of the oracle, relative to the scale of the quantity
-(the larger of |value| and the magnitude of the terms that make it up, and at least 1); every returned lower
-bound must not exceed the oracle's (the outward margin covers the FP32 rounding); integer, index and box
-outputs are bit-exact.
+Tolerances: FP32 results must lie within 1e-5 relative of the oracle; for bounds "relative" means relative to
+the oracle's sum of |every term added into the bound| (the magnitude FP32 rounding scales with, at least 1),
+for other values relative to the value.  Bounds from the 3-term BF16 split products on tensor cores have a
+stated band of 5e-5 of that scale.  Every returned lower bound must not exceed the oracle's (the outward
+margin covers the rounding); integer, index and box outputs are bit-exact.
 """
 import numpy as np
 import pytest
@@ -38,10 +39,10 @@ def gp():
         g.close()
 
 
-def bound_scale(lb_o, mu_o, lo, hi):
-    """|lb| and the magnitude of the concretized linear terms, per box."""
-    box = np.maximum(np.abs(lo), np.abs(hi)).astype(np.float64)
-    return np.maximum(np.maximum(np.abs(lb_o), np.sum(np.abs(mu_o) * box, axis=1)), 1.0)
+def bound_scale(o):
+    """Tolerance scale of a bound: the oracle's sum of |every term added into it| (at least 1), the magnitude
+    that FP32 rounding in any evaluation order scales with."""
+    return np.maximum(o["scale"], 1.0)
 
 
 def tiny():
@@ -136,7 +137,7 @@ def test_ibp_matches_oracle_and_contains_it(oracle, gp, name, n):
 # ----------------------------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name,n,maxw", [("tiny", 64, 2.0), ("tiny", 37, 0.3), ("pushing", 21, 0.2),
-                                         ("pushing", 5, 2.0)])
+                                         ("pushing", 5, 2.0), ("pushing", 200, 2.0)])
 def test_crown_matches_oracle(oracle, gp, name, n, maxw):
     p = W.config_problem(name, 3)
     d = p["k"] * p["H"]
@@ -148,7 +149,7 @@ def test_crown_matches_oracle(oracle, gp, name, n, maxw):
     g = gp(p)
     r = g.crown(lo, hi)
     o = oracle.crown(p, lo, hi)
-    scale = bound_scale(o["lb"], o["lin_coef"], lo, hi)
+    scale = bound_scale(o)
     raw = r["lb"].astype(np.float64) + r["margin"]
     assert np.all(r["margin"] >= 0)
     assert np.all(np.abs(raw - o["lb"]) <= REL * scale), np.max(np.abs(raw - o["lb"]) / scale)
@@ -187,7 +188,7 @@ def test_crown_given_alpha_matches_oracle(oracle, gp):
     g = gp(p)
     r = g.crown(lo, hi, alpha=alpha)
     o = oracle.crown(p, lo, hi, alpha=alpha.astype(np.float64))
-    scale = bound_scale(o["lb"], o["lin_coef"], lo, hi)
+    scale = bound_scale(o)
     assert np.all(np.abs(r["lb"] + r["margin"] - o["lb"]) <= REL * scale)
     assert np.all(r["lb"] <= o["lb"] + 1e-12 * np.abs(o["lb"]))
 
@@ -206,7 +207,7 @@ def test_alpha_gradient_and_step_match_oracle(oracle, gp):
     gs = np.maximum(np.abs(grad_o).max(axis=(1, 2), keepdims=True), 1e-30)
     assert np.all(np.abs(hist[0]["grad"] - grad_o) <= 1e-4 * gs)
     o = oracle.crown(p, lo, hi, a0)
-    scale = bound_scale(o["lb"], o["lin_coef"], lo, hi)
+    scale = bound_scale(o)
     assert np.all(np.abs(hist[0]["lb"] - lb_o) <= REL * scale)
     a = a0.copy()
     m, v = np.zeros_like(a), np.zeros_like(a)
@@ -277,7 +278,7 @@ def test_pushing_full_size_sampled(oracle, gp):
     ub_o, _, _ = oracle.rollout(p, lo[rows], hi[rows], ids[rows], 1024, 2024)
     np.testing.assert_allclose(r["ub"][rows], ub_o, rtol=REL)
     o = oracle.crown(p, lo[rows], hi[rows])
-    scale = bound_scale(o["lb"], o["lin_coef"], lo[rows], hi[rows])
+    scale = bound_scale(o)
     assert np.all(np.abs(c["lb"][rows] + c["margin"][rows] - o["lb"]) <= REL * scale)
     assert np.all(c["lb"][rows] <= o["lb"])
     # properties at every box: bounds below the sampled objective, finite margins
@@ -331,3 +332,54 @@ def test_tc_bf16_rollout_rescored(oracle, gp):
     np.testing.assert_allclose(r["ub"], f_best, rtol=REL)
     assert np.all(f_best >= ub_o * (1 - 1e-12))
     np.testing.assert_allclose(r["ub"], ub_o, rtol=1e-2)
+
+
+# ----------------------------------------------------------------------------------------------------------------
+# tensor-core CROWN (3-term BF16 split products, margin covers the split)
+# ----------------------------------------------------------------------------------------------------------------
+
+REL_TC = 5e-5      # band of the 3-term BF16 split products, relative to the bound's scale
+MARGIN_TC = 2e-4   # worst-case split margin: (3.1 * 2^-16 + gamma_K) per product term, relative to the bound's scale
+
+
+@pytest.mark.parametrize("name,n,maxw", [("tiny", 64, 2.0), ("tiny", 130, 0.3), ("pushing", 21, 0.2),
+                                         ("pushing", 200, 2.0)])
+def test_crown_tc_matches_oracle(oracle, gp, name, n, maxw):
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem(name, 3)
+    d = p["k"] * p["H"]
+    lo, hi, _ = W.random_boxes(d, n, seed=n, min_width=0.0, max_width=maxw)
+    g = gp(p)
+    r = g.crown(lo, hi, precision=B.PREC_BF16X3)
+    o = oracle.crown(p, lo, hi)
+    scale = bound_scale(o)
+    raw = r["lb"].astype(np.float64) + r["margin"]
+    assert np.all(r["margin"] >= 0)
+    assert np.all(np.abs(raw - o["lb"]) <= REL_TC * scale), np.max(np.abs(raw - o["lb"]) / scale)
+    assert np.all(r["lb"] <= o["lb"] + 1e-12 * np.abs(o["lb"])), "returned bound above the exact CROWN bound"
+    assert np.all(r["margin"] <= MARGIN_TC * scale)
+    # the coefficients of early steps pass through up to H*L chained split products and lose more relative
+    # accuracy than the bound (which is checked above): a sanity band of 1e-3 of the row's L1 norm
+    mu_scale = np.maximum(np.abs(o["lin_coef"]).sum(axis=1, keepdims=True), 1.0)
+    err = np.abs(r["lin_coef"] - o["lin_coef"]) / mu_scale
+    assert np.all(err <= 1e-3), err.max()
+
+
+def test_crown_tc_given_alpha_and_zero_width(oracle, gp):
+    from paper_2412_09584_gb300 import binding as B
+    p = W.make_problem(4, 2, [32, 32], 5, 0.01, seed=10, weight_scale=0.3)
+    lo, hi, _ = W.random_boxes(10, 40, seed=11, min_width=0.3, max_width=1.0)
+    alpha = np.random.default_rng(1).uniform(0, 1, size=(40, 5, 64)).astype(np.float32)
+    g = gp(p)
+    r = g.crown(lo, hi, alpha=alpha, precision=B.PREC_BF16X3)
+    o = oracle.crown(p, lo, hi, alpha=alpha.astype(np.float64))
+    scale = bound_scale(o)
+    assert np.all(np.abs(r["lb"] + r["margin"] - o["lb"]) <= REL_TC * scale)
+    assert np.all(r["lb"] <= o["lb"] + 1e-12 * np.abs(o["lb"]))
+    q = W.config_problem("pushing", 4)
+    z, _, _ = W.random_boxes(40, 6, seed=6, min_width=0.0, max_width=0.0)
+    g2 = gp(q)
+    rz = g2.crown(z, z, precision=B.PREC_BF16X3)
+    f = np.array([oracle.objective(q, z[i].astype(np.float64)) for i in range(6)])
+    assert np.all(rz["lb"] <= f)
+    np.testing.assert_allclose(rz["lb"] + rz["margin"], f, rtol=REL_TC)

@@ -293,6 +293,7 @@ def test_crown_sound_random_points_large_boxes(oracle):
     p = scaled_problem(8, 2, [64, 64, 64], 6, 0.01, seed=23, scale=2.0)
     lo, hi, _ = W.random_boxes(12, 4, seed=24, min_width=0.5, max_width=2.0)
     r = oracle.crown(p, lo, hi)
+    assert np.all(r["scale"] >= np.abs(r["lb"]) * (1 - 1e-12))  # the term scale dominates the bound
     lbi = oracle.ibp(p, lo, hi)[0]
     rng = np.random.default_rng(2)
     for i in range(4):
