@@ -6,12 +6,15 @@ bisect them (4096 children), search every child with 1024 uniform rollouts of
 H = 20 steps (upper bounds, FP64 re-score of the best plan), and bound every
 child from below (interval bounds + CROWN + concretization, outward margin).
 All of it runs in libbab's kernels through the C-ABI binding; the pool stays
-in device memory and the iteration chains its calls through device counts,
-with no host synchronisation.
+in device memory, the iteration chains its calls through device counts with
+no host synchronisation, and the timed steps replay the iteration as a CUDA
+graph.
 
 Metric: CROWN subdomain-bounds/s (children bounded per second, whole job);
-rollout-steps/s is reported beside it.  `--impl reference` times the FP64 CPU
-oracle on a bounded sample of the same workload instead.
+rollout-steps/s is reported beside it, and a time-to-gap comparison (alpha-CROWN
+with split precision vs plain FP32 CROWN+IBP BaB) on the 4096-box alpha
+workload.  `--impl reference` times the FP64 CPU oracle on a bounded sample of
+the same workload instead.
 
 Multi-GPU (torchrun): each rank runs an independent planning problem (seed +
 rank) on its own GPU; no data-path collective; value = all ranks' boxes / the
@@ -33,24 +36,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "pushing"
-N_PICK = 2048          # parents per iteration -> 4096 children bounded per iteration (--boxes changes it)
 SEED = 2024
 METRIC = "CROWN subdomain-bounds/s & rollout-steps/s at H=20"
-PRECISION = "bf16x3"   # rollout arithmetic (--precision)
-
-
-def workload_config():
-    from paper_2412_09584_gb300 import workloads as W
-    c = W.CONFIGS[WORKLOAD]
-    return {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
-                        "rho=0.01, 4096 children bounded per iteration (2048 picked, widest-dim bisection), "
-                        "1024 uniform rollouts per child",
-            "rollout_arithmetic": {"fp32": "FP32 CUDA cores", "bf16x3": "tcgen05, 3-term BF16 split, FP32 accumulate",
-                                   "bf16": "tcgen05, BF16 operands, FP32 accumulate, FP32 re-score"}[PRECISION],
-            "bound_arithmetic": "FP32 CUDA cores, outward-rounded intervals, margin-corrected CROWN",
-            "boxes_per_step": 2 * N_PICK, "samples_per_box": c["samples"], "H": c["H"],
-            "initial_pool": "4096-box grid over [-1,1]^40", "l2": "flushed between steps (256 MiB write)"}
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+ARITH = {"fp32": "FP32 CUDA cores", "bf16x3": "tcgen05, 3-term BF16 split, FP32 accumulate",
+         "bf16": "tcgen05, BF16 operands, FP32 accumulate, FP32 re-score of each box's pick"}
 
 
 def dist_env():
@@ -110,55 +100,66 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
-
-
 def fp32_alu_peak_tflops(sm_mhz):
     """Dense FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-class BabIteration:
-    """Device-resident BaB state and one iteration = prune/pick/split, rollouts, bounds."""
+class BabState:
+    """Device-resident BaB pool and one iteration: prune/pick/split, rollouts, bounds (plain or alpha-CROWN).
 
-    def __init__(self, seed, device):
+    Every call of an iteration reads its live counts from the device, so an iteration can be captured as a
+    CUDA graph; with `fixed_launch` the pool calls are sized for the largest pool so every replay launches
+    the same grids."""
+
+    def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
+                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
         self.torch, self.B = torch, B
         self.dev = device
-        c = W.CONFIGS[WORKLOAD]
-        self.p = W.config_problem(WORKLOAD, seed)
-        self.H, self.rho, self.M = c["H"], c["rho"], c["samples"]
+        c = W.CONFIGS[workload]
+        self.p = W.config_problem(workload, seed)
+        self.H, self.rho = c["H"], c["rho"]
+        self.M = samples or c["samples"]
         self.d = self.p["k"] * self.H
-        self.nb = 2 * N_PICK
+        self.sumh = sum(self.p["dims"][1:-1])
+        self.n_pick = n_pick
+        self.nb = 2 * n_pick
         self.seed = seed
+        self.rprec, self.bprec = PRECISIONS[rollout_prec], PRECISIONS[bound_prec]
+        self.alpha_steps, self.alpha_lr = alpha_steps, alpha_lr
         self.ctx = B.bab_load_dynamics(self.p["dims"], self.p["params"], self.p["s"], self.p["k"])
         f = dict(device=device, dtype=torch.float32)
         self.x0 = torch.as_tensor(self.p["x0"]).to(**f)
         self.goal = torch.as_tensor(self.p["goal"]).to(**f)
-        lo, hi, ids = W.grid_boxes(self.d, int(np.log2(self.nb)))  # 4096 boxes = the 12-level grid
-        self.cap = 4096 + 64 * N_PICK  # enough for 60+ iterations of pool growth
+        levels = min(int(np.log2(self.nb)), self.d)
+        lo, hi, ids = W.grid_boxes(self.d, levels)
+        n0 = lo.shape[0]
+        self.cap = n0 + pool_iters * n_pick
         self.pool = [self._alloc(), self._alloc()]
         self.cur = 0
         P = self.pool[0]
-        n0 = lo.shape[0]
         P["lo"][:n0] = torch.as_tensor(lo).to(**f)
         P["hi"][:n0] = torch.as_tensor(hi).to(**f)
         P["id"][:n0] = torch.as_tensor(ids.astype(np.int64)).to(device)
-        self.n_max = n0
-        self.best_u = torch.empty(max(self.nb, n0), self.d, **f)
+        self.fixed = fixed_launch
+        self.n_max = self.cap - n_pick if fixed_launch else n0
+        nbuf = max(self.nb, n0)
+        self.best_u = torch.empty(nbuf, self.d, **f)
+        self.margin = torch.empty(nbuf, **f)
         self.keep = torch.empty(self.cap, dtype=torch.uint8, device=device)
         self.counts = torch.zeros(3, dtype=torch.int32, device=device)
+        self.counts[2] = n0
         self.inc_val = torch.full((1,), float("inf"), dtype=torch.float64, device=device)
         self.inc_u = torch.zeros(self.d, **f)
-        self.margin = torch.empty(max(self.nb, n0), **f)
         self.n_live_dev = torch.tensor([n0], dtype=torch.int32, device=device)
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+        self.ev = []
         # initial search and bound of the starting pool (Algorithm 2, lines 2-3)
         self.search_and_bound(P, n0, None)
-        self.launches_per_step = 2 + 4 + 2  # prune/branch 2, rollout 4, interval bounds + CROWN 2
-        self.ev = []
+        self.launches_per_step = 2 + 4 + (2 if not alpha_steps else 3 + alpha_steps * 3)
 
     def _alloc(self):
         torch = self.torch
@@ -167,38 +168,68 @@ class BabIteration:
                 "lb": torch.empty(self.cap, **f), "ub": torch.empty(self.cap, **f),
                 "id": torch.empty(self.cap, dtype=torch.int64, device=self.dev)}
 
-    def search_and_bound(self, P, n, d_n, time_rollout=False):
+    def search_and_bound(self, P, n, d_n, events=False):
         B, torch = self.B, self.torch
-        if time_rollout:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
+        if events:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
         B.bab_rollout(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
-                      self.seed, PRECISIONS[PRECISION], P["ub"], self.best_u, self.inc_val, self.inc_u, d_n=d_n)
-        if time_rollout:
-            e1.record()
-            e2 = torch.cuda.Event(enable_timing=True)
-        B.bab_bound_crown(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n, P["lb"],
-                          margin=self.margin, d_n=d_n)
-        if time_rollout:
-            e2.record()
-            self.ev.append((e0, e1, e2))
+                      self.seed, self.rprec, P["ub"], self.best_u, self.inc_val, self.inc_u, d_n=d_n)
+        if events:
+            e[1].record()
+        if not self.alpha_steps:
+            B.bab_bound_crown(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n, P["lb"],
+                              precision=self.bprec, margin=self.margin, d_n=d_n)
+        else:
+            B.bab_alpha_optimize(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n,
+                                 self.alpha_steps, self.alpha_lr, P["lb"][:n], precision=self.bprec, d_n=d_n)
+        if events:
+            e[2].record()
+            self.ev.append(e)
 
-    def step(self, timed=False):
+    def step(self, events=False):
         B = self.B
         src, dst = self.pool[self.cur], self.pool[self.cur ^ 1]
         B.bab_prune_branch(self.ctx, self.d, src["lo"], src["hi"], src["lb"], src["ub"], src["id"], self.n_max,
-                           self.inc_val, N_PICK, 0.75, self.cap, dst["lo"], dst["hi"], dst["lb"], dst["ub"],
+                           self.inc_val, self.n_pick, 0.75, self.cap, dst["lo"], dst["hi"], dst["lb"], dst["ub"],
                            dst["id"], self.keep, self.counts, d_n=self.n_live_dev)
-        self.n_max = min(self.n_max + N_PICK, self.cap - N_PICK)
-        self.search_and_bound(dst, self.nb, self.counts[0:1], time_rollout=timed)
+        if not self.fixed:
+            self.n_max = min(self.n_max + self.n_pick, self.cap - self.n_pick)
+        self.search_and_bound(dst, self.nb, self.counts[0:1], events=events)
         self.n_live_dev.copy_(self.counts[2:3])
         self.cur ^= 1
+
+    def gap(self):
+        """Incumbent (FP64) minus the smallest lower bound of the live pool (synchronises)."""
+        n = int(self.counts[2].item())
+        P = self.pool[self.cur]
+        lbmin = float(P["lb"][:n].min().item()) if n > 0 else float("inf")
+        return float(self.inc_val.item()) - lbmin, n
 
     def flush_l2(self):
         self.flush.fill_(1.0)
 
     def close(self):
         self.B.bab_destroy(self.ctx)
+
+
+def capture_graphs(st):
+    """CUDA graphs of one iteration for each pool parity (the pool ping-pongs between two buffers)."""
+    torch = st.torch
+    graphs = []
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            st.step()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                st.step()
+            graphs.append(g)
+    torch.cuda.current_stream().wait_stream(s)
+    return graphs
 
 
 def run_ours(args):
@@ -211,10 +242,13 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    it = BabIteration(SEED + rank, dev)
+    n_pick = args.boxes // 2
+    st = BabState("pushing", SEED + rank, dev, n_pick, args.precision, args.bound_precision,
+                  fixed_launch=not args.no_graph)
     for _ in range(args.warmup):
-        it.step()
-        it.flush_l2()
+        st.step()
+        st.flush_l2()
+    graphs = None if args.no_graph else capture_graphs(st)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -222,61 +256,76 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         t0.record()
-        for _ in range(args.steps):
-            it.step(timed=True)
-            it.flush_l2()
+        for i in range(args.steps):
+            if graphs is not None:
+                graphs[st.cur].replay()
+                st.cur ^= 1
+            else:
+                st.step()
+            st.flush_l2()
         t1.record()
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     ms = t0.elapsed_time(t1)
-    roll_ms = [a.elapsed_time(b) for a, b, _ in it.ev]
-    crown_ms = [b.elapsed_time(c) for _, b, c in it.ev]
     if ws > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     clocks = clk.summary()
+    # per-kernel times on the launching stream (eager steps, same shapes)
+    for _ in range(3):
+        st.step(events=True)
+        st.flush_l2()
+    torch.cuda.synchronize()
+    roll_ms = [e[0].elapsed_time(e[1]) for e in st.ev]
+    bound_ms = [e[1].elapsed_time(e[2]) for e in st.ev]
+    # end to end through the C-ABI with host buffers
+    e2e = run_e2e(st, args.steps)
+    inc = float(st.inc_val.item())
+    st.close()
+    ttg = None if args.no_time_to_gap else time_to_gap(dev)
 
-    # end to end through the C-ABI: each step copies its batch of boxes in from pinned host memory and the
-    # next batch plus the bounds and incumbent back out
-    e2e = run_e2e(it, args.steps)
-    inc = float(it.inc_val.item())
-    it.close()
-
-    boxes = it.nb * args.steps * ws
+    boxes = st.nb * args.steps * ws
     value = boxes / (ms / 1e3)
-    rsteps = boxes * it.M * it.H / (ms / 1e3)
-    macs = sum(a * b for a, b in zip(it.p["dims"][1:], it.p["dims"][:-1]))
-    flops_roll = 2.0 * it.nb * it.M * it.H * macs
-    roll_avg = statistics.mean(roll_ms) / 1e3
-    achieved = flops_roll / roll_avg / 1e12
-    if PRECISION == "fp32":
+    rsteps = boxes * st.M * st.H / (ms / 1e3)
+    macs = sum(a * b for a, b in zip(st.p["dims"][1:], st.p["dims"][:-1]))
+    flops_roll = 2.0 * st.nb * st.M * st.H * macs
+    achieved = flops_roll / (statistics.mean(roll_ms) / 1e3) / 1e12
+    if args.precision == "fp32":
         roof = {"kernel": "k_rollout_fp32 (bab_rollout)", "bound": "alu", "peak": fp32_alu_peak_tflops(2070.0),
                 "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz max SM clock"}
     else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        pk = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"kernel": "k_rollout_tc (bab_rollout)", "bound": "tensor", "peak": pk,
+        path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peaks = json.load(open(path)) if os.path.exists(path) else {}
+        roof = {"kernel": "k_rollout_tc (bab_rollout)", "bound": "tensor",
+                "peak": peaks.get("bf16_tflops_sustained", 1700.0),
                 "peak_note": ("of measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "of fallback") +
-                             "; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe "
-                             "executes " + ("3x that (3-term BF16 split)" if PRECISION == "bf16x3" else
-                                            "the same (BF16 operands)") + " plus padding to multiples of 16"}
+                             "; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe executes "
+                             + ("3x that (3-term BF16 split)" if args.precision == "bf16x3" else "the same") +
+                             " plus padding to multiples of 16"}
     roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": None})
     if rank != 0:
         return
+    cfg = {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
+                       f"rho=0.01, {st.nb} children bounded per iteration ({n_pick} picked, widest-dim bisection), "
+                       f"{st.M} uniform rollouts per child",
+           "rollout_arithmetic": ARITH[args.precision],
+           "bound_arithmetic": "outward-rounded FP32 intervals; CROWN products " +
+                               ("on tcgen05, 3-term BF16 split" if args.bound_precision == "bf16x3"
+                                else "in FP32 on CUDA cores") + ", margin-corrected",
+           "boxes_per_step": st.nb, "samples_per_box": st.M, "H": st.H,
+           "initial_pool": f"{st.nb}-box grid over [-1,1]^{st.d}", "l2": "flushed between steps (256 MiB write)",
+           "timed_region": "CUDA-graph replays of the whole iteration" if graphs is not None else "eager launches",
+           "parallelism": f"independent problems x{ws}" if ws > 1 else "single GPU"}
     out = {"metric": METRIC, "value": value, "unit": "subdomain-bounds/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16"}[PRECISION],
-           "data": "synthetic (seeded random network, start and goal)",
-           "config": dict(workload_config(), parallelism=f"independent problems x{ws}" if ws > 1 else "single GPU"),
-           "rollout_steps_per_s": rsteps,
-           "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound_crown": statistics.mean(crown_ms)},
-           "crown_subdomain_bounds_per_s_kernel_only": it.nb / (statistics.mean(crown_ms) / 1e3),
-           "incumbent_fp64": inc,
-           "roofline": roof,
-           "clocks": clocks, "e2e": e2e, "gpu_launches": it.launches_per_step * args.steps}
+           "vs_baseline": None, "dtype": args.precision, "data": "synthetic (seeded random network, start and goal)",
+           "config": cfg, "rollout_steps_per_s": rsteps,
+           "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound": statistics.mean(bound_ms)},
+           "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
+           "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -284,17 +333,19 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(it, steps):
-    """Same iteration with the batch of boxes crossing the host boundary every step."""
-    torch, B = it.torch, it.B
-    nb, d = it.nb, it.d
+def run_e2e(st, steps):
+    """Same iteration with the batch of boxes crossing the host boundary every step: the batch is copied in
+    from pinned host memory, searched and bounded, pruned and branched, and the next batch plus the bounds and
+    the incumbent are copied back out."""
+    torch, B = st.torch, st.B
+    nb, d = st.nb, st.d
     h_lo = torch.empty(nb, d, dtype=torch.float32, pin_memory=True)
     h_hi = torch.empty_like(h_lo, pin_memory=True)
     h_id = torch.empty(nb, dtype=torch.int64, pin_memory=True)
     h_lb = torch.empty(nb, dtype=torch.float32, pin_memory=True)
     h_ub = torch.empty_like(h_lb, pin_memory=True)
     h_inc = torch.empty(1, dtype=torch.float64, pin_memory=True)
-    src = it.pool[it.cur]
+    src = st.pool[st.cur]
     h_lo.copy_(src["lo"][:nb])
     h_hi.copy_(src["hi"][:nb])
     h_id.copy_(src["id"][:nb])
@@ -302,25 +353,24 @@ def run_e2e(it, steps):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(steps):
-        P = it.pool[it.cur]
+        P = st.pool[st.cur]
         P["lo"][:nb].copy_(h_lo, non_blocking=True)
         P["hi"][:nb].copy_(h_hi, non_blocking=True)
         P["id"][:nb].copy_(h_id, non_blocking=True)
-        it.search_and_bound(P, nb, None)
+        st.search_and_bound(P, nb, None)
         h_lb.copy_(P["lb"][:nb], non_blocking=True)
         h_ub.copy_(P["ub"][:nb], non_blocking=True)
-        dst = it.pool[it.cur ^ 1]
-        B.bab_prune_branch(it.ctx, d, P["lo"], P["hi"], P["lb"], P["ub"], P["id"], it.n_max, it.inc_val, N_PICK,
-                           0.75, it.cap, dst["lo"], dst["hi"], dst["lb"], dst["ub"], dst["id"], it.keep, it.counts,
-                           d_n=it.n_live_dev)
-        it.n_max = min(it.n_max + N_PICK, it.cap - N_PICK)
-        it.n_live_dev.copy_(it.counts[2:3])
+        dst = st.pool[st.cur ^ 1]
+        B.bab_prune_branch(st.ctx, d, P["lo"], P["hi"], P["lb"], P["ub"], P["id"], st.n_max, st.inc_val,
+                           st.n_pick, 0.75, st.cap, dst["lo"], dst["hi"], dst["lb"], dst["ub"], dst["id"], st.keep,
+                           st.counts, d_n=st.n_live_dev)
+        st.n_live_dev.copy_(st.counts[2:3])
         h_lo.copy_(dst["lo"][:nb], non_blocking=True)
         h_hi.copy_(dst["hi"][:nb], non_blocking=True)
         h_id.copy_(dst["id"][:nb], non_blocking=True)
-        h_inc.copy_(it.inc_val, non_blocking=True)
-        it.cur ^= 1
-        it.flush_l2()
+        h_inc.copy_(st.inc_val, non_blocking=True)
+        st.cur ^= 1
+        st.flush_l2()
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
@@ -330,7 +380,46 @@ def run_e2e(it, steps):
             "d2h_bytes_per_step": d2h}
 
 
-def oracle_sample_step(problem, lo, hi, ids, M, n_roll, n_bound, pool_n):
+def time_to_gap(dev, iters=20, max_iters=60):
+    """Wall time for alpha-optimised, split-precision BaB to reach the optimality gap that plain FP32
+    CROWN+IBP BaB reaches after `iters` iterations, on the 4096-box alpha workload (tiny network, H=5,
+    20 Adam steps of lr 0.1 per iteration).  Gap = FP64 incumbent - smallest lower bound of the live pool."""
+    import torch
+
+    def run(rprec, bprec, alpha_steps, n_iter, target=None):
+        st = BabState("alpha", SEED, dev, 2048, rprec, bprec, alpha_steps=alpha_steps, pool_iters=max_iters + 2)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        hist = []
+        for it in range(n_iter):
+            st.step()
+            g, n = st.gap()
+            hist.append((time.perf_counter() - t, g, n))
+            if target is not None and g <= target:
+                break
+        st.close()
+        return hist
+
+    variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
+                "alpha_split": ("bf16x3", "bf16x3", 20)}
+    for v in variants.values():  # load every kernel and size every scratch buffer before timing
+        run(*v, n_iter=2)
+    plain = run(*variants["plain_fp32"], n_iter=iters)
+    target = plain[-1][1]
+    out = {"workload": "alpha: MLP 6-32-32-4, H=5, 4096 children per iteration, 256 rollouts each; gap = FP64 "
+                       "incumbent - min lower bound of the live pool; target = plain FP32 BaB's gap after "
+                       f"{iters} iterations", "target_gap": target}
+    for name, v in variants.items():
+        h = plain if name == "plain_fp32" else run(*v, n_iter=max_iters, target=target)
+        reached = h[-1][1] <= target
+        out[name] = {"seconds": h[-1][0], "iterations": len(h), "reached": reached,
+                     "ms_per_iteration": 1e3 * h[-1][0] / len(h), "gap_curve": [round(x[1], 6) for x in h]}
+        if name != "plain_fp32":
+            out[name]["speedup_vs_plain"] = plain[-1][0] / h[-1][0] if reached else None
+    return out
+
+
+def oracle_sample_step(problem, lo, hi, ids, M, n_roll, n_bound, pool_n, n_pick):
     """The oracle on a bounded sample of one iteration: rollouts of n_roll boxes, bounds of n_bound boxes and
     prune/branch of a pool of pool_n boxes. Returns seconds per box for search and bound, and prune seconds."""
     from oracle import oracle as O
@@ -348,26 +437,27 @@ def oracle_sample_step(problem, lo, hi, ids, M, n_roll, n_bound, pool_n):
     phi = np.tile(hi, (reps, 1))[:pool_n]
     pid = np.arange(1, pool_n + 1, dtype=np.uint64)
     t = time.perf_counter()
-    O.prune_branch(plo, phi, lb, ub, pid, 11.0, N_PICK)
+    O.prune_branch(plo, phi, lb, ub, pid, 11.0, n_pick)
     t_prune = time.perf_counter() - t
     return t_roll, t_bound, t_prune
 
 
-def cpu_baseline(budget_s=20.0):
+def cpu_baseline(budget_s=20.0, n_pick=2048):
     from paper_2412_09584_gb300 import workloads as W
-    c = W.CONFIGS[WORKLOAD]
-    p = W.config_problem(WORKLOAD, SEED)
+    c = W.CONFIGS["pushing"]
+    p = W.config_problem("pushing", SEED)
     lo, hi, ids = W.grid_boxes(c["H"] * p["k"], c["grid_dims"])
     # calibrate on one box, then size the sample to the budget
-    t_roll, t_bound, t_prune = oracle_sample_step(p, lo, hi, ids, c["samples"], 1, 4, 4096)
+    t_roll, t_bound, t_prune = oracle_sample_step(p, lo, hi, ids, c["samples"], 1, 4, 4096, n_pick)
     n_roll = max(1, min(64, int(0.7 * budget_s / max(t_roll, 1e-6))))
     n_bound = max(4, min(4096, int(0.2 * budget_s / max(t_bound, 1e-6))))
-    t_roll, t_bound, t_prune = oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 4096 + N_PICK)
-    step_s = 2 * N_PICK * (t_roll + t_bound) + t_prune
-    return {"value": 2 * N_PICK / step_s, "unit": "subdomain-bounds/s", "cores": 1, "kind": "oracle",
+    t_roll, t_bound, t_prune = oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 4096 + n_pick,
+                                                  n_pick)
+    step_s = 2 * n_pick * (t_roll + t_bound) + t_prune
+    return {"value": 2 * n_pick / step_s, "unit": "subdomain-bounds/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 C oracle, single thread: rollouts of {n_roll} boxes x {c['samples']} samples x H={c['H']}, "
-                      f"CROWN of {n_bound} boxes, prune/branch of a {4096 + N_PICK}-box pool; per-box times scaled to "
-                      f"one {2 * N_PICK}-box iteration ({step_s:.1f} s)"}
+                      f"CROWN of {n_bound} boxes, prune/branch of a {4096 + n_pick}-box pool; per-box times scaled to "
+                      f"one {2 * n_pick}-box iteration ({step_s:.1f} s)"}
 
 
 def run_reference(args):
@@ -377,23 +467,25 @@ def run_reference(args):
     from oracle import oracle as O
     from paper_2412_09584_gb300 import workloads as W
     O.build()
-    c = W.CONFIGS[WORKLOAD]
-    p = W.config_problem(WORKLOAD, SEED)
+    c = W.CONFIGS["pushing"]
+    p = W.config_problem("pushing", SEED)
     lo, hi, ids = W.grid_boxes(c["H"] * p["k"], c["grid_dims"])
     n_roll, n_bound = 2, 2
     for _ in range(args.warmup):
-        oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 1024)
+        oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 1024, args.boxes // 2)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 1024)
+        oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 1024, args.boxes // 2)
     sec = (time.perf_counter() - t) / args.steps
     value = n_bound / sec
     sample = (f"per step: FP64 C oracle on {n_roll} boxes (1024 rollouts of H=20 each, then CROWN) and prune/branch "
               f"of a 1024-box pool, single thread")
+    cfg = {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
+                       "rho=0.01, 1024 uniform rollouts per child (bounded sample per step)",
+           "boxes_per_step": n_bound, "samples_per_box": c["samples"], "H": c["H"]}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "subdomain-bounds/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(),
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
            "cpu_baseline": {"value": value, "unit": "subdomain-bounds/s", "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "subdomain-bounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -401,21 +493,22 @@ def run_reference(args):
 
 
 def main():
-    global N_PICK, PRECISION
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-gap", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of CUDA-graph replays")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default=PRECISION,
+    ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="fp32",
+                    help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16x3",
                     help="rollout arithmetic: fp32 (CUDA cores), bf16x3 (tcgen05, 3-term split), bf16 (tcgen05)")
-    ap.add_argument("--boxes", type=int, default=2 * N_PICK,
+    ap.add_argument("--boxes", type=int, default=4096,
                     help="children bounded per iteration; smaller values make small cases for profiler captures")
     args = ap.parse_args()
-    N_PICK = args.boxes // 2
-    PRECISION = args.precision
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -177,6 +177,7 @@ int bab_bound_crown(bab_ctx *ctx, const float *x0, const float *goal, int horizo
  *      alpha to [0, 1].
  *   alpha, adam_m, adam_v  device float[n][H][sumh], updated in place
  *              (m, v start at 0; alpha typically at the adaptive slopes).
+ *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3 (the CROWN products, as bab_bound_crown).
  *   lb         device float[n] (nullable): bound at the incoming alpha.
  *   lb_best    device float[n] (nullable): running maximum, updated.
  *   grad_alpha device float[n][H][sumh] (nullable): the gradient.
@@ -184,7 +185,37 @@ int bab_bound_crown(bab_ctx *ctx, const float *x0, const float *goal, int horizo
  */
 int bab_alpha_step(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
                    const float *hi, int n, const int *d_n, float *alpha, float *adam_m, float *adam_v, int step,
-                   float lr, float *lb, float *lb_best, float *grad_alpha, void *stream);
+                   float lr, int precision, float *lb, float *lb_best, float *grad_alpha, void *stream);
+
+/*
+ * The bound at alpha and its gradient with respect to alpha, without an
+ * optimiser step: step 1 of bab_alpha_step alone (Lemma 1's free lower slope;
+ * dLB/dalpha_j = A_j z~_j(u*) for unstable neurons with the lower bound
+ * selected, 0 elsewhere).  For use under an autodiff framework.
+ *   alpha      device float[n][H][sumh] (read only).
+ *   lb         device float[n]: the bound at alpha (margin subtracted).
+ *   grad_alpha device float[n][H][sumh]: d lb[i] / d alpha[i].
+ * Errors: as bab_bound_crown.
+ */
+int bab_alpha_grad(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                   const float *hi, int n, const int *d_n, const float *alpha, int precision, float *lb,
+                   float *grad_alpha, void *stream);
+
+/*
+ * alpha-CROWN in one call: `steps` rounds of bab_alpha_step from the adaptive
+ * slopes, with the interval bounds (which do not depend on alpha) computed
+ * once, and the Adam moments in context scratch.  lb_best[i] receives the
+ * best bound of box i over all steps (each a valid bound, margin subtracted).
+ *   steps      number of Adam steps (>= 1); lr their learning rate.
+ *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3.
+ *   alpha      device float[n][H][sumh] (nullable): receives the final slopes.
+ *   lb_best    device float[n].
+ * All work is queued on `stream` without host synchronisation.
+ * Errors: as bab_bound_crown.
+ */
+int bab_alpha_optimize(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                       const float *hi, int n, const int *d_n, int steps, float lr, int precision, float *alpha,
+                       float *lb_best, void *stream);
 
 /*
  * The adaptive lower slopes of every hidden neuron (1 where u >= -l, else 0,

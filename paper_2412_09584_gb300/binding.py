@@ -63,7 +63,9 @@ def load(path: str = LIB_PATH):
     L.bab_bound_ibp.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P]
     L.bab_bound_crown.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P]
     L.bab_alpha_init.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
-    L.bab_alpha_step.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _I, _F, _P, _P, _P, _P]
+    L.bab_alpha_step.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _I, _F, _I, _P, _P, _P, _P]
+    L.bab_alpha_grad.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _I, _P, _P, _P]
+    L.bab_alpha_optimize.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _I, _F, _I, _P, _P, _P]
     L.bab_prune_branch.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _I, _P, _P, _P, _P, _P, _P, _P,
                                    _P]
     L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
@@ -161,12 +163,21 @@ def bab_alpha_init(ctx, x0, goal, horizon, rho, lo, hi, n, alpha, d_n=None, stre
 
 
 def bab_alpha_step(ctx, x0, goal, horizon, rho, lo, hi, n, alpha, adam_m, adam_v, step, lr, lb=None, lb_best=None,
-                   grad_alpha=None, d_n=None, stream=None):
+                   grad_alpha=None, precision=PREC_FP32, d_n=None, stream=None):
     f32 = torch.float32
     rc = load().bab_alpha_step(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
                                _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), _ptr(alpha, f32), _ptr(adam_m, f32),
-                               _ptr(adam_v, f32), int(step), float(lr), _ptr(lb, f32), _ptr(lb_best, f32),
-                               _ptr(grad_alpha, f32), _stream(stream))
+                               _ptr(adam_v, f32), int(step), float(lr), int(precision), _ptr(lb, f32),
+                               _ptr(lb_best, f32), _ptr(grad_alpha, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_alpha_grad(ctx, x0, goal, horizon, rho, lo, hi, n, alpha, lb, grad_alpha, precision=PREC_FP32, d_n=None,
+                   stream=None):
+    f32 = torch.float32
+    rc = load().bab_alpha_grad(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
+                               _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), _ptr(alpha, f32), int(precision),
+                               _ptr(lb, f32), _ptr(grad_alpha, f32), _stream(stream))
     _check(ctx, rc)
 
 
@@ -192,3 +203,12 @@ def bab_bound_crown_static(dims, params, state_dim, action_dim, x0, goal, horizo
                                          int(action_dim), _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho),
                                          _ptr(lo, f32), _ptr(hi, f32), int(n), _ptr(lb, f32), _ptr(margin, f32),
                                          _stream(stream))
+
+
+def bab_alpha_optimize(ctx, x0, goal, horizon, rho, lo, hi, n, steps, lr, lb_best, alpha=None, precision=PREC_FP32,
+                       d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_alpha_optimize(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
+                                   _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), int(steps), float(lr),
+                                   int(precision), _ptr(alpha, f32), _ptr(lb_best, f32), _stream(stream))
+    _check(ctx, rc)

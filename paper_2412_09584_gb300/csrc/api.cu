@@ -482,23 +482,17 @@ int bab_alpha_init(bab_ctx *c, const float *x0, const float *goal, int H, float 
     return BAB_OK;
 }
 
-int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
-                   int n, const int *d_n, float *alpha, float *adam_m, float *adam_v, int step, float lr, float *lb,
-                   float *lb_best, float *grad_alpha, void *stream)
+}  // extern "C"
+
+namespace {
+
+// Bound at alpha and its gradient (interval bounds, CROWN storing the pre-relaxation coefficients and the
+// concretizing point, forward pass of the relaxed network).  `a` keeps the scratch pointers for the caller.
+int alpha_grad_core(bab_ctx *c, BoundArgs &a, Carver &cv, int precision, const float *alpha, float *lb,
+                    float *lb_best, float *grad_alpha, cudaStream_t st)
 {
-    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
-    if (rc) return rc;
-    if (n > 0 && (!alpha || !adam_m || !adam_v)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, m and v are required");
-    if (step < 1) return fail(c, BAB_ERR_INVALID_ARG, "step counts from 1");
-    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
-    if (n == 0) return BAB_OK;
-    const int d = c->net.k * H;
-    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, d, true));
-    if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
-    Carver cv{reinterpret_cast<char *>(c->scratch)};
-    rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    const int n = a.n, H = a.H, d = a.d;
+    int rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
     if (rc) return rc;
     const size_t nh = (size_t)n * H * c->net.sumh;
     a.alpha = alpha;
@@ -507,13 +501,124 @@ int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float 
     a.grad_alpha = grad_alpha ? grad_alpha : cv.take<float>(nh);
     a.lb = lb ? lb : cv.take<float>(n);
     a.lb_best = lb_best;
-    cudaError_t e = launch_crown(a, c->num_sms, st);
+    cudaError_t e;
+    if (precision == BAB_PREC_BF16X3) {
+        a.tcb_img = c->d_tcb;
+        a.tc_bias = c->d_tc_bias;
+        a.mu = cv.take<float>((size_t)n * d);
+        e = launch_crown_tc(a, c->num_sms, st);
+    } else {
+        e = launch_crown(a, c->num_sms, st);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
     e = launch_alpha_fwd(a, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha adjoint kernel");
+    return BAB_OK;
+}
+
+int check_bound_precision(bab_ctx *c, int precision)
+{
+    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
+        return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
+    if (precision == BAB_PREC_BF16X3 && !crown_tc_supported(c->net, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN is not available for this network");
+    return BAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bab_alpha_grad(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                   int n, const int *d_n, const float *alpha, int precision, float *lb, float *grad_alpha, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && (!alpha || !lb || !grad_alpha)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, lb and grad are required");
+    rc = check_bound_precision(c, precision);
+    if (rc) return rc;
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, true) +
+                               (size_t)n * c->net.k * H * sizeof(float) + 256);
+    if (rc) return rc;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    return alpha_grad_core(c, a, cv, precision, alpha, lb, nullptr, grad_alpha, (cudaStream_t)stream);
+}
+
+int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                   int n, const int *d_n, float *alpha, float *adam_m, float *adam_v, int step, float lr,
+                   int precision, float *lb, float *lb_best, float *grad_alpha, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && (!alpha || !adam_m || !adam_v)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, m and v are required");
+    if (step < 1) return fail(c, BAB_ERR_INVALID_ARG, "step counts from 1");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
+    rc = check_bound_precision(c, precision);
+    if (rc) return rc;
+    if (n == 0) return BAB_OK;
+    const int d = c->net.k * H;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, d, true) + (size_t)n * d * sizeof(float) + 256);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    rc = alpha_grad_core(c, a, cv, precision, alpha, lb, lb_best, grad_alpha, st);
+    if (rc) return rc;
+    const size_t nh = (size_t)n * H * c->net.sumh;
     const double bc1 = 1.0 - std::pow(0.9, step), bc2 = 1.0 - std::pow(0.999, step);
-    e = launch_adam(alpha, adam_m, adam_v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);
+    cudaError_t e = launch_adam(alpha, adam_m, adam_v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "Adam kernel");
+    return BAB_OK;
+}
+
+int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                       const float *hi, int n, const int *d_n, int steps, float lr, int precision, float *alpha,
+                       float *lb_best, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && !lb_best) return fail(c, BAB_ERR_INVALID_ARG, "lb_best is required");
+    if (steps < 1 || steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "steps must be in [1, 100000]");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
+    rc = check_bound_precision(c, precision);
+    if (rc) return rc;
+    if (n == 0) return BAB_OK;
+    const int d = c->net.k * H;
+    const size_t nh = (size_t)n * H * c->net.sumh;
+    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, d, true) + (3 * nh + (size_t)n * d) * sizeof(float) +
+                               4 * 256);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    // interval bounds do not depend on alpha: once for all steps
+    rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    float *al = alpha ? alpha : cv.take<float>(nh);
+    float *m = cv.take<float>(nh), *v = cv.take<float>(nh);
+    a.A_pre = cv.take<float>(nh);
+    a.ustar = cv.take<float>((size_t)n * d);
+    a.grad_alpha = cv.take<float>(nh);
+    a.lb = cv.take<float>(n);
+    a.mu = cv.take<float>((size_t)n * d);
+    a.tcb_img = c->d_tcb;
+    a.tc_bias = c->d_tc_bias;
+    a.alpha = al;
+    cudaError_t e = launch_alpha_init(a, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, nh * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, nh * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_fill(lb_best, n, -INFINITY, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "alpha set-up");
+    a.lb_best = lb_best;
+    for (int step = 1; step <= steps; ++step) {
+        e = precision == BAB_PREC_BF16X3 ? launch_crown_tc(a, c->num_sms, st) : launch_crown(a, c->num_sms, st);
+        if (e == cudaSuccess) e = launch_alpha_fwd(a, c->num_sms, st);
+        const double bc1 = 1.0 - std::pow(0.9, step), bc2 = 1.0 - std::pow(0.999, step);
+        if (e == cudaSuccess) e = launch_adam(al, m, v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "alpha step");
+    }
     return BAB_OK;
 }
 

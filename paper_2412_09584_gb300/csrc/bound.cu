@@ -563,6 +563,18 @@ cudaError_t launch_alpha_fwd(const BoundArgs &a, int, cudaStream_t st)
     return launch_rows_kernel(k_alpha_fwd<true>, k_alpha_fwd<false>, (size_t)N.img_floats * 4, rest, a.n, a, st);
 }
 
+__global__ void k_fill_f32(float *p, int n, float v)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+cudaError_t launch_fill(float *p, int n, float v, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_fill_f32<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return cudaSuccess;

@@ -146,6 +146,7 @@ cudaError_t launch_crown_tc(BoundArgs a, int num_sms, cudaStream_t st);
 bool crown_tc_supported(const NetDesc &N, int max_smem);
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
+cudaError_t launch_fill(float *p, int n, float v, cudaStream_t st);
 cudaError_t launch_adam(float *alpha, float *m, float *v, const float *grad, long long count, float lr, float bc1,
                         float bc2, cudaStream_t st);
 

@@ -77,7 +77,7 @@ class GpuProblem:
         B.bab_alpha_init(self.ctx, self.x0, self.goal, self.H, self.rho, T(lo), T(hi), n, alpha)
         return alpha
 
-    def alpha_steps(self, lo, hi, steps, lr, alpha=None):
+    def alpha_steps(self, lo, hi, steps, lr, alpha=None, precision=B.PREC_FP32):
         n = lo.shape[0]
         tlo, thi = T(lo), T(hi)
         alpha = self.alpha_init(lo, hi) if alpha is None else T(alpha)
@@ -89,7 +89,7 @@ class GpuProblem:
         hist = []
         for step in range(1, steps + 1):
             B.bab_alpha_step(self.ctx, self.x0, self.goal, self.H, self.rho, tlo, thi, n, alpha, m, v, step, lr,
-                             lb=lb, lb_best=lb_best, grad_alpha=g)
+                             lb=lb, lb_best=lb_best, grad_alpha=g, precision=precision)
             hist.append({"lb": lb.cpu().numpy(), "grad": g.cpu().numpy(), "alpha": alpha.cpu().numpy()})
         torch.cuda.synchronize()
         return lb_best.cpu().numpy(), alpha.cpu().numpy(), hist
