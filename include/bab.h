@@ -229,7 +229,8 @@ int bab_alpha_init(bab_ctx *ctx, const float *x0, const float *goal, int horizon
  * Prune, pick out and split one pool of n boxes (Algorithm 2: Pruner, then
  * batch_pick_out and batch_split of Section 3.1).
  *   1. Prune: box i is dropped iff (double)lb[i] > *inc_val (strict; a NaN
- *      bound is kept).  keep[i] = 1 if kept.
+ *      bound is kept and latches BAB_ERR_NUMERIC in the device status read by
+ *      bab_status, without stopping the call).  keep[i] = 1 if kept.
  *   2. Pick out up to n_pick survivors: all of them if there are at most
  *      n_pick; otherwise the ceil(eta * n_pick) smallest by (ub, id), then the
  *      rest of the quota by smallest (lb, id) among the others.

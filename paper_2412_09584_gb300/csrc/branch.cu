@@ -119,10 +119,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
     const double inc = *a.inc_val;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // prune (strict, in FP64; a NaN bound is kept)
+    // prune (strict, in FP64; a NaN bound is kept and latched as BAB_ERR_NUMERIC)
     int cnt = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint8_t k = !((double)a.lb[i] > inc);
+        const float lbi = a.lb[i];
+        if (lbi != lbi) set_status(a.status, BAB_ERR_NUMERIC);
+        const uint8_t k = !((double)lbi > inc);
         a.keep[i] = k;
         cnt += k;
     }

@@ -242,13 +242,17 @@ def test_alpha_optimisation_twenty_steps(oracle, gp):
                                                     (1000, 200, 9.5, 0.3, 0.02), (5000, 1024, 13.0, 0.05, 0.0),
                                                     (77, 0, 10.0, 0.0, 0.0), (64, 32, -1e9, 0.0, 0.0)])
 def test_prune_branch_bit_exact(oracle, gp, n, n_pick, inc, ties, nans):
+    from paper_2412_09584_gb300 import binding as B
     p, _, _, _ = tiny()
     g = gp(p)
     d = 10
     lo, hi, ids = W.dyadic_boxes(d, n, seed=n + n_pick, max_depth=5)
     lb, ub = W.pool_values(n, seed=n, nan_frac=nans, tie_frac=ties)
+    B.bab_status(g.ctx)  # clear
     r = g.prune_branch(lo, hi, lb, ub, ids, inc, n_pick)
     o = oracle.prune_branch(lo, hi, lb, ub, ids, inc, n_pick)
+    # a NaN bound is kept and reported through the device status, without failing the call
+    assert B.bab_status(g.ctx) == (-6 if np.isnan(lb).any() else 0)
     assert np.array_equal(r["keep"], o["keep"])
     assert (r["n_children"], r["n_rest"]) == (o["n_children"], o["n_rest"])
     for key in ("lo", "hi", "lb", "ub"):
