@@ -113,7 +113,7 @@ class BabState:
     the same grids."""
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
-                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64):
+                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -157,9 +157,18 @@ class BabState:
         self.n_live_dev = torch.tensor([n0], dtype=torch.int32, device=device)
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
         self.ev = []
+        self.variants = None
+        if autotune:
+            # tile shapes timed on the starting pool (outside any timed region)
+            B.bab_autotune(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n0, self.M,
+                           alpha_steps=alpha_steps)
+            names = {"rollout_fp32": B.KERNEL_ROLLOUT_FP32, "alpha_fused": B.KERNEL_ALPHA_FUSED,
+                     "rollout_tc_tiles_per_cta": B.KERNEL_ROLLOUT_TC, "crown_tc_tiles_per_cta": B.KERNEL_CROWN_TC}
+            self.variants = {k: B.bab_get_variant(self.ctx, v) for k, v in names.items()}
         # initial search and bound of the starting pool (Algorithm 2, lines 2-3)
         self.search_and_bound(P, n0, None)
-        self.launches_per_step = 2 + 4 + (2 if not alpha_steps else 3 + alpha_steps * 3)
+        fused = alpha_steps and self.bprec == B.PREC_FP32 and (self.variants or {}).get("alpha_fused", -1) != -2
+        self.launches_per_step = 2 + 4 + (2 if not alpha_steps else (2 if fused else 3 + alpha_steps * 3))
 
     def _alloc(self):
         torch = self.torch
@@ -244,7 +253,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     n_pick = args.boxes // 2
     st = BabState("pushing", SEED + rank, dev, n_pick, args.precision, args.bound_precision,
-                  fixed_launch=not args.no_graph)
+                  fixed_launch=not args.no_graph, autotune=not args.no_autotune)
     for _ in range(args.warmup):
         st.step()
         st.flush_l2()
@@ -317,6 +326,7 @@ def run_ours(args):
            "boxes_per_step": st.nb, "samples_per_box": st.M, "H": st.H,
            "initial_pool": f"{st.nb}-box grid over [-1,1]^{st.d}", "l2": "flushed between steps (256 MiB write)",
            "timed_region": "CUDA-graph replays of the whole iteration" if graphs is not None else "eager launches",
+           "launch_variants": st.variants or "built-in heuristic",
            "parallelism": f"independent problems x{ws}" if ws > 1 else "single GPU"}
     out = {"metric": METRIC, "value": value, "unit": "subdomain-bounds/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -387,7 +397,8 @@ def time_to_gap(dev, iters=20, max_iters=60):
     import torch
 
     def run(rprec, bprec, alpha_steps, n_iter, target=None):
-        st = BabState("alpha", SEED, dev, 2048, rprec, bprec, alpha_steps=alpha_steps, pool_iters=max_iters + 2)
+        st = BabState("alpha", SEED, dev, 2048, rprec, bprec, alpha_steps=alpha_steps, pool_iters=max_iters + 2,
+                      autotune=True)
         torch.cuda.synchronize()
         t = time.perf_counter()
         hist = []
@@ -398,10 +409,14 @@ def time_to_gap(dev, iters=20, max_iters=60):
             if target is not None and g <= target:
                 break
         st.close()
+        run.variants = st.variants
         return hist
 
+    # plain: FP32 rollouts and FP32 CROWN; split: 3-term BF16 tensor-core rollouts and CROWN; alpha_split: split
+    # plus 20 Adam steps per iteration, each a tensor-core CROWN + adjoint + Adam launch; alpha_fused: 3-term BF16
+    # rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration
     variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
-                "alpha_split": ("bf16x3", "bf16x3", 20)}
+                "alpha_split": ("bf16x3", "bf16x3", 20), "alpha_fused": ("bf16x3", "fp32", 20)}
     for v in variants.values():  # load every kernel and size every scratch buffer before timing
         run(*v, n_iter=2)
     plain = run(*variants["plain_fp32"], n_iter=iters)
@@ -409,11 +424,14 @@ def time_to_gap(dev, iters=20, max_iters=60):
     out = {"workload": "alpha: MLP 6-32-32-4, H=5, 4096 children per iteration, 256 rollouts each; gap = FP64 "
                        "incumbent - min lower bound of the live pool; target = plain FP32 BaB's gap after "
                        f"{iters} iterations", "target_gap": target}
+    plain_variants = run.variants
     for name, v in variants.items():
         h = plain if name == "plain_fp32" else run(*v, n_iter=max_iters, target=target)
         reached = h[-1][1] <= target
         out[name] = {"seconds": h[-1][0], "iterations": len(h), "reached": reached,
-                     "ms_per_iteration": 1e3 * h[-1][0] / len(h), "gap_curve": [round(x[1], 6) for x in h]}
+                     "ms_per_iteration": 1e3 * h[-1][0] / len(h), "gap_curve": [round(x[1], 6) for x in h],
+                     "rollout": v[0], "bound": v[1], "alpha_steps": v[2],
+                     "launch_variants": plain_variants if name == "plain_fp32" else run.variants}
         if name != "plain_fp32":
             out[name]["speedup_vs_plain"] = plain[-1][0] / h[-1][0] if reached else None
     return out
@@ -501,6 +519,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-gap", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of CUDA-graph replays")
+    ap.add_argument("--no-autotune", action="store_true", help="built-in launch heuristics instead of bab_autotune")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")

@@ -210,7 +210,10 @@ int bab_alpha_grad(bab_ctx *ctx, const float *x0, const float *goal, int horizon
  *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3.
  *   alpha      device float[n][H][sumh] (nullable): receives the final slopes.
  *   lb_best    device float[n].
- * All work is queued on `stream` without host synchronisation.
+ * All work is queued on `stream` without host synchronisation.  In FP32 the
+ * whole loop runs as one launch after the interval bounds
+ * (BAB_KERNEL_ALPHA_FUSED) with the same arithmetic, step for step, as the
+ * separate bound, adjoint and Adam launches.
  * Errors: as bab_bound_crown.
  */
 int bab_alpha_optimize(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
@@ -262,6 +265,46 @@ int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, cons
  * a BAB_ERR_* code recorded by a kernel), then clear it.
  */
 int bab_status(bab_ctx *ctx, void *stream);
+
+/*
+ * Launch variants (tile shapes) and their autotuner.  The paper has no
+ * counterpart: these choose between equivalent launch configurations only;
+ * no variant changes a result beyond floating-point summation order (the
+ * FP32 rollout variants, and the fused alpha loop against the separate
+ * launches, give bit-identical results: each output is summed in the same
+ * order whatever the tile).
+ *   BAB_KERNEL_ROLLOUT_FP32  0: 64 samples x 256 threads, one CTA per SM;
+ *                            1: 64 x 256 with <= 128 registers; 2: 32 x 128.
+ *   BAB_KERNEL_ALPHA_FUSED   -2: separate bound / adjoint / Adam launches;
+ *                            0, 1, 2: one launch, 2, 4 or 8 boxes per CTA with
+ *                            all per-box state in shared memory (small
+ *                            networks and horizons only: BAB_ERR_UNSUPPORTED
+ *                            otherwise); 3 (and -1): one launch, one warp per
+ *                            box, per-box state in global memory.
+ *   BAB_KERNEL_ROLLOUT_TC    1 or 2 sample tiles per CTA.
+ *   BAB_KERNEL_CROWN_TC      1 or 2 box tiles per CTA.
+ * -1 selects the built-in heuristic everywhere.  bab_set_variant returns
+ * BAB_ERR_INVALID_ARG for an unknown kernel or variant; a variant whose tile
+ * does not fit the network makes the later call fail with BAB_ERR_CUDA.
+ */
+#define BAB_KERNEL_ROLLOUT_FP32 0
+#define BAB_KERNEL_ALPHA_FUSED 1
+#define BAB_KERNEL_ROLLOUT_TC 2
+#define BAB_KERNEL_CROWN_TC 3
+int bab_set_variant(bab_ctx *ctx, int kernel, int variant);
+int bab_get_variant(bab_ctx *ctx, int kernel, int *variant);
+
+/*
+ * Times every variant of every kernel above on this problem (n boxes given as
+ * for bab_rollout, `samples` rollouts each, alpha_steps Adam steps when > 0;
+ * 3 timed runs after a warm-up, CUDA events on `stream`) and keeps the
+ * fastest in ctx for later calls.  Synchronises the stream, allocates and
+ * frees temporary device buffers, and must not be called while the stream is
+ * being captured (BAB_ERR_INVALID_ARG).  Results of the timed calls are
+ * discarded; the context's incumbent arguments are not touched.
+ */
+int bab_autotune(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                 const float *hi, const uint64_t *id, int n, int samples, int alpha_steps, void *stream);
 
 /* Size of the fixed device working area of bab_bound_crown_static. */
 #define BAB_STATIC_SCRATCH_BYTES (16u << 20)

@@ -24,6 +24,7 @@ ERRORS = {-1: "BAB_ERR_INVALID_ARG", -2: "BAB_ERR_SHAPE", -3: "BAB_ERR_CUDA", -4
           -5: "BAB_ERR_TIMEOUT", -6: "BAB_ERR_NUMERIC", -7: "BAB_ERR_UNSUPPORTED"}
 PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
 SPLIT_WIDEST = 0
+KERNEL_ROLLOUT_FP32, KERNEL_ALPHA_FUSED, KERNEL_ROLLOUT_TC, KERNEL_CROWN_TC = 0, 1, 2, 3
 
 
 class BabError(RuntimeError):
@@ -69,6 +70,9 @@ def load(path: str = LIB_PATH):
     L.bab_prune_branch.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _I, _P, _P, _P, _P, _P, _P, _P,
                                    _P]
     L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
+    L.bab_set_variant.argtypes = [_P, _I, _I]
+    L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
+    L.bab_autotune.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _I, _I, _P]
     _lib = L
     return L
 
@@ -211,4 +215,22 @@ def bab_alpha_optimize(ctx, x0, goal, horizon, rho, lo, hi, n, steps, lr, lb_bes
     rc = load().bab_alpha_optimize(ctx, _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho), _ptr(lo, f32),
                                    _ptr(hi, f32), int(n), _ptr(d_n, torch.int32), int(steps), float(lr),
                                    int(precision), _ptr(alpha, f32), _ptr(lb_best, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_set_variant(ctx, kernel, variant):
+    _check(ctx, load().bab_set_variant(ctx, int(kernel), int(variant)))
+
+
+def bab_get_variant(ctx, kernel):
+    v = _I()
+    _check(ctx, load().bab_get_variant(ctx, int(kernel), ctypes.byref(v)))
+    return v.value
+
+
+def bab_autotune(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, alpha_steps=0, stream=None):
+    f32 = torch.float32
+    rc = load().bab_autotune(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                             _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), int(n),
+                             int(samples), int(alpha_steps), _stream(stream))
     _check(ctx, rc)

@@ -1,0 +1,357 @@
+// alpha_warp.cu -- alpha-CROWN (Lemma 1's free lower slopes, optimised by
+// projected Adam on the bound of Theorems 1-2) with one warp per box.
+//
+// Lane q of a box's warp owns neurons q, q + 32, ... of every layer: the
+// coefficient vector of the backward pass and the activations of the adjoint
+// forward pass live in registers, and each product A W_l (or W_l z) is a loop
+// over the input index k in which the k-th input is broadcast with a shuffle
+// and every lane adds its own outputs' terms.  Each output is therefore the
+// sequential FMA sum over k from the bias (or 0) that dense_rows forms, and
+// each per-box reduction is the same lane-strided partial sum plus warp tree
+// of k_crown / k_alpha_fwd: the results are bit-identical to the separate
+// bound, adjoint and Adam launches.  All `steps` rounds of a box run in the
+// warp; the per-box arrays (interval bounds, margin helpers, slopes, Adam
+// moments, coefficients before relaxation) are read from and written to
+// global memory, where the L2 keeps them for small problems.
+#include <cmath>
+
+#include "bab_internal.cuh"
+#include "kernels.cuh"
+
+namespace bab {
+
+namespace {
+
+constexpr int kWarps = 8;  // warps (boxes in flight) per CTA
+constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20)
+
+// out[p] (output j = lane + 32 p < Nn) = bias[j] + sum_{k < K} in_k B[k][j], in FMA order over k;
+// in_k is held by lane k % 32 in slot k / 32.  Outputs j >= Nn are 0.
+template <int P>
+__device__ __forceinline__ void dense_warp(const float (&in)[P], int K, const float *__restrict__ B, int Nn,
+                                           const float *__restrict__ bias, float (&out)[P])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = lane + 32 * p;
+        out[p] = (bias && j < Nn) ? bias[j] : 0.f;
+    }
+    // K is a multiple of 4: four inputs per round, their weights loaded ahead of the FMA chain
+    const float *Bj = B + lane;
+#pragma unroll
+    for (int pk = 0; pk < P; ++pk) {
+        if (32 * pk >= K) break;
+        const int kn = min(32, K - 32 * pk);
+        for (int kl = 0; kl < kn; kl += 4) {
+            float x[4], w[4][P];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u] = __shfl_sync(0xFFFFFFFFu, in[pk], kl + u);
+#pragma unroll
+                for (int p = 0; p < P; ++p) w[u][p] = (lane + 32 * p < Nn) ? Bj[32 * p] : 0.f;
+                Bj += Nn;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    if (lane + 32 * p < Nn) out[p] = fmaf(x[u], w[u][p], out[p]);
+        }
+    }
+}
+
+}  // namespace
+
+// P: neurons per lane (every layer width <= 32 P).  WSMEM: both network images in shared memory.
+template <int P, bool WSMEM>
+__global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
+    k_alpha_warp(BoundArgs a, int steps, float lr, float *alpha_g, float *m_g, float *v_g, const AdamTable tab)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, L = N.L, H = a.H, d = a.d, sumh = N.sumh, sw = sumh + s, d4 = pad4(d);
+    const float *fwd = a.fwd, *bwd = a.bwd;
+    float *p = sm;
+    if (WSMEM) {
+        for (int i = threadIdx.x; i < N.img_floats / 4; i += blockDim.x) {
+            smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
+            reinterpret_cast<float4 *>(sm + N.img_floats)[i] = reinterpret_cast<const float4 *>(a.bwd)[i];
+        }
+        fwd = sm;
+        bwd = sm + N.img_floats;
+        p += 2 * N.img_floats;
+    }
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *mu = p + (size_t)wib * 2 * d4;  // coefficients of u, per warp
+    float *us = mu + d4;                   // concretizing point u*, per warp
+    __syncthreads();
+
+    const int nlive = live_count(a.n, a.d_n);
+    const size_t hs = (size_t)H * sumh;
+    for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {
+        const float *pl = a.pre_lo + box * hs, *ph = a.pre_hi + box * hs;
+        const float *S = a.S + (size_t)box * H * sw;
+        const float *xlo = a.x_lo + (size_t)box * (H + 1) * s, *xhi = a.x_hi + (size_t)box * (H + 1) * s;
+        const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
+        float *al = alpha_g + box * hs, *am = m_g + box * hs, *av = v_g + box * hs, *Ap = a.A_pre + box * hs;
+        for (size_t i = lane; i < hs; i += 32) {
+            al[i] = (ph[i] >= -pl[i]) ? 1.f : 0.f;  // adaptive initial slopes
+            am[i] = 0.f;
+            av[i] = 0.f;
+        }
+        __syncwarp();
+        float lb_best = -INFINITY;
+        for (int step = 1; step <= steps; ++step) {
+            // ------------------------------ bound (Theorems 1-2) ------------------------------
+            float A[P], lam[P], tmp[P];
+            float cst, mg = 0.f;
+            {
+                float c = 0.f;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int i = lane + 32 * q;
+                    float aa = 0.f;
+                    if (i < s) {
+                        const float g = a.goal[i];
+                        const float Ls = __fsub_rd(xlo[(size_t)H * s + i], g), Us = __fsub_ru(xhi[(size_t)H * s + i], g);
+                        const float m = 0.5f * (Ls + Us);
+                        aa = 2.f * m;
+                        c = __fadd_rd(c, __fmaf_rd(-aa, g, -__fmul_ru(m, m)));
+                    }
+                    lam[q] = aa;
+                }
+                cst = warp_sum_rd(c);
+            }
+            for (int t = H - 1; t >= 0; --t) {
+                {
+                    const int NpL = pad4(N.dims[L]);
+                    const float *bL = bwd + N.bwd_b[L];
+                    float c = 0.f, e = 0.f;
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        const int i = lane + 32 * q;
+                        const float Av = i < s ? lam[q] : 0.f;
+                        A[q] = Av;
+                        if (i < s) {
+                            c = __fmaf_rd(Av, bL[i], c);
+                            e = __fmaf_ru(fabsf(Av), S[(size_t)t * sw + sumh + i], e);
+                        }
+                    }
+                    c = warp_sum_rd(c);
+                    e = warp_sum_ru(e);
+                    cst = __fadd_rd(cst, c);
+                    mg = __fmaf_ru(N.gam[L], e, mg);
+                    dense_warp<P>(A, NpL, bwd + N.bwd_w[L], pad4(N.dims[L - 1]), nullptr, tmp);
+#pragma unroll
+                    for (int q = 0; q < P; ++q) A[q] = tmp[q];
+                }
+                for (int l = L - 1; l >= 1; --l) {
+                    const int dl = N.dims[l], Npl = pad4(dl);
+                    const float *bl = bwd + N.bwd_b[l];
+                    float c = 0.f, eg = 0.f, er = 0.f;
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < dl) {
+                            const size_t idx = (size_t)t * sumh + N.hoff[l] + j;
+                            const float zl = pl[idx], zu = ph[idx];
+                            const float Av = A[q];
+                            Ap[idx] = Av;
+                            float D, ci;
+                            relax_select(zl, zu, Av, al[idx], true, D, ci);
+                            const float Apj = Av * D;
+                            A[q] = Apj;
+                            c = __fmaf_rd(Av, ci, c);
+                            c = __fmaf_rd(Apj, bl[j], c);
+                            eg = __fmaf_ru(fabsf(Apj), S[(size_t)t * sw + N.hoff[l] + j], eg);
+                            if (D != 0.f && D != 1.f) er = __fmaf_ru(fabsf(Apj), fmaxf(-zl, zu), er);
+                        }
+                    }
+                    c = warp_sum_rd(c);
+                    eg = warp_sum_ru(eg);
+                    er = warp_sum_ru(er);
+                    cst = __fadd_rd(cst, c);
+                    mg = __fadd_ru(mg, __fmaf_ru(N.gam[l], eg, __fmul_ru(kTwoU, er)));
+                    dense_warp<P>(A, Npl, bwd + N.bwd_w[l], pad4(N.dims[l - 1]), nullptr, tmp);
+#pragma unroll
+                    for (int q = 0; q < P; ++q) A[q] = tmp[q];
+                }
+                // A is on [x_t | u_t]: mu_t = A_u; lam <- lam + A_x (+ tangent of ||x_t - g||^2 for t >= 1)
+                float c = 0.f, e = 0.f;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i >= s && i < s + k) mu[t * k + (i - s)] = A[q];
+                    if (i < s) {
+                        const float Ax = A[q], lo_ = lam[q];
+                        float aa = 0.f, B;
+                        if (t >= 1) {
+                            const float g = a.goal[i];
+                            const float xl = xlo[(size_t)t * s + i], xu = xhi[(size_t)t * s + i];
+                            const float Ls = __fsub_rd(xl, g), Us = __fsub_ru(xu, g);
+                            const float m = 0.5f * (Ls + Us);
+                            aa = 2.f * m;
+                            c = __fadd_rd(c, __fmaf_rd(-aa, g, -__fmul_ru(m, m)));
+                            B = fmaxf(fabsf(xl), fabsf(xu));
+                        } else {
+                            B = fabsf(a.x0[i]);
+                        }
+                        lam[q] = (lo_ + Ax) + aa;
+                        const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
+                        e = __fmaf_ru(__fmul_ru(kTwoU, mag), B, e);
+                    }
+                }
+                c = warp_sum_rd(c);
+                e = warp_sum_ru(e);
+                cst = __fadd_rd(cst, c);
+                mg = __fadd_ru(mg, e);
+            }
+            __syncwarp();
+            // lam . x0, then Theorem 2 in box form
+            float lbv;
+            {
+                float c = 0.f, val = 0.f, e = 0.f;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i < s) c = __fmaf_rd(lam[q], a.x0[i], c);
+                }
+                c = __fadd_rd(cst, warp_sum_rd(c));
+                for (int j = lane; j < d; j += 32) {
+                    const float m_ = mu[j];
+                    const float lo = blo[j], hi = bhi[j];
+                    float u_s, vj;
+                    if (a.rho > 0.f) {
+                        const float uc = -m_ / (2.f * a.rho);
+                        if (uc >= lo && uc <= hi) {
+                            u_s = uc;
+                            vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * a.rho);
+                        } else {
+                            u_s = uc < lo ? lo : hi;
+                            vj = __fmaf_rd(m_, u_s, __fmul_rd(a.rho, __fmul_rd(u_s, u_s)));
+                            const float du = __fmul_ru(kTwoU, fabsf(uc));
+                            e = __fmaf_ru(__fmul_ru(a.rho, du), du, e);
+                        }
+                    } else {
+                        u_s = m_ >= 0.f ? lo : hi;
+                        vj = __fmul_rd(m_, u_s);
+                    }
+                    val = __fadd_rd(val, vj);
+                    us[j] = u_s;
+                }
+                val = warp_sum_rd(val);
+                e = warp_sum_ru(e);
+                const float raw = __fadd_rd(c, val);
+                const float marg = __fadd_ru(mg, e);
+                lbv = __fsub_rd(raw, marg);
+            }
+            lb_best = fmaxf(lb_best, lbv);
+            __syncwarp();
+            // ------------------ adjoint: relaxed network forward from x_0 and u*, then Adam ------------------
+            AdamStep ast;
+            ast.lr = lr;
+            if (step <= kAdamTable) {
+                ast.bc1 = tab.bc1[step - 1];
+                ast.bc2 = tab.bc2[step - 1];
+            } else {
+                ast.bc1 = (float)(1.0 - pow(0.9, (double)step));
+                ast.bc2 = (float)(1.0 - pow(0.999, (double)step));
+            }
+            float x[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int i = lane + 32 * q;
+                x[q] = i < s ? a.x0[i] : 0.f;
+            }
+            for (int t = 0; t < H; ++t) {
+                float Z[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int c = lane + 32 * q;
+                    Z[q] = c < s ? x[q] : (c < s + k ? us[t * k + (c - s)] : 0.f);
+                }
+                for (int l = 1; l <= L; ++l) {
+                    dense_warp<P>(Z, pad4(N.dims[l - 1]), fwd + N.fwd_w[l], pad4(N.dims[l]), fwd + N.fwd_b[l], tmp);
+                    if (l < L) {
+                        const int dl = N.dims[l];
+#pragma unroll
+                        for (int q = 0; q < P; ++q) {
+                            const int j = lane + 32 * q;
+                            if (j < dl) {
+                                const size_t idx = (size_t)t * sumh + N.hoff[l] + j;
+                                const float z = tmp[q];
+                                const float zl = pl[idx], zu = ph[idx], Av = Ap[idx];
+                                float D, c;
+                                relax_select(zl, zu, Av, al[idx], true, D, c);
+                                const bool unstable = zl < 0.f && zu > 0.f;
+                                const float g = (unstable && Av >= 0.f) ? Av * z : 0.f;
+                                float alv = al[idx], mv = am[idx], vv = av[idx];
+                                adam_update(alv, mv, vv, g, ast);
+                                al[idx] = alv;
+                                am[idx] = mv;
+                                av[idx] = vv;
+                                tmp[q] = fmaf(D, z, c);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < P; ++q) Z[q] = tmp[q];
+                }
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int i = lane + 32 * q;
+                    if (i < s) x[q] += Z[q];
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) a.lb_best[box] = lb_best;
+    }
+}
+
+template <int P>
+static cudaError_t launch_warp_variant(const BoundArgs &a, int steps, float lr, float *alpha, float *m, float *v,
+                                       cudaStream_t st)
+{
+    int dev, max_optin = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t per_warp = 2 * (size_t)pad4(a.d) * kWarps * sizeof(float);
+    const size_t with_img = per_warp + 2 * (size_t)a.net.img_floats * sizeof(float);
+    const bool wsmem = with_img + 1024 <= (size_t)max_optin;
+    const size_t smem = wsmem ? with_img : per_warp;
+    if (smem + 1024 > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    auto kern = wsmem ? k_alpha_warp<P, true> : k_alpha_warp<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int need = (a.n + kWarps - 1) / kWarps;
+    const int grid = need < nsm * occ ? need : nsm * occ;
+    AdamTable tab;
+    fill_adam_table(tab);
+    kern<<<grid, kWarps * 32, smem, st>>>(a, steps, lr, alpha, m, v, tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_warp(const BoundArgs &a, int steps, float lr, float *alpha, float *m, float *v,
+                              cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    int maxw = 0;
+    for (int l = 0; l <= a.net.L; ++l) maxw = a.net.dims[l] > maxw ? a.net.dims[l] : maxw;
+    // every layer's width and the input row [x | u] must fit the lanes' slots
+    const int need = pad4(maxw) > pad4(a.net.s + a.net.k) ? pad4(maxw) : pad4(a.net.s + a.net.k);
+    if (need <= 32) return launch_warp_variant<1>(a, steps, lr, alpha, m, v, st);
+    if (need <= 64) return launch_warp_variant<2>(a, steps, lr, alpha, m, v, st);
+    if (need <= 128) return launch_warp_variant<4>(a, steps, lr, alpha, m, v, st);
+    if (need <= 256) return launch_warp_variant<8>(a, steps, lr, alpha, m, v, st);
+    return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace bab

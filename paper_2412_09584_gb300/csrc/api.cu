@@ -23,6 +23,11 @@ struct bab_ctx {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     int *d_status = nullptr;
+    // launch variants chosen by bab_autotune (-1: built-in heuristic)
+    int tune_rollout_fp32 = -1;
+    int tune_alpha_fused = -1;  // -2: the unfused loop of bound, adjoint and Adam launches
+    int tune_rollout_tc = -1;   // tiles per CTA
+    int tune_crown_tc = -1;     // tiles per CTA
     char err[512] = {0};
 };
 
@@ -102,7 +107,10 @@ void build_tcb_image(NetDesc &N, const float *params, std::vector<uint8_t> &img)
         dcols = N.tcb_N[l] > dcols ? N.tcb_N[l] : dcols;
         acols = N.tcb_K[l] / 2 > acols ? N.tcb_K[l] / 2 : acols;
     }
-    for (int l = 1; l <= L; ++l) N.tcb_lo[l] = hi + N.tcb_hi[l];
+    for (int l = 1; l <= L; ++l) {
+        N.tcb_lo[l] = hi + N.tcb_hi[l];
+        N.gam_tc[l] = gamma_split(N.tcb_K[l]);
+    }
     N.tcb_bytes = 2 * hi;
     N.tcb_dcols = dcols;
     N.tcb_acols = acols;
@@ -277,6 +285,7 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
     N.sumh = h;
     N.raw_floats = raw;
     N.img_floats = img;
+    for (int l = 1; l <= n_layers; ++l) N.gam[l] = gamma_fp32(pad4(dims[l]));
     for (int i = 0; i < raw; ++i)
         if (!std::isfinite(params[i])) {
             delete c;
@@ -401,8 +410,8 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     a.tc_img = c->d_tc;
     a.tc_bias = c->d_tc_bias;
     a.tc_bytes = c->net.tc_bytes;
-    cudaError_t e = precision == BAB_PREC_FP32 ? launch_rollout_fp32(a, c->num_sms, (cudaStream_t)stream)
-                                               : launch_rollout_tc(a, split, c->num_sms, (cudaStream_t)stream);
+    cudaError_t e = precision == BAB_PREC_FP32 ? launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, (cudaStream_t)stream)
+                                               : launch_rollout_tc(a, split, c->tune_rollout_tc, c->num_sms, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "rollout kernels");
     return BAB_OK;
 }
@@ -454,7 +463,7 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
         a.tcb_img = c->d_tcb;
         a.tc_bias = c->d_tc_bias;
         a.mu = lin_coef ? lin_coef : cv.take<float>((size_t)n * a.d);
-        e = launch_crown_tc(a, c->num_sms, st);
+        e = launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st);
     } else {
         e = launch_crown(a, c->num_sms, st);
     }
@@ -506,7 +515,7 @@ int alpha_grad_core(bab_ctx *c, BoundArgs &a, Carver &cv, int precision, const f
         a.tcb_img = c->d_tcb;
         a.tc_bias = c->d_tc_bias;
         a.mu = cv.take<float>((size_t)n * d);
-        e = launch_crown_tc(a, c->num_sms, st);
+        e = launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st);
     } else {
         e = launch_crown(a, c->num_sms, st);
     }
@@ -596,8 +605,25 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
     // interval bounds do not depend on alpha: once for all steps
     rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
     if (rc) return rc;
+    const int fv = c->tune_alpha_fused;
+    if (precision == BAB_PREC_FP32 && fv >= 0 && fv < 3) {
+        // the whole loop in one launch, a tile of boxes with all its state in shared memory
+        if (!alpha_fused_fits(c->net, H, d)) return fail(c, BAB_ERR_UNSUPPORTED, "fused alpha tile does not fit");
+        a.lb_best = lb_best;
+        cudaError_t e = launch_alpha_fused(a, steps, lr, alpha, fv, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "fused alpha kernel");
+        return BAB_OK;
+    }
     float *al = alpha ? alpha : cv.take<float>(nh);
     float *m = cv.take<float>(nh), *v = cv.take<float>(nh);
+    if (precision == BAB_PREC_FP32 && (fv == -1 || fv == 3)) {
+        // the whole loop in one launch, one warp per box
+        a.A_pre = cv.take<float>(nh);
+        a.lb_best = lb_best;
+        cudaError_t e = launch_alpha_warp(a, steps, lr, al, m, v, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "warp alpha kernel");
+        return BAB_OK;
+    }
     a.A_pre = cv.take<float>(nh);
     a.ustar = cv.take<float>((size_t)n * d);
     a.grad_alpha = cv.take<float>(nh);
@@ -613,7 +639,7 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha set-up");
     a.lb_best = lb_best;
     for (int step = 1; step <= steps; ++step) {
-        e = precision == BAB_PREC_BF16X3 ? launch_crown_tc(a, c->num_sms, st) : launch_crown(a, c->num_sms, st);
+        e = precision == BAB_PREC_BF16X3 ? launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st) : launch_crown(a, c->num_sms, st);
         if (e == cudaSuccess) e = launch_alpha_fwd(a, c->num_sms, st);
         const double bc1 = 1.0 - std::pow(0.9, step), bc2 = 1.0 - std::pow(0.999, step);
         if (e == cudaSuccess) e = launch_adam(al, m, v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);
@@ -662,6 +688,140 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
     a.status = c->d_status;
     cudaError_t e = launch_prune_branch(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "prune/branch kernels");
+    return BAB_OK;
+}
+
+int bab_set_variant(bab_ctx *c, int kernel, int variant)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    switch (kernel) {
+        case BAB_KERNEL_ROLLOUT_FP32:
+            if (variant < -1 || variant >= rollout_fp32_variants()) break;
+            c->tune_rollout_fp32 = variant;
+            return BAB_OK;
+        case BAB_KERNEL_ALPHA_FUSED:
+            if (variant < -2 || variant > 3) break;
+            c->tune_alpha_fused = variant;
+            return BAB_OK;
+        case BAB_KERNEL_ROLLOUT_TC:
+            if (variant != -1 && variant != 1 && variant != 2) break;
+            c->tune_rollout_tc = variant;
+            return BAB_OK;
+        case BAB_KERNEL_CROWN_TC:
+            if (variant != -1 && variant != 1 && variant != 2) break;
+            c->tune_crown_tc = variant;
+            return BAB_OK;
+        default:
+            return fail(c, BAB_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+    }
+    return fail(c, BAB_ERR_INVALID_ARG, "variant %d out of range for kernel %d", variant, kernel);
+}
+
+int bab_get_variant(bab_ctx *c, int kernel, int *variant)
+{
+    if (!c || !variant) return BAB_ERR_INVALID_ARG;
+    switch (kernel) {
+        case BAB_KERNEL_ROLLOUT_FP32: *variant = c->tune_rollout_fp32; return BAB_OK;
+        case BAB_KERNEL_ALPHA_FUSED: *variant = c->tune_alpha_fused; return BAB_OK;
+        case BAB_KERNEL_ROLLOUT_TC: *variant = c->tune_rollout_tc; return BAB_OK;
+        case BAB_KERNEL_CROWN_TC: *variant = c->tune_crown_tc; return BAB_OK;
+        default: return fail(c, BAB_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+    }
+}
+
+}  // extern "C"
+
+namespace {
+
+// Mean milliseconds of `reps` runs of fn after one warm-up run; a negative value if fn fails.
+template <typename F>
+float time_call(cudaStream_t st, int reps, F fn)
+{
+    if (fn() != BAB_OK) return -1.f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1.f;
+    }
+    float ms = -1.f;
+    bool ok = cudaEventRecord(e0, st) == cudaSuccess;
+    for (int i = 0; i < reps && ok; ++i) ok = fn() == BAB_OK;
+    ok = ok && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+         cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ok ? ms / reps : -1.f;
+}
+
+// Times each candidate (set(v) then the call) and keeps the fastest; the setting is left at the winner,
+// or at `fallback` when every candidate failed.
+template <typename Set, typename F>
+int pick_fastest(bab_ctx *c, cudaStream_t st, const std::vector<int> &cands, int fallback, Set set, F fn)
+{
+    int best = fallback;
+    float best_ms = -1.f;
+    for (int v : cands) {
+        set(v);
+        const float ms = time_call(st, 3, fn);
+        if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = v;
+        }
+        c->err[0] = 0;
+    }
+    set(best);
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bab_autotune(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                 const uint64_t *id, int n, int samples, int alpha_steps, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n < 1 || !id) return fail(c, BAB_ERR_INVALID_ARG, "autotuning needs at least one box and its id");
+    if (samples < 1) return fail(c, BAB_ERR_SHAPE, "samples must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+        return fail(c, BAB_ERR_INVALID_ARG, "bab_autotune cannot run inside a stream capture");
+    const int d = c->net.k * H;
+    float *buf = nullptr;
+    const size_t floats = (size_t)n * (d + 2);
+    cudaError_t e = cudaMalloc(&buf, floats * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune buffers");
+    float *ub = buf, *lb = buf + n, *best_u = buf + 2 * (size_t)n;
+    const uint64_t seed = 0x5eedull;
+
+    pick_fastest(c, st, {0, 1, 2}, -1, [&](int v) { c->tune_rollout_fp32 = v; },
+                 [&] { return bab_rollout(c, x0, goal, H, rho, lo, hi, id, n, nullptr, samples, seed, BAB_PREC_FP32, ub,
+                                          best_u, nullptr, nullptr, stream); });
+    const bool tc = c->net.tc_ok && rollout_tc_supported(c->net, 3, c->max_smem);
+    if (tc)
+        pick_fastest(c, st, {1, 2}, -1, [&](int v) { c->tune_rollout_tc = v; },
+                     [&] { return bab_rollout(c, x0, goal, H, rho, lo, hi, id, n, nullptr, samples, seed,
+                                              BAB_PREC_BF16X3, ub, best_u, nullptr, nullptr, stream); });
+    if (crown_tc_supported(c->net, c->max_smem))
+        pick_fastest(c, st, {1, 2}, -1, [&](int v) { c->tune_crown_tc = v; },
+                     [&] { return bab_bound_crown(c, x0, goal, H, rho, lo, hi, n, nullptr, nullptr, BAB_PREC_BF16X3, lb,
+                                                  nullptr, nullptr, nullptr, stream); });
+    if (alpha_steps > 0) {
+        std::vector<int> cands{-2, 3};
+        if (alpha_fused_fits(c->net, H, d))
+            for (int v = 0; v < alpha_fused_variants(); ++v) cands.push_back(v);
+        pick_fastest(c, st, cands, -1, [&](int v) { c->tune_alpha_fused = v; },
+                     [&] { return bab_alpha_optimize(c, x0, goal, H, rho, lo, hi, n, nullptr, alpha_steps, 0.1f,
+                                                     BAB_PREC_FP32, nullptr, lb, stream); });
+    }
+    e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    c->err[0] = 0;
     return BAB_OK;
 }
 

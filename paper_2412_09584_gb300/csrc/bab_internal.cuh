@@ -48,6 +48,11 @@ struct NetDesc {
     int tcb_K[kMaxLayers + 1], tcb_N[kMaxLayers + 1];
     int tcb_hi[kMaxLayers + 1], tcb_lo[kMaxLayers + 1];
     int tcb_bytes, tcb_dcols, tcb_acols;
+    // rounding-error factors of the backward products, formed once on the host (FP64 is slow on the device):
+    // gam[l] = gamma_fp32(pad4(d_l)) for an FP32 product over K = pad4(d_l) terms,
+    // gam_tc[l] = gamma_split(tcb_K[l]) for a 3-term BF16 split product
+    float gam[kMaxLayers + 1];
+    float gam_tc[kMaxLayers + 1];
 };
 
 __host__ __device__ constexpr int pad16(int x) { return (x + 15) & ~15; }
@@ -96,6 +101,15 @@ __host__ __device__ __forceinline__ float gamma_fp32(int n)
     const double u = 5.9604644775390625e-08;
     double g = n * u / (1.0 - n * u);
     return (float)(g * (1.0 + 1e-6));
+}
+
+// Error factor of one 3-term BF16 split product of K terms with FP32 accumulation: 3.1 * 2^-16 for the
+// BF16 hi/lo representation of both operands and the dropped lo x lo term, plus gamma_K with unit 2^-23
+// (allowing a truncating accumulator), rounded up.
+__host__ __device__ __forceinline__ float gamma_split(int K)
+{
+    const double u = 1.1920928955078125e-07;  // 2^-23
+    return (float)(3.1 * 1.52587890625e-05 + K * u / (1.0 - K * u)) * 1.000001f;
 }
 
 __device__ __forceinline__ int live_count(int n, const int *d_n)

@@ -21,6 +21,8 @@
 // it fits (otherwise it is read through L2); the rows move through the layers
 // as register-blocked FP32 products (dense_rows), and each per-row reduction
 // is one warp with shuffles.
+#include <cmath>
+
 #include "bab_internal.cuh"
 #include "kernels.cuh"
 
@@ -220,45 +222,88 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
             if (box0 + r < nlive) a.lb_ibp[box0 + r] = lbacc[r];
 }
 
-template <bool WSMEM>
-__global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
+// ---------------------------------------------------------------------------
+// CROWN and its adjoint over a tile of rows.  The per-box arrays are reached
+// through a RowsView whose pointers start at the tile's first box, so the same
+// code runs on the global arrays (k_crown, k_alpha_fwd) and on copies held in
+// shared memory for a whole alpha optimisation (k_alpha_fused).
+// ---------------------------------------------------------------------------
+struct RowsView {
+    const float *lo, *hi;            // [rows][d]
+    const float *pre_lo, *pre_hi;    // [rows][H][sumh]
+    const float *x_lo, *x_hi;        // [rows][H+1][s]
+    const float *S;                  // [rows][H][sumh + s]
+    float *alpha;                    // [rows][H][sumh] (nullable: adaptive slopes)
+    float *A_pre;                    // [rows][H][sumh] (nullable)
+    float *ustar, *lin_coef;         // [rows][d] (nullable)
+    float *lb, *margin, *lin_const, *lb_best;  // [rows] (lb required, the rest nullable)
+    float *grad;                     // [rows][H][sumh]: adjoint output (nullable when Adam is fused)
+    float *adam_m, *adam_v;          // [rows][H][sumh]: fused Adam moments (nullable)
+};
+
+__device__ __forceinline__ RowsView global_view(const BoundArgs &a, int box0)
 {
-    extern __shared__ float4 smem4[];
-    float *sm = reinterpret_cast<float *>(smem4);
+    const size_t b = (size_t)box0, hs = (size_t)a.H * a.net.sumh;
+    RowsView v;
+    v.lo = a.lo + b * a.d;
+    v.hi = a.hi + b * a.d;
+    v.pre_lo = a.pre_lo + b * hs;
+    v.pre_hi = a.pre_hi + b * hs;
+    v.x_lo = a.x_lo + b * (a.H + 1) * a.net.s;
+    v.x_hi = a.x_hi + b * (a.H + 1) * a.net.s;
+    v.S = a.S + b * a.H * (a.net.sumh + a.net.s);
+    v.alpha = a.alpha ? const_cast<float *>(a.alpha) + b * hs : nullptr;
+    v.A_pre = a.A_pre ? a.A_pre + b * hs : nullptr;
+    v.ustar = a.ustar ? a.ustar + b * a.d : nullptr;
+    v.lin_coef = a.lin_coef ? a.lin_coef + b * a.d : nullptr;
+    v.lb = a.lb + b;
+    v.margin = a.margin ? a.margin + b : nullptr;
+    v.lin_const = a.lin_const ? a.lin_const + b : nullptr;
+    v.lb_best = a.lb_best ? a.lb_best + b : nullptr;
+    v.grad = a.grad_alpha ? a.grad_alpha + b * hs : nullptr;
+    v.adam_m = v.adam_v = nullptr;
+    return v;
+}
+
+// shared-memory floats of crown_rows / fwd_rows scratch
+__host__ __device__ inline size_t crown_rows_floats(const NetDesc &N, int rb, int d)
+{
+    return 2 * (size_t)rb * N.maxw_p + (size_t)rb * pad4(N.s) + (size_t)rb * pad4(d) + 2 * rb;
+}
+__host__ __device__ inline size_t fwd_rows_floats(const NetDesc &N, int rb)
+{
+    return 2 * (size_t)rb * N.maxw_p + (size_t)rb * pad4(N.s);
+}
+
+// Theorem 1 backward propagation of the tangent-linearised cost through all H
+// steps, then Theorem 2 in box form, for rows 0 .. nrows-1 of the view (rows
+// nrows .. RBT-1 are padding).  img: backward image; p: crown_rows_floats of
+// shared memory.
+template <int RBT, int NTT>
+__device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const RowsView &v, int nrows)
+{
     const NetDesc &N = a.net;
     const int s = N.s, k = N.k, L = N.L, d = a.d, H = a.H, sumh = N.sumh, sw = sumh + s;
     const int ld = N.maxw_p, s4 = pad4(s), d4 = pad4(d);
-    const float *img = a.bwd;
-    float *p = sm;
-    if (WSMEM) {
-        for (int i = threadIdx.x; i < N.img_floats / 4; i += NT) smem4[i] = reinterpret_cast<const float4 *>(a.bwd)[i];
-        img = sm;
-        p += N.img_floats;
-    }
     float *Ab[2];
-    Ab[0] = p; p += RB * ld;
-    Ab[1] = p; p += RB * ld;
-    float *lam = p; p += RB * s4;
-    float *mu = p; p += RB * d4;
-    float *cst = p; p += RB;
-    float *mg = p; p += RB;
-
-    const int nlive = live_count(a.n, a.d_n);
-    const int box0 = blockIdx.x * RB;
-    if (box0 >= nlive) return;
+    Ab[0] = p; p += RBT * ld;
+    Ab[1] = p; p += RBT * ld;
+    float *lam = p; p += RBT * s4;
+    float *mu = p; p += RBT * d4;
+    float *cst = p; p += RBT;
+    float *mg = p; p += RBT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool has_alpha = a.alpha != nullptr;
+    const bool has_alpha = v.alpha != nullptr;
 
     // tangent of ||x_H - g||^2: coefficient 2m, constant -(2 m g + m^2)
-    for (int r = warp; r < RB; r += NT / 32) {
-        const int box = box0 + r;
+    for (int r = warp; r < RBT; r += NTT / 32) {
         float c = 0.f;
         for (int i = lane; i < s; i += 32) {
             float aa = 0.f;
-            if (box < nlive) {
+            if (r < nrows) {
                 const float g = a.goal[i];
-                const size_t xi = ((size_t)box * (H + 1) + H) * s + i;
-                const float Ls = __fsub_rd(a.x_lo[xi], g), Us = __fsub_ru(a.x_hi[xi], g);
+                const size_t xi = ((size_t)r * (H + 1) + H) * s + i;
+                const float Ls = __fsub_rd(v.x_lo[xi], g), Us = __fsub_ru(v.x_hi[xi], g);
                 const float m = 0.5f * (Ls + Us);
                 aa = 2.f * m;
                 c = __fadd_rd(c, __fmaf_rd(-aa, g, -__fmul_ru(m, m)));
@@ -278,49 +323,47 @@ __global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
         {
             const int NpL = pad4(N.dims[L]);
             const float *bL = img + N.bwd_b[L];
-            for (int r = warp; r < RB; r += NT / 32) {
-                const int box = box0 + r;
+            for (int r = warp; r < RBT; r += NTT / 32) {
                 float c = 0.f, e = 0.f;
                 for (int q = lane; q < NpL; q += 32) {
                     const float A = q < s ? lam[r * s4 + q] : 0.f;
                     Ab[0][r * ld + q] = A;
-                    if (q < s && box < nlive) {
+                    if (q < s && r < nrows) {
                         c = __fmaf_rd(A, bL[q], c);
-                        e = __fmaf_ru(fabsf(A), a.S[((size_t)box * H + t) * sw + sumh + q], e);
+                        e = __fmaf_ru(fabsf(A), v.S[((size_t)r * H + t) * sw + sumh + q], e);
                     }
                 }
                 c = warp_sum_rd(c);
                 e = warp_sum_ru(e);
                 if (lane == 0) {
                     cst[r] = __fadd_rd(cst[r], c);
-                    mg[r] = __fmaf_ru(gamma_fp32(NpL), e, mg[r]);
+                    mg[r] = __fmaf_ru(N.gam[L], e, mg[r]);
                 }
             }
             __syncthreads();
-            dense_rows_auto<RB, NT>(Ab[0], ld, img + N.bwd_w[L], nullptr, NpL, pad4(N.dims[L - 1]), Ab[1], ld, false);
+            dense_rows_auto<RBT, NTT>(Ab[0], ld, img + N.bwd_w[L], nullptr, NpL, pad4(N.dims[L - 1]), Ab[1], ld, false);
             __syncthreads();
         }
         int cur = 1;
         for (int l = L - 1; l >= 1; --l) {
             const int dl = N.dims[l], Npl = pad4(dl);
             const float *bl = img + N.bwd_b[l];
-            for (int r = warp; r < RB; r += NT / 32) {
-                const int box = box0 + r;
+            for (int r = warp; r < RBT; r += NTT / 32) {
                 float c = 0.f, eg = 0.f, er = 0.f;
-                if (box < nlive) {
-                    const size_t base = ((size_t)box * H + t);
+                if (r < nrows) {
+                    const size_t base = ((size_t)r * H + t);
                     for (int q = lane; q < dl; q += 32) {
                         const size_t idx = base * sumh + N.hoff[l] + q;
-                        const float zl = a.pre_lo[idx], zu = a.pre_hi[idx];
+                        const float zl = v.pre_lo[idx], zu = v.pre_hi[idx];
                         const float A = Ab[cur][r * ld + q];
-                        if (a.A_pre) a.A_pre[idx] = A;
+                        if (v.A_pre) v.A_pre[idx] = A;
                         float D, ci;
-                        relax_select(zl, zu, A, has_alpha ? a.alpha[idx] : 0.f, has_alpha, D, ci);
+                        relax_select(zl, zu, A, has_alpha ? v.alpha[idx] : 0.f, has_alpha, D, ci);
                         const float Ap = A * D;
                         Ab[cur][r * ld + q] = Ap;
                         c = __fmaf_rd(A, ci, c);
                         c = __fmaf_rd(Ap, bl[q], c);
-                        eg = __fmaf_ru(fabsf(Ap), a.S[base * sw + N.hoff[l] + q], eg);
+                        eg = __fmaf_ru(fabsf(Ap), v.S[base * sw + N.hoff[l] + q], eg);
                         if (D != 0.f && D != 1.f) er = __fmaf_ru(fabsf(Ap), fmaxf(-zl, zu), er);
                     }
                 } else {
@@ -331,28 +374,27 @@ __global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
                 er = warp_sum_ru(er);
                 if (lane == 0) {
                     cst[r] = __fadd_rd(cst[r], c);
-                    mg[r] = __fadd_ru(mg[r], __fmaf_ru(gamma_fp32(Npl), eg, __fmul_ru(kTwoU, er)));
+                    mg[r] = __fadd_ru(mg[r], __fmaf_ru(N.gam[l], eg, __fmul_ru(kTwoU, er)));
                 }
             }
             __syncthreads();
-            dense_rows_auto<RB, NT>(Ab[cur], ld, img + N.bwd_w[l], nullptr, Npl, pad4(N.dims[l - 1]), Ab[cur ^ 1], ld,
-                                    false);
+            dense_rows_auto<RBT, NTT>(Ab[cur], ld, img + N.bwd_w[l], nullptr, Npl, pad4(N.dims[l - 1]), Ab[cur ^ 1],
+                                      ld, false);
             __syncthreads();
             cur ^= 1;
         }
         // A is on [x_t | u_t]: mu_t = A_u; lam <- lam + A_x (+ tangent of ||x_t - g||^2 for t >= 1)
-        for (int r = warp; r < RB; r += NT / 32) {
-            const int box = box0 + r;
+        for (int r = warp; r < RBT; r += NTT / 32) {
             float c = 0.f, e = 0.f;
             for (int j = lane; j < k; j += 32) mu[r * d4 + t * k + j] = Ab[cur][r * ld + s + j];
             for (int i = lane; i < s; i += 32) {
                 const float Ax = Ab[cur][r * ld + i];
                 const float lo_ = lam[r * s4 + i];
                 float aa = 0.f, B;
-                if (t >= 1 && box < nlive) {
+                if (t >= 1 && r < nrows) {
                     const float g = a.goal[i];
-                    const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
-                    const float xl = a.x_lo[xi], xu = a.x_hi[xi];
+                    const size_t xi = ((size_t)r * (H + 1) + t) * s + i;
+                    const float xl = v.x_lo[xi], xu = v.x_hi[xi];
                     const float Ls = __fsub_rd(xl, g), Us = __fsub_ru(xu, g);
                     const float m = 0.5f * (Ls + Us);
                     aa = 2.f * m;
@@ -377,15 +419,13 @@ __global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
     }
 
     // lam . x0, then Theorem 2 in box form: sum_j min_{u in [lo, hi]} mu_j u + rho u^2
-    for (int r = warp; r < RB; r += NT / 32) {
-        const int box = box0 + r;
-        if (box >= nlive) continue;
-        float c = 0.f, v = 0.f, e = 0.f;
+    for (int r = warp; r < nrows; r += NTT / 32) {
+        float c = 0.f, val = 0.f, e = 0.f;
         for (int i = lane; i < s; i += 32) c = __fmaf_rd(lam[r * s4 + i], a.x0[i], c);
         c = __fadd_rd(cst[r], warp_sum_rd(c));
         for (int j = lane; j < d; j += 32) {
             const float m_ = mu[r * d4 + j];
-            const float lo = a.lo[(size_t)box * d + j], hi = a.hi[(size_t)box * d + j];
+            const float lo = v.lo[(size_t)r * d + j], hi = v.hi[(size_t)r * d + j];
             float us, vj;
             if (a.rho > 0.f) {
                 const float uc = -m_ / (2.f * a.rho);
@@ -404,35 +444,112 @@ __global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
                 us = m_ >= 0.f ? lo : hi;
                 vj = __fmul_rd(m_, us);
             }
-            v = __fadd_rd(v, vj);
-            if (a.ustar) a.ustar[(size_t)box * d + j] = us;
-            if (a.lin_coef) a.lin_coef[(size_t)box * d + j] = m_;
+            val = __fadd_rd(val, vj);
+            if (v.ustar) v.ustar[(size_t)r * d + j] = us;
+            if (v.lin_coef) v.lin_coef[(size_t)r * d + j] = m_;
         }
-        v = warp_sum_rd(v);
+        val = warp_sum_rd(val);
         e = warp_sum_ru(e);
         if (lane == 0) {
-            const float raw = __fadd_rd(c, v);
+            const float raw = __fadd_rd(c, val);
             const float marg = __fadd_ru(mg[r], e);
             const float lbv = __fsub_rd(raw, marg);
-            a.lb[box] = lbv;
-            if (a.margin) a.margin[box] = marg;
-            if (a.lin_const) a.lin_const[box] = c;
-            if (a.lb_best) a.lb_best[box] = fmaxf(a.lb_best[box], lbv);
+            v.lb[r] = lbv;
+            if (v.margin) v.margin[r] = marg;
+            if (v.lin_const) v.lin_const[r] = c;
+            if (v.lb_best) v.lb_best[r] = fmaxf(v.lb_best[r], lbv);
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// alpha gradient: forward pass of the relaxed network from x_0 and u*
-// ---------------------------------------------------------------------------
+// alpha gradient: forward pass of the relaxed network from x_0 and u*;
+// dLB/dalpha_j = A_j z~_j for an unstable neuron whose coefficient A_j >= 0
+// selects the lower line, 0 otherwise.  With `adam` the projected Adam step is
+// applied to each slope as soon as its gradient is known (its own slope is
+// not needed again in this pass); otherwise the gradient goes to v.grad.
+template <int RBT, int NTT>
+__device__ void fwd_rows(const BoundArgs &a, const float *img, float *p, const RowsView &v, int nrows,
+                         const AdamStep *adam)
+{
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, L = N.L, d = a.d, H = a.H, sumh = N.sumh;
+    const int ld = N.maxw_p, s4 = pad4(s);
+    float *Z[2];
+    Z[0] = p; p += RBT * ld;
+    Z[1] = p; p += RBT * ld;
+    float *xs = p; p += RBT * s4;
+    const bool has_alpha = v.alpha != nullptr;
+    const int Kp1 = pad4(s + k);
+    for (int i = threadIdx.x; i < RBT * s; i += NTT) xs[(i / s) * s4 + i % s] = a.x0[i % s];
+    __syncthreads();
+    for (int t = 0; t < H; ++t) {
+        for (int i = threadIdx.x; i < RBT * Kp1; i += NTT) {
+            const int r = i / Kp1, c = i % Kp1;
+            float val = 0.f;
+            if (c < s) val = xs[r * s4 + c];
+            else if (c < s + k && r < nrows) val = v.ustar[(size_t)r * d + t * k + (c - s)];
+            Z[0][r * ld + c] = val;
+        }
+        __syncthreads();
+        int cur = 0;
+        for (int l = 1; l <= L; ++l) {
+            dense_rows_auto<RBT, NTT>(Z[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], pad4(N.dims[l - 1]),
+                                      pad4(N.dims[l]), Z[cur ^ 1], ld, false);
+            __syncthreads();
+            cur ^= 1;
+            if (l < L) {
+                const int dl = N.dims[l];
+                for (int i = threadIdx.x; i < RBT * dl; i += NTT) {
+                    const int r = i / dl, q = i % dl;
+                    if (r >= nrows) continue;
+                    const size_t idx = ((size_t)r * H + t) * sumh + N.hoff[l] + q;
+                    const float z = Z[cur][r * ld + q];
+                    const float zl = v.pre_lo[idx], zu = v.pre_hi[idx], A = v.A_pre[idx];
+                    float D, c;
+                    relax_select(zl, zu, A, has_alpha ? v.alpha[idx] : 0.f, has_alpha, D, c);
+                    const bool unstable = zl < 0.f && zu > 0.f;
+                    const float g = (unstable && A >= 0.f) ? A * z : 0.f;
+                    if (adam) adam_update(v.alpha[idx], v.adam_m[idx], v.adam_v[idx], g, *adam);
+                    else v.grad[idx] = g;
+                    Z[cur][r * ld + q] = fmaf(D, z, c);
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < RBT * s; i += NTT) {
+            const int r = i / s, c = i % s;
+            xs[r * s4 + c] += Z[cur][r * ld + c];
+        }
+        __syncthreads();
+    }
+}
+
+template <bool WSMEM>
+__global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const float *img = a.bwd;
+    float *p = sm;
+    if (WSMEM) {
+        for (int i = threadIdx.x; i < N.img_floats / 4; i += NT) smem4[i] = reinterpret_cast<const float4 *>(a.bwd)[i];
+        img = sm;
+        p += N.img_floats;
+    }
+    const int nlive = live_count(a.n, a.d_n);
+    const int box0 = blockIdx.x * RB;
+    if (box0 >= nlive) return;
+    const int nrows = min(RB, nlive - box0);
+    crown_rows<RB, NT>(a, img, p, global_view(a, box0), nrows);
+}
+
 template <bool WSMEM>
 __global__ void __launch_bounds__(NT) k_alpha_fwd(BoundArgs a)
 {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const NetDesc &N = a.net;
-    const int s = N.s, k = N.k, L = N.L, d = a.d, H = a.H, sumh = N.sumh;
-    const int ld = N.maxw_p, s4 = pad4(s);
     const float *img = a.fwd;
     float *p = sm;
     if (WSMEM) {
@@ -440,58 +557,122 @@ __global__ void __launch_bounds__(NT) k_alpha_fwd(BoundArgs a)
         img = sm;
         p += N.img_floats;
     }
-    float *Z[2];
-    Z[0] = p; p += RB * ld;
-    Z[1] = p; p += RB * ld;
-    float *xs = p; p += RB * s4;
-
     const int nlive = live_count(a.n, a.d_n);
     const int box0 = blockIdx.x * RB;
     if (box0 >= nlive) return;
-    const bool has_alpha = a.alpha != nullptr;
-    const int Kp1 = pad4(s + k);
-    for (int i = threadIdx.x; i < RB * s; i += NT) xs[(i / s) * s4 + i % s] = a.x0[i % s];
+    const int nrows = min(RB, nlive - box0);
+    fwd_rows<RB, NT>(a, img, p, global_view(a, box0), nrows, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Fused alpha-CROWN: the whole optimisation of a tile of RBT boxes in one CTA.
+// Both network images and every per-box array (interval bounds, margin
+// helpers, slopes, Adam moments, coefficients before relaxation, u*) stay in
+// shared memory for all `steps` (bound, adjoint + Adam) rounds; only the best
+// bound (and the final slopes, when asked for) go back to global memory.  The
+// arithmetic is that of k_crown, k_alpha_fwd and k_adam, step for step.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t fused_box_floats(const NetDesc &N, int H, int d)
+{
+    const size_t hs = (size_t)H * N.sumh;
+    return 6 * hs + (size_t)H * (N.sumh + N.s) + 2 * (size_t)(H + 1) * N.s + 3 * (size_t)d + 2;
+}
+
+template <int RBT, int NTT>
+__global__ void __launch_bounds__(NTT) k_alpha_fused(BoundArgs a, int steps, float lr, float *alpha_out,
+                                                     const AdamTable tab)
+{
+    __shared__ float bc_sh[2];
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const int H = a.H, d = a.d, s = N.s;
+    const size_t hs = (size_t)H * N.sumh, hw = (size_t)H * (N.sumh + s), xs_ = (size_t)(H + 1) * s;
+    const int nlive = live_count(a.n, a.d_n);
+    const int box0 = blockIdx.x * RBT;
+    if (box0 >= nlive) return;
+    const int nrows = min(RBT, nlive - box0);
+
+    float *p = sm;
+    const float *fwd = p;
+    for (int i = threadIdx.x; i < N.img_floats / 4; i += NTT) smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
+    p += N.img_floats;
+    const float *bwd = p;
+    for (int i = threadIdx.x; i < N.img_floats / 4; i += NTT)
+        reinterpret_cast<float4 *>(p)[i] = reinterpret_cast<const float4 *>(a.bwd)[i];
+    p += N.img_floats;
+    RowsView v;
+    float *pl = p; p += RBT * hs;
+    float *ph = p; p += RBT * hs;
+    v.alpha = p; p += RBT * hs;
+    v.adam_m = p; p += RBT * hs;
+    v.adam_v = p; p += RBT * hs;
+    v.A_pre = p; p += RBT * hs;
+    float *Sv = p; p += RBT * hw;
+    float *xl = p; p += RBT * xs_;
+    float *xu = p; p += RBT * xs_;
+    float *blo = p; p += (size_t)RBT * d;
+    float *bhi = p; p += (size_t)RBT * d;
+    v.ustar = p; p += (size_t)RBT * d;
+    v.lb = p; p += RBT;
+    v.lb_best = p; p += RBT;
+    float *scratch = sm + ((p - sm + 3) & ~(ptrdiff_t)3);  // float4-aligned for dense_rows
+    v.pre_lo = pl;
+    v.pre_hi = ph;
+    v.S = Sv;
+    v.x_lo = xl;
+    v.x_hi = xu;
+    v.lo = blo;
+    v.hi = bhi;
+    v.lin_coef = nullptr;
+    v.margin = v.lin_const = nullptr;
+    v.grad = nullptr;
+
+    const size_t b = (size_t)box0;
+    for (size_t i = threadIdx.x; i < (size_t)nrows * hs; i += NTT) {
+        const float zl = a.pre_lo[b * hs + i], zu = a.pre_hi[b * hs + i];
+        pl[i] = zl;
+        ph[i] = zu;
+        v.alpha[i] = (zu >= -zl) ? 1.f : 0.f;  // adaptive initial slopes
+        v.adam_m[i] = 0.f;
+        v.adam_v[i] = 0.f;
+    }
+    for (size_t i = threadIdx.x; i < (size_t)nrows * hw; i += NTT) Sv[i] = a.S[b * hw + i];
+    for (size_t i = threadIdx.x; i < (size_t)nrows * xs_; i += NTT) {
+        xl[i] = a.x_lo[b * xs_ + i];
+        xu[i] = a.x_hi[b * xs_ + i];
+    }
+    for (size_t i = threadIdx.x; i < (size_t)nrows * d; i += NTT) {
+        blo[i] = a.lo[b * d + i];
+        bhi[i] = a.hi[b * d + i];
+    }
+    for (int r = threadIdx.x; r < RBT; r += NTT) v.lb_best[r] = -INFINITY;
     __syncthreads();
-    for (int t = 0; t < H; ++t) {
-        for (int i = threadIdx.x; i < RB * Kp1; i += NT) {
-            const int r = i / Kp1, c = i % Kp1;
-            const int box = box0 + r;
-            float v = 0.f;
-            if (c < s) v = xs[r * s4 + c];
-            else if (c < s + k && box < nlive) v = a.ustar[(size_t)box * d + t * k + (c - s)];
-            Z[0][r * ld + c] = v;
-        }
+
+    for (int step = 1; step <= steps; ++step) {
+        crown_rows<RBT, NTT>(a, bwd, scratch, v, nrows);
         __syncthreads();
-        int cur = 0;
-        for (int l = 1; l <= L; ++l) {
-            dense_rows_auto<RB, NT>(Z[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], pad4(N.dims[l - 1]),
-                                    pad4(N.dims[l]), Z[cur ^ 1], ld, false);
-            __syncthreads();
-            cur ^= 1;
-            if (l < L) {
-                const int dl = N.dims[l];
-                for (int i = threadIdx.x; i < RB * dl; i += NT) {
-                    const int r = i / dl, q = i % dl;
-                    const int box = box0 + r;
-                    if (box >= nlive) continue;
-                    const size_t idx = ((size_t)box * H + t) * sumh + N.hoff[l] + q;
-                    const float z = Z[cur][r * ld + q];
-                    const float zl = a.pre_lo[idx], zu = a.pre_hi[idx], A = a.A_pre[idx];
-                    float D, c;
-                    relax_select(zl, zu, A, has_alpha ? a.alpha[idx] : 0.f, has_alpha, D, c);
-                    const bool unstable = zl < 0.f && zu > 0.f;
-                    a.grad_alpha[idx] = (unstable && A >= 0.f) ? A * z : 0.f;
-                    Z[cur][r * ld + q] = fmaf(D, z, c);
-                }
-                __syncthreads();
+        AdamStep st;
+        st.lr = lr;
+        if (step <= kAdamTable) {
+            st.bc1 = tab.bc1[step - 1];
+            st.bc2 = tab.bc2[step - 1];
+        } else {
+            // beyond the table: one thread forms the constants (FP64 is slow on this part)
+            if (threadIdx.x == 0) {
+                bc_sh[0] = (float)(1.0 - pow(0.9, (double)step));
+                bc_sh[1] = (float)(1.0 - pow(0.999, (double)step));
             }
+            __syncthreads();
+            st.bc1 = bc_sh[0];
+            st.bc2 = bc_sh[1];
         }
-        for (int i = threadIdx.x; i < RB * s; i += NT) {
-            const int r = i / s, c = i % s;
-            xs[r * s4 + c] += Z[cur][r * ld + c];
-        }
+        fwd_rows<RBT, NTT>(a, fwd, scratch, v, nrows, &st);
         __syncthreads();
     }
+    for (int r = threadIdx.x; r < nrows; r += NTT) a.lb_best[box0 + r] = v.lb_best[r];
+    if (alpha_out)
+        for (size_t i = threadIdx.x; i < (size_t)nrows * hs; i += NTT) alpha_out[b * hs + i] = v.alpha[i];
 }
 
 __global__ void k_alpha_init(BoundArgs a)
@@ -504,15 +685,16 @@ __global__ void k_alpha_init(BoundArgs a)
 
 __global__ void k_adam(float *alpha, float *m, float *v, const float *g, long long count, float lr, float bc1, float bc2)
 {
+    AdamStep st;
+    st.lr = lr;
+    st.bc1 = bc1;
+    st.bc2 = bc2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = 0.9f * m[i] + 0.1f * gi;
-        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        float al = alpha[i], mi = m[i], vi = v[i];
+        adam_update(al, mi, vi, g[i], st);
+        alpha[i] = al;
         m[i] = mi;
         v[i] = vi;
-        const float mh = mi / bc1, vh = vi / bc2;
-        float x = alpha[i] + lr * mh / (sqrtf(vh) + 1e-8f);
-        alpha[i] = fminf(fmaxf(x, 0.f), 1.f);
     }
 }
 
@@ -552,15 +734,55 @@ cudaError_t launch_ibp(const BoundArgs &a, int, cudaStream_t st)
 cudaError_t launch_crown(const BoundArgs &a, int, cudaStream_t st)
 {
     const NetDesc &N = a.net;
-    size_t rest = (2 * (size_t)RB * N.maxw_p + (size_t)RB * pad4(N.s) + (size_t)RB * pad4(a.d) + 2 * RB) * sizeof(float);
+    size_t rest = crown_rows_floats(N, RB, a.d) * sizeof(float);
     return launch_rows_kernel(k_crown<true>, k_crown<false>, (size_t)N.img_floats * 4, rest, a.n, a, st);
 }
 
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int, cudaStream_t st)
 {
     const NetDesc &N = a.net;
-    size_t rest = (2 * (size_t)RB * N.maxw_p + (size_t)RB * pad4(N.s)) * sizeof(float);
+    size_t rest = fwd_rows_floats(N, RB) * sizeof(float);
     return launch_rows_kernel(k_alpha_fwd<true>, k_alpha_fwd<false>, (size_t)N.img_floats * 4, rest, a.n, a, st);
+}
+
+static size_t fused_smem(const NetDesc &N, int rb, int H, int d)
+{
+    const size_t rows = crown_rows_floats(N, rb, d), fw = fwd_rows_floats(N, rb);
+    return (2 * (size_t)N.img_floats + (size_t)rb * fused_box_floats(N, H, d) + 4 + (rows > fw ? rows : fw)) *
+           sizeof(float);
+}
+
+template <int RBT, int NTT>
+static cudaError_t launch_fused_variant(const BoundArgs &a, int steps, float lr, float *alpha_out, cudaStream_t st)
+{
+    const size_t smem = fused_smem(a.net, RBT, a.H, a.d);
+    if (smem > (size_t)max_optin_smem()) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(k_alpha_fused<RBT, NTT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    AdamTable tab;
+    fill_adam_table(tab);
+    k_alpha_fused<RBT, NTT><<<(a.n + RBT - 1) / RBT, NTT, smem, st>>>(a, steps, lr, alpha_out, tab);
+    return cudaGetLastError();
+}
+
+int alpha_fused_variants() { return 3; }
+
+bool alpha_fused_fits(const NetDesc &N, int H, int d)
+{
+    return fused_smem(N, 2, H, d) <= (size_t)max_optin_smem();
+}
+
+// variant 0: 2 boxes x 64 threads per CTA; 1: 4 x 128; 2: 8 x 256; < 0: the most boxes that fit in shared memory,
+// at most 4.  Returns cudaErrorInvalidConfiguration when the tile does not fit.
+cudaError_t launch_alpha_fused(const BoundArgs &a, int steps, float lr, float *alpha_out, int variant, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    if (variant < 0) variant = fused_smem(a.net, 4, a.H, a.d) <= (size_t)max_optin_smem() ? 1 : 0;
+    switch (variant) {
+        case 0: return launch_fused_variant<2, 64>(a, steps, lr, alpha_out, st);
+        case 1: return launch_fused_variant<4, 128>(a, steps, lr, alpha_out, st);
+        default: return launch_fused_variant<8, 256>(a, steps, lr, alpha_out, st);
+    }
 }
 
 __global__ void k_fill_f32(float *p, int n, float v)
@@ -580,6 +802,14 @@ cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st)
     if (a.n <= 0) return cudaSuccess;
     k_alpha_init<<<1024, 256, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+void fill_adam_table(AdamTable &tab)
+{
+    for (int i = 0; i < kAdamTable; ++i) {
+        tab.bc1[i] = (float)(1.0 - std::pow(0.9, i + 1));
+        tab.bc2[i] = (float)(1.0 - std::pow(0.999, i + 1));
+    }
 }
 
 cudaError_t launch_adam(float *alpha, float *m, float *v, const float *grad, long long count, float lr, float bc1,

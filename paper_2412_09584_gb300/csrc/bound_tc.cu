@@ -36,13 +36,6 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kEpi = 8;
 constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20)
 
-__device__ __forceinline__ float gamma_tc(int K)
-{
-    // split error of one product term plus the FP32 accumulation of K terms
-    const double u = 1.1920928955078125e-07;  // 2^-23
-    return (float)(3.1 * 1.52587890625e-05 + K * u / (1.0 - K * u)) * 1.000001f;
-}
-
 __device__ __forceinline__ uint32_t pack2(float a, float b)
 {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -173,7 +166,7 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
                             cst = __fmaf_rd(lam[i], bL[i], cst);
                             e = __fmaf_ru(fabsf(lam[i]), a.S[rowb * sw + sumh + i], e);
                         }
-                    mg = __fmaf_ru(gamma_tc(N.tcb_K[L]), e, mg);
+                    mg = __fmaf_ru(N.gam_tc[L], e, mg);
                     tc::tmem_wait_st();
                 }
                 tc::fence_before_sync();
@@ -191,7 +184,7 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
                     const int dl = N.dims[l];
                     const int c_beg = primary ? 0 : dl / 2, c_end = (dl % 64 == 0) ? c_beg + dl / 2 : (primary ? dl : 0);
                     const float *bl = bias + N.tc_boff[l];
-                    const float gK = gamma_tc(N.tcb_K[l]);
+                    const float gK = N.gam_tc[l];
                     float eg = 0.f, er = 0.f;
                     for (int c0 = c_beg; c0 < c_end; c0 += 32) {
                         uint32_t v[32];
@@ -409,13 +402,15 @@ static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_crown_tc(BoundArgs a, int num_sms, cudaStream_t st)
+// nslot_pref: tiles per CTA (1 or 2), or -1 for two only when the tiles outnumber the SMs
+cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream_t st)
 {
     const NetDesc &N = a.net;
     if (a.n <= 0) return cudaSuccess;
     const int slot_cols = N.tcb_dcols + 2 * N.tcb_acols;
     const int ntiles = (a.n + 127) / 128;
-    const int nslot = (ntiles > num_sms && 2 * slot_cols <= 512) ? 2 : 1;
+    int nslot = (ntiles > num_sms && 2 * slot_cols <= 512) ? 2 : 1;
+    if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
     int cols = 32;
     while (cols < nslot * slot_cols) cols *= 2;
     if (cols > 512) return cudaErrorInvalidConfiguration;

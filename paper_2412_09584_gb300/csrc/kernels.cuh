@@ -58,6 +58,30 @@ struct BoundArgs {
     uint32_t tmem_cols;
 };
 
+struct AdamStep {
+    float lr, bc1, bc2;
+};
+
+// Projected Adam ascent step (beta1 0.9, beta2 0.999, eps 1e-8), every operation rounded to nearest on its own
+// (no contraction), so that the fused loop and the separate Adam launch agree bit for bit.
+__device__ __forceinline__ float adam_update(float &alpha, float &m, float &v, float g, const AdamStep &s)
+{
+    const float mi = __fadd_rn(__fmul_rn(0.9f, m), __fmul_rn(0.1f, g));
+    const float vi = __fadd_rn(__fmul_rn(0.999f, v), __fmul_rn(__fmul_rn(0.001f, g), g));
+    m = mi;
+    v = vi;
+    const float mh = __fdiv_rn(mi, s.bc1), vh = __fdiv_rn(vi, s.bc2);
+    const float x = __fadd_rn(alpha, __fdiv_rn(__fmul_rn(s.lr, mh), __fadd_rn(__fsqrt_rn(vh), 1e-8f)));
+    alpha = fminf(fmaxf(x, 0.f), 1.f);
+    return alpha;
+}
+
+// Adam bias corrections 1 - beta^step, formed on the host in FP64 exactly as for the separate Adam launches
+constexpr int kAdamTable = 128;
+struct AdamTable {
+    float bc1[kAdamTable], bc2[kAdamTable];
+};
+
 // out[r][c] = act(sum_k in[r][k] * B[k][c] + bias[c]) for r < R, c < Np, where
 // B is [Kp][Np] row-major (a forward image Wt_l, or a backward image W_l).
 // Kp % 4 == 0 and Np % 4 == 0; bias may be null.
@@ -134,18 +158,28 @@ __device__ __forceinline__ void dense_rows_auto(const float *in, int ldi, const 
 }
 
 // host launchers (return the first CUDA error)
-cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_rollout_tc(RolloutArgs a, int split, int num_sms, cudaStream_t st);
+// variant < 0 picks by shared-memory size; rollout_fp32_variants() variants exist (the autotuner times them)
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, int variant, int num_sms, cudaStream_t st);
+int rollout_fp32_variants();
+cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_sms, cudaStream_t st);
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem);
 void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st);
 void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st);
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st);
 cudaError_t launch_ibp(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_crown_tc(BoundArgs a, int num_sms, cudaStream_t st);
+cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream_t st);
 bool crown_tc_supported(const NetDesc &N, int max_smem);
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
+// the whole alpha optimisation of a tile of boxes in one CTA (needs the interval bounds of launch_ibp)
+cudaError_t launch_alpha_fused(const BoundArgs &a, int steps, float lr, float *alpha_out, int variant, cudaStream_t st);
+// the whole alpha optimisation with one warp per box; alpha (written), m, v: [n][H][sumh] device arrays
+cudaError_t launch_alpha_warp(const BoundArgs &a, int steps, float lr, float *alpha, float *m, float *v,
+                              cudaStream_t st);
+void fill_adam_table(AdamTable &tab);
+bool alpha_fused_fits(const NetDesc &N, int H, int d);
+int alpha_fused_variants();
 cudaError_t launch_fill(float *p, int n, float v, cudaStream_t st);
 cudaError_t launch_adam(float *alpha, float *m, float *v, const float *grad, long long count, float lr, float bc1,
                         float bc2, cudaStream_t st);

@@ -16,8 +16,8 @@ namespace bab {
 
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) { return a < b ? a : b; }
 
-template <int R, int NT, bool WSMEM>
-__global__ void __launch_bounds__(NT, 1) k_rollout_fp32(RolloutArgs a)
+template <int R, int NT, bool WSMEM, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
 {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
@@ -222,29 +222,52 @@ static size_t rollout_smem_bytes(const NetDesc &N, int R, int d, bool wsmem)
     return f * sizeof(float);
 }
 
-cudaError_t launch_rollout_fp32(const RolloutArgs &a, int num_sms, cudaStream_t st)
+template <int R, int NT, int MINB>
+static cudaError_t launch_fp32_variant(const RolloutArgs &a, int num_sms, size_t budget, cudaStream_t st)
 {
-    constexpr int R = 64, NT = 256;
+    bool wsmem = rollout_smem_bytes(a.net, R, a.d, true) <= budget;
+    size_t smem = rollout_smem_bytes(a.net, R, a.d, wsmem);
+    if (smem > budget) return cudaErrorInvalidConfiguration;
+    auto kern = wsmem ? k_rollout_fp32<R, NT, true, MINB> : k_rollout_fp32<R, NT, false, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const long long ntiles = (long long)a.n * ((a.M + R - 1) / R);
+    const long long slots = (long long)num_sms * occ;
+    const int grid = (int)(ntiles < slots ? ntiles : slots);
+    kern<<<grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+int rollout_fp32_variants() { return 3; }
+
+// variant 0: 64 samples x 256 threads per CTA, one CTA per SM (large networks, weights in shared memory);
+// variant 1: 64 x 256 with at most 128 registers (two or more CTAs per SM for small networks);
+// variant 2: 32 x 128, at most 128 registers.
+cudaError_t launch_rollout_fp32(const RolloutArgs &a, int variant, int num_sms, cudaStream_t st)
+{
     int dev;
     cudaGetDevice(&dev);
     int max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t budget = (size_t)max_optin - 1024;  // room for static shared memory
-    bool wsmem = rollout_smem_bytes(a.net, R, a.d, true) <= budget;
-    size_t smem = rollout_smem_bytes(a.net, R, a.d, wsmem);
-    if (smem > budget) return cudaErrorInvalidConfiguration;
+    if (rollout_smem_bytes(a.net, 64, a.d, false) > budget) return cudaErrorInvalidConfiguration;
     if (a.n <= 0) return cudaSuccess;
-    k_fill_keys(a.keys, a.n, st);
-    long long ntiles = (long long)a.n * ((a.M + R - 1) / R);
-    int grid = (int)(ntiles < (long long)num_sms ? ntiles : num_sms);
-    if (grid < 1) grid = 1;
-    if (wsmem) {
-        cudaFuncSetAttribute(k_rollout_fp32<R, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rollout_fp32<R, NT, true><<<grid, NT, smem, st>>>(a);
-    } else {
-        cudaFuncSetAttribute(k_rollout_fp32<R, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rollout_fp32<R, NT, false><<<grid, NT, smem, st>>>(a);
+    if (variant < 0) {
+        // default: the register-capped variant once two CTAs' shared memory fits on an SM
+        variant = rollout_smem_bytes(a.net, 64, a.d, true) * 2 + 2048 <= (size_t)max_optin ? 1 : 0;
     }
+    k_fill_keys(a.keys, a.n, st);
+    cudaError_t e;
+    switch (variant) {
+        case 1: e = launch_fp32_variant<64, 256, 2>(a, num_sms, budget, st); break;
+        case 2: e = launch_fp32_variant<32, 128, 4>(a, num_sms, budget, st); break;
+        default: e = launch_fp32_variant<64, 256, 1>(a, num_sms, budget, st); break;
+    }
+    if (e != cudaSuccess) return e;
     launch_rollout_finalize(a, st);
     if (a.inc_val) launch_incumbent(a, st);
     return cudaGetLastError();

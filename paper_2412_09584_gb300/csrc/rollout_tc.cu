@@ -413,13 +413,15 @@ bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
     return rollout_tc_smem(N, split, 2) + 1024 <= (size_t)max_smem;
 }
 
-cudaError_t launch_rollout_tc(RolloutArgs a, int split, int num_sms, cudaStream_t st)
+// nslot_pref: tiles per CTA (1 or 2), or -1 for two whenever both fit in tensor memory
+cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_sms, cudaStream_t st)
 {
     const NetDesc &N = a.net;
     if (a.n <= 0) return cudaSuccess;
     // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
     const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols;
-    const int nslot = (2 * slot_cols <= 512) ? 2 : 1;
+    int nslot = (2 * slot_cols <= 512) ? 2 : 1;
+    if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
     int cols = 32;
     while (cols < nslot * slot_cols) cols *= 2;
     if (cols > 512) return cudaErrorInvalidConfiguration;

@@ -85,6 +85,7 @@ bool make_net_desc(bab::NetDesc &N, int L, const int *dims, int s, int k)
     N.sumh = h;
     N.raw_floats = raw;
     N.img_floats = img;
+    for (int l = 1; l <= L; ++l) N.gam[l] = gamma_fp32(pad4(dims[l]));
     return true;
 }
 

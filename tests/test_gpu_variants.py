@@ -1,0 +1,154 @@
+"""Launch variants (tile shapes), the fused alpha-CROWN loop and the autotuner: every variant must give the
+same results as the others (bit-identical where the arithmetic is the same), and the oracle still agrees."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_09584_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _problem(name, n, seed=5):
+    from gpu_util import GpuProblem
+    p = W.config_problem(name, seed)
+    d = p["k"] * p["H"]
+    lo, hi, ids = W.random_boxes(d, n, seed=seed + 1, min_width=0.2, max_width=2.0)
+    return p, lo, hi, ids, GpuProblem(p)
+
+
+@pytest.mark.parametrize("name,n,M", [("tiny", 37, 256), ("pushing", 9, 200)])
+def test_rollout_fp32_variants_bit_identical(oracle, name, n, M):
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem(name, n)
+    try:
+        outs = []
+        for v in range(3):
+            B.bab_set_variant(g.ctx, B.KERNEL_ROLLOUT_FP32, v)
+            outs.append(g.rollout(lo, hi, ids, M=M, seed=77))
+        for o in outs[1:]:
+            assert np.array_equal(o["ub"].view(np.uint32), outs[0]["ub"].view(np.uint32))
+            assert np.array_equal(o["best_u"].view(np.uint32), outs[0]["best_u"].view(np.uint32))
+        ub_o, _, _ = oracle.rollout(p, lo, hi, ids, M, 77)
+        np.testing.assert_allclose(outs[0]["ub"], ub_o, rtol=1e-5, atol=0)
+    finally:
+        g.close()
+
+
+def test_rollout_tc_slots_bit_identical():
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem("pushing", 5)
+    try:
+        outs = []
+        for v in (1, 2):
+            B.bab_set_variant(g.ctx, B.KERNEL_ROLLOUT_TC, v)
+            outs.append(g.rollout(lo, hi, ids, M=300, seed=3, precision=B.PREC_BF16X3))
+        assert np.array_equal(outs[0]["ub"].view(np.uint32), outs[1]["ub"].view(np.uint32))
+        assert np.array_equal(outs[0]["best_u"].view(np.uint32), outs[1]["best_u"].view(np.uint32))
+    finally:
+        g.close()
+
+
+def test_crown_tc_slots_bit_identical():
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem("tiny", 300)
+    try:
+        outs = []
+        for v in (1, 2):
+            B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, v)
+            outs.append(g.crown(lo, hi, precision=B.PREC_BF16X3))
+        for key in ("lb", "margin", "lin_coef", "lin_const"):
+            assert np.array_equal(outs[0][key].view(np.uint32), outs[1][key].view(np.uint32)), key
+    finally:
+        g.close()
+
+
+def test_set_variant_rejects_bad_values():
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem("tiny", 4)
+    try:
+        for kernel, bad in ((B.KERNEL_ROLLOUT_FP32, 3), (B.KERNEL_ALPHA_FUSED, -3), (B.KERNEL_ALPHA_FUSED, 4),
+                            (B.KERNEL_ROLLOUT_TC, 0),
+                            (B.KERNEL_CROWN_TC, 3), (9, 0)):
+            with pytest.raises(B.BabError) as e:
+                B.bab_set_variant(g.ctx, kernel, bad)
+            assert e.value.code == -1
+        B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, -2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_ALPHA_FUSED) == -2
+    finally:
+        g.close()
+
+
+def _optimize(g, lo, hi, steps, variant):
+    from gpu_util import T
+    from paper_2412_09584_gb300 import binding as B
+    n = lo.shape[0]
+    B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, variant)
+    best = torch.empty(n, device="cuda")
+    alpha = torch.empty(n, g.H, g.sumh, device="cuda")
+    B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, steps, 0.1, best, alpha=alpha,
+                         precision=B.PREC_FP32)
+    torch.cuda.synchronize()
+    return best.cpu().numpy(), alpha.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,n", [("alpha", 300), ("tiny", 67)])
+def test_alpha_fused_matches_unfused_loop(oracle, name, n):
+    """One launch for the whole Adam loop gives the separate launches' bounds and slopes."""
+    p, lo, hi, ids, g = _problem(name, n, seed=9)
+    try:
+        b_ref, a_ref = _optimize(g, lo, hi, 20, -2)
+        fused = [_optimize(g, lo, hi, 20, v) for v in (3, 0, 1, 2, -1)]
+        for b, a in fused[1:]:
+            assert np.array_equal(b.view(np.uint32), fused[0][0].view(np.uint32))
+            assert np.array_equal(a.view(np.uint32), fused[0][1].view(np.uint32))
+        scale = np.maximum(oracle.crown(p, lo, hi)["scale"], 1.0)
+        b, a = fused[0]
+        # the same arithmetic in the same order, step for step
+        assert np.array_equal(b.view(np.uint32), b_ref.view(np.uint32))
+        assert np.array_equal(a.view(np.uint32), a_ref.view(np.uint32))
+        best_o, _, _, _ = oracle.alpha_optimize(p, lo[:24], hi[:24], 20, 0.1)
+        assert np.all(np.abs(b[:24] - best_o) <= 1e-3 * scale[:24])
+    finally:
+        g.close()
+
+
+def test_alpha_warp_pushing_matches_unfused_loop():
+    """The warp-per-box loop on a network whose weights stay in global memory (4 neurons per lane)."""
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem("pushing", 11, seed=2)
+    try:
+        b_ref, a_ref = _optimize(g, lo, hi, 4, -2)
+        b, a = _optimize(g, lo, hi, 4, 3)
+        assert np.array_equal(b.view(np.uint32), b_ref.view(np.uint32))
+        assert np.array_equal(a.view(np.uint32), a_ref.view(np.uint32))
+        # the shared-memory tile does not fit this network
+        with pytest.raises(B.BabError) as e:
+            _optimize(g, lo, hi, 4, 0)
+        assert e.value.code == -7
+    finally:
+        g.close()
+
+
+def test_autotune_keeps_results(oracle):
+    from gpu_util import T, ids_t
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem("tiny", 200, seed=11)
+    try:
+        before = g.rollout(lo, hi, ids, M=256, seed=5)
+        B.bab_autotune(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), ids_t(ids), lo.shape[0], 256, alpha_steps=4)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_FP32) in (0, 1, 2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_TC) in (1, 2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_CROWN_TC) in (1, 2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_ALPHA_FUSED) in (-2, 0, 1, 2, 3)
+        after = g.rollout(lo, hi, ids, M=256, seed=5)
+        assert np.array_equal(after["ub"].view(np.uint32), before["ub"].view(np.uint32))
+        assert B.bab_status(g.ctx) == 0
+    finally:
+        g.close()
