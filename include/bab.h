@@ -267,6 +267,78 @@ int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, cons
 int bab_status(bab_ctx *ctx, void *stream);
 
 /*
+ * ---------------------------------------------------------------------------
+ * Batched problems: P independent planning problems that share one network
+ * architecture (each with its own weights, x_0, goal, horizon and rho) are
+ * searched, bounded and branched together, one launch per kernel for all of
+ * them.  The paper plans one problem at a time; this is the same method
+ * (Algorithm 2 per problem) run over many problems at once.
+ *
+ * Layout: problem p's arrays are x0[p][s], goal[p][s], horizon[p] (device
+ * int, 1 <= horizon[p] <= max_horizon), rho[p] (device float, nullable: 0).
+ * Box row i belongs to problem prob[i] (device int[n]; nullable when P = 1)
+ * and stores its k * horizon[prob[i]] action coordinates first in a row of
+ * d_stride >= k * max_horizon floats; the remaining coordinates are carried
+ * along unchanged (set them to 0).  Problem indices and horizons outside
+ * their ranges are clamped so that every access stays in bounds.
+ * ---------------------------------------------------------------------------
+ */
+
+/* As bab_load_dynamics for n_problems parameter vectors stored back to back
+ * in params (host, n_problems x the packed size of one network).  The
+ * single-problem entry points use problem 0. */
+int bab_load_dynamics_batch(bab_ctx **out, int n_problems, int n_layers, const int *dims, const float *params,
+                            int state_dim, int action_dim, unsigned flags);
+
+/*
+ * bab_rollout for every row of every problem, FP32 on CUDA cores: per row
+ * `samples` uniform samples (the same counter RNG as bab_rollout, over the
+ * row's own k * H_p coordinates), ub[i], best_u[i] (coordinates beyond
+ * k * H_p are 0), and per problem the incumbent inc_val[p] (device double[P])
+ * / inc_u[p] (device float[P][d_stride]) re-scored in FP64 from the best row
+ * of that problem.
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_CUDA, BAB_ERR_OOM.
+ */
+int bab_rollout_batch(bab_ctx *ctx, const float *x0, const float *goal, const int *horizon, const float *rho,
+                      int max_horizon, int d_stride, const float *lo, const float *hi, const uint64_t *id,
+                      const int *prob, int n, const int *d_n, int samples, uint64_t seed, float *ub, float *best_u,
+                      double *inc_val, float *inc_u, void *stream);
+
+/*
+ * Sound lower bounds of every row (FP32, outward-rounded, margin
+ * subtracted): interval bounds, then CROWN with the adaptive slopes
+ * (alpha_steps = 0) or alpha-CROWN with alpha_steps projected Adam steps of
+ * learning rate lr keeping the best bound (as bab_alpha_optimize), one warp
+ * per row.  lb device float[n]; lb_ibp device float[n] (nullable): the
+ * interval bound of the cost.  Bit-identical, row by row, to bab_bound_ibp /
+ * bab_bound_crown / bab_alpha_optimize in FP32 on the row's own problem.
+ * Errors: as bab_bound_crown.
+ */
+int bab_bound_batch(bab_ctx *ctx, const float *x0, const float *goal, const int *horizon, const float *rho,
+                    int max_horizon, int d_stride, const float *lo, const float *hi, const int *prob, int n,
+                    const int *d_n, int alpha_steps, float lr, float *lb, float *lb_ibp, void *stream);
+
+/*
+ * bab_prune_branch applied to each problem's rows separately (its incumbent
+ * inc_val[p], its pick quota n_pick[p] (device int[P]), the common eta; the
+ * split uses only the problem's k * H_p coordinates), in one launch.  Output
+ * rows: the children of problem 0, of problem 1, ..., then the unpicked
+ * survivors of problem 0, of problem 1, ..., each in pool order; out_prob
+ * (device int[cap_out], nullable) receives each output row's problem.
+ * d_counts as bab_prune_branch (totals); d_pcounts (device int[P][2],
+ * nullable) receives each problem's picked and unpicked survivor counts.
+ * max_pick_total >= sum_p n_pick[p] and cap_out >= n + max_pick_total are
+ * required; rows that would land beyond cap_out are dropped and latch
+ * BAB_ERR_SHAPE in the device status.
+ */
+int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int max_horizon, const float *lo,
+                           const float *hi, const float *lb, const float *ub, const uint64_t *id, const int *prob,
+                           int n, const int *d_n, const double *inc_val, const int *n_pick, int max_pick_total,
+                           float eta, int split_rule, int cap_out, float *out_lo, float *out_hi, float *out_lb,
+                           float *out_ub, uint64_t *out_id, int *out_prob, uint8_t *keep, int *d_counts,
+                           int *d_pcounts, void *stream);
+
+/*
  * Launch variants (tile shapes) and their autotuner.  The paper has no
  * counterpart: these choose between equivalent launch configurations only;
  * no variant changes a result beyond floating-point summation order (the

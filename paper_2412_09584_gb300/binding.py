@@ -70,6 +70,13 @@ def load(path: str = LIB_PATH):
     L.bab_prune_branch.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _I, _P, _P, _P, _P, _P, _P, _P,
                                    _P]
     L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
+    L.bab_load_dynamics_batch.argtypes = [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _I,
+                                          _I, ctypes.c_uint]
+    L.bab_rollout_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _P, _P,
+                                    _P, _P, _P]
+    L.bab_bound_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _I, _P, _I, _F, _P, _P, _P]
+    L.bab_prune_branch_batch.argtypes = [_P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _F, _I, _I, _P,
+                                         _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.bab_set_variant.argtypes = [_P, _I, _I]
     L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
     L.bab_autotune.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _I, _I, _P]
@@ -233,4 +240,54 @@ def bab_autotune(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, alpha_ste
     rc = load().bab_autotune(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
                              _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), int(n),
                              int(samples), int(alpha_steps), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_load_dynamics_batch(dims, params, state_dim, action_dim, flags=0):
+    """Context for P problems of one architecture: params is [P][n_params] (host). Returns an opaque handle."""
+    L = load()
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    if p.ndim != 2:
+        raise ValueError("params must be [n_problems][n_params]")
+    dims_a = (_I * len(dims))(*[int(x) for x in dims])
+    out = _P()
+    rc = L.bab_load_dynamics_batch(ctypes.byref(out), p.shape[0], len(dims) - 1, dims_a,
+                                   p.ctypes.data_as(ctypes.POINTER(_F)), int(state_dim), int(action_dim), int(flags))
+    if rc != BAB_OK:
+        raise BabError(rc, "bab_load_dynamics_batch failed")
+    return out.value
+
+
+def bab_rollout_batch(ctx, x0, goal, horizon, rho, max_horizon, d_stride, lo, hi, ids, prob, n, samples, seed, ub,
+                      best_u=None, inc_val=None, inc_u=None, d_n=None, stream=None):
+    f32, i32 = torch.float32, torch.int32
+    rc = load().bab_rollout_batch(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), _ptr(horizon, i32, "horizon"),
+                                  _ptr(rho, f32, "rho"), int(max_horizon), int(d_stride), _ptr(lo, f32, "lo"),
+                                  _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), _ptr(prob, i32, "prob"), int(n),
+                                  _ptr(d_n, i32), int(samples), int(seed), _ptr(ub, f32, "ub"), _ptr(best_u, f32),
+                                  _ptr(inc_val, torch.float64), _ptr(inc_u, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_bound_batch(ctx, x0, goal, horizon, rho, max_horizon, d_stride, lo, hi, prob, n, lb, alpha_steps=0, lr=0.1,
+                    lb_ibp=None, d_n=None, stream=None):
+    f32, i32 = torch.float32, torch.int32
+    rc = load().bab_bound_batch(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), _ptr(horizon, i32, "horizon"),
+                                _ptr(rho, f32, "rho"), int(max_horizon), int(d_stride), _ptr(lo, f32, "lo"),
+                                _ptr(hi, f32, "hi"), _ptr(prob, i32, "prob"), int(n), _ptr(d_n, i32),
+                                int(alpha_steps), float(lr), _ptr(lb, f32, "lb"), _ptr(lb_ibp, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_prune_branch_batch(ctx, d_stride, horizon, max_horizon, lo, hi, lb, ub, ids, prob, n, inc_val, n_pick,
+                           max_pick_total, eta, cap_out, out_lo, out_hi, out_lb, out_ub, out_id, out_prob, keep,
+                           d_counts, d_pcounts=None, d_n=None, split_rule=SPLIT_WIDEST, stream=None):
+    f32, i32 = torch.float32, torch.int32
+    rc = load().bab_prune_branch_batch(
+        ctx, int(d_stride), _ptr(horizon, i32, "horizon"), int(max_horizon), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"),
+        _ptr(lb, f32, "lb"), _ptr(ub, f32, "ub"), _ptr(ids, torch.uint64, "id"), _ptr(prob, i32, "prob"), int(n),
+        _ptr(d_n, i32), _ptr(inc_val, torch.float64, "inc_val"), _ptr(n_pick, i32, "n_pick"), int(max_pick_total),
+        float(eta), int(split_rule), int(cap_out), _ptr(out_lo, f32), _ptr(out_hi, f32), _ptr(out_lb, f32),
+        _ptr(out_ub, f32), _ptr(out_id, torch.uint64), _ptr(out_prob, i32), _ptr(keep, torch.uint8),
+        _ptr(d_counts, i32, "d_counts"), _ptr(d_pcounts, i32), _stream(stream))
     _check(ctx, rc)

@@ -15,6 +15,7 @@ using namespace bab;
 struct bab_ctx {
     int device = 0;
     int num_sms = 1;
+    int n_problems = 1;
     int max_smem = 0;
     NetDesc net{};
     float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
@@ -220,6 +221,8 @@ BoundArgs make_bound_args(bab_ctx *c, const float *x0, const float *goal, int H,
     a.d = c->net.k * H;
     a.rho = rho;
     a.status = c->d_status;
+    a.batch.P = 1;
+    a.batch.Hmax = H;
     return a;
 }
 
@@ -246,11 +249,18 @@ extern "C" {
 
 int bab_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
-int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float *params, int state_dim, int action_dim,
-                      unsigned flags)
+}  // extern "C"
+
+namespace {
+
+// P problems of one architecture: params holds P packed parameter vectors back to back.  The tensor-core
+// images are built for problem 0 only (the batched calls run on CUDA cores).
+int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *params, int state_dim,
+              int action_dim, unsigned flags)
 {
     if (!out || !dims || !params) return BAB_ERR_INVALID_ARG;
     *out = nullptr;
+    if (P < 1 || P > (1 << 20)) return BAB_ERR_SHAPE;
     if (flags != 0) return BAB_ERR_INVALID_ARG;
     if (n_layers < 1 || n_layers > kMaxLayers) return BAB_ERR_SHAPE;
     if (state_dim < 1 || action_dim < 1 || dims[0] != state_dim + action_dim || dims[n_layers] != state_dim)
@@ -259,6 +269,7 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
         if (dims[l] < 1 || dims[l] > kMaxWidth) return BAB_ERR_SHAPE;
 
     bab_ctx *c = new bab_ctx();
+    c->n_problems = P;
     NetDesc &N = c->net;
     N.L = n_layers;
     N.s = state_dim;
@@ -286,22 +297,26 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
     N.raw_floats = raw;
     N.img_floats = img;
     for (int l = 1; l <= n_layers; ++l) N.gam[l] = gamma_fp32(pad4(dims[l]));
-    for (int i = 0; i < raw; ++i)
+    for (size_t i = 0; i < (size_t)P * raw; ++i)
         if (!std::isfinite(params[i])) {
             delete c;
             return BAB_ERR_NUMERIC;
         }
 
-    std::vector<float> fwd(img, 0.f), bwd(img, 0.f);
-    for (int l = 1; l <= n_layers; ++l) {
-        const int no = dims[l], ni = dims[l - 1], Kp = pad4(ni), Np = pad4(no);
-        const float *W = params + N.raw_w[l], *b = params + N.raw_b[l];
-        for (int q = 0; q < no; ++q)
-            for (int p = 0; p < ni; ++p) {
-                fwd[N.fwd_w[l] + p * Np + q] = W[q * ni + p];  // Wt [Kp][Np]
-                bwd[N.bwd_w[l] + q * Kp + p] = W[q * ni + p];  // W  [Np][Kp]
-            }
-        for (int q = 0; q < no; ++q) fwd[N.fwd_b[l] + q] = bwd[N.bwd_b[l] + q] = b[q];
+    std::vector<float> fwd((size_t)P * img, 0.f), bwd((size_t)P * img, 0.f);
+    for (int pr = 0; pr < P; ++pr) {
+        const float *prm = params + (size_t)pr * raw;
+        float *fw = fwd.data() + (size_t)pr * img, *bw = bwd.data() + (size_t)pr * img;
+        for (int l = 1; l <= n_layers; ++l) {
+            const int no = dims[l], ni = dims[l - 1], Kp = pad4(ni), Np = pad4(no);
+            const float *W = prm + N.raw_w[l], *b = prm + N.raw_b[l];
+            for (int q = 0; q < no; ++q)
+                for (int p = 0; p < ni; ++p) {
+                    fw[N.fwd_w[l] + p * Np + q] = W[q * ni + p];  // Wt [Kp][Np]
+                    bw[N.bwd_w[l] + q * Kp + p] = W[q * ni + p];  // W  [Np][Kp]
+                }
+            for (int q = 0; q < no; ++q) fw[N.fwd_b[l] + q] = bw[N.bwd_b[l] + q] = b[q];
+        }
     }
     std::vector<uint8_t> tc_img;
     std::vector<float> tc_bias;
@@ -318,13 +333,14 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tc, tc_img.data(), tc_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_tc_bias, tc_bias.data(), sizeof(float) * tc_bias.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_raw, sizeof(float) * raw);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_fwd, sizeof(float) * img);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_bwd, sizeof(float) * img);
+    const size_t nraw = (size_t)P * raw, nimg = (size_t)P * img;
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_raw, sizeof(float) * nraw);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_fwd, sizeof(float) * nimg);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bwd, sizeof(float) * nimg);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_raw, params, sizeof(float) * raw, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_fwd, fwd.data(), sizeof(float) * img, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_bwd, bwd.data(), sizeof(float) * img, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_raw, params, sizeof(float) * nraw, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_fwd, fwd.data(), sizeof(float) * nimg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_bwd, bwd.data(), sizeof(float) * nimg, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
         int code = e == cudaErrorMemoryAllocation ? BAB_ERR_OOM : BAB_ERR_CUDA;
@@ -334,6 +350,22 @@ int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float 
     }
     *out = c;
     return BAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bab_load_dynamics(bab_ctx **out, int n_layers, const int *dims, const float *params, int state_dim, int action_dim,
+                      unsigned flags)
+{
+    return load_impl(out, 1, n_layers, dims, params, state_dim, action_dim, flags);
+}
+
+int bab_load_dynamics_batch(bab_ctx **out, int n_problems, int n_layers, const int *dims, const float *params,
+                            int state_dim, int action_dim, unsigned flags)
+{
+    return load_impl(out, n_problems, n_layers, dims, params, state_dim, action_dim, flags);
 }
 
 int bab_destroy(bab_ctx *c)
@@ -387,6 +419,8 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     if (rc) return rc;
     RolloutArgs a{};
     a.net = c->net;
+    a.batch.P = 1;
+    a.batch.Hmax = H;
     a.fwd = c->d_fwd;
     a.raw = c->d_raw;
     a.x0 = x0;
@@ -662,9 +696,13 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
     if (n > 0 && (!lo || !hi || !lb || !ub || !id || !keep || !out_lo || !out_hi || !out_lb || !out_ub || !out_id))
         return fail(c, BAB_ERR_INVALID_ARG, "null array");
     if ((long long)cap_out < (long long)n + n_pick) return fail(c, BAB_ERR_SHAPE, "cap_out must be >= n + n_pick");
-    int rc = ensure_scratch(c, (size_t)(n > 0 ? n : 1) * sizeof(int) + 256);
+    int rc = ensure_scratch(c, (size_t)(n > 0 ? n : 1) * sizeof(int) + 1024);
     if (rc) return rc;
     BranchArgs a{};
+    a.batch.P = 1;
+    a.cap_out = cap_out;
+    a.eta = eta;
+    a.poff = reinterpret_cast<int *>(c->scratch) + ((n > 0 ? n : 1) + 63) / 64 * 64;
     a.d = d;
     a.n = n;
     a.d_n = d_n;
@@ -688,6 +726,184 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
     a.status = c->d_status;
     cudaError_t e = launch_prune_branch(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "prune/branch kernels");
+    return BAB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched problems (one launch per kernel for every problem of the context)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+int check_batch(bab_ctx *c, const float *x0, const float *goal, const int *horizon, const float *rho, int max_horizon,
+                int d_stride, const float *lo, const float *hi, const int *prob, int n)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!x0 || !goal || !horizon) return fail(c, BAB_ERR_INVALID_ARG, "x0, goal and horizon are required");
+    if (max_horizon < 1 || max_horizon > (1 << 20)) return fail(c, BAB_ERR_SHAPE, "max_horizon out of range");
+    if (n < 0) return fail(c, BAB_ERR_SHAPE, "n = %d < 0", n);
+    if ((long long)d_stride < (long long)c->net.k * max_horizon || d_stride > (1 << 24))
+        return fail(c, BAB_ERR_SHAPE, "d_stride must be >= action_dim * max_horizon");
+    if (n > 0 && (!lo || !hi)) return fail(c, BAB_ERR_INVALID_ARG, "lo and hi are required");
+    if (c->n_problems > 1 && n > 0 && !prob) return fail(c, BAB_ERR_INVALID_ARG, "prob is required");
+    (void)rho;
+    return BAB_OK;
+}
+
+BatchDesc make_batch(bab_ctx *c, const int *prob, const int *horizon, const float *rho, int max_horizon)
+{
+    BatchDesc b{};
+    b.prob = prob;
+    b.H = horizon;
+    b.rho = rho;
+    b.P = c->n_problems;
+    b.Hmax = max_horizon;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bab_rollout_batch(bab_ctx *c, const float *x0, const float *goal, const int *horizon, const float *rho,
+                      int max_horizon, int d_stride, const float *lo, const float *hi, const uint64_t *id,
+                      const int *prob, int n, const int *d_n, int samples, uint64_t seed, float *ub, float *best_u,
+                      double *inc_val, float *inc_u, void *stream)
+{
+    int rc = check_batch(c, x0, goal, horizon, rho, max_horizon, d_stride, lo, hi, prob, n);
+    if (rc) return rc;
+    if (samples < 1) return fail(c, BAB_ERR_SHAPE, "samples must be >= 1");
+    if (n > 0 && (!id || !ub)) return fail(c, BAB_ERR_INVALID_ARG, "id and ub are required");
+    if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
+    if (inc_val && !best_u) return fail(c, BAB_ERR_INVALID_ARG, "the incumbent update needs best_u");
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, (size_t)n * sizeof(unsigned long long) + 256);
+    if (rc) return rc;
+    RolloutArgs a{};
+    a.net = c->net;
+    a.batch = make_batch(c, prob, horizon, rho, max_horizon);
+    a.fwd = c->d_fwd;
+    a.raw = c->d_raw;
+    a.x0 = x0;
+    a.goal = goal;
+    a.lo = lo;
+    a.hi = hi;
+    a.id = id;
+    a.n = n;
+    a.d_n = d_n;
+    a.H = max_horizon;
+    a.M = samples;
+    a.d = d_stride;
+    a.rho = 0.f;
+    a.seed = seed;
+    a.keys = reinterpret_cast<unsigned long long *>(c->scratch);
+    a.ub = ub;
+    a.best_u = best_u;
+    a.inc_val = inc_val;
+    a.inc_u = inc_u;
+    a.status = c->d_status;
+    cudaError_t e = launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched rollout kernels");
+    return BAB_OK;
+}
+
+int bab_bound_batch(bab_ctx *c, const float *x0, const float *goal, const int *horizon, const float *rho,
+                    int max_horizon, int d_stride, const float *lo, const float *hi, const int *prob, int n,
+                    const int *d_n, int alpha_steps, float lr, float *lb, float *lb_ibp, void *stream)
+{
+    int rc = check_batch(c, x0, goal, horizon, rho, max_horizon, d_stride, lo, hi, prob, n);
+    if (rc) return rc;
+    if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
+    if (alpha_steps < 0 || alpha_steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "alpha_steps out of range");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
+    if (n == 0) return BAB_OK;
+    const NetDesc &N = c->net;
+    const size_t nh = (size_t)n * max_horizon * N.sumh, nx = (size_t)n * (max_horizon + 1) * N.s;
+    const size_t ns = (size_t)n * max_horizon * (N.sumh + N.s);
+    const size_t floats = 2 * nh + 2 * nx + ns + (alpha_steps > 0 ? 4 * nh : 0);
+    rc = ensure_scratch(c, floats * sizeof(float) + 16 * 256);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, max_horizon, 0.f, lo, hi, n, d_n);
+    a.d = d_stride;
+    a.batch = make_batch(c, prob, horizon, rho, max_horizon);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    a.pre_lo = cv.take<float>(nh);
+    a.pre_hi = cv.take<float>(nh);
+    a.x_lo = cv.take<float>(nx);
+    a.x_hi = cv.take<float>(nx);
+    a.S = cv.take<float>(ns);
+    a.lb_ibp = lb_ibp;
+    cudaError_t e = launch_ibp_warp(a, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched interval bounds");
+    float *al = nullptr, *m = nullptr, *v = nullptr;
+    if (alpha_steps > 0) {
+        al = cv.take<float>(nh);
+        m = cv.take<float>(nh);
+        v = cv.take<float>(nh);
+        a.A_pre = cv.take<float>(nh);
+    }
+    a.lb_best = lb;
+    e = launch_alpha_warp(a, alpha_steps, lr, al, m, v, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched bound kernel");
+    return BAB_OK;
+}
+
+int bab_prune_branch_batch(bab_ctx *c, int d_stride, const int *horizon, int max_horizon, const float *lo,
+                           const float *hi, const float *lb, const float *ub, const uint64_t *id, const int *prob,
+                           int n, const int *d_n, const double *inc_val, const int *n_pick, int max_pick_total,
+                           float eta, int split_rule, int cap_out, float *out_lo, float *out_hi, float *out_lb,
+                           float *out_ub, uint64_t *out_id, int *out_prob, uint8_t *keep, int *d_counts,
+                           int *d_pcounts, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    const int P = c->n_problems;
+    if (n < 0 || max_pick_total < 0 || max_horizon < 1) return fail(c, BAB_ERR_SHAPE, "bad n, max_pick_total or max_horizon");
+    if ((long long)d_stride < (long long)c->net.k * max_horizon) return fail(c, BAB_ERR_SHAPE, "d_stride too small");
+    if (!(eta >= 0.f && eta <= 1.f)) return fail(c, BAB_ERR_INVALID_ARG, "eta must be in [0, 1]");
+    if (split_rule != BAB_SPLIT_WIDEST) return fail(c, BAB_ERR_UNSUPPORTED, "split rule %d", split_rule);
+    if (!inc_val || !d_counts || !n_pick || !horizon) return fail(c, BAB_ERR_INVALID_ARG, "inc_val, n_pick, horizon and d_counts are required");
+    if (n > 0 && (!lo || !hi || !lb || !ub || !id || !keep || !out_lo || !out_hi || !out_lb || !out_ub || !out_id ||
+                  (P > 1 && !prob)))
+        return fail(c, BAB_ERR_INVALID_ARG, "null array");
+    if ((long long)cap_out < (long long)n + max_pick_total)
+        return fail(c, BAB_ERR_SHAPE, "cap_out must be >= n + max_pick_total");
+    const size_t nrow = (size_t)(n > 0 ? n : 1);
+    const size_t dest_ints = (nrow + 63) / 64 * 64;
+    int rc = ensure_scratch(c, (dest_ints + 4 * (size_t)P) * sizeof(int) + 1024);
+    if (rc) return rc;
+    BranchArgs a{};
+    a.batch = make_batch(c, prob, horizon, nullptr, max_horizon);
+    a.k = c->net.k;
+    a.d = d_stride;
+    a.n = n;
+    a.d_n = d_n;
+    a.lo = lo;
+    a.hi = hi;
+    a.lb = lb;
+    a.ub = ub;
+    a.id = id;
+    a.inc_val = inc_val;
+    a.n_pick_dev = n_pick;
+    a.eta = eta;
+    a.cap_out = cap_out;
+    a.out_lo = out_lo;
+    a.out_hi = out_hi;
+    a.out_lb = out_lb;
+    a.out_ub = out_ub;
+    a.out_id = out_id;
+    a.out_prob = out_prob;
+    a.keep = keep;
+    a.d_counts = d_counts;
+    a.dest = reinterpret_cast<int *>(c->scratch);
+    a.poff = a.dest + dest_ints;
+    a.pcounts = d_pcounts ? d_pcounts : a.poff + 2 * P;
+    a.status = c->d_status;
+    cudaError_t e = launch_prune_branch(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched prune/branch kernels");
     return BAB_OK;
 }
 

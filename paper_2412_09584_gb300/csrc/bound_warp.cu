@@ -1,5 +1,6 @@
-// alpha_warp.cu -- alpha-CROWN (Lemma 1's free lower slopes, optimised by
-// projected Adam on the bound of Theorems 1-2) with one warp per box.
+// bound_warp.cu -- interval bounds and alpha-CROWN (Lemma 1's free lower
+// slopes, optimised by projected Adam on the bound of Theorems 1-2) with one
+// warp per box; every box may belong to a different problem (BatchDesc).
 //
 // Lane q of a box's warp owns neurons q, q + 32, ... of every layer: the
 // coefficient vector of the backward pass and the activations of the adjoint
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const NetDesc &N = a.net;
-    const int s = N.s, k = N.k, L = N.L, H = a.H, d = a.d, sumh = N.sumh, sw = sumh + s, d4 = pad4(d);
+    const int s = N.s, k = N.k, L = N.L, Hm = a.batch.Hmax, d = a.d, sumh = N.sumh, sw = sumh + s, d4 = pad4(d);
     const float *fwd = a.fwd, *bwd = a.bwd;
     float *p = sm;
     if (WSMEM) {
@@ -89,21 +90,33 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     __syncthreads();
 
     const int nlive = live_count(a.n, a.d_n);
-    const size_t hs = (size_t)H * sumh;
+    const size_t hs = (size_t)Hm * sumh;  // per-box stride of the [H][sumh] arrays
+    const bool opt = steps > 0;           // steps == 0: one bound with the adaptive slopes, no adjoint
     for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {
-        const float *pl = a.pre_lo + box * hs, *ph = a.pre_hi + box * hs;
-        const float *S = a.S + (size_t)box * H * sw;
-        const float *xlo = a.x_lo + (size_t)box * (H + 1) * s, *xhi = a.x_hi + (size_t)box * (H + 1) * s;
-        const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
-        float *al = alpha_g + box * hs, *am = m_g + box * hs, *av = v_g + box * hs, *Ap = a.A_pre + box * hs;
-        for (size_t i = lane; i < hs; i += 32) {
-            al[i] = (ph[i] >= -pl[i]) ? 1.f : 0.f;  // adaptive initial slopes
-            am[i] = 0.f;
-            av[i] = 0.f;
+        // the box's problem: weights, start, goal, horizon and rho
+        const int pb = row_problem(a.batch, box);
+        if (!WSMEM) {
+            fwd = a.fwd + (size_t)pb * N.img_floats;
+            bwd = a.bwd + (size_t)pb * N.img_floats;
         }
+        const float *x0 = a.x0 + (size_t)pb * s, *goal = a.goal + (size_t)pb * s;
+        const int H = problem_H(a.batch, pb, a.H), dp = k * H;
+        const float rho = problem_rho(a.batch, pb, a.rho);
+        const float *pl = a.pre_lo + box * hs, *ph = a.pre_hi + box * hs;
+        const float *S = a.S + (size_t)box * Hm * sw;
+        const float *xlo = a.x_lo + (size_t)box * (Hm + 1) * s, *xhi = a.x_hi + (size_t)box * (Hm + 1) * s;
+        const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
+        float *al = opt ? alpha_g + box * hs : nullptr, *am = opt ? m_g + box * hs : nullptr;
+        float *av = opt ? v_g + box * hs : nullptr, *Ap = opt ? a.A_pre + box * hs : nullptr;
+        if (opt)
+            for (size_t i = lane; i < (size_t)H * sumh; i += 32) {
+                al[i] = (ph[i] >= -pl[i]) ? 1.f : 0.f;  // adaptive initial slopes
+                am[i] = 0.f;
+                av[i] = 0.f;
+            }
         __syncwarp();
         float lb_best = -INFINITY;
-        for (int step = 1; step <= steps; ++step) {
+        for (int step = 1; step <= (opt ? steps : 1); ++step) {
             // ------------------------------ bound (Theorems 1-2) ------------------------------
             float A[P], lam[P], tmp[P];
             float cst, mg = 0.f;
@@ -114,7 +127,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                     const int i = lane + 32 * q;
                     float aa = 0.f;
                     if (i < s) {
-                        const float g = a.goal[i];
+                        const float g = goal[i];
                         const float Ls = __fsub_rd(xlo[(size_t)H * s + i], g), Us = __fsub_ru(xhi[(size_t)H * s + i], g);
                         const float m = 0.5f * (Ls + Us);
                         aa = 2.f * m;
@@ -158,9 +171,13 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                             const size_t idx = (size_t)t * sumh + N.hoff[l] + j;
                             const float zl = pl[idx], zu = ph[idx];
                             const float Av = A[q];
-                            Ap[idx] = Av;
                             float D, ci;
-                            relax_select(zl, zu, Av, al[idx], true, D, ci);
+                            if (opt) {
+                                Ap[idx] = Av;
+                                relax_select(zl, zu, Av, al[idx], true, D, ci);
+                            } else {
+                                relax_select(zl, zu, Av, 0.f, false, D, ci);
+                            }
                             const float Apj = Av * D;
                             A[q] = Apj;
                             c = __fmaf_rd(Av, ci, c);
@@ -188,7 +205,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                         const float Ax = A[q], lo_ = lam[q];
                         float aa = 0.f, B;
                         if (t >= 1) {
-                            const float g = a.goal[i];
+                            const float g = goal[i];
                             const float xl = xlo[(size_t)t * s + i], xu = xhi[(size_t)t * s + i];
                             const float Ls = __fsub_rd(xl, g), Us = __fsub_ru(xu, g);
                             const float m = 0.5f * (Ls + Us);
@@ -196,7 +213,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                             c = __fadd_rd(c, __fmaf_rd(-aa, g, -__fmul_ru(m, m)));
                             B = fmaxf(fabsf(xl), fabsf(xu));
                         } else {
-                            B = fabsf(a.x0[i]);
+                            B = fabsf(x0[i]);
                         }
                         lam[q] = (lo_ + Ax) + aa;
                         const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
@@ -216,23 +233,23 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
 #pragma unroll
                 for (int q = 0; q < P; ++q) {
                     const int i = lane + 32 * q;
-                    if (i < s) c = __fmaf_rd(lam[q], a.x0[i], c);
+                    if (i < s) c = __fmaf_rd(lam[q], x0[i], c);
                 }
                 c = __fadd_rd(cst, warp_sum_rd(c));
-                for (int j = lane; j < d; j += 32) {
+                for (int j = lane; j < dp; j += 32) {
                     const float m_ = mu[j];
                     const float lo = blo[j], hi = bhi[j];
                     float u_s, vj;
-                    if (a.rho > 0.f) {
-                        const float uc = -m_ / (2.f * a.rho);
+                    if (rho > 0.f) {
+                        const float uc = -m_ / (2.f * rho);
                         if (uc >= lo && uc <= hi) {
                             u_s = uc;
-                            vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * a.rho);
+                            vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * rho);
                         } else {
                             u_s = uc < lo ? lo : hi;
-                            vj = __fmaf_rd(m_, u_s, __fmul_rd(a.rho, __fmul_rd(u_s, u_s)));
+                            vj = __fmaf_rd(m_, u_s, __fmul_rd(rho, __fmul_rd(u_s, u_s)));
                             const float du = __fmul_ru(kTwoU, fabsf(uc));
-                            e = __fmaf_ru(__fmul_ru(a.rho, du), du, e);
+                            e = __fmaf_ru(__fmul_ru(rho, du), du, e);
                         }
                     } else {
                         u_s = m_ >= 0.f ? lo : hi;
@@ -249,6 +266,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
             }
             lb_best = fmaxf(lb_best, lbv);
             __syncwarp();
+            if (!opt) break;
             // ------------------ adjoint: relaxed network forward from x_0 and u*, then Adam ------------------
             AdamStep ast;
             ast.lr = lr;
@@ -263,7 +281,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
 #pragma unroll
             for (int q = 0; q < P; ++q) {
                 const int i = lane + 32 * q;
-                x[q] = i < s ? a.x0[i] : 0.f;
+                x[q] = i < s ? x0[i] : 0.f;
             }
             for (int t = 0; t < H; ++t) {
                 float Z[P];
@@ -321,7 +339,7 @@ static cudaError_t launch_warp_variant(const BoundArgs &a, int steps, float lr, 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t per_warp = 2 * (size_t)pad4(a.d) * kWarps * sizeof(float);
     const size_t with_img = per_warp + 2 * (size_t)a.net.img_floats * sizeof(float);
-    const bool wsmem = with_img + 1024 <= (size_t)max_optin;
+    const bool wsmem = a.batch.P <= 1 && with_img + 1024 <= (size_t)max_optin;
     const size_t smem = wsmem ? with_img : per_warp;
     if (smem + 1024 > (size_t)max_optin) return cudaErrorInvalidConfiguration;
     auto kern = wsmem ? k_alpha_warp<P, true> : k_alpha_warp<P, false>;
@@ -339,19 +357,194 @@ static cudaError_t launch_warp_variant(const BoundArgs &a, int steps, float lr, 
     return cudaGetLastError();
 }
 
+
+// Interval bound propagation (outward-rounded FP32) through the H-step unrolled
+// network, one warp per box: lane q holds the interval of inputs and outputs
+// q, q + 32, ...; per output the three directed-rounding sums (lower, upper,
+// and S = sum_j |W_kj| max|a_j|) run over the inputs in order from the bias, as
+// in k_ibp, so the bounds are bit-identical to it.  Writes the pre-activation
+// bounds, the state intervals, S and (nullable) the interval bound of the cost.
+template <int P, bool WSMEM>
+__global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1)) k_ibp_warp(BoundArgs a)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, L = N.L, Hm = a.batch.Hmax, d = a.d, sumh = N.sumh, sw = sumh + s;
+    const float *fwd = a.fwd;
+    if (WSMEM) {
+        for (int i = threadIdx.x; i < N.img_floats / 4; i += blockDim.x)
+            smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
+        fwd = sm;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nlive = live_count(a.n, a.d_n);
+    for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {
+        const int pb = row_problem(a.batch, box);
+        if (!WSMEM) fwd = a.fwd + (size_t)pb * N.img_floats;
+        const float *x0 = a.x0 + (size_t)pb * s, *goal = a.goal + (size_t)pb * s;
+        const int H = problem_H(a.batch, pb, a.H);
+        const float rho = problem_rho(a.batch, pb, a.rho);
+        const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
+        float *pl = a.pre_lo + (size_t)box * Hm * sumh, *ph = a.pre_hi + (size_t)box * Hm * sumh;
+        float *S = a.S + (size_t)box * Hm * sw;
+        float *xlo = a.x_lo + (size_t)box * (Hm + 1) * s, *xhi = a.x_hi + (size_t)box * (Hm + 1) * s;
+        float xl[P], xu[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int i = lane + 32 * q;
+            xl[q] = xu[q] = i < s ? x0[i] : 0.f;
+            if (i < s) {
+                xlo[i] = x0[i];
+                xhi[i] = x0[i];
+            }
+        }
+        float lbacc = 0.f;
+        for (int t = 0; t < H; ++t) {
+            float zl[P], zu[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int c = lane + 32 * q;
+                zl[q] = c < s ? xl[q] : (c < s + k ? blo[t * k + (c - s)] : 0.f);
+                zu[q] = c < s ? xu[q] : (c < s + k ? bhi[t * k + (c - s)] : 0.f);
+            }
+            if (rho > 0.f) {
+                float v = 0.f;
+                for (int j = lane; j < k; j += 32) v = __fadd_rd(v, sq_min_rd(blo[t * k + j], bhi[t * k + j]));
+                v = warp_sum_rd(v);
+                lbacc = __fadd_rd(lbacc, __fmul_rd(rho, v));
+            }
+            for (int l = 1; l <= L; ++l) {
+                const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]), dl = N.dims[l];
+                const float *W = fwd + N.fwd_w[l], *bias = fwd + N.fwd_b[l];
+                float al_[P], ah_[P], as_[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int j = lane + 32 * q;
+                    const float bj = j < Np ? bias[j] : 0.f;
+                    al_[q] = ah_[q] = bj;
+                    as_[q] = 0.f;
+                }
+                const float *Wk = W + lane;
+#pragma unroll
+                for (int pk = 0; pk < P; ++pk) {
+                    if (32 * pk >= Kp) break;
+                    const int kn = min(32, Kp - 32 * pk);
+                    for (int kl = 0; kl < kn; ++kl) {
+                        const float il = __shfl_sync(0xFFFFFFFFu, zl[pk], kl);
+                        const float ih = __shfl_sync(0xFFFFFFFFu, zu[pk], kl);
+                        const float am = fmaxf(fabsf(il), fabsf(ih));
+#pragma unroll
+                        for (int q = 0; q < P; ++q) {
+                            if (lane + 32 * q < Np) {
+                                const float w = Wk[32 * q];
+                                const bool pos = w >= 0.f;
+                                al_[q] = __fmaf_rd(w, pos ? il : ih, al_[q]);
+                                ah_[q] = __fmaf_ru(w, pos ? ih : il, ah_[q]);
+                                as_[q] = __fmaf_ru(fabsf(w), am, as_[q]);
+                            }
+                        }
+                        Wk += Np;
+                    }
+                }
+                const int soff = (l < L) ? N.hoff[l] : sumh;
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int j = lane + 32 * q;
+                    if (j < dl) {
+                        S[(size_t)t * sw + soff + j] = as_[q];
+                        if (l < L) {
+                            pl[(size_t)t * sumh + N.hoff[l] + j] = al_[q];
+                            ph[(size_t)t * sumh + N.hoff[l] + j] = ah_[q];
+                        }
+                    }
+                    if (l < L && j < dl) {
+                        zl[q] = fmaxf(al_[q], 0.f);
+                        zu[q] = fmaxf(ah_[q], 0.f);
+                    } else {
+                        zl[q] = al_[q];
+                        zu[q] = ah_[q];
+                    }
+                }
+            }
+            // x_{t+1} in [x_t] + [z_L]; interval bound of ||x_{t+1} - g||^2
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int i = lane + 32 * q;
+                if (i < s) {
+                    const float nl = __fadd_rd(xl[q], zl[q]), nh = __fadd_ru(xu[q], zu[q]);
+                    xl[q] = nl;
+                    xu[q] = nh;
+                    xlo[(size_t)(t + 1) * s + i] = nl;
+                    xhi[(size_t)(t + 1) * s + i] = nh;
+                    const float g = goal[i];
+                    v = __fadd_rd(v, sq_min_rd(__fsub_rd(nl, g), __fsub_ru(nh, g)));
+                }
+            }
+            v = warp_sum_rd(v);
+            lbacc = __fadd_rd(lbacc, v);
+        }
+        if (a.lb_ibp && lane == 0) a.lb_ibp[box] = lbacc;
+    }
+}
+
+template <int P>
+static cudaError_t launch_ibp_variant(const BoundArgs &a, cudaStream_t st)
+{
+    int dev, max_optin = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t img = (size_t)a.net.img_floats * sizeof(float);
+    const bool wsmem = a.batch.P <= 1 && img + 1024 <= (size_t)max_optin;
+    const size_t smem = wsmem ? img : 0;
+    auto kern = wsmem ? k_ibp_warp<P, true> : k_ibp_warp<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int need = (a.n + kWarps - 1) / kWarps;
+    const int grid = need < nsm * occ ? need : nsm * occ;
+    kern<<<grid, kWarps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static int lanes_needed(const NetDesc &N)
+{
+    int maxw = 0;
+    for (int l = 0; l <= N.L; ++l) maxw = N.dims[l] > maxw ? N.dims[l] : maxw;
+    // every layer's width and the input row [x | u] must fit the lanes' slots
+    const int need = pad4(maxw) > pad4(N.s + N.k) ? pad4(maxw) : pad4(N.s + N.k);
+    return need <= 32 ? 1 : need <= 64 ? 2 : need <= 128 ? 4 : need <= 256 ? 8 : 0;
+}
+
+cudaError_t launch_ibp_warp(const BoundArgs &a, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    switch (lanes_needed(a.net)) {
+        case 1: return launch_ibp_variant<1>(a, st);
+        case 2: return launch_ibp_variant<2>(a, st);
+        case 4: return launch_ibp_variant<4>(a, st);
+        case 8: return launch_ibp_variant<8>(a, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
 cudaError_t launch_alpha_warp(const BoundArgs &a, int steps, float lr, float *alpha, float *m, float *v,
                               cudaStream_t st)
 {
     if (a.n <= 0) return cudaSuccess;
-    int maxw = 0;
-    for (int l = 0; l <= a.net.L; ++l) maxw = a.net.dims[l] > maxw ? a.net.dims[l] : maxw;
-    // every layer's width and the input row [x | u] must fit the lanes' slots
-    const int need = pad4(maxw) > pad4(a.net.s + a.net.k) ? pad4(maxw) : pad4(a.net.s + a.net.k);
-    if (need <= 32) return launch_warp_variant<1>(a, steps, lr, alpha, m, v, st);
-    if (need <= 64) return launch_warp_variant<2>(a, steps, lr, alpha, m, v, st);
-    if (need <= 128) return launch_warp_variant<4>(a, steps, lr, alpha, m, v, st);
-    if (need <= 256) return launch_warp_variant<8>(a, steps, lr, alpha, m, v, st);
-    return cudaErrorInvalidConfiguration;
+    switch (lanes_needed(a.net)) {
+        case 1: return launch_warp_variant<1>(a, steps, lr, alpha, m, v, st);
+        case 2: return launch_warp_variant<2>(a, steps, lr, alpha, m, v, st);
+        case 4: return launch_warp_variant<4>(a, steps, lr, alpha, m, v, st);
+        case 8: return launch_warp_variant<8>(a, steps, lr, alpha, m, v, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
 }
 
 }  // namespace bab

@@ -116,12 +116,23 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
     __shared__ int wsum[2][kPlanThreads / 32];
     __shared__ int red[kPlanThreads / 32];
     const int n = live_count(a.n, a.d_n);
-    const double inc = *a.inc_val;
+    // this CTA's problem and its rows
+    const int pb = blockIdx.x;
+    const BatchDesc &B = a.batch;
+    auto mine = [&](int i) { return B.prob == nullptr || row_problem(B, i) == pb; };
+    const double inc = a.inc_val[pb];
+    int n_pick = a.n_pick, n1 = a.n1;
+    if (a.n_pick_dev) {
+        n_pick = a.n_pick_dev[pb] < 0 ? 0 : a.n_pick_dev[pb];
+        n1 = (int)ceil((double)a.eta * n_pick);
+        n1 = n1 > n_pick ? n_pick : n1;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     // prune (strict, in FP64; a NaN bound is kept and latched as BAB_ERR_NUMERIC)
     int cnt = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (!mine(i)) continue;
         const float lbi = a.lb[i];
         if (lbi != lbi) set_status(a.status, BAB_ERR_NUMERIC);
         const uint8_t k = !((double)lbi > inc);
@@ -135,19 +146,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
     for (int w = 0; w < kPlanThreads / 32; ++w) ns += red[w];
     __syncthreads();
 
-    const bool all = ns <= a.n_pick;
+    const bool all = ns <= n_pick;
     Thresh T1, T2;
     T1.none = T2.none = true;
     if (!all) {
         const uint8_t *keep = a.keep;
-        T1 = radix_select(n, a.ub, a.id, [&](int i) { return keep[i] != 0; }, a.n1, hist, &sh_pk, &sh_pid, &sh_rem,
-                          &sh_done);
+        T1 = radix_select(n, a.ub, a.id, [&](int i) { return mine(i) && keep[i] != 0; }, n1, hist, &sh_pk, &sh_pid,
+                          &sh_rem, &sh_done);
         const float *ub = a.ub;
         const uint64_t *ids = a.id;
         T2 = radix_select(
             n, a.lb, a.id,
-            [&](int i) { return keep[i] != 0 && !le_thresh(float_order(ub[i]), ids[i], T1); }, a.n_pick - a.n1, hist,
-            &sh_pk, &sh_pid, &sh_rem, &sh_done);
+            [&](int i) { return mine(i) && keep[i] != 0 && !le_thresh(float_order(ub[i]), ids[i], T1); },
+            n_pick - n1, hist, &sh_pk, &sh_pid, &sh_rem, &sh_done);
     }
 
     // stable ranks of picked and unpicked survivors
@@ -156,7 +167,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
     for (int c0 = 0; c0 < n; c0 += blockDim.x) {
         const int i = c0 + threadIdx.x;
         bool kp = false, pk = false;
-        if (i < n) {
+        const bool own = i < n && mine(i);
+        if (own) {
             kp = a.keep[i] != 0;
             pk = kp && (all || le_thresh(float_order(a.ub[i]), a.id[i], T1) ||
                         le_thresh(float_order(a.lb[i]), a.id[i], T2));
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
             tp += wsum[0][w];
             tr += wsum[1][w];
         }
-        if (i < n) {
+        if (own) {
             if (pk) a.dest[i] = (base_p + op + __popc(bp & lt)) | kPickFlag;
             else if (rs) a.dest[i] = base_r + orr + __popc(br & lt);
             else a.dest[i] = -1;
@@ -187,10 +199,44 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        a.d_counts[0] = 2 * base_p;
-        a.d_counts[1] = base_r;
-        a.d_counts[2] = 2 * base_p + base_r;
+        if (gridDim.x == 1) {
+            a.d_counts[0] = 2 * base_p;
+            a.d_counts[1] = base_r;
+            a.d_counts[2] = 2 * base_p + base_r;
+            a.poff[0] = 0;
+            a.poff[1] = 2 * base_p;
+            if (a.pcounts) {
+                a.pcounts[0] = base_p;
+                a.pcounts[1] = base_r;
+            }
+        } else {
+            a.pcounts[2 * pb] = base_p;
+            a.pcounts[2 * pb + 1] = base_r;
+        }
     }
+}
+
+// Several problems: output offsets of each problem's children and unpicked rows, and the totals.
+__global__ void k_branch_offsets(BranchArgs a)
+{
+    if (threadIdx.x != 0) return;
+    const int P = a.batch.P;
+    long long tp = 0, tr = 0;
+    for (int p = 0; p < P; ++p) {
+        tp += a.pcounts[2 * p];
+        tr += a.pcounts[2 * p + 1];
+    }
+    long long cp = 0, cr = 2 * tp;
+    for (int p = 0; p < P; ++p) {
+        a.poff[2 * p] = (int)cp;
+        a.poff[2 * p + 1] = (int)cr;
+        cp += 2 * a.pcounts[2 * p];
+        cr += a.pcounts[2 * p + 1];
+    }
+    if (2 * tp + tr > a.cap_out) set_status(a.status, BAB_ERR_SHAPE);  // rows beyond cap_out are dropped
+    a.d_counts[0] = (int)(2 * tp);
+    a.d_counts[1] = (int)tr;
+    a.d_counts[2] = (int)(2 * tp + tr);
 }
 
 __global__ void k_branch_write(BranchArgs a)
@@ -202,10 +248,14 @@ __global__ void k_branch_write(BranchArgs a)
     const int dst = a.dest[row];
     if (dst < 0) return;
     const int d = a.d;
+    const int pb = row_problem(a.batch, row);
+    const int dp = a.batch.H ? a.k * problem_H(a.batch, pb, 0) : d;  // coordinates the problem uses
     const float *lo = a.lo + (size_t)row * d, *hi = a.hi + (size_t)row * d;
     const uint64_t id = a.id[row];
     if (!(dst & kPickFlag)) {
-        const size_t o = (size_t)a.d_counts[0] + dst;
+        const size_t o = (size_t)a.poff[2 * pb + 1] + dst;
+        if (o >= (size_t)a.cap_out) return;
+        if (a.out_prob && lane == 0) a.out_prob[o] = pb;
         for (int j = lane; j < d; j += 32) {
             a.out_lo[o * d + j] = lo[j];
             a.out_hi[o * d + j] = hi[j];
@@ -220,7 +270,7 @@ __global__ void k_branch_write(BranchArgs a)
     // widest coordinate, lowest index on ties
     float wb = -1.f;
     int jb = 0x7FFFFFFF;
-    for (int j = lane; j < d; j += 32) {
+    for (int j = lane; j < dp; j += 32) {
         const float w = __fsub_rn(hi[j], lo[j]);
         if (w > wb) {
             wb = w;
@@ -235,8 +285,11 @@ __global__ void k_branch_write(BranchArgs a)
             jb = j2;
         }
     }
+    if (jb >= dp) jb = 0;  // a problem without coordinates (H_p = 0) splits nothing meaningful
     const float mid = __fmul_rn(0.5f, __fadd_rn(lo[jb], hi[jb]));
-    const size_t o0 = 2 * (size_t)(dst & ~kPickFlag);
+    const size_t o0 = (size_t)a.poff[2 * pb] + 2 * (size_t)(dst & ~kPickFlag);
+    if (o0 + 1 >= (size_t)a.cap_out) return;
+    if (a.out_prob && lane == 0) a.out_prob[o0] = a.out_prob[o0 + 1] = pb;
     for (int j = lane; j < d; j += 32) {
         const float l = lo[j], h = hi[j];
         a.out_lo[o0 * d + j] = l;
@@ -255,7 +308,9 @@ __global__ void k_branch_write(BranchArgs a)
 
 cudaError_t launch_prune_branch(const BranchArgs &a, cudaStream_t st)
 {
-    k_branch_plan<<<1, kPlanThreads, 0, st>>>(a);
+    const int P = a.batch.P > 1 ? a.batch.P : 1;
+    k_branch_plan<<<P, kPlanThreads, 0, st>>>(a);
+    if (P > 1) k_branch_offsets<<<1, 32, 0, st>>>(a);
     if (a.n > 0) k_branch_write<<<(a.n + 7) / 8, 256, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -6,8 +6,37 @@
 
 namespace bab {
 
+// Many independent problems of one architecture in one launch.  Problem p has its own weights (images at
+// p * img_floats / raw at p * raw_floats), x0 and goal (at p * s), horizon and rho; row i of the box arrays
+// belongs to problem prob[i], uses the first k * H_p of its `d` (row stride) coordinates, and owns Hmax
+// steps of every per-step array.  P = 1 with prob = H = rho = null is the single-problem case.
+struct BatchDesc {
+    const int *prob;   // [n] (nullable: every row is problem 0)
+    const int *H;      // [P] (nullable: the call's horizon)
+    const float *rho;  // [P] (nullable: the call's rho)
+    int P;
+    int Hmax;
+};
+
+// Out-of-range problem indices and horizons are clamped (to [0, P) and [0, Hmax]) so that every access
+// stays inside the caller's arrays.
+__device__ __forceinline__ int row_problem(const BatchDesc &b, int row)
+{
+    if (!b.prob) return 0;
+    const int p = b.prob[row];
+    return p < 0 ? 0 : (p >= b.P ? b.P - 1 : p);
+}
+__device__ __forceinline__ int problem_H(const BatchDesc &b, int p, int H)
+{
+    if (!b.H) return H;
+    const int h = b.H[p];
+    return h < 0 ? 0 : (h > b.Hmax ? b.Hmax : h);
+}
+__device__ __forceinline__ float problem_rho(const BatchDesc &b, int p, float rho) { return b.rho ? b.rho[p] : rho; }
+
 struct RolloutArgs {
     NetDesc net;
+    BatchDesc batch;
     const float *fwd;   // forward image (device)
     const float *raw;   // raw parameters (device), for the FP64 re-score
     const float *x0, *goal, *lo, *hi;
@@ -31,6 +60,7 @@ struct RolloutArgs {
 
 struct BoundArgs {
     NetDesc net;
+    BatchDesc batch;
     const float *fwd, *bwd;
     const float *x0, *goal, *lo, *hi;
     int n;
@@ -174,7 +204,10 @@ cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
 // the whole alpha optimisation of a tile of boxes in one CTA (needs the interval bounds of launch_ibp)
 cudaError_t launch_alpha_fused(const BoundArgs &a, int steps, float lr, float *alpha_out, int variant, cudaStream_t st);
-// the whole alpha optimisation with one warp per box; alpha (written), m, v: [n][H][sumh] device arrays
+// interval bounds with one warp per box (any problem of the batch)
+cudaError_t launch_ibp_warp(const BoundArgs &a, cudaStream_t st);
+// the whole alpha optimisation with one warp per box; alpha (written), m, v: [n][Hmax][sumh] device arrays;
+// steps == 0: one bound with the adaptive slopes (alpha, m, v unused)
 cudaError_t launch_alpha_warp(const BoundArgs &a, int steps, float lr, float *alpha, float *m, float *v,
                               cudaStream_t st);
 void fill_adam_table(AdamTable &tab);
@@ -189,7 +222,7 @@ struct BranchArgs {
     const int *d_n;
     const float *lo, *hi, *lb, *ub;
     const uint64_t *id;
-    const double *inc_val;
+    const double *inc_val;   // [P]
     int n_pick;
     int n1;  // ceil(eta * n_pick), clamped to n_pick
     float *out_lo, *out_hi, *out_lb, *out_ub;
@@ -198,6 +231,16 @@ struct BranchArgs {
     int *d_counts;
     int *dest;     // [n] scratch: destination code per row
     int *status;
+    // several problems: one plan CTA per problem, output grouped by problem (children of every problem,
+    // then the unpicked survivors of every problem)
+    BatchDesc batch;
+    int k;                   // action dimension: problem p splits only its first k * H_p coordinates
+    const int *n_pick_dev;   // [P] per-problem pick quota (nullable: n_pick, n1)
+    float eta;
+    int cap_out;
+    int *pcounts;            // [P][2] picked and unpicked survivors per problem
+    int *poff;               // [P][2] first output row of the problem's children and of its unpicked rows
+    int *out_prob;           // [cap_out] (nullable)
 };
 cudaError_t launch_prune_branch(const BranchArgs &a, cudaStream_t st);
 

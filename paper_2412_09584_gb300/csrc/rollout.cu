@@ -41,7 +41,6 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
     float *cost = p; p += R;
     float *goal = p; p += pad4(s);
     __shared__ unsigned long long red[NT / 32];
-    for (int i = threadIdx.x; i < s; i += NT) goal[i] = a.goal[i];
 
     const int nlive = live_count(a.n, a.d_n);
     const int tpb = (a.M + R - 1) / R;
@@ -52,16 +51,23 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int box = (int)(tile / tpb);
         const int m0 = (int)(tile % tpb) * R;
+        // the box's problem: its weights, start, goal, horizon and rho
+        const int pb = row_problem(a.batch, box);
+        if (!WSMEM) img = a.fwd + (size_t)pb * N.img_floats;
+        const int Hb = problem_H(a.batch, pb, a.H), db = k * Hb;
+        const float rho = problem_rho(a.batch, pb, a.rho);
+        const float *x0 = a.x0 + (size_t)pb * s;
         __syncthreads();  // previous tile fully consumed
-        for (int j = threadIdx.x; j < d; j += NT) {
+        for (int i = threadIdx.x; i < s; i += NT) goal[i] = a.goal[(size_t)pb * s + i];
+        for (int j = threadIdx.x; j < db; j += NT) {
             blo[j] = a.lo[(size_t)box * d + j];
             bhi[j] = a.hi[(size_t)box * d + j];
         }
-        for (int i = threadIdx.x; i < R * s; i += NT) xs[(i / s) * pad4(s) + i % s] = a.x0[i % s];
+        for (int i = threadIdx.x; i < R * s; i += NT) xs[(i / s) * pad4(s) + i % s] = x0[i % s];
         for (int r = threadIdx.x; r < R; r += NT) cost[r] = 0.f;
         const uint64_t hb = box_hash(a.seed, a.id[box]);
         __syncthreads();
-        for (int t = 0; t < a.H; ++t) {
+        for (int t = 0; t < Hb; ++t) {
             // input rows [x_t | u_t | 0]
             for (int i = threadIdx.x; i < R * Kp1; i += NT) {
                 const int r = i / Kp1, c = i % Kp1;
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
                 }
                 for (int j = lane; j < k; j += 32) {
                     const float u = us[r * pad4(k) + j];
-                    c = fmaf(a.rho * u, u, c);
+                    c = fmaf(rho * u, u, c);
                 }
                 c = warp_sum(c);
                 if (lane == 0) cost[r] += c;
@@ -136,9 +142,10 @@ __global__ void k_rollout_finalize(RolloutArgs a)
     if (threadIdx.x == 0) a.ub[box] = float_unorder((uint32_t)(key >> 32));
     if (!a.best_u) return;
     const uint64_t hb = box_hash(a.seed, a.id[box]);
+    const int db = a.net.k * problem_H(a.batch, row_problem(a.batch, box), a.H);
     for (int j = threadIdx.x; j < a.d; j += blockDim.x)
         a.best_u[(size_t)box * a.d + j] =
-            draw_sample(hb, m, (uint32_t)j, a.lo[(size_t)box * a.d + j], a.hi[(size_t)box * a.d + j]);
+            j < db ? draw_sample(hb, m, (uint32_t)j, a.lo[(size_t)box * a.d + j], a.hi[(size_t)box * a.d + j]) : 0.f;
 }
 
 // Incumbent update: the box with the smallest ub (lowest index on ties) has its
@@ -147,6 +154,14 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
 {
     const NetDesc &N = a.net;
     const int nlive = live_count(a.n, a.d_n);
+    // one CTA per problem: its rows, weights, start, goal, horizon, rho and incumbent
+    const int pb = blockIdx.x;
+    const float *raw = a.raw + (size_t)pb * N.raw_floats;
+    const float *x0 = a.x0 + (size_t)pb * N.s, *goal = a.goal + (size_t)pb * N.s;
+    const int Hb = problem_H(a.batch, pb, a.H);
+    const float rho = problem_rho(a.batch, pb, a.rho);
+    double *inc_val = a.inc_val + pb;
+    float *inc_u = a.inc_u + (size_t)pb * a.d;
     __shared__ unsigned long long red[8];
     __shared__ double act[2][kMaxWidth + 4];
     __shared__ double xs[kMaxWidth];
@@ -154,7 +169,8 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
     __shared__ int row_sh;
     unsigned long long best = ~0ull;
     for (int i = threadIdx.x; i < nlive; i += blockDim.x)
-        best = umin64(best, ((unsigned long long)float_order(a.ub[i]) << 32) | (unsigned)i);
+        if (row_problem(a.batch, i) == pb)
+            best = umin64(best, ((unsigned long long)float_order(a.ub[i]) << 32) | (unsigned)i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
@@ -170,17 +186,17 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
     if (row < 0) return;
     const float *u = a.best_u + (size_t)row * a.d;
     const int s = N.s, k = N.k;
-    for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = (double)a.x0[i];
+    for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = (double)x0[i];
     __syncthreads();
-    for (int t = 0; t < a.H; ++t) {
+    for (int t = 0; t < Hb; ++t) {
         for (int c = threadIdx.x; c < s + k; c += blockDim.x)
             act[0][c] = c < s ? xs[c] : (double)u[t * k + (c - s)];
         __syncthreads();
         int cur = 0;
         for (int l = 1; l <= N.L; ++l) {
             const int no = N.dims[l], ni = N.dims[l - 1];
-            const float *W = a.raw + N.raw_w[l];
-            const float *b = a.raw + N.raw_b[l];
+            const float *W = raw + N.raw_w[l];
+            const float *b = raw + N.raw_b[l];
             for (int q = threadIdx.x; q < no; q += blockDim.x) {
                 double acc = (double)b[q];
                 for (int c = 0; c < ni; ++c) acc = fma((double)W[(size_t)q * ni + c], act[cur][c], acc);
@@ -193,22 +209,22 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
             double f = f_sh;
             for (int i = 0; i < s; ++i) {
                 xs[i] += act[cur][i];
-                const double e = xs[i] - (double)a.goal[i];
+                const double e = xs[i] - (double)goal[i];
                 f += e * e;
             }
             for (int j = 0; j < k; ++j) {
                 const double uu = (double)u[t * k + j];
-                f += (double)a.rho * uu * uu;
+                f += (double)rho * uu * uu;
             }
             f_sh = f;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) row_sh = (f_sh < *a.inc_val) ? 1 : 0;
+    if (threadIdx.x == 0) row_sh = (f_sh < *inc_val) ? 1 : 0;
     __syncthreads();
     if (row_sh) {
-        for (int j = threadIdx.x; j < a.d; j += blockDim.x) a.inc_u[j] = u[j];
-        if (threadIdx.x == 0) *a.inc_val = f_sh;
+        for (int j = threadIdx.x; j < a.d; j += blockDim.x) inc_u[j] = u[j];
+        if (threadIdx.x == 0) *inc_val = f_sh;
     }
 }
 
@@ -225,7 +241,8 @@ static size_t rollout_smem_bytes(const NetDesc &N, int R, int d, bool wsmem)
 template <int R, int NT, int MINB>
 static cudaError_t launch_fp32_variant(const RolloutArgs &a, int num_sms, size_t budget, cudaStream_t st)
 {
-    bool wsmem = rollout_smem_bytes(a.net, R, a.d, true) <= budget;
+    // several problems: every tile reads its own problem's image through L1 / L2
+    bool wsmem = a.batch.P <= 1 && rollout_smem_bytes(a.net, R, a.d, true) <= budget;
     size_t smem = rollout_smem_bytes(a.net, R, a.d, wsmem);
     if (smem > budget) return cudaErrorInvalidConfiguration;
     auto kern = wsmem ? k_rollout_fp32<R, NT, true, MINB> : k_rollout_fp32<R, NT, false, MINB>;
@@ -285,7 +302,7 @@ void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st)
 
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st)
 {
-    if (a.n > 0) k_incumbent_fp64<<<1, 256, 0, st>>>(a);
+    if (a.n > 0) k_incumbent_fp64<<<a.batch.P > 1 ? a.batch.P : 1, 256, 0, st>>>(a);
 }
 
 }  // namespace bab

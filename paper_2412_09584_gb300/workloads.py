@@ -31,6 +31,10 @@ CONFIGS = {
     "alpha": dict(s=4, k=2, hidden=[32, 32], H=5, rho=0.0, boxes=4096, samples=256, grid_dims=10,
                   alpha_steps=20, alpha_lr=0.1),
     "manip": dict(s=32, k=4, hidden=[256, 256, 256, 256], H=40, rho=0.01, boxes=16384, samples=4, grid_dims=14),
+    # many concurrent plans of the tiny architecture: horizons uniform in [H_lo, H_hi], each problem with its own
+    # seed-drawn weights, start and goal
+    "batched": dict(s=4, k=2, hidden=[32, 32], rho=0.0, problems=64, H_lo=10, H_hi=80, samples=256, alpha_steps=20,
+                    alpha_lr=0.1, rows_lo=256, rows_hi=8192),
 }
 
 
@@ -148,3 +152,51 @@ def pool_values(n, seed, nan_frac=0.0, tie_frac=0.0):
     if nan_frac > 0:
         lb[rng.uniform(size=n) < nan_frac] = np.nan
     return lb, ub
+
+
+def batch_problems(P, seed, s=4, k=2, hidden=(32, 32), H_lo=10, H_hi=80, rho=0.0):
+    """P independent problems of one architecture, problem p drawn by make_problem with seed (seed, p) and a
+    horizon uniform in [H_lo, H_hi].  Returns (list of problem dicts, horizons int32 [P])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Hs = rng.integers(H_lo, H_hi + 1, size=P).astype(np.int32)
+    probs = [make_problem(s, k, list(hidden), int(Hs[p]), rho, seed=int(seed) * 100003 + p) for p in range(P)]
+    return probs, Hs
+
+
+def pack_batch(problems):
+    """Stacked per-problem arrays: params [P][n_params], x0 [P][s], goal [P][s], H int32 [P], rho f32 [P]."""
+    return (np.stack([p["params"] for p in problems]), np.stack([p["x0"] for p in problems]),
+            np.stack([p["goal"] for p in problems]), np.array([p["H"] for p in problems], dtype=np.int32),
+            np.array([p["rho"] for p in problems], dtype=np.float32))
+
+
+def batch_grid_boxes(problems, levels, d_stride):
+    """Each problem's [-1, 1]^(k H_p) cut into the 2^levels grid of grid_boxes, rows grouped by problem, the
+    coordinates beyond k H_p set to 0.  Returns (lo, hi [n][d_stride] f32, id u64 [n], prob int32 [n])."""
+    los, his, ids, prob = [], [], [], []
+    for i, p in enumerate(problems):
+        dp = p["k"] * p["H"]
+        lo, hi, idp = grid_boxes(dp, min(levels, dp))
+        pad = np.zeros((lo.shape[0], d_stride - dp), dtype=np.float32)
+        los.append(np.concatenate([lo, pad], axis=1))
+        his.append(np.concatenate([hi, pad], axis=1))
+        ids.append(idp)
+        prob.append(np.full(lo.shape[0], i, dtype=np.int32))
+    return np.concatenate(los), np.concatenate(his), np.concatenate(ids), np.concatenate(prob)
+
+
+def batch_random_boxes(problems, rows, d_stride, seed, min_width=0.1, max_width=1.0):
+    """rows[p] random sub-boxes of problem p's [-1, 1]^(k H_p) (random_boxes), then all rows shuffled across
+    problems.  Returns (lo, hi [n][d_stride] f32, id u64 [n] distinct, prob int32 [n])."""
+    los, his, prob = [], [], []
+    for i, p in enumerate(problems):
+        dp = p["k"] * p["H"]
+        lo, hi, _ = random_boxes(dp, int(rows[i]), seed=seed * 7919 + i, min_width=min_width, max_width=max_width)
+        pad = np.zeros((lo.shape[0], d_stride - dp), dtype=np.float32)
+        los.append(np.concatenate([lo, pad], axis=1))
+        his.append(np.concatenate([hi, pad], axis=1))
+        prob.append(np.full(lo.shape[0], i, dtype=np.int32))
+    lo, hi, prob = np.concatenate(los), np.concatenate(his), np.concatenate(prob)
+    order = np.random.Generator(np.random.PCG64(seed)).permutation(lo.shape[0])
+    ids = (np.arange(lo.shape[0], dtype=np.uint64) + np.uint64(1000))
+    return lo[order], hi[order], ids, prob[order]
