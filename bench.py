@@ -294,6 +294,7 @@ def run_ours(args):
     inc = float(st.inc_val.item())
     st.close()
     ttg = None if args.no_time_to_gap else time_to_gap(dev)
+    batched = None if args.no_batched else batched_bab(dev)
 
     boxes = st.nb * args.steps * ws
     value = boxes / (ms / 1e3)
@@ -335,7 +336,7 @@ def run_ours(args):
            "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound": statistics.mean(bound_ms)},
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg}
+           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -388,6 +389,119 @@ def run_e2e(st, steps):
     d2h = nb * (2 * 4) + nb * (2 * d * 4 + 8) + 8
     return {"value": nb * steps / (ms / 1e3), "unit": "subdomain-bounds/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h}
+
+
+def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None):
+    """Many concurrent plans: P problems of the tiny architecture (own weights, start, goal; horizons uniform in
+    10..80), each pool starting as a 256-box grid; per iteration, per problem: prune against its incumbent, pick
+    n_pick boxes, split them, search (FP32 rollouts) and bound (interval bounds + alpha-CROWN) the children.
+    Every iteration is one CUDA-graph replay (one launch per kernel for all problems).  Returns timing and gaps."""
+    import torch
+    from paper_2412_09584_gb300 import binding as B
+    from paper_2412_09584_gb300 import workloads as W
+    c = W.CONFIGS["batched"]
+    P = P or c["problems"]
+    samples = samples or c["samples"]
+    alpha_steps = c["alpha_steps"] if alpha_steps is None else alpha_steps
+    probs, _ = W.batch_problems(P, SEED, H_lo=c["H_lo"], H_hi=c["H_hi"])
+    params, x0, goal, Hs, rho = W.pack_batch(probs)
+    k = probs[0]["k"]
+    Hmax = int(Hs.max())
+    d = k * Hmax
+    ctx = B.bab_load_dynamics_batch(probs[0]["dims"], params, probs[0]["s"], k)
+    f = dict(device=dev, dtype=torch.float32)
+    i32 = dict(device=dev, dtype=torch.int32)
+    tx0, tgoal, tH, trho = (torch.as_tensor(x0).to(**f), torch.as_tensor(goal).to(**f),
+                            torch.as_tensor(Hs).to(**i32), torch.as_tensor(rho).to(**f))
+    lo, hi, ids, prob = W.batch_grid_boxes(probs, 8, d)
+    n0 = lo.shape[0]
+    per_iter = P * n_pick
+    cap = n0 + (iters + 8) * per_iter
+    nb = 2 * per_iter
+
+    def alloc():
+        return {"lo": torch.zeros(cap, d, **f), "hi": torch.zeros(cap, d, **f), "lb": torch.empty(cap, **f),
+                "ub": torch.empty(cap, **f), "id": torch.zeros(cap, dtype=torch.int64, device=dev),
+                "prob": torch.zeros(cap, **i32)}
+    pool = [alloc(), alloc()]
+    P0 = pool[0]
+    P0["lo"][:n0] = torch.as_tensor(lo).to(**f)
+    P0["hi"][:n0] = torch.as_tensor(hi).to(**f)
+    P0["id"][:n0] = torch.as_tensor(ids.astype(np.int64)).to(dev)
+    P0["prob"][:n0] = torch.as_tensor(prob).to(**i32)
+    best_u = torch.empty(max(nb, n0), d, **f)
+    inc_val = torch.full((P,), float("inf"), dtype=torch.float64, device=dev)
+    inc_u = torch.zeros(P, d, **f)
+    keep = torch.empty(cap, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(3, **i32)
+    n_live = torch.tensor([n0], **i32)
+    picks = torch.full((P,), n_pick, **i32)
+    # tile shapes timed on problem 0's starting boxes (the grid rows are grouped by problem)
+    r0, d0 = int((prob == 0).sum()), k * int(Hs[0])
+    B.bab_autotune(ctx, tx0[0].contiguous(), tgoal[0].contiguous(), int(Hs[0]), float(rho[0]),
+                   P0["lo"][:r0, :d0].contiguous(), P0["hi"][:r0, :d0].contiguous(), P0["id"][:r0], r0, samples)
+
+    def search_and_bound(Q, n, d_n):
+        B.bab_rollout_batch(ctx, tx0, tgoal, tH, trho, Hmax, d, Q["lo"], Q["hi"], Q["id"], Q["prob"], n, samples,
+                            SEED, Q["ub"], best_u, inc_val, inc_u, d_n=d_n)
+        B.bab_bound_batch(ctx, tx0, tgoal, tH, trho, Hmax, d, Q["lo"], Q["hi"], Q["prob"], n, Q["lb"],
+                          alpha_steps=alpha_steps, lr=c["alpha_lr"], d_n=d_n)
+
+    state = {"cur": 0}
+    n_max = cap - per_iter
+
+    def step():
+        src, dst = pool[state["cur"]], pool[state["cur"] ^ 1]
+        B.bab_prune_branch_batch(ctx, d, tH, Hmax, src["lo"], src["hi"], src["lb"], src["ub"], src["id"],
+                                 src["prob"], n_max, inc_val, picks, per_iter, 0.75, cap, dst["lo"], dst["hi"],
+                                 dst["lb"], dst["ub"], dst["id"], dst["prob"], keep, counts, d_n=n_live)
+        search_and_bound(dst, nb, counts[0:1])
+        n_live.copy_(counts[2:3])
+        state["cur"] ^= 1
+
+    search_and_bound(P0, n0, None)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):  # warm-up (loads every kernel), then one graph per pool parity
+            step()
+        torch.cuda.synchronize()
+        graphs = []
+        for _ in range(2):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                step()
+            graphs.append(g)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    done = 2 + 2  # iterations run so far (two eager warm-up steps and the two captured ones)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(iters - done):
+        graphs[state["cur"]].replay()
+        state["cur"] ^= 1
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / (iters - done)
+    status = B.bab_status(ctx)
+    n = int(counts[2].item())
+    Q = pool[state["cur"]]
+    lbmin = torch.full((P,), float("inf"), **f).scatter_reduce(0, Q["prob"][:n].long(), Q["lb"][:n], "amin")
+    live = torch.bincount(Q["prob"][:n].long(), minlength=P)
+    gaps = (inc_val - lbmin.double()).cpu().numpy()
+    B.bab_destroy(ctx)
+    rsteps = float(nb) * samples * float(np.mean(Hs))
+    return {"workload": f"{P} problems of MLP 6-32-32-4 (own weights, start, goal), horizons uniform in "
+                        f"[{c['H_lo']}, {c['H_hi']}], 256-box starting grid each, {n_pick} boxes picked and split per "
+                        f"problem per iteration, {samples} FP32 rollouts per child, interval bounds + alpha-CROWN "
+                        f"({alpha_steps} Adam steps) per child",
+            "iterations": iters, "ms_per_iteration": ms, "children_per_iteration": nb,
+            "subdomain_bounds_per_s": nb / (ms / 1e3), "rollout_steps_per_s": rsteps / (ms / 1e3),
+            "launches_per_iteration": 3 + 4 + 2, "timed_region": "CUDA-graph replays, one launch per kernel",
+            "live_rows_end": n, "live_rows_per_problem_end": [int(live.min()), int(live.max())],
+            "gap_end": {"min": float(gaps.min()), "median": float(np.median(gaps)), "max": float(gaps.max())},
+            "device_status": status}
+
 
 
 def time_to_gap(dev, iters=20, max_iters=60):
@@ -520,6 +634,7 @@ def main():
     ap.add_argument("--no-time-to-gap", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of CUDA-graph replays")
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch heuristics instead of bab_autotune")
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-problem BaB section")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")
