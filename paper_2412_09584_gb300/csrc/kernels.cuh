@@ -56,6 +56,8 @@ struct RolloutArgs {
     const float *tc_bias;
     int tc_bytes;        // bytes of the image the kernel loads (hi only for BF16)
     uint32_t tmem_cols;
+    int stages;          // > 0: the image is streamed through a ring of `stages` buffers of stage_bytes
+    int stage_bytes;
 };
 
 struct BoundArgs {

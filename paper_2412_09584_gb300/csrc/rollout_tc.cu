@@ -39,6 +39,7 @@ namespace {
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 constexpr int kKMax = 8;                          // action dimension limit of this kernel
 constexpr int kEpiWarps = 8;                      // epilogue warps per tile slot (2 per TMEM lane quadrant)
+constexpr int kMaxStages = 8;                     // weight ring buffers when the image is streamed
 
 // (a, b) -> packed BF16 pair, a in the low half, round to nearest even
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
@@ -68,17 +69,21 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 
 }  // namespace
 
-// SP: padded state width of the last layer (16 or 32).
-template <int NSLOT, int SPLIT, int SP>
-__global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tc(RolloutArgs a)
+// SP: padded state width of the last layer (16 or 32).  STREAM: the weight
+// image does not fit in shared memory; a producer warp streams it, one K-atom
+// (64 inputs of one layer, hi and lo halves) at a time, through a ring of
+// a.stages buffers in the order the MMA issuer consumes them (NSLOT = 1).
+template <int NSLOT, int SPLIT, int SP, bool STREAM>
+__global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     const NetDesc &N = a.net;
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float *bias = reinterpret_cast<float *>(wimg + a.tc_bytes);
+    float *bias = reinterpret_cast<float *>(wimg + (STREAM ? a.stages * a.stage_bytes : a.tc_bytes));
     float *goal_s = bias + N.tc_bias_floats;
     float *x0_s = goal_s + SP;
-    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT];
+    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_fin;
+    __shared__ uint64_t bar_full[kMaxStages], bar_empty[kMaxStages];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,9 +94,14 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tc(
     if (threadIdx.x == 0) {
         abort_flag = 0;
         tc::mbar_init(&bar_w, 1);
+        tc::mbar_init(&bar_fin, 1);
         for (int i = 0; i < NSLOT; ++i) {
             tc::mbar_init(&bar_a[i], kEpiWarps);
             tc::mbar_init(&bar_d[i], 1);
+        }
+        for (int i = 0; i < kMaxStages; ++i) {
+            tc::mbar_init(&bar_full[i], 1);
+            tc::mbar_init(&bar_empty[i], 1);
         }
         tc::mbar_init_fence();
     }
@@ -104,15 +114,17 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tc(
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (threadIdx.x == mma_warp * 32) {
-        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)a.tc_bytes);
-        constexpr uint32_t kChunk = 32768;
-        for (uint32_t off = 0; off < (uint32_t)a.tc_bytes; off += kChunk) {
-            const uint32_t sz = min(kChunk, (uint32_t)a.tc_bytes - off);
-            tc::bulk_g2s(wimg + off, a.tc_img + off, sz, &bar_w);
+    if (!STREAM) {
+        if (threadIdx.x == mma_warp * 32) {
+            tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)a.tc_bytes);
+            constexpr uint32_t kChunk = 32768;
+            for (uint32_t off = 0; off < (uint32_t)a.tc_bytes; off += kChunk) {
+                const uint32_t sz = min(kChunk, (uint32_t)a.tc_bytes - off);
+                tc::bulk_g2s(wimg + off, a.tc_img + off, sz, &bar_w);
+            }
         }
+        if (warp < mma_warp + NSLOT && !warp_wait(&bar_w, 0, abort) && lane == 0) raise_abort(a.status, abort);
     }
-    if (!warp_wait(&bar_w, 0, abort) && lane == 0) raise_abort(a.status, abort);
 
     const int nlive = live_count(a.n, a.d_n);
     const int tpb = (a.M + 127) / 128;
@@ -281,14 +293,14 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tc(
                 if (lane == 0 && key != ~0ull) atomicMin(&a.keys[box], key);
             }
         }
-    } else if (lane == 0) {
+    } else if (warp < mma_warp + NSLOT && lane == 0) {
         // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
         const int sl = warp - mma_warp;
         const long long gi = (long long)blockIdx.x * NSLOT + sl;
         const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
         long long left = cnt * a.H * L;
         int l = 1;
-        uint32_t phA = 0, ncommit = 0;
+        uint32_t phA = 0, ncommit = 0, ring_it = 0;
         const uint32_t dcol = tb + sl * slot_cols;
         const uint32_t ah = dcol + Dc, al = ah + Ac;
         while (left > 0 && !*abort) {
@@ -300,25 +312,82 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tc(
             tc::fence_after_sync();
             const int Kl = N.tc_K[l], Nl = N.tc_N[l];
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
-            const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
-            for (int ks = 0; ks < Kl / 16; ++ks) {
-                const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
-                const uint64_t dh = tc::desc_sw128(bh + boff);
-                tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
-                if (SPLIT == 3) {
-                    tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
-                    tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+            if (!STREAM) {
+                const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
+                for (int ks = 0; ks < Kl / 16; ++ks) {
+                    const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
+                    const uint64_t dh = tc::desc_sw128(bh + boff);
+                    tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                    if (SPLIT == 3) {
+                        tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
+                        tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                    }
                 }
+            } else {
+                // one K-atom (64 inputs; hi, then lo for the split) per ring buffer
+                bool ok = true;
+                for (int at = 0; at < (Kl + 63) / 64; ++at, ++ring_it) {
+                    const uint32_t st = ring_it % (uint32_t)a.stages, ph = (ring_it / (uint32_t)a.stages) & 1u;
+                    if (!tc::mbar_wait(&bar_full[st], ph, abort, kWaitLimitNs)) {
+                        raise_abort(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bh = tc::smem_u32(wimg + (size_t)st * a.stage_bytes);
+                    const uint32_t blo = bh + (uint32_t)(Nl * 128);
+                    for (int kk = 0; kk < 4 && 4 * at + kk < Kl / 16; ++kk) {
+                        const int ks = 4 * at + kk;
+                        const uint64_t dh = tc::desc_sw128(bh + (uint32_t)kk * 32u);
+                        tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                        if (SPLIT == 3) {
+                            tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + (uint32_t)kk * 32u), idesc, 1u);
+                            tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&bar_empty[st]);  // the buffer is free once these MMAs have read it
+                }
+                if (!ok) break;
             }
             tc::mma_commit(&bar_d[sl]);
             ++ncommit;
             l = (l == L) ? 1 : l + 1;
             --left;
         }
-        if (*abort && ncommit) {
-            // let every issued MMA finish before the TMEM is released
+        if (*abort) {
+            // let every issued MMA finish before the TMEM and the ring are released
             volatile int never = 0;
-            tc::mbar_wait(&bar_d[sl], (ncommit - 1) & 1, &never, kWaitLimitNs);
+            tc::mma_commit(&bar_fin);
+            tc::mbar_wait(&bar_fin, 0, &never, kWaitLimitNs);
+        }
+    } else if (STREAM && warp == mma_warp + NSLOT && lane == 0) {
+        // ------------------- producer: the weight atoms in the issuer's order -------------------
+        const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+        uint32_t it = 0;
+        bool ok = true;
+        for (long long q = 0; q < cnt * a.H && ok && !*abort; ++q) {
+            for (int l = 1; l <= L && ok; ++l) {
+                const int Kl = N.tc_K[l], Nl = N.tc_N[l];
+                const uint32_t atom = (uint32_t)Nl * 128u;
+                for (int at = 0; at < (Kl + 63) / 64; ++at, ++it) {
+                    const uint32_t st = it % (uint32_t)a.stages, ph = (it / (uint32_t)a.stages) & 1u;
+                    if (!tc::mbar_wait(&bar_empty[st], ph ^ 1u, abort, kWaitLimitNs)) {
+                        raise_abort(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *dst = wimg + (size_t)st * a.stage_bytes;
+                    tc::mbar_arrive_expect_tx(&bar_full[st], (SPLIT == 3 ? 2u : 1u) * atom);
+                    tc::bulk_g2s(dst, a.tc_img + N.tc_hi[l] + (size_t)at * atom, atom, &bar_full[st]);
+                    if (SPLIT == 3) tc::bulk_g2s(dst + atom, a.tc_img + N.tc_lo[l] + (size_t)at * atom, atom, &bar_full[st]);
+                }
+            }
+        }
+        // copies still in flight must land before the shared memory is released
+        volatile int never = 0;
+        const uint32_t inflight = it < (uint32_t)a.stages ? it : (uint32_t)a.stages;
+        for (uint32_t j = 0; j < inflight; ++j) {
+            const uint32_t i2 = it - 1 - j, st = i2 % (uint32_t)a.stages;
+            tc::mbar_wait(&bar_full[st], (i2 / (uint32_t)a.stages) & 1u, &never, kWaitLimitNs);
         }
     }
     tc::fence_before_sync();
@@ -387,30 +456,52 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
             a.best_u[(size_t)box * d + j] = draw_sample(hb, m, (uint32_t)j, blo[j], bhi[j]);
 }
 
-template <int NSLOT, int SPLIT, int SP>
+template <int NSLOT, int SPLIT, int SP, bool STREAM>
 static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_rollout_tc<NSLOT, SPLIT, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = k_rollout_tc<NSLOT, SPLIT, SP, STREAM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_rollout_tc<NSLOT, SPLIT, SP><<<grid, NSLOT * (kEpiWarps + 1) * 32, smem, st>>>(a);
+    kern<<<grid, (NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// Tensor-core variant available for this network and precision?
-static size_t rollout_tc_smem(const NetDesc &N, int split, int nslot)
+// Shared memory besides the weights: biases, goal and x0, and the 1024-byte alignment of the image.
+static size_t rollout_tc_extra(const NetDesc &N)
 {
     const int SP = N.tc_N[N.L];
+    return ((size_t)N.tc_bias_floats + 2 * SP) * 4 + 1024;
+}
+
+// Bytes of one ring buffer: the largest K-atom (N_l x 64 BF16), hi and lo halves for the split.
+static size_t rollout_tc_stage(const NetDesc &N, int split)
+{
+    size_t b = 0;
+    for (int l = 1; l <= N.L; ++l) b = (size_t)N.tc_N[l] * 128 > b ? (size_t)N.tc_N[l] * 128 : b;
+    return b * (split == 3 ? 2 : 1);
+}
+
+static bool rollout_tc_resident(const NetDesc &N, int split, int max_smem)
+{
     const size_t img = split == 3 ? N.tc_bytes : N.tc_bytes_hi;
-    (void)nslot;
-    const size_t floats = (size_t)N.tc_bias_floats + 2 * SP;
-    return img + floats * 4 + 1024;
+    return img + rollout_tc_extra(N) + 1024 <= (size_t)max_smem;
 }
 
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
 {
     if (!N.tc_ok || N.L < 2 || N.s > 32 || N.k > kKMax || N.tc_K[1] > 64) return false;
-    return rollout_tc_smem(N, split, 2) + 1024 <= (size_t)max_smem;
+    // resident image, or at least two ring buffers
+    return rollout_tc_resident(N, split, max_smem) ||
+           2 * rollout_tc_stage(N, split) + rollout_tc_extra(N) + 1024 <= (size_t)max_smem;
+}
+
+template <int SPLIT, int SP>
+static cudaError_t launch_tc_shape(const RolloutArgs &a, int nslot, bool stream, int grid, size_t smem,
+                                   cudaStream_t st)
+{
+    if (stream) return launch_tc_variant<1, SPLIT, SP, true>(a, grid, smem, st);
+    return nslot == 2 ? launch_tc_variant<2, SPLIT, SP, false>(a, grid, smem, st)
+                      : launch_tc_variant<1, SPLIT, SP, false>(a, grid, smem, st);
 }
 
 // nslot_pref: tiles per CTA (1 or 2), or -1 for two whenever both fit in tensor memory
@@ -418,10 +509,14 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
 {
     const NetDesc &N = a.net;
     if (a.n <= 0) return cudaSuccess;
+    int dev, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool stream = !rollout_tc_resident(N, split, max_smem);
     // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
     const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols;
-    int nslot = (2 * slot_cols <= 512) ? 2 : 1;
-    if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
+    int nslot = (2 * slot_cols <= 512 && !stream) ? 2 : 1;
+    if (!stream && (nslot_pref == 1 || nslot_pref == 2)) nslot = nslot_pref;
     int cols = 32;
     while (cols < nslot * slot_cols) cols *= 2;
     if (cols > 512) return cudaErrorInvalidConfiguration;
@@ -430,21 +525,30 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
         // BF16 only: the weight image is the hi halves, laid out contiguously first
         a.tc_bytes = N.tc_bytes_hi;
     }
-    const size_t smem = rollout_tc_smem(N, split, nslot);
+    size_t smem;
+    if (stream) {
+        a.stage_bytes = (int)rollout_tc_stage(N, split);
+        const size_t room = (size_t)max_smem - 1024 - rollout_tc_extra(N);
+        int stages = (int)(room / a.stage_bytes);
+        stages = stages > kMaxStages ? kMaxStages : stages;
+        if (stages < 2) return cudaErrorInvalidConfiguration;
+        a.stages = stages;
+        smem = (size_t)stages * a.stage_bytes + rollout_tc_extra(N);
+    } else {
+        a.stages = 0;
+        smem = (size_t)a.tc_bytes + rollout_tc_extra(N);
+    }
     const long long ntiles = (long long)a.n * ((a.M + 127) / 128);
     int grid = (int)((ntiles + nslot - 1) / nslot);
     grid = grid < num_sms ? grid : num_sms;
     k_fill_keys(a.keys, a.n, st);
     cudaError_t e;
     const int SPv = N.tc_N[N.L];
-    if (SPv != 16 && SPv != 32) return cudaErrorInvalidConfiguration;
-    if (nslot == 2) {
-        if (split == 3) e = SPv == 16 ? launch_tc_variant<2, 3, 16>(a, grid, smem, st) : launch_tc_variant<2, 3, 32>(a, grid, smem, st);
-        else e = SPv == 16 ? launch_tc_variant<2, 1, 16>(a, grid, smem, st) : launch_tc_variant<2, 1, 32>(a, grid, smem, st);
-    } else {
-        if (split == 3) e = SPv == 16 ? launch_tc_variant<1, 3, 16>(a, grid, smem, st) : launch_tc_variant<1, 3, 32>(a, grid, smem, st);
-        else e = SPv == 16 ? launch_tc_variant<1, 1, 16>(a, grid, smem, st) : launch_tc_variant<1, 1, 32>(a, grid, smem, st);
-    }
+    if (SPv == 16) e = split == 3 ? launch_tc_shape<3, 16>(a, nslot, stream, grid, smem, st)
+                                  : launch_tc_shape<1, 16>(a, nslot, stream, grid, smem, st);
+    else if (SPv == 32) e = split == 3 ? launch_tc_shape<3, 32>(a, nslot, stream, grid, smem, st)
+                                       : launch_tc_shape<1, 32>(a, nslot, stream, grid, smem, st);
+    else return cudaErrorInvalidConfiguration;
     if (e != cudaSuccess) return e;
     if (split == 1) {
         k_rescore_fp32<<<a.n, 256, 0, st>>>(a);
