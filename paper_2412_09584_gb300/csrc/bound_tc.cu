@@ -21,7 +21,8 @@
 //
 // Warp roles are those of k_rollout_tc: per slot 8 epilogue warps (primary
 // and helper of each TMEM lane quadrant, splitting the columns of hidden
-// layers) and one MMA issuer warp.  Every wait is bounded in time.
+// layers) and one MMA issuer warp, plus a producer warp when the backward
+// image is streamed.  Every wait is bounded in time.
 #include <cuda_bf16.h>
 
 #include "bab_internal.cuh"
@@ -34,6 +35,7 @@ namespace {
 
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kEpi = 8;
+constexpr int kMaxStages = 8;  // ring buffers when the backward image is streamed
 constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20)
 
 __device__ __forceinline__ uint32_t pack2(float a, float b)
@@ -68,16 +70,20 @@ __device__ __forceinline__ void tangent(float xl, float xu, float g, float &coef
 
 }  // namespace
 
-// SP: padded state width (16 or 32); KP1: padded width of [x | u] (<= 64)
-template <int NSLOT, int SP>
-__global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundArgs a)
+// SP: padded state width (16 or 32).  STREAM: the backward image does not fit
+// in shared memory; a producer warp streams it one K-atom (64 inputs of a
+// layer's product, hi and lo halves) at a time through a ring of a.stages
+// buffers in the MMA issuer's order (NSLOT = 1).
+template <int NSLOT, int SP, bool STREAM>
+__global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 1) k_crown_tc(BoundArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     const NetDesc &N = a.net;
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float *bias = reinterpret_cast<float *>(wimg + N.tcb_bytes);
+    float *bias = reinterpret_cast<float *>(wimg + (STREAM ? (size_t)a.stages * a.stage_bytes : (size_t)N.tcb_bytes));
     float *pair = bias + N.tc_bias_floats;  // [NSLOT][128][2]: helper warps' (constant, margin) partials
-    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_p[NSLOT * 4];
+    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_p[NSLOT * 4], bar_fin;
+    __shared__ uint64_t bar_full[kMaxStages], bar_empty[kMaxStages];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -88,10 +94,15 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
     if (threadIdx.x == 0) {
         abort_flag = 0;
         tc::mbar_init(&bar_w, 1);
+        tc::mbar_init(&bar_fin, 1);
         for (int i = 0; i < NSLOT; ++i) {
             tc::mbar_init(&bar_a[i], kEpi);
             tc::mbar_init(&bar_d[i], 1);
             for (int q = 0; q < 4; ++q) tc::mbar_init(&bar_p[i * 4 + q], 1);
+        }
+        for (int i = 0; i < kMaxStages; ++i) {
+            tc::mbar_init(&bar_full[i], 1);
+            tc::mbar_init(&bar_empty[i], 1);
         }
         tc::mbar_init_fence();
     }
@@ -100,12 +111,14 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (threadIdx.x == mma_warp * 32) {
-        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
-        for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
-            tc::bulk_g2s(wimg + off, a.tcb_img + off, min(32768u, (uint32_t)N.tcb_bytes - off), &bar_w);
+    if (!STREAM) {
+        if (threadIdx.x == mma_warp * 32) {
+            tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
+            for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
+                tc::bulk_g2s(wimg + off, a.tcb_img + off, min(32768u, (uint32_t)N.tcb_bytes - off), &bar_w);
+        }
+        if (warp < mma_warp + NSLOT && !wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
     }
-    if (!wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
 
     const int nlive = live_count(a.n, a.d_n);
     const int ntiles = (nlive + 127) / 128;
@@ -336,14 +349,14 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
                 }
             }
         }
-    } else if (lane == 0) {
+    } else if (warp < mma_warp + NSLOT && lane == 0) {
         // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
         const int sl = warp - mma_warp;
         const int gi = blockIdx.x * NSLOT + sl;
         const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
         long long left = cnt * H * L;
         int l = L;
-        uint32_t phA = 0, ncommit = 0;
+        uint32_t phA = 0, ncommit = 0, ring_it = 0;
         const uint32_t dcol = tb + sl * slot_cols;
         const uint32_t ah = dcol + Dc, al = ah + Ac;
         while (left > 0 && !*abort) {
@@ -355,22 +368,77 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
             tc::fence_after_sync();
             const int Kl = N.tcb_K[l], Nl = N.tcb_N[l];
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
-            const uint32_t bh = tc::smem_u32(wimg + N.tcb_hi[l]), blo = tc::smem_u32(wimg + N.tcb_lo[l]);
-            for (int ks = 0; ks < Kl / 16; ++ks) {
-                const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
-                const uint64_t dh = tc::desc_sw128(bh + boff);
-                tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
-                tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
-                tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+            if (!STREAM) {
+                const uint32_t bh = tc::smem_u32(wimg + N.tcb_hi[l]), blo = tc::smem_u32(wimg + N.tcb_lo[l]);
+                for (int ks = 0; ks < Kl / 16; ++ks) {
+                    const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
+                    const uint64_t dh = tc::desc_sw128(bh + boff);
+                    tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
+                    tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                }
+            } else {
+                bool ok = true;
+                for (int at = 0; at < (Kl + 63) / 64; ++at, ++ring_it) {
+                    const uint32_t st = ring_it % (uint32_t)a.stages, ph = (ring_it / (uint32_t)a.stages) & 1u;
+                    if (!tc::mbar_wait(&bar_full[st], ph, abort, kWaitNs)) {
+                        abort_all(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bh = tc::smem_u32(wimg + (size_t)st * a.stage_bytes);
+                    const uint32_t blo = bh + (uint32_t)(Nl * 128);
+                    for (int kk = 0; kk < 4 && 4 * at + kk < Kl / 16; ++kk) {
+                        const int ks = 4 * at + kk;
+                        const uint64_t dh = tc::desc_sw128(bh + (uint32_t)kk * 32u);
+                        tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                        tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + (uint32_t)kk * 32u), idesc, 1u);
+                        tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                    }
+                    tc::mma_commit(&bar_empty[st]);  // the buffer is free once these MMAs have read it
+                }
+                if (!ok) break;
             }
             tc::mma_commit(&bar_d[sl]);
             ++ncommit;
             l = (l == 1) ? L : l - 1;
             --left;
         }
-        if (*abort && ncommit) {
+        if (*abort) {
+            // every issued MMA must finish before the TMEM and the ring are released
             volatile int never = 0;
-            tc::mbar_wait(&bar_d[sl], (ncommit - 1) & 1, &never, kWaitNs);
+            tc::mma_commit(&bar_fin);
+            tc::mbar_wait(&bar_fin, 0, &never, kWaitNs);
+        }
+    } else if (STREAM && warp == mma_warp + NSLOT && lane == 0) {
+        // ------------- producer: the backward image's atoms in the issuer's order (l = L .. 1) -------------
+        const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+        uint32_t it = 0;
+        bool ok = true;
+        for (long long q = 0; q < cnt * H && ok && !*abort; ++q) {
+            for (int l = L; l >= 1 && ok; --l) {
+                const int Kl = N.tcb_K[l], Nl = N.tcb_N[l];
+                const uint32_t atom = (uint32_t)Nl * 128u;
+                for (int at = 0; at < (Kl + 63) / 64; ++at, ++it) {
+                    const uint32_t st = it % (uint32_t)a.stages, ph = (it / (uint32_t)a.stages) & 1u;
+                    if (!tc::mbar_wait(&bar_empty[st], ph ^ 1u, abort, kWaitNs)) {
+                        abort_all(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *dst = wimg + (size_t)st * a.stage_bytes;
+                    tc::mbar_arrive_expect_tx(&bar_full[st], 2u * atom);
+                    tc::bulk_g2s(dst, a.tcb_img + N.tcb_hi[l] + (size_t)at * atom, atom, &bar_full[st]);
+                    tc::bulk_g2s(dst + atom, a.tcb_img + N.tcb_lo[l] + (size_t)at * atom, atom, &bar_full[st]);
+                }
+            }
+        }
+        // copies still in flight must land before the shared memory is released
+        volatile int never = 0;
+        const uint32_t inflight = it < (uint32_t)a.stages ? it : (uint32_t)a.stages;
+        for (uint32_t j = 0; j < inflight; ++j) {
+            const uint32_t i2 = it - 1 - j, st = i2 % (uint32_t)a.stages;
+            tc::mbar_wait(&bar_full[st], (i2 / (uint32_t)a.stages) & 1u, &never, kWaitNs);
         }
     }
     tc::fence_before_sync();
@@ -382,24 +450,45 @@ __global__ void __launch_bounds__(NSLOT * (kEpi + 1) * 32, 1) k_crown_tc(BoundAr
     }
 }
 
-static size_t crown_tc_smem(const NetDesc &N, int nslot)
+static size_t crown_tc_extra(const NetDesc &N, int nslot)
 {
-    return (size_t)N.tcb_bytes + (size_t)N.tc_bias_floats * 4 + (size_t)nslot * 128 * 2 * 4 + 1024;
+    return (size_t)N.tc_bias_floats * 4 + (size_t)nslot * 128 * 2 * 4 + 1024;
+}
+
+// one ring buffer: the largest K-atom of a backward product (N_l x 64 BF16), hi and lo halves
+static size_t crown_tc_stage(const NetDesc &N)
+{
+    size_t b = 0;
+    for (int l = 1; l <= N.L; ++l) b = (size_t)N.tcb_N[l] * 128 > b ? (size_t)N.tcb_N[l] * 128 : b;
+    return 2 * b;
+}
+
+static bool crown_tc_resident(const NetDesc &N, int nslot, int max_smem)
+{
+    return (size_t)N.tcb_bytes + crown_tc_extra(N, nslot) + 1024 <= (size_t)max_smem;
 }
 
 bool crown_tc_supported(const NetDesc &N, int max_smem)
 {
     if (!N.tc_ok || N.L < 2 || N.s > 32 || pad16(N.s + N.k) > 48) return false;
-    return crown_tc_smem(N, 2) + 1024 <= (size_t)max_smem;
+    return crown_tc_resident(N, 1, max_smem) || 2 * crown_tc_stage(N) + crown_tc_extra(N, 1) + 1024 <= (size_t)max_smem;
 }
 
-template <int NSLOT, int SP>
+template <int NSLOT, int SP, bool STREAM>
 static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_crown_tc<NSLOT, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = k_crown_tc<NSLOT, SP, STREAM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_crown_tc<NSLOT, SP><<<grid, NSLOT * (kEpi + 1) * 32, smem, st>>>(a);
+    kern<<<grid, (NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int SP>
+static cudaError_t launch_shape(const BoundArgs &a, int nslot, bool stream, int grid, size_t smem, cudaStream_t st)
+{
+    if (stream) return launch_variant<1, SP, true>(a, grid, smem, st);
+    return nslot == 2 ? launch_variant<2, SP, false>(a, grid, smem, st) : launch_variant<1, SP, false>(a, grid, smem, st);
 }
 
 // nslot_pref: tiles per CTA (1 or 2), or -1 for two only when the tiles outnumber the SMs
@@ -407,21 +496,39 @@ cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream
 {
     const NetDesc &N = a.net;
     if (a.n <= 0) return cudaSuccess;
+    int dev, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int slot_cols = N.tcb_dcols + 2 * N.tcb_acols;
     const int ntiles = (a.n + 127) / 128;
     int nslot = (ntiles > num_sms && 2 * slot_cols <= 512) ? 2 : 1;
     if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
+    const bool stream = !crown_tc_resident(N, nslot, max_smem) && !crown_tc_resident(N, 1, max_smem);
+    if (!stream && !crown_tc_resident(N, nslot, max_smem)) nslot = 1;
+    if (stream) nslot = 1;
     int cols = 32;
     while (cols < nslot * slot_cols) cols *= 2;
     if (cols > 512) return cudaErrorInvalidConfiguration;
     a.tmem_cols = (uint32_t)cols;
-    const size_t smem = crown_tc_smem(N, nslot);
+    size_t smem;
+    if (stream) {
+        a.stage_bytes = (int)crown_tc_stage(N);
+        const size_t room = (size_t)max_smem - 1024 - crown_tc_extra(N, 1);
+        int stages = (int)(room / a.stage_bytes);
+        stages = stages > kMaxStages ? kMaxStages : stages;
+        if (stages < 2) return cudaErrorInvalidConfiguration;
+        a.stages = stages;
+        smem = (size_t)stages * a.stage_bytes + crown_tc_extra(N, 1);
+    } else {
+        a.stages = 0;
+        smem = (size_t)N.tcb_bytes + crown_tc_extra(N, nslot);
+    }
     int grid = (ntiles + nslot - 1) / nslot;
     grid = grid < num_sms ? grid : num_sms;
     const int SP = pad16(N.s);
-    if (SP != 16 && SP != 32) return cudaErrorInvalidConfiguration;
-    if (nslot == 2) return SP == 16 ? launch_variant<2, 16>(a, grid, smem, st) : launch_variant<2, 32>(a, grid, smem, st);
-    return SP == 16 ? launch_variant<1, 16>(a, grid, smem, st) : launch_variant<1, 32>(a, grid, smem, st);
+    if (SP == 16) return launch_shape<16>(a, nslot, stream, grid, smem, st);
+    if (SP == 32) return launch_shape<32>(a, nslot, stream, grid, smem, st);
+    return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace bab

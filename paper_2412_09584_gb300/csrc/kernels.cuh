@@ -88,6 +88,8 @@ struct BoundArgs {
     const float *tc_bias;    // biases padded to multiples of 16 (offsets tc_boff)
     float *mu;               // [n][d] coefficients of u (lin_coef or scratch)
     uint32_t tmem_cols;
+    int stages;              // > 0: the backward image is streamed through `stages` ring buffers
+    int stage_bytes;
 };
 
 struct AdamStep {

@@ -118,16 +118,21 @@ def test_manip_rollout_tensor_cores_streamed(oracle, manip, prec_name):
     assert r["inc_val"] == pytest.approx(oracle.objective(p, r["inc_u"].astype(np.float64)), rel=1e-10)
 
 
-def test_manip_tensor_core_crown_reports_unsupported(manip):
-    """The backward images do not fit in shared memory and are not streamed: the call refuses cleanly."""
-    from gpu_util import DEV, T
+def test_manip_crown_tensor_cores_streamed(oracle, manip):
+    """3-term BF16 CROWN with the backward image streamed: sound (never above the exact CROWN bound) and within
+    the directed-rounding drift plus the split's per-product error of it."""
     from paper_2412_09584_gb300 import binding as B
     p, g = manip
-    lo, hi, ids = W.random_boxes(160, 2, seed=5)
-    lb = torch.empty(2, device=DEV)
-    with pytest.raises(B.BabError) as e:
-        B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 2, lb, precision=B.PREC_BF16X3)
-    assert e.value.code == -7
+    lo, hi, _ = W.random_boxes(160, 130, seed=2, min_width=0.001, max_width=0.02)  # two tiles, the second ragged
+    r = g.crown(lo, hi, precision=B.PREC_BF16X3)
+    rows = np.array([0, 5, 127, 128, 129])
+    oc = oracle.crown(p, lo[rows], hi[rows])
+    scale = np.maximum(oc["scale"], 1.0)
+    assert np.all(r["lb"][rows] <= oc["lb"] + 1e-12 * np.abs(oc["lb"]))
+    split = (len(p["dims"]) - 1) * p["H"] * 3.1 * 2.0 ** -16
+    assert np.all(np.abs(r["lb"][rows] + r["margin"][rows] - oc["lb"]) <= (drift_tol(p) + split) * scale)
+    f32 = g.crown(lo, hi)
+    assert np.all(np.abs(r["lb"] - f32["lb"]) <= (drift_tol(p) + split) * np.abs(f32["lb"]))
 
 
 def test_manip_full_batch_sampled(oracle, manip):
