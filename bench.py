@@ -295,6 +295,7 @@ def run_ours(args):
     st.close()
     ttg = None if args.no_time_to_gap else time_to_gap(dev)
     batched = None if args.no_batched else batched_bab(dev)
+    manip = None if args.no_manip else manip_scale(dev)
 
     boxes = st.nb * args.steps * ws
     value = boxes / (ms / 1e3)
@@ -336,7 +337,7 @@ def run_ours(args):
            "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound": statistics.mean(bound_ms)},
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched}
+           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -389,6 +390,61 @@ def run_e2e(st, steps):
     d2h = nb * (2 * 4) + nb * (2 * d * 4 + 8) + 8
     return {"value": nb * steps / (ms / 1e3), "unit": "subdomain-bounds/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h}
+
+
+def manip_scale(dev, reps=3):
+    """Object-manipulation scale (MLP 36-256x4-32, H = 40, 16384 boxes of [-1, 1]^160): 4 BF16 tensor-core
+    rollouts per box (65536 in all, each box's best re-scored in FP32, the incumbent in FP64), interval bounds
+    and the 3-term BF16 tensor-core CROWN, both with the weights streamed through shared memory.  CUDA events
+    around each call after a warm-up; returns milliseconds and rates."""
+    import torch
+    from paper_2412_09584_gb300 import binding as B
+    from paper_2412_09584_gb300 import workloads as W
+    c = W.CONFIGS["manip"]
+    p = W.config_problem("manip", SEED)
+    n, M, H = c["boxes"], c["samples"], c["H"]
+    d = p["k"] * H
+    lo, hi, ids = W.grid_boxes(d, c["grid_dims"])
+    ctx = B.bab_load_dynamics(p["dims"], p["params"], p["s"], p["k"])
+    f = dict(device=dev, dtype=torch.float32)
+    x0, goal = torch.as_tensor(p["x0"]).to(**f), torch.as_tensor(p["goal"]).to(**f)
+    tlo, thi = torch.as_tensor(lo).to(**f), torch.as_tensor(hi).to(**f)
+    tid = torch.as_tensor(ids.astype(np.int64)).to(dev)
+    ub, best_u = torch.empty(n, **f), torch.empty(n, d, **f)
+    inc_val = torch.full((1,), float("inf"), dtype=torch.float64, device=dev)
+    inc_u = torch.zeros(d, **f)
+    lb, lb32 = torch.empty(n, **f), torch.empty(n, **f)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_roll = timed(lambda: B.bab_rollout(ctx, x0, goal, H, p["rho"], tlo, thi, tid, n, M, SEED, B.PREC_BF16, ub,
+                                         best_u, inc_val, inc_u))
+    t_ibp = timed(lambda: B.bab_bound_ibp(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb32))
+    t_tc = timed(lambda: B.bab_bound_crown(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb, precision=B.PREC_BF16X3))
+    t_32 = timed(lambda: B.bab_bound_crown(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb32))
+    sound = bool((lb <= ub).all().item())
+    B.bab_destroy(ctx)
+    macs = sum(a * b for a, b in zip(p["dims"][1:], p["dims"][:-1]))
+    bwd_flop = 2.0 * macs * H * n  # algorithmic backward products of one CROWN call (the pipe runs 3x for the split)
+    return {"workload": f"MLP 36-256x4-32, H={H}, rho={p['rho']}, {n} boxes (2^{c['grid_dims']} grid of [-1,1]^{d}), "
+                        f"{M} rollouts per box", "rollout_bf16_ms": t_roll,
+            "rollout_steps_per_s": n * M * H / (t_roll / 1e3), "ibp_ms": t_ibp,
+            "bound_bf16x3_ms": t_tc, "bound_fp32_ms": t_32,
+            "subdomain_bounds_per_s_bf16x3": n / (t_tc / 1e3), "subdomain_bounds_per_s_fp32": n / (t_32 / 1e3),
+            "crown_backward_tflops_bf16x3": bwd_flop / ((t_tc - t_ibp) / 1e3) / 1e12,
+            "note": "bound times include the interval bounds (ibp_ms); backward TFLOP/s = algorithmic 2 x MACs x H x "
+                    "boxes over (bound - ibp) time; weights streamed through shared memory (they exceed it)",
+            "bounds_below_sampled_ub": sound}
+
 
 
 def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None):
@@ -635,6 +691,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of CUDA-graph replays")
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch heuristics instead of bab_autotune")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-problem BaB section")
+    ap.add_argument("--no-manip", action="store_true", help="skip the object-manipulation-scale section")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")

@@ -127,8 +127,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
     }
 
     const int nlive = live_count(a.n, a.d_n);
-    const int tpb = (a.M + 127) / 128;
-    const long long ntiles = (long long)nlive * tpb;
+    // tiles: a box with M >= 128 samples spans tpb tiles; smaller M packs bpt = 128 / M boxes into a tile
+    const int bpt = a.M >= 128 ? 1 : 128 / a.M;
+    const int tpb = a.M >= 128 ? (a.M + 127) / 128 : 1;
+    const long long ntiles = bpt > 1 ? ((long long)nlive + bpt - 1) / bpt : (long long)nlive * tpb;
     const long long G = (long long)gridDim.x * NSLOT;
     const uint32_t tb = tmem_base;
     const int Dc = N.tc_dcols, Ac = N.tc_acols;
@@ -149,8 +151,18 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
         const int K1 = N.tc_K[1];
         uint32_t phD = 0;
         for (long long tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
-            const int box = (int)(tile / tpb);
-            const int m = (int)(tile % tpb) * 128 + r;
+            int box, m;
+            bool lane_ok;
+            if (bpt > 1) {
+                box = (int)(tile * bpt) + r / a.M;
+                m = r % a.M;
+                lane_ok = r < bpt * a.M && box < nlive;
+                if (!lane_ok) box = (int)(tile * bpt);  // an idle lane computes on a valid box, result unused
+            } else {
+                box = (int)(tile / tpb);
+                m = (int)(tile % tpb) * 128 + r;
+                lane_ok = m < a.M;
+            }
             const uint64_t hb = box_hash(a.seed, a.id[box]);
             const float *blo = a.lo + (size_t)box * a.d, *bhi = a.hi + (size_t)box * a.d;
             float x[SP];
@@ -282,15 +294,21 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
             }
             if (!ok) break;
             if (primary) {
-                // best (f, m) of the warp's 32 rows
-                unsigned long long key =
-                    (m < a.M) ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
+                const unsigned long long key =
+                    lane_ok ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
+                if (bpt > 1) {
+                    // lanes of several boxes: each folds its own sample in
+                    if (lane_ok) atomicMin(&a.keys[box], key);
+                } else {
+                    // best (f, m) of the warp's 32 rows of one box
+                    unsigned long long kb = key;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
-                    key = other < key ? other : key;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, kb, o);
+                        kb = other < kb ? other : kb;
+                    }
+                    if (lane == 0 && kb != ~0ull) atomicMin(&a.keys[box], kb);
                 }
-                if (lane == 0 && key != ~0ull) atomicMin(&a.keys[box], key);
             }
         }
     } else if (warp < mma_warp + NSLOT && lane == 0) {
@@ -423,12 +441,13 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
         __syncthreads();
         int cur = 0;
         for (int l = 1; l <= N.L; ++l) {
-            const int no = N.dims[l], ni = N.dims[l - 1];
-            const float *W = a.raw + N.raw_w[l];
-            const float *b = a.raw + N.raw_b[l];
+            const int no = N.dims[l], ni = N.dims[l - 1], Np = pad4(no);
+            // forward image W_l^T [Kp][Np]: consecutive threads read consecutive outputs
+            const float *Wt = a.fwd + N.fwd_w[l];
+            const float *b = a.fwd + N.fwd_b[l];
             for (int q = threadIdx.x; q < no; q += blockDim.x) {
                 float acc = b[q];
-                for (int c = 0; c < ni; ++c) acc = fmaf(W[(size_t)q * ni + c], act[cur][c], acc);
+                for (int c = 0; c < ni; ++c) acc = fmaf(Wt[(size_t)c * Np + q], act[cur][c], acc);
                 act[cur ^ 1][q] = (l < N.L) ? fmaxf(acc, 0.f) : acc;
             }
             __syncthreads();
@@ -538,7 +557,7 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
         a.stages = 0;
         smem = (size_t)a.tc_bytes + rollout_tc_extra(N);
     }
-    const long long ntiles = (long long)a.n * ((a.M + 127) / 128);
+    const long long ntiles = a.M >= 128 ? (long long)a.n * ((a.M + 127) / 128) : ((long long)a.n + 128 / a.M - 1) / (128 / a.M);
     int grid = (int)((ntiles + nslot - 1) / nslot);
     grid = grid < num_sms ? grid : num_sms;
     k_fill_keys(a.keys, a.n, st);

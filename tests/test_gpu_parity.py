@@ -308,12 +308,15 @@ def test_tc_samples_bit_identical(oracle, gp):
         assert np.array_equal(r["best_u"].view(np.uint32), bu_o.view(np.uint32))
 
 
-@pytest.mark.parametrize("name,M", [("pushing", 256), ("pushing", 300), ("tiny", 256), ("tiny", 77)])
-def test_tc_bf16x3_rollout_matches_oracle(oracle, gp, name, M):
+@pytest.mark.parametrize("name,M,n", [("pushing", 256, 10), ("pushing", 300, 10), ("tiny", 256, 10), ("tiny", 77, 10),
+                                      ("pushing", 4, 130), ("tiny", 48, 37), ("pushing", 33, 9)])
+def test_tc_bf16x3_rollout_matches_oracle(oracle, gp, name, M, n):
+    """Sample tiles of 128 rows: M >= 128 spans several tiles per box; smaller M packs 128 // M boxes per tile
+    (idle rows when M does not divide 128, a ragged last tile)."""
     from paper_2412_09584_gb300 import binding as B
     p = W.config_problem(name, 8)
     d = p["k"] * p["H"]
-    lo, hi, ids = W.dyadic_boxes(d, 10, seed=8, max_depth=3)
+    lo, hi, ids = W.dyadic_boxes(d, n, seed=8, max_depth=3)
     g = gp(p)
     r = g.rollout(lo, hi, ids, M=M, seed=12, precision=B.PREC_BF16X3, incumbent=True)
     ub_o, _, _ = oracle.rollout(p, lo, hi, ids, M, 12)
