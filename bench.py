@@ -414,6 +414,7 @@ def manip_scale(dev, reps=3):
     inc_val = torch.full((1,), float("inf"), dtype=torch.float64, device=dev)
     inc_u = torch.zeros(d, **f)
     lb, lb32 = torch.empty(n, **f), torch.empty(n, **f)
+    B.bab_set_rescore_topk(ctx, 64)  # the configuration re-scores the top 64 BF16 rollouts in FP32
 
     def timed(fn):
         fn()
@@ -436,7 +437,8 @@ def manip_scale(dev, reps=3):
     macs = sum(a * b for a, b in zip(p["dims"][1:], p["dims"][:-1]))
     bwd_flop = 2.0 * macs * H * n  # algorithmic backward products of one CROWN call (the pipe runs 3x for the split)
     return {"workload": f"MLP 36-256x4-32, H={H}, rho={p['rho']}, {n} boxes (2^{c['grid_dims']} grid of [-1,1]^{d}), "
-                        f"{M} rollouts per box", "rollout_bf16_ms": t_roll,
+                        f"{M} BF16 rollouts per box, top 64 re-scored in FP32, incumbent in FP64",
+            "rollout_bf16_ms": t_roll,
             "rollout_steps_per_s": n * M * H / (t_roll / 1e3), "ibp_ms": t_ibp,
             "bound_bf16x3_ms": t_tc, "bound_fp32_ms": t_32,
             "subdomain_bounds_per_s_bf16x3": n / (t_tc / 1e3), "subdomain_bounds_per_s_fp32": n / (t_32 / 1e3),

@@ -359,6 +359,17 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  * BAB_ERR_INVALID_ARG for an unknown kernel or variant; a variant whose tile
  * does not fit the network makes the later call fail with BAB_ERR_CUDA.
  */
+/*
+ * BF16 rollouts (BAB_PREC_BF16): after the tensor-core pass, ub[i] is the BF16
+ * objective of box i's best sample.  With k = 0 (the default) every box's best
+ * sample is then re-scored in FP32, so every ub is an FP32 objective value;
+ * with k > 0 only the k boxes with the smallest BF16 ub (ties by id) are, the
+ * others keep the BF16 value (about 1e-2 relative).  The incumbent is always
+ * re-scored in FP64 from the box of smallest ub, so inc_val stays exact.
+ * Errors: BAB_ERR_INVALID_ARG for k < 0.
+ */
+int bab_set_rescore_topk(bab_ctx *ctx, int k);
+
 #define BAB_KERNEL_ROLLOUT_FP32 0
 #define BAB_KERNEL_ALPHA_FUSED 1
 #define BAB_KERNEL_ROLLOUT_TC 2

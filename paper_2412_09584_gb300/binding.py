@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.bab_prune_branch_batch.argtypes = [_P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _F, _I, _I, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.bab_set_variant.argtypes = [_P, _I, _I]
+    L.bab_set_rescore_topk.argtypes = [_P, _I]
     L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
     L.bab_autotune.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _I, _I, _P]
     _lib = L
@@ -227,6 +228,10 @@ def bab_alpha_optimize(ctx, x0, goal, horizon, rho, lo, hi, n, steps, lr, lb_bes
 
 def bab_set_variant(ctx, kernel, variant):
     _check(ctx, load().bab_set_variant(ctx, int(kernel), int(variant)))
+
+
+def bab_set_rescore_topk(ctx, k):
+    _check(ctx, load().bab_set_rescore_topk(ctx, int(k)))
 
 
 def bab_get_variant(ctx, kernel):

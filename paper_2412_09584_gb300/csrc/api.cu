@@ -29,6 +29,7 @@ struct bab_ctx {
     int tune_alpha_fused = -1;  // -2: the unfused loop of bound, adjoint and Adam launches
     int tune_rollout_tc = -1;   // tiles per CTA
     int tune_crown_tc = -1;     // tiles per CTA
+    int rescore_topk = 0;       // BF16 rollouts: FP32 re-score of the topk smallest ub (0: every box)
     char err[512] = {0};
 };
 
@@ -415,9 +416,12 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
         return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout needs hidden widths that are multiples of 32, "
                                             "s <= 32, s + k <= 64 and a weight image that fits in shared memory");
     if (n == 0) return BAB_OK;
-    rc = ensure_scratch(c, (size_t)n * sizeof(unsigned long long) + 256);
+    const size_t key_bytes = ((size_t)n * sizeof(unsigned long long) + 255) & ~size_t(255);
+    rc = ensure_scratch(c, key_bytes + 512);
     if (rc) return rc;
     RolloutArgs a{};
+    a.topk = precision == BAB_PREC_BF16 ? c->rescore_topk : 0;
+    a.topk_t = reinterpret_cast<unsigned long long *>(static_cast<char *>(c->scratch) + key_bytes);
     a.net = c->net;
     a.batch.P = 1;
     a.batch.Hmax = H;
@@ -932,6 +936,15 @@ int bab_set_variant(bab_ctx *c, int kernel, int variant)
             return fail(c, BAB_ERR_INVALID_ARG, "unknown kernel %d", kernel);
     }
     return fail(c, BAB_ERR_INVALID_ARG, "variant %d out of range for kernel %d", variant, kernel);
+}
+
+int bab_set_rescore_topk(bab_ctx *c, int k)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (k < 0) return fail(c, BAB_ERR_INVALID_ARG, "k must be >= 0");
+    c->rescore_topk = k;
+    return BAB_OK;
 }
 
 int bab_get_variant(bab_ctx *c, int kernel, int *variant)

@@ -30,6 +30,7 @@
 
 #include "bab_internal.cuh"
 #include "kernels.cuh"
+#include "select.cuh"
 #include "tc_ptx.cuh"
 
 namespace bab {
@@ -417,13 +418,38 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
     }
 }
 
-// Per box: ub and best_u from the packed minimum; in BF16 mode the chosen
-// sample is re-scored in FP32 on CUDA cores (one CTA per box).
+// BF16 mode: the threshold (order(ub), id) of the topk smallest BF16 upper bounds.
+__global__ void __launch_bounds__(1024) k_topk_select(RolloutArgs a)
+{
+    __shared__ unsigned hist[256];
+    __shared__ uint32_t sh_pk;
+    __shared__ uint64_t sh_pid;
+    __shared__ int sh_rem, sh_done;
+    const int n = live_count(a.n, a.d_n);
+    const int K = a.topk < n ? a.topk : n;
+    const Thresh T = radix_select(n, a.ub, a.id, [](int) { return true; }, K, hist, &sh_pk, &sh_pid, &sh_rem,
+                                  &sh_done);
+    if (threadIdx.x == 0) {
+        a.topk_t[0] = T.key;
+        a.topk_t[1] = T.id;
+        a.topk_t[2] = T.none ? 1ull : 0ull;
+    }
+}
+
+// BF16 mode: the chosen sample of a box is re-scored in FP32 on CUDA cores (one
+// CTA per box), for every box or for the topk of smallest BF16 ub.
 __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
 {
     const NetDesc &N = a.net;
     const int box = blockIdx.x;
     if (box >= live_count(a.n, a.d_n)) return;
+    if (a.topk > 0) {
+        Thresh T;
+        T.key = (uint32_t)a.topk_t[0];
+        T.id = a.topk_t[1];
+        T.none = a.topk_t[2] != 0;
+        if (!le_thresh(float_order(a.ub[box]), a.id[box], T)) return;
+    }
     __shared__ float act[2][kMaxWidth + 4];
     __shared__ float xs[kMaxWidth];
     __shared__ float f_sh;
@@ -569,10 +595,10 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
                                        : launch_tc_shape<1, 32>(a, nslot, stream, grid, smem, st);
     else return cudaErrorInvalidConfiguration;
     if (e != cudaSuccess) return e;
+    launch_rollout_finalize(a, st);  // ub and best_u from the packed minima
     if (split == 1) {
+        if (a.topk > 0) k_topk_select<<<1, 1024, 0, st>>>(a);
         k_rescore_fp32<<<a.n, 256, 0, st>>>(a);
-    } else {
-        launch_rollout_finalize(a, st);
     }
     if (a.inc_val) launch_incumbent(a, st);
     return cudaGetLastError();

@@ -326,6 +326,27 @@ def test_tc_bf16x3_rollout_matches_oracle(oracle, gp, name, M, n):
     assert r["inc_val"] == pytest.approx(oracle.objective(p, r["inc_u"].astype(np.float64)), rel=1e-10)
 
 
+def test_tc_bf16_rollout_topk_rescore(oracle, gp):
+    """With a top-k re-score, the k boxes of smallest BF16 ub get the FP32 objective of their best sample, the
+    others keep their BF16 value (close to it); the incumbent stays the FP64 objective of its plan."""
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem("pushing", 10)
+    lo, hi, ids = W.dyadic_boxes(40, 40, seed=10, max_depth=4)
+    g = gp(p)
+    r_all = g.rollout(lo, hi, ids, M=64, seed=17, precision=B.PREC_BF16)
+    B.bab_set_rescore_topk(g.ctx, 8)
+    r = g.rollout(lo, hi, ids, M=64, seed=17, precision=B.PREC_BF16, incumbent=True)
+    np.testing.assert_array_equal(r["best_u"], r_all["best_u"])  # the same samples are chosen
+    f_best = np.array([oracle.objective(p, u.astype(np.float64)) for u in r["best_u"]])
+    rescored = np.isclose(r["ub"], r_all["ub"], rtol=0, atol=0)
+    assert rescored.sum() >= 8
+    np.testing.assert_allclose(r["ub"][rescored], f_best[rescored], rtol=REL)
+    np.testing.assert_allclose(r["ub"], f_best, rtol=5e-2)
+    assert r["inc_val"] == pytest.approx(oracle.objective(p, r["inc_u"].astype(np.float64)), rel=1e-10)
+    with pytest.raises(B.BabError):
+        B.bab_set_rescore_topk(g.ctx, -1)
+
+
 def test_tc_bf16_rollout_rescored(oracle, gp):
     """BF16 operands pick each box's best sample; its value is then re-scored in FP32, so ub equals the objective
     of the returned plan to FP32 accuracy and is close to the best sampled value."""
