@@ -157,6 +157,7 @@ class BabState:
         self.n_live_dev = torch.tensor([n0], dtype=torch.int32, device=device)
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
         self.ev = []
+        self.side = torch.cuda.Stream(device=device)
         self.variants = None
         if autotune:
             # tile shapes timed on the starting pool (outside any timed region)
@@ -165,9 +166,10 @@ class BabState:
             names = {"rollout_fp32": B.KERNEL_ROLLOUT_FP32, "alpha_fused": B.KERNEL_ALPHA_FUSED,
                      "rollout_tc_tiles_per_cta": B.KERNEL_ROLLOUT_TC, "crown_tc_tiles_per_cta": B.KERNEL_CROWN_TC}
             self.variants = {k: B.bab_get_variant(self.ctx, v) for k, v in names.items()}
-        # initial search and bound of the starting pool (Algorithm 2, lines 2-3)
+        # Algorithm 2 starts by searching and bounding the starting pool
         self.search_and_bound(P, n0, None)
         fused = alpha_steps and self.bprec == B.PREC_FP32 and (self.variants or {}).get("alpha_fused", -1) != -2
+        # prune/branch 2, rollout 4 (keys, rollout, finalize, incumbent), bound 2 (or the alpha loop)
         self.launches_per_step = 2 + 4 + (2 if not alpha_steps else (2 if fused else 3 + alpha_steps * 3))
 
     def _alloc(self):
@@ -183,9 +185,15 @@ class BabState:
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
         B.bab_rollout(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
-                      self.seed, self.rprec, P["ub"], self.best_u, self.inc_val, self.inc_u, d_n=d_n)
+                      self.seed, self.rprec, P["ub"], self.best_u, d_n=d_n)
         if events:
             e[1].record()
+        # the FP64 incumbent re-score runs on a side stream, beside the bounds of the same boxes
+        main = torch.cuda.current_stream()
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            B.bab_update_incumbent(self.ctx, self.x0, self.goal, self.H, self.rho, P["ub"], self.best_u, n,
+                                   self.inc_val, self.inc_u, d_n=d_n)
         if not self.alpha_steps:
             B.bab_bound_crown(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n, P["lb"],
                               precision=self.bprec, margin=self.margin, d_n=d_n)
@@ -195,6 +203,7 @@ class BabState:
         if events:
             e[2].record()
             self.ev.append(e)
+        main.wait_stream(self.side)  # the next prune reads the incumbent
 
     def step(self, events=False):
         B = self.B

@@ -112,7 +112,7 @@ const char *bab_last_error(const bab_ctx *ctx);
  *   samples    M >= 1.  precision: BAB_PREC_FP32, BAB_PREC_BF16X3 or BAB_PREC_BF16.
  *   ub         device float[n]; best_u device float[n][d] (nullable).
  *   inc_val, inc_u (both nullable, device double[1], float[d]): the incumbent
- *              of Algorithm 2 (lines 10-11).  If given, the box with the
+ *              of Algorithm 2 (its incumbent update).  If given, the box with the
  *              smallest ub (lowest index on ties) has its best_u re-evaluated
  *              in FP64 on the GPU, and if that value is below *inc_val the
  *              pair (*inc_val, inc_u) is replaced by it.  Requires best_u.
@@ -122,6 +122,19 @@ const char *bab_last_error(const bab_ctx *ctx);
 int bab_rollout(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
                 const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
                 int precision, float *ub, float *best_u, double *inc_val, float *inc_u, void *stream);
+
+/*
+ * The incumbent step of Algorithm 2 on its own (bab_rollout does it when given
+ * inc_val): the box with the smallest ub (lowest index on ties) has its plan
+ * best_u re-evaluated in FP64; if that value is below *inc_val it becomes the
+ * incumbent (inc_val, inc_u).  A separate call lets the FP64 re-score run on
+ * another stream, concurrently with the bounds of the same boxes.
+ *   ub device float[n], best_u device float[n][k H] (from bab_rollout).
+ *   inc_val device double[1], inc_u device float[k H]: read and updated.
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_CUDA.
+ */
+int bab_update_incumbent(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *ub,
+                         const float *best_u, int n, const int *d_n, double *inc_val, float *inc_u, void *stream);
 
 /*
  * Interval bound propagation through the unrolled dynamics: the intermediate

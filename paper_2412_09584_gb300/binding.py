@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.bab_bound_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _I, _P, _I, _F, _P, _P, _P]
     L.bab_prune_branch_batch.argtypes = [_P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _F, _I, _I, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.bab_update_incumbent.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P]
     L.bab_set_variant.argtypes = [_P, _I, _I]
     L.bab_set_rescore_topk.argtypes = [_P, _I]
     L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
@@ -295,4 +296,13 @@ def bab_prune_branch_batch(ctx, d_stride, horizon, max_horizon, lo, hi, lb, ub, 
         float(eta), int(split_rule), int(cap_out), _ptr(out_lo, f32), _ptr(out_hi, f32), _ptr(out_lb, f32),
         _ptr(out_ub, f32), _ptr(out_id, torch.uint64), _ptr(out_prob, i32), _ptr(keep, torch.uint8),
         _ptr(d_counts, i32, "d_counts"), _ptr(d_pcounts, i32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_update_incumbent(ctx, x0, goal, horizon, rho, ub, best_u, n, inc_val, inc_u, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_update_incumbent(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                                     _ptr(ub, f32, "ub"), _ptr(best_u, f32, "best_u"), int(n), _ptr(d_n, torch.int32),
+                                     _ptr(inc_val, torch.float64, "inc_val"), _ptr(inc_u, f32, "inc_u"),
+                                     _stream(stream))
     _check(ctx, rc)

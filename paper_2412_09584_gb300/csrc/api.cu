@@ -454,6 +454,39 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     return BAB_OK;
 }
 
+int bab_update_incumbent(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *ub,
+                         const float *best_u, int n, const int *d_n, double *inc_val, float *inc_u, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (!x0 || !goal || !inc_val || !inc_u) return fail(c, BAB_ERR_INVALID_ARG, "x0, goal, inc_val and inc_u are required");
+    if (H < 1 || H > (1 << 20) || n < 0) return fail(c, BAB_ERR_SHAPE, "bad horizon or n");
+    if (!(rho >= 0.f) || !std::isfinite(rho)) return fail(c, BAB_ERR_INVALID_ARG, "rho must be finite and >= 0");
+    if (n > 0 && (!ub || !best_u)) return fail(c, BAB_ERR_INVALID_ARG, "ub and best_u are required");
+    if (n == 0) return BAB_OK;
+    RolloutArgs a{};
+    a.net = c->net;
+    a.batch.P = 1;
+    a.batch.Hmax = H;
+    a.raw = c->d_raw;
+    a.x0 = x0;
+    a.goal = goal;
+    a.n = n;
+    a.d_n = d_n;
+    a.H = H;
+    a.d = c->net.k * H;
+    a.rho = rho;
+    a.ub = const_cast<float *>(ub);
+    a.best_u = const_cast<float *>(best_u);
+    a.inc_val = inc_val;
+    a.inc_u = inc_u;
+    a.status = c->d_status;
+    launch_incumbent(a, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "incumbent kernel");
+    return BAB_OK;
+}
+
 int bab_bound_ibp(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
                   int n, const int *d_n, float *lb_ibp, float *pre_lo, float *pre_hi, float *x_lo, float *x_hi,
                   void *stream)

@@ -1,5 +1,5 @@
 // rollout.cu -- sampled search (Section 3.3, batch_search with uniform samples)
-// and the FP64 incumbent re-score (Algorithm 2, lines 10-11).
+// and the FP64 incumbent re-score (the incumbent update of Algorithm 2).
 //
 // k_rollout_fp32: a persistent kernel.  A tile is R samples of one box; a CTA
 // keeps the whole forward network image in shared memory for all H steps and

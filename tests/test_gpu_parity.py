@@ -411,3 +411,22 @@ def test_crown_tc_given_alpha_and_zero_width(oracle, gp):
     f = np.array([oracle.objective(q, z[i].astype(np.float64)) for i in range(6)])
     assert np.all(rz["lb"] <= f)
     np.testing.assert_allclose(rz["lb"] + rz["margin"], f, rtol=REL_TC)
+
+
+def test_update_incumbent_matches_rollout_incumbent(gp):
+    """The incumbent step as its own call (on another stream) equals the one bab_rollout performs."""
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem("pushing", 12)
+    lo, hi, ids = W.dyadic_boxes(40, 33, seed=12, max_depth=4)
+    g = gp(p)
+    r = g.rollout(lo, hi, ids, M=128, seed=21, precision=B.PREC_BF16X3, incumbent=True)
+    r2 = g.rollout(lo, hi, ids, M=128, seed=21, precision=B.PREC_BF16X3)
+    inc_val = torch.full((1,), np.inf, dtype=torch.float64, device=DEV)
+    inc_u = torch.zeros(g.d, device=DEV)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        B.bab_update_incumbent(g.ctx, g.x0, g.goal, g.H, g.rho, T(r2["ub"]), T(r2["best_u"]), 33, inc_val, inc_u)
+    torch.cuda.synchronize()
+    assert float(inc_val.item()) == r["inc_val"]
+    np.testing.assert_array_equal(inc_u.cpu().numpy(), r["inc_u"])
