@@ -23,6 +23,8 @@
  *                         Theorem 2 (concretization) in box form.
  *   oracle_alpha_grad     d(lower bound)/d(alpha) for the free lower slopes of
  *                         Lemma 1, by a forward pass of the relaxed network.
+ *   oracle_box_grad       d(lower bound)/d(box faces), through the relaxation
+ *                         choices and the interval bounds.
  *   oracle_adam_ascent    projected Adam ascent on alpha.
  *   oracle_prune_branch   Section 3 overview (prune when lower > incumbent),
  *                         Section 3.1 batch_pick_out and batch_split (bisection
@@ -618,6 +620,180 @@ int oracle_alpha_grad(int L, const int *dims, const double *params, int s, int k
     free(xu);
     free(at);
     free(us);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the bound with respect to the box                             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * With the relaxation choices fixed (which neurons are stable, which linear
+ * bound each unstable one uses), the bound is the relaxed network's objective
+ * at the concretizing point u*, min over the box of a function of u whose
+ * parameters are: the box itself, the upper chords D z + c of unstable neurons
+ * whose coefficient A < 0 (D = u/(u - l), c = -u l/(u - l) with [l, u] the
+ * neuron's interval bounds), and the tangent points m = (L + U)/2 of the cost
+ * terms (L, U the interval of x_{t,i} - g_i).  At a minimiser the derivative
+ * of the minimum with respect to a parameter is the partial derivative of the
+ * objective there, so (a.e., with z~, x~ the relaxed network's values at u*):
+ *   chord neuron:  dLB/dD = A z~,  dLB/dc = A, hence
+ *                  dLB/du = A l (l - z~)/(u - l)^2,  dLB/dl = A u (z~ - u)/(u - l)^2;
+ *   tangent:       dLB/dm = 2 (x~ - g - m), and dm/dL = dm/dU = 1/2;
+ *   box face:      dLB/dlo_j = mu_j + 2 rho lo_j when u*_j sits on lo_j (for
+ *                  rho > 0: -mu_j/(2 rho) <= lo_j; for rho = 0: mu_j >= 0), and
+ *                  the same at hi_j; 0 in the interior.
+ * The interval bounds are themselves piecewise-linear functions of the box
+ * (ibp_box: z_lo = W+ a_lo + W- a_hi + b, z_hi = W+ a_hi + W- a_lo + b, the
+ * ReLU passing a derivative only where its end is positive, x_{t+1} = x_t +
+ * z_L), so their sensitivities are carried back to the box by the transposed
+ * steps.  Outputs: lb [n] and grad_lo, grad_hi [n][d].  The gradient is the
+ * derivative of the bound with alpha held fixed (alpha nullable: adaptive,
+ * piecewise constant in the bounds).
+ */
+int oracle_box_grad(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                    const double *x0, const double *goal, int n, const double *lo, const double *hi,
+                    const double *alpha, double *lb, double *grad_lo, double *grad_hi)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    int d = k * H, sumh = N.sumh;
+    size_t nh = (size_t)H * sumh, nx = (size_t)(H + 1) * s;
+    double *pl = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *pu = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *Ap = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *zt = (double *)malloc(sizeof(double) * (nh ? nh : 1));   /* relaxed pre-activations at u* */
+    double *gl = (double *)malloc(sizeof(double) * (nh ? nh : 1));   /* dLB / d pre_lo */
+    double *gu = (double *)malloc(sizeof(double) * (nh ? nh : 1));   /* dLB / d pre_hi */
+    double *xl = (double *)malloc(sizeof(double) * nx);
+    double *xu = (double *)malloc(sizeof(double) * nx);
+    double *gx = (double *)calloc(nx, sizeof(double));                 /* dLB / d x_lo = dLB / d x_hi (tangents) */
+    double *at = (double *)malloc(sizeof(double) * nx);
+    double *us = (double *)malloc(sizeof(double) * d);
+    double *mu = (double *)malloc(sizeof(double) * d);
+    for (int i = 0; i < n; ++i) {
+        const double *bl = lo + (size_t)i * d, *bh = hi + (size_t)i * d;
+        const double *al = alpha ? alpha + (size_t)i * nh : NULL;
+        double *glo = grad_lo + (size_t)i * d, *ghi = grad_hi + (size_t)i * d;
+        ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, mu, us, Ap, at);
+        lb[i] = o.lb;
+
+        /* relaxed network from x_0 and u*: z~ and the state x~_t, and the sensitivities */
+        double x[ORC_MAX_WIDTH], a[ORC_MAX_WIDTH], z[ORC_MAX_WIDTH];
+        memset(gx, 0, sizeof(double) * nx);
+        for (int q = 0; q < s; ++q) x[q] = x0[q];
+        for (int t = 0; t < H; ++t) {
+            for (int q = 0; q < s; ++q) a[q] = x[q];
+            for (int j = 0; j < k; ++j) a[s + j] = us[t * k + j];
+            for (int l = 1; l <= L; ++l) {
+                int no = N.dims[l], ni = N.dims[l - 1];
+                for (int r = 0; r < no; ++r) {
+                    double acc = N.b[l][r];
+                    for (int c = 0; c < ni; ++c) acc += N.W[l][(size_t)r * ni + c] * a[c];
+                    z[r] = acc;
+                }
+                if (l < L) {
+                    for (int r = 0; r < no; ++r) {
+                        size_t idx = (size_t)t * sumh + N.hoff[l] + r;
+                        double zl = pl[idx], zu = pu[idx];
+                        double alj = al ? al[idx] : adaptive_alpha(zl, zu);
+                        int lower = Ap[idx] >= 0.0;
+                        double D, c;
+                        oracle_relu_relax(zl, zu, alj, lower ? 0 : 1, &D, &c);
+                        zt[idx] = z[r];
+                        gl[idx] = gu[idx] = 0.0;
+                        if (zl < 0.0 && zu > 0.0 && !lower) {
+                            double w2 = (zu - zl) * (zu - zl);
+                            gu[idx] = Ap[idx] * zl * (zl - z[r]) / w2;
+                            gl[idx] = Ap[idx] * zu * (z[r] - zu) / w2;
+                        }
+                        a[r] = D * z[r] + c;
+                    }
+                }
+            }
+            for (int q = 0; q < s; ++q) {
+                x[q] += z[q];
+                double m = 0.5 * at[(size_t)(t + 1) * s + q];
+                gx[(size_t)(t + 1) * s + q] = (x[q] - goal[q]) - m;
+            }
+        }
+
+        /* the interval bounds' sensitivities carried back to the box */
+        double Gxl[ORC_MAX_WIDTH], Gxh[ORC_MAX_WIDTH], Gal[ORC_MAX_WIDTH], Gah[ORC_MAX_WIDTH];
+        double Gzl[ORC_MAX_WIDTH], Gzh[ORC_MAX_WIDTH];
+        for (int q = 0; q < s; ++q) Gxl[q] = Gxh[q] = gx[(size_t)H * s + q];
+        for (int j = 0; j < d; ++j) glo[j] = ghi[j] = 0.0;
+        for (int t = H - 1; t >= 0; --t) {
+            /* x_{t+1} = x_t + z_L */
+            for (int q = 0; q < s; ++q) {
+                Gzl[q] = Gxl[q];
+                Gzh[q] = Gxh[q];
+            }
+            for (int l = L; l >= 1; --l) {
+                int no = N.dims[l], ni = N.dims[l - 1];
+                if (l < L) {
+                    /* a_l = max(z_l, 0) at each end, plus the bounds' own sensitivities */
+                    for (int r = 0; r < no; ++r) {
+                        size_t idx = (size_t)t * sumh + N.hoff[l] + r;
+                        Gzl[r] = (pl[idx] > 0.0 ? Gal[r] : 0.0) + gl[idx];
+                        Gzh[r] = (pu[idx] > 0.0 ? Gah[r] : 0.0) + gu[idx];
+                    }
+                }
+                for (int c = 0; c < ni; ++c) {
+                    double sl = 0.0, sh = 0.0;
+                    for (int r = 0; r < no; ++r) {
+                        double w = N.W[l][(size_t)r * ni + c];
+                        if (w >= 0.0) {
+                            sl += w * Gzl[r];
+                            sh += w * Gzh[r];
+                        } else {
+                            sl += w * Gzh[r];
+                            sh += w * Gzl[r];
+                        }
+                    }
+                    Gal[c] = sl;
+                    Gah[c] = sh;
+                }
+            }
+            /* a_0 = [x_t; u_t]: the box coordinates of step t, and x_t (residual path, tangent at t) */
+            for (int j = 0; j < k; ++j) {
+                glo[t * k + j] += Gal[s + j];
+                ghi[t * k + j] += Gah[s + j];
+            }
+            for (int q = 0; q < s; ++q) {
+                double tg = t >= 1 ? gx[(size_t)t * s + q] : 0.0;
+                Gxl[q] = Gxl[q] + Gal[q] + tg;
+                Gxh[q] = Gxh[q] + Gah[q] + tg;
+            }
+        }
+        /* the concretization's direct dependence on the faces */
+        for (int j = 0; j < d; ++j) {
+            int at_lo, at_hi;
+            if (rho > 0.0) {
+                double uc = -mu[j] / (2.0 * rho);
+                at_lo = uc <= bl[j];
+                at_hi = !at_lo && uc >= bh[j];
+            } else {
+                at_lo = mu[j] >= 0.0;
+                at_hi = !at_lo;
+            }
+            if (at_lo) glo[j] += mu[j] + 2.0 * rho * bl[j];
+            if (at_hi) ghi[j] += mu[j] + 2.0 * rho * bh[j];
+        }
+    }
+    free(pl);
+    free(pu);
+    free(Ap);
+    free(zt);
+    free(gl);
+    free(gu);
+    free(xl);
+    free(xu);
+    free(gx);
+    free(at);
+    free(us);
+    free(mu);
     return 0;
 }
 

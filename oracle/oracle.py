@@ -212,6 +212,23 @@ def alpha_grad(problem, lo, hi, alpha=None):
     return lb, g[:, :, :net.sumh], robj
 
 
+def box_grad(problem, lo, hi, alpha=None):
+    """(lb, dlb/dlo [n,d], dlb/dhi [n,d]) per box, alpha held fixed (None: adaptive slopes)."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _d(lo)
+    hi, phi = _d(hi)
+    n, d = lo.shape
+    alpha_a, palpha = _optd(alpha)
+    lb = np.zeros(n)
+    glo = np.zeros((n, d))
+    ghi = np.zeros((n, d))
+    rc = lib().oracle_box_grad(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi, palpha,
+                               lb.ctypes.data_as(_c_double_p), glo.ctypes.data_as(_c_double_p),
+                               ghi.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return lb, glo, ghi
+
+
 def adaptive_alpha(problem, lo, hi):
     """The adaptive lower slopes (1 where u >= -l, else 0) of every neuron, from the oracle's IBP bounds."""
     _, pl, pu, _, _ = ibp(problem, lo, hi)

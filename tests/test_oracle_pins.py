@@ -529,3 +529,78 @@ def test_bab_end_to_end_against_grid(oracle):
         assert h["global_lb"] <= min(fgrid, inc) + 1e-12 or h["pool"] == 0
     # grid resolution 0.005; the objective's slope is O(10): allow 0.05 + 1e-6
     assert inc <= fgrid + 0.05
+
+
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_box_gradient_central_fd(oracle, adaptive):
+    """d(bound)/d(box faces) against central differences of the oracle's own bound, at coordinates where no
+    relaxation choice, ReLU mask of the interval bounds, adaptive slope or concretization face changes inside the
+    stencil (the bound is piecewise smooth in the box)."""
+    p = scaled_problem(4, 2, [32, 32], 5, 0.01, seed=61, scale=0.3)
+    lo, hi, _ = W.random_boxes(10, 4, seed=62, min_width=0.3, max_width=0.8)
+    rng = np.random.default_rng(9)
+    alpha = None if adaptive else rng.uniform(0.05, 0.95, size=(4, 5, 64))
+    lb, glo, ghi = oracle.box_grad(p, lo, hi, alpha)
+    np.testing.assert_allclose(lb, oracle.crown(p, lo, hi, alpha)["lb"], rtol=1e-13)
+
+    def pattern(l_, h_, a_):
+        r = oracle.crown(p, l_, h_, a_)
+        _, pl, pu, _, _ = oracle.ibp(p, l_, h_)
+        face = np.where(r["ustar"] == l_, 1, np.where(r["ustar"] == h_, 2, 0))
+        return r["lb"][0], np.concatenate([np.sign(r["A_pre"]).ravel(), (pl > 0).ravel(), (pu > 0).ravel(),
+                                           (pu >= -pl).ravel(), face.ravel()])
+
+    eps = 1e-6
+    checked = 0
+    for _ in range(400):
+        i, j, side = rng.integers(4), rng.integers(10), rng.integers(2)
+        a_i = None if alpha is None else alpha[i:i + 1]
+        lp, hp = lo[i:i + 1].astype(np.float64).copy(), hi[i:i + 1].astype(np.float64).copy()
+        lm, hm = lp.copy(), hp.copy()
+        (lp if side == 0 else hp)[0, j] += eps
+        (lm if side == 0 else hm)[0, j] -= eps
+        fp, sp = pattern(lp, hp, a_i)
+        fm, sm = pattern(lm, hm, a_i)
+        _, s0 = pattern(lo[i:i + 1].astype(np.float64), hi[i:i + 1].astype(np.float64), a_i)
+        if not (np.array_equal(sp, sm) and np.array_equal(sp, s0)):
+            continue  # a piece boundary inside the stencil: kink, skip
+        g = (glo if side == 0 else ghi)[i, j]
+        assert g == pytest.approx((fp - fm) / (2 * eps), rel=1e-5, abs=1e-7), (i, j, side)
+        checked += 1
+        if checked == 24:
+            break
+    assert checked == 24
+
+
+def test_box_gradient_stable_one_step_closed_form(oracle):
+    """One step of a network whose ReLUs are all stable on the box (an affine map there), rho = 0: the bound is
+    f_lin(lo, hi) = sum_i [2 m_i (c_i - g_i) - m_i^2] + sum_j min(mu_j lo_j, mu_j hi_j), with x_1 = c + B u,
+    m = c - g + B (lo + hi)/2 (the tangent point: the interval of x_1 - g is exact for an affine map) and
+    mu = 2 B^T m.  Its derivative, worked out by hand:
+        d/dlo_j = sum_i (c_i - g_i - m_i) B_ij + [mu_j >= 0] mu_j + sum_k (B^T B)_kj u*_k,
+    and the same for hi_j with [mu_j < 0]."""
+    s_, k = 3, 2
+    p = stable_problem(s_, k, 1, 71, 0.6, 0.5)
+    lo, hi, _ = W.random_boxes(k, 3, seed=72, min_width=0.2, max_width=0.8)
+    _, pl, pu, _, _ = oracle.ibp(p, lo, hi)
+    assert not ((pl < 0) & (pu > 0)).any()
+    (W1, b1), (W2, b2), (W3, b3) = W.unpack_params(p)
+    W1, W2, W3 = W1.astype(np.float64), W2.astype(np.float64), W3.astype(np.float64)
+    D1, D2 = np.diag((b1 > 0).astype(float)), np.diag((b2 > 0).astype(float))
+    J = W3 @ D2 @ W2 @ D1 @ W1                      # the affine network's Jacobian on the box
+    x0, g = p["x0"].astype(np.float64), p["goal"].astype(np.float64)
+    a0 = np.concatenate([x0, np.zeros(k)])
+    z0 = W3 @ np.maximum(W2 @ np.maximum(W1 @ a0 + b1, 0) + b2, 0) + b3
+    c = x0 + z0                                    # x_1 at u = 0
+    B = J[:, s_:]
+    lb, glo, ghi = oracle.box_grad(p, lo, hi)
+    for i in range(3):
+        m = c - g + B @ (lo[i] + hi[i]) / 2
+        mu = 2 * B.T @ m
+        ustar = np.where(mu >= 0, lo[i], hi[i])
+        f = np.sum(2 * m * (c - g) - m * m) + np.sum(np.minimum(mu * lo[i], mu * hi[i]))
+        assert lb[i] == pytest.approx(f, rel=1e-10, abs=1e-12)
+        common = B.T @ (c - g - m) + (B.T @ B) @ ustar
+        tol = 1e-10 * max(np.abs(B).sum() * np.abs(m).max(), np.abs(mu).max(), 1.0)  # FP64 cancellation scale
+        np.testing.assert_allclose(glo[i], common + np.where(mu >= 0, mu, 0), rtol=1e-9, atol=tol)
+        np.testing.assert_allclose(ghi[i], common + np.where(mu < 0, mu, 0), rtol=1e-9, atol=tol)
