@@ -215,6 +215,26 @@ int bab_alpha_grad(bab_ctx *ctx, const float *x0, const float *goal, int horizon
                    float *grad_alpha, void *stream);
 
 /*
+ * The bound and its gradient with respect to the box faces, FP32: d lb[i] /
+ * d lo[i][j] and d lb[i] / d hi[i][j] with the slopes alpha held fixed (alpha
+ * nullable: adaptive), almost everywhere (the bound is piecewise smooth in the
+ * box).  The relaxation choices of Lemma 1 held fixed, the bound is the
+ * minimum over the box of the relaxed network's objective (Theorems 1-2), so
+ * it moves with each parameter of that objective as the objective's partial
+ * derivative at the concretizing point: the upper chords of unstable neurons
+ * and the tangent points of the cost (functions of the interval bounds, which
+ * are functions of the box), and the box faces themselves where u* sits on
+ * them.  No counterpart in the paper, which differentiates neither.
+ *   alpha      device float[n][H][sumh] (nullable).
+ *   lb         device float[n]: the bound (margin subtracted), as bab_bound_crown.
+ *   grad_lo, grad_hi  device float[n][k H].
+ * Errors: as bab_bound_crown.
+ */
+int bab_box_grad(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                 const float *hi, int n, const int *d_n, const float *alpha, float *lb, float *grad_lo,
+                 float *grad_hi, void *stream);
+
+/*
  * alpha-CROWN in one call: `steps` rounds of bab_alpha_step from the adaptive
  * slopes, with the interval bounds (which do not depend on alpha) computed
  * once, and the Adam moments in context scratch.  lb_best[i] receives the

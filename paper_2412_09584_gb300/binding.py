@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.bab_prune_branch_batch.argtypes = [_P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _F, _I, _I, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.bab_update_incumbent.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P]
+    L.bab_box_grad.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _P]
     L.bab_set_variant.argtypes = [_P, _I, _I]
     L.bab_set_rescore_topk.argtypes = [_P, _I]
     L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
@@ -305,4 +306,13 @@ def bab_update_incumbent(ctx, x0, goal, horizon, rho, ub, best_u, n, inc_val, in
                                      _ptr(ub, f32, "ub"), _ptr(best_u, f32, "best_u"), int(n), _ptr(d_n, torch.int32),
                                      _ptr(inc_val, torch.float64, "inc_val"), _ptr(inc_u, f32, "inc_u"),
                                      _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_box_grad(ctx, x0, goal, horizon, rho, lo, hi, n, lb, grad_lo, grad_hi, alpha=None, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_box_grad(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                             _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), int(n), _ptr(d_n, torch.int32),
+                             _ptr(alpha, f32), _ptr(lb, f32, "lb"), _ptr(grad_lo, f32, "grad_lo"),
+                             _ptr(grad_hi, f32, "grad_hi"), _stream(stream))
     _check(ctx, rc)

@@ -653,6 +653,37 @@ int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float 
     return BAB_OK;
 }
 
+int bab_box_grad(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                 int n, const int *d_n, const float *alpha, float *lb, float *grad_lo, float *grad_hi, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (n > 0 && (!lb || !grad_lo || !grad_hi)) return fail(c, BAB_ERR_INVALID_ARG, "lb, grad_lo and grad_hi are required");
+    if (n == 0) return BAB_OK;
+    const NetDesc &N = c->net;
+    const int d = N.k * H;
+    const size_t nh = (size_t)n * H * N.sumh, nx = (size_t)n * (H + 1) * N.s;
+    rc = ensure_scratch(c, bound_scratch_bytes(N, n, H, d, true) + (3 * nh + nx + 2 * (size_t)n * d) * sizeof(float) +
+                               8 * 256);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    Carver cv{reinterpret_cast<char *>(c->scratch)};
+    rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    a.alpha = alpha;
+    a.A_pre = cv.take<float>(nh);
+    a.ustar = cv.take<float>((size_t)n * d);
+    a.lin_coef = cv.take<float>((size_t)n * d);
+    a.lb = lb;
+    cudaError_t e = launch_crown(a, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
+    float *GL = cv.take<float>(nh), *GU = cv.take<float>(nh), *GX = cv.take<float>(nx);
+    e = launch_box_grad_warp(a, GL, GU, GX, grad_lo, grad_hi, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "box gradient kernel");
+    return BAB_OK;
+}
+
 int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
                        const float *hi, int n, const int *d_n, int steps, float lr, int precision, float *alpha,
                        float *lb_best, void *stream)

@@ -547,4 +547,244 @@ cudaError_t launch_alpha_warp(const BoundArgs &a, int steps, float lr, float *al
     }
 }
 
+// out_l[p] / out_h[p] (output c = lane + 32 p < Nn) = sum_{j < K} of W[j][c] times gl_j or gh_j, the factor
+// picked by the sign of W[j][c] (W+ gl + W- gh, and W+ gh + W- gl): the transposed step of an interval
+// product.  B is a backward image W_l [Kp][Np] (rows j = the layer's outputs).
+template <int P>
+__device__ __forceinline__ void dense_sign_warp(const float (&gl)[P], const float (&gh)[P], int K,
+                                                const float *__restrict__ B, int Nn, float (&out_l)[P],
+                                                float (&out_h)[P])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int p = 0; p < P; ++p) out_l[p] = out_h[p] = 0.f;
+    const float *Bj = B + lane;
+#pragma unroll
+    for (int pk = 0; pk < P; ++pk) {
+        if (32 * pk >= K) break;
+        const int kn = min(32, K - 32 * pk);
+        for (int kl = 0; kl < kn; ++kl) {
+            const float xl = __shfl_sync(0xFFFFFFFFu, gl[pk], kl), xh = __shfl_sync(0xFFFFFFFFu, gh[pk], kl);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (lane + 32 * p < Nn) {
+                    const float w = Bj[32 * p];
+                    const bool pos = w >= 0.f;
+                    out_l[p] = fmaf(w, pos ? xl : xh, out_l[p]);
+                    out_h[p] = fmaf(w, pos ? xh : xl, out_h[p]);
+                }
+            }
+            Bj += Nn;
+        }
+    }
+}
+
+// Gradient of the bound with respect to the box faces (the derivative oracle_box_grad defines), one warp per
+// box, from the interval bounds and a CROWN pass that stored A_pre, u* and mu:
+//   1. the relaxed network forward from x_0 and u*: each unstable neuron whose upper chord was selected
+//      (A < 0) gets dLB/du = A l (l - z~)/(u - l)^2 and dLB/dl = A u (z~ - u)/(u - l)^2, each cost tangent
+//      dLB/dx_lo = dLB/dx_hi = x~ - g - m;
+//   2. those sensitivities run back through the interval bounds' steps (transposed sign-split products, the
+//      ReLU passing a derivative where its end is positive, the residual x_{t+1} = x_t + z_L) to the box;
+//   3. the concretization adds mu_j + 2 rho lo_j (hi_j) where u*_j sits on that face.
+// GL, GU: [n][Hmax][sumh] scratch, GX: [n][Hmax+1][s] scratch.
+template <int P, bool WSMEM>
+__global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
+    k_box_grad_warp(BoundArgs a, float *GL, float *GU, float *GX, float *grad_lo, float *grad_hi)
+{
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, L = N.L, Hm = a.batch.Hmax, d = a.d, sumh = N.sumh;
+    const float *fwd = a.fwd, *bwd = a.bwd;
+    if (WSMEM) {
+        for (int i = threadIdx.x; i < N.img_floats / 4; i += blockDim.x) {
+            smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
+            reinterpret_cast<float4 *>(sm + N.img_floats)[i] = reinterpret_cast<const float4 *>(a.bwd)[i];
+        }
+        fwd = sm;
+        bwd = sm + N.img_floats;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nlive = live_count(a.n, a.d_n);
+    const size_t hs = (size_t)Hm * sumh;
+    const bool has_alpha = a.alpha != nullptr;
+    for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {
+        const int pb = row_problem(a.batch, box);
+        if (!WSMEM) {
+            fwd = a.fwd + (size_t)pb * N.img_floats;
+            bwd = a.bwd + (size_t)pb * N.img_floats;
+        }
+        const float *x0 = a.x0 + (size_t)pb * s, *goal = a.goal + (size_t)pb * s;
+        const int H = problem_H(a.batch, pb, a.H), dp = k * H;
+        const float rho = problem_rho(a.batch, pb, a.rho);
+        const float *pl = a.pre_lo + box * hs, *ph = a.pre_hi + box * hs, *Ap = a.A_pre + box * hs;
+        const float *al = has_alpha ? a.alpha + box * hs : nullptr;
+        const float *xlo = a.x_lo + (size_t)box * (Hm + 1) * s, *xhi = a.x_hi + (size_t)box * (Hm + 1) * s;
+        const float *us = a.ustar + (size_t)box * d, *mu = a.lin_coef + (size_t)box * d;
+        const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
+        float *gl_ = GL + box * hs, *gu_ = GU + box * hs, *gx = GX + (size_t)box * (Hm + 1) * s;
+        float *glo = grad_lo + (size_t)box * d, *ghi = grad_hi + (size_t)box * d;
+
+        // ---- 1. relaxed network forward from x_0 and u*, with the bound's sensitivities ----
+        float x[P], Z[P], tmp[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int i = lane + 32 * q;
+            x[q] = i < s ? x0[i] : 0.f;
+        }
+        for (int t = 0; t < H; ++t) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int c = lane + 32 * q;
+                Z[q] = c < s ? x[q] : (c < s + k ? us[t * k + (c - s)] : 0.f);
+            }
+            for (int l = 1; l <= L; ++l) {
+                dense_warp<P>(Z, pad4(N.dims[l - 1]), fwd + N.fwd_w[l], pad4(N.dims[l]), fwd + N.fwd_b[l], tmp);
+                if (l < L) {
+                    const int dl = N.dims[l];
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        const int j = lane + 32 * q;
+                        if (j < dl) {
+                            const size_t idx = (size_t)t * sumh + N.hoff[l] + j;
+                            const float z = tmp[q], zl = pl[idx], zu = ph[idx], A = Ap[idx];
+                            float D, c;
+                            relax_select(zl, zu, A, has_alpha ? al[idx] : 0.f, has_alpha, D, c);
+                            float gL = 0.f, gU = 0.f;
+                            if (zl < 0.f && zu > 0.f && A < 0.f) {
+                                const float w = zu - zl, w2 = w * w;
+                                gU = A * zl * (zl - z) / w2;
+                                gL = A * zu * (z - zu) / w2;
+                            }
+                            gl_[idx] = gL;
+                            gu_[idx] = gU;
+                            tmp[q] = fmaf(D, z, c);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < P; ++q) Z[q] = tmp[q];
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int i = lane + 32 * q;
+                if (i < s) {
+                    x[q] += Z[q];
+                    const float g = goal[i];
+                    const float Ls = __fsub_rd(xlo[(size_t)(t + 1) * s + i], g);
+                    const float Us = __fsub_ru(xhi[(size_t)(t + 1) * s + i], g);
+                    const float m = 0.5f * (Ls + Us);
+                    gx[(size_t)(t + 1) * s + i] = (x[q] - g) - m;
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- 2. back through the interval bounds to the box ----
+        float Gxl[P], Gxh[P], Gl[P], Gh[P], Al[P], Ah[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int i = lane + 32 * q;
+            Gxl[q] = Gxh[q] = i < s ? gx[(size_t)H * s + i] : 0.f;
+        }
+        for (int t = H - 1; t >= 0; --t) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                Gl[q] = Gxl[q];
+                Gh[q] = Gxh[q];
+            }
+            for (int l = L; l >= 1; --l) {
+                if (l < L) {
+                    const int dl = N.dims[l];
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        const int j = lane + 32 * q;
+                        Gl[q] = Gh[q] = 0.f;
+                        if (j < dl) {
+                            const size_t idx = (size_t)t * sumh + N.hoff[l] + j;
+                            Gl[q] = (pl[idx] > 0.f ? Al[q] : 0.f) + gl_[idx];
+                            Gh[q] = (ph[idx] > 0.f ? Ah[q] : 0.f) + gu_[idx];
+                        }
+                    }
+                }
+                dense_sign_warp<P>(Gl, Gh, pad4(N.dims[l]), bwd + N.bwd_w[l], pad4(N.dims[l - 1]), Al, Ah);
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                const int c = lane + 32 * q;
+                if (c >= s && c < s + k) {
+                    glo[t * k + (c - s)] = Al[q];
+                    ghi[t * k + (c - s)] = Ah[q];
+                }
+                if (c < s) {
+                    const float tg = t >= 1 ? gx[(size_t)t * s + c] : 0.f;
+                    Gxl[q] = Gxl[q] + Al[q] + tg;
+                    Gxh[q] = Gxh[q] + Ah[q] + tg;
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- 3. the concretization's own dependence on the faces ----
+        for (int j = lane; j < d; j += 32) {
+            if (j >= dp) {
+                glo[j] = ghi[j] = 0.f;
+                continue;
+            }
+            const float m_ = mu[j], lo = blo[j], hi = bhi[j];
+            bool at_lo, at_hi;
+            if (rho > 0.f) {
+                const float uc = -m_ / (2.f * rho);
+                at_lo = uc <= lo;
+                at_hi = !at_lo && uc >= hi;
+            } else {
+                at_lo = m_ >= 0.f;
+                at_hi = !at_lo;
+            }
+            (void)us;
+            if (at_lo) glo[j] += m_ + 2.f * rho * lo;
+            if (at_hi) ghi[j] += m_ + 2.f * rho * hi;
+        }
+    }
+}
+
+template <int P>
+static cudaError_t launch_box_grad_variant(const BoundArgs &a, float *GL, float *GU, float *GX, float *glo,
+                                           float *ghi, cudaStream_t st)
+{
+    int dev, max_optin = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t img = 2 * (size_t)a.net.img_floats * sizeof(float);
+    const bool wsmem = a.batch.P <= 1 && img + 1024 <= (size_t)max_optin;
+    const size_t smem = wsmem ? img : 0;
+    auto kern = wsmem ? k_box_grad_warp<P, true> : k_box_grad_warp<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int need = (a.n + kWarps - 1) / kWarps;
+    const int grid = need < nsm * occ ? need : nsm * occ;
+    kern<<<grid, kWarps * 32, smem, st>>>(a, GL, GU, GX, glo, ghi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_grad_warp(const BoundArgs &a, float *GL, float *GU, float *GX, float *glo, float *ghi,
+                                 cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    switch (lanes_needed(a.net)) {
+        case 1: return launch_box_grad_variant<1>(a, GL, GU, GX, glo, ghi, st);
+        case 2: return launch_box_grad_variant<2>(a, GL, GU, GX, glo, ghi, st);
+        case 4: return launch_box_grad_variant<4>(a, GL, GU, GX, glo, ghi, st);
+        case 8: return launch_box_grad_variant<8>(a, GL, GU, GX, glo, ghi, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
 }  // namespace bab

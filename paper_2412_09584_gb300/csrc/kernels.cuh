@@ -213,6 +213,10 @@ cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
 cudaError_t launch_alpha_fused(const BoundArgs &a, int steps, float lr, float *alpha_out, int variant, cudaStream_t st);
 // interval bounds with one warp per box (any problem of the batch)
 cudaError_t launch_ibp_warp(const BoundArgs &a, cudaStream_t st);
+// d(bound)/d(box faces), one warp per box, after interval bounds and a CROWN pass that stored A_pre, u*, mu
+// (lin_coef); GL, GU [n][Hmax][sumh] and GX [n][Hmax+1][s] are scratch
+cudaError_t launch_box_grad_warp(const BoundArgs &a, float *GL, float *GU, float *GX, float *glo, float *ghi,
+                                 cudaStream_t st);
 // the whole alpha optimisation with one warp per box; alpha (written), m, v: [n][Hmax][sumh] device arrays;
 // steps == 0: one bound with the adaptive slopes (alpha, m, v unused)
 cudaError_t launch_alpha_warp(const BoundArgs &a, int steps, float lr, float *alpha, float *m, float *v,

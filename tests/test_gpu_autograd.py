@@ -100,3 +100,49 @@ def test_alpha_optimize_matches_oracle(oracle, prec_name):
             assert b[i] <= min(oracle.objective(p, x.astype(np.float64)) for x in u)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("fixed_alpha", [False, True])
+def test_box_gradient_matches_oracle(oracle, fixed_alpha):
+    """d lb / d (lo, hi) from bab_box_grad against the oracle's (itself pinned by central differences)."""
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, g, tlo, thi = _setup(seed=70, n=40)
+    try:
+        n = lo.shape[0]
+        alpha = None
+        if fixed_alpha:
+            alpha = np.random.default_rng(3).uniform(0.05, 0.95, size=(n, g.H, g.sumh)).astype(np.float32)
+        lb = torch.empty(n, device="cuda")
+        glo, ghi = torch.empty_like(tlo), torch.empty_like(thi)
+        ta = None if alpha is None else torch.tensor(alpha, device="cuda")
+        B.bab_box_grad(g.ctx, g.x0, g.goal, g.H, g.rho, tlo, thi, n, lb, glo, ghi, alpha=ta)
+        torch.cuda.synchronize()
+        lb_o, glo_o, ghi_o = oracle.box_grad(p, lo, hi, None if alpha is None else alpha.astype(np.float64))
+        r = g.crown(lo, hi, alpha=alpha)
+        np.testing.assert_array_equal(lb.cpu().numpy(), r["lb"])  # the same bound as bab_bound_crown
+        for got, want in ((glo.cpu().numpy(), glo_o), (ghi.cpu().numpy(), ghi_o)):
+            scale = np.maximum(np.abs(want).max(axis=1, keepdims=True), 1e-30)
+            assert np.all(np.abs(got - want) <= 1e-3 * scale), np.max(np.abs(got - want) / scale)
+    finally:
+        g.close()
+
+
+def test_box_gradient_through_autograd(oracle):
+    from paper_2412_09584_gb300.autograd import CrownProblem, crown_box_bound
+    p, lo, hi, g, tlo, thi = _setup(seed=71, n=16)
+    try:
+        l_ = tlo.clone().requires_grad_(True)
+        h_ = thi.clone().requires_grad_(True)
+        prob = CrownProblem(g.ctx, g.x0, g.goal, g.H, g.rho, tlo, thi)
+        lb = crown_box_bound(l_, h_, prob)
+        w = torch.linspace(0.5, 1.5, lb.shape[0], device="cuda")
+        gl, gh = torch.autograd.grad((w * lb).sum(), (l_, h_))
+        _, glo_o, ghi_o = oracle.box_grad(p, lo, hi)
+        wn = w.cpu().numpy()[:, None]
+        for got, want in ((gl.cpu().numpy(), glo_o * wn), (gh.cpu().numpy(), ghi_o * wn)):
+            scale = np.maximum(np.abs(want).max(axis=1, keepdims=True), 1e-30)
+            assert np.all(np.abs(got - want) <= 1e-3 * scale)
+        # the forward value is the library's sound bound: never above the oracle's exact CROWN bound
+        assert np.all(lb.detach().cpu().numpy() <= oracle.crown(p, lo, hi)["lb"] + 1e-9)
+    finally:
+        g.close()
