@@ -510,7 +510,7 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
 
     def search_and_bound(Q, n, d_n):
         B.bab_rollout_batch(ctx, tx0, tgoal, tH, trho, Hmax, d, Q["lo"], Q["hi"], Q["id"], Q["prob"], n, samples,
-                            SEED, Q["ub"], best_u, inc_val, inc_u, d_n=d_n)
+                            SEED, Q["ub"], best_u, inc_val, inc_u, d_n=d_n, precision=B.PREC_BF16X3)
         B.bab_bound_batch(ctx, tx0, tgoal, tH, trho, Hmax, d, Q["lo"], Q["hi"], Q["prob"], n, Q["lb"],
                           alpha_steps=alpha_steps, lr=c["alpha_lr"], d_n=d_n)
 
@@ -560,7 +560,7 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
     rsteps = float(nb) * samples * float(np.mean(Hs))
     return {"workload": f"{P} problems of MLP 6-32-32-4 (own weights, start, goal), horizons uniform in "
                         f"[{c['H_lo']}, {c['H_hi']}], 256-box starting grid each, {n_pick} boxes picked and split per "
-                        f"problem per iteration, {samples} FP32 rollouts per child, interval bounds + alpha-CROWN "
+                        f"problem per iteration, {samples} BF16x3 tensor-core rollouts per child, interval bounds + alpha-CROWN "
                         f"({alpha_steps} Adam steps) per child",
             "iterations": iters, "ms_per_iteration": ms, "children_per_iteration": nb,
             "subdomain_bounds_per_s": nb / (ms / 1e3), "rollout_steps_per_s": rsteps / (ms / 1e3),

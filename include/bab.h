@@ -324,18 +324,20 @@ int bab_load_dynamics_batch(bab_ctx **out, int n_problems, int n_layers, const i
                             int state_dim, int action_dim, unsigned flags);
 
 /*
- * bab_rollout for every row of every problem, FP32 on CUDA cores: per row
- * `samples` uniform samples (the same counter RNG as bab_rollout, over the
- * row's own k * H_p coordinates), ub[i], best_u[i] (coordinates beyond
- * k * H_p are 0), and per problem the incumbent inc_val[p] (device double[P])
- * / inc_u[p] (device float[P][d_stride]) re-scored in FP64 from the best row
- * of that problem.
- * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_CUDA, BAB_ERR_OOM.
+ * bab_rollout for every row of every problem: per row `samples` uniform
+ * samples (the same counter RNG as bab_rollout, over the row's own k * H_p
+ * coordinates), ub[i], best_u[i] (coordinates beyond k * H_p are 0), and per
+ * problem the incumbent inc_val[p] (device double[P]) / inc_u[p] (device
+ * float[P][d_stride]) re-scored in FP64 from the best row of that problem.
+ * precision as bab_rollout; on tensor cores each sample tile streams its own
+ * problem's weights (samples >= 128 when there are several problems), and in
+ * BF16 every row's best sample is re-scored in FP32.
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_UNSUPPORTED, BAB_ERR_CUDA, BAB_ERR_OOM.
  */
 int bab_rollout_batch(bab_ctx *ctx, const float *x0, const float *goal, const int *horizon, const float *rho,
                       int max_horizon, int d_stride, const float *lo, const float *hi, const uint64_t *id,
-                      const int *prob, int n, const int *d_n, int samples, uint64_t seed, float *ub, float *best_u,
-                      double *inc_val, float *inc_u, void *stream);
+                      const int *prob, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
+                      float *best_u, double *inc_val, float *inc_u, void *stream);
 
 /*
  * Sound lower bounds of every row (FP32, outward-rounded, margin

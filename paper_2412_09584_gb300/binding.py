@@ -72,8 +72,8 @@ def load(path: str = LIB_PATH):
     L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
     L.bab_load_dynamics_batch.argtypes = [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _I,
                                           _I, ctypes.c_uint]
-    L.bab_rollout_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _P, _P,
-                                    _P, _P, _P]
+    L.bab_rollout_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _P,
+                                    _P, _P, _P, _P]
     L.bab_bound_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _I, _P, _I, _F, _P, _P, _P]
     L.bab_prune_branch_batch.argtypes = [_P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _F, _I, _I, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -266,13 +266,13 @@ def bab_load_dynamics_batch(dims, params, state_dim, action_dim, flags=0):
 
 
 def bab_rollout_batch(ctx, x0, goal, horizon, rho, max_horizon, d_stride, lo, hi, ids, prob, n, samples, seed, ub,
-                      best_u=None, inc_val=None, inc_u=None, d_n=None, stream=None):
+                      best_u=None, inc_val=None, inc_u=None, d_n=None, precision=PREC_FP32, stream=None):
     f32, i32 = torch.float32, torch.int32
     rc = load().bab_rollout_batch(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), _ptr(horizon, i32, "horizon"),
                                   _ptr(rho, f32, "rho"), int(max_horizon), int(d_stride), _ptr(lo, f32, "lo"),
                                   _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), _ptr(prob, i32, "prob"), int(n),
-                                  _ptr(d_n, i32), int(samples), int(seed), _ptr(ub, f32, "ub"), _ptr(best_u, f32),
-                                  _ptr(inc_val, torch.float64), _ptr(inc_u, f32), _stream(stream))
+                                  _ptr(d_n, i32), int(samples), int(seed), int(precision), _ptr(ub, f32, "ub"),
+                                  _ptr(best_u, f32), _ptr(inc_val, torch.float64), _ptr(inc_u, f32), _stream(stream))
     _check(ctx, rc)
 
 

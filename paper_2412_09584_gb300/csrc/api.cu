@@ -319,9 +319,16 @@ int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *
             for (int q = 0; q < no; ++q) fw[N.fwd_b[l] + q] = bw[N.bwd_b[l] + q] = b[q];
         }
     }
+    // tensor-core forward images (BF16 hi / lo) of every problem, back to back; backward image of problem 0
     std::vector<uint8_t> tc_img;
     std::vector<float> tc_bias;
-    build_tc_image(N, params, tc_img, tc_bias);
+    for (int pr = 0; pr < P; ++pr) {
+        std::vector<uint8_t> im;
+        std::vector<float> bi;
+        build_tc_image(N, params + (size_t)pr * raw, im, bi);
+        tc_img.insert(tc_img.end(), im.begin(), im.end());
+        tc_bias.insert(tc_bias.end(), bi.begin(), bi.end());
+    }
     std::vector<uint8_t> tcb_img;
     build_tcb_image(N, params, tcb_img);
     cudaError_t e = cudaGetDevice(&c->device);
@@ -837,12 +844,19 @@ extern "C" {
 
 int bab_rollout_batch(bab_ctx *c, const float *x0, const float *goal, const int *horizon, const float *rho,
                       int max_horizon, int d_stride, const float *lo, const float *hi, const uint64_t *id,
-                      const int *prob, int n, const int *d_n, int samples, uint64_t seed, float *ub, float *best_u,
-                      double *inc_val, float *inc_u, void *stream)
+                      const int *prob, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
+                      float *best_u, double *inc_val, float *inc_u, void *stream)
 {
     int rc = check_batch(c, x0, goal, horizon, rho, max_horizon, d_stride, lo, hi, prob, n);
     if (rc) return rc;
     if (samples < 1) return fail(c, BAB_ERR_SHAPE, "samples must be >= 1");
+    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3 && precision != BAB_PREC_BF16)
+        return fail(c, BAB_ERR_INVALID_ARG, "unknown precision %d", precision);
+    const int split = precision == BAB_PREC_BF16X3 ? 3 : 1;
+    if (precision != BAB_PREC_FP32 && (!rollout_tc_supported(c->net, split, c->max_smem) ||
+                                       (c->n_problems > 1 && samples < 128)))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout of batched problems needs a supported network "
+                                            "and >= 128 samples per box");
     if (n > 0 && (!id || !ub)) return fail(c, BAB_ERR_INVALID_ARG, "id and ub are required");
     if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
     if (inc_val && !best_u) return fail(c, BAB_ERR_INVALID_ARG, "the incumbent update needs best_u");
@@ -872,7 +886,12 @@ int bab_rollout_batch(bab_ctx *c, const float *x0, const float *goal, const int 
     a.inc_val = inc_val;
     a.inc_u = inc_u;
     a.status = c->d_status;
-    cudaError_t e = launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, (cudaStream_t)stream);
+    a.tc_img = c->d_tc;
+    a.tc_bias = c->d_tc_bias;
+    a.tc_bytes = c->net.tc_bytes;
+    cudaError_t e = precision == BAB_PREC_FP32
+                        ? launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, (cudaStream_t)stream)
+                        : launch_rollout_tc(a, split, c->tune_rollout_tc, c->num_sms, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched rollout kernels");
     return BAB_OK;
 }

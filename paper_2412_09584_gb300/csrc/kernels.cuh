@@ -58,6 +58,7 @@ struct RolloutArgs {
     uint32_t tmem_cols;
     int stages;          // > 0: the image is streamed through a ring of `stages` buffers of stage_bytes
     int stage_bytes;
+    size_t tc_img_stride;  // bytes between problems' tensor-core images (batched problems, streamed)
     // BF16 rollouts: re-score in FP32 only the topk boxes of smallest BF16 ub (0: every box)
     int topk;
     unsigned long long *topk_t;  // [3] scratch: the selection threshold

@@ -133,6 +133,12 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
     const int tpb = a.M >= 128 ? (a.M + 127) / 128 : 1;
     const long long ntiles = bpt > 1 ? ((long long)nlive + bpt - 1) / bpt : (long long)nlive * tpb;
     const long long G = (long long)gridDim.x * NSLOT;
+    // batched problems (streamed images only, one box per tile): each tile's problem, horizon
+    const bool batched = a.batch.P > 1;
+    auto tile_problem = [&](long long tile) {
+        return row_problem(a.batch, bpt > 1 ? (int)(tile * bpt) : (int)(tile / tpb));
+    };
+    auto tile_H = [&](long long tile) { return problem_H(a.batch, tile_problem(tile), a.H); };
     const uint32_t tb = tmem_base;
     const int Dc = N.tc_dcols, Ac = N.tc_acols;
     const int slot_cols = Dc + (SPLIT == 3 ? 2 : 1) * Ac;
@@ -166,12 +172,19 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
             }
             const uint64_t hb = box_hash(a.seed, a.id[box]);
             const float *blo = a.lo + (size_t)box * a.d, *bhi = a.hi + (size_t)box * a.d;
+            // the tile's problem: start, goal, biases, horizon, rho (shared memory holds problem 0's)
+            const int pb = batched ? tile_problem(tile) : 0;
+            const float *x0_p = batched ? a.x0 + (size_t)pb * s : x0_s;
+            const float *goal_p = batched ? a.goal + (size_t)pb * s : goal_s;
+            const float *bias_p = batched ? a.tc_bias + (size_t)pb * N.tc_bias_floats : bias;
+            const int Hb = batched ? problem_H(a.batch, pb, a.H) : a.H;
+            const float rho = batched ? problem_rho(a.batch, pb, a.rho) : a.rho;
             float x[SP];
 #pragma unroll
-            for (int i = 0; i < SP; ++i) x[i] = x0_s[i];
+            for (int i = 0; i < SP; ++i) x[i] = i < s ? x0_p[i] : 0.f;
             float cost = 0.f;
             bool ok = true;
-            for (int t = 0; t < a.H && ok; ++t) {
+            for (int t = 0; t < Hb && ok; ++t) {
                 if (primary) {
                     // layer-1 input row [x_t | u_t | 0], K1 <= 64 BF16 values
                     float u[kKMax];
@@ -180,7 +193,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                         if (j < k) {
                             const int jj = t * k + j;
                             u[j] = draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj));
-                            cost = fmaf(a.rho * u[j], u[j], cost);
+                            cost = fmaf(rho * u[j], u[j], cost);
                         } else {
                             u[j] = 0.f;
                         }
@@ -223,7 +236,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                     }
                     phD ^= 1;
                     tc::fence_after_sync();
-                    const float *bl = bias + N.tc_boff[l];
+                    const float *bl = bias_p + N.tc_boff[l];
                     const int Nl = N.tc_N[l];
                     const bool split_cols = (Nl % 64 == 0);
                     int c_beg = 0, c_end = Nl;
@@ -255,7 +268,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                             for (int i = 0; i < SP; ++i) {
                                 if (i < s) {
                                     x[i] = x[i] + (dx[i] + bl[i]);
-                                    const float e = x[i] - goal_s[i];
+                                    const float e = x[i] - goal_p[i];
                                     c = fmaf(e, e, c);
                                 }
                             }
@@ -316,13 +329,17 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
         // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
         const int sl = warp - mma_warp;
         const long long gi = (long long)blockIdx.x * NSLOT + sl;
-        const long long cnt = gi < ntiles ? (ntiles - 1 - gi) / G + 1 : 0;
-        long long left = cnt * a.H * L;
-        int l = 1;
+        // walk (tile, t, l) in the epilogue's order; a tile of horizon 0 has nothing to issue
+        long long tile = gi;
+        int Hb = tile < ntiles ? tile_H(tile) : 0, t = 0, l = 1;
+        while (tile < ntiles && Hb == 0) {
+            tile += G;
+            Hb = tile < ntiles ? tile_H(tile) : 0;
+        }
         uint32_t phA = 0, ncommit = 0, ring_it = 0;
         const uint32_t dcol = tb + sl * slot_cols;
         const uint32_t ah = dcol + Dc, al = ah + Ac;
-        while (left > 0 && !*abort) {
+        while (tile < ntiles && !*abort) {
             if (!tc::mbar_wait(&bar_a[sl], phA, abort, kWaitLimitNs)) {
                 raise_abort(a.status, abort);
                 break;
@@ -369,8 +386,16 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
             }
             tc::mma_commit(&bar_d[sl]);
             ++ncommit;
-            l = (l == L) ? 1 : l + 1;
-            --left;
+            if (++l > L) {
+                l = 1;
+                if (++t >= Hb) {
+                    t = 0;
+                    do {
+                        tile += G;
+                        Hb = tile < ntiles ? tile_H(tile) : 0;
+                    } while (tile < ntiles && Hb == 0);
+                }
+            }
         }
         if (*abort) {
             // let every issued MMA finish before the TMEM and the ring are released
@@ -380,10 +405,12 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
         }
     } else if (STREAM && warp == mma_warp + NSLOT && lane == 0) {
         // ------------------- producer: the weight atoms in the issuer's order -------------------
-        const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
         uint32_t it = 0;
         bool ok = true;
-        for (long long q = 0; q < cnt * a.H && ok && !*abort; ++q) {
+        for (long long tile = blockIdx.x; tile < ntiles && ok && !*abort; tile += G) {
+          const int Hb = tile_H(tile);
+          const uint8_t *img = a.tc_img + (batched ? (size_t)tile_problem(tile) * a.tc_img_stride : 0);
+          for (int t = 0; t < Hb && ok && !*abort; ++t) {
             for (int l = 1; l <= L && ok; ++l) {
                 const int Kl = N.tc_K[l], Nl = N.tc_N[l];
                 const uint32_t atom = (uint32_t)Nl * 128u;
@@ -396,10 +423,11 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                     }
                     uint8_t *dst = wimg + (size_t)st * a.stage_bytes;
                     tc::mbar_arrive_expect_tx(&bar_full[st], (SPLIT == 3 ? 2u : 1u) * atom);
-                    tc::bulk_g2s(dst, a.tc_img + N.tc_hi[l] + (size_t)at * atom, atom, &bar_full[st]);
-                    if (SPLIT == 3) tc::bulk_g2s(dst + atom, a.tc_img + N.tc_lo[l] + (size_t)at * atom, atom, &bar_full[st]);
+                    tc::bulk_g2s(dst, img + N.tc_hi[l] + (size_t)at * atom, atom, &bar_full[st]);
+                    if (SPLIT == 3) tc::bulk_g2s(dst + atom, img + N.tc_lo[l] + (size_t)at * atom, atom, &bar_full[st]);
                 }
             }
+          }
         }
         // copies still in flight must land before the shared memory is released
         volatile int never = 0;
@@ -457,11 +485,16 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     const uint32_t m = (uint32_t)(key & 0xFFFFFFFFu);
     const uint64_t hb = box_hash(a.seed, a.id[box]);
     const int s = N.s, k = N.k, d = a.d;
+    const int pb = row_problem(a.batch, box);
+    const float *fwd = a.fwd + (size_t)pb * N.img_floats;
+    const float *x0 = a.x0 + (size_t)pb * s, *goal = a.goal + (size_t)pb * s;
+    const int Hb = problem_H(a.batch, pb, a.H);
+    const float rho = problem_rho(a.batch, pb, a.rho);
     const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
-    for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = a.x0[i];
+    for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = x0[i];
     if (threadIdx.x == 0) f_sh = 0.f;
     __syncthreads();
-    for (int t = 0; t < a.H; ++t) {
+    for (int t = 0; t < Hb; ++t) {
         for (int c = threadIdx.x; c < s + k; c += blockDim.x)
             act[0][c] = c < s ? xs[c] : draw_sample(hb, m, (uint32_t)(t * k + c - s), blo[t * k + c - s], bhi[t * k + c - s]);
         __syncthreads();
@@ -469,8 +502,8 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
         for (int l = 1; l <= N.L; ++l) {
             const int no = N.dims[l], ni = N.dims[l - 1], Np = pad4(no);
             // forward image W_l^T [Kp][Np]: consecutive threads read consecutive outputs
-            const float *Wt = a.fwd + N.fwd_w[l];
-            const float *b = a.fwd + N.fwd_b[l];
+            const float *Wt = fwd + N.fwd_w[l];
+            const float *b = fwd + N.fwd_b[l];
             for (int q = threadIdx.x; q < no; q += blockDim.x) {
                 float acc = b[q];
                 for (int c = 0; c < ni; ++c) acc = fmaf(Wt[(size_t)c * Np + q], act[cur][c], acc);
@@ -483,22 +516,19 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
             float f = f_sh;
             for (int j = 0; j < k; ++j) {
                 const float u = draw_sample(hb, m, (uint32_t)(t * k + j), blo[t * k + j], bhi[t * k + j]);
-                f = fmaf(a.rho * u, u, f);
+                f = fmaf(rho * u, u, f);
             }
             float c = 0.f;
             for (int i = 0; i < s; ++i) {
                 xs[i] = xs[i] + act[cur][i];
-                const float e = xs[i] - a.goal[i];
+                const float e = xs[i] - goal[i];
                 c = fmaf(e, e, c);
             }
             f_sh = f + c;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) a.ub[box] = f_sh;
-    if (a.best_u)
-        for (int j = threadIdx.x; j < d; j += blockDim.x)
-            a.best_u[(size_t)box * d + j] = draw_sample(hb, m, (uint32_t)j, blo[j], bhi[j]);
+    if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
 }
 
 template <int NSLOT, int SPLIT, int SP, bool STREAM>
@@ -557,7 +587,9 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     int dev, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const bool stream = !rollout_tc_resident(N, split, max_smem);
+    // several problems: every tile streams its own problem's image
+    const bool stream = a.batch.P > 1 || !rollout_tc_resident(N, split, max_smem);
+    a.tc_img_stride = (size_t)N.tc_bytes;
     // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
     const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols;
     int nslot = (2 * slot_cols <= 512 && !stream) ? 2 : 1;

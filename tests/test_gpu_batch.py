@@ -44,19 +44,23 @@ def _rows(bt, seed, counts):
     return W.batch_random_boxes(bt.probs, counts, bt.dst, seed)
 
 
-def test_batch_rollout_matches_single_and_oracle(oracle):
+@pytest.mark.parametrize("prec_name,M", [("fp32", 64), ("bf16x3", 200), ("bf16", 130)])
+def test_batch_rollout_matches_single_and_oracle(oracle, prec_name, M):
+    """FP32 on CUDA cores, or tensor cores with each tile streaming its own problem's weights: every row equals
+    the single-problem call on its problem bit for bit."""
     from gpu_util import DEV, GpuProblem, T, ids_t
     bt = Batch()
     B = bt.B
+    prec = {"fp32": B.PREC_FP32, "bf16x3": B.PREC_BF16X3, "bf16": B.PREC_BF16}[prec_name]
     try:
         lo, hi, ids, prob = _rows(bt, 1, [7, 3, 9, 5, 6])
-        n, M, seed = lo.shape[0], 64, 11
+        n, seed = lo.shape[0], 11
         ub = torch.empty(n, device=DEV)
         best_u = torch.empty(n, bt.dst, device=DEV)
         inc_val = torch.full((bt.P,), np.inf, dtype=torch.float64, device=DEV)
         inc_u = torch.zeros(bt.P, bt.dst, device=DEV)
         B.bab_rollout_batch(bt.ctx, bt.x0, bt.goal, bt.tH, bt.trho, bt.Hmax, bt.dst, T(lo), T(hi), ids_t(ids),
-                            T(prob, torch.int32), n, M, seed, ub, best_u, inc_val, inc_u)
+                            T(prob, torch.int32), n, M, seed, ub, best_u, inc_val, inc_u, precision=prec)
         torch.cuda.synchronize()
         ub, best_u = ub.cpu().numpy(), best_u.cpu().numpy()
         inc_val, inc_u = inc_val.cpu().numpy(), inc_u.cpu().numpy()
@@ -65,14 +69,18 @@ def test_batch_rollout_matches_single_and_oracle(oracle):
             dp = bt.dp(p)
             g = GpuProblem(bt.probs[p])
             try:
-                r = g.rollout(lo[rows, :dp], hi[rows, :dp], ids[rows], M=M, seed=seed)
+                r = g.rollout(lo[rows, :dp], hi[rows, :dp], ids[rows], M=M, seed=seed, precision=prec)
             finally:
                 g.close()
             assert np.array_equal(ub[rows].view(np.uint32), r["ub"].view(np.uint32))
             assert np.array_equal(best_u[rows, :dp].view(np.uint32), r["best_u"].view(np.uint32))
             assert np.all(best_u[rows, dp:] == 0)
             ub_o, _, _ = oracle.rollout(bt.probs[p], lo[rows, :dp], hi[rows, :dp], ids[rows], M, seed)
-            np.testing.assert_allclose(ub[rows], ub_o, rtol=REL, atol=0)
+            if prec_name == "bf16":  # each row's best BF16 sample, re-scored in FP32
+                f_b = np.array([oracle.objective(bt.probs[p], u[:dp].astype(np.float64)) for u in best_u[rows]])
+                np.testing.assert_allclose(ub[rows], f_b, rtol=REL)
+            else:
+                np.testing.assert_allclose(ub[rows], ub_o, rtol=REL, atol=0)
             f = oracle.objective(bt.probs[p], inc_u[p, :dp].astype(np.float64))
             assert inc_val[p] == pytest.approx(f, rel=1e-10)
             assert inc_val[p] <= ub[rows].min() * (1 + 2 * REL)
