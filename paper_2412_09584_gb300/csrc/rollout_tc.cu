@@ -71,20 +71,21 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 }  // namespace
 
 // SP: padded state width of the last layer (16 or 32).  STREAM: the weight
-// image does not fit in shared memory; a producer warp streams it, one K-atom
-// (64 inputs of one layer, hi and lo halves) at a time, through a ring of
-// a.stages buffers in the order the MMA issuer consumes them (NSLOT = 1).
+// image does not fit in shared memory, or every tile needs its own problem's
+// image; per slot a producer warp streams it, one K-atom (64 inputs of one
+// layer, hi and lo halves) at a time, through the slot's ring of a.stages
+// buffers in the order the slot's MMA issuer consumes them.
 template <int NSLOT, int SPLIT, int SP, bool STREAM>
-__global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
+__global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     const NetDesc &N = a.net;
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float *bias = reinterpret_cast<float *>(wimg + (STREAM ? a.stages * a.stage_bytes : a.tc_bytes));
+    float *bias = reinterpret_cast<float *>(wimg + (STREAM ? (size_t)NSLOT * a.stages * a.stage_bytes : (size_t)a.tc_bytes));
     float *goal_s = bias + N.tc_bias_floats;
     float *x0_s = goal_s + SP;
     __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_fin;
-    __shared__ uint64_t bar_full[kMaxStages], bar_empty[kMaxStages];
+    __shared__ uint64_t bar_full[NSLOT * kMaxStages], bar_empty[NSLOT * kMaxStages];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
             tc::mbar_init(&bar_a[i], kEpiWarps);
             tc::mbar_init(&bar_d[i], 1);
         }
-        for (int i = 0; i < kMaxStages; ++i) {
+        for (int i = 0; i < NSLOT * kMaxStages; ++i) {
             tc::mbar_init(&bar_full[i], 1);
             tc::mbar_init(&bar_empty[i], 1);
         }
@@ -364,12 +365,13 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                 bool ok = true;
                 for (int at = 0; at < (Kl + 63) / 64; ++at, ++ring_it) {
                     const uint32_t st = ring_it % (uint32_t)a.stages, ph = (ring_it / (uint32_t)a.stages) & 1u;
-                    if (!tc::mbar_wait(&bar_full[st], ph, abort, kWaitLimitNs)) {
+                    uint64_t *full = bar_full + sl * kMaxStages, *empty = bar_empty + sl * kMaxStages;
+                    if (!tc::mbar_wait(&full[st], ph, abort, kWaitLimitNs)) {
                         raise_abort(a.status, abort);
                         ok = false;
                         break;
                     }
-                    const uint32_t bh = tc::smem_u32(wimg + (size_t)st * a.stage_bytes);
+                    const uint32_t bh = tc::smem_u32(wimg + ((size_t)sl * a.stages + st) * a.stage_bytes);
                     const uint32_t blo = bh + (uint32_t)(Nl * 128);
                     for (int kk = 0; kk < 4 && 4 * at + kk < Kl / 16; ++kk) {
                         const int ks = 4 * at + kk;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                             tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
                         }
                     }
-                    tc::mma_commit(&bar_empty[st]);  // the buffer is free once these MMAs have read it
+                    tc::mma_commit(&empty[st]);  // the buffer is free once these MMAs have read it
                 }
                 if (!ok) break;
             }
@@ -403,11 +405,14 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
             tc::mma_commit(&bar_fin);
             tc::mbar_wait(&bar_fin, 0, &never, kWaitLimitNs);
         }
-    } else if (STREAM && warp == mma_warp + NSLOT && lane == 0) {
-        // ------------------- producer: the weight atoms in the issuer's order -------------------
+    } else if (STREAM && warp >= mma_warp + NSLOT && lane == 0) {
+        // ------------------- producer of slot ps: the weight atoms in that issuer's order -------------------
+        const int ps = warp - mma_warp - NSLOT;
+        uint64_t *full = bar_full + ps * kMaxStages, *empty = bar_empty + ps * kMaxStages;
+        uint8_t *ring = wimg + (size_t)ps * a.stages * a.stage_bytes;
         uint32_t it = 0;
         bool ok = true;
-        for (long long tile = blockIdx.x; tile < ntiles && ok && !*abort; tile += G) {
+        for (long long tile = (long long)blockIdx.x * NSLOT + ps; tile < ntiles && ok && !*abort; tile += G) {
           const int Hb = tile_H(tile);
           const uint8_t *img = a.tc_img + (batched ? (size_t)tile_problem(tile) * a.tc_img_stride : 0);
           for (int t = 0; t < Hb && ok && !*abort; ++t) {
@@ -416,15 +421,15 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
                 const uint32_t atom = (uint32_t)Nl * 128u;
                 for (int at = 0; at < (Kl + 63) / 64; ++at, ++it) {
                     const uint32_t st = it % (uint32_t)a.stages, ph = (it / (uint32_t)a.stages) & 1u;
-                    if (!tc::mbar_wait(&bar_empty[st], ph ^ 1u, abort, kWaitLimitNs)) {
+                    if (!tc::mbar_wait(&empty[st], ph ^ 1u, abort, kWaitLimitNs)) {
                         raise_abort(a.status, abort);
                         ok = false;
                         break;
                     }
-                    uint8_t *dst = wimg + (size_t)st * a.stage_bytes;
-                    tc::mbar_arrive_expect_tx(&bar_full[st], (SPLIT == 3 ? 2u : 1u) * atom);
-                    tc::bulk_g2s(dst, img + N.tc_hi[l] + (size_t)at * atom, atom, &bar_full[st]);
-                    if (SPLIT == 3) tc::bulk_g2s(dst + atom, img + N.tc_lo[l] + (size_t)at * atom, atom, &bar_full[st]);
+                    uint8_t *dst = ring + (size_t)st * a.stage_bytes;
+                    tc::mbar_arrive_expect_tx(&full[st], (SPLIT == 3 ? 2u : 1u) * atom);
+                    tc::bulk_g2s(dst, img + N.tc_hi[l] + (size_t)at * atom, atom, &full[st]);
+                    if (SPLIT == 3) tc::bulk_g2s(dst + atom, img + N.tc_lo[l] + (size_t)at * atom, atom, &full[st]);
                 }
             }
           }
@@ -434,7 +439,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) *
         const uint32_t inflight = it < (uint32_t)a.stages ? it : (uint32_t)a.stages;
         for (uint32_t j = 0; j < inflight; ++j) {
             const uint32_t i2 = it - 1 - j, st = i2 % (uint32_t)a.stages;
-            tc::mbar_wait(&bar_full[st], (i2 / (uint32_t)a.stages) & 1u, &never, kWaitLimitNs);
+            tc::mbar_wait(&full[st], (i2 / (uint32_t)a.stages) & 1u, &never, kWaitLimitNs);
         }
     }
     tc::fence_before_sync();
@@ -537,7 +542,7 @@ static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem
     auto kern = k_rollout_tc<NSLOT, SPLIT, SP, STREAM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, (NSLOT * (kEpiWarps + 1) + (STREAM ? 1 : 0)) * 32, smem, st>>>(a);
+    kern<<<grid, (NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -574,7 +579,9 @@ template <int SPLIT, int SP>
 static cudaError_t launch_tc_shape(const RolloutArgs &a, int nslot, bool stream, int grid, size_t smem,
                                    cudaStream_t st)
 {
-    if (stream) return launch_tc_variant<1, SPLIT, SP, true>(a, grid, smem, st);
+    if (stream)
+        return nslot == 2 ? launch_tc_variant<2, SPLIT, SP, true>(a, grid, smem, st)
+                          : launch_tc_variant<1, SPLIT, SP, true>(a, grid, smem, st);
     return nslot == 2 ? launch_tc_variant<2, SPLIT, SP, false>(a, grid, smem, st)
                       : launch_tc_variant<1, SPLIT, SP, false>(a, grid, smem, st);
 }
@@ -592,8 +599,12 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     a.tc_img_stride = (size_t)N.tc_bytes;
     // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
     const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols;
-    int nslot = (2 * slot_cols <= 512 && !stream) ? 2 : 1;
-    if (!stream && (nslot_pref == 1 || nslot_pref == 2)) nslot = nslot_pref;
+    int nslot = (2 * slot_cols <= 512) ? 2 : 1;
+    if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
+    // a streamed image needs a ring of at least two buffers per slot
+    if (stream && nslot == 2 &&
+        2 * 2 * rollout_tc_stage(N, split) + rollout_tc_extra(N) + 1024 > (size_t)max_smem)
+        nslot = 1;
     int cols = 32;
     while (cols < nslot * slot_cols) cols *= 2;
     if (cols > 512) return cudaErrorInvalidConfiguration;
@@ -606,11 +617,11 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     if (stream) {
         a.stage_bytes = (int)rollout_tc_stage(N, split);
         const size_t room = (size_t)max_smem - 1024 - rollout_tc_extra(N);
-        int stages = (int)(room / a.stage_bytes);
+        int stages = (int)(room / ((size_t)nslot * a.stage_bytes));
         stages = stages > kMaxStages ? kMaxStages : stages;
         if (stages < 2) return cudaErrorInvalidConfiguration;
         a.stages = stages;
-        smem = (size_t)stages * a.stage_bytes + rollout_tc_extra(N);
+        smem = (size_t)nslot * stages * a.stage_bytes + rollout_tc_extra(N);
     } else {
         a.stages = 0;
         smem = (size_t)a.tc_bytes + rollout_tc_extra(N);
