@@ -62,10 +62,69 @@ __device__ __forceinline__ void dense_warp(const float (&in)[P], int K, const fl
     }
 }
 
+// out[p] (output j = lane + 32 p < Nn) = bias[j] + sum_{k < K} in_s[k] Wr[j ld + k], in FMA order over k (the
+// same sum as dense_warp).  in_s: the warp's input vector in shared memory (K a multiple of 4); Wr: one padded
+// row per output, ld = 4 mod 8 so that the float4 loads of a quarter warp hit distinct banks.
+template <int P>
+__device__ __forceinline__ void dense_rs(const float *__restrict__ in_s, int K, const float *__restrict__ Wr, int ld,
+                                         int Nn, const float *__restrict__ bias, float (&out)[P])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int j = lane + 32 * p;
+        out[p] = (bias && j < Nn) ? bias[j] : 0.f;
+    }
+    for (int k = 0; k < K; k += 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(in_s + k);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int j = lane + 32 * p;
+            if (j < Nn) {
+                const float4 w = *reinterpret_cast<const float4 *>(Wr + (size_t)j * ld + k);
+                out[p] = fmaf(x.x, w.x, out[p]);
+                out[p] = fmaf(x.y, w.y, out[p]);
+                out[p] = fmaf(x.z, w.z, out[p]);
+                out[p] = fmaf(x.w, w.w, out[p]);
+            }
+        }
+    }
+}
+
+// Padded-row layout of one network in shared memory: per layer the forward rows (W_l row q, K = pad4(d_{l-1})),
+// the backward rows (column c of W_l, K = pad4(d_l)) and the biases.
+struct RowsLayout {
+    int offF[kMaxLayers + 1], ldF[kMaxLayers + 1], offB[kMaxLayers + 1], ldB[kMaxLayers + 1], offb[kMaxLayers + 1];
+    int floats;
+};
+
+__host__ __device__ inline int row_ld(int K) { return ((K + 7) & ~7) + 4; }
+
+__host__ __device__ inline RowsLayout rows_layout(const NetDesc &N)
+{
+    RowsLayout R{};
+    int o = 0;
+    for (int l = 1; l <= N.L; ++l) {
+        const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]);
+        R.offF[l] = o;
+        R.ldF[l] = row_ld(Kp);
+        o += Np * R.ldF[l];
+        R.offB[l] = o;
+        R.ldB[l] = row_ld(Np);
+        o += Kp * R.ldB[l];
+        R.offb[l] = o;
+        o += Np;
+    }
+    R.floats = (o + 3) & ~3;
+    return R;
+}
+
 }  // namespace
 
-// P: neurons per lane (every layer width <= 32 P).  WSMEM: both network images in shared memory.
-template <int P, bool WSMEM>
+// P: neurons per lane (every layer width <= 32 P).  ROWS: the products of the boxes whose problem is the round's
+// read the network from shared memory in padded rows (dense_rs); other boxes, and ROWS = false, read the images
+// from global memory with shuffle broadcasts (dense_warp).  Both sum in the same order.
+template <int P, bool ROWS>
 __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     k_alpha_warp(BoundArgs a, int steps, float lr, float *alpha_g, float *m_g, float *v_g, const AdamTable tab)
 {
@@ -73,32 +132,75 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     float *sm = reinterpret_cast<float *>(smem4);
     const NetDesc &N = a.net;
     const int s = N.s, k = N.k, L = N.L, Hm = a.batch.Hmax, d = a.d, sumh = N.sumh, sw = sumh + s, d4 = pad4(d);
-    const float *fwd = a.fwd, *bwd = a.bwd;
-    float *p = sm;
-    if (WSMEM) {
-        for (int i = threadIdx.x; i < N.img_floats / 4; i += blockDim.x) {
-            smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
-            reinterpret_cast<float4 *>(sm + N.img_floats)[i] = reinterpret_cast<const float4 *>(a.bwd)[i];
-        }
-        fwd = sm;
-        bwd = sm + N.img_floats;
-        p += 2 * N.img_floats;
-    }
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *mu = p + (size_t)wib * 2 * d4;  // coefficients of u, per warp
-    float *us = mu + d4;                   // concretizing point u*, per warp
+    __shared__ RowsLayout R;
+    if (threadIdx.x == 0) R = rows_layout(N);
     __syncthreads();
+    float *rows = sm;
+    float *p = sm + (ROWS ? R.floats : 0);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *vin = p + (size_t)wib * (N.maxw_p + 2 * d4);  // the warp's product input
+    float *mu = vin + N.maxw_p;                          // coefficients of u, per warp
+    float *us = mu + d4;                                 // concretizing point u*, per warp
 
     const int nlive = live_count(a.n, a.d_n);
     const size_t hs = (size_t)Hm * sumh;  // per-box stride of the [H][sumh] arrays
     const bool opt = steps > 0;           // steps == 0: one bound with the adaptive slopes, no adjoint
-    for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {
+    int loaded = -1;                      // the problem whose rows are in shared memory
+    for (int base = blockIdx.x * kWarps; base < nlive; base += gridDim.x * kWarps) {
+        // a round of kWarps boxes; the rows of its first box's problem serve every box of that problem
+        const int pr = row_problem(a.batch, base);
+        if (ROWS && pr != loaded) {
+            __syncthreads();
+            const float *F = a.fwd + (size_t)pr * N.img_floats, *Bw = a.bwd + (size_t)pr * N.img_floats;
+            for (int l = 1; l <= L; ++l) {
+                const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]);
+                for (int i = threadIdx.x; i < Np * Kp; i += blockDim.x) {
+                    const int q = i / Kp, c = i % Kp;
+                    rows[R.offF[l] + q * R.ldF[l] + c] = Bw[N.bwd_w[l] + i];
+                }
+                for (int i = threadIdx.x; i < Kp * Np; i += blockDim.x) {
+                    const int c = i / Np, q = i % Np;
+                    rows[R.offB[l] + c * R.ldB[l] + q] = F[N.fwd_w[l] + i];
+                }
+                for (int i = threadIdx.x; i < Np; i += blockDim.x) rows[R.offb[l] + i] = F[N.fwd_b[l] + i];
+            }
+            __syncthreads();
+            loaded = pr;
+        }
+        const int box = base + wib;
+        if (box >= nlive) continue;
         // the box's problem: weights, start, goal, horizon and rho
         const int pb = row_problem(a.batch, box);
-        if (!WSMEM) {
-            fwd = a.fwd + (size_t)pb * N.img_floats;
-            bwd = a.bwd + (size_t)pb * N.img_floats;
-        }
+        const bool use_rows = ROWS && pb == loaded;
+        const float *fwd = a.fwd + (size_t)pb * N.img_floats, *bwd = a.bwd + (size_t)pb * N.img_floats;
+        // forward product of layer l: out[q] = b[q] + sum_c W[q][c] in[c]
+        auto dense_f = [&](const float (&in)[P], int l, float (&out)[P]) {
+            const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]);
+            if (use_rows) {
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    if (lane + 32 * q < Kp) vin[lane + 32 * q] = in[q];
+                __syncwarp();
+                dense_rs<P>(vin, Kp, rows + R.offF[l], R.ldF[l], Np, rows + R.offb[l], out);
+                __syncwarp();
+            } else {
+                dense_warp<P>(in, Kp, fwd + N.fwd_w[l], Np, fwd + N.fwd_b[l], out);
+            }
+        };
+        // backward product of layer l: out[c] = sum_q in[q] W[q][c]
+        auto dense_b = [&](const float (&in)[P], int l, float (&out)[P]) {
+            const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]);
+            if (use_rows) {
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    if (lane + 32 * q < Np) vin[lane + 32 * q] = in[q];
+                __syncwarp();
+                dense_rs<P>(vin, Np, rows + R.offB[l], R.ldB[l], Kp, nullptr, out);
+                __syncwarp();
+            } else {
+                dense_warp<P>(in, Np, bwd + N.bwd_w[l], Kp, nullptr, out);
+            }
+        };
         const float *x0 = a.x0 + (size_t)pb * s, *goal = a.goal + (size_t)pb * s;
         const int H = problem_H(a.batch, pb, a.H), dp = k * H;
         const float rho = problem_rho(a.batch, pb, a.rho);
@@ -156,12 +258,12 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                     e = warp_sum_ru(e);
                     cst = __fadd_rd(cst, c);
                     mg = __fmaf_ru(N.gam[L], e, mg);
-                    dense_warp<P>(A, NpL, bwd + N.bwd_w[L], pad4(N.dims[L - 1]), nullptr, tmp);
+                    dense_b(A, L, tmp);
 #pragma unroll
                     for (int q = 0; q < P; ++q) A[q] = tmp[q];
                 }
                 for (int l = L - 1; l >= 1; --l) {
-                    const int dl = N.dims[l], Npl = pad4(dl);
+                    const int dl = N.dims[l];
                     const float *bl = bwd + N.bwd_b[l];
                     float c = 0.f, eg = 0.f, er = 0.f;
 #pragma unroll
@@ -191,7 +293,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                     er = warp_sum_ru(er);
                     cst = __fadd_rd(cst, c);
                     mg = __fadd_ru(mg, __fmaf_ru(N.gam[l], eg, __fmul_ru(kTwoU, er)));
-                    dense_warp<P>(A, Npl, bwd + N.bwd_w[l], pad4(N.dims[l - 1]), nullptr, tmp);
+                    dense_b(A, l, tmp);
 #pragma unroll
                     for (int q = 0; q < P; ++q) A[q] = tmp[q];
                 }
@@ -291,7 +393,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                     Z[q] = c < s ? x[q] : (c < s + k ? us[t * k + (c - s)] : 0.f);
                 }
                 for (int l = 1; l <= L; ++l) {
-                    dense_warp<P>(Z, pad4(N.dims[l - 1]), fwd + N.fwd_w[l], pad4(N.dims[l]), fwd + N.fwd_b[l], tmp);
+                    dense_f(Z, l, tmp);
                     if (l < L) {
                         const int dl = N.dims[l];
 #pragma unroll
@@ -337,12 +439,13 @@ static cudaError_t launch_warp_variant(const BoundArgs &a, int steps, float lr, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const size_t per_warp = 2 * (size_t)pad4(a.d) * kWarps * sizeof(float);
-    const size_t with_img = per_warp + 2 * (size_t)a.net.img_floats * sizeof(float);
-    const bool wsmem = a.batch.P <= 1 && with_img + 1024 <= (size_t)max_optin;
-    const size_t smem = wsmem ? with_img : per_warp;
+    const size_t per_warp = (size_t)(a.net.maxw_p + 2 * pad4(a.d)) * kWarps * sizeof(float);
+    const size_t with_rows = per_warp + (size_t)rows_layout(a.net).floats * sizeof(float);
+    // the padded rows pay while a few CTAs still fit on an SM
+    const bool rows = with_rows * 2 + 2048 <= (size_t)max_optin;
+    const size_t smem = rows ? with_rows : per_warp;
     if (smem + 1024 > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    auto kern = wsmem ? k_alpha_warp<P, true> : k_alpha_warp<P, false>;
+    auto kern = rows ? k_alpha_warp<P, true> : k_alpha_warp<P, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
