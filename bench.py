@@ -50,6 +50,25 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Each rank plans its own independent problem (weak scaling, no data-path collective)."""
+    return SEED + rank
+
+
+def max_over_ranks(ms, device):
+    """The slowest rank's time: the whole job takes as long as its last rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * ws / (ms / 1e3)
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
 
@@ -261,7 +280,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n_pick = args.boxes // 2
-    st = BabState("pushing", SEED + rank, dev, n_pick, args.precision, args.bound_precision,
+    st = BabState("pushing", rank_seed(rank), dev, n_pick, args.precision, args.bound_precision,
                   fixed_launch=not args.no_graph, autotune=not args.no_autotune)
     for _ in range(args.warmup):
         st.step()
@@ -287,9 +306,7 @@ def run_ours(args):
         dist.barrier()
     ms = t0.elapsed_time(t1)
     if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(ms, dev)
     clocks = clk.summary()
     # per-kernel times on the launching stream (eager steps, same shapes)
     for _ in range(3):
@@ -307,7 +324,7 @@ def run_ours(args):
     manip = None if args.no_manip else manip_scale(dev)
 
     boxes = st.nb * args.steps * ws
-    value = boxes / (ms / 1e3)
+    value = job_rate(st.nb * args.steps, ws, ms)
     rsteps = boxes * st.M * st.H / (ms / 1e3)
     macs = sum(a * b for a, b in zip(st.p["dims"][1:], st.p["dims"][:-1]))
     flops_roll = 2.0 * st.nb * st.M * st.H * macs
