@@ -23,6 +23,10 @@
  *                         Theorem 2 (concretization) in box form.
  *   oracle_alpha_grad     d(lower bound)/d(alpha) for the free lower slopes of
  *                         Lemma 1, by a forward pass of the relaxed network.
+ *   oracle_search_bounds  search-integrated (empirical) intermediate bounds,
+ *                         Section 3.2 approach 2.
+ *   oracle_crown_given    CROWN with given intermediate bounds and propagation
+ *                         early-stop, Section 3.2 approach 1 / Algorithm 3.
  *   oracle_box_grad       d(lower bound)/d(box faces), through the relaxation
  *                         choices and the interval bounds.
  *   oracle_adam_ascent    projected Adam ascent on alpha.
@@ -411,19 +415,26 @@ typedef struct {
 static crown_out crown_box(const onet *N, int H, double rho, const double *x0, const double *goal,
                            const double *lo, const double *hi, const double *pre_lo, const double *pre_hi,
                            const double *x_lo, const double *x_hi, const double *alpha, double *mu,
-                           double *ustar, double *A_pre, double *atan)
+                           double *ustar, double *A_pre, double *atan, int t_stop)
 {
     int s = N->s, k = N->k, L = N->L, sumh = N->sumh;
     double lam[ORC_MAX_WIDTH], A[ORC_MAX_WIDTH], An[ORC_MAX_WIDTH];
     double cst = 0.0, cabs = 0.0;
-    double *mu_loc = (double *)malloc(sizeof(double) * k * H);
+    double *mu_loc = (double *)calloc((size_t)k * H, sizeof(double));
 
-    /* tangent coefficients a_{t,i} = 2 m and constants -2 m g - m^2 */
+    /* tangent coefficients a_{t,i} = 2 m and constants -2 m g - m^2 for the cost terms the backward pass
+       carries (t > t_stop); the terms at or before the early-stop step are bounded on their intervals */
     double *a = (double *)calloc((size_t)(H + 1) * s, sizeof(double));
     for (int t = 1; t <= H; ++t) {
         for (int i = 0; i < s; ++i) {
             double Ls = x_lo[(size_t)t * s + i] - goal[i];
             double Us = x_hi[(size_t)t * s + i] - goal[i];
+            if (t <= t_stop) {
+                double v = sq_min(Ls, Us);
+                cst += v;
+                cabs += v;
+                continue;
+            }
             double m = 0.5 * (Ls + Us);
             a[(size_t)t * s + i] = 2.0 * m;
             cst += -2.0 * m * goal[i] - m * m;
@@ -432,7 +443,7 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
     }
     for (int i = 0; i < s; ++i) lam[i] = a[(size_t)H * s + i];
 
-    for (int t = H - 1; t >= 0; --t) {
+    for (int t = H - 1; t >= t_stop; --t) {
         /* last linear layer: A = lam on z_L */
         int nL = N->dims[L], nLm = N->dims[L - 1];
         for (int q = 0; q < nL; ++q) A[q] = lam[q];
@@ -475,9 +486,19 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
         for (int j = 0; j < k; ++j) mu_loc[t * k + j] = A[s + j];
         for (int i = 0; i < s; ++i) lam[i] = lam[i] + A[i] + (t >= 1 ? a[(size_t)t * s + i] : 0.0);
     }
-    for (int i = 0; i < s; ++i) {
-        cst += lam[i] * x0[i];
-        cabs += fabs(lam[i] * x0[i]);
+    if (t_stop == 0) {
+        for (int i = 0; i < s; ++i) {
+            cst += lam[i] * x0[i];
+            cabs += fabs(lam[i] * x0[i]);
+        }
+    } else {
+        /* early stop: concretize the coefficient of x_{t_stop} on that state's interval (Theorem 2, box form) */
+        for (int i = 0; i < s; ++i) {
+            double a_ = lam[i] * x_lo[(size_t)t_stop * s + i], b_ = lam[i] * x_hi[(size_t)t_stop * s + i];
+            double v = a_ < b_ ? a_ : b_;
+            cst += v;
+            cabs += fabs(v);
+        }
     }
 
     double lb = cst;
@@ -522,7 +543,7 @@ int oracle_crown(int L, const int *dims, const double *params, int s, int k, int
         ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
         crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, alpha ? alpha + (size_t)i * nh : NULL,
                                 lin_coef ? lin_coef + (size_t)i * d : NULL, ustar ? ustar + (size_t)i * d : NULL,
-                                A_pre ? A_pre + (size_t)i * nh : NULL, NULL);
+                                A_pre ? A_pre + (size_t)i * nh : NULL, NULL, 0);
         lb[i] = o.lb;
         if (lin_const) lin_const[i] = o.lin_const;
         if (scale) scale[i] = o.scale;
@@ -531,6 +552,89 @@ int oracle_crown(int L, const int *dims, const double *params, int s, int k, int
     free(pu);
     free(xl);
     free(xu);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own bounding (Section 3.2, Appendix B.2)                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Search-integrated bounds: per box, the minimum and maximum over the search's
+ * samples (the same counter-based samples as oracle_rollout) of every hidden
+ * pre-activation (pre_lo/pre_hi [n][H][sumh]) and of every state x_t
+ * (x_lo/x_hi [n][H+1][s], x_0 exact).  Underestimates of the true ranges.
+ */
+int oracle_search_bounds(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                         const double *x0, const double *goal, int n, const float *lo, const float *hi,
+                         const uint64_t *id, int M, uint64_t seed, double *pre_lo, double *pre_hi, double *x_lo,
+                         double *x_hi)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    int d = k * H, sumh = N.sumh;
+    size_t nh = (size_t)H * sumh, nx = (size_t)(H + 1) * s;
+    double *u = (double *)malloc(sizeof(double) * d);
+    double *traj = (double *)malloc(sizeof(double) * nx);
+    double *pre = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    for (int i = 0; i < n; ++i) {
+        double *pl = pre_lo + (size_t)i * nh, *pu = pre_hi + (size_t)i * nh;
+        double *xl = x_lo + (size_t)i * nx, *xu = x_hi + (size_t)i * nx;
+        for (size_t q = 0; q < nh; ++q) {
+            pl[q] = INFINITY;
+            pu[q] = -INFINITY;
+        }
+        for (size_t q = 0; q < nx; ++q) {
+            xl[q] = INFINITY;
+            xu[q] = -INFINITY;
+        }
+        for (int m = 0; m < M; ++m) {
+            for (int j = 0; j < d; ++j)
+                u[j] = oracle_sample(seed, id[i], (uint32_t)m, (uint32_t)j, lo[(size_t)i * d + j], hi[(size_t)i * d + j]);
+            oracle_objective(L, dims, params, s, k, H, rho, x0, goal, u, traj, pre);
+            for (size_t q = 0; q < nh; ++q) {
+                if (pre[q] < pl[q]) pl[q] = pre[q];
+                if (pre[q] > pu[q]) pu[q] = pre[q];
+            }
+            for (size_t q = 0; q < nx; ++q) {
+                if (traj[q] < xl[q]) xl[q] = traj[q];
+                if (traj[q] > xu[q]) xu[q] = traj[q];
+            }
+        }
+    }
+    free(u);
+    free(traj);
+    free(pre);
+    return 0;
+}
+
+/*
+ * CROWN with given intermediate bounds and propagation early-stop
+ * (Algorithm 3 with the early-stop set S = {x_{t_stop}}): the cost terms after
+ * step t_stop are tangent-linearised and carried backward through steps
+ * H-1 .. t_stop, where the propagation stops and the remaining coefficient of
+ * x_{t_stop} is concretized on that state's interval (Theorem 2, box form);
+ * the cost terms at steps 1 .. t_stop are bounded on their intervals.  With
+ * t_stop = 0 and the interval bounds of oracle_ibp this is oracle_crown; with
+ * search-integrated bounds it is the paper's estimate, not a sound bound.
+ * Adaptive lower slopes; outputs lb [n].
+ */
+int oracle_crown_given(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                       const double *x0, const double *goal, int n, const double *lo, const double *hi,
+                       const double *pre_lo, const double *pre_hi, const double *x_lo, const double *x_hi,
+                       int t_stop, double *lb)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    if (t_stop < 0 || t_stop > H) return -1;
+    int d = k * H;
+    size_t nh = (size_t)H * N.sumh, nx = (size_t)(H + 1) * s;
+    for (int i = 0; i < n; ++i) {
+        crown_out o = crown_box(&N, H, rho, x0, goal, lo + (size_t)i * d, hi + (size_t)i * d, pre_lo + (size_t)i * nh,
+                                pre_hi + (size_t)i * nh, x_lo + (size_t)i * nx, x_hi + (size_t)i * nx, NULL, NULL,
+                                NULL, NULL, NULL, t_stop);
+        lb[i] = o.lb;
+    }
     return 0;
 }
 
@@ -572,7 +676,7 @@ int oracle_alpha_grad(int L, const int *dims, const double *params, int s, int k
         const double *al = alpha ? alpha + (size_t)i * nh : NULL;
         double *g = grad_alpha + (size_t)i * nh;
         ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
-        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, NULL, us, Ap, at);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, NULL, us, Ap, at, 0);
         lb[i] = o.lb;
 
         /* forward pass of the relaxed network from x_0 and u* */
@@ -676,7 +780,7 @@ int oracle_box_grad(int L, const int *dims, const double *params, int s, int k, 
         const double *al = alpha ? alpha + (size_t)i * nh : NULL;
         double *glo = grad_lo + (size_t)i * d, *ghi = grad_hi + (size_t)i * d;
         ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
-        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, mu, us, Ap, at);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, mu, us, Ap, at, 0);
         lb[i] = o.lb;
 
         /* relaxed network from x_0 and u*: z~ and the state x~_t, and the sensitivities */

@@ -229,6 +229,50 @@ def box_grad(problem, lo, hi, alpha=None):
     return lb, glo, ghi
 
 
+def search_bounds(problem, lo, hi, ids, samples, seed):
+    """Search-integrated bounds (Section 3.2): per box the min / max over the rollout samples of every hidden
+    pre-activation ([n,H,sumh]) and state ([n,H+1,s])."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _f(lo)
+    hi, phi = _f(hi)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    n, d = lo.shape
+    H = int(problem["H"])
+    pl = np.zeros((n, H, max(net.sumh, 1)))
+    pu = np.zeros_like(pl)
+    xl = np.zeros((n, H + 1, net.s))
+    xu = np.zeros_like(xl)
+    rc = lib().oracle_search_bounds(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi,
+                                    ids.ctypes.data_as(_c_u64_p), ctypes.c_int(samples), ctypes.c_uint64(seed),
+                                    pl.ctypes.data_as(_c_double_p), pu.ctypes.data_as(_c_double_p),
+                                    xl.ctypes.data_as(_c_double_p), xu.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return pl[:, :, :net.sumh], pu[:, :, :net.sumh], xl, xu
+
+
+def crown_given(problem, lo, hi, pre_lo, pre_hi, x_lo, x_hi, t_stop=0):
+    """CROWN with given intermediate bounds and propagation early-stop at step t_stop (Algorithm 3)."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _d(lo)
+    hi, phi = _d(hi)
+    n = lo.shape[0]
+    H = int(problem["H"])
+    sh = max(net.sumh, 1)
+    pl = np.zeros((n, H, sh))
+    pu = np.zeros((n, H, sh))
+    pl[:, :, :net.sumh] = pre_lo
+    pu[:, :, :net.sumh] = pre_hi
+    xl = np.ascontiguousarray(x_lo, dtype=np.float64)
+    xu = np.ascontiguousarray(x_hi, dtype=np.float64)
+    lb = np.zeros(n)
+    rc = lib().oracle_crown_given(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi,
+                                  pl.ctypes.data_as(_c_double_p), pu.ctypes.data_as(_c_double_p),
+                                  xl.ctypes.data_as(_c_double_p), xu.ctypes.data_as(_c_double_p),
+                                  ctypes.c_int(int(t_stop)), lb.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return lb
+
+
 def adaptive_alpha(problem, lo, hi):
     """The adaptive lower slopes (1 where u >= -l, else 0) of every neuron, from the oracle's IBP bounds."""
     _, pl, pu, _, _ = ibp(problem, lo, hi)

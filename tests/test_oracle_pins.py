@@ -604,3 +604,78 @@ def test_box_gradient_stable_one_step_closed_form(oracle):
         tol = 1e-10 * max(np.abs(B).sum() * np.abs(m).max(), np.abs(mu).max(), 1.0)  # FP64 cancellation scale
         np.testing.assert_allclose(glo[i], common + np.where(mu >= 0, mu, 0), rtol=1e-9, atol=tol)
         np.testing.assert_allclose(ghi[i], common + np.where(mu < 0, mu, 0), rtol=1e-9, atol=tol)
+
+
+# --------------------------------------------------------------------------
+# The paper's bounding: search-integrated bounds and propagation early-stop
+# --------------------------------------------------------------------------
+
+def test_search_bounds_are_sample_extremes(oracle):
+    """The empirical bounds are, by definition, the min / max over the search's samples: recomputed here by
+    evaluating every sample's trajectory with a direct numpy forward pass."""
+    p = W.config_problem("tiny", 3)
+    lo, hi, ids = W.random_boxes(10, 3, seed=4, min_width=0.2, max_width=1.0)
+    M, seed = 17, 5
+    pl, pu, xl, xu = oracle.search_bounds(p, lo, hi, ids, M, seed)
+    layers = [(Wl.astype(np.float64), bl.astype(np.float64)) for Wl, bl in W.unpack_params(p)]
+    for i in range(3):
+        pre_all, x_all = [], []
+        for m in range(M):
+            u = np.array([oracle.lib().oracle_sample(seed, int(ids[i]), m, j, float(lo[i, j]), float(hi[i, j]))
+                          for j in range(10)], dtype=np.float64)
+            x = p["x0"].astype(np.float64)
+            pres, xs = [], [x.copy()]
+            for t in range(p["H"]):
+                a = np.concatenate([x, u[t * 2:t * 2 + 2]])
+                hs = []
+                for l, (Wl, bl) in enumerate(layers):
+                    z = Wl @ a + bl
+                    if l < len(layers) - 1:
+                        hs.append(z)
+                        a = np.maximum(z, 0)
+                    else:
+                        x = x + z
+                pres.append(np.concatenate(hs))
+                xs.append(x.copy())
+            pre_all.append(pres)
+            x_all.append(xs)
+        pre_all, x_all = np.array(pre_all), np.array(x_all)
+        np.testing.assert_allclose(pl[i], pre_all.min(axis=0), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(pu[i], pre_all.max(axis=0), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(xl[i], x_all.min(axis=0), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(xu[i], x_all.max(axis=0), rtol=1e-12, atol=1e-12)
+
+
+def test_crown_given_reduces_to_crown_and_to_interval_costs(oracle):
+    """With the interval bounds and no early stop it is the plain CROWN bound; stopping at the last step leaves
+    only the cost terms' interval minima plus the exact minimum of rho ||u||^2 on the box."""
+    p = scaled_problem(4, 2, [32, 32], 5, 0.01, seed=81, scale=0.3)
+    lo, hi, _ = W.random_boxes(10, 4, seed=82, min_width=0.3, max_width=0.8)
+    _, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    np.testing.assert_allclose(oracle.crown_given(p, lo, hi, pl, pu, xl, xu, 0), oracle.crown(p, lo, hi)["lb"],
+                               rtol=1e-13)
+    H, g, rho = p["H"], p["goal"].astype(np.float64), p["rho"]
+    lb_H = oracle.crown_given(p, lo, hi, pl, pu, xl, xu, H)
+    for i in range(4):
+        Ls, Us = xl[i, 1:] - g, xu[i, 1:] - g
+        cost = np.where((Ls <= 0) & (Us >= 0), 0.0, np.minimum(Ls * Ls, Us * Us)).sum()
+        lo_, hi_ = lo[i].astype(np.float64), hi[i].astype(np.float64)
+        act = np.where((lo_ <= 0) & (hi_ >= 0), 0.0, np.minimum(lo_ * lo_, hi_ * hi_)).sum()
+        assert lb_H[i] == pytest.approx(cost + rho * act, rel=1e-12)
+
+
+@pytest.mark.parametrize("t_stop", [1, 3])
+def test_crown_given_sound_with_sound_bounds(oracle, t_stop):
+    """Early stop with sound (interval) bounds is still a sound bound: below the objective at sampled points of
+    the box.  The search's empirical ranges lie inside the sound ones (the samples are points of the box)."""
+    p = scaled_problem(4, 2, [32, 32], 5, 0.0, seed=83, scale=0.3)
+    lo, hi, ids = W.random_boxes(10, 3, seed=84, min_width=0.2, max_width=0.6)
+    _, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    lb = oracle.crown_given(p, lo, hi, pl, pu, xl, xu, t_stop)
+    rng = np.random.default_rng(2)
+    for i in range(3):
+        u = lo[i] + rng.uniform(size=(300, 10)) * (hi[i] - lo[i])
+        assert lb[i] <= min(oracle.objective(p, x.astype(np.float64)) for x in u)
+    epl, epu, exl, exu = oracle.search_bounds(p, lo, hi, ids, 64, 9)
+    assert np.all(epl >= pl - 1e-9) and np.all(epu <= pu + 1e-9)  # the samples lie inside the sound ranges
+    assert np.all(exl >= xl - 1e-9) and np.all(exu <= xu + 1e-9)
