@@ -124,6 +124,35 @@ int bab_rollout(bab_ctx *ctx, const float *x0, const float *goal, int horizon, f
                 int precision, float *ub, float *best_u, double *inc_val, float *inc_u, void *stream);
 
 /*
+ * The paper's own bounding (Section 3.2; Appendix B.2, Algorithm 3).
+ *
+ * bab_rollout_search_bounds: bab_rollout in FP32 (the same samples, ub,
+ * best_u, incumbent) that also records, per box, the minimum and maximum over
+ * its samples of every hidden pre-activation (pre_lo/pre_hi, device
+ * float[n][H][sumh]) and of every state (x_lo/x_hi, device float[n][H+1][s];
+ * x_0 exact): the search-integrated intermediate bounds.  They may
+ * underestimate the true ranges.
+ *
+ * bab_bound_crown_given: the CROWN bound (FP32, adaptive slopes) with the
+ * caller's intermediate bounds in place of bab_bound_ibp's, and propagation
+ * early-stop at step t_stop (0 <= t_stop <= H; the early-stop set is the
+ * state x_{t_stop}): the cost terms after t_stop are carried back to
+ * x_{t_stop} and concretized on its interval, those at steps 1 .. t_stop are
+ * bounded on their intervals, rho ||u||^2 on the box.  t_stop = 0 propagates
+ * to the input.  With search-integrated bounds the result is the paper's
+ * estimate of the lower bound, not a sound bound, and no rounding margin is
+ * subtracted.  lb device float[n].
+ * Errors: BAB_ERR_INVALID_ARG (t_stop out of range, null arrays), BAB_ERR_SHAPE, BAB_ERR_CUDA.
+ */
+int bab_rollout_search_bounds(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho,
+                              const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                              int samples, uint64_t seed, float *ub, float *best_u, double *inc_val, float *inc_u,
+                              float *pre_lo, float *pre_hi, float *x_lo, float *x_hi, void *stream);
+int bab_bound_crown_given(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                          const float *hi, int n, const int *d_n, const float *pre_lo, const float *pre_hi,
+                          const float *x_lo, const float *x_hi, int t_stop, float *lb, void *stream);
+
+/*
  * The incumbent step of Algorithm 2 on its own (bab_rollout does it when given
  * inc_val): the box with the smallest ub (lowest index on ties) has its plan
  * best_u re-evaluated in FP64; if that value is below *inc_val it becomes the

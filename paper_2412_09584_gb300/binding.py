@@ -79,6 +79,9 @@ def load(path: str = LIB_PATH):
                                          _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.bab_update_incumbent.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P]
     L.bab_box_grad.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _P]
+    L.bab_rollout_search_bounds.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _P, _P, _P,
+                                            _P, _P, _P, _P, _P, _P]
+    L.bab_bound_crown_given.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P]
     L.bab_set_variant.argtypes = [_P, _I, _I]
     L.bab_set_rescore_topk.argtypes = [_P, _I]
     L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
@@ -315,4 +318,27 @@ def bab_box_grad(ctx, x0, goal, horizon, rho, lo, hi, n, lb, grad_lo, grad_hi, a
                              _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), int(n), _ptr(d_n, torch.int32),
                              _ptr(alpha, f32), _ptr(lb, f32, "lb"), _ptr(grad_lo, f32, "grad_lo"),
                              _ptr(grad_hi, f32, "grad_hi"), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_rollout_search_bounds(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, seed, ub, pre_lo, pre_hi, x_lo,
+                              x_hi, best_u=None, inc_val=None, inc_u=None, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_rollout_search_bounds(
+        ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho), _ptr(lo, f32, "lo"),
+        _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), int(n), _ptr(d_n, torch.int32), int(samples), int(seed),
+        _ptr(ub, f32, "ub"), _ptr(best_u, f32), _ptr(inc_val, torch.float64), _ptr(inc_u, f32),
+        _ptr(pre_lo, f32, "pre_lo"), _ptr(pre_hi, f32, "pre_hi"), _ptr(x_lo, f32, "x_lo"), _ptr(x_hi, f32, "x_hi"),
+        _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_bound_crown_given(ctx, x0, goal, horizon, rho, lo, hi, n, pre_lo, pre_hi, x_lo, x_hi, t_stop, lb, d_n=None,
+                          stream=None):
+    f32 = torch.float32
+    rc = load().bab_bound_crown_given(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                                      _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), int(n), _ptr(d_n, torch.int32),
+                                      _ptr(pre_lo, f32, "pre_lo"), _ptr(pre_hi, f32, "pre_hi"),
+                                      _ptr(x_lo, f32, "x_lo"), _ptr(x_hi, f32, "x_hi"), int(t_stop),
+                                      _ptr(lb, f32, "lb"), _stream(stream))
     _check(ctx, rc)

@@ -461,6 +461,83 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     return BAB_OK;
 }
 
+int bab_rollout_search_bounds(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                              const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
+                              float *ub, float *best_u, double *inc_val, float *inc_u, float *pre_lo, float *pre_hi,
+                              float *x_lo, float *x_hi, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (samples < 1) return fail(c, BAB_ERR_SHAPE, "samples must be >= 1");
+    if (n > 0 && (!id || !ub || !pre_lo || !pre_hi || !x_lo || !x_hi))
+        return fail(c, BAB_ERR_INVALID_ARG, "id, ub and the four bound arrays are required");
+    if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
+    if (inc_val && !best_u) return fail(c, BAB_ERR_INVALID_ARG, "the incumbent update needs best_u");
+    if (n == 0) return BAB_OK;
+    rc = ensure_scratch(c, (size_t)n * sizeof(unsigned long long) + 256);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    RolloutArgs a{};
+    a.net = c->net;
+    a.batch.P = 1;
+    a.batch.Hmax = H;
+    a.fwd = c->d_fwd;
+    a.raw = c->d_raw;
+    a.x0 = x0;
+    a.goal = goal;
+    a.lo = lo;
+    a.hi = hi;
+    a.id = id;
+    a.n = n;
+    a.d_n = d_n;
+    a.H = H;
+    a.M = samples;
+    a.d = c->net.k * H;
+    a.rho = rho;
+    a.seed = seed;
+    a.keys = reinterpret_cast<unsigned long long *>(c->scratch);
+    a.ub = ub;
+    a.best_u = best_u;
+    a.inc_val = inc_val;
+    a.inc_u = inc_u;
+    a.status = c->d_status;
+    a.emp_pre_lo = reinterpret_cast<uint32_t *>(pre_lo);
+    a.emp_pre_hi = reinterpret_cast<uint32_t *>(pre_hi);
+    a.emp_x_lo = reinterpret_cast<uint32_t *>(x_lo);
+    a.emp_x_hi = reinterpret_cast<uint32_t *>(x_hi);
+    launch_emp_init(a, st);
+    cudaError_t e = launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, st);
+    if (e == cudaSuccess) {
+        launch_emp_finish(a, st);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "search-bound rollout kernels");
+    return BAB_OK;
+}
+
+int bab_bound_crown_given(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                          const float *hi, int n, const int *d_n, const float *pre_lo, const float *pre_hi,
+                          const float *x_lo, const float *x_hi, int t_stop, float *lb, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (t_stop < 0 || t_stop > H) return fail(c, BAB_ERR_INVALID_ARG, "t_stop must be in [0, horizon]");
+    if (n > 0 && (!lb || !pre_lo || !pre_hi || !x_lo || !x_hi))
+        return fail(c, BAB_ERR_INVALID_ARG, "lb and the four bound arrays are required");
+    if (n == 0) return BAB_OK;
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    a.pre_lo = const_cast<float *>(pre_lo);
+    a.pre_hi = const_cast<float *>(pre_hi);
+    a.x_lo = const_cast<float *>(x_lo);
+    a.x_hi = const_cast<float *>(x_hi);
+    a.S = nullptr;  // given bounds: an estimate, no rounding margin
+    a.t_stop = t_stop;
+    a.lb = lb;
+    cudaError_t e = launch_crown(a, c->num_sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
+    return BAB_OK;
+}
+
 int bab_update_incumbent(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *ub,
                          const float *best_u, int n, const int *d_n, double *inc_val, float *inc_u, void *stream)
 {

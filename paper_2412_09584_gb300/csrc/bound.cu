@@ -294,13 +294,31 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
     float *mg = p; p += RBT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool has_alpha = v.alpha != nullptr;
+    const int ts = a.t_stop;              // early stop: propagate back to x_ts only
+    const bool with_margin = v.S != nullptr;
 
+    // early stop: the cost terms at steps 1 .. ts on their intervals, no coefficient of u before ts
+    if (ts > 0) {
+        for (int i = threadIdx.x; i < RBT * d4; i += NTT) mu[i] = 0.f;
+        for (int r = warp; r < RBT; r += NTT / 32) {
+            float c = 0.f;
+            if (r < nrows)
+                for (int q = lane; q < ts * s; q += 32) {
+                    const int t = 1 + q / s, i = q % s;
+                    const float g = a.goal[i];
+                    const size_t xi = ((size_t)r * (H + 1) + t) * s + i;
+                    c = __fadd_rd(c, sq_min_rd(__fsub_rd(v.x_lo[xi], g), __fsub_ru(v.x_hi[xi], g)));
+                }
+            c = warp_sum_rd(c);
+            if (lane == 0) cst[r] = c;
+        }
+    }
     // tangent of ||x_H - g||^2: coefficient 2m, constant -(2 m g + m^2)
     for (int r = warp; r < RBT; r += NTT / 32) {
         float c = 0.f;
         for (int i = lane; i < s; i += 32) {
             float aa = 0.f;
-            if (r < nrows) {
+            if (r < nrows && H > ts) {
                 const float g = a.goal[i];
                 const size_t xi = ((size_t)r * (H + 1) + H) * s + i;
                 const float Ls = __fsub_rd(v.x_lo[xi], g), Us = __fsub_ru(v.x_hi[xi], g);
@@ -312,13 +330,13 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
         }
         c = warp_sum_rd(c);
         if (lane == 0) {
-            cst[r] = c;
+            cst[r] = ts > 0 ? __fadd_rd(cst[r], c) : c;
             mg[r] = 0.f;
         }
     }
     __syncthreads();
 
-    for (int t = H - 1; t >= 0; --t) {
+    for (int t = H - 1; t >= ts; --t) {
         // last layer: A = lam on z_L (rows of W_L), constant lam . b_L
         {
             const int NpL = pad4(N.dims[L]);
@@ -330,7 +348,7 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
                     Ab[0][r * ld + q] = A;
                     if (q < s && r < nrows) {
                         c = __fmaf_rd(A, bL[q], c);
-                        e = __fmaf_ru(fabsf(A), v.S[((size_t)r * H + t) * sw + sumh + q], e);
+                        if (with_margin) e = __fmaf_ru(fabsf(A), v.S[((size_t)r * H + t) * sw + sumh + q], e);
                     }
                 }
                 c = warp_sum_rd(c);
@@ -363,8 +381,10 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
                         Ab[cur][r * ld + q] = Ap;
                         c = __fmaf_rd(A, ci, c);
                         c = __fmaf_rd(Ap, bl[q], c);
-                        eg = __fmaf_ru(fabsf(Ap), v.S[base * sw + N.hoff[l] + q], eg);
-                        if (D != 0.f && D != 1.f) er = __fmaf_ru(fabsf(Ap), fmaxf(-zl, zu), er);
+                        if (with_margin) {
+                            eg = __fmaf_ru(fabsf(Ap), v.S[base * sw + N.hoff[l] + q], eg);
+                            if (D != 0.f && D != 1.f) er = __fmaf_ru(fabsf(Ap), fmaxf(-zl, zu), er);
+                        }
                     }
                 } else {
                     for (int q = lane; q < dl; q += 32) Ab[cur][r * ld + q] = 0.f;
@@ -391,7 +411,7 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
                 const float Ax = Ab[cur][r * ld + i];
                 const float lo_ = lam[r * s4 + i];
                 float aa = 0.f, B;
-                if (t >= 1 && r < nrows) {
+                if (t > ts && t >= 1 && r < nrows) {
                     const float g = a.goal[i];
                     const size_t xi = ((size_t)r * (H + 1) + t) * s + i;
                     const float xl = v.x_lo[xi], xu = v.x_hi[xi];
@@ -406,7 +426,7 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
                 const float ln = (lo_ + Ax) + aa;
                 lam[r * s4 + i] = ln;
                 const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
-                e = __fmaf_ru(__fmul_ru(kTwoU, mag), B, e);
+                if (with_margin) e = __fmaf_ru(__fmul_ru(kTwoU, mag), B, e);
             }
             c = warp_sum_rd(c);
             e = warp_sum_ru(e);
@@ -421,7 +441,16 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
     // lam . x0, then Theorem 2 in box form: sum_j min_{u in [lo, hi]} mu_j u + rho u^2
     for (int r = warp; r < nrows; r += NTT / 32) {
         float c = 0.f, val = 0.f, e = 0.f;
-        for (int i = lane; i < s; i += 32) c = __fmaf_rd(lam[r * s4 + i], a.x0[i], c);
+        if (ts == 0) {
+            for (int i = lane; i < s; i += 32) c = __fmaf_rd(lam[r * s4 + i], a.x0[i], c);
+        } else {
+            // early stop: the coefficient of x_ts on that state's interval (Theorem 2, box form)
+            for (int i = lane; i < s; i += 32) {
+                const size_t xi = ((size_t)r * (H + 1) + ts) * s + i;
+                const float li = lam[r * s4 + i];
+                c = __fadd_rd(c, fminf(__fmul_rd(li, v.x_lo[xi]), __fmul_rd(li, v.x_hi[xi])));
+            }
+        }
         c = __fadd_rd(cst[r], warp_sum_rd(c));
         for (int j = lane; j < d; j += 32) {
             const float m_ = mu[r * d4 + j];

@@ -59,6 +59,9 @@ struct RolloutArgs {
     int stages;          // > 0: the image is streamed through a ring of `stages` buffers of stage_bytes
     int stage_bytes;
     size_t tc_img_stride;  // bytes between problems' tensor-core images (batched problems, streamed)
+    // search-integrated bounds (nullable): per box the min / max over the samples of every hidden
+    // pre-activation [n][H][sumh] and state [n][H+1][s], accumulated as order-preserving uint32 keys
+    uint32_t *emp_pre_lo, *emp_pre_hi, *emp_x_lo, *emp_x_hi;
     // BF16 rollouts: re-score in FP32 only the topk boxes of smallest BF16 ub (0: every box)
     int topk;
     unsigned long long *topk_t;  // [3] scratch: the selection threshold
@@ -91,6 +94,7 @@ struct BoundArgs {
     const uint8_t *tcb_img;  // backward image (W_l^T, BF16 hi then lo)
     const float *tc_bias;    // biases padded to multiples of 16 (offsets tc_boff)
     float *mu;               // [n][d] coefficients of u (lin_coef or scratch)
+    int t_stop;              // propagation early-stop step (0: back to the input); S == null: no margin
     uint32_t tmem_cols;
     int stages;              // > 0: the backward image is streamed through `stages` ring buffers
     int stage_bytes;
@@ -203,6 +207,9 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem);
 void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st);
 void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st);
+// search-integrated bounds around an FP32 rollout (a.emp_* set): key init before, float conversion after
+void launch_emp_init(const RolloutArgs &a, cudaStream_t st);
+void launch_emp_finish(const RolloutArgs &a, cudaStream_t st);
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st);
 cudaError_t launch_ibp(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);

@@ -47,10 +47,13 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
     const long long ntiles = (long long)nlive * tpb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Kp1 = pad4(s + k);
+    const bool emit = a.emp_pre_lo != nullptr;
+    const int Hm = a.batch.Hmax;
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int box = (int)(tile / tpb);
         const int m0 = (int)(tile % tpb) * R;
+        const int rv = a.M - m0 < R ? a.M - m0 : R;  // rows holding real samples
         // the box's problem: its weights, start, goal, horizon and rho
         const int pb = row_problem(a.batch, box);
         if (!WSMEM) img = a.fwd + (size_t)pb * N.img_floats;
@@ -87,8 +90,29 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
             float *in = act0, *out = act1;
             for (int l = 1; l <= L; ++l) {
                 const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]);
-                dense_rows_auto<R, NT>(in, ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, out, ld, l < L);
+                dense_rows_auto<R, NT>(in, ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, out, ld, l < L && !emit);
                 __syncthreads();
+                if (emit && l < L) {
+                    // search-integrated bounds: the tile's extremes of each pre-activation, then the ReLU
+                    const int dl = N.dims[l];
+                    for (int c = threadIdx.x; c < Np; c += NT) {
+                        float mn = INFINITY, mx = -INFINITY;
+                        for (int r = 0; r < R; ++r) {
+                            const float v = out[r * ld + c];
+                            if (r < rv) {
+                                mn = fminf(mn, v);
+                                mx = fmaxf(mx, v);
+                            }
+                            out[r * ld + c] = fmaxf(v, 0.f);
+                        }
+                        if (c < dl) {
+                            const size_t e = ((size_t)box * Hm + t) * N.sumh + N.hoff[l] + c;
+                            atomicMin(&a.emp_pre_lo[e], float_order(mn));
+                            atomicMax(&a.emp_pre_hi[e], float_order(mx));
+                        }
+                    }
+                    __syncthreads();
+                }
                 float *tmp = in; in = out; out = tmp;
             }
             // `in` holds the network output: residual step and per-row cost (one warp per row)
@@ -108,6 +132,20 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
                 if (lane == 0) cost[r] += c;
             }
             __syncthreads();
+            if (emit) {
+                // search-integrated bounds of the state x_{t+1}
+                for (int i = threadIdx.x; i < s; i += NT) {
+                    float mn = INFINITY, mx = -INFINITY;
+                    for (int r = 0; r < rv; ++r) {
+                        const float v = xs[r * pad4(s) + i];
+                        mn = fminf(mn, v);
+                        mx = fmaxf(mx, v);
+                    }
+                    const size_t e = ((size_t)box * (Hm + 1) + t + 1) * s + i;
+                    atomicMin(&a.emp_x_lo[e], float_order(mn));
+                    atomicMax(&a.emp_x_hi[e], float_order(mx));
+                }
+            }
         }
         // best (f, m) of the tile
         unsigned long long best = ~0ull;
@@ -288,6 +326,52 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, int variant, int num_sms, 
     launch_rollout_finalize(a, st);
     if (a.inc_val) launch_incumbent(a, st);
     return cudaGetLastError();
+}
+
+// Search-integrated bounds: key arrays start at the identities of min / max; after the rollout the keys turn
+// back into floats in place, and x_0 (known exactly) is written.
+__global__ void k_emp_init(uint32_t *lo, uint32_t *hi, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        lo[i] = 0xFFFFFFFFu;
+        hi[i] = 0u;
+    }
+}
+
+__global__ void k_emp_finish(uint32_t *lo, uint32_t *hi, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        lo[i] = __float_as_uint(float_unorder(lo[i]));
+        hi[i] = __float_as_uint(float_unorder(hi[i]));
+    }
+}
+
+__global__ void k_emp_x0(const RolloutArgs a)
+{
+    const int nlive = live_count(a.n, a.d_n), s = a.net.s, Hm = a.batch.Hmax;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)nlive * s;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long box = i / s;
+        const int c = (int)(i % s);
+        const float v = a.x0[(size_t)row_problem(a.batch, (int)box) * s + c];
+        a.emp_x_lo[(size_t)box * (Hm + 1) * s + c] = __float_as_uint(v);
+        a.emp_x_hi[(size_t)box * (Hm + 1) * s + c] = __float_as_uint(v);
+    }
+}
+
+void launch_emp_init(const RolloutArgs &a, cudaStream_t st)
+{
+    const long long nh = (long long)a.n * a.batch.Hmax * a.net.sumh, nx = (long long)a.n * (a.batch.Hmax + 1) * a.net.s;
+    if (nh > 0) k_emp_init<<<1024, 256, 0, st>>>(a.emp_pre_lo, a.emp_pre_hi, nh);
+    k_emp_init<<<1024, 256, 0, st>>>(a.emp_x_lo, a.emp_x_hi, nx);
+}
+
+void launch_emp_finish(const RolloutArgs &a, cudaStream_t st)
+{
+    const long long nh = (long long)a.n * a.batch.Hmax * a.net.sumh, nx = (long long)a.n * (a.batch.Hmax + 1) * a.net.s;
+    if (nh > 0) k_emp_finish<<<1024, 256, 0, st>>>(a.emp_pre_lo, a.emp_pre_hi, nh);
+    k_emp_finish<<<1024, 256, 0, st>>>(a.emp_x_lo, a.emp_x_hi, nx);
+    k_emp_x0<<<256, 256, 0, st>>>(a);
 }
 
 void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st)

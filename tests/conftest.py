@@ -17,3 +17,19 @@ def oracle():
     from oracle import oracle as O
     O.lib()
     return O
+
+
+@pytest.fixture
+def gp():
+    """Factory of GpuProblem contexts on cuda:0, destroyed after the test."""
+    from gpu_util import GpuProblem
+    made = []
+
+    def make(problem):
+        g = GpuProblem(problem)
+        made.append(g)
+        return g
+
+    yield make
+    for g in made:
+        g.close()

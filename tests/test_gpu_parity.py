@@ -24,19 +24,6 @@ def built():
     assert torch.cuda.is_available()
 
 
-@pytest.fixture
-def gp():
-    from gpu_util import GpuProblem
-    made = []
-
-    def make(problem):
-        g = GpuProblem(problem)
-        made.append(g)
-        return g
-
-    yield make
-    for g in made:
-        g.close()
 
 
 def bound_scale(o):
