@@ -132,7 +132,7 @@ class BabState:
     the same grids."""
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
-                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False):
+                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -177,6 +177,13 @@ class BabState:
         self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
         self.ev = []
         self.side = torch.cuda.Stream(device=device)
+        # the paper's bounding (search-integrated bounds, propagation early-stop at step search_stop): FP32 rollouts
+        # record the bounds, CROWN uses them
+        self.search_stop = search_stop
+        if search_stop is not None:
+            nb_ = max(self.nb, n0)
+            self.emp = [torch.empty(nb_, self.H, self.sumh, **f), torch.empty(nb_, self.H, self.sumh, **f),
+                        torch.empty(nb_, self.H + 1, self.p["s"], **f), torch.empty(nb_, self.H + 1, self.p["s"], **f)]
         self.variants = None
         if autotune:
             # tile shapes timed on the starting pool (outside any timed region)
@@ -203,8 +210,12 @@ class BabState:
         if events:
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
-        B.bab_rollout(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
-                      self.seed, self.rprec, P["ub"], self.best_u, d_n=d_n)
+        if self.search_stop is None:
+            B.bab_rollout(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
+                          self.seed, self.rprec, P["ub"], self.best_u, d_n=d_n)
+        else:
+            B.bab_rollout_search_bounds(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n,
+                                        self.M, self.seed, P["ub"], *self.emp, best_u=self.best_u, d_n=d_n)
         if events:
             e[1].record()
         # the FP64 incumbent re-score runs on a side stream, beside the bounds of the same boxes
@@ -213,7 +224,10 @@ class BabState:
         with torch.cuda.stream(self.side):
             B.bab_update_incumbent(self.ctx, self.x0, self.goal, self.H, self.rho, P["ub"], self.best_u, n,
                                    self.inc_val, self.inc_u, d_n=d_n)
-        if not self.alpha_steps:
+        if self.search_stop is not None:
+            B.bab_bound_crown_given(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n, *self.emp,
+                                    self.search_stop, P["lb"], d_n=d_n)
+        elif not self.alpha_steps:
             B.bab_bound_crown(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n, P["lb"],
                               precision=self.bprec, margin=self.margin, d_n=d_n)
         else:
@@ -322,6 +336,7 @@ def run_ours(args):
     ttg = None if args.no_time_to_gap else time_to_gap(dev)
     batched = None if args.no_batched else batched_bab(dev)
     manip = None if args.no_manip else manip_scale(dev)
+    paper_bounds = None if args.no_time_to_gap else paper_bounding_comparison(dev)
 
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
@@ -363,7 +378,8 @@ def run_ours(args):
            "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound": statistics.mean(bound_ms)},
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip}
+           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
+           "paper_bounding": paper_bounds}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -585,6 +601,38 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
             "live_rows_end": n, "live_rows_per_problem_end": [int(live.min()), int(live.max())],
             "gap_end": {"min": float(gaps.min()), "median": float(np.median(gaps)), "max": float(gaps.max())},
             "device_status": status}
+
+
+
+def paper_bounding_comparison(dev, iters=30, stops=(0, 2)):
+    """The paper's bounding (search-integrated bounds + propagation early-stop) against sound bounds in the same
+    BaB loop (alpha workload: tiny network, H = 5, 4096 children per iteration, 256 FP32 rollouts each): the
+    incumbent reached (the plan's objective, exact in FP64), the live pool left (how much was pruned) and the
+    time per iteration.  The estimated bounds are not sound, so they certify no gap."""
+    import torch
+    out = {"workload": "alpha: MLP 6-32-32-4, H=5, 4096 children per iteration, 256 FP32 rollouts each, "
+                       f"{iters} iterations"}
+    variants = {"sound_ibp_crown": None}
+    variants.update({f"search_bounds_stop_{t}": t for t in stops})
+    for name, stop in variants.items():
+        for warm in (True, False):
+            st = BabState("alpha", SEED, dev, 2048, "fp32", "fp32", pool_iters=iters + 2, search_stop=stop)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            curve = []
+            for _ in range(2 if warm else iters):
+                st.step()
+                if not warm:
+                    curve.append(float(st.inc_val.item()))
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t
+            n_live = int(st.counts[2].item())
+            st.close()
+        out[name] = {"incumbent": curve[-1], "incumbent_curve": [round(v, 6) for v in curve],
+                     "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters,
+                     "bound": "sound (interval + CROWN, margin)" if stop is None else
+                              f"estimate: search-integrated bounds, early stop at step {stop}"}
+    return out
 
 
 
