@@ -32,7 +32,10 @@
  *   oracle_adam_ascent    projected Adam ascent on alpha.
  *   oracle_prune_branch   Section 3 overview (prune when lower > incumbent),
  *                         Section 3.1 batch_pick_out and batch_split (bisection
- *                         of the widest dimension).
+ *                         of the widest dimension); oracle_prune_branch_heuristic
+ *                         with the softmax pick-out (oracle_pick_key) and given
+ *                         split dimensions (oracle_split_dims: the sample-
+ *                         imbalance score).
  *
  * Layout conventions (these are the public conventions of the library too):
  *   network: L linear layers, dims[0] = s + k, dims[L] = s; params holds, for
@@ -960,9 +963,110 @@ static int okey_cmp(const void *pa, const void *pb)
  * unpicked survivors in pool order.  Returns 0, or -1 if a picked id is too
  * deep to split (id >= 2^63).
  */
+/*
+ * Natural logarithm of a positive normal FP32 number with basic operations
+ * only, each rounded once: x = 2^e m with m in [sqrt(1/2), sqrt(2)), then
+ * log x = e ln 2 + 2 atanh(z), z = (m - 1)/(m + 1), |z| < 0.172, from the
+ * atanh series z + z^3/3 + ... + z^13/13 (truncation below 2^-30 relative).
+ * Any IEEE implementation of the same steps returns the same bits, which
+ * keeps the softmax pick-out below reproducible across implementations.
+ */
+float oracle_log_det(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    int e = (int)((b >> 23) & 0xFF) - 127;
+    uint32_t mb = (b & 0x007FFFFFu) | 0x3F800000u;
+    volatile float m;
+    float mm;
+    memcpy(&mm, &mb, 4);
+    m = mm;
+    if (m > 1.41421356f) {
+        m = m * 0.5f;
+        e += 1;
+    }
+    volatile float num = m - 1.0f, den = m + 1.0f;
+    volatile float z = num / den;
+    volatile float z2 = z * z;
+    volatile float pp = 0.0769230769f;           /* 1/13 */
+    pp = pp * z2;
+    pp = pp + 0.0909090909f;                     /* 1/11 */
+    pp = pp * z2;
+    pp = pp + 0.111111111f;                      /* 1/9 */
+    pp = pp * z2;
+    pp = pp + 0.142857143f;                      /* 1/7 */
+    pp = pp * z2;
+    pp = pp + 0.2f;                              /* 1/5 */
+    pp = pp * z2;
+    pp = pp + 0.333333333f;                      /* 1/3 */
+    pp = pp * z2;
+    pp = pp + 1.0f;
+    volatile float t = z * pp;
+    t = t + t;
+    volatile float ef = (float)e;
+    volatile float el = ef * 0.693147181f;       /* e ln 2 */
+    volatile float r = el + t;
+    return r;
+}
+
+/*
+ * Key of the softmax pick-out (Section 3.1, Eq. lf_pick) as an exponential
+ * race: candidate i wins with probability exp(-s_i / T) / sum_j exp(-s_j / T)
+ * when the smallest key s_i / T + log(E_i) wins, E_i = -log(U_i) ~ Exp(1); the
+ * k smallest keys are a draw of k candidates without replacement (Efraimidis
+ * and Spirakis, 2006).  s = (lb - lb_min) / (lb_max - lb_min) over the
+ * candidates (0 if they are all equal); U_i in (0, 1) from SplitMix64 of
+ * (seed, id).  All in FP32, one rounding per operation.
+ */
+float oracle_pick_key(float lb, float lb_min, float lb_max, float temperature, uint64_t seed, uint64_t id)
+{
+    volatile float span = lb_max - lb_min;
+    volatile float sc = 0.0f;
+    if (span > 0.0f) {
+        volatile float dlt = lb - lb_min;
+        sc = dlt / span;
+    }
+    uint64_t h = oracle_splitmix64(seed ^ oracle_splitmix64(id));
+    volatile float uu = ((float)(h >> 41) + 0.5f) * (1.0f / 8388608.0f);  /* (k + 1/2) 2^-23, exact, in (0, 1) */
+    volatile float le = oracle_log_det(uu);
+    volatile float E = -le;
+    volatile float lg = oracle_log_det(E);
+    volatile float q = sc / temperature;
+    volatile float key = q + lg;
+    return key;
+}
+
+/* One prune-and-branch pass; pick_rule 0: the rest of the quota by smallest (lb, id); 1: by the softmax race
+   (keys of oracle_pick_key).  split_dim (nullable): the dimension to split of each pool row; NULL: widest. */
+static int prune_branch_impl(int n, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                             const uint64_t *id, double inc_val, int n_pick, double eta, int pick_rule,
+                             float temperature, uint64_t pick_seed, const int *split_dim, float *out_lo,
+                             float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep,
+                             int *n_children, int *n_rest);
+
 int oracle_prune_branch(int n, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                         const uint64_t *id, double inc_val, int n_pick, double eta, float *out_lo, float *out_hi,
                         float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep, int *n_children, int *n_rest)
+{
+    return prune_branch_impl(n, d, lo, hi, lb, ub, id, inc_val, n_pick, eta, 0, 1.0f, 0, NULL, out_lo, out_hi,
+                             out_lb, out_ub, out_id, keep, n_children, n_rest);
+}
+
+int oracle_prune_branch_heuristic(int n, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                                  const uint64_t *id, double inc_val, int n_pick, double eta, int pick_rule,
+                                  float temperature, uint64_t pick_seed, const int *split_dim, float *out_lo,
+                                  float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep,
+                                  int *n_children, int *n_rest)
+{
+    return prune_branch_impl(n, d, lo, hi, lb, ub, id, inc_val, n_pick, eta, pick_rule, temperature, pick_seed,
+                             split_dim, out_lo, out_hi, out_lb, out_ub, out_id, keep, n_children, n_rest);
+}
+
+static int prune_branch_impl(int n, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                             const uint64_t *id, double inc_val, int n_pick, double eta, int pick_rule,
+                             float temperature, uint64_t pick_seed, const int *split_dim, float *out_lo,
+                             float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep,
+                             int *n_children, int *n_rest)
 {
     int *surv = (int *)malloc(sizeof(int) * (n ? n : 1));
     uint8_t *picked = (uint8_t *)calloc(n ? n : 1, 1);
@@ -985,10 +1089,20 @@ int oracle_prune_branch(int n, int d, const float *lo, const float *hi, const fl
         }
         qsort(ks, ns, sizeof(okey), okey_cmp);
         for (int q = 0; q < n1; ++q) picked[ks[q].row] = 1;
+        float lmin = INFINITY, lmax = -INFINITY;
+        if (pick_rule == 1)
+            for (int q = 0; q < ns; ++q) {
+                float v = lb[surv[q]];
+                if (picked[surv[q]] || isnan(v)) continue;
+                if (v < lmin) lmin = v;
+                if (v > lmax) lmax = v;
+            }
         int m = 0;
         for (int q = 0; q < ns; ++q) {
             if (picked[surv[q]]) continue;
-            ks[m].key = lb[surv[q]];
+            float v = lb[surv[q]];
+            ks[m].key = (pick_rule == 1 && !isnan(v)) ? oracle_pick_key(v, lmin, lmax, temperature, pick_seed, id[surv[q]])
+                                                      : v;
             ks[m].id = id[surv[q]];
             ks[m].row = surv[q];
             ++m;
@@ -1003,12 +1117,16 @@ int oracle_prune_branch(int n, int d, const float *lo, const float *hi, const fl
         if (!picked[i]) continue;
         const float *pl = lo + (size_t)i * d, *ph = hi + (size_t)i * d;
         int js = 0;
-        float wbest = ph[0] - pl[0];
-        for (int j = 1; j < d; ++j) {
-            float w = ph[j] - pl[j];
-            if (w > wbest) {
-                wbest = w;
-                js = j;
+        if (split_dim && split_dim[i] >= 0 && split_dim[i] < d) {
+            js = split_dim[i];
+        } else {
+            float wbest = ph[0] - pl[0];
+            for (int j = 1; j < d; ++j) {
+                float w = ph[j] - pl[j];
+                if (w > wbest) {
+                    wbest = w;
+                    js = j;
+                }
             }
         }
         volatile float sum = pl[js] + ph[js];
@@ -1043,4 +1161,75 @@ int oracle_prune_branch(int n, int d, const float *lo, const float *hi, const fl
     free(surv);
     free(picked);
     return err;
+}
+
+/*
+ * The splitting heuristic of Section 3.1: for each box, the top_k samples of
+ * smallest cost (ties by sample index; costs [n][M] as the search computed
+ * them, FP32), their coordinates re-drawn from the counter-based sampler, and
+ * per dimension j the counts n_lo (u_j <= mid_j) and n_up (u_j >= mid_j) with
+ * mid_j = 0.5f (lo_j + hi_j); the score (hi_j - lo_j) |n_lo - n_up| in FP32,
+ * the largest score (lowest j on ties) is the dimension to split.  When every
+ * score is 0 (no imbalance) the widest dimension is used.
+ */
+typedef struct {
+    float c;
+    int m;
+} ocost;
+
+static int ocost_cmp(const void *pa, const void *pb)
+{
+    const ocost *a = (const ocost *)pa, *b = (const ocost *)pb;
+    int an = isnan(a->c), bn = isnan(b->c);
+    if (an != bn) return an - bn;
+    if (!an && a->c < b->c) return -1;
+    if (!an && a->c > b->c) return 1;
+    return a->m - b->m;
+}
+
+int oracle_split_dims(int n, int d, const float *lo, const float *hi, const uint64_t *id, uint64_t seed,
+                      const float *costs, int M, int top_k, int *split_dim)
+{
+    if (top_k < 1 || top_k > M) return -1;
+    ocost *cs = (ocost *)malloc(sizeof(ocost) * M);
+    for (int i = 0; i < n; ++i) {
+        const float *bl = lo + (size_t)i * d, *bh = hi + (size_t)i * d;
+        for (int m = 0; m < M; ++m) {
+            cs[m].c = costs[(size_t)i * M + m];
+            cs[m].m = m;
+        }
+        qsort(cs, M, sizeof(ocost), ocost_cmp);
+        int jb = -1;
+        float sb = 0.0f;
+        for (int j = 0; j < d; ++j) {
+            volatile float sum = bl[j] + bh[j];
+            volatile float mid = 0.5f * sum;
+            int nlo = 0, nup = 0;
+            for (int q = 0; q < top_k; ++q) {
+                float u = oracle_sample(seed, id[i], (uint32_t)cs[q].m, (uint32_t)j, bl[j], bh[j]);
+                if (u <= mid) ++nlo;
+                if (u >= mid) ++nup;
+            }
+            volatile float w = bh[j] - bl[j];
+            volatile float sc = w * (float)abs(nlo - nup);
+            if (sc > sb) {
+                sb = sc;
+                jb = j;
+            }
+        }
+        if (jb < 0) {
+            jb = 0;
+            float wb = bh[0] - bl[0];
+            for (int j = 1; j < d; ++j) {
+                float w = bh[j] - bl[j];
+                if (w > wb) {
+                    wb = w;
+                    jb = j;
+                }
+            }
+        }
+        split_dim[i] = jb;
+    }
+    free(cs);
+    return 0;
 }

@@ -348,6 +348,70 @@ def prune_branch(lo, hi, lb, ub, ids, inc_val, n_pick, eta=0.75):
             "hi": out_hi[:m], "lb": out_lb[:m], "ub": out_ub[:m], "id": out_id[:m]}
 
 
+def log_det(x):
+    """The oracle's FP32 natural logarithm from basic operations (same bits on every IEEE implementation)."""
+    L = lib()
+    L.oracle_log_det.restype = ctypes.c_float
+    L.oracle_log_det.argtypes = [ctypes.c_float]
+    return float(L.oracle_log_det(float(x)))
+
+
+def pick_key(lb, lb_min, lb_max, temperature, seed, box_id):
+    """Softmax pick-out race key of one candidate (see bab_oracle.c)."""
+    L = lib()
+    L.oracle_pick_key.restype = ctypes.c_float
+    L.oracle_pick_key.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                  ctypes.c_uint64]
+    return float(L.oracle_pick_key(lb, lb_min, lb_max, temperature, int(seed), int(box_id)))
+
+
+def split_dims(lo, hi, ids, seed, costs, top_k):
+    """Dimension to split per box by the sample-imbalance score over the top_k samples (Section 3.1)."""
+    lo, plo = _f(lo)
+    hi, phi = _f(hi)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    costs = np.ascontiguousarray(costs, dtype=np.float32)
+    n, d = lo.shape
+    M = costs.shape[1]
+    out = np.zeros(n, dtype=np.int32)
+    rc = lib().oracle_split_dims(ctypes.c_int(n), ctypes.c_int(d), plo, phi, ids.ctypes.data_as(_c_u64_p),
+                                 ctypes.c_uint64(seed), costs.ctypes.data_as(_c_float_p), ctypes.c_int(M),
+                                 ctypes.c_int(top_k), out.ctypes.data_as(_c_int_p))
+    assert rc == 0
+    return out
+
+
+def prune_branch_heuristic(lo, hi, lb, ub, ids, inc_val, n_pick, eta=0.75, pick_rule=1, temperature=0.05,
+                           pick_seed=0, split_dim=None):
+    """prune_branch with the softmax pick-out (pick_rule 1) and given split dimensions (None: widest)."""
+    lo, plo = _f(lo)
+    hi, phi = _f(hi)
+    lb, plb = _f(lb)
+    ub, pub = _f(ub)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    n, d = lo.shape
+    cap = 2 * n + 1
+    out_lo = np.zeros((cap, d), dtype=np.float32)
+    out_hi = np.zeros_like(out_lo)
+    out_lb = np.zeros(cap, dtype=np.float32)
+    out_ub = np.zeros(cap, dtype=np.float32)
+    out_id = np.zeros(cap, dtype=np.uint64)
+    keep = np.zeros(max(n, 1), dtype=np.uint8)
+    sd = None if split_dim is None else np.ascontiguousarray(split_dim, dtype=np.int32)
+    nc = ctypes.c_int()
+    nr = ctypes.c_int()
+    rc = lib().oracle_prune_branch_heuristic(
+        ctypes.c_int(n), ctypes.c_int(d), plo, phi, plb, pub, ids.ctypes.data_as(_c_u64_p), ctypes.c_double(inc_val),
+        ctypes.c_int(n_pick), ctypes.c_double(eta), ctypes.c_int(pick_rule), ctypes.c_float(temperature),
+        ctypes.c_uint64(pick_seed), None if sd is None else sd.ctypes.data_as(_c_int_p),
+        out_lo.ctypes.data_as(_c_float_p), out_hi.ctypes.data_as(_c_float_p), out_lb.ctypes.data_as(_c_float_p),
+        out_ub.ctypes.data_as(_c_float_p), out_id.ctypes.data_as(_c_u64_p), keep.ctypes.data_as(_c_u8_p),
+        ctypes.byref(nc), ctypes.byref(nr))
+    m = nc.value + nr.value
+    return {"rc": rc, "keep": keep[:n], "n_children": nc.value, "n_rest": nr.value, "lo": out_lo[:m],
+            "hi": out_hi[:m], "lb": out_lb[:m], "ub": out_ub[:m], "id": out_id[:m]}
+
+
 def bab(problem, lo, hi, ids, iters, n_pick, samples, seed, alpha_steps=0, alpha_lr=0.1, eta=0.75):
     """Algorithm 2 on the host: search and bound the initial boxes, then per iteration prune the pool
     against the incumbent, pick out and split, search and bound the children, update the incumbent.

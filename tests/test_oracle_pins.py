@@ -679,3 +679,68 @@ def test_crown_given_sound_with_sound_bounds(oracle, t_stop):
     epl, epu, exl, exu = oracle.search_bounds(p, lo, hi, ids, 64, 9)
     assert np.all(epl >= pl - 1e-9) and np.all(epu <= pu + 1e-9)  # the samples lie inside the sound ranges
     assert np.all(exl >= xl - 1e-9) and np.all(exu <= xu + 1e-9)
+
+
+# --------------------------------------------------------------------------
+# The paper's branching heuristics (Section 3.1)
+# --------------------------------------------------------------------------
+
+def test_log_det_accuracy(oracle):
+    xs = np.geomspace(1e-8, 1e3, 2000).astype(np.float32)
+    got = np.array([oracle.log_det(x) for x in xs])
+    np.testing.assert_allclose(got, np.log(xs.astype(np.float64)), rtol=4e-7, atol=2e-7)
+
+
+def test_softmax_pick_race_frequencies(oracle):
+    """The smallest race key wins with the softmax probability of Eq. lf_pick: exp(-s_i/T) / sum exp(-s_j/T)."""
+    lb = np.array([3.0, 3.5, 4.0, 5.0, 6.0, 3.2], dtype=np.float32)
+    T = 0.4
+    lmin, lmax = lb.min(), lb.max()
+    sc = (lb - lmin) / (lmax - lmin)
+    p = np.exp(-sc / T) / np.exp(-sc / T).sum()
+    trials = 6000
+    wins = np.zeros(len(lb))
+    for t in range(trials):
+        keys = [oracle.pick_key(float(v), float(lmin), float(lmax), T, 1000 + t, 7 + i) for i, v in enumerate(lb)]
+        wins[int(np.argmin(keys))] += 1
+    freq = wins / trials
+    sigma = np.sqrt(p * (1 - p) / trials)
+    assert np.all(np.abs(freq - p) <= 4.5 * sigma + 1e-3), (freq, p)
+
+
+def test_softmax_pick_cold_limit_and_default_rule(oracle):
+    """At a tiny temperature the race picks by smallest lb; with rule 0 and no split dimensions the heuristic
+    pass is the plain prune / pick-out / split."""
+    lo, hi, ids = W.dyadic_boxes(6, 80, seed=3, max_depth=4)
+    lb, ub = W.pool_values(80, seed=4)
+    cold = oracle.prune_branch_heuristic(lo, hi, lb, ub, ids, 100.0, 10, eta=0.5, pick_rule=1, temperature=1e-7,
+                                         pick_seed=9)
+    plain = oracle.prune_branch(lo, hi, lb, ub, ids, 100.0, 10, eta=0.5)
+    assert np.array_equal(np.sort(cold["id"][:cold["n_children"]]), np.sort(plain["id"][:plain["n_children"]]))
+    same = oracle.prune_branch_heuristic(lo, hi, lb, ub, ids, 100.0, 10, eta=0.5, pick_rule=0)
+    for key in ("lo", "hi", "lb", "ub", "id"):
+        assert np.array_equal(same[key], plain[key])
+
+
+def test_split_dims_recount(oracle):
+    """The chosen dimension maximises (hi - lo) |n_lo - n_up| over the top_k samples, recounted here with
+    numpy from the same counter-based samples; no imbalance anywhere falls back to the widest dimension."""
+    rng = np.random.default_rng(5)
+    n, d, M, k = 12, 7, 40, 5
+    lo, hi, ids = W.random_boxes(d, n, seed=6, min_width=0.2, max_width=1.5)
+    costs = rng.normal(size=(n, M)).astype(np.float32)
+    costs[3, :] = 1.0                                    # all equal: the top samples are m = 0 .. k-1
+    got = oracle.split_dims(lo, hi, ids, 11, costs, k)
+    for i in range(n):
+        order = sorted(range(M), key=lambda m: (costs[i, m], m))[:k]
+        best, jb = 0.0, -1
+        for j in range(d):
+            mid = np.float32(0.5) * np.float32(lo[i, j] + hi[i, j])
+            u = np.array([oracle.lib().oracle_sample(11, int(ids[i]), m, j, float(lo[i, j]), float(hi[i, j]))
+                          for m in order], dtype=np.float32)
+            sc = np.float32(hi[i, j] - lo[i, j]) * np.float32(abs(int((u <= mid).sum()) - int((u >= mid).sum())))
+            if sc > best:
+                best, jb = sc, j
+        if jb < 0:
+            jb = int(np.argmax(hi[i] - lo[i]))
+        assert got[i] == jb, i
