@@ -65,6 +65,10 @@ extern "C" {
 /* Split rules of bab_prune_branch. */
 #define BAB_SPLIT_WIDEST 0 /* bisect the widest coordinate (Section 3.1), lowest index on ties */
 
+/* Pick-out rules for the part of the quota not taken by smallest upper bound (Section 3.1). */
+#define BAB_PICK_LB 0      /* smallest (lb, id): deterministic */
+#define BAB_PICK_SOFTMAX 1 /* the softmax sampling of Eq. lf_pick (counter-based, reproducible) */
+
 /* Limits of this build. */
 #define BAB_MAX_LAYERS 8
 #define BAB_MAX_WIDTH 256
@@ -321,6 +325,46 @@ int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, cons
                      const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
                      int split_rule, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
                      uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream);
+
+/*
+ * The paper's branching heuristics (Section 3.1).
+ *
+ * bab_prune_branch_heuristic: bab_prune_branch where the part of the pick-out
+ * quota not taken by smallest ub is drawn by the softmax of Eq. lf_pick over
+ * the min-max scaled lower bounds of the remaining survivors, with
+ * temperature T (pick_rule BAB_PICK_SOFTMAX; BAB_PICK_LB keeps the smallest
+ * (lb, id)): the n_pick - ceil(eta n_pick) candidates with the smallest race
+ * keys s / T + log(-log U), U from SplitMix64 of (pick_seed, id), a draw
+ * without replacement with those probabilities, reproducible bit for bit
+ * (the logarithm is computed from basic FP32 operations).  NaN bounds come
+ * last.  split_dim (device int[n], nullable) gives the dimension to split for
+ * each pool row (out of range: widest); the rest is bab_prune_branch.
+ * Errors: as bab_prune_branch, BAB_ERR_INVALID_ARG for an unknown rule or
+ * temperature <= 0.
+ *
+ * bab_split_dims: for each box, among its top_k samples (smallest (cost, m)
+ * of costs, device float[n][samples], the objective per sample as the search
+ * computed it), counts n_lo / n_up of the coordinates below / above the
+ * midpoint of each dimension (samples re-drawn from the counter-based
+ * sampler with `seed`), and writes to split_dim (device int[n]) the dimension
+ * of largest (hi - lo) |n_lo - n_up| (lowest index on ties; the widest when
+ * none is imbalanced).  1 <= top_k <= min(64, samples).
+ *
+ * bab_rollout_split: bab_rollout that also keeps every sample's objective
+ * (costs, nullable: context scratch) and then runs bab_split_dims with
+ * top_k = ceil(top_pct / 100 * samples) (clamped to [1, 64]).
+ */
+int bab_prune_branch_heuristic(bab_ctx *ctx, int d, const float *lo, const float *hi, const float *lb,
+                               const float *ub, const uint64_t *id, int n, const int *d_n, const double *inc_val,
+                               int n_pick, float eta, int pick_rule, float temperature, uint64_t pick_seed,
+                               const int *split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb,
+                               float *out_ub, uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream);
+int bab_split_dims(bab_ctx *ctx, int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                   uint64_t seed, const float *costs, int samples, int top_k, int *split_dim, void *stream);
+int bab_rollout_split(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                      const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
+                      int precision, float top_pct, float *ub, float *best_u, double *inc_val, float *inc_u,
+                      float *costs, int *split_dim, void *stream);
 
 /*
  * Synchronise `stream` and return the sticky device-side status of ctx (0 or

@@ -24,6 +24,7 @@ ERRORS = {-1: "BAB_ERR_INVALID_ARG", -2: "BAB_ERR_SHAPE", -3: "BAB_ERR_CUDA", -4
           -5: "BAB_ERR_TIMEOUT", -6: "BAB_ERR_NUMERIC", -7: "BAB_ERR_UNSUPPORTED"}
 PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
 SPLIT_WIDEST = 0
+PICK_LB, PICK_SOFTMAX = 0, 1
 KERNEL_ROLLOUT_FP32, KERNEL_ALPHA_FUSED, KERNEL_ROLLOUT_TC, KERNEL_CROWN_TC = 0, 1, 2, 3
 
 
@@ -82,6 +83,11 @@ def load(path: str = LIB_PATH):
     L.bab_rollout_search_bounds.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _P, _P, _P,
                                             _P, _P, _P, _P, _P, _P]
     L.bab_bound_crown_given.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P]
+    L.bab_prune_branch_heuristic.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _F, ctypes.c_uint64,
+                                             _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.bab_split_dims.argtypes = [_P, _I, _P, _P, _P, _I, _P, ctypes.c_uint64, _P, _I, _I, _P, _P]
+    L.bab_rollout_split.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _F, _P, _P, _P,
+                                    _P, _P, _P, _P]
     L.bab_set_variant.argtypes = [_P, _I, _I]
     L.bab_set_rescore_topk.argtypes = [_P, _I]
     L.bab_get_variant.argtypes = [_P, _I, ctypes.POINTER(_I)]
@@ -341,4 +347,37 @@ def bab_bound_crown_given(ctx, x0, goal, horizon, rho, lo, hi, n, pre_lo, pre_hi
                                       _ptr(pre_lo, f32, "pre_lo"), _ptr(pre_hi, f32, "pre_hi"),
                                       _ptr(x_lo, f32, "x_lo"), _ptr(x_hi, f32, "x_hi"), int(t_stop),
                                       _ptr(lb, f32, "lb"), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_prune_branch_heuristic(ctx, d, lo, hi, lb, ub, ids, n, inc_val, n_pick, eta, pick_rule, temperature, pick_seed,
+                               cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts, split_dim=None,
+                               d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_prune_branch_heuristic(
+        ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(lb, f32, "lb"), _ptr(ub, f32, "ub"),
+        _ptr(ids, torch.uint64, "id"), int(n), _ptr(d_n, torch.int32), _ptr(inc_val, torch.float64, "inc_val"),
+        int(n_pick), float(eta), int(pick_rule), float(temperature), int(pick_seed), _ptr(split_dim, torch.int32),
+        int(cap_out), _ptr(out_lo, f32), _ptr(out_hi, f32), _ptr(out_lb, f32), _ptr(out_ub, f32),
+        _ptr(out_id, torch.uint64), _ptr(keep, torch.uint8), _ptr(d_counts, torch.int32, "d_counts"), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_split_dims(ctx, d, lo, hi, ids, n, seed, costs, samples, top_k, split_dim, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_split_dims(ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"),
+                               int(n), _ptr(d_n, torch.int32), int(seed), _ptr(costs, f32, "costs"), int(samples),
+                               int(top_k), _ptr(split_dim, torch.int32, "split_dim"), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_rollout_split(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, seed, precision, top_pct, ub, split_dim,
+                      best_u=None, inc_val=None, inc_u=None, costs=None, d_n=None, stream=None):
+    f32 = torch.float32
+    rc = load().bab_rollout_split(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                                  _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), int(n),
+                                  _ptr(d_n, torch.int32), int(samples), int(seed), int(precision), float(top_pct),
+                                  _ptr(ub, f32, "ub"), _ptr(best_u, f32), _ptr(inc_val, torch.float64),
+                                  _ptr(inc_u, f32), _ptr(costs, f32), _ptr(split_dim, torch.int32, "split_dim"),
+                                  _stream(stream))
     _check(ctx, rc)

@@ -406,9 +406,30 @@ int bab_status(bab_ctx *c, void *stream)
     return v;
 }
 
+}  // extern "C"
+
+namespace {
+int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                 const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
+                 float *best_u, double *inc_val, float *inc_u, float *costs, void *stream);
+}  // namespace
+
+extern "C" {
+
 int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
                 const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
                 float *best_u, double *inc_val, float *inc_u, void *stream)
+{
+    return rollout_impl(c, x0, goal, H, rho, lo, hi, id, n, d_n, samples, seed, precision, ub, best_u, inc_val, inc_u,
+                        nullptr, stream);
+}
+
+}  // extern "C"
+
+namespace {
+int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                 const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
+                 float *best_u, double *inc_val, float *inc_u, float *costs, void *stream)
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
@@ -455,10 +476,52 @@ int bab_rollout(bab_ctx *c, const float *x0, const float *goal, int H, float rho
     a.tc_img = c->d_tc;
     a.tc_bias = c->d_tc_bias;
     a.tc_bytes = c->net.tc_bytes;
+    a.costs = costs;
     cudaError_t e = precision == BAB_PREC_FP32 ? launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, (cudaStream_t)stream)
                                                : launch_rollout_tc(a, split, c->tune_rollout_tc, c->num_sms, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "rollout kernels");
     return BAB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int bab_split_dims(bab_ctx *c, int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                   uint64_t seed, const float *costs, int samples, int top_k, int *split_dim, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (d < 1 || n < 0 || samples < 1) return fail(c, BAB_ERR_SHAPE, "bad d, n or samples");
+    if (top_k < 1 || top_k > 64 || top_k > samples) return fail(c, BAB_ERR_INVALID_ARG, "top_k must be in [1, min(64, samples)]");
+    if (n > 0 && (!lo || !hi || !id || !costs || !split_dim)) return fail(c, BAB_ERR_INVALID_ARG, "null array");
+    cudaError_t e = launch_split_dims(d, lo, hi, id, n, d_n, seed, costs, samples, top_k, split_dim, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "split-dimension kernel");
+    return BAB_OK;
+}
+
+int bab_rollout_split(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                      const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed, int precision,
+                      float top_pct, float *ub, float *best_u, double *inc_val, float *inc_u, float *costs,
+                      int *split_dim, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    if (!(top_pct > 0.f && top_pct <= 100.f)) return fail(c, BAB_ERR_INVALID_ARG, "top_pct must be in (0, 100]");
+    if (n > 0 && !split_dim) return fail(c, BAB_ERR_INVALID_ARG, "split_dim is required");
+    int top_k = (int)std::ceil((double)top_pct / 100.0 * samples);
+    top_k = top_k < 1 ? 1 : (top_k > 64 ? 64 : top_k);
+    if (top_k > samples) top_k = samples;
+    float *cst = costs;
+    if (!cst && n > 0) {
+        // costs in the scratch after the rollout's own keys
+        const size_t key_bytes = ((size_t)n * sizeof(unsigned long long) + 255) & ~size_t(255);
+        int rc = ensure_scratch(c, key_bytes + 512 + (size_t)n * samples * sizeof(float) + 256);
+        if (rc) return rc;
+        cst = reinterpret_cast<float *>(static_cast<char *>(c->scratch) + key_bytes + 512);
+    }
+    int rc = rollout_impl(c, x0, goal, H, rho, lo, hi, id, n, d_n, samples, seed, precision, ub, best_u, inc_val, inc_u,
+                          cst, stream);
+    if (rc) return rc;
+    return bab_split_dims(c, c->net.k * H, lo, hi, id, n, d_n, seed, cst, samples, top_k, split_dim, stream);
 }
 
 int bab_rollout_search_bounds(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
@@ -834,10 +897,50 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
     return BAB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                      const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
+                      int split_rule, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
+                      int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id,
+                      uint8_t *keep, int *d_counts, void *stream);
+}  // namespace
+
+extern "C" {
+
 int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                      const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
                      int split_rule, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
                      uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream)
+{
+    if (c && split_rule != BAB_SPLIT_WIDEST) return fail(c, BAB_ERR_UNSUPPORTED, "split rule %d", split_rule);
+    return prune_branch_impl(c, d, lo, hi, lb, ub, id, n, d_n, inc_val, n_pick, eta, split_rule, BAB_PICK_LB, 1.f, 0,
+                             nullptr, cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts, stream);
+}
+
+int bab_prune_branch_heuristic(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                               const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick,
+                               float eta, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
+                               int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
+                               uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    if (pick_rule != BAB_PICK_LB && pick_rule != BAB_PICK_SOFTMAX) return fail(c, BAB_ERR_INVALID_ARG, "pick rule %d", pick_rule);
+    if (!(temperature > 0.f) || !std::isfinite(temperature)) return fail(c, BAB_ERR_INVALID_ARG, "temperature must be > 0");
+    return prune_branch_impl(c, d, lo, hi, lb, ub, id, n, d_n, inc_val, n_pick, eta, BAB_SPLIT_WIDEST, pick_rule,
+                             temperature, pick_seed, split_dim, cap_out, out_lo, out_hi, out_lb, out_ub, out_id,
+                             keep, d_counts, stream);
+}
+
+}  // extern "C"
+
+namespace {
+int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
+                      const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
+                      int split_rule, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
+                      int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id,
+                      uint8_t *keep, int *d_counts, void *stream)
 {
     if (!c) return BAB_ERR_INVALID_ARG;
     c->err[0] = 0;
@@ -848,13 +951,19 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
     if (n > 0 && (!lo || !hi || !lb || !ub || !id || !keep || !out_lo || !out_hi || !out_lb || !out_ub || !out_id))
         return fail(c, BAB_ERR_INVALID_ARG, "null array");
     if ((long long)cap_out < (long long)n + n_pick) return fail(c, BAB_ERR_SHAPE, "cap_out must be >= n + n_pick");
-    int rc = ensure_scratch(c, (size_t)(n > 0 ? n : 1) * sizeof(int) + 1024);
+    const size_t rows = ((size_t)(n > 0 ? n : 1) + 63) / 64 * 64;
+    int rc = ensure_scratch(c, rows * (sizeof(int) + sizeof(float)) + 1024);
     if (rc) return rc;
     BranchArgs a{};
     a.batch.P = 1;
     a.cap_out = cap_out;
     a.eta = eta;
-    a.poff = reinterpret_cast<int *>(c->scratch) + ((n > 0 ? n : 1) + 63) / 64 * 64;
+    a.poff = reinterpret_cast<int *>(c->scratch) + rows;
+    a.pick_rule = pick_rule;
+    a.temperature = temperature;
+    a.pick_seed = pick_seed;
+    a.pick_keys = reinterpret_cast<float *>(reinterpret_cast<int *>(c->scratch) + rows + 64);
+    a.split_dim = split_dim;
     a.d = d;
     a.n = n;
     a.d_n = d_n;
@@ -880,6 +989,9 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
     if (e != cudaSuccess) return cuda_fail(c, e, "prune/branch kernels");
     return BAB_OK;
 }
+}  // namespace
+
+extern "C" {
 
 // ---------------------------------------------------------------------------
 // Batched problems (one launch per kernel for every problem of the context)

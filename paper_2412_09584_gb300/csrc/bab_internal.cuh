@@ -79,6 +79,47 @@ __device__ __forceinline__ float draw_sample(uint64_t hbox, uint32_t m, uint32_t
     return __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), r));
 }
 
+// Natural logarithm of a positive normal float from basic operations only, each rounded once (no
+// contraction): x = 2^e m, m in [sqrt(1/2), sqrt(2)), log x = e ln 2 + 2 atanh(z), z = (m - 1)/(m + 1), by the
+// atanh series to z^13.  The same steps in any IEEE arithmetic give the same bits; the softmax pick-out relies
+// on that to agree with other implementations.
+__device__ __forceinline__ float log_det(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421356f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    const float z = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float z2 = __fmul_rn(z, z);
+    float pp = 0.0769230769f;                                 // 1/13
+    pp = __fadd_rn(__fmul_rn(pp, z2), 0.0909090909f);        // 1/11
+    pp = __fadd_rn(__fmul_rn(pp, z2), 0.111111111f);         // 1/9
+    pp = __fadd_rn(__fmul_rn(pp, z2), 0.142857143f);         // 1/7
+    pp = __fadd_rn(__fmul_rn(pp, z2), 0.2f);                 // 1/5
+    pp = __fadd_rn(__fmul_rn(pp, z2), 0.333333333f);         // 1/3
+    pp = __fadd_rn(__fmul_rn(pp, z2), 1.0f);
+    float t = __fmul_rn(z, pp);
+    t = __fadd_rn(t, t);
+    return __fadd_rn(__fmul_rn(__int2float_rn(e), 0.693147181f), t);
+}
+
+// Race key of the softmax pick-out (Section 3.1, Eq. lf_pick): s / T + log(-log U) with s the min-max scaled
+// lower bound and U in (0, 1) from SplitMix64 of (seed, id); the k smallest keys draw k candidates without
+// replacement with probabilities proportional to exp(-s / T).
+__device__ __forceinline__ float pick_key(float lb, float lb_min, float lb_max, float temperature, uint64_t seed,
+                                          uint64_t id)
+{
+    const float span = __fsub_rn(lb_max, lb_min);
+    const float sc = span > 0.f ? __fdiv_rn(__fsub_rn(lb, lb_min), span) : 0.f;
+    const uint64_t h = splitmix64(seed ^ splitmix64(id));
+    const float uu = __fmul_rn(__fadd_rn(__ull2float_rn(h >> 41), 0.5f), 1.1920928955078125e-07f);  // 2^-23
+    const float E = -log_det(uu);
+    return __fadd_rn(__fdiv_rn(sc, temperature), log_det(E));
+}
+
 // Order-preserving map of a float to uint32 (NaN canonicalised to the top).
 __device__ __forceinline__ uint32_t float_order(float f)
 {

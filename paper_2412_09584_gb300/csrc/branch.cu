@@ -59,16 +59,47 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
     const bool all = ns <= n_pick;
     Thresh T1, T2;
     T1.none = T2.none = true;
+    // the rest of the quota is chosen on the lower bound, or on its softmax race key (pick_rule 1)
+    const float *key2 = a.pick_rule == 1 ? a.pick_keys : a.lb;
     if (!all) {
         const uint8_t *keep = a.keep;
         T1 = radix_select(n, a.ub, a.id, [&](int i) { return mine(i) && keep[i] != 0; }, n1, hist, &sh_pk, &sh_pid,
                           &sh_rem, &sh_done);
         const float *ub = a.ub;
         const uint64_t *ids = a.id;
-        T2 = radix_select(
-            n, a.lb, a.id,
-            [&](int i) { return mine(i) && keep[i] != 0 && !le_thresh(float_order(ub[i]), ids[i], T1); },
-            n_pick - n1, hist, &sh_pk, &sh_pid, &sh_rem, &sh_done);
+        auto cand = [&](int i) { return mine(i) && keep[i] != 0 && !le_thresh(float_order(ub[i]), ids[i], T1); };
+        if (a.pick_rule == 1) {
+            // min-max scaling over the candidates' (non-NaN) lower bounds, then each candidate's race key
+            float mn = INFINITY, mx = -INFINITY;
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                if (cand(i) && a.lb[i] == a.lb[i]) {
+                    mn = fminf(mn, a.lb[i]);
+                    mx = fmaxf(mx, a.lb[i]);
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            }
+            __shared__ float rmn[kPlanThreads / 32], rmx[kPlanThreads / 32];
+            if (lane == 0) {
+                rmn[warp] = mn;
+                rmx[warp] = mx;
+            }
+            __syncthreads();
+            mn = INFINITY;
+            mx = -INFINITY;
+            for (int w = 0; w < kPlanThreads / 32; ++w) {
+                mn = fminf(mn, rmn[w]);
+                mx = fmaxf(mx, rmx[w]);
+            }
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                if (cand(i)) {
+                    const float v = a.lb[i];
+                    a.pick_keys[i] = v == v ? pick_key(v, mn, mx, a.temperature, a.pick_seed, ids[i]) : v;
+                }
+            __syncthreads();
+        }
+        T2 = radix_select(n, key2, a.id, cand, n_pick - n1, hist, &sh_pk, &sh_pid, &sh_rem, &sh_done);
     }
 
     // stable ranks of picked and unpicked survivors
@@ -80,8 +111,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_branch_plan(BranchArgs a)
         const bool own = i < n && mine(i);
         if (own) {
             kp = a.keep[i] != 0;
-            pk = kp && (all || le_thresh(float_order(a.ub[i]), a.id[i], T1) ||
-                        le_thresh(float_order(a.lb[i]), a.id[i], T2));
+            const bool by_ub = le_thresh(float_order(a.ub[i]), a.id[i], T1);
+            pk = kp && (all || by_ub || le_thresh(float_order(key2[i]), a.id[i], T2));
         }
         const bool rs = kp && !pk;
         const unsigned bp = __ballot_sync(0xFFFFFFFFu, pk), br = __ballot_sync(0xFFFFFFFFu, rs);
@@ -180,7 +211,8 @@ __global__ void k_branch_write(BranchArgs a)
     // widest coordinate, lowest index on ties
     float wb = -1.f;
     int jb = 0x7FFFFFFF;
-    for (int j = lane; j < dp; j += 32) {
+    const int given = a.split_dim ? a.split_dim[row] : -1;  // the sample-imbalance choice, when given
+    for (int j = lane; j < dp && !(given >= 0 && given < dp); j += 32) {
         const float w = __fsub_rn(hi[j], lo[j]);
         if (w > wb) {
             wb = w;
@@ -195,6 +227,7 @@ __global__ void k_branch_write(BranchArgs a)
             jb = j2;
         }
     }
+    if (given >= 0 && given < dp) jb = given;
     if (jb >= dp) jb = 0;  // a problem without coordinates (H_p = 0) splits nothing meaningful
     const float mid = __fmul_rn(0.5f, __fadd_rn(lo[jb], hi[jb]));
     const size_t o0 = (size_t)a.poff[2 * pb] + 2 * (size_t)(dst & ~kPickFlag);
@@ -214,6 +247,92 @@ __global__ void k_branch_write(BranchArgs a)
         a.out_lb[o0] = a.out_lb[o0 + 1] = a.lb[row];
         a.out_ub[o0] = a.out_ub[o0 + 1] = a.ub[row];
     }
+}
+
+// The splitting heuristic of Section 3.1, one warp per box: the top_k samples of smallest (cost, m) (selected
+// in increasing order, each the smallest key above the previous), their coordinates re-drawn from the counter
+// sampler, per dimension the counts below / above the midpoint and the score (hi - lo) |n_lo - n_up|; the
+// largest score (lowest j on ties), or the widest dimension when no dimension is imbalanced.
+__global__ void __launch_bounds__(256) k_split_dims(int d, const float *lo, const float *hi, const uint64_t *id,
+                                                    int n, const int *d_n, uint64_t seed, const float *costs, int M,
+                                                    int top_k, int *split_dim)
+{
+    __shared__ int tops[8][64];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int box = blockIdx.x * 8 + wib;
+    if (box >= live_count(n, d_n)) return;
+    const float *c = costs + (size_t)box * M;
+    unsigned long long prev = 0;
+    for (int q = 0; q < top_k; ++q) {
+        unsigned long long best = ~0ull;
+        for (int m = lane; m < M; m += 32) {
+            const unsigned long long key = ((unsigned long long)float_order(c[m]) << 32) | (unsigned)m;
+            if ((q == 0 || key > prev) && key < best) best = key;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+            best = other < best ? other : best;
+        }
+        prev = best;
+        if (lane == 0) tops[wib][q] = (int)(best & 0xFFFFFFFFu);
+    }
+    __syncwarp();
+    const uint64_t hb = box_hash(seed, id[box]);
+    const float *bl = lo + (size_t)box * d, *bh = hi + (size_t)box * d;
+    float sb = 0.f;
+    int jb = 0x7FFFFFFF;
+    for (int j = lane; j < d; j += 32) {
+        const float mid = __fmul_rn(0.5f, __fadd_rn(bl[j], bh[j]));
+        int nlo = 0, nup = 0;
+        for (int q = 0; q < top_k; ++q) {
+            const float u = draw_sample(hb, (uint32_t)tops[wib][q], (uint32_t)j, bl[j], bh[j]);
+            nlo += u <= mid;
+            nup += u >= mid;
+        }
+        const float sc = __fmul_rn(__fsub_rn(bh[j], bl[j]), (float)abs(nlo - nup));
+        if (sc > sb) {
+            sb = sc;
+            jb = j;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+        const int j2 = __shfl_xor_sync(0xFFFFFFFFu, jb, o);
+        if (s2 > sb || (s2 == sb && j2 < jb)) {
+            sb = s2;
+            jb = j2;
+        }
+    }
+    if (!(sb > 0.f)) {
+        // no imbalance: the widest dimension, lowest index on ties
+        float wb = -1.f;
+        jb = 0x7FFFFFFF;
+        for (int j = lane; j < d; j += 32) {
+            const float w = __fsub_rn(bh[j], bl[j]);
+            if (w > wb) {
+                wb = w;
+                jb = j;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w2 = __shfl_xor_sync(0xFFFFFFFFu, wb, o);
+            const int j2 = __shfl_xor_sync(0xFFFFFFFFu, jb, o);
+            if (w2 > wb || (w2 == wb && j2 < jb)) {
+                wb = w2;
+                jb = j2;
+            }
+        }
+    }
+    if (lane == 0) split_dim[box] = jb;
+}
+
+cudaError_t launch_split_dims(int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                              uint64_t seed, const float *costs, int M, int top_k, int *split_dim, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (top_k < 1 || top_k > 64 || top_k > M) return cudaErrorInvalidValue;
+    k_split_dims<<<(n + 7) / 8, 256, 0, st>>>(d, lo, hi, id, n, d_n, seed, costs, M, top_k, split_dim);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prune_branch(const BranchArgs &a, cudaStream_t st)

@@ -62,6 +62,7 @@ struct RolloutArgs {
     // search-integrated bounds (nullable): per box the min / max over the samples of every hidden
     // pre-activation [n][H][sumh] and state [n][H+1][s], accumulated as order-preserving uint32 keys
     uint32_t *emp_pre_lo, *emp_pre_hi, *emp_x_lo, *emp_x_hi;
+    float *costs;        // [n][M] (nullable): every sample's objective as the search computed it
     // BF16 rollouts: re-score in FP32 only the topk boxes of smallest BF16 ub (0: every box)
     int topk;
     unsigned long long *topk_t;  // [3] scratch: the selection threshold
@@ -260,7 +261,16 @@ struct BranchArgs {
     int *pcounts;            // [P][2] picked and unpicked survivors per problem
     int *poff;               // [P][2] first output row of the problem's children and of its unpicked rows
     int *out_prob;           // [cap_out] (nullable)
+    // the paper's heuristics: pick_rule 1 fills the rest of the quota by the softmax race (pick_keys: [n]
+    // scratch); split_dim (nullable) gives each pool row's dimension to split
+    int pick_rule;
+    float temperature;
+    uint64_t pick_seed;
+    float *pick_keys;
+    const int *split_dim;
 };
+cudaError_t launch_split_dims(int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                              uint64_t seed, const float *costs, int M, int top_k, int *split_dim, cudaStream_t st);
 cudaError_t launch_prune_branch(const BranchArgs &a, cudaStream_t st);
 
 }  // namespace bab

@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
                 }
             }
         }
+        if (a.costs)
+            for (int r = threadIdx.x; r < rv; r += NT) a.costs[(size_t)box * a.M + m0 + r] = cost[r];
         // best (f, m) of the tile
         unsigned long long best = ~0ull;
         for (int r = threadIdx.x; r < R; r += NT)

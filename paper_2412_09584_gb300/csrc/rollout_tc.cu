@@ -309,6 +309,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             }
             if (!ok) break;
             if (primary) {
+                if (a.costs && lane_ok) a.costs[(size_t)box * a.M + m] = cost;
                 const unsigned long long key =
                     lane_ok ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
                 if (bpt > 1) {
