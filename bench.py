@@ -132,7 +132,8 @@ class BabState:
     the same grids."""
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
-                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None):
+                 alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None,
+                 heuristics=None):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -184,6 +185,14 @@ class BabState:
             nb_ = max(self.nb, n0)
             self.emp = [torch.empty(nb_, self.H, self.sumh, **f), torch.empty(nb_, self.H, self.sumh, **f),
                         torch.empty(nb_, self.H + 1, self.p["s"], **f), torch.empty(nb_, self.H + 1, self.p["s"], **f)]
+        # the paper's branching heuristics (Section 3.1): softmax pick-out at temperature T and split dimensions
+        # from the imbalance of the top w% samples; None: smallest lb and widest dimension
+        self.heur = heuristics
+        self.it = 0
+        if heuristics is not None:
+            for Q in self.pool:
+                Q["sd"] = torch.full((self.cap,), -1, dtype=torch.int32, device=device)
+            self.costs = torch.empty(max(self.nb, n0), self.M, **f)
         self.variants = None
         if autotune:
             # tile shapes timed on the starting pool (outside any timed region)
@@ -210,7 +219,11 @@ class BabState:
         if events:
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
-        if self.search_stop is None:
+        if self.heur is not None:
+            B.bab_rollout_split(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
+                                self.seed, self.rprec, self.heur["w"], P["ub"], P["sd"], best_u=self.best_u,
+                                costs=self.costs, d_n=d_n)
+        elif self.search_stop is None:
             B.bab_rollout(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
                           self.seed, self.rprec, P["ub"], self.best_u, d_n=d_n)
         else:
@@ -241,9 +254,20 @@ class BabState:
     def step(self, events=False):
         B = self.B
         src, dst = self.pool[self.cur], self.pool[self.cur ^ 1]
-        B.bab_prune_branch(self.ctx, self.d, src["lo"], src["hi"], src["lb"], src["ub"], src["id"], self.n_max,
-                           self.inc_val, self.n_pick, 0.75, self.cap, dst["lo"], dst["hi"], dst["lb"], dst["ub"],
-                           dst["id"], self.keep, self.counts, d_n=self.n_live_dev)
+        if self.heur is None:
+            B.bab_prune_branch(self.ctx, self.d, src["lo"], src["hi"], src["lb"], src["ub"], src["id"], self.n_max,
+                               self.inc_val, self.n_pick, 0.75, self.cap, dst["lo"], dst["hi"], dst["lb"], dst["ub"],
+                               dst["id"], self.keep, self.counts, d_n=self.n_live_dev)
+        else:
+            # children come first in dst and get their split dimensions from their own search below
+            rule = B.PICK_SOFTMAX if self.heur["T"] is not None else B.PICK_LB
+            B.bab_prune_branch_heuristic(self.ctx, self.d, src["lo"], src["hi"], src["lb"], src["ub"], src["id"],
+                                         self.n_max, self.inc_val, self.n_pick, 0.75, rule, self.heur["T"] or 1.0,
+                                         self.seed * 1000003 + self.it, self.cap, dst["lo"], dst["hi"], dst["lb"],
+                                         dst["ub"], dst["id"], self.keep, self.counts,
+                                         split_dim=src["sd"] if self.heur["split"] else None,
+                                         out_split_dim=dst["sd"], d_n=self.n_live_dev)
+        self.it += 1
         if not self.fixed:
             self.n_max = min(self.n_max + self.n_pick, self.cap - self.n_pick)
         self.search_and_bound(dst, self.nb, self.counts[0:1], events=events)
@@ -337,6 +361,7 @@ def run_ours(args):
     batched = None if args.no_batched else batched_bab(dev)
     manip = None if args.no_manip else manip_scale(dev)
     paper_bounds = None if args.no_time_to_gap else paper_bounding_comparison(dev)
+    heuristics = None if args.no_time_to_gap else heuristics_comparison(dev)
 
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
@@ -379,7 +404,7 @@ def run_ours(args):
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
            "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
-           "paper_bounding": paper_bounds}
+           "paper_bounding": paper_bounds, "heuristics": heuristics}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -634,6 +659,49 @@ def paper_bounding_comparison(dev, iters=30, stops=(0, 2)):
                               f"estimate: search-integrated bounds, early stop at step {stop}"}
     return out
 
+
+
+def heuristics_comparison(dev, iters=30):
+    """The paper's branching heuristics (Section 3.1; T = 0.05, w = 1%, eta = 0.75 as in its hyper-parameter
+    study) against the deterministic pick-out and widest-dimension split, in the same sound BaB loop: incumbent
+    and gap per iteration, live pool, time per iteration.  Two workloads: the small alpha network (H = 5, where
+    the pool prunes) and the pushing network (H = 20)."""
+    import torch
+    work = {"alpha": ("MLP 6-32-32-4, H=5, 4096 children per iteration, 256 FP32 rollouts each", 2048, "fp32"),
+            "pushing": ("MLP 10-128-128-128-8, H=20, 512 children per iteration, 1024 BF16x3 rollouts each", 256,
+                        "bf16x3")}
+    variants = {"lb_pick_widest_split": None, "softmax_pick_widest_split": {"T": 0.05, "w": 1.0, "split": False},
+                "lb_pick_imbalance_split": {"T": None, "w": 1.0, "split": True},
+                "softmax_pick_imbalance_split": {"T": 0.05, "w": 1.0, "split": True}}
+    out = {"bound": f"sound (interval + CROWN, FP32, margin); {iters} iterations; the gap needs one host sync per "
+                    "iteration (included in the time)"}
+    for wl, (desc, n_pick, rprec) in work.items():
+        res = {"workload": f"{wl}: {desc}"}
+        # one untimed pass first, so that no variant is timed while the clocks ramp up
+        for name, h in [("warm-up", None)] + list(variants.items()):
+            for warm in (True, False):
+                st = BabState(wl, SEED, dev, n_pick, rprec, "fp32", pool_iters=iters + 2, heuristics=h)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                inc, gaps = [], []
+                for _ in range(2 if warm else iters):
+                    st.step()
+                    if not warm:
+                        g, _ = st.gap()
+                        inc.append(float(st.inc_val.item()))
+                        gaps.append(g)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t
+                n_live = int(st.counts[2].item())
+                st.close()
+            if name == "warm-up":
+                continue
+            res[name] = {"incumbent": inc[-1], "gap": gaps[-1],
+                         "incumbent_every_5": [round(v, 5) for v in inc[4::5]],
+                         "gap_every_5": [round(v, 5) for v in gaps[4::5]],
+                         "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters}
+        out[wl] = res
+    return out
 
 
 def time_to_gap(dev, iters=20, max_iters=60):

@@ -338,7 +338,10 @@ int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, cons
  * without replacement with those probabilities, reproducible bit for bit
  * (the logarithm is computed from basic FP32 operations).  NaN bounds come
  * last.  split_dim (device int[n], nullable) gives the dimension to split for
- * each pool row (out of range: widest); the rest is bab_prune_branch.
+ * each pool row (out of range: widest); out_split_dim (device int[cap_out],
+ * nullable) carries it along: unpicked rows keep theirs, children get -1
+ * (their own split dimensions come from their search).  The rest is
+ * bab_prune_branch.
  * Errors: as bab_prune_branch, BAB_ERR_INVALID_ARG for an unknown rule or
  * temperature <= 0.
  *
@@ -358,7 +361,8 @@ int bab_prune_branch_heuristic(bab_ctx *ctx, int d, const float *lo, const float
                                const float *ub, const uint64_t *id, int n, const int *d_n, const double *inc_val,
                                int n_pick, float eta, int pick_rule, float temperature, uint64_t pick_seed,
                                const int *split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb,
-                               float *out_ub, uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream);
+                               float *out_ub, uint64_t *out_id, int *out_split_dim, uint8_t *keep, int *d_counts,
+                               void *stream);
 int bab_split_dims(bab_ctx *ctx, int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
                    uint64_t seed, const float *costs, int samples, int top_k, int *split_dim, void *stream);
 int bab_rollout_split(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,

@@ -84,7 +84,7 @@ def load(path: str = LIB_PATH):
                                             _P, _P, _P, _P, _P, _P]
     L.bab_bound_crown_given.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P]
     L.bab_prune_branch_heuristic.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _F, ctypes.c_uint64,
-                                             _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]
+                                             _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.bab_split_dims.argtypes = [_P, _I, _P, _P, _P, _I, _P, ctypes.c_uint64, _P, _I, _I, _P, _P]
     L.bab_rollout_split.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _F, _P, _P, _P,
                                     _P, _P, _P, _P]
@@ -352,14 +352,15 @@ def bab_bound_crown_given(ctx, x0, goal, horizon, rho, lo, hi, n, pre_lo, pre_hi
 
 def bab_prune_branch_heuristic(ctx, d, lo, hi, lb, ub, ids, n, inc_val, n_pick, eta, pick_rule, temperature, pick_seed,
                                cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts, split_dim=None,
-                               d_n=None, stream=None):
+                               out_split_dim=None, d_n=None, stream=None):
     f32 = torch.float32
     rc = load().bab_prune_branch_heuristic(
         ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(lb, f32, "lb"), _ptr(ub, f32, "ub"),
         _ptr(ids, torch.uint64, "id"), int(n), _ptr(d_n, torch.int32), _ptr(inc_val, torch.float64, "inc_val"),
         int(n_pick), float(eta), int(pick_rule), float(temperature), int(pick_seed), _ptr(split_dim, torch.int32),
         int(cap_out), _ptr(out_lo, f32), _ptr(out_hi, f32), _ptr(out_lb, f32), _ptr(out_ub, f32),
-        _ptr(out_id, torch.uint64), _ptr(keep, torch.uint8), _ptr(d_counts, torch.int32, "d_counts"), _stream(stream))
+        _ptr(out_id, torch.uint64), _ptr(out_split_dim, torch.int32), _ptr(keep, torch.uint8),
+        _ptr(d_counts, torch.int32, "d_counts"), _stream(stream))
     _check(ctx, rc)
 
 

@@ -903,8 +903,8 @@ namespace {
 int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                       const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
                       int split_rule, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
-                      int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id,
-                      uint8_t *keep, int *d_counts, void *stream);
+                      int *out_split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
+                      uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream);
 }  // namespace
 
 extern "C" {
@@ -916,21 +916,22 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
 {
     if (c && split_rule != BAB_SPLIT_WIDEST) return fail(c, BAB_ERR_UNSUPPORTED, "split rule %d", split_rule);
     return prune_branch_impl(c, d, lo, hi, lb, ub, id, n, d_n, inc_val, n_pick, eta, split_rule, BAB_PICK_LB, 1.f, 0,
-                             nullptr, cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts, stream);
+                             nullptr, nullptr, cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts,
+                             stream);
 }
 
 int bab_prune_branch_heuristic(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                                const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick,
                                float eta, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
                                int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
-                               uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream)
+                               uint64_t *out_id, int *out_split_dim, uint8_t *keep, int *d_counts, void *stream)
 {
     if (!c) return BAB_ERR_INVALID_ARG;
     if (pick_rule != BAB_PICK_LB && pick_rule != BAB_PICK_SOFTMAX) return fail(c, BAB_ERR_INVALID_ARG, "pick rule %d", pick_rule);
     if (!(temperature > 0.f) || !std::isfinite(temperature)) return fail(c, BAB_ERR_INVALID_ARG, "temperature must be > 0");
     return prune_branch_impl(c, d, lo, hi, lb, ub, id, n, d_n, inc_val, n_pick, eta, BAB_SPLIT_WIDEST, pick_rule,
-                             temperature, pick_seed, split_dim, cap_out, out_lo, out_hi, out_lb, out_ub, out_id,
-                             keep, d_counts, stream);
+                             temperature, pick_seed, split_dim, out_split_dim, cap_out, out_lo, out_hi, out_lb,
+                             out_ub, out_id, keep, d_counts, stream);
 }
 
 }  // extern "C"
@@ -939,8 +940,8 @@ namespace {
 int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                       const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
                       int split_rule, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
-                      int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id,
-                      uint8_t *keep, int *d_counts, void *stream)
+                      int *out_split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
+                      uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream)
 {
     if (!c) return BAB_ERR_INVALID_ARG;
     c->err[0] = 0;
@@ -964,6 +965,7 @@ int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const
     a.pick_seed = pick_seed;
     a.pick_keys = reinterpret_cast<float *>(reinterpret_cast<int *>(c->scratch) + rows + 64);
     a.split_dim = split_dim;
+    a.out_split_dim = out_split_dim;
     a.d = d;
     a.n = n;
     a.d_n = d_n;

@@ -197,6 +197,7 @@ __global__ void k_branch_write(BranchArgs a)
         const size_t o = (size_t)a.poff[2 * pb + 1] + dst;
         if (o >= (size_t)a.cap_out) return;
         if (a.out_prob && lane == 0) a.out_prob[o] = pb;
+        if (a.out_split_dim && lane == 0) a.out_split_dim[o] = a.split_dim ? a.split_dim[row] : -1;
         for (int j = lane; j < d; j += 32) {
             a.out_lo[o * d + j] = lo[j];
             a.out_hi[o * d + j] = hi[j];
@@ -233,6 +234,7 @@ __global__ void k_branch_write(BranchArgs a)
     const size_t o0 = (size_t)a.poff[2 * pb] + 2 * (size_t)(dst & ~kPickFlag);
     if (o0 + 1 >= (size_t)a.cap_out) return;
     if (a.out_prob && lane == 0) a.out_prob[o0] = a.out_prob[o0 + 1] = pb;
+    if (a.out_split_dim && lane == 0) a.out_split_dim[o0] = a.out_split_dim[o0 + 1] = -1;
     for (int j = lane; j < d; j += 32) {
         const float l = lo[j], h = hi[j];
         a.out_lo[o0 * d + j] = l;

@@ -268,6 +268,7 @@ struct BranchArgs {
     uint64_t pick_seed;
     float *pick_keys;
     const int *split_dim;
+    int *out_split_dim;      // [cap_out] (nullable): unpicked rows keep theirs, children get -1 (not yet searched)
 };
 cudaError_t launch_split_dims(int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
                               uint64_t seed, const float *costs, int M, int top_k, int *split_dim, cudaStream_t st);

@@ -16,6 +16,7 @@ def built():
 
 
 def _branch(gp, lo, hi, lb, ub, ids, inc, n_pick, rule, T, seed, split_dim=None):
+    """Runs bab_prune_branch_heuristic; with split_dim given the output pool also carries the split dimensions."""
     from gpu_util import DEV, T as TT, ids_t
     from paper_2412_09584_gb300 import binding as B
     p, _, _, _ = (W.config_problem("tiny", 0), None, None, None)
@@ -26,13 +27,15 @@ def _branch(gp, lo, hi, lb, ub, ids, inc, n_pick, rule, T, seed, split_dim=None)
            torch.empty(cap, device=DEV), torch.empty(cap, device=DEV), torch.zeros(cap, dtype=torch.int64, device=DEV)]
     keep = torch.empty(max(n, 1), dtype=torch.uint8, device=DEV)
     counts = torch.zeros(3, dtype=torch.int32, device=DEV)
+    osd = None if split_dim is None else torch.full((cap,), 7777, dtype=torch.int32, device=DEV)
     B.bab_prune_branch_heuristic(g.ctx, d, TT(lo), TT(hi), TT(lb), TT(ub), ids_t(ids), n,
                                  torch.tensor([inc], dtype=torch.float64, device=DEV), n_pick, 0.75, rule, T, seed,
                                  cap, *out, keep, counts,
-                                 split_dim=None if split_dim is None else TT(split_dim, torch.int32))
+                                 split_dim=None if split_dim is None else TT(split_dim, torch.int32),
+                                 out_split_dim=osd)
     torch.cuda.synchronize()
     nc, nr, tot = (int(x) for x in counts.cpu().numpy())
-    return {"keep": keep.cpu().numpy()[:n], "n_children": nc, "n_rest": nr, "lo": out[0][:tot].cpu().numpy(),
+    return {"split_dim": None if osd is None else osd[:tot].cpu().numpy(),"keep": keep.cpu().numpy()[:n], "n_children": nc, "n_rest": nr, "lo": out[0][:tot].cpu().numpy(),
             "hi": out[1][:tot].cpu().numpy(), "lb": out[2][:tot].cpu().numpy(), "ub": out[3][:tot].cpu().numpy(),
             "id": out[4][:tot].cpu().numpy().astype(np.uint64)}
 
@@ -80,6 +83,11 @@ def test_branch_with_given_split_dims(oracle, gp):
     r = _branch(gp, lo, hi, lb, ub, ids, 12.0, 50, 0, 1.0, 0, split_dim=sd)
     o = oracle.prune_branch_heuristic(lo, hi, lb, ub, ids, 12.0, 50, pick_rule=0, split_dim=sd)
     _same(r, o)
+    # the split dimensions travel with the pool: unpicked rows keep theirs (found by id), children get -1
+    pos = {int(i): k for k, i in enumerate(ids)}
+    nc = r["n_children"]
+    assert np.all(r["split_dim"][:nc] == -1)
+    assert np.array_equal(r["split_dim"][nc:], sd[[pos[int(i)] for i in r["id"][nc:]]])
 
 
 def test_rollout_split_costs_and_choice(oracle, gp):
