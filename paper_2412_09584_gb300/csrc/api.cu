@@ -55,11 +55,12 @@ float bf16_to_f32_host(uint16_t h)
 void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, std::vector<float> &bias)
 {
     const int L = N.L;
-    bool ok = N.s <= 32 && pad16(N.s + N.k) <= 64;
+    bool ok = N.s <= 32 && N.k <= kTcU && pad16(kTcU + N.s) <= 64;
     for (int l = 1; l < L; ++l) ok = ok && (N.dims[l] % 32 == 0);
     int hi = 0, dcols = 16, acols = 8, bo = 0;
     for (int l = 1; l <= L; ++l) {
-        N.tc_K[l] = pad16(N.dims[l - 1]);
+        // layer 1 reads the input row [u_t (kTcU columns) | x_t]
+        N.tc_K[l] = pad16(l == 1 ? kTcU + N.s : N.dims[l - 1]);
         N.tc_N[l] = pad16(N.dims[l]);
         N.tc_hi[l] = hi;
         hi += ((N.tc_K[l] + 63) / 64) * N.tc_N[l] * 128;
@@ -82,10 +83,12 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
         const float *W = params + N.raw_w[l], *b = params + N.raw_b[l];
         for (int n = 0; n < no; ++n) {
             bias[N.tc_boff[l] + n] = b[n];
-            for (int kk = 0; kk < ni; ++kk) {
-                const float w = W[(size_t)n * ni + kk];
+            for (int kk0 = 0; kk0 < ni; ++kk0) {
+                const float w = W[(size_t)n * ni + kk0];
                 const uint16_t h = bf16_rn_host(w);
                 const uint16_t lo = bf16_rn_host(w - bf16_to_f32_host(h));
+                // column of input kk0 in the tensor-core row (layer 1: state after the action block)
+                const int kk = l == 1 ? (kk0 < N.s ? kTcU + kk0 : kk0 - N.s) : kk0;
                 const int kb = kk / 64, within = kk % 64;
                 const size_t off = (size_t)kb * Nl * 128 + (size_t)n * 128 + (size_t)((((within * 2) / 16) ^ (n % 8)) * 16) +
                                    (size_t)((within * 2) % 16);

@@ -24,6 +24,9 @@ constexpr int kMaxLayers = BAB_MAX_LAYERS;
 constexpr int kMaxWidth = BAB_MAX_WIDTH;
 
 __host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
+// Tensor-core rollout input row: the action u_t in columns 0 .. kTcU - 1 (zero padded), the state x_t from
+// column kTcU on, so that both sit at fixed positions; layer 1 of the forward image is permuted to match.
+constexpr int kTcU = 8;
 
 struct NetDesc {
     int L, s, k, sumh, maxw_p;                // maxw_p = pad4(max width)

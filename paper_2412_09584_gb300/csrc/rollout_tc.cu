@@ -6,9 +6,11 @@
 //
 //   warps 8s .. 8s+7 (slot s): the epilogue of slot s.  Thread r of warps
 //     8s .. 8s+3 owns sample row r: it keeps the state x_t and the running
-//     cost in registers, draws u_t (counter-based), writes the input row
-//     [x_t|u_t|0] to TMEM as the A operand of layer 1, and after the last
-//     layer adds the residual and the step cost.  After each hidden layer the
+//     cost in registers, draws u_t (counter-based; the next step's while the
+//     output layer runs), writes the input row [u_t|x_t|0] (fixed columns;
+//     layer 1 of the weight image is permuted to match) to TMEM as the A
+//     operand of layer 1, and after the last layer adds the residual and the
+//     step cost.  After each hidden layer the
 //     warp pair of a lane quadrant reads the FP32 accumulator row from TMEM
 //     (one half of the columns each), adds the bias, applies ReLU and writes
 //     the next layer's A operand back to TMEM (as BF16, or as a BF16 hi/lo
@@ -16,7 +18,10 @@
 //   warps 8*NSLOT + s: issue every layer's MMAs of slot s (M=128, N = layer
 //     width, K = 16 per instruction), signalling completion on the slot's
 //     mbarrier; the first of them allocates TMEM and loads the weight image
-//     into shared memory once with the bulk copy engine.
+//     into shared memory once with the bulk copy engine.  With two slots the
+//     issuers take turns, one layer-step each: left alone they fall into
+//     step with each other, both epilogues then run while the tensor core
+//     idles.
 //
 // Precision: SPLIT = 3 computes each product as a_hi b_hi + a_hi b_lo +
 // a_lo b_hi with BF16 halves of the FP32 operands and FP32 accumulation
@@ -38,7 +43,6 @@ namespace bab {
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
-constexpr int kKMax = 8;                          // action dimension limit of this kernel
 constexpr int kEpiWarps = 8;                      // epilogue warps per tile slot (2 per TMEM lane quadrant)
 constexpr int kMaxStages = 8;                     // weight ring buffers when the image is streamed
 
@@ -70,12 +74,13 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 
 }  // namespace
 
-// SP: padded state width of the last layer (16 or 32).  STREAM: the weight
+// SX: registers holding the state (8, 16 or 32, at least s; the output
+// layer is 16 wide for SX <= 16, else 32).  STREAM: the weight
 // image does not fit in shared memory, or every tile needs its own problem's
 // image; per slot a producer warp streams it, one K-atom (64 inputs of one
 // layer, hi and lo halves) at a time, through the slot's ring of a.stages
 // buffers in the order the slot's MMA issuer consumes them.
-template <int NSLOT, int SPLIT, int SP, bool STREAM>
+template <int NSLOT, int SPLIT, int SX, bool STREAM>
 __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -83,8 +88,8 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float *bias = reinterpret_cast<float *>(wimg + (STREAM ? (size_t)NSLOT * a.stages * a.stage_bytes : (size_t)a.tc_bytes));
     float *goal_s = bias + N.tc_bias_floats;
-    float *x0_s = goal_s + SP;
-    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_fin;
+    float *x0_s = goal_s + SX;
+    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_tok[NSLOT], bar_fin;
     __shared__ uint64_t bar_full[NSLOT * kMaxStages], bar_empty[NSLOT * kMaxStages];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -100,6 +105,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
         for (int i = 0; i < NSLOT; ++i) {
             tc::mbar_init(&bar_a[i], kEpiWarps);
             tc::mbar_init(&bar_d[i], 1);
+            tc::mbar_init(&bar_tok[i], 1);
         }
         for (int i = 0; i < NSLOT * kMaxStages; ++i) {
             tc::mbar_init(&bar_full[i], 1);
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     }
     if (warp == mma_warp) tc::tmem_alloc(&tmem_base, a.tmem_cols);
     for (int i = threadIdx.x; i < N.tc_bias_floats; i += blockDim.x) bias[i] = a.tc_bias[i];
-    for (int i = threadIdx.x; i < SP; i += blockDim.x) {
+    for (int i = threadIdx.x; i < SX; i += blockDim.x) {
         goal_s[i] = i < s ? a.goal[i] : 0.f;
         x0_s[i] = i < s ? a.x0[i] : 0.f;
     }
@@ -180,25 +186,26 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             const float *bias_p = batched ? a.tc_bias + (size_t)pb * N.tc_bias_floats : bias;
             const int Hb = batched ? problem_H(a.batch, pb, a.H) : a.H;
             const float rho = batched ? problem_rho(a.batch, pb, a.rho) : a.rho;
-            float x[SP];
+            // the state (zero beyond s) and the actions of the coming step (zero beyond k)
+            float x[SX], u[kTcU];
 #pragma unroll
-            for (int i = 0; i < SP; ++i) x[i] = i < s ? x0_p[i] : 0.f;
+            for (int i = 0; i < SX; ++i) x[i] = i < s ? x0_p[i] : 0.f;
+            auto draw_step = [&](int t) {
+#pragma unroll
+                for (int j = 0; j < kTcU; ++j) {
+                    const int jj = t * k + j;
+                    u[j] = j < k ? draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj)) : 0.f;
+                }
+            };
+            if (primary && Hb > 0) draw_step(0);
             float cost = 0.f;
             bool ok = true;
             for (int t = 0; t < Hb && ok; ++t) {
                 if (primary) {
-                    // layer-1 input row [x_t | u_t | 0], K1 <= 64 BF16 values
-                    float u[kKMax];
+                    // layer-1 input row [u_t | x_t | 0] (fixed columns), K1 <= 64 BF16 values
 #pragma unroll
-                    for (int j = 0; j < kKMax; ++j) {
-                        if (j < k) {
-                            const int jj = t * k + j;
-                            u[j] = draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj));
-                            cost = fmaf(rho * u[j], u[j], cost);
-                        } else {
-                            u[j] = 0.f;
-                        }
-                    }
+                    for (int j = 0; j < kTcU; ++j)
+                        if (j < k) cost = fmaf(rho * u[j], u[j], cost);
 #pragma unroll
                     for (int c16 = 0; c16 < 4; ++c16) {
                         if (c16 * 16 >= K1) break;
@@ -209,14 +216,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const int i = c16 * 16 + 2 * q + e;
-                                float v = 0.f;
-#pragma unroll
-                                for (int ii = 0; ii < SP; ++ii)
-                                    if (ii == i && ii < s) v = x[ii];
-#pragma unroll
-                                for (int j = 0; j < kKMax; ++j)
-                                    if (i == s + j && j < k) v = u[j];
-                                v2[e] = v;
+                                v2[e] = i < kTcU ? u[i] : (i - kTcU < SX ? x[i - kTcU] : 0.f);
                             }
                             if (SPLIT == 3) split2(v2[0], v2[1], ph[q], pl[q]);
                             else ph[q] = pack_bf16x2(v2[0], v2[1]);
@@ -250,23 +250,23 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                     if (l == L) {
                         // network output: residual step and step cost (the primary warps own the rows)
                         if (primary) {
-                            float dx[SP];
-                            if (SP == 16) {
+                            float dx[SX];
+                            if (SX <= 16) {
                                 uint32_t v[16];
                                 tc::tmem_ld16(dcol, v);
                                 tc::tmem_wait_ld();
 #pragma unroll
-                                for (int i = 0; i < 16; ++i) dx[i % SP] = __uint_as_float(v[i]);
+                                for (int i = 0; i < SX; ++i) dx[i] = __uint_as_float(v[i]);
                             } else {
                                 uint32_t v[32];
                                 tc::tmem_ld32(dcol, v);
                                 tc::tmem_wait_ld();
 #pragma unroll
-                                for (int i = 0; i < SP; ++i) dx[i] = __uint_as_float(v[i % 32]);
+                                for (int i = 0; i < SX; ++i) dx[i] = __uint_as_float(v[i % 32]);
                             }
                             float c = 0.f;
 #pragma unroll
-                            for (int i = 0; i < SP; ++i) {
+                            for (int i = 0; i < SX; ++i) {
                                 if (i < s) {
                                     x[i] = x[i] + (dx[i] + bl[i]);
                                     const float e = x[i] - goal_p[i];
@@ -276,14 +276,15 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                             cost += c;
                         }
                     } else {
-                        for (int c0 = c_beg; c0 < c_end; c0 += 32) {
-                            uint32_t v[32];
-                            tc::tmem_ld32(dcol + c0, v);
+                        // 16 columns per load: fewer live registers (no spills) for a few more load round trips
+                        for (int c0 = c_beg; c0 < c_end; c0 += 16) {
+                            uint32_t v[16];
+                            tc::tmem_ld16(dcol + c0, v);
                             tc::tmem_wait_ld();
                             const float4 *b4 = reinterpret_cast<const float4 *>(bl + c0);
-                            uint32_t ph[16], pl[16];
+                            uint32_t ph[8], pl[8];
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) {
+                            for (int q = 0; q < 4; ++q) {
                                 const float4 bb = b4[q];
                                 const float z0 = fmaxf(__uint_as_float(v[4 * q + 0]) + bb.x, 0.f);
                                 const float z1 = fmaxf(__uint_as_float(v[4 * q + 1]) + bb.y, 0.f);
@@ -297,13 +298,15 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                                     ph[2 * q + 1] = pack_bf16x2(z2, z3);
                                 }
                             }
-                            tc::tmem_st16(acol_h + c0 / 2, ph);
-                            if (SPLIT == 3) tc::tmem_st16(acol_l + c0 / 2, pl);
+                            tc::tmem_st8(acol_h + c0 / 2, ph);
+                            if (SPLIT == 3) tc::tmem_st8(acol_l + c0 / 2, pl);
                         }
                         tc::tmem_wait_st();
                         tc::fence_before_sync();
                         __syncwarp();
                         if (lane == 0) tc::mbar_arrive(&bar_a[slot]);
+                        // the next step's actions, drawn while the output layer runs
+                        if (primary && l == L - 1 && t + 1 < Hb) draw_step(t + 1);
                     }
                 }
             }
@@ -339,6 +342,12 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             Hb = tile < ntiles ? tile_H(tile) : 0;
         }
         uint32_t phA = 0, ncommit = 0, ring_it = 0;
+        // two slots take the tensor core in turns, one layer-step each, so that one slot's epilogue runs while
+        // the other's MMAs do; n_other: the other slot's layer-steps in this CTA
+        long long n_other = 0;
+        if (NSLOT == 2)
+            for (long long tt = (long long)blockIdx.x * NSLOT + (1 - sl); tt < ntiles; tt += G)
+                n_other += (long long)tile_H(tt) * L;
         const uint32_t dcol = tb + sl * slot_cols;
         const uint32_t ah = dcol + Dc, al = ah + Ac;
         while (tile < ntiles && !*abort) {
@@ -347,6 +356,19 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                 break;
             }
             phA ^= 1;
+            if (NSLOT == 2) {
+                // slot 0's step i + 1 follows slot 1's step i, which follows slot 0's step i
+                const long long i = ncommit;
+                bool w = true;
+                if (sl == 0 && i >= 1 && i - 1 < n_other)
+                    w = tc::mbar_wait(&bar_tok[1], (uint32_t)((i - 1) & 1), abort, kWaitLimitNs);
+                else if (sl == 1 && i < n_other)
+                    w = tc::mbar_wait(&bar_tok[0], (uint32_t)(i & 1), abort, kWaitLimitNs);
+                if (!w) {
+                    raise_abort(a.status, abort);
+                    break;
+                }
+            }
             tc::fence_after_sync();
             const int Kl = N.tc_K[l], Nl = N.tc_N[l];
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
@@ -388,6 +410,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                 if (!ok) break;
             }
             tc::mma_commit(&bar_d[sl]);
+            if (NSLOT == 2) tc::mbar_arrive(&bar_tok[sl]);
             ++ncommit;
             if (++l > L) {
                 l = 1;
@@ -537,10 +560,10 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
 }
 
-template <int NSLOT, int SPLIT, int SP, bool STREAM>
+template <int NSLOT, int SPLIT, int SX, bool STREAM>
 static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = k_rollout_tc<NSLOT, SPLIT, SP, STREAM>;
+    auto kern = k_rollout_tc<NSLOT, SPLIT, SX, STREAM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, (NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, smem, st>>>(a);
@@ -570,21 +593,21 @@ static bool rollout_tc_resident(const NetDesc &N, int split, int max_smem)
 
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
 {
-    if (!N.tc_ok || N.L < 2 || N.s > 32 || N.k > kKMax || N.tc_K[1] > 64) return false;
+    if (!N.tc_ok || N.L < 2 || N.s > 32 || N.k > kTcU || N.tc_K[1] > 64) return false;
     // resident image, or at least two ring buffers
     return rollout_tc_resident(N, split, max_smem) ||
            2 * rollout_tc_stage(N, split) + rollout_tc_extra(N) + 1024 <= (size_t)max_smem;
 }
 
-template <int SPLIT, int SP>
+template <int SPLIT, int SX>
 static cudaError_t launch_tc_shape(const RolloutArgs &a, int nslot, bool stream, int grid, size_t smem,
                                    cudaStream_t st)
 {
     if (stream)
-        return nslot == 2 ? launch_tc_variant<2, SPLIT, SP, true>(a, grid, smem, st)
-                          : launch_tc_variant<1, SPLIT, SP, true>(a, grid, smem, st);
-    return nslot == 2 ? launch_tc_variant<2, SPLIT, SP, false>(a, grid, smem, st)
-                      : launch_tc_variant<1, SPLIT, SP, false>(a, grid, smem, st);
+        return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, true>(a, grid, smem, st)
+                          : launch_tc_variant<1, SPLIT, SX, true>(a, grid, smem, st);
+    return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, false>(a, grid, smem, st)
+                      : launch_tc_variant<1, SPLIT, SX, false>(a, grid, smem, st);
 }
 
 // nslot_pref: tiles per CTA (1 or 2), or -1 for two whenever both fit in tensor memory
@@ -632,12 +655,13 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     grid = grid < num_sms ? grid : num_sms;
     k_fill_keys(a.keys, a.n, st);
     cudaError_t e;
-    const int SPv = N.tc_N[N.L];
-    if (SPv == 16) e = split == 3 ? launch_tc_shape<3, 16>(a, nslot, stream, grid, smem, st)
-                                  : launch_tc_shape<1, 16>(a, nslot, stream, grid, smem, st);
-    else if (SPv == 32) e = split == 3 ? launch_tc_shape<3, 32>(a, nslot, stream, grid, smem, st)
-                                       : launch_tc_shape<1, 32>(a, nslot, stream, grid, smem, st);
-    else return cudaErrorInvalidConfiguration;
+    // state registers: 8, 16 or 32 (the output layer is 16 wide up to 16 states, else 32)
+    if (N.s <= 8) e = split == 3 ? launch_tc_shape<3, 8>(a, nslot, stream, grid, smem, st)
+                                 : launch_tc_shape<1, 8>(a, nslot, stream, grid, smem, st);
+    else if (N.s <= 16) e = split == 3 ? launch_tc_shape<3, 16>(a, nslot, stream, grid, smem, st)
+                                       : launch_tc_shape<1, 16>(a, nslot, stream, grid, smem, st);
+    else e = split == 3 ? launch_tc_shape<3, 32>(a, nslot, stream, grid, smem, st)
+                        : launch_tc_shape<1, 32>(a, nslot, stream, grid, smem, st);
     if (e != cudaSuccess) return e;
     launch_rollout_finalize(a, st);  // ub and best_u from the packed minima
     if (split == 1) {
