@@ -307,6 +307,30 @@ def capture_graphs(st):
     return graphs
 
 
+# DRAM bytes (read + write) per launch of the BF16x3 tensor-core rollout at 4096 boxes x 1024 samples, from one
+# ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel sources it
+# was taken on, so it is reported only while their hash matches.
+ROLLOUT_TC_TRAFFIC = {"bytes": 1625088, "precision": "bf16x3", "boxes": 4096, "samples": 1024,
+                      "sources_sha1": "b881b2cf6d3e00168a814b18a3e27a4ee467c2e9"}
+ROLLOUT_TC_SOURCES = ("rollout_tc.cu", "tc_ptx.cuh", "kernels.cuh", "bab_internal.cuh")
+
+
+def rollout_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for name in ROLLOUT_TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2412_09584_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def rollout_traffic(precision, boxes, samples):
+    t = ROLLOUT_TC_TRAFFIC
+    if (precision, boxes, samples) != (t["precision"], t["boxes"], t["samples"]):
+        return None
+    return t["bytes"] if rollout_sources_sha1() == t["sources_sha1"] else None
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -381,7 +405,8 @@ def run_ours(args):
                              "; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe executes "
                              + ("3x that (3-term BF16 split)" if args.precision == "bf16x3" else "the same") +
                              " plus padding to multiples of 16"}
-    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": None})
+    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                 "traffic": rollout_traffic(args.precision, st.nb, st.M)})
     if rank != 0:
         return
     cfg = {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
