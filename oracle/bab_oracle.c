@@ -36,6 +36,11 @@
  *                         with the softmax pick-out (oracle_pick_key) and given
  *                         split dimensions (oracle_split_dims: the sample-
  *                         imbalance score).
+ *   oracle_cem            Section 3.3 batch_search with the cross-entropy
+ *                         method, warm-started from the parent's best input;
+ *                         it ranks samples by oracle_objective_f32 (the
+ *                         objective in FP32, the precision the search decides
+ *                         in), which is pinned to the FP64 objective.
  *
  * Layout conventions (these are the public conventions of the library too):
  *   network: L linear layers, dims[0] = s + k, dims[L] = s; params holds, for
@@ -1231,5 +1236,205 @@ int oracle_split_dims(int n, int d, const float *lo, const float *hi, const uint
         split_dim[i] = jb;
     }
     free(cs);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cross-entropy search (Section 3.3, batch_search with CEM)                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The objective of Eq. (trajop) in FP32 with one rounding per operation, the
+ * precision in which the search ranks its samples: each neuron's pre-
+ * activation starts from its bias and adds the products w_c z_c in input order
+ * c = 0, 1, ... by fused multiply-adds; ReLU; x_{t+1} = x_t + N([x_t; u_t]); the
+ * step cost starts from 0, adds (x_{t+1,i} - g_i)^2 for i = 0..s-1 and then
+ * (rho u_{t,j}) u_{t,j} for j = 0..k-1 by fused multiply-adds, and is added to
+ * the running total.
+ */
+float oracle_objective_f32(int L, const int *dims, const double *params, int s, int k, int H, float rho,
+                           const float *x0, const float *goal, const float *u)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return NAN;
+    float a[ORC_MAX_WIDTH], b[ORC_MAX_WIDTH], x[ORC_MAX_WIDTH];
+    for (int i = 0; i < s; ++i) x[i] = x0[i];
+    float total = 0.0f;
+    for (int t = 0; t < H; ++t) {
+        for (int i = 0; i < s; ++i) a[i] = x[i];
+        for (int j = 0; j < k; ++j) a[s + j] = u[t * k + j];
+        float *in = a, *out = b;
+        for (int l = 1; l <= L; ++l) {
+            for (int q = 0; q < dims[l]; ++q) {
+                float acc = (float)N.b[l][q];
+                for (int c = 0; c < dims[l - 1]; ++c) acc = fmaf((float)N.W[l][(size_t)q * dims[l - 1] + c], in[c], acc);
+                out[q] = (l < L) ? (acc > 0.0f ? acc : 0.0f) : acc;
+            }
+            float *tmp = in;
+            in = out;
+            out = tmp;
+        }
+        float c = 0.0f;
+        for (int i = 0; i < s; ++i) {
+            volatile float xn = x[i] + in[i];
+            x[i] = xn;
+            volatile float e = xn - goal[i];
+            c = fmaf(e, e, c);
+        }
+        for (int j = 0; j < k; ++j) {
+            volatile float ru = rho * u[t * k + j];
+            c = fmaf(ru, u[t * k + j], c);
+        }
+        volatile float tot = total + c;
+        total = tot;
+    }
+    return total;
+}
+
+/*
+ * The normal draw of the cross-entropy search for (box id, iteration it,
+ * sample m, coordinate j): the Irwin-Hall sum of four uniforms,
+ * z = (r_0 + r_1 + r_2 + r_3 - 2) sqrt(3), which has mean 0, variance 1 and
+ * support |z| <= 2 sqrt(3).  r_c is the top 24 bits of a SplitMix64 chain:
+ * box key b = splitmix(seed ^ splitmix(id)) as for the uniform draw, then
+ * splitmix(b + C) with C = 0x632BE59BD9B4E019 (a stream of its own), then the
+ * iteration, then (m << 32 | 4 j + c).  FP32, left to right, one rounding per
+ * operation.  Sample 0 of iteration 0 is the mean itself (z = 0).
+ */
+float oracle_cem_normal(uint64_t seed, uint64_t id, uint32_t it, uint32_t m, uint32_t j)
+{
+    if (it == 0 && m == 0) return 0.0f;
+    uint64_t h = oracle_splitmix64(seed ^ oracle_splitmix64(id));
+    h = oracle_splitmix64(h + 0x632BE59BD9B4E019ULL);
+    h = oracle_splitmix64(h ^ (uint64_t)it);
+    volatile float acc = 0.0f;
+    for (uint32_t c = 0; c < 4; ++c) {
+        uint64_t hc = oracle_splitmix64(h ^ ((uint64_t)m << 32 | (uint64_t)(4u * j + c)));
+        float r = (float)(hc >> 40) * (1.0f / 16777216.0f);
+        acc = acc + r;
+    }
+    volatile float ctr = acc - 2.0f;
+    volatile float z = ctr * 1.7320508f;
+    return z;
+}
+
+/* The sample: mu + sigma z clipped to [lo, hi], in FP32. */
+float oracle_cem_sample(uint64_t seed, uint64_t id, uint32_t it, uint32_t m, uint32_t j, float mu, float sigma,
+                        float lo, float hi)
+{
+    float z = oracle_cem_normal(seed, id, it, m, j);
+    volatile float sz = sigma * z;
+    volatile float v = mu + sz;
+    float u = v;
+    if (u < lo) u = lo;
+    if (u > hi) u = hi;
+    return u;
+}
+
+typedef struct {
+    float f;
+    int m;
+} ocem;
+
+/* rank by objective (NaN last), then by sample index */
+static int ocem_cmp(const void *pa, const void *pb)
+{
+    const ocem *a = (const ocem *)pa, *b = (const ocem *)pb;
+    const int na = isnan(a->f), nb = isnan(b->f);
+    if (na != nb) return na - nb;
+    if (!na && a->f < b->f) return -1;
+    if (!na && a->f > b->f) return 1;
+    return a->m - b->m;
+}
+
+/*
+ * Cross-entropy search of each box [lo, hi] (Section 3.3: batch_search with
+ * CEM, warm-started from the parent's best input).  The search distribution is
+ * a diagonal normal, started at mu = warm_u clipped to the box (warm_u NULL:
+ * the box centre) and sigma = (hi - lo) / 2.  Each of `iters` iterations draws
+ * M samples (oracle_cem_sample), ranks them by the FP32 objective, and refits
+ * mu and sigma to the E best (the elites, in rank order): mu_j = (sum_e u_ej)
+ * / E, sigma_j = sqrt((sum_e (u_ej - mu_j)^2) / E) + jitter, each sum in rank
+ * order (the squares by fused multiply-adds).  The result is the best sample
+ * over all iterations (ties: the earlier iteration, then the lower sample
+ * index): ub[i] (its FP32 objective) and best_u [n][d].  mu_trace (nullable,
+ * [n][iters][d]) receives mu after each refit.
+ */
+int oracle_cem(int L, const int *dims, const double *params, int s, int k, int H, float rho, const float *x0,
+               const float *goal, int n, const float *lo, const float *hi, const uint64_t *id, const float *warm_u,
+               int M, int iters, int E, float jitter, uint64_t seed, float *ub, float *best_u, float *mu_trace)
+{
+    if (M < 1 || iters < 1 || E < 1 || E > M) return -1;
+    const int d = k * H;
+    float *mu = (float *)malloc(sizeof(float) * d), *sg = (float *)malloc(sizeof(float) * d);
+    float *u = (float *)malloc(sizeof(float) * d);
+    float *nmu = (float *)malloc(sizeof(float) * d), *nsg = (float *)malloc(sizeof(float) * d);
+    ocem *rk = (ocem *)malloc(sizeof(ocem) * M);
+    for (int i = 0; i < n; ++i) {
+        const float *bl = lo + (size_t)i * d, *bh = hi + (size_t)i * d;
+        for (int j = 0; j < d; ++j) {
+            if (warm_u) {
+                float w = warm_u[(size_t)i * d + j];
+                mu[j] = w < bl[j] ? bl[j] : (w > bh[j] ? bh[j] : w);
+            } else {
+                volatile float sum = bl[j] + bh[j];
+                mu[j] = 0.5f * sum;
+            }
+            volatile float wd = bh[j] - bl[j];
+            sg[j] = 0.5f * wd;
+        }
+        float best = NAN;
+        int have = 0;
+        for (int it = 0; it < iters; ++it) {
+            for (int m = 0; m < M; ++m) {
+                for (int j = 0; j < d; ++j)
+                    u[j] = oracle_cem_sample(seed, id[i], (uint32_t)it, (uint32_t)m, (uint32_t)j, mu[j], sg[j], bl[j], bh[j]);
+                rk[m].f = oracle_objective_f32(L, dims, params, s, k, H, rho, x0, goal, u);
+                rk[m].m = m;
+            }
+            qsort(rk, M, sizeof(ocem), ocem_cmp);
+            /* the iteration's best against the best so far (strictly better wins: earlier iterations keep ties) */
+            if (!have || (!isnan(rk[0].f) && (isnan(best) || rk[0].f < best))) {
+                best = rk[0].f;
+                have = 1;
+                for (int j = 0; j < d; ++j)
+                    best_u[(size_t)i * d + j] = oracle_cem_sample(seed, id[i], (uint32_t)it, (uint32_t)rk[0].m,
+                                                                  (uint32_t)j, mu[j], sg[j], bl[j], bh[j]);
+            }
+            /* refit to the elites (every coordinate from the current mu and sigma) */
+            for (int j = 0; j < d; ++j) {
+                float sum = 0.0f;
+                for (int e = 0; e < E; ++e) {
+                    float v = oracle_cem_sample(seed, id[i], (uint32_t)it, (uint32_t)rk[e].m, (uint32_t)j, mu[j], sg[j],
+                                                bl[j], bh[j]);
+                    volatile float t = sum + v;
+                    sum = t;
+                }
+                volatile float mean = sum / (float)E;
+                float acc = 0.0f;
+                for (int e = 0; e < E; ++e) {
+                    float v = oracle_cem_sample(seed, id[i], (uint32_t)it, (uint32_t)rk[e].m, (uint32_t)j, mu[j], sg[j],
+                                                bl[j], bh[j]);
+                    volatile float dv = v - mean;
+                    acc = fmaf(dv, dv, acc);
+                }
+                volatile float var = acc / (float)E;
+                volatile float sd = sqrtf(var);
+                volatile float sj = sd + jitter;
+                nmu[j] = mean;
+                nsg[j] = sj;
+            }
+            memcpy(mu, nmu, sizeof(float) * d);
+            memcpy(sg, nsg, sizeof(float) * d);
+            if (mu_trace) memcpy(mu_trace + ((size_t)i * iters + it) * d, mu, sizeof(float) * d);
+        }
+        ub[i] = best;
+    }
+    free(mu);
+    free(sg);
+    free(u);
+    free(nmu);
+    free(nsg);
+    free(rk);
     return 0;
 }

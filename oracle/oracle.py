@@ -17,6 +17,8 @@ citations are to arXiv 2412.09584 (BaB-ND):
 * ``adam_ascent``   projected Adam on the slopes
 * ``prune_branch``  Section 3 overview (Pruner), Section 3.1 (pick out, split)
 * ``bab``           Algorithm 2 (search, bound, incumbent, prune, pick, split)
+* ``objective_f32`` Eq. (trajop) in FP32 (the precision the search ranks in)
+* ``cem``           Section 3.3 (batch_search with the cross-entropy method)
 """
 from __future__ import annotations
 
@@ -451,3 +453,58 @@ def bab(problem, lo, hi, ids, iters, n_pick, samples, seed, alpha_steps=0, alpha
         if len(lb) == 0:
             break
     return inc_val, inc_u, hist
+
+
+def objective_f32(problem, u):
+    """Eq. (trajop) in FP32 with one rounding per operation (dot products as fused multiply-add chains in input
+    order): the value the search ranks samples by."""
+    net = net_of(problem)
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    x0f = np.ascontiguousarray(problem["x0"], dtype=np.float32)
+    gf = np.ascontiguousarray(problem["goal"], dtype=np.float32)
+    fn = lib().oracle_objective_f32
+    fn.restype = ctypes.c_float
+    return float(fn(*net.cargs(), ctypes.c_int(int(problem["H"])), ctypes.c_float(float(problem["rho"])),
+                    x0f.ctypes.data_as(_c_float_p), gf.ctypes.data_as(_c_float_p), u.ctypes.data_as(_c_float_p)))
+
+
+def cem_normal(seed, box_id, it, m, j):
+    fn = lib().oracle_cem_normal
+    fn.restype = ctypes.c_float
+    fn.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]
+    return float(fn(seed, box_id, it, m, j))
+
+
+def cem_sample(seed, box_id, it, m, j, mu, sigma, lo, hi):
+    fn = lib().oracle_cem_sample
+    fn.restype = ctypes.c_float
+    fn.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                   ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    return float(fn(seed, box_id, it, m, j, mu, sigma, lo, hi))
+
+
+def cem(problem, lo, hi, ids, samples, iters, elites, jitter, seed, warm_u=None, with_trace=False):
+    """Cross-entropy search of each box (Section 3.3): returns ub [n] (FP32 objective of the best sample), best_u
+    [n, d] and, with_trace, mu after every refit [n, iters, d]."""
+    net = net_of(problem)
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    n, d = lo.shape
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    x0f = np.ascontiguousarray(problem["x0"], dtype=np.float32)
+    gf = np.ascontiguousarray(problem["goal"], dtype=np.float32)
+    warm = None if warm_u is None else np.ascontiguousarray(warm_u, dtype=np.float32)
+    ub = np.empty(n, dtype=np.float32)
+    bu = np.empty((n, d), dtype=np.float32)
+    tr = np.empty((n, iters, d), dtype=np.float32) if with_trace else None
+    fn = lib().oracle_cem
+    fn.restype = ctypes.c_int
+    rc = fn(*net.cargs(), ctypes.c_int(int(problem["H"])), ctypes.c_float(float(problem["rho"])),
+            x0f.ctypes.data_as(_c_float_p), gf.ctypes.data_as(_c_float_p), n, lo.ctypes.data_as(_c_float_p),
+            hi.ctypes.data_as(_c_float_p), ids.ctypes.data_as(_c_u64_p),
+            None if warm is None else warm.ctypes.data_as(_c_float_p), samples, iters, elites,
+            ctypes.c_float(jitter), ctypes.c_uint64(seed), ub.ctypes.data_as(_c_float_p),
+            bu.ctypes.data_as(_c_float_p), None if tr is None else tr.ctypes.data_as(_c_float_p))
+    if rc != 0:
+        raise ValueError("oracle_cem: bad arguments")
+    return (ub, bu, tr) if with_trace else (ub, bu)

@@ -744,3 +744,118 @@ def test_split_dims_recount(oracle):
         if jb < 0:
             jb = int(np.argmax(hi[i] - lo[i]))
         assert got[i] == jb, i
+
+
+# --------------------------------------------------------------------------
+# Cross-entropy search (Section 3.3)
+# --------------------------------------------------------------------------
+
+def test_objective_f32_close_to_fp64(oracle):
+    """The FP32 objective the search ranks by is the FP64 objective up to FP32 rounding."""
+    for name, seed in (("tiny", 3), ("pushing", 4)):
+        p = W.config_problem(name, seed)
+        d = p["k"] * p["H"]
+        rng = np.random.default_rng(seed)
+        for _ in range(5):
+            u = rng.uniform(-1, 1, size=d).astype(np.float32)
+            f64 = oracle.objective(p, u.astype(np.float64))
+            assert oracle.objective_f32(p, u) == pytest.approx(f64, rel=2e-6)
+
+
+def test_cem_normal_moments_and_support(oracle):
+    """Irwin-Hall with four uniforms, centred and scaled: mean 0, variance 1, excess kurtosis -6/(5*4) = -0.3,
+    support |z| <= 2 sqrt(3); the first sample of the first iteration is the mean itself."""
+    z = np.array([oracle.cem_normal(11, 5, it, m, j) for it in range(1, 3) for m in range(200) for j in range(100)])
+    assert abs(z.mean()) < 0.01
+    assert abs(z.var() - 1.0) < 0.02
+    kurt = np.mean((z - z.mean()) ** 4) / z.var() ** 2 - 3.0
+    assert abs(kurt + 0.3) < 0.05
+    assert np.abs(z).max() <= 2.0 * np.sqrt(3.0) + 1e-6
+    assert all(oracle.cem_normal(11, 5, 0, 0, j) == 0.0 for j in range(10))
+    assert oracle.cem_normal(11, 5, 0, 1, 0) != 0.0
+
+
+def test_cem_single_sample_is_the_start(oracle):
+    """One iteration of one sample evaluates the start: the box centre, or the warm start clipped to the box."""
+    p = W.config_problem("tiny", 5)
+    lo, hi, ids = W.random_boxes(10, 4, seed=6, min_width=0.2, max_width=1.0)
+    ub, bu = oracle.cem(p, lo, hi, ids, 1, 1, 1, 1e-3, 9)
+    centre = (np.float32(0.5) * (lo + hi)).astype(np.float32)
+    np.testing.assert_array_equal(bu, centre)
+    np.testing.assert_array_equal(ub, np.array([oracle.objective_f32(p, c) for c in centre], dtype=np.float32))
+    warm = np.random.default_rng(1).uniform(-1.5, 1.5, size=lo.shape).astype(np.float32)
+    ub, bu = oracle.cem(p, lo, hi, ids, 1, 1, 1, 1e-3, 9, warm_u=warm)
+    np.testing.assert_array_equal(bu, np.clip(warm, lo, hi))
+
+
+def test_cem_first_refit_is_the_elite_mean(oracle):
+    """mu after the first iteration is the mean of the E samples of smallest FP32 objective (recounted here)."""
+    p = W.config_problem("tiny", 7)
+    lo, hi, ids = W.random_boxes(10, 2, seed=8, min_width=0.3, max_width=1.5)
+    M, E = 40, 6
+    ub, bu, tr = oracle.cem(p, lo, hi, ids, M, 3, E, 1e-3, 13, with_trace=True)
+    for i in range(2):
+        mu0 = np.float32(0.5) * (lo[i] + hi[i])
+        sg0 = np.float32(0.5) * (hi[i] - lo[i])
+        S = np.array([[oracle.cem_sample(13, int(ids[i]), 0, m, j, mu0[j], sg0[j], lo[i, j], hi[i, j])
+                       for j in range(10)] for m in range(M)], dtype=np.float32)
+        f = np.array([oracle.objective_f32(p, S[m]) for m in range(M)])
+        elite = sorted(range(M), key=lambda m: (f[m], m))[:E]
+        np.testing.assert_allclose(tr[i, 0], S[elite].astype(np.float64).mean(axis=0), rtol=1e-6, atol=1e-7)
+        assert np.all(S >= lo[i]) and np.all(S <= hi[i])
+
+
+def test_cem_monotone_in_iterations_and_warm_start(oracle):
+    """More iterations never give a worse best (the first iterations are the same draws), and a warm start
+    inside the box is never beaten by the result."""
+    p = W.config_problem("tiny", 10)
+    lo, hi, ids = W.random_boxes(10, 5, seed=11, min_width=0.3, max_width=1.5)
+    prev = None
+    for iters in (1, 2, 4):
+        ub, _ = oracle.cem(p, lo, hi, ids, 32, iters, 4, 1e-3, 3)
+        if prev is not None:
+            assert np.all(ub <= prev)
+        prev = ub
+    warm = (lo + np.random.default_rng(2).uniform(size=lo.shape).astype(np.float32) * (hi - lo)).astype(np.float32)
+    ub, bu = oracle.cem(p, lo, hi, ids, 16, 2, 4, 1e-3, 3, warm_u=warm)
+    assert np.all(ub <= np.array([oracle.objective_f32(p, w) for w in warm]))
+    assert np.all(bu >= lo) and np.all(bu <= hi)
+    np.testing.assert_array_equal(ub, np.array([oracle.objective_f32(p, b) for b in bu], dtype=np.float32))
+
+
+def test_cem_converges_on_convex_problem(oracle):
+    """All ReLUs active makes f a convex quadratic in u (closed form by matrix algebra); its box-constrained
+    minimum (projected Newton / L-BFGS-B in FP64) is approached by the search from above."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    s, k, H, rho = 3, 2, 4, 0.05
+    rng = np.random.default_rng(19)
+    layers = [(rng.normal(size=(8, s + k)), np.full(8, 50.0)),
+              (rng.uniform(0, 0.1, size=(8, 8)), np.full(8, 1.0)),
+              (0.05 * rng.normal(size=(s, 8)), 0.1 * rng.normal(size=s))]
+    p = dict(dims=[s + k, 8, 8, s], params=W.pack_params(layers), x0=rng.normal(size=s).astype(np.float32),
+             goal=rng.normal(size=s).astype(np.float32), H=H, rho=rho, s=s, k=k)
+    lw = [(Wl.astype(np.float64), bl.astype(np.float64)) for Wl, bl in W.unpack_params(p)]
+    Weff, beff = np.eye(s + k), np.zeros(s + k)
+    for Wl, bl in lw:
+        beff = Wl @ beff + bl
+        Weff = Wl @ Weff
+
+    def f(u):
+        x = p["x0"].astype(np.float64)
+        tot = 0.0
+        for t in range(H):
+            ut = u[t * k:(t + 1) * k]
+            x = x + Weff[:, :s] @ x + Weff[:, s:] @ ut + beff
+            tot += np.sum((x - p["goal"]) ** 2) + rho * np.sum(ut ** 2)
+        return tot
+
+    d = k * H
+    best = scipy_opt.minimize(f, np.zeros(d), method="L-BFGS-B", bounds=[(-1, 1)] * d,
+                              options=dict(ftol=1e-15, gtol=1e-12, maxiter=10000))
+    fstar = best.fun
+    lo = np.full((1, d), -1.0, dtype=np.float32)
+    hi = np.full((1, d), 1.0, dtype=np.float32)
+    ub, bu = oracle.cem(p, lo, hi, np.array([3], dtype=np.uint64), 256, 40, 16, 1e-5, 21)
+    assert ub[0] >= fstar * (1 - 1e-5)
+    assert ub[0] <= fstar * (1 + 1e-3)
+    assert f(bu[0].astype(np.float64)) == pytest.approx(float(ub[0]), rel=1e-5)
