@@ -340,7 +340,11 @@ int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, cons
  * last.  split_dim (device int[n], nullable) gives the dimension to split for
  * each pool row (out of range: widest); out_split_dim (device int[cap_out],
  * nullable) carries it along: unpicked rows keep theirs, children get -1
- * (their own split dimensions come from their search).  The rest is
+ * (their own split dimensions come from their search).  row_u (device
+ * float[n][d], nullable) is a vector per pool row, such as the best input its
+ * search found; out_row_u (float[cap_out][d], given with row_u) receives it:
+ * unpicked rows keep theirs and both children inherit the parent's (the warm
+ * start of their cross-entropy search, Section 3.3).  The rest is
  * bab_prune_branch.
  * Errors: as bab_prune_branch, BAB_ERR_INVALID_ARG for an unknown rule or
  * temperature <= 0.
@@ -361,14 +365,45 @@ int bab_prune_branch_heuristic(bab_ctx *ctx, int d, const float *lo, const float
                                const float *ub, const uint64_t *id, int n, const int *d_n, const double *inc_val,
                                int n_pick, float eta, int pick_rule, float temperature, uint64_t pick_seed,
                                const int *split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb,
-                               float *out_ub, uint64_t *out_id, int *out_split_dim, uint8_t *keep, int *d_counts,
-                               void *stream);
+                               float *out_ub, uint64_t *out_id, int *out_split_dim, const float *row_u,
+                               float *out_row_u, uint8_t *keep, int *d_counts, void *stream);
 int bab_split_dims(bab_ctx *ctx, int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
                    uint64_t seed, const float *costs, int samples, int top_k, int *split_dim, void *stream);
 int bab_rollout_split(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
                       const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
                       int precision, float top_pct, float *ub, float *best_u, double *inc_val, float *inc_u,
                       float *costs, int *split_dim, void *stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Cross-entropy search (Section 3.3: batch_search with CEM, warm-started from
+ * the parent's best input).  Per box [lo, hi] the search distribution is a
+ * diagonal normal (mu, sigma): mu starts at warm_u clipped to the box (device
+ * float[n][d], nullable: the box centre), sigma at (hi - lo) / 2.  Each of
+ * `iters` iterations draws `samples` inputs u = clip(mu + sigma z, lo, hi)
+ * (z: the Irwin-Hall sum of four counter-based uniforms, centred and scaled
+ * to unit variance; sample 0 of iteration 0 is mu itself), evaluates them,
+ * ranks them by (objective, sample index) and refits mu and sigma to the
+ * `elites` best: mu = their mean, sigma = their standard deviation plus
+ * `jitter`, each sum in rank order.
+ *
+ * Results: ub[i] the best objective over all iterations (ties keep the earlier
+ * iteration) and best_u [n][d] its input (both required); the incumbent
+ * (inc_val, inc_u, nullable together) is updated as in bab_rollout.
+ * precision BAB_PREC_FP32 (the objective with every dot product a fused
+ * multiply-add chain in input order, the step cost summed state terms then
+ * action terms: decisions reproducible by any implementation of that
+ * definition) or BAB_PREC_BF16X3 (tensor cores); BAB_PREC_BF16 is
+ * BAB_ERR_UNSUPPORTED.  1 <= samples <= BAB_CEM_MAX_SAMPLES,
+ * 1 <= elites <= samples, iters >= 1, jitter finite and >= 0, warm_u finite.
+ * The context keeps mu, sigma and the objectives of one iteration in its
+ * scratch (grown on first use, so not inside a graph capture the first time).
+ */
+#define BAB_CEM_MAX_SAMPLES 4096
+int bab_rollout_cem(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
+                    const float *hi, const uint64_t *id, int n, const int *d_n, int samples, int iters, int elites,
+                    float jitter, uint64_t seed, int precision, const float *warm_u, float *ub, float *best_u,
+                    double *inc_val, float *inc_u, void *stream);
 
 /*
  * Synchronise `stream` and return the sticky device-side status of ctx (0 or

@@ -83,8 +83,10 @@ def load(path: str = LIB_PATH):
     L.bab_rollout_search_bounds.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _P, _P, _P,
                                             _P, _P, _P, _P, _P, _P]
     L.bab_bound_crown_given.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P]
+    L.bab_rollout_cem.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, _I, _I, _F, ctypes.c_uint64, _I, _P,
+                                  _P, _P, _P, _P, _P]
     L.bab_prune_branch_heuristic.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _F, ctypes.c_uint64,
-                                             _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+                                             _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.bab_split_dims.argtypes = [_P, _I, _P, _P, _P, _I, _P, ctypes.c_uint64, _P, _I, _I, _P, _P]
     L.bab_rollout_split.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _F, _P, _P, _P,
                                     _P, _P, _P, _P]
@@ -352,14 +354,15 @@ def bab_bound_crown_given(ctx, x0, goal, horizon, rho, lo, hi, n, pre_lo, pre_hi
 
 def bab_prune_branch_heuristic(ctx, d, lo, hi, lb, ub, ids, n, inc_val, n_pick, eta, pick_rule, temperature, pick_seed,
                                cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts, split_dim=None,
-                               out_split_dim=None, d_n=None, stream=None):
+                               out_split_dim=None, row_u=None, out_row_u=None, d_n=None, stream=None):
     f32 = torch.float32
     rc = load().bab_prune_branch_heuristic(
         ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(lb, f32, "lb"), _ptr(ub, f32, "ub"),
         _ptr(ids, torch.uint64, "id"), int(n), _ptr(d_n, torch.int32), _ptr(inc_val, torch.float64, "inc_val"),
         int(n_pick), float(eta), int(pick_rule), float(temperature), int(pick_seed), _ptr(split_dim, torch.int32),
         int(cap_out), _ptr(out_lo, f32), _ptr(out_hi, f32), _ptr(out_lb, f32), _ptr(out_ub, f32),
-        _ptr(out_id, torch.uint64), _ptr(out_split_dim, torch.int32), _ptr(keep, torch.uint8),
+        _ptr(out_id, torch.uint64), _ptr(out_split_dim, torch.int32), _ptr(row_u, f32), _ptr(out_row_u, f32),
+        _ptr(keep, torch.uint8),
         _ptr(d_counts, torch.int32, "d_counts"), _stream(stream))
     _check(ctx, rc)
 
@@ -381,4 +384,20 @@ def bab_rollout_split(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, seed
                                   _ptr(ub, f32, "ub"), _ptr(best_u, f32), _ptr(inc_val, torch.float64),
                                   _ptr(inc_u, f32), _ptr(costs, f32), _ptr(split_dim, torch.int32, "split_dim"),
                                   _stream(stream))
+    _check(ctx, rc)
+
+
+CEM_MAX_SAMPLES = 4096
+
+
+def bab_rollout_cem(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, iters, elites, jitter, seed, precision, ub,
+                    best_u, warm_u=None, inc_val=None, inc_u=None, d_n=None, stream=None):
+    """Cross-entropy search of each box (Section 3.3 batch_search with CEM); see include/bab.h."""
+    f32 = torch.float32
+    rc = load().bab_rollout_cem(ctx, _ptr(x0, f32, "x0"), _ptr(goal, f32, "goal"), int(horizon), float(rho),
+                                _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"), int(n),
+                                _ptr(d_n, torch.int32), int(samples), int(iters), int(elites), float(jitter),
+                                int(seed), int(precision), _ptr(warm_u, f32), _ptr(ub, f32, "ub"),
+                                _ptr(best_u, f32, "best_u"), _ptr(inc_val, torch.float64), _ptr(inc_u, f32),
+                                _stream(stream))
     _check(ctx, rc)

@@ -527,6 +527,98 @@ int bab_rollout_split(bab_ctx *c, const float *x0, const float *goal, int H, flo
     return bab_split_dims(c, c->net.k * H, lo, hi, id, n, d_n, seed, cst, samples, top_k, split_dim, stream);
 }
 
+int bab_rollout_cem(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                    const uint64_t *id, int n, const int *d_n, int samples, int iters, int elites, float jitter,
+                    uint64_t seed, int precision, const float *warm_u, float *ub, float *best_u, double *inc_val,
+                    float *inc_u, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (samples < 1 || samples > BAB_CEM_MAX_SAMPLES) return fail(c, BAB_ERR_SHAPE, "samples must be in [1, 4096]");
+    if (iters < 1 || elites < 1 || elites > samples)
+        return fail(c, BAB_ERR_INVALID_ARG, "need iters >= 1 and 1 <= elites <= samples");
+    if (!(jitter >= 0.f) || !std::isfinite(jitter)) return fail(c, BAB_ERR_INVALID_ARG, "jitter must be finite and >= 0");
+    if (n > 0 && (!id || !ub || !best_u)) return fail(c, BAB_ERR_INVALID_ARG, "id, ub and best_u are required");
+    if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
+    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
+        return fail(c, BAB_ERR_UNSUPPORTED, "the cross-entropy search runs in FP32 or BF16x3 (precision %d)", precision);
+    if ((long long)iters * samples >= (1ll << 32)) return fail(c, BAB_ERR_SHAPE, "iters * samples must be < 2^32");
+    if (precision == BAB_PREC_BF16X3 && !rollout_tc_supported(c->net, 3, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout not available for this network");
+    if (n == 0) return BAB_OK;
+    const int d = c->net.k * H;
+    // scratch: rollout keys, top-k threshold, costs [n][M], mu and sigma [n][d], best keys [n]
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t kb = al((size_t)n * 8), cb = al((size_t)n * samples * 4), db = al((size_t)n * d * 4);
+    rc = ensure_scratch(c, kb + 512 + cb + 2 * db + kb);
+    if (rc) return rc;
+    char *sp = static_cast<char *>(c->scratch);
+    float *costs = reinterpret_cast<float *>(sp + kb + 512);
+    CemArgs g{};
+    g.lo = lo;
+    g.hi = hi;
+    g.id = id;
+    g.n = n;
+    g.d_n = d_n;
+    g.d = d;
+    g.M = samples;
+    g.E = elites;
+    g.jitter = jitter;
+    g.seed = seed;
+    g.costs = costs;
+    g.mu = reinterpret_cast<float *>(sp + kb + 512 + cb);
+    g.sigma = reinterpret_cast<float *>(sp + kb + 512 + cb + db);
+    g.best = reinterpret_cast<unsigned long long *>(sp + kb + 512 + cb + 2 * db);
+    g.ub = ub;
+    g.best_u = best_u;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_cem_init(g, warm_u, st);
+    RolloutArgs a{};
+    a.net = c->net;
+    a.batch.P = 1;
+    a.batch.Hmax = H;
+    a.fwd = c->d_fwd;
+    a.raw = c->d_raw;
+    a.x0 = x0;
+    a.goal = goal;
+    a.lo = lo;
+    a.hi = hi;
+    a.id = id;
+    a.n = n;
+    a.d_n = d_n;
+    a.H = H;
+    a.M = samples;
+    a.d = d;
+    a.rho = rho;
+    a.seed = seed;
+    a.keys = reinterpret_cast<unsigned long long *>(sp);
+    a.topk_t = reinterpret_cast<unsigned long long *>(sp + kb);
+    a.ub = ub;
+    a.best_u = best_u;
+    a.inc_val = inc_val;
+    a.inc_u = inc_u;
+    a.status = c->d_status;
+    a.tc_img = c->d_tc;
+    a.tc_bias = c->d_tc_bias;
+    a.tc_bytes = c->net.tc_bytes;
+    a.costs = costs;
+    a.cem_mu = g.mu;
+    a.cem_sigma = g.sigma;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        a.cem_it = it;
+        g.it = it;
+        e = precision == BAB_PREC_FP32 ? launch_rollout_fp32(a, c->tune_rollout_fp32, c->num_sms, st)
+                                       : launch_rollout_tc(a, 3, c->tune_rollout_tc, c->num_sms, st);
+        if (e == cudaSuccess) e = launch_cem_step(g, st);
+    }
+    if (e == cudaSuccess && inc_val) {
+        launch_incumbent(a, st);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cross-entropy search kernels");
+    return BAB_OK;
+}
+
 int bab_rollout_search_bounds(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
                               const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
                               float *ub, float *best_u, double *inc_val, float *inc_u, float *pre_lo, float *pre_hi,
@@ -906,8 +998,9 @@ namespace {
 int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                       const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
                       int split_rule, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
-                      int *out_split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
-                      uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream);
+                      int *out_split_dim, const float *row_u, float *out_row_u, int cap_out, float *out_lo,
+                      float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep, int *d_counts,
+                      void *stream);
 }  // namespace
 
 extern "C" {
@@ -919,22 +1012,25 @@ int bab_prune_branch(bab_ctx *c, int d, const float *lo, const float *hi, const 
 {
     if (c && split_rule != BAB_SPLIT_WIDEST) return fail(c, BAB_ERR_UNSUPPORTED, "split rule %d", split_rule);
     return prune_branch_impl(c, d, lo, hi, lb, ub, id, n, d_n, inc_val, n_pick, eta, split_rule, BAB_PICK_LB, 1.f, 0,
-                             nullptr, nullptr, cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep, d_counts,
-                             stream);
+                             nullptr, nullptr, nullptr, nullptr, cap_out, out_lo, out_hi, out_lb, out_ub, out_id, keep,
+                             d_counts, stream);
 }
 
 int bab_prune_branch_heuristic(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                                const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick,
                                float eta, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
                                int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
-                               uint64_t *out_id, int *out_split_dim, uint8_t *keep, int *d_counts, void *stream)
+                               uint64_t *out_id, int *out_split_dim, const float *row_u, float *out_row_u,
+                               uint8_t *keep, int *d_counts, void *stream)
 {
     if (!c) return BAB_ERR_INVALID_ARG;
     if (pick_rule != BAB_PICK_LB && pick_rule != BAB_PICK_SOFTMAX) return fail(c, BAB_ERR_INVALID_ARG, "pick rule %d", pick_rule);
     if (!(temperature > 0.f) || !std::isfinite(temperature)) return fail(c, BAB_ERR_INVALID_ARG, "temperature must be > 0");
+    if ((row_u == nullptr) != (out_row_u == nullptr))
+        return fail(c, BAB_ERR_INVALID_ARG, "row_u and out_row_u go together");
     return prune_branch_impl(c, d, lo, hi, lb, ub, id, n, d_n, inc_val, n_pick, eta, BAB_SPLIT_WIDEST, pick_rule,
-                             temperature, pick_seed, split_dim, out_split_dim, cap_out, out_lo, out_hi, out_lb,
-                             out_ub, out_id, keep, d_counts, stream);
+                             temperature, pick_seed, split_dim, out_split_dim, row_u, out_row_u, cap_out, out_lo,
+                             out_hi, out_lb, out_ub, out_id, keep, d_counts, stream);
 }
 
 }  // extern "C"
@@ -943,8 +1039,9 @@ namespace {
 int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                       const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
                       int split_rule, int pick_rule, float temperature, uint64_t pick_seed, const int *split_dim,
-                      int *out_split_dim, int cap_out, float *out_lo, float *out_hi, float *out_lb, float *out_ub,
-                      uint64_t *out_id, uint8_t *keep, int *d_counts, void *stream)
+                      int *out_split_dim, const float *row_u, float *out_row_u, int cap_out, float *out_lo,
+                      float *out_hi, float *out_lb, float *out_ub, uint64_t *out_id, uint8_t *keep, int *d_counts,
+                      void *stream)
 {
     if (!c) return BAB_ERR_INVALID_ARG;
     c->err[0] = 0;
@@ -969,6 +1066,8 @@ int prune_branch_impl(bab_ctx *c, int d, const float *lo, const float *hi, const
     a.pick_keys = reinterpret_cast<float *>(reinterpret_cast<int *>(c->scratch) + rows + 64);
     a.split_dim = split_dim;
     a.out_split_dim = out_split_dim;
+    a.row_u = row_u;
+    a.out_row_u = out_row_u;
     a.d = d;
     a.n = n;
     a.d_n = d_n;

@@ -82,6 +82,33 @@ __device__ __forceinline__ float draw_sample(uint64_t hbox, uint32_t m, uint32_t
     return __fadd_rn(lo, __fmul_rn(__fsub_rn(hi, lo), r));
 }
 
+// The normal draw of the cross-entropy search for (box key hbox, iteration it, sample m, coordinate j): the
+// Irwin-Hall sum of four 24-bit uniforms, z = (r0 + r1 + r2 + r3 - 2) sqrt(3) (mean 0, variance 1, |z| <= 2
+// sqrt(3)); the uniforms come from a SplitMix64 chain of the box key plus a stream constant, the iteration,
+// then (m << 32 | 4 j + c).  FP32 left to right, one rounding per operation.  Sample 0 of iteration 0 is the
+// mean itself (z = 0).
+__device__ __forceinline__ float cem_normal(uint64_t hbox, uint32_t it, uint32_t m, uint32_t j)
+{
+    if (it == 0 && m == 0) return 0.f;
+    uint64_t h = splitmix64(hbox + 0x632BE59BD9B4E019ull);
+    h = splitmix64(h ^ (uint64_t)it);
+    float acc = 0.f;
+#pragma unroll
+    for (uint32_t c = 0; c < 4; ++c) {
+        const uint64_t hc = splitmix64(h ^ (((uint64_t)m << 32) | (uint64_t)(4u * j + c)));
+        acc = __fadd_rn(acc, __fmul_rn(__ull2float_rn(hc >> 40), 5.9604644775390625e-08f));
+    }
+    return __fmul_rn(__fsub_rn(acc, 2.f), 1.7320508f);
+}
+
+// The search sample: mu + sigma z clipped to [lo, hi], in FP32.
+__device__ __forceinline__ float cem_sample(uint64_t hbox, uint32_t it, uint32_t m, uint32_t j, float mu, float sigma,
+                                            float lo, float hi)
+{
+    const float v = __fadd_rn(mu, __fmul_rn(sigma, cem_normal(hbox, it, m, j)));
+    return fminf(fmaxf(v, lo), hi);
+}
+
 // Natural logarithm of a positive normal float from basic operations only, each rounded once (no
 // contraction): x = 2^e m, m in [sqrt(1/2), sqrt(2)), log x = e ln 2 + 2 atanh(z), z = (m - 1)/(m + 1), by the
 // atanh series to z^13.  The same steps in any IEEE arithmetic give the same bits; the softmax pick-out relies

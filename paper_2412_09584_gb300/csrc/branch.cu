@@ -202,6 +202,8 @@ __global__ void k_branch_write(BranchArgs a)
             a.out_lo[o * d + j] = lo[j];
             a.out_hi[o * d + j] = hi[j];
         }
+        if (a.out_row_u)
+            for (int j = lane; j < d; j += 32) a.out_row_u[o * d + j] = a.row_u[(size_t)row * d + j];
         if (lane == 0) {
             a.out_id[o] = id;
             a.out_lb[o] = a.lb[row];
@@ -242,6 +244,12 @@ __global__ void k_branch_write(BranchArgs a)
         a.out_lo[(o0 + 1) * d + j] = (j == jb) ? mid : l;
         a.out_hi[(o0 + 1) * d + j] = h;
     }
+    if (a.out_row_u)
+        for (int j = lane; j < d; j += 32) {
+            const float v = a.row_u[(size_t)row * d + j];
+            a.out_row_u[o0 * d + j] = v;
+            a.out_row_u[(o0 + 1) * d + j] = v;
+        }
     if (lane == 0) {
         if (id >> 63) set_status(a.status, BAB_ERR_SHAPE);
         a.out_id[o0] = 2 * id;

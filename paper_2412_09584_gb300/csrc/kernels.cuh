@@ -66,6 +66,25 @@ struct RolloutArgs {
     // BF16 rollouts: re-score in FP32 only the topk boxes of smallest BF16 ub (0: every box)
     int topk;
     unsigned long long *topk_t;  // [3] scratch: the selection threshold
+    // cross-entropy search (nullable): samples are cem_sample(.., cem_it, m, j, cem_mu[j], cem_sigma[j], ..) of
+    // each box's [n][d] mean and spread instead of uniform draws
+    const float *cem_mu, *cem_sigma;
+    int cem_it;
+};
+
+// one refit of the cross-entropy search (after a rollout of iteration `it` that wrote costs)
+struct CemArgs {
+    const float *lo, *hi;
+    const uint64_t *id;
+    int n;
+    const int *d_n;
+    int d, M, E, it;
+    float jitter;
+    uint64_t seed;
+    const float *costs;       // [n][M]
+    float *mu, *sigma;        // [n][d], refitted in place
+    unsigned long long *best; // [n]: (order(f), it * M + m) of the best sample so far, ~0 before any
+    float *ub, *best_u;       // [n], [n][d]
 };
 
 struct BoundArgs {
@@ -205,6 +224,9 @@ __device__ __forceinline__ void dense_rows_auto(const float *in, int ldi, const 
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, int variant, int num_sms, cudaStream_t st);
 int rollout_fp32_variants();
 cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_sms, cudaStream_t st);
+// cross-entropy search: start (mu, sigma, best) and one refit
+cudaError_t launch_cem_init(const CemArgs &c, const float *warm_u, cudaStream_t st);
+cudaError_t launch_cem_step(const CemArgs &c, cudaStream_t st);
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem);
 void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st);
 void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st);
@@ -269,6 +291,8 @@ struct BranchArgs {
     float *pick_keys;
     const int *split_dim;
     int *out_split_dim;      // [cap_out] (nullable): unpicked rows keep theirs, children get -1 (not yet searched)
+    const float *row_u;      // [n][d] (nullable): a vector per pool row (the best input of its search)
+    float *out_row_u;        // [cap_out][d] (with row_u): unpicked rows keep theirs, children inherit the parent's
 };
 cudaError_t launch_split_dims(int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
                               uint64_t seed, const float *costs, int M, int top_k, int *split_dim, cudaStream_t st);

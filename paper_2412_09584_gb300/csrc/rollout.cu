@@ -79,7 +79,10 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
                     v = xs[r * pad4(s) + c];
                 } else if (c < s + k) {
                     const int j = t * k + (c - s);
-                    v = draw_sample(hb, (uint32_t)(m0 + r), (uint32_t)j, blo[j], bhi[j]);
+                    v = a.cem_mu ? cem_sample(hb, (uint32_t)a.cem_it, (uint32_t)(m0 + r), (uint32_t)j,
+                                              a.cem_mu[(size_t)box * d + j], a.cem_sigma[(size_t)box * d + j], blo[j],
+                                              bhi[j])
+                                 : draw_sample(hb, (uint32_t)(m0 + r), (uint32_t)j, blo[j], bhi[j]);
                     us[r * pad4(k) + (c - s)] = v;
                 } else {
                     v = 0.f;
@@ -115,21 +118,21 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
                 }
                 float *tmp = in; in = out; out = tmp;
             }
-            // `in` holds the network output: residual step and per-row cost (one warp per row)
-            for (int r = warp; r < R; r += NT / 32) {
+            // `in` holds the network output: residual step and the step cost of each row (one thread per row,
+            // state terms then action terms in index order, so the value has a plain sequential definition)
+            for (int r = threadIdx.x; r < R; r += NT) {
                 float c = 0.f;
-                for (int i = lane; i < s; i += 32) {
+                for (int i = 0; i < s; ++i) {
                     const float x = xs[r * pad4(s) + i] + in[r * ld + i];
                     xs[r * pad4(s) + i] = x;
                     const float e = x - goal[i];
                     c = fmaf(e, e, c);
                 }
-                for (int j = lane; j < k; j += 32) {
+                for (int j = 0; j < k; ++j) {
                     const float u = us[r * pad4(k) + j];
                     c = fmaf(rho * u, u, c);
                 }
-                c = warp_sum(c);
-                if (lane == 0) cost[r] += c;
+                cost[r] += c;
             }
             __syncthreads();
             if (emit) {
@@ -325,6 +328,7 @@ cudaError_t launch_rollout_fp32(const RolloutArgs &a, int variant, int num_sms, 
         default: e = launch_fp32_variant<64, 256, 1>(a, num_sms, budget, st); break;
     }
     if (e != cudaSuccess) return e;
+    if (a.cem_mu) return cudaGetLastError();  // the cross-entropy search keeps its own best (launch_cem_step)
     launch_rollout_finalize(a, st);
     if (a.inc_val) launch_incumbent(a, st);
     return cudaGetLastError();

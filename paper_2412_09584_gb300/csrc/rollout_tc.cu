@@ -194,7 +194,15 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
 #pragma unroll
                 for (int j = 0; j < kTcU; ++j) {
                     const int jj = t * k + j;
-                    u[j] = j < k ? draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj)) : 0.f;
+                    if (j >= k) {
+                        u[j] = 0.f;
+                    } else if (a.cem_mu) {
+                        const size_t e = (size_t)box * a.d + jj;
+                        u[j] = cem_sample(hb, (uint32_t)a.cem_it, (uint32_t)m, (uint32_t)jj, __ldg(a.cem_mu + e),
+                                          __ldg(a.cem_sigma + e), __ldg(blo + jj), __ldg(bhi + jj));
+                    } else {
+                        u[j] = draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj));
+                    }
                 }
             };
             if (primary && Hb > 0) draw_step(0);
@@ -663,6 +671,7 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     else e = split == 3 ? launch_tc_shape<3, 32>(a, nslot, stream, grid, smem, st)
                         : launch_tc_shape<1, 32>(a, nslot, stream, grid, smem, st);
     if (e != cudaSuccess) return e;
+    if (a.cem_mu) return cudaGetLastError();  // the cross-entropy search keeps its own best (launch_cem_step)
     launch_rollout_finalize(a, st);  // ub and best_u from the packed minima
     if (split == 1) {
         if (a.topk > 0) k_topk_select<<<1, 1024, 0, st>>>(a);
