@@ -133,7 +133,7 @@ class BabState:
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
                  alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None,
-                 heuristics=None):
+                 heuristics=None, cem=None):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -189,6 +189,16 @@ class BabState:
         # from the imbalance of the top w% samples; None: smallest lb and widest dimension
         self.heur = heuristics
         self.it = 0
+        # cross-entropy search (Section 3.3) instead of uniform samples: dict(iters, elites, jitter), samples per
+        # iteration = M / iters; every pool row carries its best input, the warm start of its children
+        self.cem = cem
+        if cem is not None:
+            for Q in self.pool:
+                Q["bu"] = torch.zeros(self.cap, self.d, **f)
+            if heuristics is None:
+                self.heur = {"T": None, "w": 1.0, "split": False}
+            for Q in self.pool:
+                Q.setdefault("sd", torch.full((self.cap,), -1, dtype=torch.int32, device=device))
         if heuristics is not None:
             for Q in self.pool:
                 Q["sd"] = torch.full((self.cap,), -1, dtype=torch.int32, device=device)
@@ -219,7 +229,13 @@ class BabState:
         if events:
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
-        if self.heur is not None:
+        if self.cem is not None:
+            c = self.cem
+            warm = P["bu"] if self.it > 0 else None   # the starting pool has no parents
+            B.bab_rollout_cem(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n,
+                              self.M // c["iters"], c["iters"], c["elites"], c["jitter"], self.seed + self.it,
+                              self.rprec, P["ub"], P["bu"], warm_u=warm, d_n=d_n)
+        elif self.heur is not None:
             B.bab_rollout_split(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], P["id"], n, self.M,
                                 self.seed, self.rprec, self.heur["w"], P["ub"], P["sd"], best_u=self.best_u,
                                 costs=self.costs, d_n=d_n)
@@ -235,8 +251,9 @@ class BabState:
         main = torch.cuda.current_stream()
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
-            B.bab_update_incumbent(self.ctx, self.x0, self.goal, self.H, self.rho, P["ub"], self.best_u, n,
-                                   self.inc_val, self.inc_u, d_n=d_n)
+            B.bab_update_incumbent(self.ctx, self.x0, self.goal, self.H, self.rho, P["ub"],
+                                   P["bu"] if self.cem is not None else self.best_u, n, self.inc_val, self.inc_u,
+                                   d_n=d_n)
         if self.search_stop is not None:
             B.bab_bound_crown_given(self.ctx, self.x0, self.goal, self.H, self.rho, P["lo"], P["hi"], n, *self.emp,
                                     self.search_stop, P["lb"], d_n=d_n)
@@ -266,7 +283,8 @@ class BabState:
                                          self.seed * 1000003 + self.it, self.cap, dst["lo"], dst["hi"], dst["lb"],
                                          dst["ub"], dst["id"], self.keep, self.counts,
                                          split_dim=src["sd"] if self.heur["split"] else None,
-                                         out_split_dim=dst["sd"], d_n=self.n_live_dev)
+                                         out_split_dim=dst["sd"], row_u=src.get("bu"), out_row_u=dst.get("bu"),
+                                         d_n=self.n_live_dev)
         self.it += 1
         if not self.fixed:
             self.n_max = min(self.n_max + self.n_pick, self.cap - self.n_pick)
@@ -386,6 +404,7 @@ def run_ours(args):
     manip = None if args.no_manip else manip_scale(dev)
     paper_bounds = None if args.no_time_to_gap else paper_bounding_comparison(dev)
     heuristics = None if args.no_time_to_gap else heuristics_comparison(dev)
+    cem_cmp = None if args.no_time_to_gap else cem_comparison(dev)
 
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
@@ -429,7 +448,7 @@ def run_ours(args):
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
            "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
-           "paper_bounding": paper_bounds, "heuristics": heuristics}
+           "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -724,6 +743,45 @@ def heuristics_comparison(dev, iters=30):
             res[name] = {"incumbent": inc[-1], "gap": gaps[-1],
                          "incumbent_every_5": [round(v, 5) for v in inc[4::5]],
                          "gap_every_5": [round(v, 5) for v in gaps[4::5]],
+                         "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters}
+        out[wl] = res
+    return out
+
+
+def cem_comparison(dev, iters=30):
+    """Cross-entropy search (Section 3.3; each child warm-started from its parent's best input, 10 elites as in the
+    paper's CEM settings) against uniform samples with the same number of rollouts per box, in the same sound BaB
+    loop: incumbent and gap per iteration, time per iteration."""
+    import torch
+    work = {"alpha": ("MLP 6-32-32-4, H=5, 4096 children per iteration, 256 FP32 rollouts each", 2048, "fp32"),
+            "pushing": ("MLP 10-128-128-128-8, H=20, 512 children per iteration, 1024 BF16x3 rollouts each", 256,
+                        "bf16x3")}
+    variants = {"uniform": None, "cem_4x": {"iters": 4, "elites": 10, "jitter": 1e-3},
+                "cem_8x": {"iters": 8, "elites": 10, "jitter": 1e-3}}
+    out = {"bound": f"sound (interval + CROWN, FP32, margin); {iters} iterations; the same rollouts per box "
+                    "(CEM: samples / iterations per iteration); deterministic pick-out and widest split"}
+    for wl, (desc, n_pick, rprec) in work.items():
+        res = {"workload": f"{wl}: {desc}"}
+        for name, c in [("warm-up", None)] + list(variants.items()):
+            for warm in (True, False):
+                st = BabState(wl, SEED, dev, n_pick, rprec, "fp32", pool_iters=iters + 2, cem=c)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                inc, gaps = [], []
+                for _ in range(2 if warm else iters):
+                    st.step()
+                    if not warm:
+                        g, _ = st.gap()
+                        inc.append(float(st.inc_val.item()))
+                        gaps.append(g)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t
+                n_live = int(st.counts[2].item())
+                st.close()
+            if name == "warm-up":
+                continue
+            res[name] = {"incumbent": inc[-1], "gap": gaps[-1],
+                         "incumbent_every_5": [round(v, 6) for v in inc[4::5]],
                          "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters}
         out[wl] = res
     return out
