@@ -36,6 +36,9 @@
  *                         with the softmax pick-out (oracle_pick_key) and given
  *                         split dimensions (oracle_split_dims: the sample-
  *                         imbalance score).
+ *   oracle_synth_*        Section 4, synthetic example: f(u) = sum 5 u_i^2 +
+ *                         cos(50 u_i); its sampled search and the exact per-
+ *                         term interval bound.
  *   oracle_cem            Section 3.3 batch_search with the cross-entropy
  *                         method, warm-started from the parent's best input;
  *                         it ranks samples by oracle_objective_f32 (the
@@ -1436,5 +1439,74 @@ int oracle_cem(int L, const int *dims, const double *params, int s, int k, int H
     free(nmu);
     free(nsg);
     free(rk);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Synthetic objective (Section 4, synthetic example)                         */
+/* ------------------------------------------------------------------------ */
+
+/* f(u) = sum_i 5 u_i^2 + cos(50 u_i), u in [-1, 1]^d. */
+double oracle_synth_f(int d, const double *u)
+{
+    double f = 0.0;
+    for (int i = 0; i < d; ++i) f += 5.0 * u[i] * u[i] + cos(50.0 * u[i]);
+    return f;
+}
+
+#define ORC_PI 3.14159265358979323846
+
+/* min of cos over [a, b], a <= b: -1 if an odd multiple of pi lies in [a, b], else the smaller end value. */
+double oracle_cos_min(double a, double b)
+{
+    const double k = ceil((a / ORC_PI - 1.0) / 2.0); /* smallest k with (2k + 1) pi >= a */
+    if ((2.0 * k + 1.0) * ORC_PI <= b) return -1.0;
+    double ca = cos(a), cb = cos(b);
+    return ca < cb ? ca : cb;
+}
+
+/*
+ * Lower bound of f over each box: the sum over coordinates of the separate
+ * minima of 5 u^2 over [lo, hi] and of cos(50 u) over [50 lo, 50 hi].  Each
+ * term's minimum is exact; a separable objective's bound cannot be tighter than
+ * the sum of its terms' minima under any linear relaxation of the terms.
+ */
+int oracle_synth_bound(int n, int d, const float *lo, const float *hi, double *lb)
+{
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) {
+            double l = lo[(size_t)i * d + j], h = hi[(size_t)i * d + j];
+            s += 5.0 * sq_min(l, h) + oracle_cos_min(50.0 * l, 50.0 * h);
+        }
+        lb[i] = s;
+    }
+    return 0;
+}
+
+/* The search of each box: M uniform samples (oracle_sample), f in FP64, the minimum and its sample (ties: lowest
+   sample index). */
+int oracle_synth_search(int n, int d, const float *lo, const float *hi, const uint64_t *id, int M, uint64_t seed,
+                        double *ub, float *best_u)
+{
+    double *u = (double *)malloc(sizeof(double) * d);
+    float *uf = (float *)malloc(sizeof(float) * d);
+    for (int i = 0; i < n; ++i) {
+        double best = INFINITY;
+        for (int m = 0; m < M; ++m) {
+            for (int j = 0; j < d; ++j) {
+                uf[j] = oracle_sample(seed, id[i], (uint32_t)m, (uint32_t)j, lo[(size_t)i * d + j], hi[(size_t)i * d + j]);
+                u[j] = uf[j];
+            }
+            double f = oracle_synth_f(d, u);
+            if (f < best || m == 0) {
+                best = f;
+                memcpy(best_u + (size_t)i * d, uf, sizeof(float) * d);
+            }
+        }
+        ub[i] = best;
+    }
+    free(u);
+    free(uf);
     return 0;
 }

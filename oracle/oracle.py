@@ -19,6 +19,7 @@ citations are to arXiv 2412.09584 (BaB-ND):
 * ``bab``           Algorithm 2 (search, bound, incumbent, prune, pick, split)
 * ``objective_f32`` Eq. (trajop) in FP32 (the precision the search ranks in)
 * ``cem``           Section 3.3 (batch_search with the cross-entropy method)
+* ``synth_*``       Section 4, synthetic example f(u) = sum 5 u_i^2 + cos(50 u_i)
 """
 from __future__ import annotations
 
@@ -508,3 +509,41 @@ def cem(problem, lo, hi, ids, samples, iters, elites, jitter, seed, warm_u=None,
     if rc != 0:
         raise ValueError("oracle_cem: bad arguments")
     return (ub, bu, tr) if with_trace else (ub, bu)
+
+
+def synth_f(u):
+    """Section 4, synthetic example: f(u) = sum_i 5 u_i^2 + cos(50 u_i) in FP64."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    fn = lib().oracle_synth_f
+    fn.restype = ctypes.c_double
+    return float(fn(int(u.size), u.ctypes.data_as(_c_double_p)))
+
+
+def cos_min(a, b):
+    fn = lib().oracle_cos_min
+    fn.restype = ctypes.c_double
+    fn.argtypes = [ctypes.c_double, ctypes.c_double]
+    return float(fn(a, b))
+
+
+def synth_bound(lo, hi):
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    n, d = lo.shape
+    lb = np.empty(n)
+    lib().oracle_synth_bound(n, d, lo.ctypes.data_as(_c_float_p), hi.ctypes.data_as(_c_float_p),
+                             lb.ctypes.data_as(_c_double_p))
+    return lb
+
+
+def synth_search(lo, hi, ids, samples, seed):
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    n, d = lo.shape
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    ub = np.empty(n)
+    bu = np.empty((n, d), dtype=np.float32)
+    lib().oracle_synth_search(n, d, lo.ctypes.data_as(_c_float_p), hi.ctypes.data_as(_c_float_p),
+                              ids.ctypes.data_as(_c_u64_p), int(samples), ctypes.c_uint64(seed),
+                              ub.ctypes.data_as(_c_double_p), bu.ctypes.data_as(_c_float_p))
+    return ub, bu
