@@ -305,7 +305,9 @@ int bab_alpha_init(bab_ctx *ctx, const float *x0, const float *goal, int horizon
  *      rest of the quota by smallest (lb, id) among the others.
  *   3. Split each picked box on its widest coordinate (lowest index on ties)
  *      at mid = 0.5f * (lo + hi) in FP32: child 2p is the lower half, child
- *      2p + 1 the upper half, ids 2 id and 2 id + 1, lb and ub inherited.
+ *      2p + 1 the upper half, ids 2 id and 2 id + 1 (deeper than 62 splits,
+ *      id >= 2^62: 2^62 + (splitmix64(2 id + c) >> 2), c = 0, 1), lb and ub
+ *      inherited.
  * Output rows: the 2P children (picked boxes in pool order) followed by the R
  * unpicked survivors in pool order.  d_counts (device int[3]) receives
  * {2P, R, 2P + R}: pass d_counts (children) or d_counts + 2 (whole pool) as
@@ -404,6 +406,35 @@ int bab_rollout_cem(bab_ctx *ctx, const float *x0, const float *goal, int horizo
                     const float *hi, const uint64_t *id, int n, const int *d_n, int samples, int iters, int elites,
                     float jitter, uint64_t seed, int precision, const float *warm_u, float *ub, float *best_u,
                     double *inc_val, float *inc_u, void *stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * The paper's synthetic objective (Section 4, synthetic example):
+ * f(u) = sum_i 5 u_i^2 + cos(50 u_i) over boxes of [-1, 1]^d, searched and
+ * bounded for the same prune / pick-out / bisect calls.  It needs no network:
+ * bab_context_create makes a context without one (for these calls and
+ * bab_prune_branch*; the network calls then return BAB_ERR_INVALID_ARG).
+ *
+ * bab_synth_search: per box (lo, hi, id: device [n][d], [n]) `samples` FP32
+ * evaluations of f, uniform (iters = 0; the counter sampler of bab_rollout) or
+ * by the cross-entropy search of bab_rollout_cem (iters >= 1 iterations of
+ * `samples` each, elites, jitter, warm_u nullable); ub[n] the best value and
+ * best_u [n][d] its input (required); inc_val / inc_u (nullable together) the
+ * incumbent, the best row re-evaluated in FP64.
+ *
+ * bab_synth_bound: lb[n], a sound lower bound of f over each box: the sum
+ * over coordinates of the exact minima of 5 u^2 and of cos(50 u) over the
+ * coordinate's interval (no linear relaxation of a separable objective does
+ * better), rounded outward (directed rounding; the cosine's 2-ulp error
+ * covered by 2^-21 per coordinate).
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_CUDA, BAB_ERR_OOM.
+ */
+int bab_context_create(bab_ctx **out);
+int bab_synth_search(bab_ctx *ctx, int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                     int samples, uint64_t seed, int iters, int elites, float jitter, const float *warm_u, float *ub,
+                     float *best_u, double *inc_val, float *inc_u, void *stream);
+int bab_synth_bound(bab_ctx *ctx, int d, const float *lo, const float *hi, int n, const int *d_n, float *lb,
+                    void *stream);
 
 /*
  * Synchronise `stream` and return the sticky device-side status of ctx (0 or

@@ -968,9 +968,21 @@ static int okey_cmp(const void *pa, const void *pb)
  *     half, child 2p + 1 the upper half; ids 2 id and 2 id + 1; both inherit
  *     the parent's lb and ub.
  * Output rows: the 2 P children (picked boxes in pool order), then the R
- * unpicked survivors in pool order.  Returns 0, or -1 if a picked id is too
- * deep to split (id >= 2^63).
+ * unpicked survivors in pool order.  Returns 0.
+ *
+ * Child identifiers (oracle_child_id): 2 id + c (c = 0 lower, 1 upper half)
+ * while id < 2^62, i.e. the binary path from the root box (id 1) through 62
+ * splits; deeper, the path continues as a hash, 2^62 + (splitmix(2 id + c)
+ * >> 2) (taken mod 2^64), so that the search can go arbitrarily deep; two
+ * boxes then share an identifier (and so their samples) with probability
+ * about 2^-62.
  */
+uint64_t oracle_child_id(uint64_t id, int c)
+{
+    if (id < (1ULL << 62)) return 2 * id + (uint64_t)c;
+    return (1ULL << 62) | (oracle_splitmix64(2 * id + (uint64_t)c) >> 2);
+}
+
 /*
  * Natural logarithm of a positive normal FP32 number with basic operations
  * only, each rounded once: x = 2^e m with m in [sqrt(1/2), sqrt(2)), then
@@ -1119,7 +1131,7 @@ static int prune_branch_impl(int n, int d, const float *lo, const float *hi, con
         for (int q = 0; q < n_pick - n1 && q < m; ++q) picked[ks[q].row] = 1;
         free(ks);
     }
-    int P = 0, err = 0;
+    int P = 0;
     for (int q = 0; q < ns; ++q) {
         int i = surv[q];
         if (!picked[i]) continue;
@@ -1139,14 +1151,13 @@ static int prune_branch_impl(int n, int d, const float *lo, const float *hi, con
         }
         volatile float sum = pl[js] + ph[js];
         volatile float mid = 0.5f * sum;
-        if (id[i] >> 63) err = -1;
         for (int c = 0; c < 2; ++c) {
             size_t o = (size_t)(2 * P + c);
             memcpy(out_lo + o * d, pl, sizeof(float) * d);
             memcpy(out_hi + o * d, ph, sizeof(float) * d);
             if (c == 0) out_hi[o * d + js] = mid;
             else out_lo[o * d + js] = mid;
-            out_id[o] = 2 * id[i] + (uint64_t)c;
+            out_id[o] = oracle_child_id(id[i], c);
             out_lb[o] = lb[i];
             out_ub[o] = ub[i];
         }
@@ -1168,7 +1179,7 @@ static int prune_branch_impl(int n, int d, const float *lo, const float *hi, con
     *n_rest = R;
     free(surv);
     free(picked);
-    return err;
+    return 0;
 }
 
 /*

@@ -83,6 +83,10 @@ def load(path: str = LIB_PATH):
     L.bab_rollout_search_bounds.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _P, _P, _P,
                                             _P, _P, _P, _P, _P, _P]
     L.bab_bound_crown_given.argtypes = [_P, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P, _P, _P, _I, _P, _P]
+    L.bab_context_create.argtypes = [ctypes.POINTER(_P)]
+    L.bab_synth_search.argtypes = [_P, _I, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _I, _F, _P, _P, _P, _P, _P,
+                                   _P]
+    L.bab_synth_bound.argtypes = [_P, _I, _P, _P, _I, _P, _P, _P]
     L.bab_rollout_cem.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, _I, _I, _F, ctypes.c_uint64, _I, _P,
                                   _P, _P, _P, _P, _P]
     L.bab_prune_branch_heuristic.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _F, ctypes.c_uint64,
@@ -400,4 +404,32 @@ def bab_rollout_cem(ctx, x0, goal, horizon, rho, lo, hi, ids, n, samples, iters,
                                 int(seed), int(precision), _ptr(warm_u, f32), _ptr(ub, f32, "ub"),
                                 _ptr(best_u, f32, "best_u"), _ptr(inc_val, torch.float64), _ptr(inc_u, f32),
                                 _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_context_create():
+    """A context without a network (the synthetic objective and the prune / branch calls)."""
+    out = _P()
+    rc = load().bab_context_create(ctypes.byref(out))
+    if rc != BAB_OK:
+        raise BabError(rc, "bab_context_create failed")
+    return out.value
+
+
+def bab_synth_search(ctx, d, lo, hi, ids, n, samples, seed, ub, best_u, iters=0, elites=10, jitter=1e-3,
+                     warm_u=None, inc_val=None, inc_u=None, d_n=None, stream=None):
+    """The synthetic objective sum 5 u^2 + cos(50 u) (Section 4): sampled search; see include/bab.h."""
+    f32 = torch.float32
+    rc = load().bab_synth_search(ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), _ptr(ids, torch.uint64, "id"),
+                                 int(n), _ptr(d_n, torch.int32), int(samples), int(seed), int(iters), int(elites),
+                                 float(jitter), _ptr(warm_u, f32), _ptr(ub, f32, "ub"), _ptr(best_u, f32, "best_u"),
+                                 _ptr(inc_val, torch.float64), _ptr(inc_u, f32), _stream(stream))
+    _check(ctx, rc)
+
+
+def bab_synth_bound(ctx, d, lo, hi, n, lb, d_n=None, stream=None):
+    """Sound lower bound of the synthetic objective over each box (Section 4); see include/bab.h."""
+    f32 = torch.float32
+    rc = load().bab_synth_bound(ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), int(n), _ptr(d_n, torch.int32),
+                                _ptr(lb, f32, "lb"), _stream(stream))
     _check(ctx, rc)

@@ -203,6 +203,7 @@ int check_problem(bab_ctx *c, const float *x0, const float *goal, int H, float r
     if (n < 0) return fail(c, BAB_ERR_SHAPE, "n = %d < 0", n);
     if (n > 0 && (!lo || !hi)) return fail(c, BAB_ERR_INVALID_ARG, "lo and hi are required");
     if (!(rho >= 0.f) || !std::isfinite(rho)) return fail(c, BAB_ERR_INVALID_ARG, "rho must be finite and >= 0");
+    if (c->net.L < 1) return fail(c, BAB_ERR_INVALID_ARG, "the context holds no network (bab_context_create)");
     long long d = (long long)c->net.k * H;
     if (d > (1 << 24)) return fail(c, BAB_ERR_SHAPE, "action dimension k*H too large");
     return BAB_OK;
@@ -377,6 +378,93 @@ int bab_load_dynamics_batch(bab_ctx **out, int n_problems, int n_layers, const i
                             int state_dim, int action_dim, unsigned flags)
 {
     return load_impl(out, n_problems, n_layers, dims, params, state_dim, action_dim, flags);
+}
+
+int bab_context_create(bab_ctx **out)
+{
+    if (!out) return BAB_ERR_INVALID_ARG;
+    *out = nullptr;
+    bab_ctx *c = new bab_ctx();
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? BAB_ERR_OOM : BAB_ERR_CUDA;
+    }
+    *out = c;
+    return BAB_OK;
+}
+
+int bab_synth_search(bab_ctx *c, int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                     int samples, uint64_t seed, int iters, int elites, float jitter, const float *warm_u, float *ub,
+                     float *best_u, double *inc_val, float *inc_u, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (d < 1 || d > (1 << 20) || n < 0) return fail(c, BAB_ERR_SHAPE, "bad d or n");
+    if (samples < 1 || samples > BAB_CEM_MAX_SAMPLES) return fail(c, BAB_ERR_SHAPE, "samples must be in [1, 4096]");
+    if (iters < 0 || (iters > 0 && (elites < 1 || elites > samples)))
+        return fail(c, BAB_ERR_INVALID_ARG, "need iters >= 0 and, for the cross-entropy search, 1 <= elites <= samples");
+    if ((long long)(iters > 0 ? iters : 1) * samples >= (1ll << 32)) return fail(c, BAB_ERR_SHAPE, "too many samples");
+    if (iters > 0 && (!(jitter >= 0.f) || !std::isfinite(jitter)))
+        return fail(c, BAB_ERR_INVALID_ARG, "jitter must be finite and >= 0");
+    if (n > 0 && (!lo || !hi || !id || !ub || !best_u)) return fail(c, BAB_ERR_INVALID_ARG, "null array");
+    if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
+    if (n == 0) return BAB_OK;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t kb = al((size_t)n * 8), cb = al((size_t)n * samples * 4), db = al((size_t)n * d * 4);
+    int rc = ensure_scratch(c, iters > 0 ? kb + cb + 2 * db + kb : kb);
+    if (rc) return rc;
+    char *sp = static_cast<char *>(c->scratch);
+    auto *keys = reinterpret_cast<unsigned long long *>(sp);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (iters == 0) {
+        e = launch_synth_search(d, lo, hi, id, n, d_n, samples, 0, seed, nullptr, nullptr, keys, nullptr, ub, best_u, st);
+    } else {
+        CemArgs g{};
+        g.lo = lo;
+        g.hi = hi;
+        g.id = id;
+        g.n = n;
+        g.d_n = d_n;
+        g.d = d;
+        g.M = samples;
+        g.E = elites;
+        g.jitter = jitter;
+        g.seed = seed;
+        g.costs = reinterpret_cast<float *>(sp + kb);
+        g.mu = reinterpret_cast<float *>(sp + kb + cb);
+        g.sigma = reinterpret_cast<float *>(sp + kb + cb + db);
+        g.best = reinterpret_cast<unsigned long long *>(sp + kb + cb + 2 * db);
+        g.ub = ub;
+        g.best_u = best_u;
+        e = launch_cem_init(g, warm_u, st);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            g.it = it;
+            e = launch_synth_search(d, lo, hi, id, n, d_n, samples, it, seed, g.mu, g.sigma, keys,
+                                    const_cast<float *>(g.costs), ub, best_u, st);
+            if (e == cudaSuccess) e = launch_cem_step(g, st);
+        }
+    }
+    if (e == cudaSuccess && inc_val) e = launch_synth_incumbent(d, ub, best_u, n, d_n, inc_val, inc_u, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synthetic-objective search kernels");
+    return BAB_OK;
+}
+
+int bab_synth_bound(bab_ctx *c, int d, const float *lo, const float *hi, int n, const int *d_n, float *lb, void *stream)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (d < 1 || n < 0) return fail(c, BAB_ERR_SHAPE, "bad d or n");
+    if (n > 0 && (!lo || !hi || !lb)) return fail(c, BAB_ERR_INVALID_ARG, "null array");
+    cudaError_t e = launch_synth_bound(d, lo, hi, n, d_n, lb, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synthetic-objective bound kernel");
+    return BAB_OK;
 }
 
 int bab_destroy(bab_ctx *c)

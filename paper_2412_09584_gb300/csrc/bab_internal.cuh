@@ -74,6 +74,15 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 
 __device__ __forceinline__ uint64_t box_hash(uint64_t seed, uint64_t id) { return splitmix64(seed ^ splitmix64(id)); }
 
+// Identifier of child c (0: lower, 1: upper half) of box `id`: 2 id + c while id < 2^62 (the binary path from the
+// root box, id 1, through 62 splits), deeper 2^62 + (splitmix64(2 id + c) >> 2): the path continues as a hash so
+// that the search can go arbitrarily deep (two boxes then share an identifier with probability about 2^-62).
+__device__ __forceinline__ uint64_t child_id(uint64_t id, int c)
+{
+    if (id < (1ull << 62)) return 2 * id + (uint64_t)c;
+    return (1ull << 62) | (splitmix64(2 * id + (uint64_t)c) >> 2);
+}
+
 // u = lo + (hi - lo) * r in FP32, one rounding per operation (no contraction).
 __device__ __forceinline__ float draw_sample(uint64_t hbox, uint32_t m, uint32_t j, float lo, float hi)
 {

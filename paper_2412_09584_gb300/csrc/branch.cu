@@ -251,9 +251,8 @@ __global__ void k_branch_write(BranchArgs a)
             a.out_row_u[(o0 + 1) * d + j] = v;
         }
     if (lane == 0) {
-        if (id >> 63) set_status(a.status, BAB_ERR_SHAPE);
-        a.out_id[o0] = 2 * id;
-        a.out_id[o0 + 1] = 2 * id + 1;
+        a.out_id[o0] = child_id(id, 0);
+        a.out_id[o0 + 1] = child_id(id, 1);
         a.out_lb[o0] = a.out_lb[o0 + 1] = a.lb[row];
         a.out_ub[o0] = a.out_ub[o0 + 1] = a.ub[row];
     }

@@ -224,6 +224,15 @@ __device__ __forceinline__ void dense_rows_auto(const float *in, int ldi, const 
 cudaError_t launch_rollout_fp32(const RolloutArgs &a, int variant, int num_sms, cudaStream_t st);
 int rollout_fp32_variants();
 cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_sms, cudaStream_t st);
+// the synthetic objective sum 5 u^2 + cos(50 u): sampled search (uniform, or the cross-entropy mode with
+// cem_mu / cem_sigma and costs), sound interval bound, FP64 incumbent
+cudaError_t launch_synth_search(int d, const float *lo, const float *hi, const uint64_t *id, int n, const int *d_n,
+                                int M, int it, uint64_t seed, const float *cem_mu, const float *cem_sigma,
+                                unsigned long long *keys, float *costs, float *ub, float *best_u, cudaStream_t st);
+cudaError_t launch_synth_bound(int d, const float *lo, const float *hi, int n, const int *d_n, float *lb,
+                               cudaStream_t st);
+cudaError_t launch_synth_incumbent(int d, const float *ub, const float *best_u, int n, const int *d_n,
+                                   double *inc_val, float *inc_u, cudaStream_t st);
 // cross-entropy search: start (mu, sigma, best) and one refit
 cudaError_t launch_cem_init(const CemArgs &c, const float *warm_u, cudaStream_t st);
 cudaError_t launch_cem_step(const CemArgs &c, cudaStream_t st);

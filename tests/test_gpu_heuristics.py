@@ -123,3 +123,16 @@ def test_rollout_split_costs_and_choice(oracle, gp):
         want = int(np.argmax(scores)) if scores.max() > 0 else int(np.argmax(hi[i] - lo[i]))
         assert sd[i] == want
     assert np.array_equal(ub.cpu().numpy().view(np.uint32), c.min(axis=1).view(np.uint32))
+
+
+def test_deep_identifiers_bit_exact(oracle, gp):
+    """Boxes deeper than 62 splits: the children's identifiers continue as a hash of the path, as in the oracle."""
+    lo, hi, _ = W.dyadic_boxes(10, 60, seed=11, max_depth=4)
+    rng = np.random.default_rng(12)
+    ids = np.concatenate([rng.integers(1 << 62, (1 << 63) - 1, size=30, dtype=np.int64).astype(np.uint64),
+                          np.arange(1, 31, dtype=np.uint64) + np.uint64((1 << 62) - 31)])
+    lb, ub = W.pool_values(60, seed=13)
+    r = _branch(gp, lo, hi, lb, ub, ids, 12.0, 40, 0, 1.0, 0)
+    o = oracle.prune_branch_heuristic(lo, hi, lb, ub, ids, 12.0, 40, pick_rule=0)
+    _same(r, o)
+    assert np.any(r["id"] >= np.uint64(1 << 62))

@@ -489,10 +489,17 @@ def test_prune_branch_edge_cases(oracle):
     r = oracle.prune_branch(lo, hi, np.array([5, 6], np.float32), np.array([7, 8], np.float32),
                             np.array([2, 3], np.uint64), 1.0, n_pick=4)
     assert list(r["keep"]) == [0, 0] and r["n_children"] == 0 and r["n_rest"] == 0
-    # too deep to split
+    # deeper than 62 splits the identifier continues as a hash of the path: 2^62 + (splitmix(2 id + c) >> 2)
+    for deep in (1 << 62, (1 << 63) - 1, (1 << 63) + 5):
+        r = oracle.prune_branch(lo[:1], hi[:1], np.array([0], np.float32), np.array([1], np.float32),
+                                np.array([deep], np.uint64), 1.0, n_pick=4)
+        assert r["rc"] == 0 and r["n_children"] == 2
+        want = [(1 << 62) | (oracle.lib().oracle_splitmix64((2 * deep + c) % (1 << 64)) >> 2) for c in (0, 1)]
+        assert [int(v) for v in r["id"]] == want
+        assert all((1 << 62) <= v < (1 << 63) for v in want) and want[0] != want[1]
     r = oracle.prune_branch(lo[:1], hi[:1], np.array([0], np.float32), np.array([1], np.float32),
-                            np.array([1 << 63], np.uint64), 1.0, n_pick=4)
-    assert r["rc"] == -1
+                            np.array([(1 << 62) - 1], np.uint64), 1.0, n_pick=4)
+    assert [int(v) for v in r["id"]] == [(1 << 63) - 2, (1 << 63) - 1]
 
 
 def test_grid_boxes_match_repeated_bisection(oracle):
