@@ -405,6 +405,7 @@ def run_ours(args):
     paper_bounds = None if args.no_time_to_gap else paper_bounding_comparison(dev)
     heuristics = None if args.no_time_to_gap else heuristics_comparison(dev)
     cem_cmp = None if args.no_time_to_gap else cem_comparison(dev)
+    synth = None if args.no_time_to_gap else synthetic_sweep(dev)
 
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
@@ -448,7 +449,8 @@ def run_ours(args):
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
            "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
-           "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp}
+           "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp,
+           "synthetic_objective": synth}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -784,6 +786,81 @@ def cem_comparison(dev, iters=30):
                          "incumbent_every_5": [round(v, 6) for v in inc[4::5]],
                          "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters}
         out[wl] = res
+    return out
+
+
+SYNTH_G_STAR = -0.98033911  # per-coordinate minimum of 5 u^2 + cos(50 u) (the oracle pins it to 1e-6)
+
+
+def synthetic_bab(dev, d=100, iters=1000, n_pick=512, samples=256, cem_iters=0, levels=10, eta=0.75):
+    """Algorithm 2 on the paper's synthetic objective (Section 4): f(u) = sum 5 u_i^2 + cos(50 u_i) over
+    [-1, 1]^d, d = 100.  Search: `samples` uniform draws per child, or the cross-entropy search (cem_iters
+    iterations of samples / cem_iters, 10 elites, each child warm-started from its parent's best input); bound:
+    the sound per-term interval minima; prune / pick-out / widest-dimension bisection on the device.  Reports the
+    incumbent against f* = d g*, the certified gap and the coordinates in the global basin."""
+    import torch
+    from paper_2412_09584_gb300 import binding as B
+    from paper_2412_09584_gb300 import workloads as W
+    ctx = B.bab_context_create()
+    f = dict(device=dev, dtype=torch.float32)
+    lo, hi, ids = W.grid_boxes(d, levels)
+    n0 = lo.shape[0]
+    cap = n0 + (iters + 2) * n_pick
+    pools = [{"lo": torch.empty(cap, d, **f), "hi": torch.empty(cap, d, **f), "lb": torch.empty(cap, **f),
+              "ub": torch.empty(cap, **f), "id": torch.empty(cap, dtype=torch.int64, device=dev),
+              "bu": torch.empty(cap, d, **f)} for _ in range(2)]
+    P = pools[0]
+    P["lo"][:n0] = torch.as_tensor(lo).to(**f)
+    P["hi"][:n0] = torch.as_tensor(hi).to(**f)
+    P["id"][:n0] = torch.as_tensor(ids.astype(np.int64)).to(dev)
+    iv = torch.full((1,), float("inf"), dtype=torch.float64, device=dev)
+    iu = torch.zeros(d, **f)
+    keep = torch.empty(cap, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(3, dtype=torch.int32, device=dev)
+    live = torch.tensor([n0], dtype=torch.int32, device=dev)
+    m_it = samples // cem_iters if cem_iters else samples
+
+    def search(Q, n, d_n, seed, warm):
+        B.bab_synth_search(ctx, d, Q["lo"], Q["hi"], Q["id"], n, m_it, seed, Q["ub"], Q["bu"], iters=cem_iters,
+                           elites=10, jitter=1e-3, warm_u=warm, inc_val=iv, inc_u=iu, d_n=d_n)
+        B.bab_synth_bound(ctx, d, Q["lo"], Q["hi"], n, Q["lb"], d_n=d_n)
+
+    search(P, n0, None, 1, None)
+    cur, nmax = 0, n0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(iters):
+        src, dst = pools[cur], pools[cur ^ 1]
+        B.bab_prune_branch_heuristic(ctx, d, src["lo"], src["hi"], src["lb"], src["ub"], src["id"], nmax, iv,
+                                     n_pick, eta, B.PICK_LB, 1.0, 0, cap, dst["lo"], dst["hi"], dst["lb"],
+                                     dst["ub"], dst["id"], keep, counts, row_u=src["bu"], out_row_u=dst["bu"],
+                                     d_n=live)
+        nmax = min(nmax + n_pick, cap - n_pick)
+        search(dst, 2 * n_pick, counts[0:1], 2 + it, dst["bu"] if cem_iters else None)
+        live.copy_(counts[2:3])
+        cur ^= 1
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nl = int(counts[2].item())
+    lbmin = float(pools[cur]["lb"][:nl].min().item()) if nl else float("inf")
+    inc = float(iv.item())
+    u = iu.cpu().numpy().astype(np.float64)
+    g = 5 * u * u + np.cos(50 * u)
+    status = B.bab_status(ctx)
+    B.bab_destroy(ctx)
+    return {"d": d, "f_star": d * SYNTH_G_STAR, "incumbent": inc, "gap_to_f_star": inc - d * SYNTH_G_STAR,
+            "certified_gap": inc - min(lbmin, inc), "coordinates_in_global_basin": int((g < SYNTH_G_STAR + 0.05).sum()),
+            "iterations": iters, "children_per_iteration": 2 * n_pick, "eta": eta,
+            "search": f"cross-entropy {cem_iters} x {m_it}, warm-started" if cem_iters else f"{samples} uniform",
+            "live_pool_end": nl, "ms_per_iteration": 1e3 * sec / iters, "status": status}
+
+
+def synthetic_sweep(dev):
+    """The synthetic objective at d = 10, 30 and 100 (the paper's figure spans d <= 100): warm-started
+    cross-entropy search (4 x 64 per child), eta = 0.25, 1024 children per iteration."""
+    out = {}
+    for d, iters in ((10, 300), (30, 600), (100, 1000)):
+        out[f"d{d}"] = synthetic_bab(dev, d=d, iters=iters, cem_iters=4, eta=0.25, levels=min(10, d))
     return out
 
 

@@ -80,7 +80,7 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 // image; per slot a producer warp streams it, one K-atom (64 inputs of one
 // layer, hi and lo halves) at a time, through the slot's ring of a.stages
 // buffers in the order the slot's MMA issuer consumes them.
-template <int NSLOT, int SPLIT, int SX, bool STREAM>
+template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM>
 __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                     const int jj = t * k + j;
                     if (j >= k) {
                         u[j] = 0.f;
-                    } else if (a.cem_mu) {
+                    } else if (CEM) {
                         const size_t e = (size_t)box * a.d + jj;
                         u[j] = cem_sample(hb, (uint32_t)a.cem_it, (uint32_t)m, (uint32_t)jj, __ldg(a.cem_mu + e),
                                           __ldg(a.cem_sigma + e), __ldg(blo + jj), __ldg(bhi + jj));
@@ -568,10 +568,10 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
 }
 
-template <int NSLOT, int SPLIT, int SX, bool STREAM>
+template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM>
 static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = k_rollout_tc<NSLOT, SPLIT, SX, STREAM>;
+    auto kern = k_rollout_tc<NSLOT, SPLIT, SX, STREAM, CEM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, (NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, smem, st>>>(a);
@@ -607,15 +607,16 @@ bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
            2 * rollout_tc_stage(N, split) + rollout_tc_extra(N) + 1024 <= (size_t)max_smem;
 }
 
-template <int SPLIT, int SX>
+// CEM: the cross-entropy sampling mode (a separate instance, so that the uniform kernel carries none of its code)
+template <int SPLIT, int SX, bool CEM>
 static cudaError_t launch_tc_shape(const RolloutArgs &a, int nslot, bool stream, int grid, size_t smem,
                                    cudaStream_t st)
 {
     if (stream)
-        return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, true>(a, grid, smem, st)
-                          : launch_tc_variant<1, SPLIT, SX, true>(a, grid, smem, st);
-    return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, false>(a, grid, smem, st)
-                      : launch_tc_variant<1, SPLIT, SX, false>(a, grid, smem, st);
+        return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, true, CEM>(a, grid, smem, st)
+                          : launch_tc_variant<1, SPLIT, SX, true, CEM>(a, grid, smem, st);
+    return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, false, CEM>(a, grid, smem, st)
+                      : launch_tc_variant<1, SPLIT, SX, false, CEM>(a, grid, smem, st);
 }
 
 // nslot_pref: tiles per CTA (1 or 2), or -1 for two whenever both fit in tensor memory
@@ -664,12 +665,22 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     k_fill_keys(a.keys, a.n, st);
     cudaError_t e;
     // state registers: 8, 16 or 32 (the output layer is 16 wide up to 16 states, else 32)
-    if (N.s <= 8) e = split == 3 ? launch_tc_shape<3, 8>(a, nslot, stream, grid, smem, st)
-                                 : launch_tc_shape<1, 8>(a, nslot, stream, grid, smem, st);
-    else if (N.s <= 16) e = split == 3 ? launch_tc_shape<3, 16>(a, nslot, stream, grid, smem, st)
-                                       : launch_tc_shape<1, 16>(a, nslot, stream, grid, smem, st);
-    else e = split == 3 ? launch_tc_shape<3, 32>(a, nslot, stream, grid, smem, st)
-                        : launch_tc_shape<1, 32>(a, nslot, stream, grid, smem, st);
+    if (a.cem_mu) {
+        // the cross-entropy search runs the 3-term split only
+        if (split != 3) return cudaErrorInvalidValue;
+        if (N.s <= 8) e = launch_tc_shape<3, 8, true>(a, nslot, stream, grid, smem, st);
+        else if (N.s <= 16) e = launch_tc_shape<3, 16, true>(a, nslot, stream, grid, smem, st);
+        else e = launch_tc_shape<3, 32, true>(a, nslot, stream, grid, smem, st);
+    } else if (N.s <= 8) {
+        e = split == 3 ? launch_tc_shape<3, 8, false>(a, nslot, stream, grid, smem, st)
+                       : launch_tc_shape<1, 8, false>(a, nslot, stream, grid, smem, st);
+    } else if (N.s <= 16) {
+        e = split == 3 ? launch_tc_shape<3, 16, false>(a, nslot, stream, grid, smem, st)
+                       : launch_tc_shape<1, 16, false>(a, nslot, stream, grid, smem, st);
+    } else {
+        e = split == 3 ? launch_tc_shape<3, 32, false>(a, nslot, stream, grid, smem, st)
+                       : launch_tc_shape<1, 32, false>(a, nslot, stream, grid, smem, st);
+    }
     if (e != cudaSuccess) return e;
     if (a.cem_mu) return cudaGetLastError();  // the cross-entropy search keeps its own best (launch_cem_step)
     launch_rollout_finalize(a, st);  // ub and best_u from the packed minima
