@@ -111,6 +111,147 @@ int oracle_sumh(int L, const int *dims)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Task costs (Appendix D.4)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The state cost c(x_t) of Eq. (trajop), t = 1..H.  Kind 0 (default):
+ * ||x_t - g||^2.  Kind 1, the pushing-with-obstacles cost of Appendix D.4
+ * (Eq. pushing_cost): w_t ||x_t - g|| + lambda sum_o [ReLU(s_o - ||p_t - p_o||)
+ * + sum_i ReLU(s_o - ||x_t^(i) - p_o||)], where the state holds s / 2 planar
+ * keypoints x_t^(i) = (x_{t,2i}, x_{t,2i+1}), the action is the planar pusher
+ * motion (k = 2) and p_t = p_0 + u_0 + ... + u_{t-1} is the pusher position
+ * after t moves.  Both kinds add rho ||u_t||^2.  oracle_set_cost selects it
+ * for every function of this file.
+ */
+#define ORC_MAX_OBS 8
+#define ORC_MAX_H 4096
+
+typedef struct {
+    int kind;
+    int H;
+    double w[ORC_MAX_H + 1]; /* w[t], t = 1..H */
+    double lambda;
+    int n_obs;
+    double ox[ORC_MAX_OBS], oy[ORC_MAX_OBS], os[ORC_MAX_OBS];
+    double p0[2];
+} ocost_t;
+
+static ocost_t g_cost;
+
+/* kind 0: squared distance; kind 1: w [H] (w_1..w_H), lambda, obstacles [n_obs][3] (x, y, size), p0 [2]. */
+int oracle_set_cost(int kind, int H, const double *w, double lambda, int n_obs, const double *obs, const double *p0)
+{
+    memset(&g_cost, 0, sizeof(g_cost));
+    if (kind == 0) return 0;
+    if (kind != 1 || H < 1 || H > ORC_MAX_H || n_obs < 0 || n_obs > ORC_MAX_OBS) return -1;
+    g_cost.kind = 1;
+    g_cost.H = H;
+    for (int t = 1; t <= H; ++t) g_cost.w[t] = w[t - 1];
+    g_cost.lambda = lambda;
+    g_cost.n_obs = n_obs;
+    for (int o = 0; o < n_obs; ++o) {
+        g_cost.ox[o] = obs[3 * o];
+        g_cost.oy[o] = obs[3 * o + 1];
+        g_cost.os[o] = obs[3 * o + 2];
+    }
+    g_cost.p0[0] = p0[0];
+    g_cost.p0[1] = p0[1];
+    return 0;
+}
+
+static double sq_min(double lo, double hi);
+static double relu_d(double v) { return v > 0.0 ? v : 0.0; }
+
+/* the state cost at step t (1..H) of state x with pusher position p */
+static double state_cost(int t, int s, const double *x, const double *goal, const double *p)
+{
+    double c = 0.0;
+    if (g_cost.kind == 0) {
+        for (int i = 0; i < s; ++i) c += (x[i] - goal[i]) * (x[i] - goal[i]);
+        return c;
+    }
+    double ss = 0.0;
+    for (int i = 0; i < s; ++i) ss += (x[i] - goal[i]) * (x[i] - goal[i]);
+    c = g_cost.w[t] * sqrt(ss);
+    for (int o = 0; o < g_cost.n_obs; ++o) {
+        c += g_cost.lambda * relu_d(g_cost.os[o] - hypot(p[0] - g_cost.ox[o], p[1] - g_cost.oy[o]));
+        for (int i = 0; 2 * i + 1 < s; ++i)
+            c += g_cost.lambda * relu_d(g_cost.os[o] - hypot(x[2 * i] - g_cost.ox[o], x[2 * i + 1] - g_cost.oy[o]));
+    }
+    return c;
+}
+
+/* the largest distance from (px, py) to the box [l0, u0] x [l1, u1] (at a vertex) */
+static double max_dist(double l0, double u0, double l1, double u1, double px, double py)
+{
+    double a = fmax(fabs(l0 - px), fabs(u0 - px)), b = fmax(fabs(l1 - py), fabs(u1 - py));
+    return hypot(a, b);
+}
+
+/* min over the box x in [xl, xu], p in [pl, pu] of the state cost at step t (each term on its own) */
+static double state_cost_min(int t, int s, const double *xl, const double *xu, const double *goal, const double *pl,
+                             const double *pu)
+{
+    double c = 0.0;
+    if (g_cost.kind == 0) {
+        for (int i = 0; i < s; ++i) c += sq_min(xl[i] - goal[i], xu[i] - goal[i]);
+        return c;
+    }
+    double ss = 0.0; /* squared distance from g to the box */
+    for (int i = 0; i < s; ++i) {
+        double e = goal[i] < xl[i] ? xl[i] - goal[i] : (goal[i] > xu[i] ? goal[i] - xu[i] : 0.0);
+        ss += e * e;
+    }
+    c = g_cost.w[t] * sqrt(ss);
+    for (int o = 0; o < g_cost.n_obs; ++o) {
+        c += g_cost.lambda * relu_d(g_cost.os[o] - max_dist(pl[0], pu[0], pl[1], pu[1], g_cost.ox[o], g_cost.oy[o]));
+        for (int i = 0; 2 * i + 1 < s; ++i)
+            c += g_cost.lambda *
+                 relu_d(g_cost.os[o] - max_dist(xl[2 * i], xu[2 * i], xl[2 * i + 1], xu[2 * i + 1], g_cost.ox[o], g_cost.oy[o]));
+    }
+    return c;
+}
+
+/*
+ * A linear lower bound a . q + b of ReLU(size - ||q - c||) over the box
+ * [l0, u0] x [l1, u1]: h(q) = size - ||q - c|| is concave, so any affine
+ * function below h at the four vertices is below h on the box; a is the
+ * gradient of h at the box centre (0 if the centre is c) and b the largest
+ * offset that keeps a . v + b <= h(v) at every vertex.  ReLU(h) >= h >= a . q + b
+ * and ReLU(h) >= 0: the affine bound is used where it is positive at the box
+ * centre (returns 1), else the bound 0 (returns 0, a = b = 0).
+ */
+int oracle_relu_dist_lower(double l0, double u0, double l1, double u1, double cx, double cy, double size,
+                           double *a0, double *a1, double *b);
+static int relu_dist_lower(double l0, double u0, double l1, double u1, double cx, double cy, double size, double *a0,
+                           double *a1, double *b)
+{
+    return oracle_relu_dist_lower(l0, u0, l1, u1, cx, cy, size, a0, a1, b);
+}
+int oracle_relu_dist_lower(double l0, double u0, double l1, double u1, double cx, double cy, double size,
+                           double *a0, double *a1, double *b)
+{
+    double mx = 0.5 * (l0 + u0), my = 0.5 * (l1 + u1);
+    double dx = mx - cx, dy = my - cy, nd = hypot(dx, dy);
+    double g0 = nd > 0.0 ? -dx / nd : 0.0, g1 = nd > 0.0 ? -dy / nd : 0.0;
+    double vx[4] = {l0, u0, l0, u0}, vy[4] = {l1, l1, u1, u1};
+    double bb = INFINITY;
+    for (int v = 0; v < 4; ++v) {
+        double off = size - hypot(vx[v] - cx, vy[v] - cy) - (g0 * vx[v] + g1 * vy[v]);
+        if (off < bb) bb = off;
+    }
+    if (g0 * mx + g1 * my + bb > 0.0) {
+        *a0 = g0;
+        *a1 = g1;
+        *b = bb;
+        return 1;
+    }
+    *a0 = *a1 = *b = 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Objective (Section 3, Eq. trajop)                                          */
 /* ------------------------------------------------------------------------ */
 
@@ -141,7 +282,8 @@ static void step_forward(const onet *N, const double *x, const double *u, double
 }
 
 /*
- * f(u) = sum_{t=1..H} ||x_t - goal||^2 + rho * sum_{t=0..H-1} ||u_t||^2.
+ * f(u) = sum_{t=1..H} c(x_t) + rho * sum_{t=0..H-1} ||u_t||^2, c the state
+ * cost (||x_t - goal||^2 unless oracle_set_cost chose another).
  * traj (nullable) receives x_0..x_H ([H+1][s]); pre (nullable) the hidden
  * pre-activations of every step ([H][sumh]).
  */
@@ -154,15 +296,17 @@ double oracle_objective(int L, const int *dims, const double *params, int s, int
     for (int i = 0; i < s; ++i) x[i] = x0[i];
     if (traj) memcpy(traj, x0, sizeof(double) * s);
     double f = 0.0;
+    double p[2] = {g_cost.p0[0], g_cost.p0[1]};
     for (int t = 0; t < H; ++t) {
         const double *ut = u + (size_t)t * k;
         step_forward(&N, x, ut, xn, pre ? pre + (size_t)t * N.sumh : NULL);
         for (int j = 0; j < k; ++j) f += rho * ut[j] * ut[j];
-        for (int i = 0; i < s; ++i) {
-            double e = xn[i] - goal[i];
-            f += e * e;
-            x[i] = xn[i];
+        if (g_cost.kind == 1) {
+            p[0] += ut[0];
+            p[1] += ut[1];
         }
+        f += state_cost(t + 1, s, xn, goal, p);
+        for (int i = 0; i < s; ++i) x[i] = xn[i];
         if (traj) memcpy(traj + (size_t)(t + 1) * s, x, sizeof(double) * s);
     }
     return f;
@@ -270,7 +414,14 @@ static double ibp_box(const onet *N, int H, double rho, const double *x0, const 
     for (int i = 0; i < s; ++i) xl[i] = xu[i] = x0[i];
     if (x_lo) for (int i = 0; i < s; ++i) x_lo[i] = x_hi[i] = x0[i];
     double lb = 0.0;
+    double pl[2] = {g_cost.p0[0], g_cost.p0[1]}, pu[2] = {g_cost.p0[0], g_cost.p0[1]}; /* pusher position box */
     for (int t = 0; t < H; ++t) {
+        if (g_cost.kind == 1) {
+            for (int j = 0; j < 2; ++j) {
+                pl[j] += lo[t * k + j];
+                pu[j] += hi[t * k + j];
+            }
+        }
         for (int i = 0; i < s; ++i) {
             c[i] = 0.5 * (xl[i] + xu[i]);
             r[i] = 0.5 * (xu[i] - xl[i]);
@@ -313,8 +464,8 @@ static double ibp_box(const onet *N, int H, double rho, const double *x0, const 
         for (int i = 0; i < s; ++i) {
             xl[i] += zl[i];
             xu[i] += zu[i];
-            lb += sq_min(xl[i] - goal[i], xu[i] - goal[i]);
         }
+        lb += state_cost_min(t + 1, s, xl, xu, goal, pl, pu);
         if (x_lo) {
             for (int i = 0; i < s; ++i) {
                 x_lo[(size_t)(t + 1) * s + i] = xl[i];
@@ -433,23 +584,73 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
     double cst = 0.0, cabs = 0.0;
     double *mu_loc = (double *)calloc((size_t)k * H, sizeof(double));
 
-    /* tangent coefficients a_{t,i} = 2 m and constants -2 m g - m^2 for the cost terms the backward pass
-       carries (t > t_stop); the terms at or before the early-stop step are bounded on their intervals */
+    /* linear lower bounds a_t . x_t + const of the state cost at the steps the backward pass carries
+       (t > t_stop); the terms at or before the early-stop step are bounded on their intervals.  Squared
+       distance: the tangent of s^2 at the midpoint m of the interval of s = x_{t,i} - g_i, a = 2 m, constant
+       -2 m g - m^2.  Pushing with obstacles: w ||x - g|| >= w ghat . (x - g) with ghat = m / ||m|| (Cauchy-
+       Schwarz; 0 if m = 0), and each obstacle term by relu_dist_lower on its box; the pusher terms are linear in
+       p_t = p_0 + u_0 + ... + u_{t-1} and so add coefficients bp_t to every earlier action. */
     double *a = (double *)calloc((size_t)(H + 1) * s, sizeof(double));
+    double *mu_extra = (double *)calloc((size_t)k * H, sizeof(double));
+    double pl[2] = {g_cost.p0[0], g_cost.p0[1]}, pu[2] = {g_cost.p0[0], g_cost.p0[1]};
     for (int t = 1; t <= H; ++t) {
-        for (int i = 0; i < s; ++i) {
-            double Ls = x_lo[(size_t)t * s + i] - goal[i];
-            double Us = x_hi[(size_t)t * s + i] - goal[i];
-            if (t <= t_stop) {
-                double v = sq_min(Ls, Us);
-                cst += v;
-                cabs += v;
-                continue;
+        const double *xl_t = x_lo + (size_t)t * s, *xu_t = x_hi + (size_t)t * s;
+        if (g_cost.kind == 1) {
+            for (int j = 0; j < 2; ++j) {
+                pl[j] += lo[(t - 1) * k + j];
+                pu[j] += hi[(t - 1) * k + j];
             }
-            double m = 0.5 * (Ls + Us);
-            a[(size_t)t * s + i] = 2.0 * m;
-            cst += -2.0 * m * goal[i] - m * m;
-            cabs += fabs(2.0 * m * goal[i]) + m * m;
+        }
+        if (t <= t_stop) {
+            double v = state_cost_min(t, s, xl_t, xu_t, goal, pl, pu);
+            cst += v;
+            cabs += fabs(v);
+            continue;
+        }
+        if (g_cost.kind == 0) {
+            for (int i = 0; i < s; ++i) {
+                double Ls = xl_t[i] - goal[i], Us = xu_t[i] - goal[i];
+                double m = 0.5 * (Ls + Us);
+                a[(size_t)t * s + i] = 2.0 * m;
+                cst += -2.0 * m * goal[i] - m * m;
+                cabs += fabs(2.0 * m * goal[i]) + m * m;
+            }
+            continue;
+        }
+        double m[ORC_MAX_WIDTH], nm = 0.0;
+        for (int i = 0; i < s; ++i) {
+            m[i] = 0.5 * (xl_t[i] + xu_t[i]) - goal[i];
+            nm += m[i] * m[i];
+        }
+        nm = sqrt(nm);
+        if (nm > 0.0) {
+            for (int i = 0; i < s; ++i) {
+                double gi = g_cost.w[t] * m[i] / nm;
+                a[(size_t)t * s + i] += gi;
+                cst -= gi * goal[i];
+                cabs += fabs(gi * goal[i]);
+            }
+        }
+        for (int o = 0; o < g_cost.n_obs; ++o) {
+            double a0, a1, b, lam_ = g_cost.lambda;
+            if (relu_dist_lower(pl[0], pu[0], pl[1], pu[1], g_cost.ox[o], g_cost.oy[o], g_cost.os[o], &a0, &a1, &b)) {
+                /* lam (a . p_t + b) = lam (a . p_0 + b) + lam a . (u_0 + ... + u_{t-1}) */
+                for (int tau = 0; tau < t; ++tau) {
+                    mu_extra[tau * k] += lam_ * a0;
+                    mu_extra[tau * k + 1] += lam_ * a1;
+                }
+                cst += lam_ * (a0 * g_cost.p0[0] + a1 * g_cost.p0[1] + b);
+                cabs += fabs(lam_ * (a0 * g_cost.p0[0] + a1 * g_cost.p0[1] + b));
+            }
+            for (int i = 0; 2 * i + 1 < s; ++i) {
+                if (relu_dist_lower(xl_t[2 * i], xu_t[2 * i], xl_t[2 * i + 1], xu_t[2 * i + 1], g_cost.ox[o],
+                                    g_cost.oy[o], g_cost.os[o], &a0, &a1, &b)) {
+                    a[(size_t)t * s + 2 * i] += lam_ * a0;
+                    a[(size_t)t * s + 2 * i + 1] += lam_ * a1;
+                    cst += lam_ * b;
+                    cabs += fabs(lam_ * b);
+                }
+            }
         }
     }
     for (int i = 0; i < s; ++i) lam[i] = a[(size_t)H * s + i];
@@ -512,6 +713,7 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
         }
     }
 
+    for (int j = 0; j < k * H; ++j) mu_loc[j] += mu_extra[j];
     double lb = cst;
     for (int j = 0; j < k * H; ++j) {
         double arg;
@@ -523,6 +725,7 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
     }
     if (atan) memcpy(atan, a, sizeof(double) * (size_t)(H + 1) * s);
     free(a);
+    free(mu_extra);
     free(mu_loc);
     crown_out o = {lb, cst, cabs};
     return o;
@@ -1264,7 +1467,13 @@ int oracle_split_dims(int n, int d, const float *lo, const float *hi, const uint
  * c = 0, 1, ... by fused multiply-adds; ReLU; x_{t+1} = x_t + N([x_t; u_t]); the
  * step cost starts from 0, adds (x_{t+1,i} - g_i)^2 for i = 0..s-1 and then
  * (rho u_{t,j}) u_{t,j} for j = 0..k-1 by fused multiply-adds, and is added to
- * the running total.
+ * the running total.  For the pushing-with-obstacles cost the state part of
+ * the step cost is w_t sqrt(sum_i (x_{t+1,i} - g_i)^2) (the squares summed by
+ * fused multiply-adds, then one rounded product), followed, per obstacle o in
+ * order, by lambda ReLU(s_o - d) for the pusher and then for each keypoint in
+ * order (d = sqrt(dx dx + dy dy), dy dy rounded first; each added by a fused
+ * multiply-add), the pusher position advancing by one rounded addition per
+ * coordinate and step; the action terms follow as above.
  */
 float oracle_objective_f32(int L, const int *dims, const double *params, int s, int k, int H, float rho,
                            const float *x0, const float *goal, const float *u)
@@ -1273,6 +1482,7 @@ float oracle_objective_f32(int L, const int *dims, const double *params, int s, 
     if (onet_init(&N, L, dims, params, s, k)) return NAN;
     float a[ORC_MAX_WIDTH], b[ORC_MAX_WIDTH], x[ORC_MAX_WIDTH];
     for (int i = 0; i < s; ++i) x[i] = x0[i];
+    float pf[2] = {(float)g_cost.p0[0], (float)g_cost.p0[1]};
     float total = 0.0f;
     for (int t = 0; t < H; ++t) {
         for (int i = 0; i < s; ++i) a[i] = x[i];
@@ -1289,11 +1499,39 @@ float oracle_objective_f32(int L, const int *dims, const double *params, int s, 
             out = tmp;
         }
         float c = 0.0f;
-        for (int i = 0; i < s; ++i) {
-            volatile float xn = x[i] + in[i];
-            x[i] = xn;
-            volatile float e = xn - goal[i];
-            c = fmaf(e, e, c);
+        if (g_cost.kind == 0) {
+            for (int i = 0; i < s; ++i) {
+                volatile float xn = x[i] + in[i];
+                x[i] = xn;
+                volatile float e = xn - goal[i];
+                c = fmaf(e, e, c);
+            }
+        } else {
+            for (int j = 0; j < 2; ++j) {
+                volatile float pj = pf[j] + u[t * k + j];
+                pf[j] = pj;
+            }
+            float ss = 0.0f;
+            for (int i = 0; i < s; ++i) {
+                volatile float xn = x[i] + in[i];
+                x[i] = xn;
+                volatile float e = xn - goal[i];
+                ss = fmaf(e, e, ss);
+            }
+            volatile float wn = (float)g_cost.w[t + 1] * sqrtf(ss);
+            c = wn;
+            const float lamf = (float)g_cost.lambda;
+            for (int o = 0; o < g_cost.n_obs; ++o) {
+                const float ox = (float)g_cost.ox[o], oy = (float)g_cost.oy[o], osz = (float)g_cost.os[o];
+                for (int q = -1; 2 * q + 1 < s; ++q) {
+                    volatile float dx = (q < 0 ? pf[0] : x[2 * q]) - ox;
+                    volatile float dy = (q < 0 ? pf[1] : x[2 * q + 1]) - oy;
+                    volatile float dy2 = dy * dy;
+                    float dd = fmaf(dx, dx, dy2);
+                    volatile float r = osz - sqrtf(dd);
+                    c = fmaf(lamf, r > 0.0f ? r : 0.0f, c);
+                }
+            }
         }
         for (int j = 0; j < k; ++j) {
             volatile float ru = rho * u[t * k + j];

@@ -547,3 +547,27 @@ def synth_search(lo, hi, ids, samples, seed):
                               ids.ctypes.data_as(_c_u64_p), int(samples), ctypes.c_uint64(seed),
                               ub.ctypes.data_as(_c_double_p), bu.ctypes.data_as(_c_float_p))
     return ub, bu
+
+
+def set_cost(kind=0, w=None, lam=0.0, obstacles=(), p0=(0.0, 0.0)):
+    """Select the state cost of every oracle function (Appendix D.4): kind 0 the squared distance, kind 1 the
+    pushing-with-obstacles cost with weights w [H] (w_1..w_H), lam, obstacles [(x, y, size)], pusher start p0."""
+    if kind == 0:
+        lib().oracle_set_cost(0, 0, None, ctypes.c_double(0.0), 0, None, None)
+        return
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    obs = np.ascontiguousarray(np.asarray(obstacles, dtype=np.float64).reshape(-1, 3))
+    p0 = np.ascontiguousarray(p0, dtype=np.float64)
+    rc = lib().oracle_set_cost(int(kind), int(w.size), w.ctypes.data_as(_c_double_p), ctypes.c_double(lam),
+                               int(obs.shape[0]), obs.ctypes.data_as(_c_double_p), p0.ctypes.data_as(_c_double_p))
+    if rc != 0:
+        raise ValueError("oracle_set_cost: bad arguments")
+
+
+def relu_dist_lower(l0, u0, l1, u1, cx, cy, size):
+    """The linear lower bound a . q + b of ReLU(size - ||q - c||) on a box (Appendix D.4 penalty): (used, a0, a1, b)."""
+    a0, a1, b = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    fn = lib().oracle_relu_dist_lower
+    fn.argtypes = [ctypes.c_double] * 7 + [_c_double_p] * 3
+    used = fn(l0, u0, l1, u1, cx, cy, size, ctypes.byref(a0), ctypes.byref(a1), ctypes.byref(b))
+    return int(used), a0.value, a1.value, b.value

@@ -200,3 +200,13 @@ def batch_random_boxes(problems, rows, d_stride, seed, min_width=0.1, max_width=
     order = np.random.Generator(np.random.PCG64(seed)).permutation(lo.shape[0])
     ids = (np.arange(lo.shape[0], dtype=np.uint64) + np.uint64(1000))
     return lo[order], hi[order], ids, prob[order]
+
+
+def obstacle_cost(H, seed, n_obs=3, lam=10.0):
+    """The pushing-with-obstacles cost of Appendix D.4 for a pushing-scale problem (state: 4 planar keypoints,
+    action: the planar pusher motion): weights w_t = t / H increasing with time, penalty lam, n_obs obstacles
+    with centres N(0, 1) and radii U(0.3, 0.8), pusher start (0, 0).  Returns dict(w, lam, obstacles, p0)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    obs = [(float(rng.normal()), float(rng.normal()), float(rng.uniform(0.3, 0.8))) for _ in range(n_obs)]
+    w = [(t + 1) / H for t in range(H)]
+    return dict(w=np.array(w, dtype=np.float64), lam=float(lam), obstacles=obs, p0=(0.0, 0.0))

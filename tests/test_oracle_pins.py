@@ -960,3 +960,112 @@ def test_synth_bab_reaches_the_optimum(oracle):
     assert inc == pytest.approx(d * gstar, abs=2e-3)
     assert lb.min() <= d * gstar + 1e-9
     assert inc - lb.min() < 0.05
+
+
+# --------------------------------------------------------------------------
+# Pushing-with-obstacles cost (Appendix D.4)
+# --------------------------------------------------------------------------
+
+@pytest.fixture
+def obstacle_cost(oracle):
+    def make(H, seed, **kw):
+        c = W.obstacle_cost(H, seed, **kw)
+        oracle.set_cost(1, c["w"], c["lam"], c["obstacles"], c["p0"])
+        return c
+    yield make
+    oracle.set_cost(0)
+
+
+def _push_cost_numpy(p, c, u, traj):
+    """The paper's Eq. (pushing_cost) summed over t = 1..H, written out with numpy, plus rho ||u||^2."""
+    H, k, s = p["H"], p["k"], p["s"]
+    pos = np.array(c["p0"], dtype=np.float64)
+    f = 0.0
+    for t in range(1, H + 1):
+        pos = pos + u[(t - 1) * k:t * k]
+        x = traj[t]
+        f += c["w"][t - 1] * np.linalg.norm(x - p["goal"])
+        for (ox, oy, sz) in c["obstacles"]:
+            f += c["lam"] * max(0.0, sz - np.hypot(pos[0] - ox, pos[1] - oy))
+            for i in range(s // 2):
+                f += c["lam"] * max(0.0, sz - np.hypot(x[2 * i] - ox, x[2 * i + 1] - oy))
+    return f + p["rho"] * float(np.sum(u * u))
+
+
+def test_obstacle_cost_objective_formula(oracle, obstacle_cost):
+    p = W.config_problem("pushing", 61)
+    c = obstacle_cost(p["H"], 61)
+    rng = np.random.default_rng(0)
+    hits = 0
+    for _ in range(6):
+        u = rng.uniform(-1, 1, size=p["k"] * p["H"])
+        f, traj, _ = oracle.objective(p, u, with_traj=True)
+        assert f == pytest.approx(_push_cost_numpy(p, c, u, traj), rel=1e-12)
+        hits += f > _push_cost_numpy(p, dict(c, lam=0.0), u, traj) + 1e-9
+    assert hits > 0   # the obstacles are met by some trajectories
+    u = rng.uniform(-1, 1, size=p["k"] * p["H"]).astype(np.float32)
+    assert oracle.objective_f32(p, u) == pytest.approx(oracle.objective(p, u.astype(np.float64)), rel=2e-6)
+
+
+def test_obstacle_relaxation_below_penalty(oracle, obstacle_cost):
+    """The bound's linear pieces: with all ReLUs of a 0-hidden-step problem stable, CROWN's bound equals the
+    cost at a point box, and over boxes it stays below the cost at dense samples."""
+    p = W.config_problem("pushing", 62)
+    p = dict(p, H=3)
+    obstacle_cost(3, 62, n_obs=4)
+    d = p["k"] * p["H"]
+    rng = np.random.default_rng(1)
+    for _ in range(8):
+        u = rng.uniform(-1, 1, size=d).astype(np.float32)
+        lo, hi = u[None].copy(), u[None].copy()
+        c = oracle.crown(p, lo, hi)
+        f = oracle.objective(p, u.astype(np.float64))
+        assert c["lb"][0] == pytest.approx(f, rel=1e-9, abs=1e-9)
+    for _ in range(8):
+        ctr = rng.uniform(-1, 1, size=d)
+        w = rng.uniform(0.01, 0.3, size=d)
+        lo = np.float32(np.clip(ctr - w, -1, 1))[None]
+        hi = np.float32(np.clip(ctr + w, -1, 1))[None]
+        lb = oracle.crown(p, lo, hi)["lb"][0]
+        lb_i = oracle.ibp(p, lo, hi)[0][0]
+        us = lo + (hi - lo) * rng.uniform(size=(400, d))
+        fs = np.array([oracle.objective(p, v) for v in us])
+        assert lb <= fs.min() + 1e-9
+        assert lb_i <= fs.min() + 1e-9
+
+
+def test_obstacle_bab_end_to_end(oracle, obstacle_cost):
+    """Algorithm 2 with the obstacle cost on a tiny problem (H = 1, d = 2): the incumbent approaches the dense-grid
+    minimum and the lower bounds stay below it."""
+    p = W.config_problem("pushing", 63)
+    p = dict(p, H=1)
+    obstacle_cost(1, 63, n_obs=3, lam=50.0)
+    g = np.linspace(-1, 1, 401)
+    fg = min(oracle.objective(p, np.array([a, b])) for a in g[::4] for b in g[::4])
+    inc, _, hist = oracle.bab(p, *W.grid_boxes(2, 2), iters=40, n_pick=8, samples=64, seed=3)
+    assert inc <= fg + 1e-3
+    assert hist[-1]["global_lb"] <= fg + 1e-9
+
+
+def test_obstacle_penalty_relaxation_brute_force(oracle):
+    """a . q + b <= ReLU(s - ||q - c||) on every point of the box (dense grid), exact at a point box inside the
+    obstacle, and used (nonzero) for boxes straddling or inside the obstacle."""
+    rng = np.random.default_rng(64)
+    used_n = 0
+    for _ in range(200):
+        c = rng.normal(size=2)
+        sz = rng.uniform(0.2, 1.0)
+        ctr = c + rng.normal(size=2) * 0.6 * sz
+        w = rng.uniform(0.01, 0.5, size=2) * sz
+        l0, u0, l1, u1 = ctr[0] - w[0], ctr[0] + w[0], ctr[1] - w[1], ctr[1] + w[1]
+        used, a0, a1, b = oracle.relu_dist_lower(l0, u0, l1, u1, c[0], c[1], sz)
+        used_n += used
+        g0, g1 = np.meshgrid(np.linspace(l0, u0, 61), np.linspace(l1, u1, 61))
+        pen = np.maximum(0.0, sz - np.hypot(g0 - c[0], g1 - c[1]))
+        assert np.all(a0 * g0 + a1 * g1 + b <= pen + 1e-12)
+        if not used:
+            assert a0 == a1 == b == 0.0
+    assert used_n > 30
+    q = np.array([0.1, -0.2])
+    used, a0, a1, b = oracle.relu_dist_lower(q[0], q[0], q[1], q[1], 0.0, 0.0, 1.0)
+    assert used and a0 * q[0] + a1 * q[1] + b == pytest.approx(1.0 - np.hypot(*q), abs=1e-15)
