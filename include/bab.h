@@ -69,6 +69,10 @@ extern "C" {
 #define BAB_PICK_LB 0      /* smallest (lb, id): deterministic */
 #define BAB_PICK_SOFTMAX 1 /* the softmax sampling of Eq. lf_pick (counter-based, reproducible) */
 
+/* state cost of the objective (bab_set_cost) */
+#define BAB_COST_SQUARED 0           /* ||x_t - g||^2 (default) */
+#define BAB_COST_PUSHING_OBSTACLES 1 /* Appendix D.4, Eq. pushing_cost */
+
 /* Limits of this build. */
 #define BAB_MAX_LAYERS 8
 #define BAB_MAX_WIDTH 256
@@ -375,6 +379,33 @@ int bab_rollout_split(bab_ctx *ctx, const float *x0, const float *goal, int hori
                       const float *hi, const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed,
                       int precision, float top_pct, float *ub, float *best_u, double *inc_val, float *inc_u,
                       float *costs, int *split_dim, void *stream);
+
+/*
+ * ---------------------------------------------------------------------------
+ * The state cost c(x_t), t = 1..H, of the objective f(u) = sum_t c(x_t) +
+ * rho sum_t ||u_t||^2 (Section 3, Eq. trajop).  BAB_COST_SQUARED (default):
+ * ||x_t - g||^2.  BAB_COST_PUSHING_OBSTACLES (Appendix D.4, Eq. pushing_cost):
+ * w_t ||x_t - g|| + lambda sum_o [ReLU(s_o - ||p_t - p_o||) + sum_i ReLU(s_o -
+ * ||x_t^(i) - p_o||)], the state being s / 2 planar keypoints x_t^(i) =
+ * (x_{t,2i}, x_{t,2i+1}) and the action the planar pusher motion (k = 2), with
+ * p_t = p0 + u_0 + ... + u_{t-1}.  Arguments (host): w [H] (w[t - 1] = w_t,
+ * finite, >= 0; calls with a longer horizon are refused), lambda >= 0,
+ * obstacles [n_obs][3] (x, y, size), n_obs <= 8, p0 [2].  The context keeps a
+ * device copy; kind BAB_COST_SQUARED clears it.
+ *
+ * Paths that support the obstacle cost: bab_rollout (FP32, and BF16X3 for
+ * s <= 8), bab_rollout_cem (FP32), bab_update_incumbent, bab_bound_ibp and
+ * bab_bound_crown (FP32, adaptive slopes); the other bound paths (alpha
+ * steps, tensor-core CROWN, early stop, batched problems, the static entry
+ * point, the box gradient) and BF16 rollouts return BAB_ERR_UNSUPPORTED.
+ * Sound as for the squared cost: interval minima per term rounded down; in
+ * CROWN the norm by its tangent plane at the box centre (w ||y|| >= w ghat . y,
+ * |ghat| <= 1), each penalty by an affine function below the concave
+ * s_o - distance at the box's vertices (or 0), with the same margin.
+ * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_UNSUPPORTED (s odd or k != 2), BAB_ERR_CUDA.
+ */
+int bab_set_cost(bab_ctx *ctx, int kind, int H, const float *w, float lambda, int n_obs, const float *obstacles,
+                 const float *p0);
 
 /*
  * ---------------------------------------------------------------------------

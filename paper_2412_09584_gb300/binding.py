@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
     L.bab_synth_search.argtypes = [_P, _I, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _I, _F, _P, _P, _P, _P, _P,
                                    _P]
     L.bab_synth_bound.argtypes = [_P, _I, _P, _P, _I, _P, _P, _P]
+    L.bab_set_cost.argtypes = [_P, _I, _I, _P, _F, _I, _P, _P]
     L.bab_rollout_cem.argtypes = [_P, _P, _P, _I, _F, _P, _P, _P, _I, _P, _I, _I, _I, _F, ctypes.c_uint64, _I, _P,
                                   _P, _P, _P, _P, _P]
     L.bab_prune_branch_heuristic.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _F, ctypes.c_uint64,
@@ -433,3 +434,21 @@ def bab_synth_bound(ctx, d, lo, hi, n, lb, d_n=None, stream=None):
     rc = load().bab_synth_bound(ctx, int(d), _ptr(lo, f32, "lo"), _ptr(hi, f32, "hi"), int(n), _ptr(d_n, torch.int32),
                                 _ptr(lb, f32, "lb"), _stream(stream))
     _check(ctx, rc)
+
+
+COST_SQUARED = 0
+COST_PUSHING_OBSTACLES = 1
+
+
+def bab_set_cost(ctx, kind, w=None, lam=0.0, obstacles=(), p0=(0.0, 0.0)):
+    """Select the state cost (Appendix D.4 pushing-with-obstacles, or the squared distance); see include/bab.h.
+    w: the weights w_1..w_H (host), obstacles: [(x, y, size)], p0: the pusher start."""
+    L = load()
+    if kind == COST_SQUARED:
+        _check(ctx, L.bab_set_cost(ctx, 0, 0, None, 0.0, 0, None, None))
+        return
+    wa = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+    ob = np.ascontiguousarray(np.asarray(obstacles, dtype=np.float32).reshape(-1, 3))
+    pa = np.ascontiguousarray(np.asarray(p0, dtype=np.float32))
+    _check(ctx, L.bab_set_cost(ctx, int(kind), int(wa.size), wa.ctypes.data, float(lam), int(ob.shape[0]),
+                               ob.ctypes.data if ob.size else None, pa.ctypes.data))

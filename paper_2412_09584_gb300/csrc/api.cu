@@ -30,6 +30,9 @@ struct bab_ctx {
     int tune_rollout_tc = -1;   // tiles per CTA
     int tune_crown_tc = -1;     // tiles per CTA
     int rescore_topk = 0;       // BF16 rollouts: FP32 re-score of the topk smallest ub (0: every box)
+    CostDesc cost{};            // the state cost (bab_set_cost); kind 0 by default
+    int cost_H = 0;             // horizon its weights cover
+    float *d_cost_w = nullptr;  // its weights w_t on the device
     char err[512] = {0};
 };
 
@@ -204,8 +207,17 @@ int check_problem(bab_ctx *c, const float *x0, const float *goal, int H, float r
     if (n > 0 && (!lo || !hi)) return fail(c, BAB_ERR_INVALID_ARG, "lo and hi are required");
     if (!(rho >= 0.f) || !std::isfinite(rho)) return fail(c, BAB_ERR_INVALID_ARG, "rho must be finite and >= 0");
     if (c->net.L < 1) return fail(c, BAB_ERR_INVALID_ARG, "the context holds no network (bab_context_create)");
+    if (c->cost.kind != 0 && H > c->cost_H)
+        return fail(c, BAB_ERR_INVALID_ARG, "the cost weights cover horizons up to %d (H = %d)", c->cost_H, H);
     long long d = (long long)c->net.k * H;
     if (d > (1 << 24)) return fail(c, BAB_ERR_SHAPE, "action dimension k*H too large");
+    return BAB_OK;
+}
+
+// The paths without the obstacle cost refuse it.
+int refuse_obstacles(bab_ctx *c, const char *what)
+{
+    if (c->cost.kind != 0) return fail(c, BAB_ERR_UNSUPPORTED, "%s does not support the obstacle cost", what);
     return BAB_OK;
 }
 
@@ -213,6 +225,7 @@ BoundArgs make_bound_args(bab_ctx *c, const float *x0, const float *goal, int H,
                           const float *hi, int n, const int *d_n)
 {
     BoundArgs a{};
+    a.cost = c->cost;
     a.net = c->net;
     a.fwd = c->d_fwd;
     a.bwd = c->d_bwd;
@@ -380,6 +393,49 @@ int bab_load_dynamics_batch(bab_ctx **out, int n_problems, int n_layers, const i
     return load_impl(out, n_problems, n_layers, dims, params, state_dim, action_dim, flags);
 }
 
+int bab_set_cost(bab_ctx *c, int kind, int H, const float *w, float lambda, int n_obs, const float *obstacles,
+                 const float *p0)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (kind == BAB_COST_SQUARED) {
+        c->cost = CostDesc{};
+        return BAB_OK;
+    }
+    if (kind != BAB_COST_PUSHING_OBSTACLES) return fail(c, BAB_ERR_INVALID_ARG, "unknown cost kind %d", kind);
+    if (c->net.L >= 1 && (c->net.k != 2 || c->net.s % 2 != 0))
+        return fail(c, BAB_ERR_UNSUPPORTED, "the obstacle cost needs planar keypoints (s even) and a planar pusher (k = 2)");
+    if (H < 1 || H > (1 << 20) || !w || !p0 || n_obs < 0 || n_obs > kMaxObstacles || (n_obs > 0 && !obstacles))
+        return fail(c, BAB_ERR_INVALID_ARG, "bad horizon, weights, obstacles (at most %d) or pusher start", kMaxObstacles);
+    if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(c, BAB_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    for (int t = 0; t < H; ++t)
+        if (!(w[t] >= 0.f) || !std::isfinite(w[t])) return fail(c, BAB_ERR_INVALID_ARG, "weights must be finite and >= 0");
+    float *dw = nullptr;
+    cudaError_t e = cudaMalloc(&dw, sizeof(float) * H);
+    if (e == cudaSuccess) e = cudaMemcpy(dw, w, sizeof(float) * H, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dw);
+        return cuda_fail(c, e, "cost weights");
+    }
+    cudaFree(c->d_cost_w);
+    c->d_cost_w = dw;
+    CostDesc cd{};
+    cd.kind = 1;
+    cd.n_obs = n_obs;
+    cd.lam = lambda;
+    for (int o = 0; o < n_obs; ++o) {
+        cd.ox[o] = obstacles[3 * o];
+        cd.oy[o] = obstacles[3 * o + 1];
+        cd.os[o] = obstacles[3 * o + 2];
+    }
+    cd.p0x = p0[0];
+    cd.p0y = p0[1];
+    cd.w = dw;
+    c->cost = cd;
+    c->cost_H = H;
+    return BAB_OK;
+}
+
 int bab_context_create(bab_ctx **out)
 {
     if (!out) return BAB_ERR_INVALID_ARG;
@@ -479,6 +535,7 @@ int bab_destroy(bab_ctx *c)
     cudaFree(c->d_tc_bias);
     cudaFree(c->scratch);
     cudaFree(c->d_status);
+    cudaFree(c->d_cost_w);
     delete c;
     return BAB_OK;
 }
@@ -531,6 +588,8 @@ int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rh
     if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3 && precision != BAB_PREC_BF16)
         return fail(c, BAB_ERR_INVALID_ARG, "unknown precision %d", precision);
     const int split = precision == BAB_PREC_BF16X3 ? 3 : 1;
+    if (c->cost.kind != 0 && (precision == BAB_PREC_BF16 || (precision == BAB_PREC_BF16X3 && c->net.s > 8)))
+        return refuse_obstacles(c, "BF16 rollouts (and tensor-core rollouts with more than 8 states)");
     if (precision != BAB_PREC_FP32 && !rollout_tc_supported(c->net, split, c->max_smem))
         return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout needs hidden widths that are multiples of 32, "
                                             "s <= 32, s + k <= 64 and a weight image that fits in shared memory");
@@ -539,6 +598,7 @@ int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rh
     rc = ensure_scratch(c, key_bytes + 512);
     if (rc) return rc;
     RolloutArgs a{};
+    a.cost = c->cost;
     a.topk = precision == BAB_PREC_BF16 ? c->rescore_topk : 0;
     a.topk_t = reinterpret_cast<unsigned long long *>(static_cast<char *>(c->scratch) + key_bytes);
     a.net = c->net;
@@ -630,6 +690,8 @@ int bab_rollout_cem(bab_ctx *c, const float *x0, const float *goal, int H, float
     if ((inc_val == nullptr) != (inc_u == nullptr)) return fail(c, BAB_ERR_INVALID_ARG, "inc_val and inc_u go together");
     if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
         return fail(c, BAB_ERR_UNSUPPORTED, "the cross-entropy search runs in FP32 or BF16x3 (precision %d)", precision);
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core cross-entropy search")) != BAB_OK)
+        return rc;
     if ((long long)iters * samples >= (1ll << 32)) return fail(c, BAB_ERR_SHAPE, "iters * samples must be < 2^32");
     if (precision == BAB_PREC_BF16X3 && !rollout_tc_supported(c->net, 3, c->max_smem))
         return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout not available for this network");
@@ -662,6 +724,7 @@ int bab_rollout_cem(bab_ctx *c, const float *x0, const float *goal, int H, float
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_cem_init(g, warm_u, st);
     RolloutArgs a{};
+    a.cost = c->cost;
     a.net = c->net;
     a.batch.P = 1;
     a.batch.Hmax = H;
@@ -724,6 +787,7 @@ int bab_rollout_search_bounds(bab_ctx *c, const float *x0, const float *goal, in
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     RolloutArgs a{};
+    a.cost = c->cost;
     a.net = c->net;
     a.batch.P = 1;
     a.batch.Hmax = H;
@@ -767,6 +831,8 @@ int bab_bound_crown_given(bab_ctx *c, const float *x0, const float *goal, int H,
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
+    rc = refuse_obstacles(c, "CROWN with given bounds and early stop");
+    if (rc) return rc;
     if (t_stop < 0 || t_stop > H) return fail(c, BAB_ERR_INVALID_ARG, "t_stop must be in [0, horizon]");
     if (n > 0 && (!lb || !pre_lo || !pre_hi || !x_lo || !x_hi))
         return fail(c, BAB_ERR_INVALID_ARG, "lb and the four bound arrays are required");
@@ -795,6 +861,7 @@ int bab_update_incumbent(bab_ctx *c, const float *x0, const float *goal, int H, 
     if (n > 0 && (!ub || !best_u)) return fail(c, BAB_ERR_INVALID_ARG, "ub and best_u are required");
     if (n == 0) return BAB_OK;
     RolloutArgs a{};
+    a.cost = c->cost;
     a.net = c->net;
     a.batch.P = 1;
     a.batch.Hmax = H;
@@ -839,6 +906,7 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core CROWN")) != BAB_OK) return rc;
     if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
     if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
         return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
@@ -876,6 +944,8 @@ int bab_alpha_init(bab_ctx *c, const float *x0, const float *goal, int H, float 
                    int n, const int *d_n, float *alpha, void *stream)
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    rc = refuse_obstacles(c, "the alpha slopes");
     if (rc) return rc;
     if (n > 0 && !alpha) return fail(c, BAB_ERR_INVALID_ARG, "alpha is required");
     if (n == 0) return BAB_OK;
@@ -944,6 +1014,8 @@ int bab_alpha_grad(bab_ctx *c, const float *x0, const float *goal, int H, float 
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
+    rc = refuse_obstacles(c, "the alpha gradient");
+    if (rc) return rc;
     if (n > 0 && (!alpha || !lb || !grad_alpha)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, lb and grad are required");
     rc = check_bound_precision(c, precision);
     if (rc) return rc;
@@ -961,6 +1033,8 @@ int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float 
                    int precision, float *lb, float *lb_best, float *grad_alpha, void *stream)
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    rc = refuse_obstacles(c, "the alpha step");
     if (rc) return rc;
     if (n > 0 && (!alpha || !adam_m || !adam_v)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, m and v are required");
     if (step < 1) return fail(c, BAB_ERR_INVALID_ARG, "step counts from 1");
@@ -987,6 +1061,8 @@ int bab_box_grad(bab_ctx *c, const float *x0, const float *goal, int H, float rh
                  int n, const int *d_n, const float *alpha, float *lb, float *grad_lo, float *grad_hi, void *stream)
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    rc = refuse_obstacles(c, "the box gradient");
     if (rc) return rc;
     if (n > 0 && (!lb || !grad_lo || !grad_hi)) return fail(c, BAB_ERR_INVALID_ARG, "lb, grad_lo and grad_hi are required");
     if (n == 0) return BAB_OK;
@@ -1019,6 +1095,8 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
                        float *lb_best, void *stream)
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    rc = refuse_obstacles(c, "the alpha optimisation");
     if (rc) return rc;
     if (n > 0 && !lb_best) return fail(c, BAB_ERR_INVALID_ARG, "lb_best is required");
     if (steps < 1 || steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "steps must be in [1, 100000]");
@@ -1197,6 +1275,7 @@ int check_batch(bab_ctx *c, const float *x0, const float *goal, const int *horiz
 {
     if (!c) return BAB_ERR_INVALID_ARG;
     c->err[0] = 0;
+    if (c->cost.kind != 0) return refuse_obstacles(c, "batched problems");
     if (!x0 || !goal || !horizon) return fail(c, BAB_ERR_INVALID_ARG, "x0, goal and horizon are required");
     if (max_horizon < 1 || max_horizon > (1 << 20)) return fail(c, BAB_ERR_SHAPE, "max_horizon out of range");
     if (n < 0) return fail(c, BAB_ERR_SHAPE, "n = %d < 0", n);
@@ -1245,6 +1324,7 @@ int bab_rollout_batch(bab_ctx *c, const float *x0, const float *goal, const int 
     rc = ensure_scratch(c, (size_t)n * sizeof(unsigned long long) + 256);
     if (rc) return rc;
     RolloutArgs a{};
+    a.cost = c->cost;
     a.net = c->net;
     a.batch = make_batch(c, prob, horizon, rho, max_horizon);
     a.fwd = c->d_fwd;
@@ -1475,6 +1555,7 @@ extern "C" {
 int bab_autotune(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
                  const uint64_t *id, int n, int samples, int alpha_steps, void *stream)
 {
+    if (c && c->cost.kind != 0) return refuse_obstacles(c, "the autotuner");
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
     if (n < 1 || !id) return fail(c, BAB_ERR_INVALID_ARG, "autotuning needs at least one box and its id");

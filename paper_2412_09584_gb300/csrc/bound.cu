@@ -32,6 +32,62 @@ constexpr int RB = 16;
 constexpr int NT = 256;
 constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20): twice the unit roundoff, rounded up
 
+// The pushing-with-obstacles state cost at step t on the box [xl, xu] of x_t, one warp per row (lane i owns
+// coordinate i, s <= 32): lane i's coefficient aa of a linear lower bound aa . x + constant; returns the constant
+// (rounded down, on every lane).  The norm by its tangent plane at the box centre, w ||x - g|| >= w ghat . (x - g)
+// with |ghat| < 1 (the unit vector shrunk by 1e-5 against rounding); each keypoint penalty by penalty_lower.
+__device__ __forceinline__ float obstacle_state_lin(const CostDesc &c, int t, int s, const float *xl, const float *xu,
+                                                    const float *goal, int lane, float &aa)
+{
+    const float m = lane < s ? 0.5f * (xl[lane] + xu[lane]) - goal[lane] : 0.f;
+    const float nm = sqrtf(warp_sum(m * m));
+    float a_ = 0.f, cst = 0.f;
+    if (nm > 0.f && lane < s) {
+        a_ = c.w[t - 1] * (m / nm) * 0.99999f;
+        cst = __fmul_rd(-a_, goal[lane]);
+    }
+    if (lane < s) {
+        const int kp = lane >> 1;
+        for (int o = 0; o < c.n_obs; ++o) {
+            float a0, a1, b;
+            if (penalty_lower(c, o, xl[2 * kp], xu[2 * kp], xl[2 * kp + 1], xu[2 * kp + 1], a0, a1, b)) {
+                a_ += c.lam * ((lane & 1) ? a1 : a0);
+                if (!(lane & 1)) cst = __fadd_rd(cst, __fmul_rd(c.lam, b));
+            }
+        }
+    }
+    aa = a_;
+    return warp_sum_rd(cst);
+}
+
+// The pusher penalties at step t (1..H): the box of p_t = p_0 + u_0 + ... + u_{t-1} (directed rounding), then
+// per obstacle the linear lower bound lam (a . p_t + b) = lam (a . p_0 + b) + lam a . (u_0 + ... + u_{t-1}):
+// adds lam a to P[0..1] (the coefficient of every earlier action) and |lam a| to Pabs; returns the constant
+// lam (a . p_0 + b), rounded down.  One thread.
+__device__ __forceinline__ float pusher_lin(const CostDesc &c, int t, int k, const float *lo, const float *hi,
+                                            float *P, float *Pabs)
+{
+    float l0 = c.p0x, l1 = c.p0y, u0 = c.p0x, u1 = c.p0y;
+    for (int tau = 0; tau < t; ++tau) {
+        l0 = __fadd_rd(l0, lo[tau * k]);
+        l1 = __fadd_rd(l1, lo[tau * k + 1]);
+        u0 = __fadd_ru(u0, hi[tau * k]);
+        u1 = __fadd_ru(u1, hi[tau * k + 1]);
+    }
+    float cst = 0.f;
+    for (int o = 0; o < c.n_obs; ++o) {
+        float a0, a1, b;
+        if (penalty_lower(c, o, l0, u0, l1, u1, a0, a1, b)) {
+            P[0] += c.lam * a0;
+            P[1] += c.lam * a1;
+            Pabs[0] += fabsf(c.lam * a0);
+            Pabs[1] += fabsf(c.lam * a1);
+            cst = __fadd_rd(cst, __fmul_rd(c.lam, __fadd_rd(__fmaf_rd(a0, c.p0x, __fmul_rd(a1, c.p0y)), b)));
+        }
+    }
+    return cst;
+}
+
 // ---------------------------------------------------------------------------
 // IBP
 // ---------------------------------------------------------------------------
@@ -119,6 +175,7 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
     float *xl = p; p += RB * s4;
     float *xu = p; p += RB * s4;
     float *lbacc = p; p += RB;
+    float *pbx = p; p += 4 * RB;  // pusher position box per row (obstacle cost): lo x, lo y, hi x, hi y
 
     const int nlive = live_count(a.n, a.d_n);
     const int box0 = blockIdx.x * RB;
@@ -135,7 +192,11 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
             a.x_hi[(size_t)(box0 + r) * (H + 1) * s + c] = a.x0[c];
         }
     }
-    for (int r = threadIdx.x; r < RB; r += NT) lbacc[r] = 0.f;
+    for (int r = threadIdx.x; r < RB; r += NT) {
+        lbacc[r] = 0.f;
+        pbx[4 * r] = pbx[4 * r + 2] = a.cost.p0x;
+        pbx[4 * r + 1] = pbx[4 * r + 3] = a.cost.p0y;
+    }
     __syncthreads();
 
     for (int t = 0; t < H; ++t) {
@@ -153,6 +214,15 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
             blo[0][r * ld + c] = vl;
             bhi[0][r * ld + c] = vh;
         }
+        if (a.cost.kind == 1)
+            for (int r = threadIdx.x; r < RB; r += NT)
+                if (box0 + r < nlive) {
+                    const float *ul = a.lo + (size_t)(box0 + r) * d + t * k, *uh = a.hi + (size_t)(box0 + r) * d + t * k;
+                    pbx[4 * r] = __fadd_rd(pbx[4 * r], ul[0]);
+                    pbx[4 * r + 1] = __fadd_rd(pbx[4 * r + 1], ul[1]);
+                    pbx[4 * r + 2] = __fadd_ru(pbx[4 * r + 2], uh[0]);
+                    pbx[4 * r + 3] = __fadd_ru(pbx[4 * r + 3], uh[1]);
+                }
         if (a.rho > 0.f) {
             for (int r = warp; r < RB; r += NT / 32) {
                 const int box = box0 + r;
@@ -210,9 +280,30 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
                     a.x_hi[((size_t)box * (H + 1) + t + 1) * s + i] = nh;
                 }
                 const float g = a.goal[i];
-                v = __fadd_rd(v, sq_min_rd(__fsub_rd(nl, g), __fsub_ru(nh, g)));
+                if (a.cost.kind == 0) {
+                    v = __fadd_rd(v, sq_min_rd(__fsub_rd(nl, g), __fsub_ru(nh, g)));
+                } else {
+                    // distance from g to the interval, rounded down, squared rounded down
+                    const float e = fmaxf(fmaxf(__fsub_rd(nl, g), __fsub_rd(g, nh)), 0.f);
+                    v = __fmaf_rd(e, e, v);
+                }
             }
             v = warp_sum_rd(v);
+            if (a.cost.kind == 1) {
+                // w_t times the distance from g to the box, then the penalties at their minima (each rounded down)
+                __syncwarp();
+                float pen = 0.f;
+                const int nq = s / 2 + 1;
+                for (int q = lane; q < a.cost.n_obs * nq; q += 32) {
+                    const int o = q / nq, kp = q % nq - 1;
+                    pen = __fadd_rd(pen, kp < 0 ? penalty_min_rd(a.cost, o, pbx[4 * r], pbx[4 * r + 2], pbx[4 * r + 1],
+                                                                 pbx[4 * r + 3])
+                                                : penalty_min_rd(a.cost, o, xl[r * s4 + 2 * kp], xu[r * s4 + 2 * kp],
+                                                                 xl[r * s4 + 2 * kp + 1], xu[r * s4 + 2 * kp + 1]));
+                }
+                pen = warp_sum_rd(pen);
+                v = __fadd_rd(__fmul_rd(a.cost.w[t], __fsqrt_rd(v)), pen);
+            }
             if (lane == 0) lbacc[r] = __fadd_rd(lbacc[r], v);
         }
         __syncthreads();
@@ -268,7 +359,7 @@ __device__ __forceinline__ RowsView global_view(const BoundArgs &a, int box0)
 // shared-memory floats of crown_rows / fwd_rows scratch
 __host__ __device__ inline size_t crown_rows_floats(const NetDesc &N, int rb, int d)
 {
-    return 2 * (size_t)rb * N.maxw_p + (size_t)rb * pad4(N.s) + (size_t)rb * pad4(d) + 2 * rb;
+    return 2 * (size_t)rb * N.maxw_p + (size_t)rb * pad4(N.s) + (size_t)rb * pad4(d) + 2 * rb + 4 * rb;
 }
 __host__ __device__ inline size_t fwd_rows_floats(const NetDesc &N, int rb)
 {
@@ -292,7 +383,9 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
     float *mu = p; p += RBT * d4;
     float *cst = p; p += RBT;
     float *mg = p; p += RBT;
+    float *Pu = p; p += 4 * RBT;  // obstacle cost: per row the pusher coefficient of the actions (2) and its |sum| (2)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool obst = a.cost.kind == 1;
     const bool has_alpha = v.alpha != nullptr;
     const int ts = a.t_stop;              // early stop: propagate back to x_ts only
     const bool with_margin = v.S != nullptr;
@@ -315,6 +408,23 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
     }
     // tangent of ||x_H - g||^2: coefficient 2m, constant -(2 m g + m^2)
     for (int r = warp; r < RBT; r += NTT / 32) {
+        if (obst) {
+            // the obstacle cost at step H: its linear lower bound on x_H, and the pusher penalties at H
+            float aa = 0.f, c = 0.f;
+            if (r < nrows && H > ts) {
+                const size_t xi = ((size_t)r * (H + 1) + H) * s;
+                c = obstacle_state_lin(a.cost, H, s, v.x_lo + xi, v.x_hi + xi, a.goal, lane, aa);
+            }
+            if (lane < s) lam[r * s4 + lane] = aa;
+            if (lane == 0) {
+                Pu[4 * r] = Pu[4 * r + 1] = Pu[4 * r + 2] = Pu[4 * r + 3] = 0.f;
+                if (r < nrows) c = __fadd_rd(c, pusher_lin(a.cost, H, k, v.lo + (size_t)r * d, v.hi + (size_t)r * d,
+                                                           Pu + 4 * r, Pu + 4 * r + 2));
+                cst[r] = c;
+                mg[r] = 0.f;
+            }
+            continue;
+        }
         float c = 0.f;
         for (int i = lane; i < s; i += 32) {
             float aa = 0.f;
@@ -406,6 +516,41 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
         // A is on [x_t | u_t]: mu_t = A_u; lam <- lam + A_x (+ tangent of ||x_t - g||^2 for t >= 1)
         for (int r = warp; r < RBT; r += NTT / 32) {
             float c = 0.f, e = 0.f;
+            if (obst) {
+                // mu_t = A_u + the pusher coefficient of the later steps; its rounding (H additions) in the margin
+                const float *lo_r = v.lo + (size_t)r * d, *hi_r = v.hi + (size_t)r * d;
+                for (int j = lane; j < k; j += 32) {
+                    const float Au = Ab[cur][r * ld + s + j];
+                    const float Pj = j < 2 ? Pu[4 * r + j] : 0.f, Pa = j < 2 ? Pu[4 * r + 2 + j] : 0.f;
+                    mu[r * d4 + t * k + j] = Au + Pj;
+                    if (with_margin && r < nrows) {
+                        const float um = fmaxf(fabsf(lo_r[t * k + j]), fabsf(hi_r[t * k + j]));
+                        e = __fmaf_ru(__fmul_ru(__fmul_ru((float)(H + 2), kTwoU), __fadd_ru(fabsf(Au), Pa)), um, e);
+                    }
+                }
+                float aa = 0.f;
+                if (t > ts && t >= 1 && r < nrows) {
+                    const size_t xi = ((size_t)r * (H + 1) + t) * s;
+                    c = obstacle_state_lin(a.cost, t, s, v.x_lo + xi, v.x_hi + xi, a.goal, lane, aa);
+                }
+                if (lane < s) {
+                    const float Ax = Ab[cur][r * ld + lane];
+                    const float lo_ = lam[r * s4 + lane];
+                    const size_t xi = ((size_t)r * (H + 1) + t) * s + lane;
+                    const float B = (t >= 1 && r < nrows) ? fmaxf(fabsf(v.x_lo[xi]), fabsf(v.x_hi[xi])) : fabsf(a.x0[lane]);
+                    lam[r * s4 + lane] = (lo_ + Ax) + aa;
+                    const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
+                    if (with_margin) e = __fmaf_ru(__fmul_ru(kTwoU, mag), B, e);
+                }
+                e = warp_sum_ru(e);
+                if (lane == 0) {
+                    if (t >= 1 && r < nrows)
+                        c = __fadd_rd(c, pusher_lin(a.cost, t, k, lo_r, hi_r, Pu + 4 * r, Pu + 4 * r + 2));
+                    cst[r] = __fadd_rd(cst[r], c);
+                    mg[r] = __fadd_ru(mg[r], e);
+                }
+                continue;
+            }
             for (int j = lane; j < k; j += 32) mu[r * d4 + t * k + j] = Ab[cur][r * ld + s + j];
             for (int i = lane; i < s; i += 32) {
                 const float Ax = Ab[cur][r * ld + i];
@@ -756,7 +901,7 @@ static cudaError_t launch_rows_kernel(K kern_smem, K kern_glob, size_t img_bytes
 cudaError_t launch_ibp(const BoundArgs &a, int, cudaStream_t st)
 {
     const NetDesc &N = a.net;
-    size_t rest = (5 * (size_t)RB * N.maxw_p + 2 * (size_t)RB * pad4(N.s) + RB) * sizeof(float);
+    size_t rest = (5 * (size_t)RB * N.maxw_p + 2 * (size_t)RB * pad4(N.s) + 5 * (size_t)RB) * sizeof(float);
     return launch_rows_kernel(k_ibp<true>, k_ibp<false>, (size_t)N.img_floats * 4, rest, a.n, a, st);
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "bab_internal.cuh"
+#include "cost.cuh"
 
 namespace bab {
 
@@ -70,6 +71,7 @@ struct RolloutArgs {
     // each box's [n][d] mean and spread instead of uniform draws
     const float *cem_mu, *cem_sigma;
     int cem_it;
+    CostDesc cost;           // the state cost (kind 0: squared distance)
 };
 
 // one refit of the cross-entropy search (after a rollout of iteration `it` that wrote costs)
@@ -118,6 +120,7 @@ struct BoundArgs {
     uint32_t tmem_cols;
     int stages;              // > 0: the backward image is streamed through `stages` ring buffers
     int stage_bytes;
+    CostDesc cost;           // the state cost (kind 0: squared distance)
 };
 
 struct AdamStep {

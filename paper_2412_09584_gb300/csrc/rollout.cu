@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
     float *bhi = p; p += pad4(d);
     float *cost = p; p += R;
     float *goal = p; p += pad4(s);
+    float *ps = p; p += 2 * R;  // pusher position per row (obstacle cost)
     __shared__ unsigned long long red[NT / 32];
 
     const int nlive = live_count(a.n, a.d_n);
@@ -67,7 +68,11 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
             bhi[j] = a.hi[(size_t)box * d + j];
         }
         for (int i = threadIdx.x; i < R * s; i += NT) xs[(i / s) * pad4(s) + i % s] = x0[i % s];
-        for (int r = threadIdx.x; r < R; r += NT) cost[r] = 0.f;
+        for (int r = threadIdx.x; r < R; r += NT) {
+            cost[r] = 0.f;
+            ps[2 * r] = a.cost.p0x;
+            ps[2 * r + 1] = a.cost.p0y;
+        }
         const uint64_t hb = box_hash(a.seed, a.id[box]);
         __syncthreads();
         for (int t = 0; t < Hb; ++t) {
@@ -122,11 +127,19 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout_fp32(RolloutArgs a)
             // state terms then action terms in index order, so the value has a plain sequential definition)
             for (int r = threadIdx.x; r < R; r += NT) {
                 float c = 0.f;
-                for (int i = 0; i < s; ++i) {
-                    const float x = xs[r * pad4(s) + i] + in[r * ld + i];
-                    xs[r * pad4(s) + i] = x;
-                    const float e = x - goal[i];
-                    c = fmaf(e, e, c);
+                if (a.cost.kind == 0) {
+                    for (int i = 0; i < s; ++i) {
+                        const float x = xs[r * pad4(s) + i] + in[r * ld + i];
+                        xs[r * pad4(s) + i] = x;
+                        const float e = x - goal[i];
+                        c = fmaf(e, e, c);
+                    }
+                } else {
+                    // the pusher moves by u_t, then the state cost at t + 1 (Appendix D.4)
+                    ps[2 * r] = __fadd_rn(ps[2 * r], us[r * pad4(k)]);
+                    ps[2 * r + 1] = __fadd_rn(ps[2 * r + 1], us[r * pad4(k) + 1]);
+                    for (int i = 0; i < s; ++i) xs[r * pad4(s) + i] = __fadd_rn(xs[r * pad4(s) + i], in[r * ld + i]);
+                    c = obstacle_cost_f32(a.cost, t + 1, s, xs + r * pad4(s), goal, ps[2 * r], ps[2 * r + 1]);
                 }
                 for (int j = 0; j < k; ++j) {
                     const float u = us[r * pad4(k) + j];
@@ -229,6 +242,7 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
     if (row < 0) return;
     const float *u = a.best_u + (size_t)row * a.d;
     const int s = N.s, k = N.k;
+    double px = (double)a.cost.p0x, py = (double)a.cost.p0y;  // pusher position (obstacle cost; thread 0)
     for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = (double)x0[i];
     __syncthreads();
     for (int t = 0; t < Hb; ++t) {
@@ -250,10 +264,16 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
         }
         if (threadIdx.x == 0) {
             double f = f_sh;
-            for (int i = 0; i < s; ++i) {
-                xs[i] += act[cur][i];
-                const double e = xs[i] - (double)goal[i];
-                f += e * e;
+            for (int i = 0; i < s; ++i) xs[i] += act[cur][i];
+            if (a.cost.kind == 0) {
+                for (int i = 0; i < s; ++i) {
+                    const double e = xs[i] - (double)goal[i];
+                    f += e * e;
+                }
+            } else {
+                px += (double)u[t * k];
+                py += (double)u[t * k + 1];
+                f += obstacle_cost_f64(a.cost, t + 1, s, xs, goal, px, py);
             }
             for (int j = 0; j < k; ++j) {
                 const double uu = (double)u[t * k + j];
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
 static size_t rollout_smem_bytes(const NetDesc &N, int R, int d, bool wsmem)
 {
     size_t f = (wsmem ? (size_t)N.img_floats : 0) + 2 * (size_t)R * N.maxw_p + (size_t)R * pad4(N.s) +
-               (size_t)R * pad4(N.k) + 2 * (size_t)pad4(d) + R + pad4(N.s);
+               (size_t)R * pad4(N.k) + 2 * (size_t)pad4(d) + R + pad4(N.s) + 2 * (size_t)R;
     return f * sizeof(float);
 }
 

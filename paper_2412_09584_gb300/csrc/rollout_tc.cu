@@ -80,7 +80,7 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 // image; per slot a producer warp streams it, one K-atom (64 inputs of one
 // layer, hi and lo halves) at a time, through the slot's ring of a.stages
 // buffers in the order the slot's MMA issuer consumes them.
-template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM>
+template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM, bool OBST>
 __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -207,6 +207,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             };
             if (primary && Hb > 0) draw_step(0);
             float cost = 0.f;
+            float px = a.cost.p0x, py = a.cost.p0y;  // pusher position (obstacle cost)
             bool ok = true;
             for (int t = 0; t < Hb && ok; ++t) {
                 if (primary) {
@@ -214,6 +215,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
 #pragma unroll
                     for (int j = 0; j < kTcU; ++j)
                         if (j < k) cost = fmaf(rho * u[j], u[j], cost);
+                    if (OBST) {
+                        px = __fadd_rn(px, u[0]);
+                        py = __fadd_rn(py, u[1]);
+                    }
 #pragma unroll
                     for (int c16 = 0; c16 < 4; ++c16) {
                         if (c16 * 16 >= K1) break;
@@ -281,6 +286,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                                     c = fmaf(e, e, c);
                                 }
                             }
+                            if (OBST) c = obstacle_cost_f32(a.cost, t + 1, s, x, goal_p, px, py);
                             cost += c;
                         }
                     } else {
@@ -568,10 +574,10 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
 }
 
-template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM>
+template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM, bool OBST>
 static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = k_rollout_tc<NSLOT, SPLIT, SX, STREAM, CEM>;
+    auto kern = k_rollout_tc<NSLOT, SPLIT, SX, STREAM, CEM, OBST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, (NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, smem, st>>>(a);
@@ -608,15 +614,16 @@ bool rollout_tc_supported(const NetDesc &N, int split, int max_smem)
 }
 
 // CEM: the cross-entropy sampling mode (a separate instance, so that the uniform kernel carries none of its code)
-template <int SPLIT, int SX, bool CEM>
+// OBST: the pushing-with-obstacles state cost (another instance for the same reason)
+template <int SPLIT, int SX, bool CEM, bool OBST = false>
 static cudaError_t launch_tc_shape(const RolloutArgs &a, int nslot, bool stream, int grid, size_t smem,
                                    cudaStream_t st)
 {
     if (stream)
-        return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, true, CEM>(a, grid, smem, st)
-                          : launch_tc_variant<1, SPLIT, SX, true, CEM>(a, grid, smem, st);
-    return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, false, CEM>(a, grid, smem, st)
-                      : launch_tc_variant<1, SPLIT, SX, false, CEM>(a, grid, smem, st);
+        return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, true, CEM, OBST>(a, grid, smem, st)
+                          : launch_tc_variant<1, SPLIT, SX, true, CEM, OBST>(a, grid, smem, st);
+    return nslot == 2 ? launch_tc_variant<2, SPLIT, SX, false, CEM, OBST>(a, grid, smem, st)
+                      : launch_tc_variant<1, SPLIT, SX, false, CEM, OBST>(a, grid, smem, st);
 }
 
 // nslot_pref: tiles per CTA (1 or 2), or -1 for two whenever both fit in tensor memory
@@ -665,7 +672,11 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     k_fill_keys(a.keys, a.n, st);
     cudaError_t e;
     // state registers: 8, 16 or 32 (the output layer is 16 wide up to 16 states, else 32)
-    if (a.cem_mu) {
+    if (a.cost.kind == 1) {
+        // the obstacle cost: 3-term split, uniform samples, at most 8 states
+        if (split != 3 || a.cem_mu || N.s > 8) return cudaErrorInvalidValue;
+        e = launch_tc_shape<3, 8, false, true>(a, nslot, stream, grid, smem, st);
+    } else if (a.cem_mu) {
         // the cross-entropy search runs the 3-term split only
         if (split != 3) return cudaErrorInvalidValue;
         if (N.s <= 8) e = launch_tc_shape<3, 8, true>(a, nslot, stream, grid, smem, st);

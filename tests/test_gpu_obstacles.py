@@ -1,0 +1,116 @@
+"""The pushing-with-obstacles cost (Appendix D.4, Eq. pushing_cost) on the GPU against the oracle: the FP32
+cross-entropy search bit-exact (its decisions are taken on the FP32 objective), rollouts by value, the interval and
+CROWN bounds close to the oracle's and never above them beyond rounding, the FP64 incumbent, and the refusals of
+the paths that do not carry this cost."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_09584_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture
+def obst(oracle, gp):
+    """A pushing-scale problem with the obstacle cost set on both sides."""
+    from paper_2412_09584_gb300 import binding as B
+
+    def make(name="pushing", seed=71, H=None, lam=10.0, n_obs=3):
+        p = W.config_problem(name, seed)
+        if H is not None:
+            p = dict(p, H=H)
+        c = W.obstacle_cost(p["H"], seed, n_obs=n_obs, lam=lam)
+        # the oracle takes the parameters the GPU holds (FP32)
+        f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)
+        oracle.set_cost(1, f32(c["w"]), float(f32(c["lam"])), f32(c["obstacles"]), f32(c["p0"]))
+        g = gp(p)
+        B.bab_set_cost(g.ctx, B.COST_PUSHING_OBSTACLES, c["w"], c["lam"], c["obstacles"], c["p0"])
+        return p, g
+    yield make
+    oracle.set_cost(0)
+
+
+def test_obstacle_cem_fp32_bit_exact(oracle, obst):
+    from gpu_util import DEV, T, ids_t
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst()
+    lo, hi, ids = W.random_boxes(40, 4, seed=72, min_width=0.3, max_width=2.0)
+    ub = torch.empty(4, device=DEV)
+    bu = torch.empty(4, 40, device=DEV)
+    B.bab_rollout_cem(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), ids_t(ids), 4, 48, 3, 6, 1e-3, 5, B.PREC_FP32,
+                      ub, bu)
+    torch.cuda.synchronize()
+    ub_o, bu_o = oracle.cem(p, lo, hi, ids, 48, 3, 6, 1e-3, 5)
+    assert np.array_equal(ub.cpu().numpy().view(np.uint32), ub_o.view(np.uint32))
+    assert np.array_equal(bu.cpu().numpy().view(np.uint32), bu_o.view(np.uint32))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_obstacle_rollout_values_and_incumbent(oracle, obst, precision):
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst()
+    lo, hi, ids = W.random_boxes(40, 8, seed=73, min_width=0.5, max_width=2.0)
+    prec = B.PREC_FP32 if precision == "fp32" else B.PREC_BF16X3
+    r = g.rollout(lo, hi, ids, M=128, seed=9, precision=prec, incumbent=True)
+    ub_o, _, _ = oracle.rollout(p, lo, hi, ids, 128, 9)
+    f = np.array([oracle.objective(p, r["best_u"][i].astype(np.float64)) for i in range(8)])
+    np.testing.assert_allclose(r["ub"], f, rtol=2e-6)
+    np.testing.assert_allclose(r["ub"], ub_o, rtol=2e-6)   # the same samples; the minimum within rounding
+    best = int(np.argmin(r["ub"]))
+    assert r["inc_val"] == pytest.approx(f[best], rel=1e-10)   # FP64 on both sides, in different orders
+
+
+def test_obstacle_bounds_against_oracle(oracle, obst):
+    """Interval and CROWN bounds: at most the oracle's exact ones (plus rounding), and close to them."""
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst(H=8, n_obs=4, lam=20.0)
+    lo, hi, _ = W.random_boxes(16, 24, seed=74, min_width=0.02, max_width=0.6)
+    n = 24
+    c_o = oracle.crown(p, lo, hi)
+    lb_ibp_o = oracle.ibp(p, lo, hi)[0]
+    scale = np.maximum(c_o["scale"], 1.0)
+    lb_c = torch.empty(n, device=DEV)
+    margin = torch.empty(n, device=DEV)
+    B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, lb_c, margin=margin)
+    lb_i = torch.empty(n, device=DEV)
+    B.bab_bound_ibp(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, lb_i)
+    torch.cuda.synchronize()
+    lb_c, lb_i = lb_c.cpu().numpy().astype(np.float64), lb_i.cpu().numpy().astype(np.float64)
+    assert np.all(lb_c <= c_o["lb"] + 1e-6 * scale)
+    assert np.all(lb_c >= c_o["lb"] - 1e-4 * scale)
+    ibp_scale = np.maximum(np.abs(lb_ibp_o), 1.0)
+    assert np.all(lb_i <= lb_ibp_o + 1e-6 * ibp_scale)
+    assert np.all(lb_i >= lb_ibp_o - 1e-4 * ibp_scale)
+    # sound against sampled objectives
+    rng = np.random.default_rng(5)
+    for i in range(0, n, 6):
+        us = lo[i] + (hi[i] - lo[i]) * rng.uniform(size=(200, 16))
+        fmin = min(oracle.objective(p, u) for u in us)
+        assert lb_c[i] <= fmin and lb_i[i] <= fmin
+
+
+def test_obstacle_cost_refusals(obst):
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst(H=5)
+    lo, hi, ids = W.random_boxes(10, 3, seed=75)
+    lb = torch.empty(3, device=DEV)
+    with pytest.raises(B.BabError):
+        B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, precision=B.PREC_BF16X3)
+    with pytest.raises(B.BabError):
+        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, 2, 0.1, lb)
+    with pytest.raises(B.BabError):
+        g.rollout(lo, hi, ids, M=64, seed=1, precision=B.PREC_BF16)
+    with pytest.raises(B.BabError):   # horizon beyond the weights
+        B.bab_bound_crown(g.ctx, g.x0, g.goal, 6, g.rho, T(np.zeros((3, 12), np.float32)),
+                          T(np.ones((3, 12), np.float32)), 3, lb)
+    B.bab_set_cost(g.ctx, B.COST_SQUARED)   # back to the default: the same call now runs
+    B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, precision=B.PREC_BF16X3)
