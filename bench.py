@@ -133,7 +133,7 @@ class BabState:
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
                  alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None,
-                 heuristics=None, cem=None):
+                 heuristics=None, cem=None, cost=None):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -151,6 +151,9 @@ class BabState:
         self.rprec, self.bprec = PRECISIONS[rollout_prec], PRECISIONS[bound_prec]
         self.alpha_steps, self.alpha_lr = alpha_steps, alpha_lr
         self.ctx = B.bab_load_dynamics(self.p["dims"], self.p["params"], self.p["s"], self.p["k"])
+        if cost is not None:
+            # the pushing-with-obstacles state cost (Appendix D.4) instead of the squared distance
+            B.bab_set_cost(self.ctx, B.COST_PUSHING_OBSTACLES, cost["w"], cost["lam"], cost["obstacles"], cost["p0"])
         f = dict(device=device, dtype=torch.float32)
         self.x0 = torch.as_tensor(self.p["x0"]).to(**f)
         self.goal = torch.as_tensor(self.p["goal"]).to(**f)
@@ -406,6 +409,7 @@ def run_ours(args):
     heuristics = None if args.no_time_to_gap else heuristics_comparison(dev)
     cem_cmp = None if args.no_time_to_gap else cem_comparison(dev)
     synth = None if args.no_time_to_gap else synthetic_sweep(dev)
+    obst = None if args.no_time_to_gap else obstacle_bab(dev)
 
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
@@ -450,7 +454,7 @@ def run_ours(args):
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
            "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
            "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp,
-           "synthetic_objective": synth}
+           "synthetic_objective": synth, "obstacle_cost": obst}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -861,6 +865,45 @@ def synthetic_sweep(dev):
     out = {}
     for d, iters in ((10, 300), (30, 600), (100, 1000)):
         out[f"d{d}"] = synthetic_bab(dev, d=d, iters=iters, cem_iters=4, eta=0.25, levels=min(10, d))
+    return out
+
+
+def obstacle_bab(dev, iters=30):
+    """Algorithm 2 with the pushing-with-obstacles cost (Appendix D.4: weighted norm to the target, w_t = t / H,
+    plus lambda = 10 times the obstacle penalties of the pusher and the 4 keypoints; 3 obstacles) on the pushing
+    network: 512 children per iteration, 1024 BF16x3 rollouts each (uniform, or the warm-started cross-entropy
+    search 4 x 256 in FP32), sound FP32 interval + CROWN bounds."""
+    import torch
+    from paper_2412_09584_gb300 import workloads as W
+    p = W.config_problem("pushing", SEED)
+    cost = W.obstacle_cost(p["H"], SEED)
+    out = {"workload": "pushing network, H=20, 3 obstacles, lambda 10, w_t = t/H; sound FP32 bounds; "
+                       f"{iters} iterations",
+           "obstacles": [[round(v, 4) for v in o] for o in cost["obstacles"]]}
+    variants = (("uniform_bf16x3", dict(rollout_prec="bf16x3")),
+                ("cem_fp32_4x256", dict(rollout_prec="fp32", cem={"iters": 4, "elites": 10, "jitter": 1e-3})))
+    # one untimed pass first, so that no variant is timed while the clocks ramp up
+    for name, kw in (("warm-up", variants[0][1]),) + variants:
+        for warm in (True, False):
+            st = BabState("pushing", SEED, dev, 256, bound_prec="fp32", pool_iters=iters + 2, cost=cost, **kw)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            inc, gaps = [], []
+            for _ in range(2 if warm else iters):
+                st.step()
+                if not warm:
+                    g, _ = st.gap()
+                    inc.append(float(st.inc_val.item()))
+                    gaps.append(g)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t
+            n_live = int(st.counts[2].item())
+            status = st.B.bab_status(st.ctx)
+            st.close()
+        if name == "warm-up":
+            continue
+        out[name] = {"incumbent": inc[-1], "gap": gaps[-1], "incumbent_every_5": [round(v, 5) for v in inc[4::5]],
+                     "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters, "status": status}
     return out
 
 
