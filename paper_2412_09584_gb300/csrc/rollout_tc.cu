@@ -10,9 +10,9 @@
 //     output layer runs), writes the input row [u_t|x_t|0] (fixed columns;
 //     layer 1 of the weight image is permuted to match) to TMEM as the A
 //     operand of layer 1, and after the last layer adds the residual and the
-//     step cost.  After each hidden layer the
-//     warp pair of a lane quadrant reads the FP32 accumulator row from TMEM
-//     (one half of the columns each), adds the bias, applies ReLU and writes
+//     step cost.  After each hidden layer the warp pair of a lane quadrant
+//     reads the FP32 accumulator row from TMEM 16 columns at a time (one half
+//     of the columns each), adds the bias, applies ReLU and writes
 //     the next layer's A operand back to TMEM (as BF16, or as a BF16 hi/lo
 //     pair for the 3-term split).  No shared memory is written per layer.
 //   warps 8*NSLOT + s: issue every layer's MMAs of slot s (M=128, N = layer
@@ -79,7 +79,11 @@ __device__ __forceinline__ void raise_abort(int *status, volatile int *abort)
 // image does not fit in shared memory, or every tile needs its own problem's
 // image; per slot a producer warp streams it, one K-atom (64 inputs of one
 // layer, hi and lo halves) at a time, through the slot's ring of a.stages
-// buffers in the order the slot's MMA issuer consumes them.
+// buffers in the order the slot's MMA issuer consumes them.  CEM: samples
+// from the cross-entropy search's per-box normal (cem_sample) instead of
+// uniform draws.  OBST: the pushing-with-obstacles state cost (the pusher
+// position kept beside the state).  Each is a separate instance, so that the
+// plain kernel carries none of their code.
 template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM, bool OBST>
 __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0)) * 32, 1) k_rollout_tc(RolloutArgs a)
 {

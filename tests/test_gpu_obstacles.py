@@ -114,3 +114,33 @@ def test_obstacle_cost_refusals(obst):
                           T(np.ones((3, 12), np.float32)), 3, lb)
     B.bab_set_cost(g.ctx, B.COST_SQUARED)   # back to the default: the same call now runs
     B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, precision=B.PREC_BF16X3)
+
+
+def test_set_cost_argument_errors(gp):
+    from paper_2412_09584_gb300 import binding as B
+    g = gp(W.config_problem("manip", 76))           # k = 4: not a planar pusher
+    with pytest.raises(B.BabError):
+        B.bab_set_cost(g.ctx, B.COST_PUSHING_OBSTACLES, np.ones(40), 1.0, [(0, 0, 1)], (0, 0))
+    g = gp(W.config_problem("tiny", 76))
+    with pytest.raises(B.BabError):
+        B.bab_set_cost(g.ctx, 7, np.ones(5), 1.0, [(0, 0, 1)], (0, 0))          # unknown kind
+    with pytest.raises(B.BabError):
+        B.bab_set_cost(g.ctx, B.COST_PUSHING_OBSTACLES, np.ones(5), 1.0, [(0, 0, 1)] * 9, (0, 0))  # too many
+    with pytest.raises(B.BabError):
+        B.bab_set_cost(g.ctx, B.COST_PUSHING_OBSTACLES, -np.ones(5), 1.0, [(0, 0, 1)], (0, 0))     # w < 0
+    B.bab_set_cost(g.ctx, B.COST_PUSHING_OBSTACLES, np.ones(5), 1.0, [], (0, 0))                 # no obstacles
+
+
+def test_obstacle_cost_empty_batch(obst):
+    """n = 0 is a no-op on every supported path."""
+    from gpu_util import DEV, T, ids_t
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst(H=5)
+    e = torch.empty(0, 10, device=DEV)
+    z = torch.empty(0, device=DEV)
+    B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, e, e, 0, z)
+    B.bab_bound_ibp(g.ctx, g.x0, g.goal, g.H, g.rho, e, e, 0, z)
+    B.bab_rollout(g.ctx, g.x0, g.goal, g.H, g.rho, e, e, torch.empty(0, dtype=torch.int64, device=DEV), 0, 64, 1,
+                  B.PREC_FP32, z, e)
+    torch.cuda.synchronize()
+    assert B.bab_status(g.ctx) == 0

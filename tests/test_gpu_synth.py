@@ -134,3 +134,23 @@ def test_synth_bab_reaches_the_optimum(sctx):
     assert inc == pytest.approx(d * G_STAR, abs=5e-3)
     assert lbmin <= d * G_STAR + 1e-6
     assert B.bab_status(sctx) == 0
+
+
+def test_synth_argument_errors_and_empty(sctx):
+    from gpu_util import DEV, T, ids_t
+    from paper_2412_09584_gb300 import binding as B
+    lo, hi, ids = W.random_boxes(4, 2, seed=54)
+    ub, bu = torch.empty(2, device=DEV), torch.empty(2, 4, device=DEV)
+    for M, iters, E in ((B.CEM_MAX_SAMPLES + 1, 0, 1), (16, 2, 17), (16, -1, 4)):
+        with pytest.raises(B.BabError):
+            B.bab_synth_search(sctx, 4, T(lo), T(hi), ids_t(ids), 2, M, 1, ub, bu, iters=iters, elites=E)
+    e = torch.empty(0, 4, device=DEV)
+    B.bab_synth_search(sctx, 4, e, e, torch.empty(0, dtype=torch.int64, device=DEV), 0, 16, 1,
+                       torch.empty(0, device=DEV), e)
+    B.bab_synth_bound(sctx, 4, e, e, 0, torch.empty(0, device=DEV))
+    # a context without a network refuses the network calls
+    lb = torch.empty(2, device=DEV)
+    with pytest.raises(B.BabError):
+        B.bab_bound_crown(sctx, T(np.zeros(4)), T(np.zeros(4)), 2, 0.0, T(lo), T(hi), 2, lb)
+    torch.cuda.synchronize()
+    assert B.bab_status(sctx) == 0
