@@ -112,6 +112,7 @@ __device__ __forceinline__ void ibp_dense(const float *__restrict__ alo, const f
                 accs[i][j] = 0.f;
             }
         }
+        const bool full = (c0 + TN <= Np);
         for (int k = 0; k < Kp; k += 4) {
             float4 l4[TR], h4[TR];
 #pragma unroll
@@ -122,8 +123,21 @@ __device__ __forceinline__ void ibp_dense(const float *__restrict__ alo, const f
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 float w[TN];
+                const float *wr = Wt + (size_t)(k + kk) * Np + c0;
+                if (full && TN % 4 == 0) {
+                    // whole 16-byte groups (Np and c0 are multiples of 4)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) w[j] = (c0 + j < Np) ? Wt[(size_t)(k + kk) * Np + c0 + j] : 0.f;
+                    for (int j = 0; j < TN; j += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(wr + j);
+                        w[j] = q.x;
+                        w[j + 1] = q.y;
+                        w[j + 2] = q.z;
+                        w[j + 3] = q.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) w[j] = (c0 + j < Np) ? wr[j] : 0.f;
+                }
 #pragma unroll
                 for (int i = 0; i < TR; ++i) {
                     const float al = kk == 0 ? l4[i].x : kk == 1 ? l4[i].y : kk == 2 ? l4[i].z : l4[i].w;
