@@ -414,6 +414,7 @@ def run_ours(args):
     inc = float(st.inc_val.item())
     st.close()
     ttg = None if args.no_time_to_gap else time_to_gap(dev)
+    tiny = None if args.no_time_to_gap else tiny_latency(dev)
     batched = None if args.no_batched else batched_bab(dev)
     manip = None if args.no_manip else manip_scale(dev)
     paper_bounds = None if args.no_time_to_gap else paper_bounding_comparison(dev)
@@ -465,7 +466,7 @@ def run_ours(args):
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
            "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
            "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp,
-           "synthetic_objective": synth, "obstacle_cost": obst}
+           "synthetic_objective": synth, "obstacle_cost": obst, "tiny_latency": tiny}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
@@ -915,6 +916,42 @@ def obstacle_bab(dev, iters=30):
             continue
         out[name] = {"incumbent": inc[-1], "gap": gaps[-1], "incumbent_every_5": [round(v, 5) for v in inc[4::5]],
                      "live_pool_end": n_live, "ms_per_iteration": 1e3 * sec / iters, "status": status}
+    return out
+
+
+def tiny_latency(dev, reps=200):
+    """Configuration 1 (the small sanity case): MLP 6-32-32-4, H = 5, 64 children per iteration (32 picked),
+    256 FP32 rollouts each, FP32 interval + CROWN bounds.  Latency-bound: microseconds per BaB iteration as a
+    CUDA-graph replay (and as eager launches), inputs resident."""
+    import torch
+    out = {"workload": "tiny: MLP 6-32-32-4, H=5, 64 children per iteration, 256 FP32 rollouts each, FP32 bounds"}
+    st = BabState("tiny", SEED, dev, 32, "fp32", "fp32", fixed_launch=True, pool_iters=2 * reps + 64)
+    for _ in range(3):
+        st.step()
+    graphs = capture_graphs(st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        graphs[st.cur].replay()
+        st.cur ^= 1
+    e1.record()
+    torch.cuda.synchronize()
+    out["us_per_iteration_graph"] = 1e3 * e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps // 4):
+        st.step()
+    e1.record()
+    torch.cuda.synchronize()
+    out["us_per_iteration_eager"] = 1e3 * e0.elapsed_time(e1) / (reps // 4)
+    for _ in range(5):
+        st.step(events=True)
+    torch.cuda.synchronize()
+    out["us_rollout"] = 1e3 * float(np.mean([e[0].elapsed_time(e[1]) for e in st.ev[-5:]]))
+    out["us_bound"] = 1e3 * float(np.mean([e[1].elapsed_time(e[2]) for e in st.ev[-5:]]))
+    out["launches_per_iteration"] = st.launches_per_step
+    out["status"] = st.B.bab_status(st.ctx)
+    st.close()
     return out
 
 
