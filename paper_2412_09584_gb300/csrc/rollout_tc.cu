@@ -390,10 +390,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             tc::fence_after_sync();
             bool passed = false;  // the turn handed to the other slot
             const int Kl = N.tc_K[l], Nl = N.tc_N[l];
+            const int kpass = (Kl / 16 + 1) / 2;  // the other slot may start once half of this layer is issued
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
             if (!STREAM) {
                 const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
-                const int kpass = (Kl / 16 + 1) / 2;  // the other slot may start once half of this layer is issued
                 for (int ks = 0; ks < Kl / 16; ++ks) {
                     const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
                     const uint64_t dh = tc::desc_sw128(bh + boff);
@@ -427,6 +427,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                         if (SPLIT == 3) {
                             tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + (uint32_t)kk * 32u), idesc, 1u);
                             tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                        }
+                        if (NSLOT == 2 && ks + 1 == kpass) {
+                            tc::mbar_arrive(&bar_tok[sl]);
+                            passed = true;
                         }
                     }
                     tc::mma_commit(&empty[st]);  // the buffer is free once these MMAs have read it
