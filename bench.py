@@ -85,10 +85,18 @@ class ClockSampler:
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file,
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.file,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # nvidia-smi takes a while to start: wait (at most 5 s) for its first row so the samples cover the
+        # whole timed region that follows
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.file.name) > 0:
+                break
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
@@ -331,8 +339,8 @@ def capture_graphs(st):
 # DRAM bytes (read + write) per launch of the BF16x3 tensor-core rollout at 4096 boxes x 1024 samples, from one
 # ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel sources it
 # was taken on, so it is reported only while their digest (comments and whitespace removed) matches.
-ROLLOUT_TC_TRAFFIC = {"bytes": 1949952, "precision": "bf16x3", "boxes": 4096, "samples": 1024,
-                      "sources_sha1": "7246d1f51936605247ee435783ddef60b53c0bcd"}
+ROLLOUT_TC_TRAFFIC = {"bytes": 1993472, "precision": "bf16x3", "boxes": 4096, "samples": 1024,
+                      "sources_sha1": "6920cf61011d967fc985ea581306d114f3722e4a"}
 ROLLOUT_TC_SOURCES = ("rollout_tc.cu", "tc_ptx.cuh", "kernels.cuh", "bab_internal.cuh")
 
 
