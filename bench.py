@@ -1033,22 +1033,78 @@ def oracle_sample_step(problem, lo, hi, ids, M, n_roll, n_bound, pool_n, n_pick)
     return t_roll, t_bound, t_prune
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker_init():
+    from oracle import oracle as O
+    O.lib()
+
+
+def _oracle_boxes(job):
+    """One worker's share of the all-cores baseline: the oracle's rollouts and CROWN bounds of a few boxes."""
+    problem, lo, hi, ids, M = job
+    from oracle import oracle as O
+    O.rollout(problem, lo, hi, ids, M, SEED)
+    O.crown(problem, lo, hi)
+    return lo.shape[0]
+
+
+def oracle_pool(cores):
+    """A pool of `cores` fresh interpreters (spawned, so it is safe after CUDA is initialised), warmed up."""
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_worker_init)
+    pool.map(abs, range(cores))
+    return pool
+
+
+def oracle_boxes_parallel(pool, cores, problem, lo, hi, ids, M, per_worker):
+    """Wall seconds for `cores` workers to search and bound `per_worker` distinct boxes each."""
+    jobs = [(problem, lo[w * per_worker:(w + 1) * per_worker], hi[w * per_worker:(w + 1) * per_worker],
+             ids[w * per_worker:(w + 1) * per_worker], M) for w in range(cores)]
+    t = time.perf_counter()
+    done = sum(pool.map(_oracle_boxes, jobs))
+    assert done == cores * per_worker
+    return time.perf_counter() - t
+
+
 def cpu_baseline(budget_s=20.0, n_pick=2048):
+    """The FP64 oracle, as it stands, on the host: one process over every host core (independent boxes split
+    across spawned workers), and one thread; bounded samples scaled to one iteration of 2 n_pick children."""
     from paper_2412_09584_gb300 import workloads as W
     c = W.CONFIGS["pushing"]
     p = W.config_problem("pushing", SEED)
     lo, hi, ids = W.grid_boxes(c["H"] * p["k"], c["grid_dims"])
     # calibrate on one box, then size the sample to the budget
     t_roll, t_bound, t_prune = oracle_sample_step(p, lo, hi, ids, c["samples"], 1, 4, 4096, n_pick)
-    n_roll = max(1, min(64, int(0.7 * budget_s / max(t_roll, 1e-6))))
-    n_bound = max(4, min(4096, int(0.2 * budget_s / max(t_bound, 1e-6))))
+    single_budget = 0.5 * budget_s
+    n_roll = max(1, min(64, int(0.7 * single_budget / max(t_roll, 1e-6))))
+    n_bound = max(4, min(4096, int(0.2 * single_budget / max(t_bound, 1e-6))))
     t_roll, t_bound, t_prune = oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 4096 + n_pick,
                                                   n_pick)
     step_s = 2 * n_pick * (t_roll + t_bound) + t_prune
-    return {"value": 2 * n_pick / step_s, "unit": "subdomain-bounds/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, single thread: rollouts of {n_roll} boxes x {c['samples']} samples x H={c['H']}, "
-                      f"CROWN of {n_bound} boxes, prune/branch of a {4096 + n_pick}-box pool; per-box times scaled to "
-                      f"one {2 * n_pick}-box iteration ({step_s:.1f} s)"}
+    single = {"value": 2 * n_pick / step_s, "cores": 1,
+              "sample": f"rollouts of {n_roll} boxes x {c['samples']} samples x H={c['H']}, CROWN of {n_bound} "
+                        f"boxes, prune/branch of a {4096 + n_pick}-box pool; per-box times scaled to one "
+                        f"{2 * n_pick}-box iteration ({step_s:.1f} s)"}
+    cores = host_cores()
+    per_worker = max(1, min(lo.shape[0] // cores, int(0.5 * budget_s / max(t_roll + t_bound, 1e-6))))
+    pool = oracle_pool(cores)
+    try:
+        wall = oracle_boxes_parallel(pool, cores, p, lo, hi, ids, c["samples"], per_worker)
+    finally:
+        pool.close()
+        pool.join()
+    step_all = 2 * n_pick * wall / (cores * per_worker) + t_prune
+    return {"value": 2 * n_pick / step_all, "unit": "subdomain-bounds/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 C oracle in {cores} spawned processes: {cores} x {per_worker} distinct boxes, each "
+                      f"{c['samples']} rollouts of H={c['H']} then CROWN ({wall:.1f} s wall), plus one prune/branch of "
+                      f"a {4096 + n_pick}-box pool; scaled to one {2 * n_pick}-box iteration ({step_all:.1f} s)",
+            "single_thread": single}
 
 
 def run_reference(args):
@@ -1061,23 +1117,41 @@ def run_reference(args):
     c = W.CONFIGS["pushing"]
     p = W.config_problem("pushing", SEED)
     lo, hi, ids = W.grid_boxes(c["H"] * p["k"], c["grid_dims"])
-    n_roll, n_bound = 2, 2
-    for _ in range(args.warmup):
-        oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 1024, args.boxes // 2)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_sample_step(p, lo, hi, ids, c["samples"], n_roll, n_bound, 1024, args.boxes // 2)
-    sec = (time.perf_counter() - t) / args.steps
-    value = n_bound / sec
-    sample = (f"per step: FP64 C oracle on {n_roll} boxes (1024 rollouts of H=20 each, then CROWN) and prune/branch "
-              f"of a 1024-box pool, single thread")
+    # one box per host core per step (independent boxes in spawned workers), then prune/branch in this process
+    cores = host_cores()
+    pool = oracle_pool(cores)
+    rng = np.random.default_rng(0)
+    pool_n = 1024
+    lb = rng.normal(10, 3, pool_n).astype(np.float32)
+    ub = (lb + 1).astype(np.float32)
+    plo, phi = lo[:pool_n], hi[:pool_n]
+    pid = np.arange(1, pool_n + 1, dtype=np.uint64)
+
+    def step(i):
+        off = (i * cores) % (lo.shape[0] - cores)
+        oracle_boxes_parallel(pool, cores, p, lo[off:], hi[off:], ids[off:], c["samples"], 1)
+        O.prune_branch(plo, phi, lb, ub, pid, 11.0, args.boxes // 2)
+
+    try:
+        for i in range(args.warmup):
+            step(i)
+        t = time.perf_counter()
+        for i in range(args.steps):
+            step(args.warmup + i)
+        sec = (time.perf_counter() - t) / args.steps
+    finally:
+        pool.close()
+        pool.join()
+    value = cores / sec
+    sample = (f"per step: FP64 C oracle on {cores} boxes, one per spawned process (1024 rollouts of H=20 each, then "
+              f"CROWN), and prune/branch of a {pool_n}-box pool")
     cfg = {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
                        "rho=0.01, 1024 uniform rollouts per child (bounded sample per step)",
-           "boxes_per_step": n_bound, "samples_per_box": c["samples"], "H": c["H"]}
+           "boxes_per_step": cores, "samples_per_box": c["samples"], "H": c["H"]}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "subdomain-bounds/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-           "cpu_baseline": {"value": value, "unit": "subdomain-bounds/s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": "subdomain-bounds/s", "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": "subdomain-bounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
