@@ -28,7 +28,7 @@
 
 namespace bab {
 
-constexpr int RB = 32;  // boxes per CTA: 4096 boxes fill one wave of 128 CTAs (16 boxes took 1.7 waves)
+constexpr int RB = 28;  // boxes per CTA: 4096 boxes make 147 CTAs, one wave on 152 SMs (32 left 24 SMs idle)
 constexpr int NT = 512;
 constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20): twice the unit roundoff, rounded up
 
