@@ -421,15 +421,17 @@ def run_ours(args):
     e2e = run_e2e(st, args.steps)
     inc = float(st.inc_val.item())
     st.close()
-    ttg = None if args.no_time_to_gap else time_to_gap(dev)
-    tiny = None if args.no_time_to_gap else tiny_latency(dev)
-    batched = None if args.no_batched else batched_bab(dev)
-    manip = None if args.no_manip else manip_scale(dev)
-    paper_bounds = None if args.no_time_to_gap else paper_bounding_comparison(dev)
-    heuristics = None if args.no_time_to_gap else heuristics_comparison(dev)
-    cem_cmp = None if args.no_time_to_gap else cem_comparison(dev)
-    synth = None if args.no_time_to_gap else synthetic_sweep(dev)
-    obst = None if args.no_time_to_gap else obstacle_bab(dev)
+    # the single-GPU comparisons run at N = 1 only (a multi-rank run reports the scaled iteration alone)
+    extra = ws == 1
+    ttg = time_to_gap(dev) if extra and not args.no_time_to_gap else None
+    tiny = tiny_latency(dev) if extra and not args.no_time_to_gap else None
+    batched = batched_bab(dev) if extra and not args.no_batched else None
+    manip = manip_scale(dev) if extra and not args.no_manip else None
+    paper_bounds = paper_bounding_comparison(dev) if extra and not args.no_time_to_gap else None
+    heuristics = heuristics_comparison(dev) if extra and not args.no_time_to_gap else None
+    cem_cmp = cem_comparison(dev) if extra and not args.no_time_to_gap else None
+    synth = synthetic_sweep(dev) if extra and not args.no_time_to_gap else None
+    obst = obstacle_bab(dev) if extra and not args.no_time_to_gap else None
 
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
@@ -475,7 +477,7 @@ def run_ours(args):
            "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
            "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp,
            "synthetic_objective": synth, "obstacle_cost": obst, "tiny_latency": tiny}
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
     if ws > 1:
