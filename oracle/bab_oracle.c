@@ -867,8 +867,11 @@ int oracle_crown_given(int L, const int *dims, const double *params, int s, int 
  * z_j the neuron's pre-activation in the relaxed network at u*.  Hence
  *   dLB/dalpha_j = A_j * z~_j(u*)   (unstable neurons whose lower bound was
  *                                    selected), 0 otherwise.
- * relaxed_obj (nullable) receives the relaxed network's objective at u*, which
- * must equal lb.
+ * The argument holds for any cost relaxation that is linear in the states and
+ * actions, the pushing-with-obstacles one included (its tangent plane and
+ * penalty pieces do not depend on alpha).  relaxed_obj (nullable) receives the
+ * relaxed network's objective at u*, which must equal lb; it is written out
+ * for the squared-distance cost only (NaN for the obstacle cost).
  */
 int oracle_alpha_grad(int L, const int *dims, const double *params, int s, int k, int H, double rho,
                       const double *x0, const double *goal, int n, const double *lo, const double *hi,
@@ -929,7 +932,7 @@ int oracle_alpha_grad(int L, const int *dims, const double *params, int s, int k
                 obj += 2.0 * m * (x[q] - goal[q]) - m * m;
             }
         }
-        if (relaxed_obj) relaxed_obj[i] = obj;
+        if (relaxed_obj) relaxed_obj[i] = g_cost.kind == 0 ? obj : NAN;
     }
     free(pl);
     free(pu);

@@ -198,7 +198,8 @@ def crown(problem, lo, hi, alpha=None):
 
 
 def alpha_grad(problem, lo, hi, alpha=None):
-    """(lb, dlb/dalpha [n,H,sumh], relaxed-network objective at u*) per box."""
+    """(lb, dlb/dalpha [n,H,sumh], relaxed-network objective at u*) per box; the relaxed objective is NaN for
+    the obstacle cost."""
     net, keep, (cH, crho, px0, pg) = _prob(problem)
     lo, plo = _d(lo)
     hi, phi = _d(hi)

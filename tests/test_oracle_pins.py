@@ -380,8 +380,26 @@ def test_alpha_gradient_central_fd(oracle):
     # weights and box sized so that the bound is O(1): the stencil difference is then far above FP64 rounding
     p = scaled_problem(4, 2, [32, 32], 5, 0.01, seed=51, scale=0.3)
     lo, hi, _ = W.random_boxes(10, 4, seed=52, min_width=0.5, max_width=1.0)
-    rng = np.random.default_rng(7)
-    alpha = rng.uniform(0.05, 0.95, size=(4, 5, 64))
+    _alpha_fd_check(oracle, p, lo, hi, 7)
+
+
+def test_alpha_gradient_central_fd_obstacle_cost(oracle, obstacle_cost):
+    """The same pin with the pushing-with-obstacles cost (Appendix D.4): its relaxation is linear in the states and
+    actions and does not depend on the slopes, so dLB/dalpha = A_j z~_j still holds."""
+    p = scaled_problem(4, 2, [32, 32], 5, 0.01, seed=53, scale=0.3)
+    lo, hi, _ = W.random_boxes(10, 4, seed=54, min_width=0.5, max_width=1.0)
+    lb_sq = oracle.crown(p, lo, hi)["lb"]
+    obstacle_cost(5, 53, n_obs=3, lam=10.0)
+    lb_obs = _alpha_fd_check(oracle, p, lo, hi, 9)
+    assert not np.allclose(lb_obs, lb_sq)   # the bound is the obstacle cost's, not the squared distance's
+
+
+def _alpha_fd_check(oracle, p, lo, hi, seed):
+    """The oracle's alpha gradient against central differences of its own bound on 16 coordinates (kinks
+    skipped); exact zeros where a slope is unused.  Returns the bound."""
+    rng = np.random.default_rng(seed)
+    n, H, sumh = lo.shape[0], p["H"], sum(p["dims"][1:-1])
+    alpha = rng.uniform(0.05, 0.95, size=(n, H, sumh))
     lb, g, _ = oracle.alpha_grad(p, lo, hi, alpha)
     Ap = oracle.crown(p, lo, hi, alpha)["A_pre"]
     _, pl, pu, _, _ = oracle.ibp(p, lo, hi)
@@ -414,6 +432,7 @@ def test_alpha_gradient_central_fd(oracle):
         if checked == 16:
             break
     assert checked == 16
+    return lb
 
 
 # --------------------------------------------------------------------------
