@@ -394,10 +394,13 @@ int bab_rollout_split(bab_ctx *ctx, const float *x0, const float *goal, int hori
  * device copy; kind BAB_COST_SQUARED clears it.
  *
  * Paths that support the obstacle cost: bab_rollout (FP32, and BF16X3 for
- * s <= 8), bab_rollout_cem (FP32), bab_update_incumbent, bab_bound_ibp and
- * bab_bound_crown (FP32, adaptive slopes); the other bound paths (alpha
- * steps, tensor-core CROWN, early stop, batched problems, the static entry
- * point, the box gradient) and BF16 rollouts return BAB_ERR_UNSUPPORTED.
+ * s <= 8), bab_rollout_cem (FP32), bab_update_incumbent, bab_bound_ibp,
+ * bab_bound_crown (FP32, adaptive or given slopes), bab_alpha_init and the
+ * FP32 alpha calls (bab_alpha_grad, bab_alpha_step, bab_alpha_optimize; the
+ * optimisation then runs as separate launches or in the shared-memory tiles,
+ * not as the warp-per-box loop); the other bound paths (tensor-core CROWN and
+ * alpha, early stop, batched problems, the static entry point, the box
+ * gradient) and BF16 rollouts return BAB_ERR_UNSUPPORTED.
  * Sound as for the squared cost: interval minima per term rounded down; in
  * CROWN the norm by its tangent plane at the box centre (w ||y|| >= w ghat . y,
  * |ghat| <= 1), each penalty by an affine function below the concave
@@ -561,7 +564,9 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  *                            all per-box state in shared memory (small
  *                            networks and horizons only: BAB_ERR_UNSUPPORTED
  *                            otherwise); 3 (and -1): one launch, one warp per
- *                            box, per-box state in global memory.
+ *                            box, per-box state in global memory (squared-
+ *                            distance cost only: with the obstacle cost -1
+ *                            takes the separate launches and 3 is refused).
  *   BAB_KERNEL_ROLLOUT_TC    1 or 2 sample tiles per CTA.
  *   BAB_KERNEL_CROWN_TC      1 or 2 box tiles per CTA.
  * -1 selects the built-in heuristic everywhere.  bab_set_variant returns

@@ -945,8 +945,6 @@ int bab_alpha_init(bab_ctx *c, const float *x0, const float *goal, int H, float 
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    rc = refuse_obstacles(c, "the alpha slopes");
-    if (rc) return rc;
     if (n > 0 && !alpha) return fail(c, BAB_ERR_INVALID_ARG, "alpha is required");
     if (n == 0) return BAB_OK;
     rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, false));
@@ -1014,8 +1012,8 @@ int bab_alpha_grad(bab_ctx *c, const float *x0, const float *goal, int H, float 
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    rc = refuse_obstacles(c, "the alpha gradient");
-    if (rc) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha gradient")) != BAB_OK)
+        return rc;
     if (n > 0 && (!alpha || !lb || !grad_alpha)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, lb and grad are required");
     rc = check_bound_precision(c, precision);
     if (rc) return rc;
@@ -1034,8 +1032,8 @@ int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float 
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    rc = refuse_obstacles(c, "the alpha step");
-    if (rc) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha step")) != BAB_OK)
+        return rc;
     if (n > 0 && (!alpha || !adam_m || !adam_v)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, m and v are required");
     if (step < 1) return fail(c, BAB_ERR_INVALID_ARG, "step counts from 1");
     if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
@@ -1096,8 +1094,8 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    rc = refuse_obstacles(c, "the alpha optimisation");
-    if (rc) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha optimisation")) != BAB_OK)
+        return rc;
     if (n > 0 && !lb_best) return fail(c, BAB_ERR_INVALID_ARG, "lb_best is required");
     if (steps < 1 || steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "steps must be in [1, 100000]");
     if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
@@ -1126,7 +1124,11 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
     }
     float *al = alpha ? alpha : cv.take<float>(nh);
     float *m = cv.take<float>(nh), *v = cv.take<float>(nh);
-    if (precision == BAB_PREC_FP32 && (fv == -1 || fv == 3)) {
+    // the warp-per-box loop has the squared-distance cost only: with the obstacle cost the heuristic choice (-1)
+    // takes the separate launches and an explicit request (3) is refused
+    if (precision == BAB_PREC_FP32 && fv == 3 && (rc = refuse_obstacles(c, "the warp-per-box alpha loop")) != BAB_OK)
+        return rc;
+    if (precision == BAB_PREC_FP32 && (fv == -1 || fv == 3) && c->cost.kind == 0) {
         // the whole loop in one launch, one warp per box
         a.A_pre = cv.take<float>(nh);
         a.lb_best = lb_best;

@@ -97,6 +97,59 @@ def test_obstacle_bounds_against_oracle(oracle, obst):
         assert lb_c[i] <= fmin and lb_i[i] <= fmin
 
 
+def test_obstacle_alpha_gradient_and_step(oracle, obst):
+    """alpha-CROWN with the obstacle cost: the adjoint gradient at the adaptive slopes and the bound against the
+    oracle's, and Adam's first step."""
+    p, g = obst(name="tiny", seed=77)
+    lo, hi, _ = W.random_boxes(10, 24, seed=78, min_width=0.3, max_width=1.0)
+    best, alpha, hist = g.alpha_steps(lo, hi, steps=1, lr=0.1)
+    a0 = oracle.adaptive_alpha(p, lo, hi)
+    lb_o, grad_o, _ = oracle.alpha_grad(p, lo, hi, a0)
+    gs = np.maximum(np.abs(grad_o).max(axis=(1, 2), keepdims=True), 1e-30)
+    assert np.all(np.abs(hist[0]["grad"] - grad_o) <= 1e-4 * gs)
+    scale = np.maximum(oracle.crown(p, lo, hi, a0)["scale"], 1.0)
+    assert np.all(np.abs(hist[0]["lb"] - lb_o) <= 1e-5 * scale)
+    assert np.all(hist[0]["lb"] <= lb_o + 1e-12 * np.abs(lb_o))
+    a = a0.copy()
+    m, v = np.zeros_like(a), np.zeros_like(a)
+    oracle.adam_ascent(a, m, v, grad_o, 1, 0.1)
+    clear = np.abs(grad_o) > 1e-3 * gs
+    assert clear.sum() > 0
+    np.testing.assert_allclose(alpha[clear], a[clear], atol=1e-5)
+
+
+def test_obstacle_alpha_optimize(oracle, obst):
+    """bab_alpha_optimize with the obstacle cost: the one-call loop (separate launches, or the shared-memory tile)
+    bit-identical to repeated bab_alpha_step; the best bound at least the adaptive CROWN bound (up to rounding)
+    and below the objective at sampled points."""
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst(name="tiny", seed=79)
+    n = 40
+    lo, hi, _ = W.random_boxes(10, n, seed=80, min_width=0.2, max_width=1.5)
+    steps = 20
+    ref, _, _ = g.alpha_steps(lo, hi, steps=steps, lr=0.1)
+    outs = []
+    for variant in (-1, -2, 0):
+        B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, variant)
+        lb_best = torch.empty(n, device=DEV)
+        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, steps, 0.1, lb_best)
+        torch.cuda.synchronize()
+        outs.append(lb_best.cpu().numpy())
+    for o in outs:
+        assert np.array_equal(o.view(np.uint32), ref.view(np.uint32))
+    B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, 3)   # the warp-per-box loop carries the squared distance only
+    with pytest.raises(B.BabError):
+        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, steps, 0.1, torch.empty(n, device=DEV))
+    lb0 = g.crown(lo, hi)["lb"]
+    assert np.all(ref >= lb0 - 1e-5 * np.maximum(np.abs(lb0), 1.0))
+    assert np.mean(ref > lb0) > 0.5
+    rng = np.random.default_rng(81)
+    for i in range(n):
+        us = lo[i] + (hi[i] - lo[i]) * rng.uniform(size=(100, 10))
+        assert ref[i] <= min(oracle.objective(p, u) for u in us)
+
+
 def test_obstacle_cost_refusals(obst):
     from gpu_util import DEV, T
     from paper_2412_09584_gb300 import binding as B
@@ -106,7 +159,10 @@ def test_obstacle_cost_refusals(obst):
     with pytest.raises(B.BabError):
         B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, precision=B.PREC_BF16X3)
     with pytest.raises(B.BabError):
-        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, 2, 0.1, lb)
+        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, 2, 0.1, lb, precision=B.PREC_BF16X3)
+    with pytest.raises(B.BabError):
+        B.bab_box_grad(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, torch.empty(3, 10, device=DEV),
+                       torch.empty(3, 10, device=DEV))
     with pytest.raises(B.BabError):
         g.rollout(lo, hi, ids, M=64, seed=1, precision=B.PREC_BF16)
     with pytest.raises(B.BabError):   # horizon beyond the weights
