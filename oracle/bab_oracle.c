@@ -3,8 +3,8 @@
  * BaB-ND (branch-and-bound planning over neural dynamics, arXiv 2412.09584).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the checker, not the product: only
- * the test suite, the package's smoke() check and the CPU-baseline leg of the
- * benchmark may load it.  It shares no code, header, table or helper with the
+ * the test suite, the package's smoke() check and the CPU-baseline and
+ * reference legs of the benchmark may load it.  It shares no code, header, table or helper with the
  * CUDA library (paper_2412_09584_gb300/csrc), and the CUDA library never calls it.
  *
  * Everything is written as straight loops in double precision, in the order

@@ -1,8 +1,8 @@
 """Python face of the FP64 CPU oracle (``bab_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY.  The oracle is the checker for the CUDA library:
-only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import it.  It shares no code with the CUDA path.
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and reference
+(``--impl reference``) legs of ``bench.py`` may import it.  It shares no code with the CUDA path.
 
 Each function converts its numpy inputs to the C layout (float64 for real
 inputs; the FP32 boxes stay FP32 where the method fixes FP32 arithmetic, i.e.
