@@ -453,6 +453,15 @@ def run_ours(args):
                              " plus padding to multiples of 16"}
     roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
                  "traffic": rollout_traffic(args.precision, st.nb, st.M)})
+    if args.precision != "fp32":
+        # what the tensor pipe executes: each product split into 3 (or 1) BF16 MMAs, every layer padded to
+        # multiples of 16 (layer 1 reads the 8 action columns plus the state)
+        dims = st.p["dims"]
+        pad16 = lambda v: (v + 15) // 16 * 16
+        ex = sum(pad16(8 + st.p["s"] if l == 1 else dims[l - 1]) * pad16(dims[l]) for l in range(1, len(dims)))
+        ratio = (3 if args.precision == "bf16x3" else 1) * ex / macs
+        roof.update({"executed_per_algorithmic": ratio, "executed": achieved * ratio,
+                     "executed_frac": achieved * ratio / roof["peak"]})
     if rank != 0:
         return
     cfg = {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
