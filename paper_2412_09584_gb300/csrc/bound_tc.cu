@@ -369,13 +369,21 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
             const int Kl = N.tcb_K[l], Nl = N.tcb_N[l];
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
             if (!STREAM) {
-                const uint32_t bh = tc::smem_u32(wimg + N.tcb_hi[l]), blo = tc::smem_u32(wimg + N.tcb_lo[l]);
-                for (int ks = 0; ks < Kl / 16; ++ks) {
-                    const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
-                    const uint64_t dh = tc::desc_sw128(bh + boff);
-                    tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
-                    tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
-                    tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                // operands stepped with 32-bit adds on precomputed descriptor words, one K-atom unrolled
+                const int nks = Kl / 16;
+                const uint32_t atom = (uint32_t)Nl * 8u;
+                uint32_t qh = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_hi[l]));
+                uint32_t ql = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_lo[l]));
+                uint32_t th = ah, tl = al;
+                for (int ks0 = 0; ks0 < nks; ks0 += 4, qh += atom, ql += atom, th += 32u, tl += 32u) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        if (ks0 + kk >= nks) break;
+                        const uint64_t dh = tc::desc_join(qh + 2u * kk);
+                        tc::mma_ts(dcol, th + 8u * kk, dh, idesc, ks0 + kk > 0 ? 1u : 0u);
+                        tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(ql + 2u * kk), idesc, 1u);
+                        tc::mma_ts(dcol, tl + 8u * kk, dh, idesc, 1u);
+                    }
                 }
             } else {
                 bool ok = true;
@@ -386,14 +394,17 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                         ok = false;
                         break;
                     }
-                    const uint32_t bh = tc::smem_u32(wimg + (size_t)st * a.stage_bytes);
-                    const uint32_t blo = bh + (uint32_t)(Nl * 128);
-                    for (int kk = 0; kk < 4 && 4 * at + kk < Kl / 16; ++kk) {
+                    const uint32_t qh = tc::desc_sw128_lo(tc::smem_u32(wimg + (size_t)st * a.stage_bytes));
+                    const uint32_t ql = qh + (uint32_t)Nl * 8u;  // the lo half follows the hi half in the buffer
+                    const uint32_t th = ah + 32u * at, tl = al + 32u * at;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
                         const int ks = 4 * at + kk;
-                        const uint64_t dh = tc::desc_sw128(bh + (uint32_t)kk * 32u);
-                        tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
-                        tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + (uint32_t)kk * 32u), idesc, 1u);
-                        tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                        if (ks >= Kl / 16) break;
+                        const uint64_t dh = tc::desc_join(qh + 2u * kk);
+                        tc::mma_ts(dcol, th + 8u * kk, dh, idesc, ks > 0 ? 1u : 0u);
+                        tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(ql + 2u * kk), idesc, 1u);
+                        tc::mma_ts(dcol, tl + 8u * kk, dh, idesc, 1u);
                     }
                     tc::mma_commit(&bar_empty[st]);  // the buffer is free once these MMAs have read it
                 }

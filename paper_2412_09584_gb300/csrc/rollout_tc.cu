@@ -393,18 +393,27 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             const int kpass = (Kl / 16 + 1) / 2;  // the other slot may start once half of this layer is issued
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
             if (!STREAM) {
-                const uint32_t bh = tc::smem_u32(wimg + N.tc_hi[l]), blo = tc::smem_u32(wimg + N.tc_lo[l]);
-                for (int ks = 0; ks < Kl / 16; ++ks) {
-                    const uint32_t boff = (uint32_t)(ks >> 2) * (uint32_t)(Nl * 128) + (uint32_t)(ks & 3) * 32u;
-                    const uint64_t dh = tc::desc_sw128(bh + boff);
-                    tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
-                    if (SPLIT == 3) {
-                        tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + boff), idesc, 1u);
-                        tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
-                    }
-                    if (NSLOT == 2 && ks + 1 == kpass) {
-                        tc::mbar_arrive(&bar_tok[sl]);
-                        passed = true;
+                // operands stepped with 32-bit adds on precomputed descriptor words, four K steps (one 64-wide
+                // K-atom) unrolled: the issuing thread's own instructions, not the tensor core, set the MMA rate
+                const int nks = Kl / 16;
+                const uint32_t atom = (uint32_t)Nl * 8u;  // one K-atom of the image in 16-byte units
+                uint32_t qh = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tc_hi[l]));
+                uint32_t ql = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tc_lo[l]));
+                uint32_t th = ah, tl = al;
+                for (int ks0 = 0; ks0 < nks; ks0 += 4, qh += atom, ql += atom, th += 32u, tl += 32u) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        if (ks0 + kk >= nks) break;
+                        const uint64_t dh = tc::desc_join(qh + 2u * kk);
+                        tc::mma_ts(dcol, th + 8u * kk, dh, idesc, ks0 + kk > 0 ? 1u : 0u);
+                        if (SPLIT == 3) {
+                            tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(ql + 2u * kk), idesc, 1u);
+                            tc::mma_ts(dcol, tl + 8u * kk, dh, idesc, 1u);
+                        }
+                        if (NSLOT == 2 && ks0 + kk + 1 == kpass) {
+                            tc::mbar_arrive(&bar_tok[sl]);
+                            passed = true;
+                        }
                     }
                 }
             } else {
@@ -418,15 +427,18 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                         ok = false;
                         break;
                     }
-                    const uint32_t bh = tc::smem_u32(wimg + ((size_t)sl * a.stages + st) * a.stage_bytes);
-                    const uint32_t blo = bh + (uint32_t)(Nl * 128);
-                    for (int kk = 0; kk < 4 && 4 * at + kk < Kl / 16; ++kk) {
+                    const uint32_t qh = tc::desc_sw128_lo(tc::smem_u32(wimg + ((size_t)sl * a.stages + st) * a.stage_bytes));
+                    const uint32_t ql = qh + (uint32_t)Nl * 8u;  // the lo half follows the hi half in the buffer
+                    const uint32_t th = ah + 32u * at, tl = al + 32u * at;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
                         const int ks = 4 * at + kk;
-                        const uint64_t dh = tc::desc_sw128(bh + (uint32_t)kk * 32u);
-                        tc::mma_ts(dcol, ah + ks * 8, dh, idesc, ks > 0 ? 1u : 0u);
+                        if (ks >= Kl / 16) break;
+                        const uint64_t dh = tc::desc_join(qh + 2u * kk);
+                        tc::mma_ts(dcol, th + 8u * kk, dh, idesc, ks > 0 ? 1u : 0u);
                         if (SPLIT == 3) {
-                            tc::mma_ts(dcol, ah + ks * 8, tc::desc_sw128(blo + (uint32_t)kk * 32u), idesc, 1u);
-                            tc::mma_ts(dcol, al + ks * 8, dh, idesc, 1u);
+                            tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(ql + 2u * kk), idesc, 1u);
+                            tc::mma_ts(dcol, tl + 8u * kk, dh, idesc, 1u);
                         }
                         if (NSLOT == 2 && ks + 1 == kpass) {
                             tc::mbar_arrive(&bar_tok[sl]);

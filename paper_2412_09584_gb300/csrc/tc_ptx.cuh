@@ -145,6 +145,13 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
     d |= (uint64_t)2 << 61;            // 128-byte swizzle
     return d;
 }
+// The same descriptor split in its two 32-bit words: the low word carries the start address (16-byte units)
+// and the unused leading byte offset, the high word is the same for every 128-byte swizzled K-major operand.
+// desc_join(desc_sw128_lo(a) + o) == desc_sw128(a + 16 o) while the address stays in shared memory, so an MMA
+// loop can step its operands with one 32-bit add.
+constexpr uint32_t kDescSw128Hi = (uint32_t)(1024 >> 4) | (1u << (46 - 32)) | (2u << (61 - 32));
+__device__ __forceinline__ uint32_t desc_sw128_lo(uint32_t saddr) { return ((saddr & 0x3FFFFu) >> 4) | (1u << 16); }
+__device__ __forceinline__ uint64_t desc_join(uint32_t lo) { return ((uint64_t)kDescSw128Hi << 32) | lo; }
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
