@@ -390,7 +390,8 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
             tc::fence_after_sync();
             bool passed = false;  // the turn handed to the other slot
             const int Kl = N.tc_K[l], Nl = N.tc_N[l];
-            const int kpass = (Kl / 16 + 1) / 2;  // the other slot may start once half of this layer is issued
+            // the other slot may start once three quarters of this layer are issued
+            const int kpass = (3 * (Kl / 16) + 3) / 4;
             const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
             if (!STREAM) {
                 // operands stepped with 32-bit adds on precomputed descriptor words, four K steps (one 64-wide
