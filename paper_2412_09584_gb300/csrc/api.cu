@@ -74,7 +74,8 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
     }
     for (int l = 1; l <= L; ++l) N.tc_lo[l] = hi + N.tc_hi[l];
     N.tc_bytes_hi = hi;
-    N.tc_bytes = 2 * hi;
+    N.tc_mg = 2 * hi;
+    N.tc_bytes = 2 * hi + ((N.tc_K[L] + 63) / 64) * 2 * N.tc_N[L] * 128;
     N.tc_bias_floats = bo;
     N.tc_dcols = dcols;
     N.tc_acols = acols;
@@ -97,6 +98,12 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
                                    (size_t)((within * 2) % 16);
                 std::memcpy(&img[N.tc_hi[l] + off], &h, 2);
                 std::memcpy(&img[N.tc_lo[l] + off], &lo, 2);
+                if (l == L) {
+                    // stacked copy: K-atom kb holds rows n (hi) and N_L + n (lo); (N_L + n) % 8 = n % 8
+                    const size_t offm = off + (size_t)kb * Nl * 128;
+                    std::memcpy(&img[N.tc_mg + offm], &h, 2);
+                    std::memcpy(&img[N.tc_mg + offm + (size_t)Nl * 128], &lo, 2);
+                }
             }
         }
     }

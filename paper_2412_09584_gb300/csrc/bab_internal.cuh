@@ -43,6 +43,7 @@ struct NetDesc {
     int tc_ok;
     int tc_K[kMaxLayers + 1], tc_N[kMaxLayers + 1];
     int tc_hi[kMaxLayers + 1], tc_lo[kMaxLayers + 1];  // byte offsets in the image
+    int tc_mg;  // byte offset of the output layer stacked per K-atom as [hi rows; lo rows] (after the lo halves)
     int tc_boff[kMaxLayers + 1];                       // float offsets in the bias vector
     int tc_bytes, tc_bytes_hi, tc_bias_floats;
     int tc_dcols, tc_acols;                            // TMEM columns: accumulator, A operand

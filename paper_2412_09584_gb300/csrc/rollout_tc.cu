@@ -153,6 +153,9 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     const uint32_t tb = tmem_base;
     const int Dc = N.tc_dcols, Ac = N.tc_acols;
     const int slot_cols = Dc + (SPLIT == 3 ? 2 : 1) * Ac;
+    // the output layer's split as two MMAs per K step, a_hi [b_hi; b_lo] (2 N_L wide) and a_lo b_hi, where the
+    // 2 N_L accumulator columns fit: columns 0.. hold a_hi b_hi + a_lo b_hi, columns N_L.. hold a_hi b_lo
+    const bool stacked = SPLIT == 3 && 2 * N.tc_N[L] <= Dc && 2 * N.tc_N[L] <= 256;
 
     if (warp < mma_warp) {
         // ------------------------------- epilogue -------------------------------
@@ -268,7 +271,25 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                         // network output: residual step and step cost (the primary warps own the rows)
                         if (primary) {
                             float dx[SX];
-                            if (SX <= 16) {
+                            if (SPLIT == 3 && stacked && SX == 8) {
+                                uint32_t v[8], w[8];
+                                tc::tmem_ld8(dcol, v);
+                                tc::tmem_ld8(dcol + N.tc_N[L], w);
+                                tc::tmem_wait_ld();
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) dx[i] = __uint_as_float(v[i]) + __uint_as_float(w[i]);
+                            } else if (SPLIT == 3 && stacked) {
+#pragma unroll
+                                for (int c0 = 0; c0 < SX; c0 += 16) {
+                                    uint32_t v[16], w[16];
+                                    tc::tmem_ld16(dcol + c0, v);
+                                    tc::tmem_ld16(dcol + N.tc_N[L] + c0, w);
+                                    tc::tmem_wait_ld();
+#pragma unroll
+                                    for (int i = 0; i < 16; ++i)
+                                        if (c0 + i < SX) dx[c0 + i] = __uint_as_float(v[i]) + __uint_as_float(w[i]);
+                                }
+                            } else if (SX <= 16) {
                                 uint32_t v[16];
                                 tc::tmem_ld16(dcol, v);
                                 tc::tmem_wait_ld();
@@ -401,6 +422,23 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                 uint32_t qh = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tc_hi[l]));
                 uint32_t ql = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tc_lo[l]));
                 uint32_t th = ah, tl = al;
+                if (SPLIT == 3 && stacked && l == L) {
+                    // stacked atoms: 2 N_L rows each, hi rows first
+                    uint32_t qm = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tc_mg));
+                    const uint32_t idesc2 = tc::idesc_bf16_f32(128, 2 * Nl);
+                    for (int ks0 = 0; ks0 < nks; ks0 += 4, qh += atom, qm += 2u * atom, th += 32u, tl += 32u) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if (ks0 + kk >= nks) break;
+                            tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(qm + 2u * kk), idesc2, ks0 + kk > 0 ? 1u : 0u);
+                            tc::mma_ts(dcol, tl + 8u * kk, tc::desc_join(qh + 2u * kk), idesc, 1u);
+                            if (NSLOT == 2 && ks0 + kk + 1 == kpass) {
+                                tc::mbar_arrive(&bar_tok[sl]);
+                                passed = true;
+                            }
+                        }
+                    }
+                } else {
                 for (int ks0 = 0; ks0 < nks; ks0 += 4, qh += atom, ql += atom, th += 32u, tl += 32u) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
@@ -416,6 +454,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                             passed = true;
                         }
                     }
+                }
                 }
             } else {
                 // one K-atom (64 inputs; hi, then lo for the split) per ring buffer
@@ -436,10 +475,16 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                         const int ks = 4 * at + kk;
                         if (ks >= Kl / 16) break;
                         const uint64_t dh = tc::desc_join(qh + 2u * kk);
-                        tc::mma_ts(dcol, th + 8u * kk, dh, idesc, ks > 0 ? 1u : 0u);
-                        if (SPLIT == 3) {
-                            tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(ql + 2u * kk), idesc, 1u);
+                        if (SPLIT == 3 && stacked && l == L) {
+                            // the buffer holds the atom's hi rows, then its lo rows: already stacked
+                            tc::mma_ts(dcol, th + 8u * kk, dh, tc::idesc_bf16_f32(128, 2 * Nl), ks > 0 ? 1u : 0u);
                             tc::mma_ts(dcol, tl + 8u * kk, dh, idesc, 1u);
+                        } else {
+                            tc::mma_ts(dcol, th + 8u * kk, dh, idesc, ks > 0 ? 1u : 0u);
+                            if (SPLIT == 3) {
+                                tc::mma_ts(dcol, th + 8u * kk, tc::desc_join(ql + 2u * kk), idesc, 1u);
+                                tc::mma_ts(dcol, tl + 8u * kk, dh, idesc, 1u);
+                            }
                         }
                         if (NSLOT == 2 && ks + 1 == kpass) {
                             tc::mbar_arrive(&bar_tok[sl]);
