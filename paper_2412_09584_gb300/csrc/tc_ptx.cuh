@@ -55,6 +55,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t phase)
                  : "memory");
     return done != 0;
 }
+// The same test, letting the thread sleep up to `hint_ns` for the phase to complete (a waiting warp then takes
+// no issue slots from the warps that work).
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t phase, uint32_t hint_ns)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_u32(bar)), "r"(phase), "r"(hint_ns)
+                 : "memory");
+    return done != 0;
+}
 // Wait for the phase with parity `phase` to complete; gives up after `limit_ns`
 // or as soon as *abort is set.  Returns false on time-out or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, volatile int *abort, uint64_t limit_ns)
@@ -62,7 +73,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, volatil
     if (mbar_try(bar, phase)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
-        if (mbar_try(bar, phase)) return true;
+        if (mbar_try_sleep(bar, phase, 20000u)) return true;
         if (*abort) return false;
         if (globaltimer() - t0 > limit_ns) return false;
     }
