@@ -324,8 +324,8 @@ int bab_alpha_init(bab_ctx *ctx, const float *x0, const float *goal, int horizon
  *   cap_out    rows available in the outputs; must be >= n + n_pick.
  *   out_*      device arrays of cap_out rows; keep device uint8[n].
  * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE (cap_out too small), BAB_ERR_CUDA.
- * A picked box whose id is >= 2^63 cannot be split; the call then records
- * BAB_ERR_SHAPE in the context's device status (see bab_status).
+ * Every picked box can be split, whatever its id: past 2^62 the children's
+ * ids continue as the hash given above, so no depth limit is latched.
  */
 int bab_prune_branch(bab_ctx *ctx, int d, const float *lo, const float *hi, const float *lb, const float *ub,
                      const uint64_t *id, int n, const int *d_n, const double *inc_val, int n_pick, float eta,
@@ -617,8 +617,9 @@ int bab_autotune(bab_ctx *ctx, const float *x0, const float *goal, int horizon, 
  * It takes no context (creating one allocates).  The network comes as a
  * DEVICE pointer in the layout of bab_load_dynamics, and all working memory
  * (padded weight images, interval bounds, rounding-error helpers) lives in
- * one fixed array of BAB_STATIC_SCRATCH_BYTES inside the library, which
- * every GPU that loads the library keeps until the process exits.
+ * one fixed array of BAB_STATIC_SCRATCH_BYTES inside the library.  A GPU
+ * holds the array from this entry point's first call on it until the
+ * process exits.
  *   n_layers, dims (HOST int[L+1]), state_dim, action_dim: as bab_load_dynamics.
  *   params     DEVICE float array, packed W_1, b_1, ..., W_L, b_L (caller-owned).
  *   x0, goal, horizon, rho, lo, hi, n: as bab_bound_crown (adaptive slopes,
@@ -627,9 +628,13 @@ int bab_autotune(bab_ctx *ctx, const float *x0, const float *goal, int horizon, 
  * The call needs 4 * (2 * image + n * H * (3 * sumh + s) + 2 * n * (H + 1) * s)
  * bytes (image = the padded network, about the parameter count); if that
  * exceeds BAB_STATIC_SCRATCH_BYTES it returns BAB_ERR_SHAPE before any
- * device work.  The first call on a device (with that device current) looks
- * up the array's device address once; make that first call before any stream
- * capture.  All calls share the one array, so calls whose GPU work overlaps
+ * device work (sizes that large are refused before any product of them is
+ * formed).  The first call on a device (with that device current) looks up
+ * the array's device address and loads the entry point's kernels; under
+ * CUDA's lazy module loading that first call may itself allocate device
+ * memory.  So make one warm-up call per device first, with n = 0 (it does
+ * only this set-up and returns BAB_OK), before the section that must not
+ * allocate and before any stream capture.  All calls share the one array, so calls whose GPU work overlaps
  * (on different streams or host threads) race: order them on one stream.
  * Errors: BAB_ERR_INVALID_ARG, BAB_ERR_SHAPE, BAB_ERR_UNSUPPORTED (device
  * index >= 64), BAB_ERR_CUDA.  There is no context, so no bab_last_error.

@@ -27,6 +27,9 @@
  *                         Section 3.2 approach 2.
  *   oracle_crown_given    CROWN with given intermediate bounds and propagation
  *                         early-stop, Section 3.2 approach 1 / Algorithm 3.
+ *   oracle_crown_margin   the CROWN bound with the outward rounding margin of
+ *                         an FP32 or split-BF16 evaluation (the paper is silent
+ *                         on floating point: a reading, see margin_gamma).
  *   oracle_box_grad       d(lower bound)/d(box faces), through the relaxation
  *                         choices and the interval bounds.
  *   oracle_adam_ascent    projected Adam ascent on alpha.
@@ -555,7 +558,64 @@ typedef struct {
     double lb;          /* concretized lower bound */
     double lin_const;   /* f(u) >= lin_const + mu . u + rho ||u||^2 on the box */
     double scale;       /* sum of |each term added into the bound|: the magnitude rounding errors scale with */
+    double margin;      /* the outward rounding margin of an FP32 / split-BF16 evaluation (see margin_gamma) */
 } crown_out;
+
+/*
+ * Outward rounding margin (the paper is silent on floating point; the bound
+ * stays sound if every coefficient error is charged against the largest
+ * magnitude its variable can take on the box).  A product of a coefficient
+ * row A' (K = d_l entries) with W_l evaluated in floating point has, in each
+ * output j, an error of at most gamma * sum_k |A'_k| |W_kj| (Higham,
+ * "Accuracy and Stability of Numerical Algorithms", 2nd ed., Section 3.1);
+ * charged against max |a_j| over the interval of the layer's input a, the
+ * bound moves by at most gamma * sum_k |A'_k| S_k with
+ * S_k = sum_j |W_kj| max|a_j|.  gamma per arithmetic (prec):
+ *   0: FP32 products over K = d_l rounded up to a multiple of 4 terms,
+ *      gamma_K = K u / (1 - K u), u = 2^-24;
+ *   1: 3-term BF16 split (a_hi b_hi + a_hi b_lo + a_lo b_hi) with FP32
+ *      accumulation over K = d_l rounded up to a multiple of 16 terms:
+ *      3.1 * 2^-16 for the BF16 halves of both operands and the dropped
+ *      lo * lo term, plus gamma_K with unit 2^-23 (an accumulator that may
+ *      truncate).
+ * Each other rounded coefficient operation costs at most 2^-23 (twice the
+ * unit roundoff) of its magnitude times the largest magnitude of its
+ * variable: the relaxation product A D of a neuron whose slope is neither 0
+ * nor 1 (variable z in [l, u]), the state update lam + A_x + a_t (variable
+ * x_t), and, for rho > 0, the choice of a face when the unconstrained
+ * minimiser u_c of mu u + rho u^2 lies outside the box: rho (2^-23 u_c)^2.
+ */
+static double margin_gamma(int prec, int d)
+{
+    if (prec == 1) {
+        double K = (double)((d + 15) / 16 * 16), u = ldexp(1.0, -23);
+        return 3.1 * ldexp(1.0, -16) + K * u / (1.0 - K * u);
+    }
+    double K = (double)((d + 3) / 4 * 4), u = ldexp(1.0, -24);
+    return K * u / (1.0 - K * u);
+}
+
+/* S_q = sum_p |W_l[q][p]| max|a_p| over the interval of layer l's input at step t (layer 1: [x_t; u_t]). */
+static void margin_rowsums(const onet *N, int l, int t, const double *lo, const double *hi, const double *pre_hi,
+                           const double *x_lo, const double *x_hi, double *S)
+{
+    int s = N->s, k = N->k, no = N->dims[l], ni = N->dims[l - 1];
+    double amax[ORC_MAX_WIDTH];
+    for (int p = 0; p < ni; ++p) {
+        if (l == 1) {
+            if (p < s) amax[p] = fmax(fabs(x_lo[(size_t)t * s + p]), fabs(x_hi[(size_t)t * s + p]));
+            else amax[p] = fmax(fabs(lo[t * k + p - s]), fabs(hi[t * k + p - s]));
+        } else {
+            double u = pre_hi[(size_t)t * N->sumh + N->hoff[l - 1] + p];
+            amax[p] = u > 0.0 ? u : 0.0;  /* ReLU output in [max(l, 0), max(u, 0)] */
+        }
+    }
+    for (int q = 0; q < no; ++q) {
+        double acc = 0.0;
+        for (int p = 0; p < ni; ++p) acc += fabs(N->W[l][(size_t)q * ni + p]) * amax[p];
+        S[q] = acc;
+    }
+}
 
 /*
  * The bound of one box.  The cost term ||x_t - g||^2 (t >= 1) is bounded below
@@ -577,11 +637,12 @@ typedef struct {
 static crown_out crown_box(const onet *N, int H, double rho, const double *x0, const double *goal,
                            const double *lo, const double *hi, const double *pre_lo, const double *pre_hi,
                            const double *x_lo, const double *x_hi, const double *alpha, double *mu,
-                           double *ustar, double *A_pre, double *atan, int t_stop)
+                           double *ustar, double *A_pre, double *atan, int t_stop, int prec)
 {
     int s = N->s, k = N->k, L = N->L, sumh = N->sumh;
-    double lam[ORC_MAX_WIDTH], A[ORC_MAX_WIDTH], An[ORC_MAX_WIDTH];
-    double cst = 0.0, cabs = 0.0;
+    double lam[ORC_MAX_WIDTH], A[ORC_MAX_WIDTH], An[ORC_MAX_WIDTH], S[ORC_MAX_WIDTH];
+    double cst = 0.0, cabs = 0.0, marg = 0.0;
+    const double two_u = ldexp(1.0, -23);
     double *mu_loc = (double *)calloc((size_t)k * H, sizeof(double));
 
     /* linear lower bounds a_t . x_t + const of the state cost at the steps the backward pass carries
@@ -663,6 +724,8 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
             cst += A[q] * N->b[L][q];
             cabs += fabs(A[q] * N->b[L][q]);
         }
+        margin_rowsums(N, L, t, lo, hi, pre_hi, x_lo, x_hi, S);
+        for (int q = 0; q < nL; ++q) marg += margin_gamma(prec, nL) * fabs(A[q]) * S[q];
         for (int p = 0; p < nLm; ++p) {
             double acc = 0.0;
             for (int q = 0; q < nL; ++q) acc += A[q] * N->W[L][(size_t)q * nLm + p];
@@ -682,11 +745,14 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
                 cst += A[q] * c;
                 cabs += fabs(A[q] * c);
                 A[q] *= D;
+                if (D != 0.0 && D != 1.0) marg += two_u * fabs(A[q]) * fmax(-zl, zu);
             }
             for (int q = 0; q < no; ++q) {
                 cst += A[q] * N->b[l][q];
                 cabs += fabs(A[q] * N->b[l][q]);
             }
+            margin_rowsums(N, l, t, lo, hi, pre_hi, x_lo, x_hi, S);
+            for (int q = 0; q < no; ++q) marg += margin_gamma(prec, no) * fabs(A[q]) * S[q];
             for (int p = 0; p < ni; ++p) {
                 double acc = 0.0;
                 for (int q = 0; q < no; ++q) acc += A[q] * N->W[l][(size_t)q * ni + p];
@@ -696,7 +762,12 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
         }
         /* A is now on [x_t; u_t] */
         for (int j = 0; j < k; ++j) mu_loc[t * k + j] = A[s + j];
-        for (int i = 0; i < s; ++i) lam[i] = lam[i] + A[i] + (t >= 1 ? a[(size_t)t * s + i] : 0.0);
+        for (int i = 0; i < s; ++i) {
+            double at = t >= 1 ? a[(size_t)t * s + i] : 0.0;
+            double B = t >= 1 ? fmax(fabs(x_lo[(size_t)t * s + i]), fabs(x_hi[(size_t)t * s + i])) : fabs(x0[i]);
+            marg += two_u * (fabs(lam[i]) + fabs(A[i]) + fabs(at)) * B;
+            lam[i] = lam[i] + A[i] + at;
+        }
     }
     if (t_stop == 0) {
         for (int i = 0; i < s; ++i) {
@@ -720,6 +791,10 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
         double v = quad_min(mu_loc[j], rho, lo[j], hi[j], &arg);
         lb += v;
         cabs += fabs(v);
+        if (rho > 0.0) {
+            double uc = -mu_loc[j] / (2.0 * rho);
+            if (uc < lo[j] || uc > hi[j]) marg += rho * (two_u * uc) * (two_u * uc);
+        }
         if (ustar) ustar[j] = arg;
         if (mu) mu[j] = mu_loc[j];
     }
@@ -727,7 +802,8 @@ static crown_out crown_box(const onet *N, int H, double rho, const double *x0, c
     free(a);
     free(mu_extra);
     free(mu_loc);
-    crown_out o = {lb, cst, cabs};
+    /* the obstacle cost's margin (pusher coefficients) is not stated here */
+    crown_out o = {lb, cst, cabs, g_cost.kind == 0 ? marg : NAN};
     return o;
 }
 
@@ -757,7 +833,7 @@ int oracle_crown(int L, const int *dims, const double *params, int s, int k, int
         ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
         crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, alpha ? alpha + (size_t)i * nh : NULL,
                                 lin_coef ? lin_coef + (size_t)i * d : NULL, ustar ? ustar + (size_t)i * d : NULL,
-                                A_pre ? A_pre + (size_t)i * nh : NULL, NULL, 0);
+                                A_pre ? A_pre + (size_t)i * nh : NULL, NULL, 0, 0);
         lb[i] = o.lb;
         if (lin_const) lin_const[i] = o.lin_const;
         if (scale) scale[i] = o.scale;
@@ -846,9 +922,56 @@ int oracle_crown_given(int L, const int *dims, const double *params, int s, int 
     for (int i = 0; i < n; ++i) {
         crown_out o = crown_box(&N, H, rho, x0, goal, lo + (size_t)i * d, hi + (size_t)i * d, pre_lo + (size_t)i * nh,
                                 pre_hi + (size_t)i * nh, x_lo + (size_t)i * nx, x_hi + (size_t)i * nx, NULL, NULL,
-                                NULL, NULL, NULL, t_stop);
+                                NULL, NULL, NULL, t_stop, 0);
         lb[i] = o.lb;
     }
+    return 0;
+}
+
+/*
+ * CROWN bound with its outward rounding margin (margin_gamma) for the
+ * arithmetic `prec` (0: FP32 products, 1: 3-term BF16 split), with given
+ * intermediate bounds (pre_lo/pre_hi [n][H][sumh], x_lo/x_hi [n][H+1][s]) or,
+ * when pre_lo is NULL, the interval bounds of oracle_ibp; alpha [n][H][sumh]
+ * nullable (adaptive slopes).  Outputs per box: lb (exact FP64, no margin
+ * subtracted), margin, scale (all but lb nullable).  The margin is stated for
+ * the squared-distance cost (NaN otherwise).
+ */
+int oracle_crown_margin(int L, const int *dims, const double *params, int s, int k, int H, double rho,
+                        const double *x0, const double *goal, int n, const double *lo, const double *hi,
+                        const double *pre_lo, const double *pre_hi, const double *x_lo, const double *x_hi,
+                        const double *alpha, int prec, double *lb, double *margin, double *scale)
+{
+    onet N;
+    if (onet_init(&N, L, dims, params, s, k)) return -1;
+    if (prec != 0 && prec != 1) return -1;
+    int d = k * H;
+    size_t nh = (size_t)H * N.sumh, nx = (size_t)(H + 1) * s;
+    double *pl = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *pu = (double *)malloc(sizeof(double) * (nh ? nh : 1));
+    double *xl = (double *)malloc(sizeof(double) * nx);
+    double *xu = (double *)malloc(sizeof(double) * nx);
+    for (int i = 0; i < n; ++i) {
+        const double *bl = lo + (size_t)i * d, *bh = hi + (size_t)i * d;
+        const double *a_pl = pl, *a_pu = pu, *a_xl = xl, *a_xu = xu;
+        if (pre_lo) {
+            a_pl = pre_lo + (size_t)i * nh;
+            a_pu = pre_hi + (size_t)i * nh;
+            a_xl = x_lo + (size_t)i * nx;
+            a_xu = x_hi + (size_t)i * nx;
+        } else {
+            ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
+        }
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, a_pl, a_pu, a_xl, a_xu,
+                                alpha ? alpha + (size_t)i * nh : NULL, NULL, NULL, NULL, NULL, 0, prec);
+        lb[i] = o.lb;
+        if (margin) margin[i] = o.margin;
+        if (scale) scale[i] = o.scale;
+    }
+    free(pl);
+    free(pu);
+    free(xl);
+    free(xu);
     return 0;
 }
 
@@ -893,7 +1016,7 @@ int oracle_alpha_grad(int L, const int *dims, const double *params, int s, int k
         const double *al = alpha ? alpha + (size_t)i * nh : NULL;
         double *g = grad_alpha + (size_t)i * nh;
         ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
-        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, NULL, us, Ap, at, 0);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, NULL, us, Ap, at, 0, 0);
         lb[i] = o.lb;
 
         /* forward pass of the relaxed network from x_0 and u* */
@@ -997,7 +1120,7 @@ int oracle_box_grad(int L, const int *dims, const double *params, int s, int k, 
         const double *al = alpha ? alpha + (size_t)i * nh : NULL;
         double *glo = grad_lo + (size_t)i * d, *ghi = grad_hi + (size_t)i * d;
         ibp_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu);
-        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, mu, us, Ap, at, 0);
+        crown_out o = crown_box(&N, H, rho, x0, goal, bl, bh, pl, pu, xl, xu, al, mu, us, Ap, at, 0, 0);
         lb[i] = o.lb;
 
         /* relaxed network from x_0 and u*: z~ and the state x~_t, and the sensitivities */

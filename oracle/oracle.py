@@ -13,6 +13,7 @@ citations are to arXiv 2412.09584 (BaB-ND):
 * ``rollout``       Section 3.3 (batch_search, uniform samples)
 * ``ibp``           interval intermediate bounds used by Lemma 1
 * ``crown``         Appendix B.1, Lemma 1, Theorem 1, Theorem 2 (box form)
+* ``crown_margin``  the same bound with the outward rounding margin of an FP32 / split-BF16 evaluation
 * ``alpha_grad``    gradient of the Theorem 1/2 bound in the Lemma 1 slopes
 * ``adam_ascent``   projected Adam on the slopes
 * ``prune_branch``  Section 3 overview (Pruner), Section 3.1 (pick out, split)
@@ -275,6 +276,40 @@ def crown_given(problem, lo, hi, pre_lo, pre_hi, x_lo, x_hi, t_stop=0):
                                   ctypes.c_int(int(t_stop)), lb.ctypes.data_as(_c_double_p))
     assert rc == 0
     return lb
+
+
+def crown_margin(problem, lo, hi, intervals=None, alpha=None, prec=0):
+    """CROWN bound with the outward rounding margin of an FP32 (prec 0) or 3-term BF16 split (prec 1)
+    evaluation, in FP64: dict with lb (no margin subtracted), margin and scale.  `intervals` = (pre_lo, pre_hi,
+    x_lo, x_hi) gives the intermediate bounds (else the oracle's interval bounds); alpha: lower slopes or None
+    (adaptive)."""
+    net, keep, (cH, crho, px0, pg) = _prob(problem)
+    lo, plo = _d(lo)
+    hi, phi = _d(hi)
+    n = lo.shape[0]
+    H = int(problem["H"])
+    sh = max(net.sumh, 1)
+    ptrs = [None, None, None, None]
+    held = []
+    if intervals is not None:
+        pre_lo, pre_hi, x_lo, x_hi = intervals
+        pl = np.zeros((n, H, sh))
+        pu = np.zeros((n, H, sh))
+        pl[:, :, :net.sumh] = pre_lo
+        pu[:, :, :net.sumh] = pre_hi
+        xl = np.ascontiguousarray(x_lo, dtype=np.float64)
+        xu = np.ascontiguousarray(x_hi, dtype=np.float64)
+        held = [pl, pu, xl, xu]
+        ptrs = [a.ctypes.data_as(_c_double_p) for a in held]
+    alpha_a, palpha = _optd(alpha)
+    lb = np.zeros(n)
+    mg = np.zeros(n)
+    scale = np.zeros(n)
+    rc = lib().oracle_crown_margin(*net.cargs(), cH, crho, px0, pg, ctypes.c_int(n), plo, phi, *ptrs, palpha,
+                                   ctypes.c_int(int(prec)), lb.ctypes.data_as(_c_double_p),
+                                   mg.ctypes.data_as(_c_double_p), scale.ctypes.data_as(_c_double_p))
+    assert rc == 0
+    return {"lb": lb, "margin": mg, "scale": scale}
 
 
 def adaptive_alpha(problem, lo, hi):

@@ -571,18 +571,19 @@ __device__ void crown_rows(const BoundArgs &a, const float *img, float *p, const
             for (int i = lane; i < s; i += 32) {
                 const float Ax = Ab[cur][r * ld + i];
                 const float lo_ = lam[r * s4 + i];
-                float aa = 0.f, B;
-                if (t > ts && t >= 1 && r < nrows) {
-                    const float g = a.goal[i];
+                float aa = 0.f, B = fabsf(a.x0[i]);
+                if (t >= 1 && r < nrows) {
+                    // the updated coefficient multiplies x_t (concretized on its interval at an early stop)
                     const size_t xi = ((size_t)r * (H + 1) + t) * s + i;
                     const float xl = v.x_lo[xi], xu = v.x_hi[xi];
-                    const float Ls = __fsub_rd(xl, g), Us = __fsub_ru(xu, g);
-                    const float m = 0.5f * (Ls + Us);
-                    aa = 2.f * m;
-                    c = __fadd_rd(c, __fmaf_rd(-aa, g, -__fmul_ru(m, m)));
                     B = fmaxf(fabsf(xl), fabsf(xu));
-                } else {
-                    B = fabsf(a.x0[i]);
+                    if (t > ts) {
+                        const float g = a.goal[i];
+                        const float Ls = __fsub_rd(xl, g), Us = __fsub_ru(xu, g);
+                        const float m = 0.5f * (Ls + Us);
+                        aa = 2.f * m;
+                        c = __fadd_rd(c, __fmaf_rd(-aa, g, -__fmul_ru(m, m)));
+                    }
                 }
                 const float ln = (lo_ + Ax) + aa;
                 lam[r * s4 + i] = ln;
@@ -926,6 +927,16 @@ cudaError_t launch_crown(const BoundArgs &a, int, cudaStream_t st)
     const NetDesc &N = a.net;
     size_t rest = crown_rows_floats(N, RB, a.d) * sizeof(float);
     return launch_rows_kernel(k_crown<true>, k_crown<false>, (size_t)N.img_floats * 4, rest, a.n, a, st);
+}
+
+cudaError_t preload_ibp_crown()
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_ibp<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_ibp<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_crown<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_crown<false>);
+    return e;
 }
 
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int, cudaStream_t st)

@@ -8,12 +8,17 @@
 // it has started.  This entry point takes no context: the network comes in as
 // a device pointer, and every byte of working memory (the padded weight
 // images, the interval bounds and the rounding-error helpers) lives in one
-// file-scope __device__ array of BAB_STATIC_SCRATCH_BYTES, which every GPU
-// that loads the library holds until the process exits.
+// file-scope __device__ array of BAB_STATIC_SCRATCH_BYTES.  A GPU holds the
+// array from the moment this file's module is loaded on it (the first call
+// there) until the process exits.
 //
 // Host code cannot use the array's name as a device address, so the first
 // call on each device (with that device current) asks the runtime for the
-// array's device address once with cudaGetSymbolAddress and keeps it.
+// array's device address once with cudaGetSymbolAddress and keeps it; the
+// same call also loads the kernels the entry point launches.  With CUDA's
+// lazy module loading both steps may allocate device memory, so a caller
+// makes one warm-up call per device (n = 0 does nothing else) before the
+// section that must not allocate, and before any stream capture.
 // All calls share the array, so calls whose GPU work overlaps (for example
 // on two streams) race.  Every word the kernels read is written earlier in
 // the same call, so nothing needs clearing.
@@ -31,7 +36,11 @@ constexpr int kMaxDevices = 64;
 void *g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Device address of g_static_scratch on the current device (looked up once per device).
+__global__ void k_pack_images(bab::NetDesc N, const float *__restrict__ params, float *__restrict__ fwd,
+                              float *__restrict__ bwd);
+
+// Device address of g_static_scratch on the current device, looked up once per device; the first lookup also
+// loads the kernels this entry point launches.
 int static_scratch_address(void **out)
 {
     int dev = -1;
@@ -43,7 +52,10 @@ int static_scratch_address(void **out)
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pack_images);
+        if (e == cudaSuccess) e = bab::preload_ibp_crown();
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return BAB_ERR_CUDA;
@@ -129,19 +141,23 @@ extern "C" int bab_bound_crown_static(int n_layers, const int *dims, const float
     if (horizon < 1 || horizon > (1 << 20) || n < 0) return BAB_ERR_SHAPE;
     if (!(rho >= 0.f) || rho != rho || rho > 3.0e38f) return BAB_ERR_INVALID_ARG;
     if (n > 0 && (!lo || !hi || !lb)) return BAB_ERR_INVALID_ARG;
-    if (n == 0) return BAB_OK;
 
-    // working set, each piece 256-byte aligned
+    // working set, each piece 256-byte aligned: per box 4 (H (3 sumh + s) + 2 (H + 1) s) bytes (at most about
+    // 2^20 * 2^12 * 4, so no product below can wrap), plus the two images and five alignment pads; the box count
+    // is checked against the room left before any total is formed
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t nh = (size_t)n * horizon * N.sumh, nx = (size_t)n * (horizon + 1) * N.s;
-    const size_t ns = (size_t)n * horizon * (N.sumh + N.s);
     const size_t img = up((size_t)N.img_floats * sizeof(float));
-    const size_t need = 2 * img + 2 * up(nh * 4) + 2 * up(nx * 4) + up(ns * 4);
-    if (need > (size_t)BAB_STATIC_SCRATCH_BYTES) return BAB_ERR_SHAPE;
+    const size_t per_box = 4 * ((size_t)horizon * (3 * (size_t)N.sumh + N.s) + 2 * ((size_t)horizon + 1) * N.s);
+    const size_t cap = (size_t)BAB_STATIC_SCRATCH_BYTES;
+    if (2 * img + 5 * 256 > cap || (size_t)n > (cap - 2 * img - 5 * 256) / per_box) return BAB_ERR_SHAPE;
+    const size_t nh = (size_t)n * horizon * N.sumh, nx = (size_t)n * (horizon + 1) * N.s;
 
+    // the address lookup (and, on a device's first call, the module loading) comes before the n = 0 return,
+    // so that a call with n = 0 is the warm-up
     void *base = nullptr;
     int rc = static_scratch_address(&base);
     if (rc != BAB_OK) return rc;
+    if (n == 0) return BAB_OK;
     char *p = static_cast<char *>(base);
     float *fwd = reinterpret_cast<float *>(p);
     p += img;

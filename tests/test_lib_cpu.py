@@ -44,3 +44,21 @@ def test_rejects_bad_arguments_without_device_work(lib):
     assert lib.bab_load_dynamics(ctypes.byref(out), 2, dims, params, 4, 2, 7) == -1
     with pytest.raises(TypeError):
         binding._ptr([1, 2, 3], None, "x")
+
+
+def test_static_bound_refuses_sizes_beyond_its_array_on_the_host(lib):
+    """bab_bound_crown_static sizes its working set per box first and refuses any batch that would not fit its
+    fixed array before forming a total or touching the device, so even sizes whose byte count would wrap in
+    64 bits (n near 2^31 with H = 2^20) come back as BAB_ERR_SHAPE; the pointers are never dereferenced here."""
+    lib.bab_bound_crown_static.restype = ctypes.c_int
+    dims = (ctypes.c_int * 5)(10, 128, 128, 128, 8)
+    fake = ctypes.c_void_p(0x1000)  # stands in for device pointers: never read when the shape is refused
+    for n, H in ((2 ** 31 - 1, 1 << 20), (1, 1 << 20), (4096, 20), (200, 20)):
+        rc = lib.bab_bound_crown_static(4, dims, fake, 8, 2, fake, fake, H, ctypes.c_float(0.01), fake, fake, n,
+                                        fake, None, None)
+        assert rc == -2, (n, H)
+    # the horizon limit and argument checks come first
+    assert lib.bab_bound_crown_static(4, dims, fake, 8, 2, fake, fake, (1 << 20) + 1, ctypes.c_float(0.0), fake,
+                                      fake, 1, fake, None, None) == -2
+    assert lib.bab_bound_crown_static(4, dims, fake, 8, 2, fake, fake, 20, ctypes.c_float(-1.0), fake, fake, 1,
+                                      fake, None, None) == -1

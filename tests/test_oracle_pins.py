@@ -1088,3 +1088,191 @@ def test_obstacle_penalty_relaxation_brute_force(oracle):
     q = np.array([0.1, -0.2])
     used, a0, a1, b = oracle.relu_dist_lower(q[0], q[0], q[1], q[1], 0.0, 0.0, 1.0)
     assert used and a0 * q[0] + a1 * q[1] + b == pytest.approx(1.0 - np.hypot(*q), abs=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Outward rounding margin of an FP32 / split-BF16 evaluation (oracle_crown_margin)
+# --------------------------------------------------------------------------
+
+def _fp32_chain(p, lo, hi, pl, pu, xl, xu, A_pre, order, seed=0):
+    """The coefficient chain of the CROWN bound evaluated in FP32 (numpy float32, one rounding per multiply and
+    per add, products summed in `order`: 'fwd', 'rev' or 'perm'), with the oracle's relaxation choices (lower line
+    where the oracle's pre-relaxation coefficient is >= 0) and every constant term and the concretization taken
+    in FP64 from the FP32 coefficients.  Returns the bound per box; its distance from the FP64 bound is the
+    rounding the margin has to cover."""
+    f32 = np.float32
+    layers = W.unpack_params(p)
+    L, s, k, H, rho = len(layers), p["s"], p["k"], p["H"], float(p["rho"])
+    dims = p["dims"]
+    hoff = np.concatenate([[0], np.cumsum(dims[1:-1])]).astype(int)
+    x0 = np.asarray(p["x0"], np.float64)
+    goal = np.asarray(p["goal"], np.float64)
+    rng = np.random.default_rng(seed)
+    n = lo.shape[0]
+
+    def prod(A, Wl):  # A [n, K] float32 times Wl [K, J]: sum over K in the chosen order
+        K = Wl.shape[0]
+        idx = np.arange(K) if order == "fwd" else (np.arange(K)[::-1] if order == "rev" else rng.permutation(K))
+        acc = np.zeros((A.shape[0], Wl.shape[1]), f32)
+        W32 = Wl.astype(f32)
+        for kk in idx:
+            acc = (acc + (A[:, kk:kk + 1] * W32[kk][None, :]).astype(f32)).astype(f32)
+        return acc
+
+    out = np.zeros(n)
+    for b in range(n):
+        cst = 0.0
+        m = 0.5 * (xl[b, H] + xu[b, H]) - goal
+        lam = (2 * m).astype(f32)[None, :]
+        cst += float(np.sum(-2 * m * goal - m * m))
+        mu = np.zeros(k * H)
+        for t in range(H - 1, -1, -1):
+            Wl_, bl_ = layers[L - 1]
+            A = lam.copy()
+            cst += float(A[0].astype(np.float64) @ bl_)
+            A = prod(A, Wl_)  # W_L is [d_L, d_{L-1}]: A W_L
+            for l in range(L - 1, 0, -1):
+                Wl_, bl_ = layers[l - 1]
+                zl = pl[b, t, hoff[l - 1]:hoff[l - 1] + dims[l]]
+                zu = pu[b, t, hoff[l - 1]:hoff[l - 1] + dims[l]]
+                Ao = A_pre[b, t, hoff[l - 1]:hoff[l - 1] + dims[l]]
+                D = np.where(zl >= 0, 1.0, np.where(zu <= 0, 0.0, np.where(Ao >= 0, np.where(zu >= -zl, 1.0, 0.0),
+                                                                            zu / np.where(zu > zl, zu - zl, 1.0))))
+                c = np.where((zl < 0) & (zu > 0) & (Ao < 0), -zu * zl / np.where(zu > zl, zu - zl, 1.0), 0.0)
+                cst += float(A[0].astype(np.float64) @ c)
+                A = (A * D.astype(f32)[None, :]).astype(f32)
+                cst += float(A[0].astype(np.float64) @ bl_)
+                A = prod(A, Wl_)
+            mu[t * k:(t + 1) * k] = A[0, s:s + k]
+            at = np.zeros(s, f32)
+            if t >= 1:
+                mt = 0.5 * (xl[b, t] + xu[b, t]) - goal
+                at = (2 * mt).astype(f32)
+                cst += float(np.sum(-2 * mt * goal - mt * mt))
+            lam = ((lam[0] + A[0, :s]).astype(f32) + at).astype(f32)[None, :]
+        cst += float(lam[0].astype(np.float64) @ x0)
+        for j in range(k * H):
+            if rho > 0:
+                u = min(max(-mu[j] / (2 * rho), lo[b, j]), hi[b, j])
+            else:
+                u = lo[b, j] if mu[j] >= 0 else hi[b, j]
+            cst += mu[j] * u + rho * u * u
+        out[b] = cst
+    return out
+
+
+@pytest.mark.parametrize("s,k,hidden,H,rho,wscale,maxw", [(4, 2, [32, 32], 5, 0.0, 0.3, 1.0),
+                                                          (4, 2, [32, 32], 5, 0.01, 1.0, 0.5),
+                                                          (8, 2, [128, 128], 3, 0.01, 0.3, 1.0)])
+def test_margin_covers_fp32_evaluations(oracle, s, k, hidden, H, rho, wscale, maxw):
+    """The margin of an FP32 evaluation covers the rounding of the coefficient chain in any summation order:
+    the FP32 chain's bound minus the margin never exceeds the exact FP64 bound (checked in three orders)."""
+    p = W.make_problem(s, k, hidden, H, rho, seed=31, weight_scale=wscale)
+    lo, hi, _ = W.random_boxes(k * H, 6, seed=32, min_width=0.1, max_width=maxw)
+    _, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    o = oracle.crown(p, lo, hi)
+    r = oracle.crown_margin(p, lo, hi)
+    np.testing.assert_allclose(r["lb"], o["lb"], rtol=1e-14, atol=1e-12)
+    assert np.all(r["margin"] > 0)
+    worst = 0.0
+    for order in ("fwd", "rev", "perm"):
+        v32 = _fp32_chain(p, lo, hi, pl, pu, xl, xu, o["A_pre"], order)
+        assert np.all(v32 - r["margin"] <= r["lb"] + 1e-12 * np.abs(r["lb"])), order
+        worst = max(worst, float(np.max(np.abs(v32 - r["lb"]) / r["margin"])))
+    assert worst > 0  # the FP32 chain does round: the check is not vacuous
+    # the split-BF16 margin charges 3.1 * 2^-16 per product term on top of its FP32 accumulation: larger
+    r1 = oracle.crown_margin(p, lo, hi, prec=1)
+    assert np.all(r1["margin"] > 10 * r["margin"])
+
+
+def test_margin_single_step_linear_closed_form(oracle):
+    """One step of a network without hidden layers (x_1 = x_0 + W [x_0; u_0] + b), rho = 0: the tangent
+    coefficient lam = 2 m of ||x_1 - g||^2 is carried through W once, so the margin is the FP32 product bound
+    gamma_4 |lam|^T |W| amax (amax = [|x_0|; max(|lo|, |hi|)], Higham's gamma_n = n u / (1 - n u), u = 2^-24, over
+    the 4 terms of a 3-wide product rounded up to a multiple of 4) plus the state update lam + lam W_x charged
+    at 2^-23 against |x_0|."""
+    rng = np.random.default_rng(5)
+    s, k = 3, 2
+    Wm = rng.uniform(-0.5, 0.5, size=(s, s + k))
+    b = rng.normal(0, 0.1, size=s)
+    p = dict(dims=[s + k, s], params=W.pack_params([(Wm, b)]), x0=np.array([0.3, -1.2, 0.7]),
+             goal=np.array([1.0, 0.5, -0.25]), H=1, rho=0.0, s=s, k=k)
+    lo = np.array([[-0.4, 0.1]])
+    hi = np.array([[0.2, 0.9]])
+    x0 = p["x0"]
+    c = x0 + Wm[:, :s] @ x0 + Wm[:, s:] @ (0.5 * (lo[0] + hi[0])) + b
+    r_ = np.abs(Wm[:, s:]) @ (0.5 * (hi[0] - lo[0]))
+    m = c - p["goal"]  # midpoint of [c - r, c + r] - g
+    lam = 2 * m
+    amax = np.concatenate([np.abs(x0), np.maximum(np.abs(lo[0]), np.abs(hi[0]))])
+    u = 2.0 ** -24
+    g4 = 4 * u / (1 - 4 * u)
+    expect = g4 * np.abs(lam) @ np.abs(Wm) @ amax + 2.0 ** -23 * (np.abs(lam) + np.abs(lam @ Wm[:, :s])) @ np.abs(x0)
+    got = oracle.crown_margin(p, lo, hi)["margin"][0]
+    assert got == pytest.approx(expect, rel=1e-12)
+    assert r_.shape == (s,)
+
+
+def test_margin_scales_with_square_of_homogeneous_scaling(oracle):
+    """The ReLU network is positively homogeneous once its biases scale too: scaling x_0, the goal, the boxes
+    and every bias by c > 0 scales every state, pre-activation and coefficient by c and the objective by c^2,
+    so every margin term (a coefficient times a variable's magnitude) scales by c^2."""
+    p = W.make_problem(4, 2, [32, 32], 5, 0.01, seed=40, weight_scale=0.5)
+    lo, hi, _ = W.random_boxes(10, 4, seed=41, min_width=0.2, max_width=1.0)
+    r = oracle.crown_margin(p, lo, hi)
+    cfac = 4.0  # a power of two: the scaled inputs are exact
+    q = dict(p)
+    q["x0"] = np.asarray(p["x0"], np.float64) * cfac
+    q["goal"] = np.asarray(p["goal"], np.float64) * cfac
+    q["params"] = W.pack_params([(Wl, bl * cfac) for Wl, bl in W.unpack_params(p)])
+    rq = oracle.crown_margin(q, lo * cfac, hi * cfac)
+    np.testing.assert_allclose(rq["lb"], r["lb"] * cfac ** 2, rtol=1e-12)
+    np.testing.assert_allclose(rq["margin"], r["margin"] * cfac ** 2, rtol=1e-12)
+
+
+def test_margin_one_hidden_layer_closed_form(oracle):
+    """One step through a 2-2-1 network (s = k = 1) whose first hidden neuron is active and whose second is
+    unstable with a negative coefficient (the chord of Lemma 1), with rho > 0 and the minimiser of mu u + rho u^2
+    outside the box: every term of the margin is present and each is written out here from the intervals by
+    hand: gamma_4 |lam| S^(2) for the output layer, gamma_4 sum_q |A'_q| S^(1)_q for the hidden layer,
+    2^-23 |A'_1| max(-l_1, u_1) for the chord's slope product, 2^-23 (|lam| + |A_x|) |x_0| for the state update
+    and rho (2^-23 u_c)^2 for the face of the box."""
+    rng = np.random.default_rng(11)
+    gam4 = 4 * 2.0 ** -24 / (1 - 4 * 2.0 ** -24)
+    tu = 2.0 ** -23
+    for _ in range(2000):
+        W1 = rng.uniform(-1, 1, size=(2, 2))
+        b1 = rng.uniform(-0.5, 0.5, size=2)
+        W2 = rng.uniform(-1, 1, size=(1, 2))
+        b2 = rng.uniform(-0.2, 0.2, size=1)
+        x0, g = rng.uniform(-1, 1), rng.uniform(-1, 1)
+        lo, hi = sorted(rng.uniform(-1, 1, size=2))
+        rho = 1e-3
+        # interval bounds by hand (centre / radius)
+        c0, r0 = np.array([x0, 0.5 * (lo + hi)]), np.array([0.0, 0.5 * (hi - lo)])
+        zc, zr = W1 @ c0 + b1, np.abs(W1) @ r0
+        l1, u1 = zc - zr, zc + zr
+        a_lo, a_hi = np.maximum(l1, 0), np.maximum(u1, 0)
+        c1, r1 = 0.5 * (a_lo + a_hi), 0.5 * (a_hi - a_lo)
+        x1l = x0 + (W2 @ c1 + b2 - np.abs(W2) @ r1)[0]
+        x1u = x0 + (W2 @ c1 + b2 + np.abs(W2) @ r1)[0]
+        lam = 2 * (0.5 * (x1l + x1u) - g)
+        A = lam * W2[0]
+        if not (l1[0] > 0 and l1[1] < 0 < u1[1] and A[1] < 0):
+            continue
+        D1 = u1[1] / (u1[1] - l1[1])
+        Ap = np.array([A[0], A[1] * D1])
+        Ax, Au = Ap @ W1[:, 0], Ap @ W1[:, 1]
+        uc = -Au / (2 * rho)
+        if lo <= uc <= hi:
+            continue
+        S2 = np.abs(W2[0]) @ a_hi
+        S1 = np.abs(W1) @ np.array([abs(x0), max(abs(lo), abs(hi))])
+        expect = (gam4 * abs(lam) * S2 + gam4 * np.abs(Ap) @ S1 + tu * abs(Ap[1]) * max(-l1[1], u1[1])
+                  + tu * (abs(lam) + abs(Ax)) * abs(x0) + rho * (tu * uc) ** 2)
+        p = dict(dims=[2, 2, 1], params=W.pack_params([(W1, b1), (W2, b2)]), x0=np.array([x0]), goal=np.array([g]),
+                 H=1, rho=rho, s=1, k=1)
+        got = oracle.crown_margin(p, np.array([[lo]]), np.array([[hi]]))["margin"][0]
+        assert got == pytest.approx(expect, rel=1e-12)
+        return
+    pytest.fail("no network with the wanted neuron pattern was drawn")
