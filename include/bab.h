@@ -603,6 +603,20 @@ int bab_get_variant(bab_ctx *ctx, int kernel, int *variant);
 int bab_autotune(bab_ctx *ctx, const float *x0, const float *goal, int horizon, float rho, const float *lo,
                  const float *hi, const uint64_t *id, int n, int samples, int alpha_steps, void *stream);
 
+/*
+ * The FP32 FMA rate of the current GPU in TFLOP/s (2 FLOP per FMA), measured
+ * with CUDA events on `stream`: independent FMA chains in every thread of two
+ * 1024-thread CTAs per SM, best of three timed runs after a warm-up.  No
+ * counterpart in the paper: it is the roof of the kernels that run on CUDA
+ * cores (FP32 rollouts, interval bounds, FP32 CROWN), as the measured copy
+ * bandwidth and BF16 GEMM rate are the roofs of the others.  Synchronises
+ * `stream`.
+ *   tflops         host double: scalar FMA rate (fma.rn.f32).
+ *   tflops_paired  host double (nullable): rate of paired FMAs (fma.rn.f32x2).
+ * Errors: BAB_ERR_INVALID_ARG (tflops NULL), BAB_ERR_CUDA.
+ */
+int bab_probe_fp32_peak(double *tflops, double *tflops_paired, void *stream);
+
 /* Size of the fixed device working area of bab_bound_crown_static. */
 #define BAB_STATIC_SCRATCH_BYTES (16u << 20)
 

@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
     L.bab_prune_branch.argtypes = [_P, _I, _P, _P, _P, _P, _P, _I, _P, _P, _I, _F, _I, _I, _P, _P, _P, _P, _P, _P, _P,
                                    _P]
     L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
+    L.bab_probe_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P]
     L.bab_load_dynamics_batch.argtypes = [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _I,
                                           _I, ctypes.c_uint]
     L.bab_rollout_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _P,
@@ -233,6 +234,15 @@ def bab_bound_crown_static(dims, params, state_dim, action_dim, x0, goal, horizo
                                          int(action_dim), _ptr(x0, f32), _ptr(goal, f32), int(horizon), float(rho),
                                          _ptr(lo, f32), _ptr(hi, f32), int(n), _ptr(lb, f32), _ptr(margin, f32),
                                          _stream(stream))
+
+
+def bab_probe_fp32_peak(stream=None):
+    """Measured FP32 FMA rate of the current GPU in TFLOP/s: (scalar FMAs, paired FMAs)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = load().bab_probe_fp32_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream))
+    if rc != BAB_OK:
+        raise BabError(rc, "bab_probe_fp32_peak failed")
+    return a.value, b.value
 
 
 def bab_alpha_optimize(ctx, x0, goal, horizon, rho, lo, hi, n, steps, lr, lb_best, alpha=None, precision=PREC_FP32,

@@ -240,9 +240,6 @@ cudaError_t launch_synth_incumbent(int d, const float *ub, const float *best_u, 
 cudaError_t launch_cem_init(const CemArgs &c, const float *warm_u, cudaStream_t st);
 cudaError_t launch_cem_step(const CemArgs &c, cudaStream_t st);
 bool rollout_tc_supported(const NetDesc &N, int split, int max_smem);
-// BF16 search with four sample tiles per SM and the activations in shared memory (k_rollout_ss)
-bool rollout_ss_supported(const RolloutArgs &a, int max_smem);
-cudaError_t launch_rollout_ss(RolloutArgs a, int num_sms, cudaStream_t st);
 void k_fill_keys(unsigned long long *keys, int n, cudaStream_t st);
 void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st);
 // search-integrated bounds around an FP32 rollout (a.emp_* set): key init before, float conversion after

@@ -60,6 +60,36 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = pack_bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xFFFF0000u));
 }
 
+// (a.x + b.x, a.y + b.y) and (a.x - b.x, a.y - b.y), each rounded to nearest, as one paired FP32 instruction.
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long x = *reinterpret_cast<unsigned long long *>(&a), y = *reinterpret_cast<unsigned long long *>(&b), z;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    return *reinterpret_cast<float2 *>(&z);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long x = *reinterpret_cast<unsigned long long *>(&a), y = *reinterpret_cast<unsigned long long *>(&b), z;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    return *reinterpret_cast<float2 *>(&z);
+}
+
+// The hidden-layer epilogue of a pair of accumulator columns z = (acc + bias) in one conversion per half:
+// SPLIT = 1: hi = bf16_rn(ReLU(z)); SPLIT = 3: hi = bf16 of ReLU(z) rounded toward zero, so that the residual
+// ReLU(z) - hi is never negative (and is z itself, negative, where z < 0), lo = bf16_rn(ReLU(residual)); hi + lo
+// then carries ReLU(z) to 2^-15 relative.  Low halves hold the even column.
+template <int SPLIT>
+__device__ __forceinline__ void relu_split2(float2 z, uint32_t &hi, uint32_t &lo)
+{
+    if (SPLIT == 3) {
+        asm("cvt.rz.relu.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(z.y), "f"(z.x));
+        const float2 r = sub2(z, make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xFFFF0000u)));
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r.y), "f"(r.x));
+    } else {
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(z.y), "f"(z.x));
+    }
+}
+
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t phase, volatile int *abort)
 {
     bool ok = tc::mbar_wait(bar, phase, abort, kWaitLimitNs);
@@ -315,7 +345,9 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                             cost += c;
                         }
                     } else {
-                        // 16 columns per load: fewer live registers (no spills) for a few more load round trips
+                        // 16 columns per load: fewer live registers (no spills) for a few more load round trips (two
+                        // loads per wait spill at the 96-register cap; four epilogue warps per tile with two 64-column
+                        // waits per layer measured slower: the conversions then run on half as many warps)
                         for (int c0 = c_beg; c0 < c_end; c0 += 16) {
                             uint32_t v[16];
                             tc::tmem_ld16(dcol + c0, v);
@@ -325,17 +357,12 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const float4 bb = b4[q];
-                                const float z0 = fmaxf(__uint_as_float(v[4 * q + 0]) + bb.x, 0.f);
-                                const float z1 = fmaxf(__uint_as_float(v[4 * q + 1]) + bb.y, 0.f);
-                                const float z2 = fmaxf(__uint_as_float(v[4 * q + 2]) + bb.z, 0.f);
-                                const float z3 = fmaxf(__uint_as_float(v[4 * q + 3]) + bb.w, 0.f);
-                                if (SPLIT == 3) {
-                                    split2(z0, z1, ph[2 * q], pl[2 * q]);
-                                    split2(z2, z3, ph[2 * q + 1], pl[2 * q + 1]);
-                                } else {
-                                    ph[2 * q] = pack_bf16x2(z0, z1);
-                                    ph[2 * q + 1] = pack_bf16x2(z2, z3);
-                                }
+                                const float2 z01 = add2(make_float2(__uint_as_float(v[4 * q + 0]), __uint_as_float(v[4 * q + 1])),
+                                                        make_float2(bb.x, bb.y));
+                                const float2 z23 = add2(make_float2(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])),
+                                                        make_float2(bb.z, bb.w));
+                                relu_split2<SPLIT>(z01, ph[2 * q], pl[2 * q]);
+                                relu_split2<SPLIT>(z23, ph[2 * q + 1], pl[2 * q + 1]);
                             }
                             tc::tmem_st8(acol_h + c0 / 2, ph);
                             if (SPLIT == 3) tc::tmem_st8(acol_l + c0 / 2, pl);
@@ -646,6 +673,120 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
 }
 
+// BF16 mode, one problem: the same FP32 re-score as k_rescore_fp32 for a tile of RR boxes at once (one row per
+// box: its chosen sample), the layers as register-blocked FP32 products over the tile with the network image in
+// shared memory (WSMEM) or read through L1, so that each weight read serves RR boxes.  Every box of the tile is
+// evaluated; only those the top-k selection admits (all without one) get their ub replaced.
+constexpr int kRescoreRows = 28;  // 4096 boxes make 147 CTAs: one wave on 152 SMs
+template <bool WSMEM>
+__global__ void __launch_bounds__(256) k_rescore_rows(RolloutArgs a)
+{
+    constexpr int RR = kRescoreRows, NT = 256;
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, L = N.L, d = a.d, ld = N.maxw_p, s4 = pad4(s), Kp1 = pad4(s + k);
+    const float *img = a.fwd;
+    float *p = sm;
+    if (WSMEM) {
+        for (int i = threadIdx.x; i < N.img_floats / 4; i += NT) smem4[i] = reinterpret_cast<const float4 *>(a.fwd)[i];
+        img = sm;
+        p += N.img_floats;
+    }
+    float *act0 = p; p += RR * ld;
+    float *act1 = p; p += RR * ld;
+    float *xs = p; p += RR * s4;
+    float *us = p; p += RR * pad4(k);
+    float *fsum = p; p += RR;
+    __shared__ uint64_t hbs[RR];
+    __shared__ uint32_t ms[RR];
+    __shared__ int take[RR];
+    const int nlive = live_count(a.n, a.d_n);
+    const int row0 = blockIdx.x * RR;
+    if (row0 >= nlive) return;  // the whole tile is beyond the live rows (so below, nlive >= 1)
+    Thresh T;
+    if (a.topk > 0) {
+        T.key = (uint32_t)a.topk_t[0];
+        T.id = a.topk_t[1];
+        T.none = a.topk_t[2] != 0;
+    }
+    for (int r = threadIdx.x; r < RR; r += NT) {
+        const int box = row0 + r < nlive ? row0 + r : nlive - 1;  // idle rows recompute a valid box, unused
+        take[r] = row0 + r < nlive && (a.topk <= 0 || le_thresh(float_order(a.ub[box]), a.id[box], T));
+        hbs[r] = box_hash(a.seed, a.id[box]);
+        ms[r] = (uint32_t)(a.keys[box] & 0xFFFFFFFFull);
+        fsum[r] = 0.f;
+    }
+    for (int i = threadIdx.x; i < RR * s; i += NT) xs[(i / s) * s4 + i % s] = a.x0[i % s];
+    __syncthreads();
+    for (int t = 0; t < a.H; ++t) {
+        for (int i = threadIdx.x; i < RR * Kp1; i += NT) {
+            const int r = i / Kp1, c = i % Kp1;
+            const int box = row0 + r < nlive ? row0 + r : nlive - 1;
+            float v = 0.f;
+            if (c < s) {
+                v = xs[r * s4 + c];
+            } else if (c < s + k) {
+                const int j = t * k + (c - s);
+                v = draw_sample(hbs[r], ms[r], (uint32_t)j, a.lo[(size_t)box * d + j], a.hi[(size_t)box * d + j]);
+                us[r * pad4(k) + (c - s)] = v;
+            }
+            act0[r * ld + c] = v;
+        }
+        __syncthreads();
+        float *in = act0, *out = act1;
+        for (int l = 1; l <= L; ++l) {
+            dense_rows_auto<RR, NT>(in, ld, img + N.fwd_w[l], img + N.fwd_b[l], pad4(N.dims[l - 1]), pad4(N.dims[l]),
+                                    out, ld, l < L);
+            __syncthreads();
+            float *tmp = in;
+            in = out;
+            out = tmp;
+        }
+        // the step's action cost (inputs in index order), then the state cost, as k_rescore_fp32 sums them
+        for (int r = threadIdx.x; r < RR; r += NT) {
+            float f = fsum[r];
+            for (int j = 0; j < k; ++j) {
+                const float u = us[r * pad4(k) + j];
+                f = fmaf(a.rho * u, u, f);
+            }
+            float c = 0.f;
+            for (int i = 0; i < s; ++i) {
+                const float x = xs[r * s4 + i] + in[r * ld + i];
+                xs[r * s4 + i] = x;
+                const float e = x - a.goal[i];
+                c = fmaf(e, e, c);
+            }
+            fsum[r] = f + c;
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < RR; r += NT)
+        if (take[r]) a.ub[row0 + r] = fsum[r];
+}
+
+static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
+{
+    const NetDesc &N = a.net;
+    if (a.batch.P > 1) {
+        k_rescore_fp32<<<a.n, 256, 0, st>>>(a);  // each box reads its own problem's image
+        return cudaGetLastError();
+    }
+    int dev, budget = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&budget, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t rest =
+        ((size_t)2 * kRescoreRows * N.maxw_p + (size_t)kRescoreRows * (pad4(N.s) + pad4(N.k)) + kRescoreRows) * 4;
+    const size_t img = (size_t)N.img_floats * 4;
+    const bool wsmem = img + rest + 1024 <= (size_t)budget;
+    const size_t smem = (wsmem ? img : 0) + rest;
+    auto kern = wsmem ? k_rescore_rows<true> : k_rescore_rows<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(a.n + kRescoreRows - 1) / kRescoreRows, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NSLOT, int SPLIT, int SX, bool STREAM, bool CEM, bool OBST>
 static cudaError_t launch_tc_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
 {
@@ -769,7 +910,8 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     launch_rollout_finalize(a, st);  // ub and best_u from the packed minima
     if (split == 1) {
         if (a.topk > 0) k_topk_select<<<1, 1024, 0, st>>>(a);
-        k_rescore_fp32<<<a.n, 256, 0, st>>>(a);
+        e = launch_rescore(a, st);
+        if (e != cudaSuccess) return e;
     }
     if (a.inc_val) launch_incumbent(a, st);
     return cudaGetLastError();
