@@ -127,9 +127,57 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def fp32_alu_peak_tflops(sm_mhz):
-    """Dense FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+_FP32_PEAK = None
+
+
+def fp32_peak_measured():
+    """The FP32 FMA rate measured on this GPU by the library's probe kernel (best of scalar and paired FMAs),
+    TFLOP/s; measured once per process."""
+    global _FP32_PEAK
+    if _FP32_PEAK is None:
+        from paper_2412_09584_gb300 import binding as B
+        scalar, paired = B.bab_probe_fp32_peak()
+        _FP32_PEAK = {"tflops": max(scalar, paired), "scalar": scalar, "paired": paired}
+    return _FP32_PEAK
+
+
+def bf16_peaks():
+    """Measured BF16 GEMM rates of the GB300s (burst, sustained) in TFLOP/s, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        return pk.get("bf16_tflops", 1900.0), pk.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 1900.0, 1700.0, "fallback"
+
+
+def rollout_roofline(precision, p, nb, M, H, roll_ms):
+    """Roofline of the rollout kernel: algorithmic FLOPs (2 x the network's MACs per rollout-step) per launch over
+    its CUDA-event duration, against the measured FP32 FMA rate (CUDA cores) or the measured BF16 burst rate (the
+    kernel is timed on its own); for the tensor-core paths also what the pipe executes (3 MMAs per product for the
+    3-term split, layers padded to multiples of 16)."""
+    macs = sum(a * b for a, b in zip(p["dims"][1:], p["dims"][:-1]))
+    achieved = 2.0 * nb * M * H * macs / (roll_ms / 1e3) / 1e12
+    if precision == "fp32":
+        pk = fp32_peak_measured()
+        roof = {"kernel": "k_rollout_fp32 (bab_rollout)", "bound": "alu", "peak": pk["tflops"],
+                "peak_note": "of measured FP32 FMA rate (bab_probe_fp32_peak on this GPU, best of scalar "
+                             f"{pk['scalar']:.1f} and paired {pk['paired']:.1f} TFLOP/s)"}
+    else:
+        burst, _, kind = bf16_peaks()
+        roof = {"kernel": "k_rollout_tc (bab_rollout)", "bound": "tensor", "peak": burst,
+                "peak_note": f"of {kind} bf16 burst (MEASURED_PEAKS.json): the kernel is timed on its own with CUDA "
+                             "events; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe "
+                             "executes " + ("3x that (3-term BF16 split)" if precision == "bf16x3" else "the same") +
+                             " plus padding to multiples of 16"}
+    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
+    if precision != "fp32":
+        dims = p["dims"]
+        pad16 = lambda v: (v + 15) // 16 * 16
+        ex = sum(pad16(8 + p["s"] if l == 1 else dims[l - 1]) * pad16(dims[l]) for l in range(1, len(dims)))
+        ratio = (3 if precision == "bf16x3" else 1) * ex / macs
+        roof.update({"executed_per_algorithmic": ratio, "executed": achieved * ratio,
+                     "executed_frac": achieved * ratio / roof["peak"]})
+    return roof
 
 
 class BabState:
@@ -430,6 +478,7 @@ def run_ours(args):
     # the single-GPU comparisons run at N = 1 only (a multi-rank run reports the scaled iteration alone)
     extra = ws == 1
     ttg = time_to_gap(dev) if extra and not args.no_time_to_gap else None
+    ttg_push = time_to_gap_pushing(dev) if extra and not args.no_time_to_gap else None
     tiny = tiny_latency(dev) if extra and not args.no_time_to_gap else None
     batched = batched_bab(dev) if extra and not args.no_batched else None
     manip = manip_scale(dev) if extra and not args.no_manip else None
@@ -442,32 +491,12 @@ def run_ours(args):
     boxes = st.nb * args.steps * ws
     value = job_rate(st.nb * args.steps, ws, ms)
     rsteps = boxes * st.M * st.H / (ms / 1e3)
-    macs = sum(a * b for a, b in zip(st.p["dims"][1:], st.p["dims"][:-1]))
-    flops_roll = 2.0 * st.nb * st.M * st.H * macs
-    achieved = flops_roll / (statistics.mean(roll_ms) / 1e3) / 1e12
-    if args.precision == "fp32":
-        roof = {"kernel": "k_rollout_fp32 (bab_rollout)", "bound": "alu", "peak": fp32_alu_peak_tflops(2070.0),
-                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz max SM clock"}
-    else:
-        path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-        peaks = json.load(open(path)) if os.path.exists(path) else {}
-        roof = {"kernel": "k_rollout_tc (bab_rollout)", "bound": "tensor",
-                "peak": peaks.get("bf16_tflops_sustained", 1700.0),
-                "peak_note": ("of measured bf16 sustained (MEASURED_PEAKS.json)" if peaks else "of fallback") +
-                             "; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe executes "
-                             + ("3x that (3-term BF16 split)" if args.precision == "bf16x3" else "the same") +
-                             " plus padding to multiples of 16"}
-    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
-                 "traffic": rollout_traffic(args.precision, st.nb, st.M)})
-    if args.precision != "fp32":
-        # what the tensor pipe executes: each product split into 3 (or 1) BF16 MMAs, every layer padded to
-        # multiples of 16 (layer 1 reads the 8 action columns plus the state)
-        dims = st.p["dims"]
-        pad16 = lambda v: (v + 15) // 16 * 16
-        ex = sum(pad16(8 + st.p["s"] if l == 1 else dims[l - 1]) * pad16(dims[l]) for l in range(1, len(dims)))
-        ratio = (3 if args.precision == "bf16x3" else 1) * ex / macs
-        roof.update({"executed_per_algorithmic": ratio, "executed": achieved * ratio,
-                     "executed_frac": achieved * ratio / roof["peak"]})
+    roof = rollout_roofline(args.precision, st.p, st.nb, st.M, st.H, statistics.mean(roll_ms))
+    roof["traffic"] = rollout_traffic(args.precision, st.nb, st.M)
+    # the same iteration with the rollouts in the other arithmetics: all-FP32 (the configuration as named) and
+    # plain BF16 with each box's pick re-scored in FP32 (the search precision the method's plan prescribes)
+    lines = precision_lines(dev, rank_seed(rank), n_pick, args.precision, args.bound_precision) \
+        if ws == 1 and not args.no_precision_lines else None
     if rank != 0:
         return
     cfg = {"workload": "pushing-scale BaB iteration: state 8, action 2, MLP 10-128-128-128-8 ReLU residual, H=20, "
@@ -489,14 +518,55 @@ def run_ours(args):
            "kernel_ms": {"rollout": statistics.mean(roll_ms), "bound": statistics.mean(bound_ms)},
            "crown_subdomain_bounds_per_s_kernel_only": st.nb / (statistics.mean(bound_ms) / 1e3),
            "incumbent_fp64": inc, "roofline": roof, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "batched": batched, "manip_scale": manip,
+           "gpu_launches": st.launches_per_step * args.steps, "time_to_gap": ttg, "time_to_gap_pushing": ttg_push, "batched": batched, "manip_scale": manip,
            "paper_bounding": paper_bounds, "heuristics": heuristics, "cem_search": cem_cmp,
-           "synthetic_objective": synth, "obstacle_cost": obst, "tiny_latency": tiny}
+           "synthetic_objective": synth, "obstacle_cost": obst, "tiny_latency": tiny, "precision_lines": lines,
+           "fp32_peak_measured": fp32_peak_measured()}
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def precision_lines(dev, seed, n_pick, headline, bound_precision, steps=3):
+    """The bench iteration with the rollouts in each arithmetic other than the headline's: CUDA-graph replays of
+    the same pushing-scale iteration, L2 flushed between steps, per-kernel times by CUDA events after the timed
+    region; each with its rollout roofline (FP32 against the measured FP32 FMA rate)."""
+    import torch
+    out = {}
+    for prec in ("fp32", "bf16x3", "bf16"):
+        if prec == headline:
+            continue
+        st = BabState("pushing", seed, dev, n_pick, prec, bound_precision, fixed_launch=True)
+        for _ in range(3):
+            st.step()
+            st.flush_l2()
+        graphs = capture_graphs(st)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(steps):
+            graphs[st.cur].replay()
+            st.cur ^= 1
+            st.flush_l2()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        st.ev = []
+        for _ in range(2):
+            st.step(events=True)
+            st.flush_l2()
+        torch.cuda.synchronize()
+        roll = statistics.mean(e[0].elapsed_time(e[1]) for e in st.ev)
+        bound = statistics.mean(e[1].elapsed_time(e[2]) for e in st.ev)
+        out[prec] = {"rollout_arithmetic": ARITH[prec], "ms_per_step": ms, "subdomain_bounds_per_s": st.nb / (ms / 1e3),
+                     "rollout_steps_per_s": st.nb * st.M * st.H / (ms / 1e3),
+                     "kernel_ms": {"rollout": roll, "bound": bound},
+                     "roofline": rollout_roofline(prec, st.p, st.nb, st.M, st.H, roll), "steps": steps}
+        del graphs
+        st.close()
+    return out
 
 
 def run_e2e(st, steps):
@@ -603,11 +673,14 @@ def manip_scale(dev, reps=3):
 
 
 
-def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None):
+def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None, picks_choices=(8, 16, 32, 64, 128, 160)):
     """Many concurrent plans: P problems of the tiny architecture (own weights, start, goal; horizons uniform in
     10..80), each pool starting as a 256-box grid; per iteration, per problem: prune against its incumbent, pick
-    n_pick boxes, split them, search (FP32 rollouts) and bound (interval bounds + alpha-CROWN) the children.
-    Every iteration is one CUDA-graph replay (one launch per kernel for all problems).  Returns timing and gaps."""
+    a problem- and iteration-dependent number of boxes (drawn from picks_choices, so that the live pools spread
+    over about 256-8192 rows and change size every iteration; n_pick for all when picks_choices is None), split
+    them, search (BF16x3 tensor-core rollouts) and bound (interval bounds + alpha-CROWN) the children.  Every
+    iteration is one CUDA-graph replay (one launch per kernel for all problems) after a device-side copy of that
+    iteration's pick counts.  Returns timing, live-pool sizes, pruned rows and gaps."""
     import torch
     from paper_2412_09584_gb300 import binding as B
     from paper_2412_09584_gb300 import workloads as W
@@ -627,6 +700,12 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
                             torch.as_tensor(Hs).to(**i32), torch.as_tensor(rho).to(**f))
     lo, hi, ids, prob = W.batch_grid_boxes(probs, 8, d)
     n0 = lo.shape[0]
+    if picks_choices is not None:
+        rng = np.random.default_rng(SEED + 5)
+        sched_np = rng.choice(np.asarray(picks_choices, dtype=np.int32), size=(iters + 4, P))
+        n_pick = int(max(picks_choices))
+    else:
+        sched_np = np.full((iters + 4, P), n_pick, dtype=np.int32)
     per_iter = P * n_pick
     cap = n0 + (iters + 8) * per_iter
     nb = 2 * per_iter
@@ -648,6 +727,7 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
     counts = torch.zeros(3, **i32)
     n_live = torch.tensor([n0], **i32)
     picks = torch.full((P,), n_pick, **i32)
+    sched = torch.as_tensor(sched_np).to(**i32)
     # tile shapes timed on problem 0's starting boxes (the grid rows are grouped by problem)
     r0, d0 = int((prob == 0).sum()), k * int(Hs[0])
     B.bab_autotune(ctx, tx0[0].contiguous(), tgoal[0].contiguous(), int(Hs[0]), float(rho[0]),
@@ -659,7 +739,7 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
         B.bab_bound_batch(ctx, tx0, tgoal, tH, trho, Hmax, d, Q["lo"], Q["hi"], Q["prob"], n, Q["lb"],
                           alpha_steps=alpha_steps, lr=c["alpha_lr"], d_n=d_n)
 
-    state = {"cur": 0}
+    state = {"cur": 0, "it": 0}
     n_max = cap - per_iter
 
     def step():
@@ -675,11 +755,13 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        for _ in range(2):  # warm-up (loads every kernel), then one graph per pool parity
+        for i in range(2):  # warm-up (loads every kernel), then one graph per pool parity
+            picks.copy_(sched[i])
             step()
         torch.cuda.synchronize()
         graphs = []
-        for _ in range(2):
+        for i in range(2):
+            picks.copy_(sched[2 + i])
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 step()
@@ -687,30 +769,43 @@ def batched_bab(dev, iters=50, n_pick=64, samples=None, alpha_steps=None, P=None
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
     done = 2 + 2  # iterations run so far (two eager warm-up steps and the two captured ones)
+    picked = sched_np[:done].sum(axis=0).astype(np.int64)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
-    for _ in range(iters - done):
+    for i in range(done, iters):
+        picks.copy_(sched[i])  # this iteration's quota per problem, read by the graph's prune/branch
         graphs[state["cur"]].replay()
         state["cur"] ^= 1
     t1.record()
+    picked += sched_np[done:iters].sum(axis=0)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / (iters - done)
     status = B.bab_status(ctx)
     n = int(counts[2].item())
     Q = pool[state["cur"]]
     lbmin = torch.full((P,), float("inf"), **f).scatter_reduce(0, Q["prob"][:n].long(), Q["lb"][:n], "amin")
-    live = torch.bincount(Q["prob"][:n].long(), minlength=P)
+    live = torch.bincount(Q["prob"][:n].long(), minlength=P).cpu().numpy()
     gaps = (inc_val - lbmin.double()).cpu().numpy()
     B.bab_destroy(ctx)
-    rsteps = float(nb) * samples * float(np.mean(Hs))
+    # every pick replaces a box by its two children (+1 row), every prune removes one: rows created minus live
+    start = np.bincount(prob, minlength=P)
+    pruned = start + picked - live
+    quota = ("per problem and iteration drawn from " + str(list(picks_choices))) if picks_choices is not None \
+        else f"{n_pick} per problem per iteration"
+    children = 2.0 * float(sched_np[done:iters].sum()) / (iters - done)  # children bounded per timed iteration
     return {"workload": f"{P} problems of MLP 6-32-32-4 (own weights, start, goal), horizons uniform in "
-                        f"[{c['H_lo']}, {c['H_hi']}], 256-box starting grid each, {n_pick} boxes picked and split per "
-                        f"problem per iteration, {samples} BF16x3 tensor-core rollouts per child, interval bounds + alpha-CROWN "
+                        f"[{c['H_lo']}, {c['H_hi']}], 256-box starting grid each, boxes picked and split {quota}, "
+                        f"{samples} BF16x3 tensor-core rollouts per child, interval bounds + alpha-CROWN "
                         f"({alpha_steps} Adam steps) per child",
-            "iterations": iters, "ms_per_iteration": ms, "children_per_iteration": nb,
-            "subdomain_bounds_per_s": nb / (ms / 1e3), "rollout_steps_per_s": rsteps / (ms / 1e3),
-            "launches_per_iteration": 3 + 4 + 2, "timed_region": "CUDA-graph replays, one launch per kernel",
-            "live_rows_end": n, "live_rows_per_problem_end": [int(live.min()), int(live.max())],
+            "iterations": iters, "ms_per_iteration": ms, "children_per_iteration_mean": children,
+            "launch_rows_per_iteration": nb,
+            "subdomain_bounds_per_s": children / (ms / 1e3),
+            "rollout_steps_per_s": children * samples * float(np.mean(Hs)) / (ms / 1e3),
+            "launches_per_iteration": 3 + 4 + 2 + 1, "timed_region": "CUDA-graph replays, one launch per kernel, "
+                                                                    "after a device copy of the iteration's quotas",
+            "live_rows_end": n, "live_rows_per_problem_end": {"min": int(live.min()), "median": float(np.median(live)),
+                                                               "max": int(live.max())},
+            "pruned_rows": {"total": int(pruned.sum()), "problems_with_pruning": int((pruned > 0).sum())},
             "gap_end": {"min": float(gaps.min()), "median": float(np.median(gaps)), "max": float(gaps.max())},
             "device_status": status}
 
@@ -981,15 +1076,15 @@ def tiny_latency(dev, reps=200):
     return out
 
 
-def time_to_gap(dev, iters=20, max_iters=60):
-    """Wall time for alpha-optimised, split-precision BaB to reach the optimality gap that plain FP32
-    CROWN+IBP BaB reaches after `iters` iterations, on the 4096-box alpha workload (tiny network, H=5,
-    20 Adam steps of lr 0.1 per iteration).  Gap = FP64 incumbent - smallest lower bound of the live pool."""
+def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, variants=None):
+    """Wall time for alpha-optimised and split-precision BaB variants to reach the optimality gap that plain FP32
+    CROWN+IBP BaB reaches after `iters` iterations.  Gap = FP64 incumbent - smallest lower bound of the live pool
+    (read back every iteration by every variant alike)."""
     import torch
 
     def run(rprec, bprec, alpha_steps, n_iter, target=None):
-        st = BabState("alpha", SEED, dev, 2048, rprec, bprec, alpha_steps=alpha_steps, pool_iters=max_iters + 2,
-                      autotune=True)
+        st = BabState(workload, SEED, dev, n_pick, rprec, bprec, alpha_steps=alpha_steps,
+                      pool_iters=max_iters + 2, autotune=True)
         torch.cuda.synchronize()
         t = time.perf_counter()
         hist = []
@@ -1005,16 +1100,21 @@ def time_to_gap(dev, iters=20, max_iters=60):
 
     # plain: FP32 rollouts and FP32 CROWN; split: 3-term BF16 tensor-core rollouts and CROWN; alpha_split: split
     # plus 20 Adam steps per iteration, each a tensor-core CROWN + adjoint + Adam launch; alpha_fused: 3-term BF16
-    # rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration
-    variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
-                "alpha_split": ("bf16x3", "bf16x3", 20), "alpha_fused": ("bf16x3", "fp32", 20)}
+    # rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration; alpha_fused_5: the same with 5
+    # Adam steps (the bound gains most in the first steps)
+    if variants is None:
+        variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
+                    "alpha_split": ("bf16x3", "bf16x3", 20), "alpha_fused": ("bf16x3", "fp32", 20),
+                    "alpha_fused_5": ("bf16x3", "fp32", 5)}
     for v in variants.values():  # load every kernel and size every scratch buffer before timing
         run(*v, n_iter=2)
     plain = run(*variants["plain_fp32"], n_iter=iters)
     target = plain[-1][1]
-    out = {"workload": "alpha: MLP 6-32-32-4, H=5, 4096 children per iteration, 256 rollouts each; gap = FP64 "
-                       "incumbent - min lower bound of the live pool; target = plain FP32 BaB's gap after "
-                       f"{iters} iterations", "target_gap": target}
+    c = W_CONFIGS()[workload]
+    dims = "-".join(str(x) for x in [c["s"] + c["k"]] + list(c["hidden"]) + [c["s"]])
+    out = {"workload": f"{workload}: MLP {dims}, H={c['H']}, {2 * n_pick} children per iteration, "
+                       f"{c['samples']} rollouts each; gap = FP64 incumbent - min lower bound of the live pool; "
+                       f"target = plain FP32 BaB's gap after {iters} iterations", "target_gap": target}
     plain_variants = run.variants
     for name, v in variants.items():
         h = plain if name == "plain_fp32" else run(*v, n_iter=max_iters, target=target)
@@ -1026,6 +1126,19 @@ def time_to_gap(dev, iters=20, max_iters=60):
         if name != "plain_fp32":
             out[name]["speedup_vs_plain"] = plain[-1][0] / h[-1][0] if reached else None
     return out
+
+
+def W_CONFIGS():
+    from paper_2412_09584_gb300 import workloads as W
+    return W.CONFIGS
+
+
+def time_to_gap_pushing(dev):
+    """Time-to-gap on the pushing network (MLP 10-128-128-128-8, H = 20), 512 children per iteration."""
+    variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
+                "split_fp32_bound": ("bf16x3", "fp32", 0), "alpha_fused": ("bf16x3", "fp32", 20),
+                "alpha_fused_5": ("bf16x3", "fp32", 5), "alpha_split": ("bf16x3", "bf16x3", 5)}
+    return time_to_gap(dev, "pushing", n_pick=256, iters=10, max_iters=30, variants=variants)
 
 
 def oracle_sample_step(problem, lo, hi, ids, M, n_roll, n_bound, pool_n, n_pick):
@@ -1187,10 +1300,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch heuristics instead of bab_autotune")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-problem BaB section")
     ap.add_argument("--no-manip", action="store_true", help="skip the object-manipulation-scale section")
+    ap.add_argument("--no-precision-lines", action="store_true",
+                    help="skip the same iteration with the rollouts in the other arithmetics")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")
-    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16x3",
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16",
                     help="rollout arithmetic: fp32 (CUDA cores), bf16x3 (tcgen05, 3-term split), bf16 (tcgen05)")
     ap.add_argument("--boxes", type=int, default=4096,
                     help="children bounded per iteration; smaller values make small cases for profiler captures")

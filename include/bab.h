@@ -584,6 +584,24 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  */
 int bab_set_rescore_topk(bab_ctx *ctx, int k);
 
+/*
+ * Limit the context's scratch device memory to `bytes` (0: no limit, the
+ * default).  The working set of a bound call grows with n x H x (hidden
+ * width): interval bounds, the rounding-error helpers and, for the alpha
+ * adjoint, the pre-relaxation coefficients and the concretizing point of every
+ * box (about 1.3 MB a box for MLP 36-256x4-32 at H = 40).  Under a limit,
+ * bab_bound_crown, bab_box_grad and bab_alpha_optimize bound the boxes in
+ * consecutive chunks whose working set fits, recomputing each chunk's interval
+ * bounds instead of holding them for all n; every box is bounded on its own,
+ * so the results are bit-identical to one pass.  With d_n the device count is
+ * read relative to each chunk's first row.  A scratch larger than the new
+ * limit is freed at once (the call synchronises the device then).  No
+ * counterpart in the paper (a memory policy of this library).
+ * Errors: BAB_ERR_INVALID_ARG (null context); a later call whose single box
+ * needs more than the limit returns BAB_ERR_OOM.
+ */
+int bab_set_scratch_limit(bab_ctx *ctx, size_t bytes);
+
 #define BAB_KERNEL_ROLLOUT_FP32 0
 #define BAB_KERNEL_ALPHA_FUSED 1
 #define BAB_KERNEL_ROLLOUT_TC 2

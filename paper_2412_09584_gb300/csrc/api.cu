@@ -30,6 +30,7 @@ struct bab_ctx {
     int tune_rollout_tc = -1;   // tiles per CTA
     int tune_crown_tc = -1;     // tiles per CTA
     int rescore_topk = 0;       // BF16 rollouts: FP32 re-score of the topk smallest ub (0: every box)
+    size_t scratch_limit = 0;   // bab_set_scratch_limit: bound calls chunk their boxes to stay within it (0: none)
     CostDesc cost{};            // the state cost (bab_set_cost); kind 0 by default
     int cost_H = 0;             // horizon its weights cover
     float *d_cost_w = nullptr;  // its weights w_t on the device
@@ -203,6 +204,17 @@ size_t bound_scratch_bytes(const NetDesc &N, int n, int H, int d, bool alpha)
     return f * sizeof(float) + 16 * 256;
 }
 
+// Boxes per pass of a bound call whose scratch is `fixed` bytes plus `per_row` bytes a box: all n without a
+// limit or when they fit it, else as many as fit (0 when not even one box does).  Every box is bounded
+// independently, so consecutive passes give the same bits as one.
+int chunk_rows(const bab_ctx *c, size_t fixed, size_t per_row, int n)
+{
+    if (c->scratch_limit == 0 || fixed + (size_t)n * per_row <= c->scratch_limit) return n;
+    if (fixed + per_row > c->scratch_limit) return 0;
+    const size_t r = (c->scratch_limit - fixed) / per_row;
+    return r < (size_t)n ? (int)r : n;
+}
+
 int check_problem(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
                   int n)
 {
@@ -229,9 +241,10 @@ int refuse_obstacles(bab_ctx *c, const char *what)
 }
 
 BoundArgs make_bound_args(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
-                          const float *hi, int n, const int *d_n)
+                          const float *hi, int n, const int *d_n, int row0 = 0)
 {
     BoundArgs a{};
+    a.row0 = row0;
     a.cost = c->cost;
     a.net = c->net;
     a.fwd = c->d_fwd;
@@ -907,25 +920,16 @@ int bab_bound_ibp(bab_ctx *c, const float *x0, const float *goal, int H, float r
     return run_ibp(c, a, cv, pre_lo, pre_hi, x_lo, x_hi, lb_ibp, (cudaStream_t)stream);
 }
 
-int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
-                    int n, const int *d_n, const float *alpha, int precision, float *lb, float *margin,
-                    float *lin_coef, float *lin_const, void *stream)
+// One pass of bab_bound_crown over rows row0 .. row0 + n - 1 (pointers already offset to row0).
+static int bound_crown_pass(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                            const float *hi, int n, const int *d_n, int row0, const float *alpha, int precision,
+                            float *lb, float *margin, float *lin_coef, float *lin_const, void *stream)
 {
-    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
-    if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core CROWN")) != BAB_OK) return rc;
-    if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
-    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
-        return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
     const bool tc = precision == BAB_PREC_BF16X3;
-    if (tc && !crown_tc_supported(c->net, c->max_smem))
-        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN needs hidden widths that are multiples of 32, "
-                                            "s <= 32, s + k <= 48 and a weight image that fits in shared memory");
-    if (n == 0) return BAB_OK;
-    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, tc));
+    int rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, tc));
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n, row0);
     Carver cv{reinterpret_cast<char *>(c->scratch)};
     rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
     if (rc) return rc;
@@ -944,6 +948,37 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
         e = launch_crown(a, c->num_sms, st);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
+    return BAB_OK;
+}
+
+int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                    int n, const int *d_n, const float *alpha, int precision, float *lb, float *margin,
+                    float *lin_coef, float *lin_const, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core CROWN")) != BAB_OK) return rc;
+    if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
+    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
+        return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
+    const bool tc = precision == BAB_PREC_BF16X3;
+    if (tc && !crown_tc_supported(c->net, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN needs hidden widths that are multiples of 32, "
+                                            "s <= 32, s + k <= 48 and a weight image that fits in shared memory");
+    if (n == 0) return BAB_OK;
+    const int d = c->net.k * H;
+    const size_t per_row = bound_scratch_bytes(c->net, 1, H, d, tc) - 16 * 256 + (tc && !lin_coef ? (size_t)d * 4 : 0);
+    const int rows = chunk_rows(c, 16 * 256 + 256, per_row, n);
+    if (rows == 0) return fail(c, BAB_ERR_OOM, "one box needs more scratch than the limit");
+    for (int r0 = 0; r0 < n; r0 += rows) {
+        const int m = n - r0 < rows ? n - r0 : rows;
+        const size_t ro = (size_t)r0;
+        rc = bound_crown_pass(c, x0, goal, H, rho, lo + ro * d, hi + ro * d, m, d_n, r0,
+                              alpha ? alpha + ro * H * c->net.sumh : nullptr, precision, lb + ro,
+                              margin ? margin + ro : nullptr, lin_coef ? lin_coef + ro * d : nullptr,
+                              lin_const ? lin_const + ro : nullptr, stream);
+        if (rc) return rc;
+    }
     return BAB_OK;
 }
 
@@ -1062,23 +1097,19 @@ int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float 
     return BAB_OK;
 }
 
-int bab_box_grad(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
-                 int n, const int *d_n, const float *alpha, float *lb, float *grad_lo, float *grad_hi, void *stream)
+// One pass of bab_box_grad over rows row0 .. row0 + n - 1 (pointers already offset to row0).
+static int box_grad_pass(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                         const float *hi, int n, const int *d_n, int row0, const float *alpha, float *lb,
+                         float *grad_lo, float *grad_hi, void *stream)
 {
-    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
-    if (rc) return rc;
-    rc = refuse_obstacles(c, "the box gradient");
-    if (rc) return rc;
-    if (n > 0 && (!lb || !grad_lo || !grad_hi)) return fail(c, BAB_ERR_INVALID_ARG, "lb, grad_lo and grad_hi are required");
-    if (n == 0) return BAB_OK;
     const NetDesc &N = c->net;
     const int d = N.k * H;
     const size_t nh = (size_t)n * H * N.sumh, nx = (size_t)n * (H + 1) * N.s;
-    rc = ensure_scratch(c, bound_scratch_bytes(N, n, H, d, true) + (3 * nh + nx + 2 * (size_t)n * d) * sizeof(float) +
+    int rc = ensure_scratch(c, bound_scratch_bytes(N, n, H, d, true) + (3 * nh + nx + 2 * (size_t)n * d) * sizeof(float) +
                                8 * 256);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n, row0);
     Carver cv{reinterpret_cast<char *>(c->scratch)};
     rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
     if (rc) return rc;
@@ -1095,27 +1126,44 @@ int bab_box_grad(bab_ctx *c, const float *x0, const float *goal, int H, float rh
     return BAB_OK;
 }
 
-int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
-                       const float *hi, int n, const int *d_n, int steps, float lr, int precision, float *alpha,
-                       float *lb_best, void *stream)
+int bab_box_grad(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
+                 int n, const int *d_n, const float *alpha, float *lb, float *grad_lo, float *grad_hi, void *stream)
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha optimisation")) != BAB_OK)
-        return rc;
-    if (n > 0 && !lb_best) return fail(c, BAB_ERR_INVALID_ARG, "lb_best is required");
-    if (steps < 1 || steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "steps must be in [1, 100000]");
-    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
-    rc = check_bound_precision(c, precision);
+    rc = refuse_obstacles(c, "the box gradient");
     if (rc) return rc;
+    if (n > 0 && (!lb || !grad_lo || !grad_hi)) return fail(c, BAB_ERR_INVALID_ARG, "lb, grad_lo and grad_hi are required");
     if (n == 0) return BAB_OK;
+    const NetDesc &N = c->net;
+    const int d = N.k * H;
+    const size_t per_row = bound_scratch_bytes(N, 1, H, d, true) - 16 * 256 +
+                           (3 * (size_t)H * N.sumh + (size_t)(H + 1) * N.s + 2 * (size_t)d) * sizeof(float);
+    const int rows = chunk_rows(c, 16 * 256 + 8 * 256, per_row, n);
+    if (rows == 0) return fail(c, BAB_ERR_OOM, "one box needs more scratch than the limit");
+    for (int r0 = 0; r0 < n; r0 += rows) {
+        const int m = n - r0 < rows ? n - r0 : rows;
+        const size_t ro = (size_t)r0;
+        rc = box_grad_pass(c, x0, goal, H, rho, lo + ro * d, hi + ro * d, m, d_n, r0,
+                           alpha ? alpha + ro * H * N.sumh : nullptr, lb + ro, grad_lo + ro * d, grad_hi + ro * d,
+                           stream);
+        if (rc) return rc;
+    }
+    return BAB_OK;
+}
+
+// One pass of bab_alpha_optimize over rows row0 .. row0 + n - 1 (pointers already offset to row0).
+static int alpha_optimize_pass(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                               const float *hi, int n, const int *d_n, int row0, int steps, float lr, int precision,
+                               float *alpha, float *lb_best, void *stream)
+{
     const int d = c->net.k * H;
     const size_t nh = (size_t)n * H * c->net.sumh;
-    rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, d, true) + (3 * nh + (size_t)n * d) * sizeof(float) +
+    int rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, d, true) + (3 * nh + (size_t)n * d) * sizeof(float) +
                                4 * 256);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n);
+    BoundArgs a = make_bound_args(c, x0, goal, H, rho, lo, hi, n, d_n, row0);
     Carver cv{reinterpret_cast<char *>(c->scratch)};
     // interval bounds do not depend on alpha: once for all steps
     rc = run_ibp(c, a, cv, nullptr, nullptr, nullptr, nullptr, nullptr, st);
@@ -1163,6 +1211,35 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
         const double bc1 = 1.0 - std::pow(0.9, step), bc2 = 1.0 - std::pow(0.999, step);
         if (e == cudaSuccess) e = launch_adam(al, m, v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "alpha step");
+    }
+    return BAB_OK;
+}
+
+int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
+                       const float *hi, int n, const int *d_n, int steps, float lr, int precision, float *alpha,
+                       float *lb_best, void *stream)
+{
+    int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
+    if (rc) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha optimisation")) != BAB_OK)
+        return rc;
+    if (n > 0 && !lb_best) return fail(c, BAB_ERR_INVALID_ARG, "lb_best is required");
+    if (steps < 1 || steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "steps must be in [1, 100000]");
+    if (!(lr >= 0.f) || !std::isfinite(lr)) return fail(c, BAB_ERR_INVALID_ARG, "bad learning rate");
+    rc = check_bound_precision(c, precision);
+    if (rc) return rc;
+    if (n == 0) return BAB_OK;
+    const int d = c->net.k * H;
+    const size_t per_row = bound_scratch_bytes(c->net, 1, H, d, true) - 16 * 256 +
+                           (3 * (size_t)H * c->net.sumh + (size_t)d) * sizeof(float);
+    const int rows = chunk_rows(c, 16 * 256 + 4 * 256, per_row, n);
+    if (rows == 0) return fail(c, BAB_ERR_OOM, "one box needs more scratch than the limit");
+    for (int r0 = 0; r0 < n; r0 += rows) {
+        const int m = n - r0 < rows ? n - r0 : rows;
+        const size_t ro = (size_t)r0;
+        rc = alpha_optimize_pass(c, x0, goal, H, rho, lo + ro * d, hi + ro * d, m, d_n, r0, steps, lr, precision,
+                                 alpha ? alpha + ro * H * c->net.sumh : nullptr, lb_best + ro, stream);
+        if (rc) return rc;
     }
     return BAB_OK;
 }
@@ -1489,6 +1566,21 @@ int bab_set_variant(bab_ctx *c, int kernel, int variant)
             return fail(c, BAB_ERR_INVALID_ARG, "unknown kernel %d", kernel);
     }
     return fail(c, BAB_ERR_INVALID_ARG, "variant %d out of range for kernel %d", variant, kernel);
+}
+
+int bab_set_scratch_limit(bab_ctx *c, size_t bytes)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    c->scratch_limit = bytes;
+    if (bytes > 0 && c->scratch_bytes > bytes) {
+        // give back a larger scratch now; the next call allocates what it needs within the limit
+        cudaDeviceSynchronize();
+        cudaFree(c->scratch);
+        c->scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    return BAB_OK;
 }
 
 int bab_set_rescore_topk(bab_ctx *c, int k)

@@ -199,6 +199,14 @@ __device__ __forceinline__ int live_count(int n, const int *d_n)
     int v = *d_n;
     return v < n ? (v < 0 ? 0 : v) : n;
 }
+// The live rows of a launch that covers rows off .. off + n - 1 of the caller's arrays (a call processed in
+// chunks under a scratch limit): the device count minus the offset, clamped to [0, n].
+__device__ __forceinline__ int live_count(int n, const int *d_n, int off)
+{
+    if (!d_n) return n;
+    int v = *d_n - off;
+    return v < n ? (v < 0 ? 0 : v) : n;
+}
 
 __device__ __forceinline__ float warp_sum(float v)
 {

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
     float *lbacc = p; p += RB;
     float *pbx = p; p += 4 * RB;  // pusher position box per row (obstacle cost): lo x, lo y, hi x, hi y
 
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const int box0 = blockIdx.x * RB;
     if (box0 >= nlive) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(NT) k_crown(BoundArgs a)
         img = sm;
         p += N.img_floats;
     }
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const int box0 = blockIdx.x * RB;
     if (box0 >= nlive) return;
     const int nrows = min(RB, nlive - box0);
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(NT) k_alpha_fwd(BoundArgs a)
         img = sm;
         p += N.img_floats;
     }
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const int box0 = blockIdx.x * RB;
     if (box0 >= nlive) return;
     const int nrows = min(RB, nlive - box0);
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(NTT) k_alpha_fused(BoundArgs a, int steps, flo
     const NetDesc &N = a.net;
     const int H = a.H, d = a.d, s = N.s;
     const size_t hs = (size_t)H * N.sumh, hw = (size_t)H * (N.sumh + s), xs_ = (size_t)(H + 1) * s;
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const int box0 = blockIdx.x * RBT;
     if (box0 >= nlive) return;
     const int nrows = min(RBT, nlive - box0);
@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(NTT) k_alpha_fused(BoundArgs a, int steps, flo
 
 __global__ void k_alpha_init(BoundArgs a)
 {
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const long long total = (long long)nlive * a.H * a.net.sumh;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
         const_cast<float *>(a.alpha)[i] = (a.pre_hi[i] >= -a.pre_lo[i]) ? 1.f : 0.f;

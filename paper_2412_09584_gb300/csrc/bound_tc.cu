@@ -120,7 +120,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
         if (warp < mma_warp + NSLOT && !wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
     }
 
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const int ntiles = (nlive + 127) / 128;
     const int G = gridDim.x * NSLOT;
     const uint32_t tb = tmem_base;

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     float *mu = vin + N.maxw_p;                          // coefficients of u, per warp
     float *us = mu + d4;                                 // concretizing point u*, per warp
 
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const size_t hs = (size_t)Hm * sumh;  // per-box stride of the [H][sumh] arrays
     const bool opt = steps > 0;           // steps == 0: one bound with the adaptive slopes, no adjoint
     int loaded = -1;                      // the problem whose rows are in shared memory
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1)) k_
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {
         const int pb = row_problem(a.batch, box);
         if (!WSMEM) fwd = a.fwd + (size_t)pb * N.img_floats;
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nlive = live_count(a.n, a.d_n);
+    const int nlive = live_count(a.n, a.d_n, a.row0);
     const size_t hs = (size_t)Hm * sumh;
     const bool has_alpha = a.alpha != nullptr;
     for (int box = blockIdx.x * kWarps + wib; box < nlive; box += gridDim.x * kWarps) {

@@ -96,6 +96,7 @@ struct BoundArgs {
     const float *x0, *goal, *lo, *hi;
     int n;
     const int *d_n;
+    int row0;                // the launch's first row within the caller's arrays (chunked calls; d_n counts from 0)
     int H, d;
     float rho;
     // interval bounds (written by k_ibp, read by k_crown / k_alpha_fwd)

@@ -673,10 +673,9 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
 }
 
-// BF16 mode, one problem: the same FP32 re-score as k_rescore_fp32 for a tile of RR boxes at once (one row per
-// box: its chosen sample), the layers as register-blocked FP32 products over the tile with the network image in
-// shared memory (WSMEM) or read through L1, so that each weight read serves RR boxes.  Every box of the tile is
-// evaluated; only those the top-k selection admits (all without one) get their ub replaced.
+// BF16 mode, one problem, every box re-scored: the same FP32 re-score as k_rescore_fp32 for a tile of RR boxes
+// at once (one row per box: its chosen sample), the layers as register-blocked FP32 products over the tile with
+// the network image in shared memory (WSMEM) or read through L1, so that each weight read serves RR boxes.
 constexpr int kRescoreRows = 28;  // 4096 boxes make 147 CTAs: one wave on 152 SMs
 template <bool WSMEM>
 __global__ void __launch_bounds__(256) k_rescore_rows(RolloutArgs a)
@@ -704,15 +703,9 @@ __global__ void __launch_bounds__(256) k_rescore_rows(RolloutArgs a)
     const int nlive = live_count(a.n, a.d_n);
     const int row0 = blockIdx.x * RR;
     if (row0 >= nlive) return;  // the whole tile is beyond the live rows (so below, nlive >= 1)
-    Thresh T;
-    if (a.topk > 0) {
-        T.key = (uint32_t)a.topk_t[0];
-        T.id = a.topk_t[1];
-        T.none = a.topk_t[2] != 0;
-    }
     for (int r = threadIdx.x; r < RR; r += NT) {
         const int box = row0 + r < nlive ? row0 + r : nlive - 1;  // idle rows recompute a valid box, unused
-        take[r] = row0 + r < nlive && (a.topk <= 0 || le_thresh(float_order(a.ub[box]), a.id[box], T));
+        take[r] = row0 + r < nlive;
         hbs[r] = box_hash(a.seed, a.id[box]);
         ms[r] = (uint32_t)(a.keys[box] & 0xFFFFFFFFull);
         fsum[r] = 0.f;
@@ -768,8 +761,9 @@ __global__ void __launch_bounds__(256) k_rescore_rows(RolloutArgs a)
 static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
 {
     const NetDesc &N = a.net;
-    if (a.batch.P > 1) {
-        k_rescore_fp32<<<a.n, 256, 0, st>>>(a);  // each box reads its own problem's image
+    if (a.batch.P > 1 || a.topk > 0) {
+        // each box reads its own problem's image; with a top-k selection all but k boxes return at once
+        k_rescore_fp32<<<a.n, 256, 0, st>>>(a);
         return cudaGetLastError();
     }
     int dev, budget = 0;
