@@ -423,8 +423,9 @@ int bab_set_cost(bab_ctx *c, int kind, int H, const float *w, float lambda, int 
         return BAB_OK;
     }
     if (kind != BAB_COST_PUSHING_OBSTACLES) return fail(c, BAB_ERR_INVALID_ARG, "unknown cost kind %d", kind);
-    if (c->net.L >= 1 && (c->net.k != 2 || c->net.s % 2 != 0))
-        return fail(c, BAB_ERR_UNSUPPORTED, "the obstacle cost needs planar keypoints (s even) and a planar pusher (k = 2)");
+    if (c->net.L >= 1 && (c->net.k != 2 || c->net.s % 2 != 0 || c->net.s > 32))
+        return fail(c, BAB_ERR_UNSUPPORTED, "the obstacle cost needs planar keypoints (s even, at most 32 states: its "
+                                            "relaxation gives one warp lane to each coordinate) and a planar pusher (k = 2)");
     if (H < 1 || H > (1 << 20) || !w || !p0 || n_obs < 0 || n_obs > kMaxObstacles || (n_obs > 0 && !obstacles))
         return fail(c, BAB_ERR_INVALID_ARG, "bad horizon, weights, obstacles (at most %d) or pusher start", kMaxObstacles);
     if (!(lambda >= 0.f) || !std::isfinite(lambda)) return fail(c, BAB_ERR_INVALID_ARG, "lambda must be finite and >= 0");
@@ -1179,11 +1180,7 @@ static int alpha_optimize_pass(bab_ctx *c, const float *x0, const float *goal, i
     }
     float *al = alpha ? alpha : cv.take<float>(nh);
     float *m = cv.take<float>(nh), *v = cv.take<float>(nh);
-    // the warp-per-box loop has the squared-distance cost only: with the obstacle cost the heuristic choice (-1)
-    // takes the separate launches and an explicit request (3) is refused
-    if (precision == BAB_PREC_FP32 && fv == 3 && (rc = refuse_obstacles(c, "the warp-per-box alpha loop")) != BAB_OK)
-        return rc;
-    if (precision == BAB_PREC_FP32 && (fv == -1 || fv == 3) && c->cost.kind == 0) {
+    if (precision == BAB_PREC_FP32 && (fv == -1 || fv == 3)) {
         // the whole loop in one launch, one warp per box
         a.A_pre = cv.take<float>(nh);
         a.lb_best = lb_best;

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     const int nlive = live_count(a.n, a.d_n, a.row0);
     const size_t hs = (size_t)Hm * sumh;  // per-box stride of the [H][sumh] arrays
     const bool opt = steps > 0;           // steps == 0: one bound with the adaptive slopes, no adjoint
+    const bool obst = a.cost.kind == 1;   // the pushing-with-obstacles cost (one problem, s <= 32)
     int loaded = -1;                      // the problem whose rows are in shared memory
     for (int base = blockIdx.x * kWarps; base < nlive; base += gridDim.x * kWarps) {
         // a round of kWarps boxes; the rows of its first box's problem serve every box of that problem
@@ -222,7 +223,18 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
             // ------------------------------ bound (Theorems 1-2) ------------------------------
             float A[P], lam[P], tmp[P];
             float cst, mg = 0.f;
-            {
+            // the pushing-with-obstacles cost: the pusher penalties' coefficient of every earlier action (2) and
+            // the sum of its magnitudes (2), accumulated backward from step H (the same values on every lane)
+            float Pu[4] = {0.f, 0.f, 0.f, 0.f};
+            if (obst) {
+                // its linear lower bound on x_H (lane i the coefficient of coordinate i < s <= 32), then the pusher
+                // penalties at H
+                float aa = 0.f;
+                float c = obstacle_state_lin(a.cost, H, s, xlo + (size_t)H * s, xhi + (size_t)H * s, goal, lane, aa);
+#pragma unroll
+                for (int q = 0; q < P; ++q) lam[q] = (q == 0 && lane < s) ? aa : 0.f;
+                cst = __fadd_rd(c, pusher_lin(a.cost, H, k, blo, bhi, Pu, Pu + 2));
+            } else {
                 float c = 0.f;
 #pragma unroll
                 for (int q = 0; q < P; ++q) {
@@ -296,6 +308,42 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
                     dense_b(A, l, tmp);
 #pragma unroll
                     for (int q = 0; q < P; ++q) A[q] = tmp[q];
+                }
+                if (obst) {
+                    // mu_t = A_u + the pusher coefficient of the later steps (its rounding, H additions, in the
+                    // margin), each action's term on lane j as in crown_rows; lam <- lam + A_x + the obstacle cost's
+                    // coefficient at x_t; then the pusher penalties at t
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        const int i = lane + 32 * q;
+                        if (i >= s && i < s + k) mu[t * k + (i - s)] = A[q];
+                    }
+                    __syncwarp();
+                    float e = 0.f;
+                    for (int j = lane; j < k; j += 32) {
+                        const float Au = mu[t * k + j];
+                        const float Pj = j < 2 ? Pu[j] : 0.f, Pa = j < 2 ? Pu[2 + j] : 0.f;
+                        mu[t * k + j] = Au + Pj;
+                        const float um = fmaxf(fabsf(blo[t * k + j]), fabsf(bhi[t * k + j]));
+                        e = __fmaf_ru(__fmul_ru(__fmul_ru((float)(H + 2), kTwoU), __fadd_ru(fabsf(Au), Pa)), um, e);
+                    }
+                    __syncwarp();
+                    float aa = 0.f, c = 0.f;
+                    if (t >= 1)
+                        c = obstacle_state_lin(a.cost, t, s, xlo + (size_t)t * s, xhi + (size_t)t * s, goal, lane, aa);
+                    if (lane < s) {
+                        const float Ax = A[0], lo_ = lam[0];
+                        const float B = t >= 1 ? fmaxf(fabsf(xlo[(size_t)t * s + lane]), fabsf(xhi[(size_t)t * s + lane]))
+                                               : fabsf(x0[lane]);
+                        lam[0] = (lo_ + Ax) + aa;
+                        const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
+                        e = __fmaf_ru(__fmul_ru(kTwoU, mag), B, e);
+                    }
+                    e = warp_sum_ru(e);
+                    if (t >= 1) c = __fadd_rd(c, pusher_lin(a.cost, t, k, blo, bhi, Pu, Pu + 2));
+                    cst = __fadd_rd(cst, c);
+                    mg = __fadd_ru(mg, e);
+                    continue;
                 }
                 // A is on [x_t | u_t]: mu_t = A_u; lam <- lam + A_x (+ tangent of ||x_t - g||^2 for t >= 1)
                 float c = 0.f, e = 0.f;

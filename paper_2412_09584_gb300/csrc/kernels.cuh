@@ -124,6 +124,62 @@ struct BoundArgs {
     CostDesc cost;           // the state cost (kind 0: squared distance)
 };
 
+// The pushing-with-obstacles state cost at step t on the box [xl, xu] of x_t, one warp per row (lane i owns
+// coordinate i, s <= 32): lane i's coefficient aa of a linear lower bound aa . x + constant; returns the constant
+// (rounded down, on every lane).  The norm by its tangent plane at the box centre, w ||x - g|| >= w ghat . (x - g)
+// with |ghat| < 1 (the unit vector shrunk by 1e-5 against rounding); each keypoint penalty by penalty_lower.
+__device__ __forceinline__ float obstacle_state_lin(const CostDesc &c, int t, int s, const float *xl, const float *xu,
+                                                    const float *goal, int lane, float &aa)
+{
+    const float m = lane < s ? 0.5f * (xl[lane] + xu[lane]) - goal[lane] : 0.f;
+    const float nm = sqrtf(warp_sum(m * m));
+    float a_ = 0.f, cst = 0.f;
+    if (nm > 0.f && lane < s) {
+        a_ = c.w[t - 1] * (m / nm) * 0.99999f;
+        cst = __fmul_rd(-a_, goal[lane]);
+    }
+    if (lane < s) {
+        const int kp = lane >> 1;
+        for (int o = 0; o < c.n_obs; ++o) {
+            float a0, a1, b;
+            if (penalty_lower(c, o, xl[2 * kp], xu[2 * kp], xl[2 * kp + 1], xu[2 * kp + 1], a0, a1, b)) {
+                a_ += c.lam * ((lane & 1) ? a1 : a0);
+                if (!(lane & 1)) cst = __fadd_rd(cst, __fmul_rd(c.lam, b));
+            }
+        }
+    }
+    aa = a_;
+    return warp_sum_rd(cst);
+}
+
+// The pusher penalties at step t (1..H): the box of p_t = p_0 + u_0 + ... + u_{t-1} (directed rounding), then
+// per obstacle the linear lower bound lam (a . p_t + b) = lam (a . p_0 + b) + lam a . (u_0 + ... + u_{t-1}):
+// adds lam a to P[0..1] (the coefficient of every earlier action) and |lam a| to Pabs; returns the constant
+// lam (a . p_0 + b), rounded down.  One thread.
+__device__ __forceinline__ float pusher_lin(const CostDesc &c, int t, int k, const float *lo, const float *hi,
+                                            float *P, float *Pabs)
+{
+    float l0 = c.p0x, l1 = c.p0y, u0 = c.p0x, u1 = c.p0y;
+    for (int tau = 0; tau < t; ++tau) {
+        l0 = __fadd_rd(l0, lo[tau * k]);
+        l1 = __fadd_rd(l1, lo[tau * k + 1]);
+        u0 = __fadd_ru(u0, hi[tau * k]);
+        u1 = __fadd_ru(u1, hi[tau * k + 1]);
+    }
+    float cst = 0.f;
+    for (int o = 0; o < c.n_obs; ++o) {
+        float a0, a1, b;
+        if (penalty_lower(c, o, l0, u0, l1, u1, a0, a1, b)) {
+            P[0] += c.lam * a0;
+            P[1] += c.lam * a1;
+            Pabs[0] += fabsf(c.lam * a0);
+            Pabs[1] += fabsf(c.lam * a1);
+            cst = __fadd_rd(cst, __fmul_rd(c.lam, __fadd_rd(__fmaf_rd(a0, c.p0x, __fmul_rd(a1, c.p0y)), b)));
+        }
+    }
+    return cst;
+}
+
 struct AdamStep {
     float lr, bc1, bc2;
 };

@@ -119,9 +119,9 @@ def test_obstacle_alpha_gradient_and_step(oracle, obst):
 
 
 def test_obstacle_alpha_optimize(oracle, obst):
-    """bab_alpha_optimize with the obstacle cost: the one-call loop (separate launches, or the shared-memory tile)
-    bit-identical to repeated bab_alpha_step; the best bound at least the adaptive CROWN bound (up to rounding)
-    and below the objective at sampled points."""
+    """bab_alpha_optimize with the obstacle cost: the one-call loop (separate launches, the shared-memory tile, or
+    one warp per box) bit-identical to repeated bab_alpha_step; the best bound at least the adaptive CROWN bound (up
+    to rounding) and below the objective at sampled points."""
     from gpu_util import DEV, T
     from paper_2412_09584_gb300 import binding as B
     p, g = obst(name="tiny", seed=79)
@@ -130,7 +130,7 @@ def test_obstacle_alpha_optimize(oracle, obst):
     steps = 20
     ref, _, _ = g.alpha_steps(lo, hi, steps=steps, lr=0.1)
     outs = []
-    for variant in (-1, -2, 0):
+    for variant in (-1, -2, 0, 3):
         B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, variant)
         lb_best = torch.empty(n, device=DEV)
         B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, steps, 0.1, lb_best)
@@ -138,9 +138,6 @@ def test_obstacle_alpha_optimize(oracle, obst):
         outs.append(lb_best.cpu().numpy())
     for o in outs:
         assert np.array_equal(o.view(np.uint32), ref.view(np.uint32))
-    B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, 3)   # the warp-per-box loop carries the squared distance only
-    with pytest.raises(B.BabError):
-        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, steps, 0.1, torch.empty(n, device=DEV))
     lb0 = g.crown(lo, hi)["lb"]
     assert np.all(ref >= lb0 - 1e-5 * np.maximum(np.abs(lb0), 1.0))
     assert np.mean(ref > lb0) > 0.5
@@ -148,6 +145,26 @@ def test_obstacle_alpha_optimize(oracle, obst):
     for i in range(n):
         us = lo[i] + (hi[i] - lo[i]) * rng.uniform(size=(100, 10))
         assert ref[i] <= min(oracle.objective(p, u) for u in us)
+
+
+def test_obstacle_alpha_warp_pushing(obst):
+    """The warp-per-box alpha loop with the obstacle cost on the pushing network (H = 20, 3 obstacles): bit-identical
+    to the separate bound, adjoint and Adam launches."""
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst()
+    n = 24
+    lo, hi, _ = W.random_boxes(40, n, seed=83, min_width=0.05, max_width=0.5)
+    outs = []
+    for variant in (-2, 3):
+        B.bab_set_variant(g.ctx, B.KERNEL_ALPHA_FUSED, variant)
+        lb_best = torch.empty(n, device=DEV)
+        alpha = torch.empty(n, g.H, g.sumh, device=DEV)
+        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, 5, 0.1, lb_best, alpha=alpha)
+        torch.cuda.synchronize()
+        outs.append((lb_best.cpu().numpy(), alpha.cpu().numpy()))
+    assert np.array_equal(outs[0][0].view(np.uint32), outs[1][0].view(np.uint32))
+    assert np.array_equal(outs[0][1].view(np.uint32), outs[1][1].view(np.uint32))
 
 
 def test_obstacle_cost_refusals(obst):
