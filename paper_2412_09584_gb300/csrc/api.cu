@@ -77,17 +77,33 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
     N.tc_bytes_hi = hi;
     N.tc_mg = 2 * hi;
     N.tc_bytes = 2 * hi + ((N.tc_K[L] + 63) / 64) * 2 * N.tc_N[L] * 128;
+    // the hidden layers' bias atoms after all of that (tc_bytes, what the split kernels load, excludes them)
+    int bb = 0;
+    for (int l = 1; l < L; ++l) {
+        N.tc_bb[l] = bb;
+        bb += N.tc_N[l] * 128;
+    }
+    N.tc_bbase = N.tc_bytes;
+    N.tc_bbytes = bb;
     N.tc_bias_floats = bo;
     N.tc_dcols = dcols;
     N.tc_acols = acols;
     N.tc_ok = ok ? 1 : 0;
-    img.assign((size_t)N.tc_bytes, 0);
+    img.assign((size_t)N.tc_bytes + N.tc_bbytes, 0);
     bias.assign((size_t)bo, 0.f);
     for (int l = 1; l <= L; ++l) {
         const int no = N.dims[l], ni = N.dims[l - 1], Nl = N.tc_N[l];
         const float *W = params + N.raw_w[l], *b = params + N.raw_b[l];
         for (int n = 0; n < no; ++n) {
             bias[N.tc_boff[l] + n] = b[n];
+            if (l < L) {
+                // bias atom: K 0 and 1 of row n (chunk 0, at its swizzled position)
+                const uint16_t bh = bf16_rn_host(b[n]);
+                const uint16_t bl = bf16_rn_host(b[n] - bf16_to_f32_host(bh));
+                const size_t offb = (size_t)N.tc_bbase + N.tc_bb[l] + (size_t)n * 128 + (size_t)((0 ^ (n % 8)) * 16);
+                std::memcpy(&img[offb], &bh, 2);
+                std::memcpy(&img[offb + 2], &bl, 2);
+            }
             for (int kk0 = 0; kk0 < ni; ++kk0) {
                 const float w = W[(size_t)n * ni + kk0];
                 const uint16_t h = bf16_rn_host(w);

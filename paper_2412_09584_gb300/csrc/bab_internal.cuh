@@ -44,6 +44,12 @@ struct NetDesc {
     int tc_K[kMaxLayers + 1], tc_N[kMaxLayers + 1];
     int tc_hi[kMaxLayers + 1], tc_lo[kMaxLayers + 1];  // byte offsets in the image
     int tc_mg;  // byte offset of the output layer stacked per K-atom as [hi rows; lo rows] (after the lo halves)
+    // BF16 bias atoms of the hidden layers l < L: one K-atom of N_l rows whose row n holds b_hi[n], b_lo[n] (the
+    // BF16 halves of b_l) at K 0 and 1, so that one K = 16 MMA against an A block of [1, 1, 0, ...] adds the bias
+    // to the accumulator.  They follow everything else in the image (at tc_bbase, tc_bbytes long; tc_bb[l]
+    // relative to it); the BF16 kernel copies them into shared memory right after the hi halves.
+    int tc_bb[kMaxLayers + 1];
+    int tc_bbase, tc_bbytes;
     int tc_boff[kMaxLayers + 1];                       // float offsets in the bias vector
     int tc_bytes, tc_bytes_hi, tc_bias_floats;
     int tc_dcols, tc_acols;                            // TMEM columns: accumulator, A operand

@@ -131,6 +131,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     const int mma_warp = NSLOT * kEpiWarps;
     const int L = N.L, s = N.s, k = N.k;
     volatile int *abort = &abort_flag;
+    // BF16 with the image resident: each hidden layer's bias enters the accumulator through one more K = 16 MMA of
+    // a constant A block [1, 1, 0, ...] (8 TMEM columns after the slot's A operand) against the layer's bias atom
+    // (b_hi, b_lo), so the epilogue adds nothing
+    constexpr bool BMMA = SPLIT == 1 && !STREAM;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -158,12 +162,17 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     tc::fence_after_sync();
     if (!STREAM) {
         if (threadIdx.x == mma_warp * 32) {
+            // the image's first tc_bytes (BF16 with bias MMAs: the hi halves, then the bias atoms from the end of
+            // the image), in 32 KB copies
             tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)a.tc_bytes);
             constexpr uint32_t kChunk = 32768;
-            for (uint32_t off = 0; off < (uint32_t)a.tc_bytes; off += kChunk) {
-                const uint32_t sz = min(kChunk, (uint32_t)a.tc_bytes - off);
-                tc::bulk_g2s(wimg + off, a.tc_img + off, sz, &bar_w);
-            }
+            const uint32_t first = BMMA ? (uint32_t)N.tc_bytes_hi : (uint32_t)a.tc_bytes;
+            for (uint32_t off = 0; off < first; off += kChunk)
+                tc::bulk_g2s(wimg + off, a.tc_img + off, min(kChunk, first - off), &bar_w);
+            if (BMMA)
+                for (uint32_t off = 0; off < (uint32_t)N.tc_bbytes; off += kChunk)
+                    tc::bulk_g2s(wimg + first + off, a.tc_img + N.tc_bbase + off, min(kChunk, (uint32_t)N.tc_bbytes - off),
+                                 &bar_w);
         }
         if (warp < mma_warp + NSLOT && !warp_wait(&bar_w, 0, abort) && lane == 0) raise_abort(a.status, abort);
     }
@@ -182,7 +191,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     auto tile_H = [&](long long tile) { return problem_H(a.batch, tile_problem(tile), a.H); };
     const uint32_t tb = tmem_base;
     const int Dc = N.tc_dcols, Ac = N.tc_acols;
-    const int slot_cols = Dc + (SPLIT == 3 ? 2 : 1) * Ac;
+    const int slot_cols = Dc + (SPLIT == 3 ? 2 : 1) * Ac + (BMMA ? 8 : 0);
     // the output layer's split as two MMAs per K step, a_hi [b_hi; b_lo] (2 N_L wide) and a_lo b_hi, where the
     // 2 N_L accumulator columns fit: columns 0.. hold a_hi b_hi + a_lo b_hi, columns N_L.. hold a_hi b_lo
     const bool stacked = SPLIT == 3 && 2 * N.tc_N[L] <= Dc && 2 * N.tc_N[L] <= 256;
@@ -201,6 +210,13 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
         const uint32_t acol_h = dcol + Dc, acol_l = acol_h + Ac;
         const int K1 = N.tc_K[1];
         uint32_t phD = 0;
+        if (BMMA && primary) {
+            // the constant A block of the bias MMAs (its two first BF16 elements 1), once per slot; the first
+            // arrive on bar_a below orders it before every MMA
+            const uint32_t ones[8] = {0x3F803F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            tc::tmem_st8(acol_l, ones);
+            tc::tmem_wait_st();
+        }
         for (long long tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
             int box, m;
             bool lane_ok;
@@ -345,27 +361,38 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                             cost += c;
                         }
                     } else {
-                        // 16 columns per load: fewer live registers (no spills) for a few more load round trips (two
-                        // loads per wait spill at the 96-register cap; four epilogue warps per tile with two 64-column
-                        // waits per layer measured slower: the conversions then run on half as many warps)
-                        for (int c0 = c_beg; c0 < c_end; c0 += 16) {
-                            uint32_t v[16];
-                            tc::tmem_ld16(dcol + c0, v);
-                            tc::tmem_wait_ld();
-                            const float4 *b4 = reinterpret_cast<const float4 *>(bl + c0);
-                            uint32_t ph[8], pl[8];
+                        // 16 columns per TMEM round trip: two loads per wait spill at the 96-register cap with the
+                        // bias additions or the hi/lo split, and measured slower for BF16 with the bias in the MMA
+                        // (11.1 against 10.5 ms); four epilogue warps per tile with two 64-column waits per layer
+                        // measured slower too: the conversions then run on half as many warps
+                        constexpr int kCols = 16;
+                        for (int c0 = c_beg; c0 < c_end; c0 += kCols) {
+                            uint32_t v[kCols / 16][16];
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float4 bb = b4[q];
-                                const float2 z01 = add2(make_float2(__uint_as_float(v[4 * q + 0]), __uint_as_float(v[4 * q + 1])),
-                                                        make_float2(bb.x, bb.y));
-                                const float2 z23 = add2(make_float2(__uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])),
-                                                        make_float2(bb.z, bb.w));
-                                relu_split2<SPLIT>(z01, ph[2 * q], pl[2 * q]);
-                                relu_split2<SPLIT>(z23, ph[2 * q + 1], pl[2 * q + 1]);
+                            for (int g = 0; g < kCols / 16; ++g)
+                                if (c0 + 16 * g < c_end) tc::tmem_ld16(dcol + c0 + 16 * g, v[g]);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int g = 0; g < kCols / 16; ++g) {
+                                if (c0 + 16 * g >= c_end) break;
+                                const int cc = c0 + 16 * g;
+                                const float4 *b4 = reinterpret_cast<const float4 *>(bl + cc);
+                                uint32_t ph[8], pl[8];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    float2 z01 = make_float2(__uint_as_float(v[g][4 * q + 0]), __uint_as_float(v[g][4 * q + 1]));
+                                    float2 z23 = make_float2(__uint_as_float(v[g][4 * q + 2]), __uint_as_float(v[g][4 * q + 3]));
+                                    if (!BMMA) {
+                                        const float4 bb = b4[q];
+                                        z01 = add2(z01, make_float2(bb.x, bb.y));
+                                        z23 = add2(z23, make_float2(bb.z, bb.w));
+                                    }
+                                    relu_split2<SPLIT>(z01, ph[2 * q], pl[2 * q]);
+                                    relu_split2<SPLIT>(z23, ph[2 * q + 1], pl[2 * q + 1]);
+                                }
+                                tc::tmem_st8(acol_h + cc / 2, ph);
+                                if (SPLIT == 3) tc::tmem_st8(acol_l + cc / 2, pl);
                             }
-                            tc::tmem_st8(acol_h + c0 / 2, ph);
-                            if (SPLIT == 3) tc::tmem_st8(acol_l + c0 / 2, pl);
                         }
                         tc::tmem_wait_st();
                         tc::fence_before_sync();
@@ -482,6 +509,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
                         }
                     }
                 }
+                // the bias: the constant block [1, 1, 0, ...] against the layer's (b_hi, b_lo) atom
+                if (BMMA && l < L)
+                    tc::mma_ts(dcol, al, tc::desc_join(tc::desc_sw128_lo(tc::smem_u32(wimg + N.tc_bytes_hi + N.tc_bb[l]))),
+                               idesc, 1u);
                 }
             } else {
                 // one K-atom (64 inputs; hi, then lo for the split) per ring buffer
@@ -808,7 +839,7 @@ static size_t rollout_tc_stage(const NetDesc &N, int split)
 
 static bool rollout_tc_resident(const NetDesc &N, int split, int max_smem)
 {
-    const size_t img = split == 3 ? N.tc_bytes : N.tc_bytes_hi;
+    const size_t img = split == 3 ? N.tc_bytes : (size_t)N.tc_bytes_hi + N.tc_bbytes;
     return img + rollout_tc_extra(N) + 1024 <= (size_t)max_smem;
 }
 
@@ -843,9 +874,10 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // several problems: every tile streams its own problem's image
     const bool stream = a.batch.P > 1 || !rollout_tc_resident(N, split, max_smem);
-    a.tc_img_stride = (size_t)N.tc_bytes;
+    a.tc_img_stride = (size_t)N.tc_bytes + N.tc_bbytes;  // one problem's whole image
     // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
-    const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols;
+    // (plus, BF16 resident, the 8 columns of the bias MMAs' constant block)
+    const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols + (split == 1 && !stream ? 8 : 0);
     int nslot = (2 * slot_cols <= 512) ? 2 : 1;
     if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
     // a streamed image needs a ring of at least two buffers per slot
@@ -857,8 +889,8 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     if (cols > 512) return cudaErrorInvalidConfiguration;
     a.tmem_cols = (uint32_t)cols;
     if (split == 1) {
-        // BF16 only: the weight image is the hi halves, laid out contiguously first
-        a.tc_bytes = N.tc_bytes_hi;
+        // BF16 only: the hi halves and the bias atoms
+        a.tc_bytes = N.tc_bytes_hi + N.tc_bbytes;
     }
     size_t smem;
     if (stream) {
