@@ -256,6 +256,14 @@ int refuse_obstacles(bab_ctx *c, const char *what)
     return BAB_OK;
 }
 
+// The tensor-core CROWN carries the obstacle cost when its backward image is resident in shared memory.
+int check_tc_obstacles(bab_ctx *c, const char *what)
+{
+    if (c->cost.kind != 0 && !crown_tc_obstacles_supported(c->net, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "%s carries the obstacle cost only with its weights in shared memory", what);
+    return BAB_OK;
+}
+
 BoundArgs make_bound_args(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
                           const float *hi, int n, const int *d_n, int row0 = 0)
 {
@@ -974,7 +982,7 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core CROWN")) != BAB_OK) return rc;
+    if (precision == BAB_PREC_BF16X3 && (rc = check_tc_obstacles(c, "the tensor-core CROWN")) != BAB_OK) return rc;
     if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
     if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
         return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
@@ -1071,7 +1079,7 @@ int bab_alpha_grad(bab_ctx *c, const float *x0, const float *goal, int H, float 
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha gradient")) != BAB_OK)
+    if (precision == BAB_PREC_BF16X3 && (rc = check_tc_obstacles(c, "the tensor-core alpha gradient")) != BAB_OK)
         return rc;
     if (n > 0 && (!alpha || !lb || !grad_alpha)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, lb and grad are required");
     rc = check_bound_precision(c, precision);
@@ -1091,7 +1099,7 @@ int bab_alpha_step(bab_ctx *c, const float *x0, const float *goal, int H, float 
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha step")) != BAB_OK)
+    if (precision == BAB_PREC_BF16X3 && (rc = check_tc_obstacles(c, "the tensor-core alpha step")) != BAB_OK)
         return rc;
     if (n > 0 && (!alpha || !adam_m || !adam_v)) return fail(c, BAB_ERR_INVALID_ARG, "alpha, m and v are required");
     if (step < 1) return fail(c, BAB_ERR_INVALID_ARG, "step counts from 1");
@@ -1234,7 +1242,7 @@ int bab_alpha_optimize(bab_ctx *c, const float *x0, const float *goal, int H, fl
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = refuse_obstacles(c, "the tensor-core alpha optimisation")) != BAB_OK)
+    if (precision == BAB_PREC_BF16X3 && (rc = check_tc_obstacles(c, "the tensor-core alpha optimisation")) != BAB_OK)
         return rc;
     if (n > 0 && !lb_best) return fail(c, BAB_ERR_INVALID_ARG, "lb_best is required");
     if (steps < 1 || steps > 100000) return fail(c, BAB_ERR_INVALID_ARG, "steps must be in [1, 100000]");

@@ -74,7 +74,10 @@ __device__ __forceinline__ void tangent(float xl, float xu, float g, float &coef
 // in shared memory; a producer warp streams it one K-atom (64 inputs of a
 // layer's product, hi and lo halves) at a time through a ring of a.stages
 // buffers in the MMA issuer's order (NSLOT = 1).
-template <int NSLOT, int SP, bool STREAM>
+// OBST: the pushing-with-obstacles cost (Appendix D.4; a separate instance): the norm's tangent plane and the
+// penalties' affine underestimators on each state's box (obstacle_state_lin_row), the pusher penalties' coefficients
+// carried to every earlier action, as crown_rows does for the CUDA-core CROWN.
+template <int NSLOT, int SP, bool STREAM, bool OBST = false>
 __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 1) k_crown_tc(BoundArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -140,8 +143,22 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
             const bool valid = box < nlive;
             float lam[SP];
             float cst = 0.f, mg = 0.f;  // constant (rounded down), margin (rounded up): this warp's share
+            float Pu[4] = {0.f, 0.f, 0.f, 0.f};  // obstacle cost: pusher coefficient of the actions (2), its |sum| (2)
+            const float *lo_b = a.lo + (size_t)(valid ? box : 0) * d, *hi_b = a.hi + (size_t)(valid ? box : 0) * d;
             bool ok = true;
-            if (primary) {
+            if (primary && OBST) {
+                // the obstacle cost's linear lower bound on x_H, then the pusher penalties at H
+                float xl[SP], xu[SP];
+#pragma unroll
+                for (int i = 0; i < SP; ++i) {
+                    const size_t xi = ((size_t)box * (H + 1) + H) * s + i;
+                    xl[i] = (i < s && valid) ? a.x_lo[xi] : 0.f;
+                    xu[i] = (i < s && valid) ? a.x_hi[xi] : 0.f;
+                }
+                float c = obstacle_state_lin_row<SP>(a.cost, H, s, xl, xu, a.goal, lam);
+                if (valid) c = __fadd_rd(c, pusher_lin(a.cost, H, k, lo_b, hi_b, Pu, Pu + 2));
+                cst = valid ? c : 0.f;
+            } else if (primary) {
                 // tangent of ||x_H - g||^2
 #pragma unroll
                 for (int i = 0; i < SP; ++i) {
@@ -265,12 +282,42 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
 #pragma unroll
                         for (int j = 0; j < 16; ++j) ax[c16 * 16 + j] = __uint_as_float(v[j]);
                     }
+                    float e = 0.f;
                     if (valid) {
 #pragma unroll
                         for (int j = 0; j < SP + 16; ++j)
-                            if (j >= s && j < s + k) a.mu[(size_t)box * d + t * k + (j - s)] = ax[j];
+                            if (j >= s && j < s + k) {
+                                const int ja = j - s;
+                                float m_ = ax[j];
+                                if (OBST) {
+                                    // mu_t = A_u + the pusher coefficient of the later steps (H additions)
+                                    const float Pj = ja < 2 ? Pu[ja] : 0.f, Pa = ja < 2 ? Pu[2 + ja] : 0.f;
+                                    const float um = fmaxf(fabsf(lo_b[t * k + ja]), fabsf(hi_b[t * k + ja]));
+                                    e = __fmaf_ru(__fmul_ru(__fmul_ru((float)(H + 2), kTwoU), __fadd_ru(fabsf(m_), Pa)), um, e);
+                                    m_ = m_ + Pj;
+                                }
+                                a.mu[(size_t)box * d + t * k + ja] = m_;
+                            }
                     }
-                    float e = 0.f;
+                    float aao[SP];  // obstacle cost: its coefficient of x_t
+                    if (OBST) {
+                        float xl[SP], xu[SP];
+#pragma unroll
+                        for (int i = 0; i < SP; ++i) {
+                            const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
+                            xl[i] = (i < s && valid && t >= 1) ? a.x_lo[xi] : 0.f;
+                            xu[i] = (i < s && valid && t >= 1) ? a.x_hi[xi] : 0.f;
+                        }
+                        float c = 0.f;
+                        if (t >= 1 && valid) {
+                            c = obstacle_state_lin_row<SP>(a.cost, t, s, xl, xu, a.goal, aao);
+                            c = __fadd_rd(c, pusher_lin(a.cost, t, k, lo_b, hi_b, Pu, Pu + 2));
+                            cst = __fadd_rd(cst, c);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < SP; ++i) aao[i] = 0.f;
+                        }
+                    }
 #pragma unroll
                     for (int i = 0; i < SP; ++i) {
                         if (i < s) {
@@ -278,9 +325,13 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                             if (t >= 1 && valid) {
                                 const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
                                 const float xl = a.x_lo[xi], xu = a.x_hi[xi];
-                                float ct;
-                                tangent(xl, xu, a.goal[i], aa, ct);
-                                cst = __fadd_rd(cst, ct);
+                                if (OBST) {
+                                    aa = aao[i];
+                                } else {
+                                    float ct;
+                                    tangent(xl, xu, a.goal[i], aa, ct);
+                                    cst = __fadd_rd(cst, ct);
+                                }
                                 B = fmaxf(fabsf(xl), fabsf(xu));
                             } else {
                                 B = fabsf(a.x0[i]);
@@ -479,16 +530,19 @@ static bool crown_tc_resident(const NetDesc &N, int nslot, int max_smem)
     return (size_t)N.tcb_bytes + crown_tc_extra(N, nslot) + 1024 <= (size_t)max_smem;
 }
 
+// The obstacle cost runs only with the backward image resident in shared memory.
+bool crown_tc_obstacles_supported(const NetDesc &N, int max_smem) { return crown_tc_resident(N, 1, max_smem); }
+
 bool crown_tc_supported(const NetDesc &N, int max_smem)
 {
     if (!N.tc_ok || N.L < 2 || N.s > 32 || pad16(N.s + N.k) > 48) return false;
     return crown_tc_resident(N, 1, max_smem) || 2 * crown_tc_stage(N) + crown_tc_extra(N, 1) + 1024 <= (size_t)max_smem;
 }
 
-template <int NSLOT, int SP, bool STREAM>
+template <int NSLOT, int SP, bool STREAM, bool OBST>
 static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = k_crown_tc<NSLOT, SP, STREAM>;
+    auto kern = k_crown_tc<NSLOT, SP, STREAM, OBST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, (NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, smem, st>>>(a);
@@ -498,8 +552,15 @@ static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cud
 template <int SP>
 static cudaError_t launch_shape(const BoundArgs &a, int nslot, bool stream, int grid, size_t smem, cudaStream_t st)
 {
-    if (stream) return launch_variant<1, SP, true>(a, grid, smem, st);
-    return nslot == 2 ? launch_variant<2, SP, false>(a, grid, smem, st) : launch_variant<1, SP, false>(a, grid, smem, st);
+    if (a.cost.kind == 1) {
+        // the obstacle cost: resident backward image only (the caller checks crown_tc_obstacles_supported)
+        if (stream) return cudaErrorNotSupported;
+        return nslot == 2 ? launch_variant<2, SP, false, true>(a, grid, smem, st)
+                          : launch_variant<1, SP, false, true>(a, grid, smem, st);
+    }
+    if (stream) return launch_variant<1, SP, true, false>(a, grid, smem, st);
+    return nslot == 2 ? launch_variant<2, SP, false, false>(a, grid, smem, st)
+                      : launch_variant<1, SP, false, false>(a, grid, smem, st);
 }
 
 // nslot_pref: tiles per CTA (1 or 2), or -1 for two only when the tiles outnumber the SMs

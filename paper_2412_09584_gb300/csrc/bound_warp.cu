@@ -124,7 +124,9 @@ __host__ __device__ inline RowsLayout rows_layout(const NetDesc &N)
 // P: neurons per lane (every layer width <= 32 P).  ROWS: the products of the boxes whose problem is the round's
 // read the network from shared memory in padded rows (dense_rs); other boxes, and ROWS = false, read the images
 // from global memory with shuffle broadcasts (dense_warp).  Both sum in the same order.
-template <int P, bool ROWS>
+// OBST: the pushing-with-obstacles cost (a separate instance, so that the squared-distance kernel carries none of
+// its code or registers).
+template <int P, bool ROWS, bool OBST>
 __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     k_alpha_warp(BoundArgs a, int steps, float lr, float *alpha_g, float *m_g, float *v_g, const AdamTable tab)
 {
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(kWarps * 32, P <= 2 ? 4 : (P <= 4 ? 2 : 1))
     const int nlive = live_count(a.n, a.d_n, a.row0);
     const size_t hs = (size_t)Hm * sumh;  // per-box stride of the [H][sumh] arrays
     const bool opt = steps > 0;           // steps == 0: one bound with the adaptive slopes, no adjoint
-    const bool obst = a.cost.kind == 1;   // the pushing-with-obstacles cost (one problem, s <= 32)
+    constexpr bool obst = OBST;           // the pushing-with-obstacles cost (one problem, s <= 32)
     int loaded = -1;                      // the problem whose rows are in shared memory
     for (int base = blockIdx.x * kWarps; base < nlive; base += gridDim.x * kWarps) {
         // a round of kWarps boxes; the rows of its first box's problem serve every box of that problem
@@ -493,7 +495,9 @@ static cudaError_t launch_warp_variant(const BoundArgs &a, int steps, float lr, 
     const bool rows = with_rows * 2 + 2048 <= (size_t)max_optin;
     const size_t smem = rows ? with_rows : per_warp;
     if (smem + 1024 > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    auto kern = rows ? k_alpha_warp<P, true> : k_alpha_warp<P, false>;
+    const bool ob = a.cost.kind == 1;
+    auto kern = rows ? (ob ? k_alpha_warp<P, true, true> : k_alpha_warp<P, true, false>)
+                     : (ob ? k_alpha_warp<P, false, true> : k_alpha_warp<P, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;

@@ -180,6 +180,46 @@ __device__ __forceinline__ float pusher_lin(const CostDesc &c, int t, int k, con
     return cst;
 }
 
+// The same linear lower bound as obstacle_state_lin for one box held by one thread (the tensor-core CROWN):
+// coefficients aa[i] of x_t's coordinates i < s (xl, xu, goal: the box of x_t and the target, SP >= s values)
+// and the constant (rounded down), the sums taken in index order.  |ghat| < 1 holds as there (the unit vector
+// shrunk by 1e-5, far above the rounding of an s-term sum).
+template <int SP>
+__device__ __forceinline__ float obstacle_state_lin_row(const CostDesc &c, int t, int s, const float (&xl)[SP],
+                                                        const float (&xu)[SP], const float *goal, float (&aa)[SP])
+{
+    float m[SP], ss = 0.f;
+#pragma unroll
+    for (int i = 0; i < SP; ++i) {
+        m[i] = i < s ? 0.5f * (xl[i] + xu[i]) - goal[i] : 0.f;
+        ss = fmaf(m[i], m[i], ss);
+    }
+    const float nm = sqrtf(ss);
+    float cst = 0.f;
+#pragma unroll
+    for (int i = 0; i < SP; ++i) {
+        float a_ = 0.f;
+        if (nm > 0.f && i < s) {
+            a_ = c.w[t - 1] * (m[i] / nm) * 0.99999f;
+            cst = __fadd_rd(cst, __fmul_rd(-a_, goal[i]));
+        }
+        aa[i] = a_;
+    }
+#pragma unroll
+    for (int kp = 0; kp < SP / 2; ++kp) {
+        if (2 * kp >= s) break;
+        for (int o = 0; o < c.n_obs; ++o) {
+            float a0, a1, b;
+            if (penalty_lower(c, o, xl[2 * kp], xu[2 * kp], xl[2 * kp + 1], xu[2 * kp + 1], a0, a1, b)) {
+                aa[2 * kp] += c.lam * a0;
+                aa[2 * kp + 1] += c.lam * a1;
+                cst = __fadd_rd(cst, __fmul_rd(c.lam, b));
+            }
+        }
+    }
+    return cst;
+}
+
 struct AdamStep {
     float lr, bc1, bc2;
 };
@@ -310,6 +350,7 @@ cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t preload_ibp_crown();
 cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream_t st);
 bool crown_tc_supported(const NetDesc &N, int max_smem);
+bool crown_tc_obstacles_supported(const NetDesc &N, int max_smem);
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_alpha_init(const BoundArgs &a, cudaStream_t st);
 // the whole alpha optimisation of a tile of boxes in one CTA (needs the interval bounds of launch_ibp)

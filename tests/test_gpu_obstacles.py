@@ -97,6 +97,36 @@ def test_obstacle_bounds_against_oracle(oracle, obst):
         assert lb_c[i] <= fmin and lb_i[i] <= fmin
 
 
+def test_obstacle_crown_tensor_cores(oracle, obst):
+    """The tensor-core CROWN (3-term BF16 split products) with the obstacle cost: at most the oracle's exact bound
+    (plus rounding), within the split band plus the relaxation's 1e-5 shrink of it, close to the CUDA-core CROWN,
+    below sampled objectives; and alpha-CROWN on tensor cores with it, never below the adaptive bound."""
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst(H=8, n_obs=4, lam=20.0)
+    n = 150  # two tiles of 128 boxes, the second ragged
+    lo, hi, _ = W.random_boxes(16, n, seed=84, min_width=0.02, max_width=0.6)
+    c_o = oracle.crown(p, lo, hi)
+    scale = np.maximum(c_o["scale"], 1.0)
+    lb_t, mg_t, lb_f = (torch.empty(n, device=DEV) for _ in range(3))
+    B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, lb_t, precision=B.PREC_BF16X3, margin=mg_t)
+    B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, lb_f)
+    best = torch.empty(n, device=DEV)
+    B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, 5, 0.1, best, precision=B.PREC_BF16X3)
+    torch.cuda.synchronize()
+    assert B.bab_status(g.ctx) == 0
+    lb_t, lb_f, best = (x.cpu().numpy().astype(np.float64) for x in (lb_t, lb_f, best))
+    assert np.all(lb_t <= c_o["lb"] + 1e-6 * scale)
+    assert np.all(lb_t >= c_o["lb"] - 2e-4 * scale)
+    assert np.all(np.abs(lb_t - lb_f) <= 2e-4 * scale)
+    assert np.all(best >= lb_t - 1e-5 * scale)
+    rng = np.random.default_rng(6)
+    for i in range(0, n, 15):
+        us = lo[i] + (hi[i] - lo[i]) * rng.uniform(size=(200, 16))
+        fmin = min(oracle.objective(p, u) for u in us)
+        assert lb_t[i] <= fmin and best[i] <= fmin
+
+
 def test_obstacle_alpha_gradient_and_step(oracle, obst):
     """alpha-CROWN with the obstacle cost: the adjoint gradient at the adaptive slopes and the bound against the
     oracle's, and Adam's first step."""
@@ -173,10 +203,6 @@ def test_obstacle_cost_refusals(obst):
     p, g = obst(H=5)
     lo, hi, ids = W.random_boxes(10, 3, seed=75)
     lb = torch.empty(3, device=DEV)
-    with pytest.raises(B.BabError):
-        B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, precision=B.PREC_BF16X3)
-    with pytest.raises(B.BabError):
-        B.bab_alpha_optimize(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, 2, 0.1, lb, precision=B.PREC_BF16X3)
     with pytest.raises(B.BabError):
         B.bab_box_grad(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), 3, lb, torch.empty(3, 10, device=DEV),
                        torch.empty(3, 10, device=DEV))
