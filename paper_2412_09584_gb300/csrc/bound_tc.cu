@@ -1,8 +1,10 @@
 // bound_tc.cu -- backward CROWN (Appendix B.1, Theorem 1) with the per-layer
 // products A' W_l on tcgen05 tensor cores, 3-term BF16 split, FP32 accumulate.
 //
-// A tile is 128 boxes, one box per TMEM lane.  Per time step t = H-1 .. 0 the
-// coefficient row of each box runs backward through the network:
+// A tile is one 128-row MMA holding up to 128 boxes, one per TMEM lane: tc_rows of them (32, 64 or 128; spread
+// over the four lane quadrants), fewer when the batch would otherwise leave SMs idle, since the per-box work of
+// each layer step (interval-bound loads, relaxation, margin) and not the MMAs bounds the kernel.  Per time step t = H-1 .. 0 the coefficient row
+// of each box runs backward through the network:
 //
 //   lam (coefficient of x_{t+1})  --x W_L^T-->  coefficient on a_{L-1}
 //   relax (Lemma 1)               --x W_{L-1}^T--> ...  --x W_1^T-->  [x_t | u_t]
@@ -124,7 +126,10 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
     }
 
     const int nlive = live_count(a.n, a.d_n, a.row0);
-    const int ntiles = (nlive + 127) / 128;
+    // a tile is one 128-row MMA; it holds tc_rows boxes (fewer than 128 when the batch is small, so that the
+    // per-box work spreads over more SMs: the MMAs are a small part of each layer step)
+    const int bpt = a.tc_rows;
+    const int ntiles = (nlive + bpt - 1) / bpt;
     const int G = gridDim.x * NSLOT;
     const uint32_t tb = tmem_base;
     const int Dc = N.tcb_dcols, Ac = N.tcb_acols;
@@ -139,8 +144,11 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
         const uint32_t acol_h = dcol + Dc, acol_l = acol_h + Ac;
         uint32_t phD = 0, phP = 0;
         for (int tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
-            const int box = tile * 128 + r;
-            const bool valid = box < nlive;
+            // the tile's boxes spread evenly over the four lane quadrants (bpt / 4 lanes of each), so that every
+            // epilogue warp has boxes to work on
+            const int rq = bpt >> 2, lq = r & 31;
+            const int box = tile * bpt + (r >> 5) * rq + lq;
+            const bool valid = lq < rq && box < nlive;
             float lam[SP];
             float cst = 0.f, mg = 0.f;  // constant (rounded down), margin (rounded up): this warp's share
             float Pu[4] = {0.f, 0.f, 0.f, 0.f};  // obstacle cost: pusher coefficient of the actions (2), its |sum| (2)
@@ -572,7 +580,11 @@ cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int slot_cols = N.tcb_dcols + 2 * N.tcb_acols;
-    const int ntiles = (a.n + 127) / 128;
+    // boxes per tile: 128 when the tiles at least fill the SMs, else 64 or 32
+    a.tc_rows = 128;
+    while (a.tc_rows > 32 && (a.n + a.tc_rows - 1) / a.tc_rows < num_sms) a.tc_rows /= 2;
+    if ((a.n + a.tc_rows - 1) / a.tc_rows > num_sms && a.tc_rows < 128) a.tc_rows *= 2;
+    const int ntiles = (a.n + a.tc_rows - 1) / a.tc_rows;
     int nslot = (ntiles > num_sms && 2 * slot_cols <= 512) ? 2 : 1;
     if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
     const bool stream = !crown_tc_resident(N, nslot, max_smem) && !crown_tc_resident(N, 1, max_smem);

@@ -119,6 +119,7 @@ struct BoundArgs {
     float *mu;               // [n][d] coefficients of u (lin_coef or scratch)
     int t_stop;              // propagation early-stop step (0: back to the input); S == null: no margin
     uint32_t tmem_cols;
+    int tc_rows;             // boxes per 128-row tile of the tensor-core CROWN (32, 64 or 128; the other rows idle)
     int stages;              // > 0: the backward image is streamed through `stages` ring buffers
     int stage_bytes;
     CostDesc cost;           // the state cost (kind 0: squared distance)
