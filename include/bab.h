@@ -568,7 +568,12 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  *                            distance cost only: with the obstacle cost -1
  *                            takes the separate launches and 3 is refused).
  *   BAB_KERNEL_ROLLOUT_TC    1 or 2 sample tiles per CTA.
- *   BAB_KERNEL_CROWN_TC      1 or 2 box tiles per CTA.
+ *   BAB_KERNEL_CROWN_TC      0: one tile of up to 32 boxes per CTA, each
+ *                            epilogue thread staging its next layer's interval
+ *                            bounds in shared memory while the tensor core
+ *                            runs (the default where it fits; 1 otherwise);
+ *                            1 or 2: tiles of up to 128 boxes per CTA, the
+ *                            bounds read from global memory where needed.
  * -1 selects the built-in heuristic everywhere.  bab_set_variant returns
  * BAB_ERR_INVALID_ARG for an unknown kernel or variant; a variant whose tile
  * does not fit the network makes the later call fail with BAB_ERR_CUDA.

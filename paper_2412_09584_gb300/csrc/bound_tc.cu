@@ -51,6 +51,33 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = pack2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xFFFF0000u));
 }
 
+// Per-thread asynchronous copies global -> shared (16 or 4 bytes), grouped; the issuing thread alone reads what
+// it copied, after waiting for its group, so no barrier is involved.
+__device__ __forceinline__ void cp16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NG>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(NG) : "memory");
+}
+// n floats; 16-byte copies when both ends and n allow it
+__device__ __forceinline__ void cp_row(float *dst, const float *src, int n, bool vec)
+{
+    if (vec)
+        for (int c = 0; c < n; c += 4) cp16(dst + c, src + c);
+    else
+        for (int c = 0; c < n; ++c) cp4(dst + c, src + c);
+}
+
 __device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t phase, volatile int *abort)
 {
     return __all_sync(0xFFFFFFFFu, tc::mbar_wait(bar, phase, abort, kWaitNs));
@@ -79,7 +106,11 @@ __device__ __forceinline__ void tangent(float xl, float xu, float g, float &coef
 // OBST: the pushing-with-obstacles cost (Appendix D.4; a separate instance): the norm's tangent plane and the
 // penalties' affine underestimators on each state's box (obstacle_state_lin_row), the pusher penalties' coefficients
 // carried to every earlier action, as crown_rows does for the CUDA-core CROWN.
-template <int NSLOT, int SP, bool STREAM, bool OBST = false>
+// STG: each epilogue thread copies the interval bounds, margin helpers and slopes of its columns of the next
+// hidden layer (and, for the primary, the next step's output-layer helpers and state box) into its own shared
+// memory area with cp.async while the tensor core runs the current product, instead of loading them from global
+// memory column by column when it needs them (resident image, one slot).
+template <int NSLOT, int SP, bool STREAM, bool OBST = false, bool STG = false>
 __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 1) k_crown_tc(BoundArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -87,6 +118,11 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float *bias = reinterpret_cast<float *>(wimg + (STREAM ? (size_t)a.stages * a.stage_bytes : (size_t)N.tcb_bytes));
     float *pair = bias + N.tc_bias_floats;  // [NSLOT][128][2]: helper warps' (constant, margin) partials
+    // STG areas (16-byte aligned): per column half h and box slot b of the tile, [zl | zu | S | alpha] of
+    // a.stg_cols floats each (a.stg_hid floats in all, an odd number of 16-byte units, so that the lanes of a warp
+    // reading their areas at one offset hit distinct banks); then per box slot [2][S_L | xl | xu] of SP floats
+    // each, double-buffered by the parity of t (a.stg_step floats)
+    float *stg = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(pair + NSLOT * 256) + 15) & ~uintptr_t(15));
     __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_p[NSLOT * 4], bar_fin;
     __shared__ uint64_t bar_full[kMaxStages], bar_empty[kMaxStages];
     __shared__ uint32_t tmem_base;
@@ -143,10 +179,17 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
         const uint32_t dcol = tb + ((uint32_t)(32 * quad) << 16) + slot * slot_cols;
         const uint32_t acol_h = dcol + Dc, acol_l = acol_h + Ac;
         uint32_t phD = 0, phP = 0;
+        // the tile's boxes spread evenly over the four lane quadrants (bpt / 4 lanes of each), so that every
+        // epilogue warp has boxes to work on
+        const int rq = bpt >> 2, lq = r & 31;
+        const int bslot = lq < rq ? quad * rq + lq : 0;
+        // STG: this thread's hidden-layer area (one per box slot and column half) and its box slot's step area
+        const int CW = a.stg_cols;
+        float *hz = stg + (size_t)((primary ? 0 : bpt) + bslot) * a.stg_hid;
+        float *sa = stg + (size_t)2 * bpt * a.stg_hid + (size_t)bslot * a.stg_step;
+        const bool s_vec = (sw & 3) == 0 && (reinterpret_cast<uintptr_t>(a.S) & 15) == 0;
+        const bool a_vec = (reinterpret_cast<uintptr_t>(a.alpha) & 15) == 0;
         for (int tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
-            // the tile's boxes spread evenly over the four lane quadrants (bpt / 4 lanes of each), so that every
-            // epilogue warp has boxes to work on
-            const int rq = bpt >> 2, lq = r & 31;
             const int box = tile * bpt + (r >> 5) * rq + lq;
             const bool valid = lq < rq && box < nlive;
             float lam[SP];
@@ -154,6 +197,39 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
             float Pu[4] = {0.f, 0.f, 0.f, 0.f};  // obstacle cost: pusher coefficient of the actions (2), its |sum| (2)
             const float *lo_b = a.lo + (size_t)(valid ? box : 0) * d, *hi_b = a.hi + (size_t)(valid ? box : 0) * d;
             bool ok = true;
+            // this thread's columns [cb, ce) of hidden layer l: the primary and helper warps of a quadrant split
+            // a width that is a multiple of 64, else the primary takes them all
+            auto cols = [&](int l, int &cb, int &ce) {
+                const int dl = N.dims[l];
+                cb = primary ? 0 : dl / 2;
+                ce = (dl % 64 == 0) ? cb + dl / 2 : (primary ? dl : 0);
+            };
+            // STG copies: hidden layer l of step t (one group), and the primary's step-t helpers (one group)
+            auto stage_hidden = [&](int t, int l) {
+                if (!STG || !valid) return;
+                int cb, ce;
+                cols(l, cb, ce);
+                if (ce > cb) {
+                    const size_t ib = ((size_t)box * H + t) * sumh + N.hoff[l] + cb;
+                    cp_row(hz, a.pre_lo + ib, ce - cb, true);
+                    cp_row(hz + CW, a.pre_hi + ib, ce - cb, true);
+                    cp_row(hz + 2 * CW, a.S + ((size_t)box * H + t) * sw + N.hoff[l] + cb, ce - cb, s_vec);
+                    if (has_alpha) cp_row(hz + 3 * CW, a.alpha + ib, ce - cb, a_vec);
+                }
+                cp_commit();
+            };
+            auto stage_step = [&](int t) {
+                if (!STG || !valid || !primary) return;
+                float *p = sa + (t & 1) * 3 * SP;
+                cp_row(p, a.S + ((size_t)box * H + t) * sw + sumh, s, false);
+                if (t >= 1) {
+                    cp_row(p + SP, a.x_lo + ((size_t)box * (H + 1) + t) * s, s, false);
+                    cp_row(p + 2 * SP, a.x_hi + ((size_t)box * (H + 1) + t) * s, s, false);
+                }
+                cp_commit();
+            };
+            stage_step(H - 1);
+            stage_hidden(H - 1, L - 1);
             if (primary && OBST) {
                 // the obstacle cost's linear lower bound on x_H, then the pusher penalties at H
                 float xl[SP], xu[SP];
@@ -182,6 +258,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
             }
             for (int t = H - 1; t >= 0 && ok; --t) {
                 const size_t rowb = ((size_t)box * H + t);
+                const float *sx = sa + (t & 1) * 3 * SP;  // STG: the step's [S_L | xl | xu]
                 // ---- last layer: A = lam on z_L; constant lam . b_L; product lam W_L^T ----
                 if (primary) {
                     const float *bL = bias + N.tc_boff[L];
@@ -198,11 +275,12 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                         tc::tmem_st8(acol_h + c16 * 8, ph);
                         tc::tmem_st8(acol_l + c16 * 8, pl);
                     }
+                    if (STG) cp_wait<1>();  // the step's group (the hidden layer's may still be in flight)
 #pragma unroll
                     for (int i = 0; i < SP; ++i)
                         if (i < s && valid) {
                             cst = __fmaf_rd(lam[i], bL[i], cst);
-                            e = __fmaf_ru(fabsf(lam[i]), a.S[rowb * sw + sumh + i], e);
+                            e = __fmaf_ru(fabsf(lam[i]), STG ? sx[i] : a.S[rowb * sw + sumh + i], e);
                         }
                     mg = __fmaf_ru(N.gam_tc[L], e, mg);
                     tc::tmem_wait_st();
@@ -219,27 +297,38 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                     }
                     phD ^= 1;
                     tc::fence_after_sync();
-                    const int dl = N.dims[l];
-                    const int c_beg = primary ? 0 : dl / 2, c_end = (dl % 64 == 0) ? c_beg + dl / 2 : (primary ? dl : 0);
+                    int c_beg, c_end;
+                    cols(l, c_beg, c_end);
                     const float *bl = bias + N.tc_boff[l];
                     const float gK = N.gam_tc[l];
                     float eg = 0.f, er = 0.f;
-                    for (int c0 = c_beg; c0 < c_end; c0 += 32) {
-                        uint32_t v[32];
-                        tc::tmem_ld32(dcol + c0, v);
+                    if (STG) cp_wait<0>();
+                    for (int c0 = c_beg; c0 < c_end; c0 += 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(dcol + c0, v);
                         tc::tmem_wait_ld();
                         const size_t ib = rowb * sumh + N.hoff[l] + c0;
-                        uint32_t ph[16], pl[16];
+                        uint32_t ph[8], pl[8];
 #pragma unroll
-                        for (int q4 = 0; q4 < 8; ++q4) {
-                            float4 zl4 = make_float4(0.f, 0.f, 0.f, 0.f), zu4 = zl4, al4 = zl4;
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            float4 zl4 = make_float4(0.f, 0.f, 0.f, 0.f), zu4 = zl4, al4 = zl4, s4 = zl4;
                             if (valid) {
-                                zl4 = *reinterpret_cast<const float4 *>(a.pre_lo + ib + 4 * q4);
-                                zu4 = *reinterpret_cast<const float4 *>(a.pre_hi + ib + 4 * q4);
-                                if (has_alpha) al4 = *reinterpret_cast<const float4 *>(a.alpha + ib + 4 * q4);
+                                if (STG) {
+                                    const int o = c0 - c_beg + 4 * q4;
+                                    zl4 = *reinterpret_cast<const float4 *>(hz + o);
+                                    zu4 = *reinterpret_cast<const float4 *>(hz + CW + o);
+                                    s4 = *reinterpret_cast<const float4 *>(hz + 2 * CW + o);
+                                    if (has_alpha) al4 = *reinterpret_cast<const float4 *>(hz + 3 * CW + o);
+                                } else {
+                                    zl4 = *reinterpret_cast<const float4 *>(a.pre_lo + ib + 4 * q4);
+                                    zu4 = *reinterpret_cast<const float4 *>(a.pre_hi + ib + 4 * q4);
+                                    if (has_alpha) al4 = *reinterpret_cast<const float4 *>(a.alpha + ib + 4 * q4);
+                                    const float *Sr = a.S + rowb * sw + N.hoff[l] + c0 + 4 * q4;
+                                    s4 = make_float4(Sr[0], Sr[1], Sr[2], Sr[3]);
+                                }
                             }
                             const float zlv[4] = {zl4.x, zl4.y, zl4.z, zl4.w}, zuv[4] = {zu4.x, zu4.y, zu4.z, zu4.w};
-                            const float alv[4] = {al4.x, al4.y, al4.z, al4.w};
+                            const float alv[4] = {al4.x, al4.y, al4.z, al4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
                             float ap[4];
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
@@ -253,15 +342,22 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                                     if (a.A_pre) a.A_pre[ib + j] = A;
                                     cst = __fmaf_rd(A, c, cst);
                                     cst = __fmaf_rd(Ap, bl[c0 + j], cst);
-                                    eg = __fmaf_ru(fabsf(Ap), a.S[rowb * sw + N.hoff[l] + c0 + j], eg);
+                                    eg = __fmaf_ru(fabsf(Ap), sv[e], eg);
                                     if (D != 0.f && D != 1.f) er = __fmaf_ru(fabsf(Ap), fmaxf(-zlv[e], zuv[e]), er);
                                 }
                             }
                             split2(ap[0], ap[1], ph[2 * q4], pl[2 * q4]);
                             split2(ap[2], ap[3], ph[2 * q4 + 1], pl[2 * q4 + 1]);
                         }
-                        tc::tmem_st16(acol_h + c0 / 2, ph);
-                        tc::tmem_st16(acol_l + c0 / 2, pl);
+                        tc::tmem_st8(acol_h + c0 / 2, ph);
+                        tc::tmem_st8(acol_l + c0 / 2, pl);
+                    }
+                    // the next hidden layer's data (this thread is done with its area), or the next step's
+                    if (l > 1) {
+                        stage_hidden(t, l - 1);
+                    } else if (t >= 1) {
+                        stage_step(t - 1);
+                        stage_hidden(t - 1, L - 1);
                     }
                     mg = __fadd_ru(mg, __fmaf_ru(gK, eg, __fmul_ru(kTwoU, er)));
                     tc::tmem_wait_st();
@@ -307,18 +403,23 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                                 a.mu[(size_t)box * d + t * k + ja] = m_;
                             }
                     }
+                    // the state box of x_t (t >= 1)
+                    auto xbox = [&](int i, float &xl, float &xu) {
+                        const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
+                        xl = STG ? sx[SP + i] : a.x_lo[xi];
+                        xu = STG ? sx[2 * SP + i] : a.x_hi[xi];
+                    };
                     float aao[SP];  // obstacle cost: its coefficient of x_t
                     if (OBST) {
-                        float xl[SP], xu[SP];
-#pragma unroll
-                        for (int i = 0; i < SP; ++i) {
-                            const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
-                            xl[i] = (i < s && valid && t >= 1) ? a.x_lo[xi] : 0.f;
-                            xu[i] = (i < s && valid && t >= 1) ? a.x_hi[xi] : 0.f;
-                        }
                         float c = 0.f;
                         if (t >= 1 && valid) {
-                            c = obstacle_state_lin_row<SP>(a.cost, t, s, xl, xu, a.goal, aao);
+                            float xlt[SP], xut[SP];
+#pragma unroll
+                            for (int i = 0; i < SP; ++i) {
+                                xlt[i] = xut[i] = 0.f;
+                                if (i < s) xbox(i, xlt[i], xut[i]);
+                            }
+                            c = obstacle_state_lin_row<SP>(a.cost, t, s, xlt, xut, a.goal, aao);
                             c = __fadd_rd(c, pusher_lin(a.cost, t, k, lo_b, hi_b, Pu, Pu + 2));
                             cst = __fadd_rd(cst, c);
                         } else {
@@ -331,8 +432,8 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                         if (i < s) {
                             float aa = 0.f, B;
                             if (t >= 1 && valid) {
-                                const size_t xi = ((size_t)box * (H + 1) + t) * s + i;
-                                const float xl = a.x_lo[xi], xu = a.x_hi[xi];
+                                float xl, xu;
+                                xbox(i, xl, xu);
                                 if (OBST) {
                                     aa = aao[i];
                                 } else {
@@ -375,28 +476,41 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                     for (int i = 0; i < SP; ++i)
                         if (i < s) c = __fmaf_rd(lam[i], a.x0[i], c);
                     c = __fadd_rd(cst, c);
-                    for (int j = 0; j < d; ++j) {
-                        const float m_ = a.mu[(size_t)box * d + j];
-                        const float lo = a.lo[(size_t)box * d + j], hi = a.hi[(size_t)box * d + j];
-                        float us, vj;
-                        if (a.rho > 0.f) {
-                            const float uc = -m_ / (2.f * a.rho);
-                            if (uc >= lo && uc <= hi) {
-                                us = uc;
-                                vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * a.rho);
-                            } else {
-                                us = uc < lo ? lo : hi;
-                                vj = __fmaf_rd(m_, us, __fmul_rd(a.rho, __fmul_rd(us, us)));
-                                const float du = __fmul_ru(kTwoU, fabsf(uc));
-                                e = __fmaf_ru(__fmul_ru(a.rho, du), du, e);
-                            }
-                        } else {
-                            us = m_ >= 0.f ? lo : hi;
-                            vj = __fmul_rd(m_, us);
+                    // eight actions at a time: their coefficients and bounds loaded before any result is stored
+                    for (int j0 = 0; j0 < d; j0 += 8) {
+                        float mv[8], lv[8], hv[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const size_t e8 = (size_t)box * d + (j0 + q < d ? j0 + q : j0);
+                            mv[q] = a.mu[e8];
+                            lv[q] = a.lo[e8];
+                            hv[q] = a.hi[e8];
                         }
-                        vsum = __fadd_rd(vsum, vj);
-                        if (a.ustar) a.ustar[(size_t)box * d + j] = us;
-                        if (a.lin_coef && a.lin_coef != a.mu) a.lin_coef[(size_t)box * d + j] = m_;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            if (j0 + q >= d) break;
+                            const int j = j0 + q;
+                            const float m_ = mv[q], lo = lv[q], hi = hv[q];
+                            float us, vj;
+                            if (a.rho > 0.f) {
+                                const float uc = -m_ / (2.f * a.rho);
+                                if (uc >= lo && uc <= hi) {
+                                    us = uc;
+                                    vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * a.rho);
+                                } else {
+                                    us = uc < lo ? lo : hi;
+                                    vj = __fmaf_rd(m_, us, __fmul_rd(a.rho, __fmul_rd(us, us)));
+                                    const float du = __fmul_ru(kTwoU, fabsf(uc));
+                                    e = __fmaf_ru(__fmul_ru(a.rho, du), du, e);
+                                }
+                            } else {
+                                us = m_ >= 0.f ? lo : hi;
+                                vj = __fmul_rd(m_, us);
+                            }
+                            vsum = __fadd_rd(vsum, vj);
+                            if (a.ustar) a.ustar[(size_t)box * d + j] = us;
+                            if (a.lin_coef && a.lin_coef != a.mu) a.lin_coef[(size_t)box * d + j] = m_;
+                        }
                     }
                     const float raw = __fadd_rd(c, vsum);
                     const float marg = __fadd_ru(mg, e);
@@ -408,6 +522,7 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
                 }
             }
         }
+        if (STG) cp_wait<0>();  // no copy may land after the shared memory is released
     } else if (warp < mma_warp + NSLOT && lane == 0) {
         // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
         const int sl = warp - mma_warp;
@@ -547,10 +662,26 @@ bool crown_tc_supported(const NetDesc &N, int max_smem)
     return crown_tc_resident(N, 1, max_smem) || 2 * crown_tc_stage(N) + crown_tc_extra(N, 1) + 1024 <= (size_t)max_smem;
 }
 
-template <int NSLOT, int SP, bool STREAM, bool OBST>
+// Staged launches: the floats of the per-thread areas for tiles of bpt boxes (a.stg_* set as a side effect).
+static size_t crown_tc_stg_floats(const NetDesc &N, int bpt, bool alpha, BoundArgs &a)
+{
+    int cols = 0;
+    for (int l = 1; l < N.L; ++l) {
+        const int dl = N.dims[l], c = dl % 64 == 0 ? dl / 2 : dl;
+        cols = c > cols ? c : cols;
+    }
+    int hid = (alpha ? 4 : 3) * cols + 4;
+    if ((hid / 4) % 2 == 0) hid += 4;
+    a.stg_cols = cols;
+    a.stg_hid = hid;
+    a.stg_step = 6 * pad16(N.s) + 4;
+    return (size_t)2 * bpt * hid + (size_t)bpt * a.stg_step;
+}
+
+template <int NSLOT, int SP, bool STREAM, bool OBST, bool STG>
 static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = k_crown_tc<NSLOT, SP, STREAM, OBST>;
+    auto kern = k_crown_tc<NSLOT, SP, STREAM, OBST, STG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, (NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, smem, st>>>(a);
@@ -558,21 +689,25 @@ static cudaError_t launch_variant(const BoundArgs &a, int grid, size_t smem, cud
 }
 
 template <int SP>
-static cudaError_t launch_shape(const BoundArgs &a, int nslot, bool stream, int grid, size_t smem, cudaStream_t st)
+static cudaError_t launch_shape(const BoundArgs &a, int nslot, bool stream, bool stg, int grid, size_t smem,
+                                cudaStream_t st)
 {
     if (a.cost.kind == 1) {
         // the obstacle cost: resident backward image only (the caller checks crown_tc_obstacles_supported)
         if (stream) return cudaErrorNotSupported;
-        return nslot == 2 ? launch_variant<2, SP, false, true>(a, grid, smem, st)
-                          : launch_variant<1, SP, false, true>(a, grid, smem, st);
+        if (stg) return launch_variant<1, SP, false, true, true>(a, grid, smem, st);
+        return nslot == 2 ? launch_variant<2, SP, false, true, false>(a, grid, smem, st)
+                          : launch_variant<1, SP, false, true, false>(a, grid, smem, st);
     }
-    if (stream) return launch_variant<1, SP, true, false>(a, grid, smem, st);
-    return nslot == 2 ? launch_variant<2, SP, false, false>(a, grid, smem, st)
-                      : launch_variant<1, SP, false, false>(a, grid, smem, st);
+    if (stream) return launch_variant<1, SP, true, false, false>(a, grid, smem, st);
+    if (stg) return launch_variant<1, SP, false, false, true>(a, grid, smem, st);
+    return nslot == 2 ? launch_variant<2, SP, false, false, false>(a, grid, smem, st)
+                      : launch_variant<1, SP, false, false, false>(a, grid, smem, st);
 }
 
-// nslot_pref: tiles per CTA (1 or 2), or -1 for two only when the tiles outnumber the SMs
-cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream_t st)
+// variant: 0 staged (one slot, a multiple of 4 up to 32 boxes per tile, the fewest that spread the batch over
+// the SMs; falls back to 1 when the areas do not fit), 1 or 2 unstaged tiles per CTA, -1 staged when it fits
+cudaError_t launch_crown_tc(BoundArgs a, int variant, int num_sms, cudaStream_t st)
 {
     const NetDesc &N = a.net;
     if (a.n <= 0) return cudaSuccess;
@@ -580,17 +715,40 @@ cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int slot_cols = N.tcb_dcols + 2 * N.tcb_acols;
+    const int SP = pad16(N.s);
+    int cols = 32;
+    while (cols < slot_cols) cols *= 2;
+    if (variant == -1 || variant == 0) {
+        int bpt = (a.n + num_sms - 1) / num_sms;
+        bpt = (bpt + 3) & ~3;
+        bpt = bpt < 4 ? 4 : (bpt > 32 ? 32 : bpt);
+        const bool resident = crown_tc_resident(N, 1, max_smem);
+        for (; resident && bpt >= 4; bpt -= 4) {
+            const size_t smem = (size_t)N.tcb_bytes + crown_tc_extra(N, 1) + 16 +
+                                4 * crown_tc_stg_floats(N, bpt, a.alpha != nullptr, a);
+            if (smem + 1024 > (size_t)max_smem) continue;
+            a.tc_rows = bpt;
+            a.tmem_cols = (uint32_t)cols;
+            a.stages = 0;
+            const int ntiles = (a.n + bpt - 1) / bpt;
+            const int grid = ntiles < num_sms ? ntiles : num_sms;
+            if (SP == 16) return launch_shape<16>(a, 1, false, true, grid, smem, st);
+            if (SP == 32) return launch_shape<32>(a, 1, false, true, grid, smem, st);
+            return cudaErrorInvalidConfiguration;
+        }
+    }
+    a.stg_cols = a.stg_hid = a.stg_step = 0;
     // boxes per tile: 128 when the tiles at least fill the SMs, else 64 or 32
     a.tc_rows = 128;
     while (a.tc_rows > 32 && (a.n + a.tc_rows - 1) / a.tc_rows < num_sms) a.tc_rows /= 2;
     if ((a.n + a.tc_rows - 1) / a.tc_rows > num_sms && a.tc_rows < 128) a.tc_rows *= 2;
     const int ntiles = (a.n + a.tc_rows - 1) / a.tc_rows;
     int nslot = (ntiles > num_sms && 2 * slot_cols <= 512) ? 2 : 1;
-    if (nslot_pref == 1 || nslot_pref == 2) nslot = nslot_pref;
+    if (variant == 1 || variant == 2) nslot = variant;
     const bool stream = !crown_tc_resident(N, nslot, max_smem) && !crown_tc_resident(N, 1, max_smem);
     if (!stream && !crown_tc_resident(N, nslot, max_smem)) nslot = 1;
     if (stream) nslot = 1;
-    int cols = 32;
+    cols = 32;
     while (cols < nslot * slot_cols) cols *= 2;
     if (cols > 512) return cudaErrorInvalidConfiguration;
     a.tmem_cols = (uint32_t)cols;
@@ -609,9 +767,8 @@ cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream
     }
     int grid = (ntiles + nslot - 1) / nslot;
     grid = grid < num_sms ? grid : num_sms;
-    const int SP = pad16(N.s);
-    if (SP == 16) return launch_shape<16>(a, nslot, stream, grid, smem, st);
-    if (SP == 32) return launch_shape<32>(a, nslot, stream, grid, smem, st);
+    if (SP == 16) return launch_shape<16>(a, nslot, stream, false, grid, smem, st);
+    if (SP == 32) return launch_shape<32>(a, nslot, stream, false, grid, smem, st);
     return cudaErrorInvalidConfiguration;
 }
 

@@ -122,6 +122,7 @@ struct BoundArgs {
     int tc_rows;             // boxes per 128-row tile of the tensor-core CROWN (32, 64 or 128; the other rows idle)
     int stages;              // > 0: the backward image is streamed through `stages` ring buffers
     int stage_bytes;
+    int stg_cols, stg_hid, stg_step;  // staged tensor-core CROWN: columns a thread takes, floats per area
     CostDesc cost;           // the state cost (kind 0: squared distance)
 };
 

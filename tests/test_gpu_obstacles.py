@@ -127,6 +127,26 @@ def test_obstacle_crown_tensor_cores(oracle, obst):
         assert lb_t[i] <= fmin and best[i] <= fmin
 
 
+def test_obstacle_crown_tc_variants_bit_identical(obst):
+    """The obstacle cost on the staged tensor-core CROWN (next-layer interval bounds and state boxes copied to
+    shared memory ahead of use) and on one and two unstaged tiles per CTA: bit-identical outputs."""
+    from paper_2412_09584_gb300 import binding as B
+    p, g = obst(H=8, n_obs=4, lam=20.0)
+    n = 150
+    lo, hi, _ = W.random_boxes(16, n, seed=85, min_width=0.02, max_width=0.6)
+    try:
+        outs = []
+        for v in (0, 1, 2):
+            B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, v)
+            outs.append(g.crown(lo, hi, precision=B.PREC_BF16X3))
+        for o in outs[1:]:
+            for key in ("lb", "margin", "lin_coef", "lin_const"):
+                assert np.array_equal(outs[0][key].view(np.uint32), o[key].view(np.uint32)), key
+        assert B.bab_status(g.ctx) == 0
+    finally:
+        B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, -1)
+
+
 def test_obstacle_alpha_gradient_and_step(oracle, obst):
     """alpha-CROWN with the obstacle cost: the adjoint gradient at the adaptive slopes and the bound against the
     oracle's, and Adam's first step."""

@@ -55,16 +55,27 @@ def test_rollout_tc_slots_bit_identical():
         g.close()
 
 
-def test_crown_tc_slots_bit_identical():
+@pytest.mark.parametrize("name,n,with_alpha", [("tiny", 300, False), ("pushing", 300, False), ("pushing", 211, True),
+                                                ("pushing", 5000, False)])
+def test_crown_tc_variants_bit_identical(name, n, with_alpha):
+    """Staged (each thread's next-layer interval bounds copied to shared memory ahead of use, up to 32 boxes a
+    tile; 5000 boxes give each CTA several tiles), one and two unstaged tiles per CTA: the same arithmetic in the
+    same order, so every output agrees bit for bit, with and without given slopes."""
     from paper_2412_09584_gb300 import binding as B
-    p, lo, hi, ids, g = _problem("tiny", 300)
+    p, lo, hi, ids, g = _problem(name, n)
     try:
+        alpha = None
+        if with_alpha:
+            rng = np.random.default_rng(3)
+            alpha = rng.uniform(0.0, 1.0, size=(n, g.H, g.sumh)).astype(np.float32)
         outs = []
-        for v in (1, 2):
+        for v in (0, 1, 2):
             B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, v)
-            outs.append(g.crown(lo, hi, precision=B.PREC_BF16X3))
-        for key in ("lb", "margin", "lin_coef", "lin_const"):
-            assert np.array_equal(outs[0][key].view(np.uint32), outs[1][key].view(np.uint32)), key
+            outs.append(g.crown(lo, hi, alpha=alpha, precision=B.PREC_BF16X3))
+        for o in outs[1:]:
+            for key in ("lb", "margin", "lin_coef", "lin_const"):
+                assert np.array_equal(outs[0][key].view(np.uint32), o[key].view(np.uint32)), key
+        assert B.bab_status(g.ctx) == 0
     finally:
         g.close()
 
@@ -145,7 +156,7 @@ def test_autotune_keeps_results(oracle):
         B.bab_autotune(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), ids_t(ids), lo.shape[0], 256, alpha_steps=4)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_FP32) in (0, 1, 2)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_TC) in (1, 2)
-        assert B.bab_get_variant(g.ctx, B.KERNEL_CROWN_TC) in (1, 2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_CROWN_TC) in (0, 1, 2)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ALPHA_FUSED) in (-2, 0, 1, 2, 3)
         after = g.rollout(lo, hi, ids, M=256, seed=5)
         assert np.array_equal(after["ub"].view(np.uint32), before["ub"].view(np.uint32))
