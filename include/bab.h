@@ -568,12 +568,20 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  *                            distance cost only: with the obstacle cost -1
  *                            takes the separate launches and 3 is refused).
  *   BAB_KERNEL_ROLLOUT_TC    1 or 2 sample tiles per CTA.
- *   BAB_KERNEL_CROWN_TC      0: one tile of up to 32 boxes per CTA, each
- *                            epilogue thread staging its next layer's interval
- *                            bounds in shared memory while the tensor core
- *                            runs (the default where it fits; 1 otherwise);
- *                            1 or 2: tiles of up to 128 boxes per CTA, the
- *                            bounds read from global memory where needed.
+ *   BAB_KERNEL_CROWN_TC      3 or 4: feature-major products (the layer's
+ *                            features on the MMA's 128 rows, 32 boxes on its
+ *                            columns) with 8 or 16 epilogue warps; squared-
+ *                            distance cost and widths <= 128 only, 0 otherwise
+ *                            (4 is the default where it applies);
+ *                            0: box-major, one tile of up to 32 boxes per CTA,
+ *                            each epilogue thread staging its next layer's
+ *                            interval bounds in shared memory while the tensor
+ *                            core runs (the default otherwise, where it fits;
+ *                            1 where not); 1 or 2: tiles of up to 128 boxes
+ *                            per CTA, the bounds read where needed.  Variants
+ *                            0, 1, 2 give bit-identical results, and so do 3
+ *                            and 4; the feature-major kernels sum each box's
+ *                            constant in another order (within rounding).
  * -1 selects the built-in heuristic everywhere.  bab_set_variant returns
  * BAB_ERR_INVALID_ARG for an unknown kernel or variant; a variant whose tile
  * does not fit the network makes the later call fail with BAB_ERR_CUDA.

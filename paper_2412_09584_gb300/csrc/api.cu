@@ -28,7 +28,7 @@ struct bab_ctx {
     int tune_rollout_fp32 = -1;
     int tune_alpha_fused = -1;  // -2: the unfused loop of bound, adjoint and Adam launches
     int tune_rollout_tc = -1;   // tiles per CTA
-    int tune_crown_tc = -1;     // 0 staged, 1 or 2 tiles per CTA, -1 staged where it fits
+    int tune_crown_tc = -1;     // 3, 4 feature-major, 0 staged, 1 or 2 tiles per CTA, -1 the first that applies
     int rescore_topk = 0;       // BF16 rollouts: FP32 re-score of the topk smallest ub (0: every box)
     size_t scratch_limit = 0;   // bab_set_scratch_limit: bound calls chunk their boxes to stay within it (0: none)
     CostDesc cost{};            // the state cost (bab_set_cost); kind 0 by default
@@ -1580,7 +1580,7 @@ int bab_set_variant(bab_ctx *c, int kernel, int variant)
             c->tune_rollout_tc = variant;
             return BAB_OK;
         case BAB_KERNEL_CROWN_TC:
-            if (variant < -1 || variant > 2) break;
+            if (variant < -1 || variant > 4) break;
             c->tune_crown_tc = variant;
             return BAB_OK;
         default:
@@ -1703,7 +1703,7 @@ int bab_autotune(bab_ctx *c, const float *x0, const float *goal, int H, float rh
                      [&] { return bab_rollout(c, x0, goal, H, rho, lo, hi, id, n, nullptr, samples, seed,
                                               BAB_PREC_BF16X3, ub, best_u, nullptr, nullptr, stream); });
     if (crown_tc_supported(c->net, c->max_smem))
-        pick_fastest(c, st, {0, 1, 2}, -1, [&](int v) { c->tune_crown_tc = v; },
+        pick_fastest(c, st, {4, 3, 0, 1, 2}, -1, [&](int v) { c->tune_crown_tc = v; },
                      [&] { return bab_bound_crown(c, x0, goal, H, rho, lo, hi, n, nullptr, nullptr, BAB_PREC_BF16X3, lb,
                                                   nullptr, nullptr, nullptr, stream); });
     if (alpha_steps > 0) {

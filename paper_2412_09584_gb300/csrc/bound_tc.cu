@@ -635,6 +635,418 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
     }
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// Feature-major tensor-core CROWN.  The same backward pass with every product transposed,
+//
+//   D[i][b] = sum_j W_l[j][i] A'[b][j]      M = 128 feature rows (the layer's inputs, one per TMEM lane),
+//                                           N = 32 boxes (a tile), K = d_l,
+//
+// A = the backward image in shared memory (a layer with fewer than 128 inputs: the rows past them read the
+// image's next bytes and their accumulator lanes are ignored), B = the tile's relaxed coefficients A'[b][j],
+// written to shared memory by the epilogue as BF16 hi and lo halves (K-major, 128-byte swizzle).  With WQ
+// epilogue warps per TMEM lane quadrant (2 or 4), warp (quadrant q, share h) lane `lane` owns feature
+// j = 32 q + lane of the tile's boxes 32/WQ h .. 32/WQ (h + 1) - 1: every lane works,
+// and a warp's interval-bound loads for one box are 128 contiguous bytes, issued for the next layer while the
+// tensor core runs the current product.  Each thread keeps, per box, partial sums over its features of the
+// constant (rounded down) and of the rounding-error margin (rounded up); a warp shuffle and the four quadrant
+// warps reduce them per box at the end of the tile.  The state lanes (j < s) carry the coefficient of the state
+// from step to step, the action lanes (s <= j < s + k) write mu.  Squared-distance cost, resident image, every
+// width at most 128.
+// ---------------------------------------------------------------------------------------------------------------
+constexpr int kNB = 32;   // boxes per tile: the MMA's N
+constexpr uint32_t kBopHalf = 2 * kNB * 128;  // one half (hi or lo) of the B operand: K <= 128 in two 64-wide blocks
+
+// byte offset of element (box n, k) in the K-major 128-byte-swizzled B operand of kNB rows
+__device__ __forceinline__ uint32_t bop_off(int n, int k)
+{
+    const int kb = k >> 6, w = k & 63;
+    return (uint32_t)(kb * kNB * 128 + (n >> 3) * 1024 + (n & 7) * 128 + ((((w * 2) >> 4) ^ (n & 7)) << 4) +
+                      ((w * 2) & 15));
+}
+__device__ __forceinline__ void st_bf16_pair(uint8_t *bop, uint32_t off, float v)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    *reinterpret_cast<__nv_bfloat16 *>(bop + off) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(bop + kBopHalf + off) = l;
+}
+
+// Lemma 1's relaxation without branches (the lanes of a warp hold different neurons).  The upper slope of an
+// unstable neuron is a fast quotient bounded upward: any slope at least u / (u - l) gives a valid upper line
+// through (l, 0), and the quotient of __fdividef (2 ulp) over the denominator rounded down, scaled up by
+// 2^-20 and capped at 1, is one; slope 1 where the quotient could be inexact (huge denominator, tiny numerator).
+__device__ __forceinline__ void relax_nb(float zl, float zu, float A, float alpha_j, bool has_alpha, float &D, float &c)
+{
+    const bool on = zl >= 0.f, off = zu <= 0.f;
+    const float den = __fsub_rd(zu, zl);
+    const bool fast = den < 1e36f && zu > 1e-30f;
+    const float du = fast ? fminf(__fmul_ru(__fdividef(zu, den), 1.00000095367431640625f), 1.f) : 1.f;
+    const float lower = has_alpha ? alpha_j : (zu >= -zl ? 1.f : 0.f);
+    const bool up = !on && !off && A < 0.f;
+    D = on ? 1.f : (off ? 0.f : (up ? du : lower));
+    c = up ? __fmul_ru(du, -zl) : 0.f;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void tmem_ld_bpt(uint32_t taddr, uint32_t (&r)[16]) { tc::tmem_ld16(taddr, r); }
+__device__ __forceinline__ void tmem_ld_bpt(uint32_t taddr, uint32_t (&r)[8]) { tc::tmem_ld8(taddr, r); }
+
+template <bool ALPHA, int WQ>
+__global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
+{
+    constexpr int NE = 4 * WQ, BPT = kNB / WQ;  // epilogue warps, boxes per epilogue thread
+    extern __shared__ uint8_t smem_raw[];
+    const NetDesc &N = a.net;
+    uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *bop = wimg + (((size_t)N.tcb_bytes + 1023) & ~size_t(1023));
+    float *bias = reinterpret_cast<float *>(bop + 2 * kBopHalf);
+    float *red = bias + ((N.tc_bias_floats + 3) & ~3);  // [2 tile parities][4 quadrants][kNB][2]
+    float *small = red + 2 * 4 * kNB * 2;               // [WQ][32 lanes][2 step parities][3][BPT]
+    __shared__ uint64_t bar_w, bar_a, bar_d, bar_r, bar_fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = N.L, s = N.s, k = N.k, H = a.H, d = a.d, sumh = N.sumh, sw = N.sumh + N.s;
+    volatile int *abort = &abort_flag;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        tc::mbar_init(&bar_w, 1);
+        tc::mbar_init(&bar_a, NE);
+        tc::mbar_init(&bar_d, 1);
+        tc::mbar_init(&bar_r, NE);
+        tc::mbar_init(&bar_fin, 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == NE) tc::tmem_alloc(&tmem_base, 32);
+    for (int i = threadIdx.x; i < N.tc_bias_floats; i += blockDim.x) bias[i] = a.tc_bias[i];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == NE * 32) {
+        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
+        for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
+            tc::bulk_g2s(wimg + off, a.tcb_img + off, min(32768u, (uint32_t)N.tcb_bytes - off), &bar_w);
+    }
+    if (!wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
+
+    const int nlive = live_count(a.n, a.d_n, a.row0);
+    const int ntiles = (nlive + kNB - 1) / kNB;
+    const uint32_t tb = tmem_base;
+
+    if (warp < NE) {
+        const int q = warp & 3, h = warp >> 2, j = 32 * q + lane;  // h: the warp's share of the tile's boxes
+        const uint32_t dcol = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(BPT * h);
+        float *sm = small + (size_t)(h * 32 + lane) * (2 * 3 * BPT);
+        const bool state = j < s;
+        uint32_t phD = 0, phR = 0;
+        int par = 0;
+        for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, par ^= 1) {
+            const int box0 = tile * kNB + BPT * h;
+            float lam[BPT], cp[BPT], mp[BPT];
+            float pzl[BPT], pzu[BPT], pS[BPT], pal[BPT];
+            bool ok = true;
+            // feature j of hidden layer l at step t for the thread's boxes: interval bounds, margin helper, slope;
+            // and the layer after it into L2 (lane L: box L % 16, arrays L / 16 and 2 + L / 16)
+            auto prefetch = [&](int t, int l) {
+                const int t2 = l > 1 ? t : t - 1, l2 = l > 1 ? l - 1 : L - 1;
+                if (t2 >= 0 && box0 + (lane % BPT) < nlive) {
+                    const size_t rb = (size_t)(box0 + (lane % BPT)) * H + t2;
+                    const size_t ib = rb * sumh + N.hoff[l2];
+                    prefetch_l2((lane / BPT) % 2 == 0 ? a.pre_lo + ib : a.pre_hi + ib);
+                    if ((lane / BPT) % 2 == 0) prefetch_l2(a.S + rb * sw + N.hoff[l2]);
+                    else if (ALPHA) prefetch_l2(a.alpha + ib);
+                }
+                const bool fj = j < N.dims[l];
+#pragma unroll
+                for (int bi = 0; bi < BPT; ++bi) {
+                    const bool v = fj && box0 + bi < nlive;
+                    const size_t rb = (size_t)(box0 + bi) * H + t;
+                    const size_t ib = rb * sumh + N.hoff[l] + j;
+                    pzl[bi] = v ? a.pre_lo[ib] : 0.f;
+                    pzu[bi] = v ? a.pre_hi[ib] : 0.f;
+                    pS[bi] = v ? a.S[rb * sw + N.hoff[l] + j] : 0.f;
+                    if (ALPHA) pal[bi] = v ? a.alpha[ib] : 0.f;
+                }
+            };
+            // state lanes: the output layer's margin helper at step t and the box of x_t, copied ahead of use
+            auto stage_step = [&](int t) {
+                if (!state) return;
+                float *p = sm + (t & 1) * 3 * BPT;
+                for (int bi = 0; bi < BPT && box0 + bi < nlive; ++bi) {
+                    const size_t b = (size_t)(box0 + bi);
+                    cp4(p + bi, a.S + (b * H + t) * sw + sumh + j);
+                    if (t >= 1) {
+                        cp4(p + BPT + bi, a.x_lo + (b * (H + 1) + t) * s + j);
+                        cp4(p + 2 * BPT + bi, a.x_hi + (b * (H + 1) + t) * s + j);
+                    }
+                }
+                cp_commit();
+            };
+#pragma unroll
+            for (int bi = 0; bi < BPT; ++bi) {
+                lam[bi] = cp[bi] = mp[bi] = 0.f;
+                if (state && box0 + bi < nlive) {
+                    // tangent of ||x_H - g||^2
+                    const size_t xi = ((size_t)(box0 + bi) * (H + 1) + H) * s + j;
+                    float ct;
+                    tangent(a.x_lo[xi], a.x_hi[xi], a.goal[j], lam[bi], ct);
+                    cp[bi] = ct;
+                }
+            }
+            stage_step(H - 1);
+            prefetch(H - 1, L - 1);
+            for (int t = H - 1; t >= 0 && ok; --t) {
+                const float *sx = sm + (t & 1) * 3 * BPT;
+                // ---- output layer: B = lam (zero up to K), constant lam . b_L, margin of the product ----
+                if (q == 0 && j < N.tcb_K[L]) {
+                    float bL = 0.f;
+                    if (state) {
+                        cp_wait<0>();
+                        bL = bias[N.tc_boff[L] + j];
+                    }
+                    const float gL = N.gam_tc[L];
+#pragma unroll
+                    for (int bi = 0; bi < BPT; ++bi) {
+                        const float v = state ? lam[bi] : 0.f;
+                        st_bf16_pair(bop, bop_off(BPT * h + bi, j), v);
+                        if (state && box0 + bi < nlive) {
+                            cp[bi] = __fmaf_rd(v, bL, cp[bi]);
+                            mp[bi] = __fmaf_ru(__fmul_ru(gL, fabsf(v)), sx[bi], mp[bi]);
+                        }
+                    }
+                }
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bar_a);
+                // ---- hidden layers l = L-1 .. 1: relax the coefficient on a_l, B = A' for the product with W_l ----
+                for (int l = L - 1; l >= 1; --l) {
+                    if (!wwait(&bar_d, phD, abort)) {
+                        if (lane == 0) abort_all(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    phD ^= 1;
+                    tc::fence_after_sync();
+                    uint32_t v[BPT];
+                    tmem_ld_bpt(dcol, v);
+                    tc::tmem_wait_ld();
+                    if (j < N.dims[l]) {
+                        const float bj = bias[N.tc_boff[l] + j], gK = N.gam_tc[l];
+#pragma unroll
+                        for (int bi = 0; bi < BPT; ++bi) {
+                            const bool vb = box0 + bi < nlive;
+                            const float A = vb ? __uint_as_float(v[bi]) : 0.f;
+                            float D, c;
+                            relax_nb(pzl[bi], pzu[bi], A, ALPHA ? pal[bi] : 0.f, ALPHA, D, c);
+                            const float Ap = A * D;
+                            if (vb) {
+                                if (a.A_pre) a.A_pre[((size_t)(box0 + bi) * H + t) * sumh + N.hoff[l] + j] = A;
+                                cp[bi] = __fmaf_rd(A, c, cp[bi]);
+                                cp[bi] = __fmaf_rd(Ap, bj, cp[bi]);
+                                mp[bi] = __fmaf_ru(__fmul_ru(gK, fabsf(Ap)), pS[bi], mp[bi]);
+                                if (D != 0.f && D != 1.f)
+                                    mp[bi] = __fmaf_ru(__fmul_ru(kTwoU, fabsf(Ap)), fmaxf(-pzl[bi], pzu[bi]), mp[bi]);
+                            }
+                            st_bf16_pair(bop, bop_off(BPT * h + bi, j), Ap);
+                        }
+                    }
+                    tc::fence_proxy_async_smem();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bar_a);
+                    // the next layer's data, loaded while the tensor core runs this product
+                    if (l > 1) {
+                        prefetch(t, l - 1);
+                    } else if (t >= 1) {
+                        stage_step(t - 1);
+                        prefetch(t - 1, L - 1);
+                    }
+                }
+                if (!ok) break;
+                // ---- coefficient on [x_t | u_t]: state lanes update lam (+ tangent of x_t), action lanes write mu ----
+                if (!wwait(&bar_d, phD, abort)) {
+                    if (lane == 0) abort_all(a.status, abort);
+                    ok = false;
+                    break;
+                }
+                phD ^= 1;
+                tc::fence_after_sync();
+                uint32_t v[BPT];
+                tmem_ld_bpt(dcol, v);
+                tc::tmem_wait_ld();
+                if (state) {
+#pragma unroll
+                    for (int bi = 0; bi < BPT; ++bi) {
+                        if (box0 + bi >= nlive) continue;
+                        float aa = 0.f, B;
+                        if (t >= 1) {
+                            const float xl = sx[BPT + bi], xu = sx[2 * BPT + bi];
+                            float ct;
+                            tangent(xl, xu, a.goal[j], aa, ct);
+                            cp[bi] = __fadd_rd(cp[bi], ct);
+                            B = fmaxf(fabsf(xl), fabsf(xu));
+                        } else {
+                            B = fabsf(a.x0[j]);
+                        }
+                        const float lo_ = lam[bi], Ax = __uint_as_float(v[bi]);
+                        lam[bi] = (lo_ + Ax) + aa;
+                        const float mag = __fadd_ru(__fadd_ru(fabsf(lo_), fabsf(Ax)), fabsf(aa));
+                        mp[bi] = __fmaf_ru(__fmul_ru(kTwoU, mag), B, mp[bi]);
+                    }
+                } else if (j < s + k) {
+#pragma unroll
+                    for (int bi = 0; bi < BPT; ++bi)
+                        if (box0 + bi < nlive) a.mu[(size_t)(box0 + bi) * d + t * k + (j - s)] = __uint_as_float(v[bi]);
+                }
+            }
+            if (!ok) break;
+            // ---- per box: the constant with lam . x_0, summed over the warp's features, then over the quadrants ----
+#pragma unroll
+            for (int bi = 0; bi < BPT; ++bi) {
+                if (state && box0 + bi < nlive) cp[bi] = __fmaf_rd(lam[bi], a.x0[j], cp[bi]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    cp[bi] = __fadd_rd(cp[bi], __shfl_xor_sync(0xFFFFFFFFu, cp[bi], o));
+                    mp[bi] = __fadd_ru(mp[bi], __shfl_xor_sync(0xFFFFFFFFu, mp[bi], o));
+                }
+            }
+            float *rp = red + (size_t)par * 4 * kNB * 2 + ((size_t)q * kNB + BPT * h) * 2;
+            if (lane == 0)
+#pragma unroll
+                for (int bi = 0; bi < BPT; ++bi) {
+                    rp[2 * bi] = cp[bi];
+                    rp[2 * bi + 1] = mp[bi];
+                }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_r);
+            if (warp != 0) continue;
+            // ---- warp 0: concretize (Theorem 2, box form) box `lane` of the tile and write ----
+            if (!wwait(&bar_r, phR, abort)) {
+                if (lane == 0) abort_all(a.status, abort);
+                break;
+            }
+            phR ^= 1;
+            const int box = tile * kNB + lane;
+            if (box < nlive) {
+            const float *rr = red + (size_t)par * 4 * kNB * 2 + (size_t)lane * 2;
+            float c = rr[0], mg = rr[1];
+            for (int q2 = 1; q2 < 4; ++q2) {
+                c = __fadd_rd(c, rr[(size_t)q2 * kNB * 2]);
+                mg = __fadd_ru(mg, rr[(size_t)q2 * kNB * 2 + 1]);
+            }
+            float vsum = 0.f, e = 0.f;
+            for (int j0 = 0; j0 < d; j0 += 8) {
+                float mv[8], lv[8], hv[8];
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    const size_t e8 = (size_t)box * d + (j0 + qq < d ? j0 + qq : j0);
+                    mv[qq] = a.mu[e8];
+                    lv[qq] = a.lo[e8];
+                    hv[qq] = a.hi[e8];
+                }
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq) {
+                    if (j0 + qq >= d) break;
+                    const int jj = j0 + qq;
+                    const float m_ = mv[qq], lo = lv[qq], hi = hv[qq];
+                    float us, vj;
+                    if (a.rho > 0.f) {
+                        const float uc = -m_ / (2.f * a.rho);
+                        if (uc >= lo && uc <= hi) {
+                            us = uc;
+                            vj = __fdiv_rd(-__fmul_ru(m_, m_), 4.f * a.rho);
+                        } else {
+                            us = uc < lo ? lo : hi;
+                            vj = __fmaf_rd(m_, us, __fmul_rd(a.rho, __fmul_rd(us, us)));
+                            const float du = __fmul_ru(kTwoU, fabsf(uc));
+                            e = __fmaf_ru(__fmul_ru(a.rho, du), du, e);
+                        }
+                    } else {
+                        us = m_ >= 0.f ? lo : hi;
+                        vj = __fmul_rd(m_, us);
+                    }
+                    vsum = __fadd_rd(vsum, vj);
+                    if (a.ustar) a.ustar[(size_t)box * d + jj] = us;
+                    if (a.lin_coef && a.lin_coef != a.mu) a.lin_coef[(size_t)box * d + jj] = m_;
+                }
+            }
+            const float raw = __fadd_rd(c, vsum);
+            const float marg = __fadd_ru(mg, e);
+            const float lbv = __fsub_rd(raw, marg);
+            a.lb[box] = lbv;
+            if (a.margin) a.margin[box] = marg;
+            if (a.lin_const) a.lin_const[box] = c;
+            if (a.lb_best) a.lb_best[box] = fmaxf(a.lb_best[box], lbv);
+            }
+        }
+        cp_wait<0>();  // no copy may land after the shared memory is released
+    } else if (warp == NE && lane == 0) {
+        // ---------------------- MMA issuer ----------------------
+        const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        long long left = cnt * H * L;
+        int l = L;
+        uint32_t phA = 0;
+        const uint32_t idesc = tc::idesc_bf16_f32(128, kNB);
+        const uint32_t bh = tc::desc_sw128_lo(tc::smem_u32(bop)), bl = tc::desc_sw128_lo(tc::smem_u32(bop + kBopHalf));
+        while (left > 0 && !*abort) {
+            if (!tc::mbar_wait(&bar_a, phA, abort, kWaitNs)) {
+                abort_all(a.status, abort);
+                break;
+            }
+            phA ^= 1;
+            tc::fence_after_sync();
+            const int nks = N.tcb_K[l] / 16, Nl = N.tcb_N[l];
+            const uint32_t ah = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_hi[l]));
+            const uint32_t al = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_lo[l]));
+            for (int ks = 0; ks < nks; ++ks) {
+                // 16-byte units: K-block ks / 4 of the operand, then 32 bytes per K = 16 step inside it
+                const uint32_t ao = (uint32_t)((ks >> 2) * Nl * 8 + (ks & 3) * 2);
+                const uint32_t bo = (uint32_t)((ks >> 2) * kNB * 8 + (ks & 3) * 2);
+                const uint64_t Ah = tc::desc_join(ah + ao), Bh = tc::desc_join(bh + bo);
+                tc::mma_ss(tb, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
+                tc::mma_ss(tb, tc::desc_join(al + ao), Bh, idesc, 1u);
+                tc::mma_ss(tb, Ah, tc::desc_join(bl + bo), idesc, 1u);
+            }
+            tc::mma_commit(&bar_d);
+            l = (l == 1) ? L : l - 1;
+            --left;
+        }
+        if (*abort) {
+            volatile int never = 0;
+            tc::mma_commit(&bar_fin);
+            tc::mbar_wait(&bar_fin, 0, &never, kWaitNs);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == NE) {
+        __syncwarp();
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tb, 32);
+    }
+}
+
+// shared memory of k_crown_tcf beyond the image
+static size_t crown_tcf_extra(const NetDesc &N)
+{
+    return 1024 + 1024 + 2 * kBopHalf + ((size_t)((N.tc_bias_floats + 3) & ~3) + 2 * 4 * kNB * 2 + 32 * 2 * 3 * kNB) * 4;
+}
+
+// The feature-major kernel: squared-distance cost, every width at most 128 (the MMA's 128 rows), the image resident
+bool crown_tcf_supported(const NetDesc &N, int max_smem)
+{
+    for (int l = 0; l <= N.L; ++l)
+        if (N.dims[l] > 128) return false;
+    return N.tc_ok && N.L >= 2 && N.s <= 32 && N.tcb_K[N.L] <= 32 &&
+           (size_t)N.tcb_bytes + crown_tcf_extra(N) <= (size_t)max_smem;
+}
+
 static size_t crown_tc_extra(const NetDesc &N, int nslot)
 {
     return (size_t)N.tc_bias_floats * 4 + (size_t)nslot * 128 * 2 * 4 + 1024;
@@ -705,8 +1117,9 @@ static cudaError_t launch_shape(const BoundArgs &a, int nslot, bool stream, bool
                       : launch_variant<1, SP, false, false, false>(a, grid, smem, st);
 }
 
-// variant: 0 staged (one slot, a multiple of 4 up to 32 boxes per tile, the fewest that spread the batch over
-// the SMs; falls back to 1 when the areas do not fit), 1 or 2 unstaged tiles per CTA, -1 staged when it fits
+// variant: 3 or 4 feature-major with 8 or 16 epilogue warps (fall back to 0 where it does not apply), 0 staged (one slot, a multiple of 4 up to
+// 32 boxes per tile, the fewest that spread the batch over the SMs; falls back to 1 when the areas do not fit),
+// 1 or 2 unstaged tiles per CTA, -1 the first of 4, 0, 1 that applies
 cudaError_t launch_crown_tc(BoundArgs a, int variant, int num_sms, cudaStream_t st)
 {
     const NetDesc &N = a.net;
@@ -714,6 +1127,19 @@ cudaError_t launch_crown_tc(BoundArgs a, int variant, int num_sms, cudaStream_t 
     int dev, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((variant == -1 || variant == 3 || variant == 4) && a.cost.kind == 0 && crown_tcf_supported(N, max_smem)) {
+        const size_t smem = (size_t)N.tcb_bytes + crown_tcf_extra(N);
+        const int ntiles = (a.n + kNB - 1) / kNB;
+        const int grid = ntiles < num_sms ? ntiles : num_sms;
+        const int wq = variant == 3 ? 2 : 4;  // epilogue warps per TMEM lane quadrant
+        auto kern = wq == 2 ? (a.alpha ? k_crown_tcf<true, 2> : k_crown_tcf<false, 2>)
+                            : (a.alpha ? k_crown_tcf<true, 4> : k_crown_tcf<false, 4>);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, (4 * wq + 1) * 32, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (variant == 3 || variant == 4) variant = 0;
     const int slot_cols = N.tcb_dcols + 2 * N.tcb_acols;
     const int SP = pad16(N.s);
     int cols = 32;

@@ -80,13 +80,47 @@ def test_crown_tc_variants_bit_identical(name, n, with_alpha):
         g.close()
 
 
+@pytest.mark.parametrize("name,n,with_alpha", [("tiny", 300, False), ("pushing", 211, True), ("pushing", 5000, False)])
+def test_crown_tc_feature_major_matches_box_major(oracle, name, n, with_alpha):
+    """The feature-major kernel (features on the MMA's rows, 32 boxes on its columns) against the staged
+    box-major one (16 and 8 epilogue warps bit-identical): the same products, a branch-free relaxation whose
+    unstable upper slope is a quotient bounded upward, and the constant summed per feature and then across
+    features instead of in one running sum per box, so the downward roundings differ (the tree loses less: the
+    feature-major bound is the tighter one, by about 4e-6 relative here); bounds agree to 2e-5 of the bound's
+    scale, margins to 1e-3, coefficients to 1e-5 of the row's L1 norm, and both stay below the oracle's bound."""
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem(name, n)
+    try:
+        alpha = None
+        if with_alpha:
+            alpha = np.random.default_rng(4).uniform(0.0, 1.0, size=(n, g.H, g.sumh)).astype(np.float32)
+        outs = []
+        for v in (4, 3, 0):
+            B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, v)
+            outs.append(g.crown(lo, hi, alpha=alpha, precision=B.PREC_BF16X3))
+        assert B.bab_status(g.ctx) == 0
+        f, f8, b = outs
+        for key in ("lb", "margin", "lin_coef", "lin_const"):  # 16 and 8 epilogue warps: the same sums
+            assert np.array_equal(f[key].view(np.uint32), f8[key].view(np.uint32)), key
+        scale = np.maximum(np.abs(b["lin_const"]) + np.abs(b["lb"]), 1.0)
+        assert np.all(np.abs(f["lb"].astype(np.float64) - b["lb"]) <= 2e-5 * scale)
+        np.testing.assert_allclose(f["margin"], b["margin"], rtol=1e-3, atol=1e-12)
+        mu_scale = np.maximum(np.abs(b["lin_coef"]).sum(axis=1, keepdims=True), 1.0)
+        assert np.all(np.abs(f["lin_coef"] - b["lin_coef"]) <= 1e-5 * mu_scale)
+        rows = np.arange(0, n, max(1, n // 12))
+        o = oracle.crown(p, lo[rows], hi[rows], alpha=None if alpha is None else alpha[rows].astype(np.float64))
+        assert np.all(f["lb"][rows] <= o["lb"] + 1e-12 * np.abs(o["lb"]))
+    finally:
+        g.close()
+
+
 def test_set_variant_rejects_bad_values():
     from paper_2412_09584_gb300 import binding as B
     p, lo, hi, ids, g = _problem("tiny", 4)
     try:
         for kernel, bad in ((B.KERNEL_ROLLOUT_FP32, 3), (B.KERNEL_ALPHA_FUSED, -3), (B.KERNEL_ALPHA_FUSED, 4),
                             (B.KERNEL_ROLLOUT_TC, 0),
-                            (B.KERNEL_CROWN_TC, 3), (9, 0)):
+                            (B.KERNEL_CROWN_TC, 5), (9, 0)):
             with pytest.raises(B.BabError) as e:
                 B.bab_set_variant(g.ctx, kernel, bad)
             assert e.value.code == -1
@@ -156,7 +190,7 @@ def test_autotune_keeps_results(oracle):
         B.bab_autotune(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), ids_t(ids), lo.shape[0], 256, alpha_steps=4)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_FP32) in (0, 1, 2)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_TC) in (1, 2)
-        assert B.bab_get_variant(g.ctx, B.KERNEL_CROWN_TC) in (0, 1, 2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_CROWN_TC) in (0, 1, 2, 3, 4)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ALPHA_FUSED) in (-2, 0, 1, 2, 3)
         after = g.rollout(lo, hi, ids, M=256, seed=5)
         assert np.array_equal(after["ub"].view(np.uint32), before["ub"].view(np.uint32))
