@@ -35,25 +35,63 @@ constexpr float kTwoU = 1.1920930376163597e-07f;  // 2^-23 (1 + 2^-20): twice th
 // ---------------------------------------------------------------------------
 // IBP
 // ---------------------------------------------------------------------------
+// Paired FP32 FMA with directed rounding: (a.x b.x + c.x, a.y b.y + c.y), each rounded down (RD) or up (RU);
+// per element the same result as the scalar __fmaf_rd / __fmaf_ru.
+__device__ __forceinline__ unsigned long long ffma2_rd(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long ffma2_ru(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rp.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long pack2f(float x, float y)
+{
+    return (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
+}
+__device__ __forceinline__ float half2f(unsigned long long v, int e)
+{
+    return __uint_as_float((uint32_t)(e ? v >> 32 : v));
+}
+
+// Where a layer's outputs go: the interval bounds and S of step t to global memory (rows < nlive, columns < dl;
+// no pre-activation bounds for the output layer), and the next layer's input (ReLU of the bounds, or the bounds
+// of the output layer themselves) to the tile's shared-memory buffers.
+struct IbpSink {
+    float *pre_lo, *pre_hi, *S;  // at (box0 * H + t) of the [n][H][...] arrays
+    size_t rstride_h, rstride_s; // per row: H * sumh, H * (sumh + s)
+    int hoff, soff, dl, nrows;
+    bool hidden;
+};
+
+// One layer of interval bounds for RB rows, TR rows x TN columns per thread: per output the three directed-
+// rounding sums (lower, upper, and S = sum_k |W_jk| max|a_k|) over the inputs in order from the bias, the
+// endpoint of each input picked by the sign of the weight; two adjacent columns run as one paired FMA.
 template <int TR, int TN>
 __device__ __forceinline__ void ibp_dense(const float *__restrict__ alo, const float *__restrict__ ahi, int ld,
                                           const float *__restrict__ Wt, const float *__restrict__ bias, int Kp, int Np,
-                                          float *__restrict__ zlo, float *__restrict__ zhi, float *__restrict__ Sout)
+                                          float *__restrict__ zlo, float *__restrict__ zhi, const IbpSink &o)
 {
+    static_assert(TN % 2 == 0, "column pairs");
+    constexpr int TP = TN / 2;
     const int ngc = (Np + TN - 1) / TN;
     const int items = (RB / TR) * ngc;
     for (int it = threadIdx.x; it < items; it += NT) {
         const int cg = it % ngc, rg = it / ngc;
         const int c0 = cg * TN, r0 = rg * TR;
-        float accl[TR][TN], acch[TR][TN], accs[TR][TN];
+        unsigned long long accl[TR][TP], acch[TR][TP], accs[TR][TP];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const float bj = (c0 + j < Np) ? bias[c0 + j] : 0.f;
+        for (int jp = 0; jp < TP; ++jp) {
+            const int j = c0 + 2 * jp;
+            const unsigned long long b2 = pack2f(j < Np ? bias[j] : 0.f, j + 1 < Np ? bias[j + 1] : 0.f);
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
-                accl[i][j] = bj;
-                acch[i][j] = bj;
-                accs[i][j] = 0.f;
+                accl[i][jp] = acch[i][jp] = b2;
+                accs[i][jp] = 0ull;
             }
         }
         const bool full = (c0 + TN <= Np);
@@ -82,30 +120,55 @@ __device__ __forceinline__ void ibp_dense(const float *__restrict__ alo, const f
 #pragma unroll
                     for (int j = 0; j < TN; ++j) w[j] = (c0 + j < Np) ? wr[j] : 0.f;
                 }
+                bool pos[TN];
+                unsigned long long w2[TP], a2[TP];
+#pragma unroll
+                for (int jp = 0; jp < TP; ++jp) {
+                    pos[2 * jp] = w[2 * jp] >= 0.f;
+                    pos[2 * jp + 1] = w[2 * jp + 1] >= 0.f;
+                    w2[jp] = pack2f(w[2 * jp], w[2 * jp + 1]);
+                    a2[jp] = pack2f(fabsf(w[2 * jp]), fabsf(w[2 * jp + 1]));
+                }
 #pragma unroll
                 for (int i = 0; i < TR; ++i) {
                     const float al = kk == 0 ? l4[i].x : kk == 1 ? l4[i].y : kk == 2 ? l4[i].z : l4[i].w;
                     const float ah = kk == 0 ? h4[i].x : kk == 1 ? h4[i].y : kk == 2 ? h4[i].z : h4[i].w;
                     const float am = fmaxf(fabsf(al), fabsf(ah));
+                    const unsigned long long m2 = pack2f(am, am);
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) {
-                        const bool pos = w[j] >= 0.f;
-                        accl[i][j] = __fmaf_rd(w[j], pos ? al : ah, accl[i][j]);
-                        acch[i][j] = __fmaf_ru(w[j], pos ? ah : al, acch[i][j]);
-                        accs[i][j] = __fmaf_ru(fabsf(w[j]), am, accs[i][j]);
+                    for (int jp = 0; jp < TP; ++jp) {
+                        const bool p0 = pos[2 * jp], p1 = pos[2 * jp + 1];
+                        accl[i][jp] = ffma2_rd(w2[jp], pack2f(p0 ? al : ah, p1 ? al : ah), accl[i][jp]);
+                        acch[i][jp] = ffma2_ru(w2[jp], pack2f(p0 ? ah : al, p1 ? ah : al), acch[i][jp]);
+                        accs[i][jp] = ffma2_ru(a2[jp], m2, accs[i][jp]);
                     }
                 }
             }
         }
+        // write the rows' bounds and S, and the next layer's input
 #pragma unroll
-        for (int i = 0; i < TR; ++i)
+        for (int i = 0; i < TR; ++i) {
+            const int r = r0 + i;
+            const bool live = r < o.nrows;
 #pragma unroll
-            for (int j = 0; j < TN; ++j)
-                if (c0 + j < Np) {
-                    zlo[(r0 + i) * ld + c0 + j] = accl[i][j];
-                    zhi[(r0 + i) * ld + c0 + j] = acch[i][j];
-                    Sout[(r0 + i) * ld + c0 + j] = accs[i][j];
+            for (int jp = 0; jp < TP; ++jp)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = c0 + 2 * jp + e;
+                    if (j >= Np) continue;
+                    const float zl = half2f(accl[i][jp], e), zh = half2f(acch[i][jp], e);
+                    if (live && j < o.dl) {
+                        o.S[r * o.rstride_s + o.soff + j] = half2f(accs[i][jp], e);
+                        if (o.hidden) {
+                            o.pre_lo[r * o.rstride_h + o.hoff + j] = zl;
+                            o.pre_hi[r * o.rstride_h + o.hoff + j] = zh;
+                        }
+                    }
+                    const bool relu = o.hidden && j < o.dl;
+                    zlo[r * ld + j] = relu ? fmaxf(zl, 0.f) : zl;
+                    zhi[r * ld + j] = relu ? fmaxf(zh, 0.f) : zh;
                 }
+        }
     }
 }
 
@@ -129,7 +192,6 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
     bhi[0] = p; p += RB * ld;
     blo[1] = p; p += RB * ld;
     bhi[1] = p; p += RB * ld;
-    float *Sb = p; p += RB * ld;
     float *xl = p; p += RB * s4;
     float *xu = p; p += RB * s4;
     float *lbacc = p; p += RB;
@@ -198,33 +260,26 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
             const int Kp = pad4(N.dims[l - 1]), Np = pad4(N.dims[l]), dl = N.dims[l];
             // 2 rows x 4 columns per thread: a 16-row tile of a 128-wide layer is then one item per thread
             // (2 x 8 left half the threads idle: 21% slower on both the pushing and manipulation networks)
+            IbpSink o;
+            const size_t base = (size_t)box0 * H + t;
+            o.pre_lo = a.pre_lo + base * sumh;
+            o.pre_hi = a.pre_hi + base * sumh;
+            o.S = a.S + base * (sumh + s);
+            o.rstride_h = (size_t)H * sumh;
+            o.rstride_s = (size_t)H * (sumh + s);
+            o.hoff = l < L ? N.hoff[l] : 0;
+            o.soff = l < L ? N.hoff[l] : sumh;
+            o.dl = dl;
+            o.nrows = nlive - box0;
+            o.hidden = l < L;
             if (Np >= 64)
                 ibp_dense<2, 4>(blo[cur], bhi[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, blo[cur ^ 1],
-                                bhi[cur ^ 1], Sb);
+                                bhi[cur ^ 1], o);
             else
                 ibp_dense<1, 4>(blo[cur], bhi[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, blo[cur ^ 1],
-                                bhi[cur ^ 1], Sb);
+                                bhi[cur ^ 1], o);
             __syncthreads();
             cur ^= 1;
-            const int soff = (l < L) ? N.hoff[l] : sumh;
-            for (int i = threadIdx.x; i < RB * dl; i += NT) {
-                const int r = i / dl, c = i % dl;
-                const int box = box0 + r;
-                const float zl = blo[cur][r * ld + c], zh = bhi[cur][r * ld + c];
-                if (box < nlive) {
-                    const size_t base = ((size_t)box * H + t);
-                    a.S[base * (sumh + s) + soff + c] = Sb[r * ld + c];
-                    if (l < L) {
-                        a.pre_lo[base * sumh + N.hoff[l] + c] = zl;
-                        a.pre_hi[base * sumh + N.hoff[l] + c] = zh;
-                    }
-                }
-                if (l < L) {
-                    blo[cur][r * ld + c] = fmaxf(zl, 0.f);
-                    bhi[cur][r * ld + c] = fmaxf(zh, 0.f);
-                }
-            }
-            __syncthreads();
         }
         // x_{t+1} in [x_t] + [z_L]; interval bound of ||x_{t+1} - g||^2
         for (int r = warp; r < RB; r += NT / 32) {
@@ -862,7 +917,7 @@ static cudaError_t launch_rows_kernel(K kern_smem, K kern_glob, size_t img_bytes
 cudaError_t launch_ibp(const BoundArgs &a, int, cudaStream_t st)
 {
     const NetDesc &N = a.net;
-    size_t rest = (5 * (size_t)RB * N.maxw_p + 2 * (size_t)RB * pad4(N.s) + 5 * (size_t)RB) * sizeof(float);
+    size_t rest = (4 * (size_t)RB * N.maxw_p + 2 * (size_t)RB * pad4(N.s) + 5 * (size_t)RB) * sizeof(float);
     return launch_rows_kernel(k_ibp<true>, k_ibp<false>, (size_t)N.img_floats * 4, rest, a.n, a, st);
 }
 
