@@ -384,11 +384,11 @@ def capture_graphs(st):
     return graphs
 
 
-# DRAM bytes (read + write) per launch of the BF16x3 tensor-core rollout at 4096 boxes x 1024 samples, from one
+# DRAM bytes (read + write) per launch of the BF16 tensor-core rollout at 4096 boxes x 1024 samples, from one
 # ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel sources it
 # was taken on, so it is reported only while their digest (comments and whitespace removed) matches.
-ROLLOUT_TC_TRAFFIC = {"bytes": 1974016, "precision": "bf16x3", "boxes": 4096, "samples": 1024,
-                      "sources_sha1": "4b1f6ceb7baa12a363b0e052c5fc98c9da091491"}
+ROLLOUT_TC_TRAFFIC = {"bytes": 1609216, "precision": "bf16", "boxes": 4096, "samples": 1024,
+                      "sources_sha1": "5c88cd40796f108391ab4e3a7db11a620366f9bd"}
 ROLLOUT_TC_SOURCES = ("rollout_tc.cu", "tc_ptx.cuh", "kernels.cuh", "bab_internal.cuh")
 
 
@@ -530,15 +530,17 @@ def run_ours(args):
 
 
 def precision_lines(dev, seed, n_pick, headline, bound_precision, steps=3):
-    """The bench iteration with the rollouts in each arithmetic other than the headline's: CUDA-graph replays of
-    the same pushing-scale iteration, L2 flushed between steps, per-kernel times by CUDA events after the timed
-    region; each with its rollout roofline (FP32 against the measured FP32 FMA rate)."""
+    """The bench iteration with the rollouts in each arithmetic other than the headline's, and with the headline's
+    rollouts and the other CROWN arithmetic: CUDA-graph replays of the same pushing-scale iteration, L2 flushed
+    between steps, per-kernel times by CUDA events after the timed region; each with its rollout roofline (FP32
+    against the measured FP32 FMA rate)."""
     import torch
     out = {}
-    for prec in ("fp32", "bf16x3", "bf16"):
-        if prec == headline:
-            continue
-        st = BabState("pushing", seed, dev, n_pick, prec, bound_precision, fixed_launch=True)
+    other_bound = "fp32" if bound_precision == "bf16x3" else "bf16x3"
+    combos = [(p, bound_precision) for p in ("fp32", "bf16x3", "bf16") if p != headline] + [(headline, other_bound)]
+    for prec, bprec in combos:
+        key = prec if bprec == bound_precision else f"{prec}, {bprec} CROWN products"
+        st = BabState("pushing", seed, dev, n_pick, prec, bprec, fixed_launch=True)
         for _ in range(3):
             st.step()
             st.flush_l2()
@@ -560,10 +562,11 @@ def precision_lines(dev, seed, n_pick, headline, bound_precision, steps=3):
         torch.cuda.synchronize()
         roll = statistics.mean(e[0].elapsed_time(e[1]) for e in st.ev)
         bound = statistics.mean(e[1].elapsed_time(e[2]) for e in st.ev)
-        out[prec] = {"rollout_arithmetic": ARITH[prec], "ms_per_step": ms, "subdomain_bounds_per_s": st.nb / (ms / 1e3),
-                     "rollout_steps_per_s": st.nb * st.M * st.H / (ms / 1e3),
-                     "kernel_ms": {"rollout": roll, "bound": bound},
-                     "roofline": rollout_roofline(prec, st.p, st.nb, st.M, st.H, roll), "steps": steps}
+        out[key] = {"rollout_arithmetic": ARITH[prec], "bound_arithmetic": bprec, "ms_per_step": ms,
+                    "subdomain_bounds_per_s": st.nb / (ms / 1e3),
+                    "rollout_steps_per_s": st.nb * st.M * st.H / (ms / 1e3),
+                    "kernel_ms": {"rollout": roll, "bound": bound},
+                    "roofline": rollout_roofline(prec, st.p, st.nb, st.M, st.H, roll), "steps": steps}
         del graphs
         st.close()
     return out
@@ -1099,13 +1102,13 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
         return hist
 
     # plain: FP32 rollouts and FP32 CROWN; split: 3-term BF16 tensor-core rollouts and CROWN; alpha_split: split
-    # plus 20 Adam steps per iteration, each a tensor-core CROWN + adjoint + Adam launch; alpha_fused: 3-term BF16
-    # rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration; alpha_fused_5: the same with 5
-    # Adam steps (the bound gains most in the first steps)
+    # plus 5 Adam steps per iteration (alpha_split_20: 20), each a tensor-core CROWN + adjoint + Adam launch;
+    # alpha_fused: 3-term BF16 rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration;
+    # alpha_fused_5: the same with 5 Adam steps (the bound gains most in the first steps)
     if variants is None:
         variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
-                    "alpha_split": ("bf16x3", "bf16x3", 20), "alpha_fused": ("bf16x3", "fp32", 20),
-                    "alpha_fused_5": ("bf16x3", "fp32", 5)}
+                    "alpha_split": ("bf16x3", "bf16x3", 5), "alpha_split_20": ("bf16x3", "bf16x3", 20),
+                    "alpha_fused": ("bf16x3", "fp32", 20), "alpha_fused_5": ("bf16x3", "fp32", 5)}
     for v in variants.values():  # load every kernel and size every scratch buffer before timing
         run(*v, n_iter=2)
     plain = run(*variants["plain_fp32"], n_iter=iters)
@@ -1303,7 +1306,7 @@ def main():
     ap.add_argument("--no-precision-lines", action="store_true",
                     help="skip the same iteration with the rollouts in the other arithmetics")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="fp32",
+    ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="bf16x3",
                     help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16",
                     help="rollout arithmetic: fp32 (CUDA cores), bf16x3 (tcgen05, 3-term split), bf16 (tcgen05)")
