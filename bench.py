@@ -164,16 +164,29 @@ def rollout_roofline(precision, p, nb, M, H, roll_ms):
                              f"{pk['scalar']:.1f} and paired {pk['paired']:.1f} TFLOP/s)"}
     else:
         burst, _, kind = bf16_peaks()
-        roof = {"kernel": "k_rollout_tc (bab_rollout)", "bound": "tensor", "peak": burst,
+        fused = precision == "bf16" and len(p["dims"]) >= 4
+        roof = {"kernel": ("k_rollout_tcf" if fused else "k_rollout_tc") + " (bab_rollout)", "bound": "tensor",
+                "peak": burst,
                 "peak_note": f"of {kind} bf16 burst (MEASURED_PEAKS.json): the kernel is timed on its own with CUDA "
                              "events; achieved counts algorithmic FLOPs (2 x MACs of the network); the tensor pipe "
                              "executes " + ("3x that (3-term BF16 split)" if precision == "bf16x3" else "the same") +
-                             " plus padding to multiples of 16"}
+                             " plus padding to multiples of 16" +
+                             ("; the fused step (output layer and next first layer as one product over [a | u x], "
+                              "the bias by one more K = 16 step) executes more" if fused else "")}
     roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
     if precision != "fp32":
         dims = p["dims"]
         pad16 = lambda v: (v + 15) // 16 * 16
-        ex = sum(pad16(8 + p["s"] if l == 1 else dims[l - 1]) * pad16(dims[l]) for l in range(1, len(dims)))
+        L = len(dims) - 1
+        K = [0] + [pad16(8 + p["s"] if l == 1 else dims[l - 1]) for l in range(1, L + 1)]
+        Nn = [0] + [pad16(dims[l]) for l in range(1, L + 1)]
+        if precision == "bf16" and L >= 3:
+            # per rollout: layer 1 of step 0 once; per step layers 2 .. L-1 and the fused product, each with its
+            # bias step (K + 16)
+            per_step = sum((K[l] + 16) * Nn[l] for l in range(2, L)) + (K[L] + K[1] + 16) * (Nn[1] + Nn[L])
+            ex = per_step + ((K[1] + 16) * Nn[1]) / H
+        else:
+            ex = sum(K[l] * Nn[l] for l in range(1, L + 1))
         ratio = (3 if precision == "bf16x3" else 1) * ex / macs
         roof.update({"executed_per_algorithmic": ratio, "executed": achieved * ratio,
                      "executed_frac": achieved * ratio / roof["peak"]})
@@ -384,11 +397,12 @@ def capture_graphs(st):
     return graphs
 
 
-# DRAM bytes (read + write) per launch of the BF16 tensor-core rollout at 4096 boxes x 1024 samples, from one
-# ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel sources it
-# was taken on, so it is reported only while their digest (comments and whitespace removed) matches.
-ROLLOUT_TC_TRAFFIC = {"bytes": 1609216, "precision": "bf16", "boxes": 4096, "samples": 1024,
-                      "sources_sha1": "5c88cd40796f108391ab4e3a7db11a620366f9bd"}
+# DRAM bytes (read + write) per launch of the BF16 tensor-core rollout (the fused-step kernel) at 4096 boxes x
+# 1024 samples, from one ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
+# the kernel sources it was taken on, so it is reported only while their digest (comments and whitespace removed)
+# matches.
+ROLLOUT_TC_TRAFFIC = {"bytes": 1805056, "precision": "bf16", "boxes": 4096, "samples": 1024,
+                      "sources_sha1": "6459b409fdcd9e0a5dae32e54d241f831381503e"}
 ROLLOUT_TC_SOURCES = ("rollout_tc.cu", "tc_ptx.cuh", "kernels.cuh", "bab_internal.cuh")
 
 

@@ -567,7 +567,12 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  *                            box, per-box state in global memory (squared-
  *                            distance cost only: with the obstacle cost -1
  *                            takes the separate launches and 3 is refused).
- *   BAB_KERNEL_ROLLOUT_TC    1 or 2 sample tiles per CTA.
+ *   BAB_KERNEL_ROLLOUT_TC    1 or 2 sample tiles per CTA; BF16 rollouts with
+ *                            the image in shared memory, uniform samples and
+ *                            the squared-distance cost run the fused-step
+ *                            kernel (the output layer of step t and layer 1 of
+ *                            step t + 1 as one product); 3 or 4: 1 or 2 tiles
+ *                            per CTA, layer by layer in every case.
  *   BAB_KERNEL_CROWN_TC      3 or 4: feature-major products (the layer's
  *                            features on the MMA's 128 rows, 32 boxes on its
  *                            columns) with 8 or 16 epilogue warps; squared-

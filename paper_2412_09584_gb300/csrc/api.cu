@@ -27,7 +27,7 @@ struct bab_ctx {
     // launch variants chosen by bab_autotune (-1: built-in heuristic)
     int tune_rollout_fp32 = -1;
     int tune_alpha_fused = -1;  // -2: the unfused loop of bound, adjoint and Adam launches
-    int tune_rollout_tc = -1;   // tiles per CTA
+    int tune_rollout_tc = -1;   // tiles per CTA (3, 4: 1 or 2 without the fused step)
     int tune_crown_tc = -1;     // 3, 4 feature-major, 0 staged, 1 or 2 tiles per CTA, -1 the first that applies
     int rescore_topk = 0;       // BF16 rollouts: FP32 re-score of the topk smallest ub (0: every box)
     size_t scratch_limit = 0;   // bab_set_scratch_limit: bound calls chunk their boxes to stay within it (0: none)
@@ -53,6 +53,48 @@ float bf16_to_f32_host(uint16_t h)
     float f;
     std::memcpy(&f, &u, 4);
     return f;
+}
+
+// One BF16 element (row n, input kk) of a 128-byte swizzled K-major operand of Nr rows at byte offset base.
+void put_bf16(std::vector<uint8_t> &img, size_t base, int Nr, int n, int kk, float v)
+{
+    const int kb = kk / 64, within = kk % 64;
+    const size_t off = base + (size_t)kb * Nr * 128 + (size_t)n * 128 + (size_t)((((within * 2) / 16) ^ (n % 8)) * 16) +
+                       (size_t)((within * 2) % 16);
+    const uint16_t h = bf16_rn_host(v);
+    std::memcpy(&img[off], &h, 2);
+}
+
+// The fused step's BF16 image (see NetDesc::tc_fbase): with x_{t+1} = x_t + W_L a + b_L,
+//   z1_{t+1} = (W1x W_L) a + W1x x_t + W1u u_{t+1} + (b1 + W1x b_L),
+// rows 0 .. d_1 - 1 over the row [a | input row of layer 1], rows tc_N[1] + i the step's output W_L a (its bias
+// b_L is added in FP32 by the epilogue, as in the unfused kernel).  Products and sums in double, then BF16.
+void build_fused_image(const NetDesc &N, const float *params, std::vector<uint8_t> &img)
+{
+    const int L = N.L, s = N.s, NF = N.tc_N[1] + N.tc_N[L], kin = N.dims[L - 1], ni1 = N.dims[0], d1 = N.dims[1];
+    const float *W1 = params + N.raw_w[1], *b1 = params + N.raw_b[1];
+    const float *WL = params + N.raw_w[L], *bL = params + N.raw_b[L];
+    const size_t base = (size_t)N.tc_fbase;
+    for (int n = 0; n < d1; ++n) {
+        for (int kk = 0; kk < kin; ++kk) {
+            double c = 0.0;
+            for (int i = 0; i < s; ++i) c += (double)W1[(size_t)n * ni1 + i] * (double)WL[(size_t)i * kin + kk];
+            put_bf16(img, base, NF, n, kk, (float)c);
+        }
+        for (int kk0 = 0; kk0 < ni1; ++kk0) {
+            const int kk = kk0 < s ? kTcU + kk0 : kk0 - s;  // the input row: u_t first, then x_t
+            put_bf16(img, base, NF, n, N.tc_K[L] + kk, W1[(size_t)n * ni1 + kk0]);
+        }
+        double b = (double)b1[n];
+        for (int i = 0; i < s; ++i) b += (double)W1[(size_t)n * ni1 + i] * (double)bL[i];
+        const uint16_t bh = bf16_rn_host((float)b);
+        const uint16_t bl = bf16_rn_host((float)(b - (double)bf16_to_f32_host(bh)));
+        const size_t offb = base + (size_t)N.tc_fb + (size_t)n * 128 + (size_t)((0 ^ (n % 8)) * 16);
+        std::memcpy(&img[offb], &bh, 2);
+        std::memcpy(&img[offb + 2], &bl, 2);
+    }
+    for (int i = 0; i < s; ++i)
+        for (int kk = 0; kk < kin; ++kk) put_bf16(img, base, NF, N.tc_N[1] + i, kk, WL[(size_t)i * kin + kk]);
 }
 
 // Tensor-core layout of the network (see NetDesc) and its BF16 hi/lo image.
@@ -89,7 +131,13 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
     N.tc_dcols = dcols;
     N.tc_acols = acols;
     N.tc_ok = ok ? 1 : 0;
-    img.assign((size_t)N.tc_bytes + N.tc_bbytes, 0);
+    // the fused step's image after the bias atoms
+    const int NF = N.tc_N[1] + N.tc_N[L], KF = N.tc_K[L] + N.tc_K[1];
+    N.tc_fok = ok && L >= 3 && NF <= 256 ? 1 : 0;
+    N.tc_fbase = N.tc_bbase + N.tc_bbytes;
+    N.tc_fb = ((KF + 63) / 64) * NF * 128;
+    N.tc_fbytes = N.tc_fok ? N.tc_fb + NF * 128 : 0;
+    img.assign((size_t)N.tc_bytes + N.tc_bbytes + N.tc_fbytes, 0);
     bias.assign((size_t)bo, 0.f);
     for (int l = 1; l <= L; ++l) {
         const int no = N.dims[l], ni = N.dims[l - 1], Nl = N.tc_N[l];
@@ -124,6 +172,7 @@ void build_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img, 
             }
         }
     }
+    if (N.tc_fok) build_fused_image(N, params, img);
 }
 
 // Backward tensor-core image: B_l = W_l^T (rows n < d_{l-1}, K = d_l), BF16 hi then lo, 128-byte swizzled.
@@ -1576,7 +1625,7 @@ int bab_set_variant(bab_ctx *c, int kernel, int variant)
             c->tune_alpha_fused = variant;
             return BAB_OK;
         case BAB_KERNEL_ROLLOUT_TC:
-            if (variant != -1 && variant != 1 && variant != 2) break;
+            if (variant < -1 || variant == 0 || variant > 4) break;
             c->tune_rollout_tc = variant;
             return BAB_OK;
         case BAB_KERNEL_CROWN_TC:

@@ -50,6 +50,11 @@ struct NetDesc {
     // relative to it); the BF16 kernel copies them into shared memory right after the hi halves.
     int tc_bb[kMaxLayers + 1];
     int tc_bbase, tc_bbytes;
+    // Fused step (BF16): the output layer of step t and layer 1 of step t + 1 as one product over the row
+    // [a_{L-1} | u_{t+1} x_t] (K = tc_K[L] + tc_K[1]) with N = tc_N[1] + tc_N[L] rows: [W1x W_L | W1 (input-row
+    // layout)] for z1_{t+1}, then [W_L | 0] for the step's output; its bias atom (b1 + W1x b_L, then 0) after it.
+    // At tc_fbase in the image, tc_fbytes long (bias atom at tc_fb relative to tc_fbase); tc_fok: it applies.
+    int tc_fbase, tc_fbytes, tc_fb, tc_fok;
     int tc_boff[kMaxLayers + 1];                       // float offsets in the bias vector
     int tc_bytes, tc_bytes_hi, tc_bias_floats;
     int tc_dcols, tc_acols;                            // TMEM columns: accumulator, A operand

@@ -619,6 +619,349 @@ __global__ void __launch_bounds__((NSLOT * (kEpiWarps + 1) + (STREAM ? NSLOT : 0
     }
 }
 
+// ---------------------------------------------------------------------------------------------------------------
+// Fused-step tensor-core rollout: BF16, the image resident in shared memory, uniform samples, squared-distance cost,
+// at least two hidden layers.  With x_{t+1} = x_t + W_L a_{L-1} + b_L, the first layer of step t + 1 is
+//
+//   z1_{t+1} = (W1x W_L) a_{L-1} + W1x x_t + W1u u_{t+1} + (b1 + W1x b_L),
+//
+// so one product over the row [a_{L-1} | u_{t+1} x_t] against the fused image (NetDesc::tc_fbase) gives z1_{t+1}
+// in accumulator columns 0 .. tc_N[1] - 1 and the step's output W_L a_{L-1} in the tc_N[L] columns after them.
+// A time step is then L - 1 layer steps (layers 2 .. L-1 and the fused one) instead of L: one MMA / epilogue
+// hand-off fewer per step on each slot's chain; layer 1 of step 0 runs on its own.  Warp roles, the two slots'
+// turns, the bias MMAs and the bounded waits are those of k_rollout_tc.  The A region of a slot holds the layer
+// input in columns 0 .. tc_K[L] / 2 - 1 and the input row [u | x] after it; the constant block of the bias MMAs
+// follows the region.
+template <int NSLOT, int SX>
+__global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf(RolloutArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const NetDesc &N = a.net;
+    uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float *bias = reinterpret_cast<float *>(wimg + (size_t)a.tc_bytes);
+    float *goal_s = bias + N.tc_bias_floats;
+    float *x0_s = goal_s + SX;
+    __shared__ uint64_t bar_w, bar_a[NSLOT], bar_d[NSLOT], bar_tok[NSLOT], bar_fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mma_warp = NSLOT * kEpiWarps;
+    const int L = N.L, s = N.s, k = N.k;
+    volatile int *abort = &abort_flag;
+    const int N1 = N.tc_N[1], NF = N.tc_N[1] + N.tc_N[L], KF = N.tc_K[L] + N.tc_K[1];
+    const int Dc = N.tc_dcols > NF ? N.tc_dcols : NF, Ac = N.tc_acols > KF / 2 ? N.tc_acols : KF / 2;
+    const int slot_cols = Dc + Ac + 8;
+    const uint32_t rowc = (uint32_t)N.tc_K[L] / 2;  // TMEM column of the input row in the A region
+    const uint32_t fimg = (uint32_t)(N.tc_bytes_hi + N.tc_bbytes);  // the fused image in shared memory
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        tc::mbar_init(&bar_w, 1);
+        tc::mbar_init(&bar_fin, 1);
+        for (int i = 0; i < NSLOT; ++i) {
+            tc::mbar_init(&bar_a[i], kEpiWarps);
+            tc::mbar_init(&bar_d[i], 1);
+            tc::mbar_init(&bar_tok[i], 1);
+        }
+        tc::mbar_init_fence();
+    }
+    if (warp == mma_warp) tc::tmem_alloc(&tmem_base, a.tmem_cols);
+    for (int i = threadIdx.x; i < N.tc_bias_floats; i += blockDim.x) bias[i] = a.tc_bias[i];
+    for (int i = threadIdx.x; i < SX; i += blockDim.x) {
+        goal_s[i] = i < s ? a.goal[i] : 0.f;
+        x0_s[i] = i < s ? a.x0[i] : 0.f;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == mma_warp * 32) {
+        // the hi halves, the hidden layers' bias atoms, the fused image: three ranges, 32 KB copies
+        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)a.tc_bytes);
+        constexpr uint32_t kChunk = 32768;
+        const uint32_t src[3] = {0u, (uint32_t)N.tc_bbase, (uint32_t)N.tc_fbase};
+        const uint32_t len[3] = {(uint32_t)N.tc_bytes_hi, (uint32_t)N.tc_bbytes, (uint32_t)N.tc_fbytes};
+        uint32_t dst = 0;
+        for (int r = 0; r < 3; ++r) {
+            for (uint32_t off = 0; off < len[r]; off += kChunk)
+                tc::bulk_g2s(wimg + dst + off, a.tc_img + src[r] + off, min(kChunk, len[r] - off), &bar_w);
+            dst += len[r];
+        }
+    }
+    if (warp < mma_warp + NSLOT && !warp_wait(&bar_w, 0, abort) && lane == 0) raise_abort(a.status, abort);
+
+    const int nlive = live_count(a.n, a.d_n);
+    const int bpt = a.M >= 128 ? 1 : 128 / a.M;
+    const int tpb = a.M >= 128 ? (a.M + 127) / 128 : 1;
+    const long long ntiles = bpt > 1 ? ((long long)nlive + bpt - 1) / bpt : (long long)nlive * tpb;
+    const long long G = (long long)gridDim.x * NSLOT;
+    const uint32_t tb = tmem_base;
+
+    if (warp < mma_warp) {
+        // ------------------------------- epilogue -------------------------------
+        const int slot = warp / kEpiWarps, qw = warp % kEpiWarps, quad = qw & 3;
+        const bool primary = qw < 4;
+        const int r = 32 * quad + lane;
+        const uint32_t dcol = tb + ((uint32_t)(32 * quad) << 16) + slot * slot_cols;
+        const uint32_t acol = dcol + Dc;
+        const int K1 = N.tc_K[1];
+        uint32_t phD = 0;
+        if (primary) {
+            // the constant A block of the bias MMAs, once per slot (ordered before every MMA by the first arrive)
+            const uint32_t ones[8] = {0x3F803F80u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            tc::tmem_st8(acol + Ac, ones);
+            tc::tmem_wait_st();
+        }
+        // ReLU and BF16 conversion of accumulator columns [c_beg, c_end) (the bias came in by its MMA) into the A
+        // region, 16 columns per TMEM round trip
+        auto hidden = [&](int Nl) {
+            const bool split_cols = (Nl % 64 == 0);
+            int c_beg = 0, c_end = Nl;
+            if (split_cols) {
+                c_beg = primary ? 0 : Nl / 2;
+                c_end = c_beg + Nl / 2;
+            } else if (!primary) {
+                c_end = 0;
+            }
+            for (int c0 = c_beg; c0 < c_end; c0 += 16) {
+                uint32_t v[16];
+                tc::tmem_ld16(dcol + c0, v);
+                tc::tmem_wait_ld();
+                uint32_t ph[8], pl[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    relu_split2<1>(make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])), ph[q], pl[q]);
+                tc::tmem_st8(acol + c0 / 2, ph);
+            }
+        };
+        auto handoff = [&]() {
+            tc::tmem_wait_st();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_a[slot]);
+        };
+        auto wait_d = [&]() -> bool {
+            if (!warp_wait(&bar_d[slot], phD, abort)) {
+                if (lane == 0) raise_abort(a.status, abort);
+                return false;
+            }
+            phD ^= 1;
+            tc::fence_after_sync();
+            return true;
+        };
+        for (long long tile = blockIdx.x * NSLOT + slot; tile < ntiles && !*abort; tile += G) {
+            int box, m;
+            bool lane_ok;
+            if (bpt > 1) {
+                box = (int)(tile * bpt) + r / a.M;
+                m = r % a.M;
+                lane_ok = r < bpt * a.M && box < nlive;
+                if (!lane_ok) box = (int)(tile * bpt);  // an idle lane computes on a valid box, result unused
+            } else {
+                box = (int)(tile / tpb);
+                m = (int)(tile % tpb) * 128 + r;
+                lane_ok = m < a.M;
+            }
+            const uint64_t hb = box_hash(a.seed, a.id[box]);
+            const float *blo = a.lo + (size_t)box * a.d, *bhi = a.hi + (size_t)box * a.d;
+            const int Hb = a.H;
+            const float rho = a.rho;
+            float x[SX], u[kTcU];
+#pragma unroll
+            for (int i = 0; i < SX; ++i) x[i] = i < s ? x0_s[i] : 0.f;
+            auto draw_step = [&](int t) {
+#pragma unroll
+                for (int j = 0; j < kTcU; ++j) {
+                    const int jj = t * k + j;
+                    u[j] = j < k ? draw_sample(hb, (uint32_t)m, (uint32_t)jj, __ldg(blo + jj), __ldg(bhi + jj)) : 0.f;
+                }
+            };
+            // the input row [u | x | 0] (u zero: the row of the last step feeds no further step)
+            auto write_row = [&](bool with_u) {
+#pragma unroll
+                for (int c16 = 0; c16 < 4; ++c16) {
+                    if (c16 * 16 >= K1) break;
+                    uint32_t ph[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float v2[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int i = c16 * 16 + 2 * q + e;
+                            v2[e] = i < kTcU ? (with_u ? u[i] : 0.f) : (i - kTcU < SX ? x[i - kTcU] : 0.f);
+                        }
+                        ph[q] = pack_bf16x2(v2[0], v2[1]);
+                    }
+                    tc::tmem_st8(acol + rowc + c16 * 8, ph);
+                }
+            };
+            auto rho_term = [&](float &c) {
+#pragma unroll
+                for (int j = 0; j < kTcU; ++j)
+                    if (j < k) c = fmaf(rho * u[j], u[j], c);
+            };
+            float cost = 0.f;
+            bool ok = Hb > 0;
+            if (primary && ok) {
+                draw_step(0);
+                rho_term(cost);
+                write_row(true);
+            }
+            if (ok) handoff();  // layer 1 of step 0 may start
+            // z1_0
+            if (ok && (ok = wait_d())) {
+                hidden(N1);
+                handoff();
+            }
+            for (int t = 0; t < Hb && ok; ++t) {
+                const bool more = t + 1 < Hb;
+                if (primary && more) draw_step(t + 1);  // the next step's actions, drawn while layer 2 runs
+                for (int l = 2; l <= L - 1 && ok; ++l) {
+                    if (!(ok = wait_d())) break;
+                    hidden(N.tc_N[l]);
+                    if (l == L - 1 && primary) write_row(more);  // the fused product's input row [u_{t+1} | x_t]
+                    handoff();
+                }
+                if (!ok || !(ok = wait_d())) break;
+                // the fused product: the step's output (residual and cost), then z1_{t+1}
+                if (primary) {
+                    float dx[SX];
+                    if (SX <= 8) {
+                        uint32_t v[8];
+                        tc::tmem_ld8(dcol + N1, v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < SX; ++i) dx[i] = __uint_as_float(v[i % 8]);
+                    } else if (SX <= 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(dcol + N1, v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < SX; ++i) dx[i] = __uint_as_float(v[i % 16]);
+                    } else {
+                        uint32_t v[32];
+                        tc::tmem_ld32(dcol + N1, v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < SX; ++i) dx[i] = __uint_as_float(v[i % 32]);
+                    }
+                    const float *bl = bias + N.tc_boff[L];
+                    float c = 0.f;
+#pragma unroll
+                    for (int i = 0; i < SX; ++i) {
+                        if (i < s) {
+                            x[i] = x[i] + (dx[i] + bl[i]);
+                            const float e = x[i] - goal_s[i];
+                            c = fmaf(e, e, c);
+                        }
+                    }
+                    cost += c;
+                    if (more) rho_term(cost);
+                }
+                if (more) {
+                    hidden(N1);
+                    handoff();
+                }
+            }
+            if (!ok) break;
+            if (primary) {
+                if (a.costs && lane_ok) a.costs[(size_t)box * a.M + m] = cost;
+                const unsigned long long key =
+                    lane_ok ? (((unsigned long long)float_order(cost) << 32) | (unsigned)m) : ~0ull;
+                if (bpt > 1) {
+                    if (lane_ok) atomicMin(&a.keys[box], key);
+                } else {
+                    unsigned long long kb = key;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, kb, o);
+                        kb = other < kb ? other : kb;
+                    }
+                    if (lane == 0 && kb != ~0ull) atomicMin(&a.keys[box], kb);
+                }
+            }
+        }
+    } else if (warp < mma_warp + NSLOT && lane == 0) {
+        // ---------------------- MMA issuer of slot (warp - mma_warp) ----------------------
+        // per tile: layer 1 of step 0 (phase 0), then per step layers 2 .. L-1 and the fused product
+        const int sl = warp - mma_warp;
+        const long long gi = (long long)blockIdx.x * NSLOT + sl;
+        const long long per_tile = a.H > 0 ? 1 + (long long)a.H * (L - 1) : 0;
+        long long left = gi < ntiles ? ((ntiles - 1 - gi) / G + 1) * per_tile : 0;
+        long long n_other = 0;
+        if (NSLOT == 2) {
+            const long long go = (long long)blockIdx.x * NSLOT + (1 - sl);
+            n_other = go < ntiles ? ((ntiles - 1 - go) / G + 1) * per_tile : 0;
+        }
+        uint32_t phA = 0, ncommit = 0;
+        int ph = 0;  // phase within the tile: 0 layer 1; then 1 .. L-2 layers 2 .. L-1; L-1 the fused product
+        const uint32_t dcol = tb + sl * slot_cols;
+        const uint32_t acol = dcol + Dc, ones = acol + Ac;
+        while (left > 0 && !*abort) {
+            if (!tc::mbar_wait(&bar_a[sl], phA, abort, kWaitLimitNs)) {
+                raise_abort(a.status, abort);
+                break;
+            }
+            phA ^= 1;
+            if (NSLOT == 2) {
+                const long long i = ncommit;
+                bool w = true;
+                if (sl == 0 && i >= 1 && i - 1 < n_other)
+                    w = tc::mbar_wait(&bar_tok[1], (uint32_t)((i - 1) & 1), abort, kWaitLimitNs);
+                else if (sl == 1 && i < n_other)
+                    w = tc::mbar_wait(&bar_tok[0], (uint32_t)(i & 1), abort, kWaitLimitNs);
+                if (!w) {
+                    raise_abort(a.status, abort);
+                    break;
+                }
+            }
+            tc::fence_after_sync();
+            const bool fused = ph == L - 1;
+            const int l = fused ? 0 : ph + 1;
+            const int Kl = fused ? KF : N.tc_K[l], Nl = fused ? NF : N.tc_N[l];
+            const uint32_t boff = fused ? fimg : (uint32_t)N.tc_hi[l];
+            const uint32_t bboff = fused ? fimg + (uint32_t)N.tc_fb : (uint32_t)(N.tc_bytes_hi + N.tc_bb[l]);
+            const uint32_t a0 = ph == 0 ? acol + rowc : acol;  // layer 1 of step 0 reads the input row
+            const uint32_t idesc = tc::idesc_bf16_f32(128, Nl);
+            const int nks = Kl / 16, kpass = (3 * nks + 3) / 4;
+            const uint32_t atom = (uint32_t)Nl * 8u;
+            uint32_t q = tc::desc_sw128_lo(tc::smem_u32(wimg + boff));
+            bool passed = false;
+            for (int ks0 = 0; ks0 < nks; ks0 += 4, q += atom) {
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    if (ks0 + kk >= nks) break;
+                    tc::mma_ts(dcol, a0 + 8u * (ks0 + kk), tc::desc_join(q + 2u * kk), idesc, ks0 + kk > 0 ? 1u : 0u);
+                    if (NSLOT == 2 && ks0 + kk + 1 == kpass) {
+                        tc::mbar_arrive(&bar_tok[sl]);
+                        passed = true;
+                    }
+                }
+            }
+            // the bias: the constant block [1, 1, 0, ...] against the bias atom
+            tc::mma_ts(dcol, ones, tc::desc_join(tc::desc_sw128_lo(tc::smem_u32(wimg + bboff))), idesc, 1u);
+            tc::mma_commit(&bar_d[sl]);
+            if (NSLOT == 2 && !passed) tc::mbar_arrive(&bar_tok[sl]);
+            ++ncommit;
+            --left;
+            // next phase: after the fused product the step's layers 2 .. again (phase 1), a new tile after its last
+            ph = ph == L - 1 ? 1 : ph + 1;
+            if (per_tile > 0 && (ncommit % per_tile) == 0) ph = 0;
+        }
+        if (*abort) {
+            volatile int never = 0;
+            tc::mma_commit(&bar_fin);
+            tc::mbar_wait(&bar_fin, 0, &never, kWaitLimitNs);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == mma_warp) {
+        __syncwarp();
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tb, a.tmem_cols);
+    }
+}
+
 // BF16 mode: the threshold (order(ub), id) of the topk smallest BF16 upper bounds.
 __global__ void __launch_bounds__(1024) k_topk_select(RolloutArgs a)
 {
@@ -864,7 +1207,27 @@ static cudaError_t launch_tc_shape(const RolloutArgs &a, int nslot, bool stream,
                       : launch_tc_variant<1, SPLIT, SX, false, CEM, OBST>(a, grid, smem, st);
 }
 
-// nslot_pref: tiles per CTA (1 or 2), or -1 for two whenever both fit in tensor memory
+// The fused-step kernel (k_rollout_tcf): its image in shared memory, and the tensor-memory columns of one slot.
+static size_t rollout_tcf_bytes(const NetDesc &N) { return (size_t)N.tc_bytes_hi + N.tc_bbytes + N.tc_fbytes; }
+static int rollout_tcf_slot_cols(const NetDesc &N)
+{
+    const int NF = N.tc_N[1] + N.tc_N[N.L], KF = N.tc_K[N.L] + N.tc_K[1];
+    return (N.tc_dcols > NF ? N.tc_dcols : NF) + (N.tc_acols > KF / 2 ? N.tc_acols : KF / 2) + 8;
+}
+
+template <int NSLOT, int SX>
+static cudaError_t launch_tcf_variant(const RolloutArgs &a, int grid, size_t smem, cudaStream_t st)
+{
+    auto kern = k_rollout_tcf<NSLOT, SX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NSLOT * (kEpiWarps + 1) * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// nslot_pref: 1 or 2 tiles per CTA, or -1 for two whenever both fit in tensor memory; the fused-step kernel where
+// it applies (BF16, resident image, uniform samples, squared-distance cost), else layer by layer; 3 or 4: layer
+// by layer with 1 or 2 tiles per CTA
 cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_sms, cudaStream_t st)
 {
     const NetDesc &N = a.net;
@@ -872,9 +1235,41 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     int dev, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const long long ntiles_all =
+        a.M >= 128 ? (long long)a.n * ((a.M + 127) / 128) : ((long long)a.n + 128 / a.M - 1) / (128 / a.M);
+    const bool fuse = split == 1 && a.batch.P <= 1 && a.cost.kind == 0 && !a.cem_mu && N.tc_fok &&
+                      rollout_tcf_bytes(N) + rollout_tc_extra(N) + 1024 <= (size_t)max_smem &&
+                      nslot_pref != 3 && nslot_pref != 4;
+    if (fuse) {
+        const int slot_cols = rollout_tcf_slot_cols(N);
+        int nslot = nslot_pref == 1 || 2 * slot_cols > 512 ? 1 : 2;
+        int cols = 32;
+        while (cols < nslot * slot_cols) cols *= 2;
+        if (cols > 512) return cudaErrorInvalidConfiguration;
+        a.tmem_cols = (uint32_t)cols;
+        a.tc_bytes = (int)rollout_tcf_bytes(N);
+        a.stages = 0;
+        const size_t smem = (size_t)a.tc_bytes + rollout_tc_extra(N);
+        int grid = (int)((ntiles_all + nslot - 1) / nslot);
+        grid = grid < num_sms ? grid : num_sms;
+        k_fill_keys(a.keys, a.n, st);
+        cudaError_t e;
+        if (N.s <= 8) e = nslot == 2 ? launch_tcf_variant<2, 8>(a, grid, smem, st) : launch_tcf_variant<1, 8>(a, grid, smem, st);
+        else if (N.s <= 16)
+            e = nslot == 2 ? launch_tcf_variant<2, 16>(a, grid, smem, st) : launch_tcf_variant<1, 16>(a, grid, smem, st);
+        else e = nslot == 2 ? launch_tcf_variant<2, 32>(a, grid, smem, st) : launch_tcf_variant<1, 32>(a, grid, smem, st);
+        if (e != cudaSuccess) return e;
+        launch_rollout_finalize(a, st);
+        if (a.topk > 0) k_topk_select<<<1, 1024, 0, st>>>(a);
+        e = launch_rescore(a, st);
+        if (e != cudaSuccess) return e;
+        if (a.inc_val) launch_incumbent(a, st);
+        return cudaGetLastError();
+    }
+    if (nslot_pref == 3 || nslot_pref == 4) nslot_pref -= 2;
     // several problems: every tile streams its own problem's image
     const bool stream = a.batch.P > 1 || !rollout_tc_resident(N, split, max_smem);
-    a.tc_img_stride = (size_t)N.tc_bytes + N.tc_bbytes;  // one problem's whole image
+    a.tc_img_stride = (size_t)N.tc_bytes + N.tc_bbytes + N.tc_fbytes;  // one problem's whole image
     // tensor memory: per slot the accumulator (widest layer) and the A operand(s) (widest input, 2 BF16 per column)
     // (plus, BF16 resident, the 8 columns of the bias MMAs' constant block)
     const int slot_cols = N.tc_dcols + (split == 3 ? 2 : 1) * N.tc_acols + (split == 1 && !stream ? 8 : 0);

@@ -47,7 +47,8 @@ def _rows(bt, seed, counts):
 @pytest.mark.parametrize("prec_name,M", [("fp32", 64), ("bf16x3", 200), ("bf16", 130)])
 def test_batch_rollout_matches_single_and_oracle(oracle, prec_name, M):
     """FP32 on CUDA cores, or tensor cores with each tile streaming its own problem's weights: every row equals
-    the single-problem call on its problem bit for bit."""
+    the single-problem call on its problem bit for bit (the single-problem BF16 call taken layer by layer, as the
+    batched kernel runs; its default fused-step kernel is compared with it in test_gpu_variants)."""
     from gpu_util import DEV, GpuProblem, T, ids_t
     bt = Batch()
     B = bt.B
@@ -69,6 +70,7 @@ def test_batch_rollout_matches_single_and_oracle(oracle, prec_name, M):
             dp = bt.dp(p)
             g = GpuProblem(bt.probs[p])
             try:
+                B.bab_set_variant(g.ctx, B.KERNEL_ROLLOUT_TC, 4)  # two tiles per CTA, layer by layer
                 r = g.rollout(lo[rows, :dp], hi[rows, :dp], ids[rows], M=M, seed=seed, precision=prec)
             finally:
                 g.close()

@@ -55,6 +55,44 @@ def test_rollout_tc_slots_bit_identical():
         g.close()
 
 
+@pytest.mark.parametrize("name,M", [("pushing", 256), ("tiny", 256), ("pushing", 40)])
+def test_rollout_fused_step_bf16(oracle, name, M):
+    """BF16 rollouts with the output layer of each step and the first layer of the next as one product (the
+    default where it applies) against the layer-by-layer kernel: one and two tiles per CTA bit-identical in each;
+    every sample's BF16 cost within 1e-4 of its FP64 objective and of the layer-by-layer cost (both measured
+    below 1e-5), and each box's pick re-scored to its FP32 objective."""
+    from gpu_util import DEV, T, ids_t
+    from paper_2412_09584_gb300 import binding as B
+    p, lo, hi, ids, g = _problem(name, 6)
+    n, d, seed = lo.shape[0], g.d, 9
+    try:
+        out = {}
+        for v in (1, 2, 3, 4):
+            B.bab_set_variant(g.ctx, B.KERNEL_ROLLOUT_TC, v)
+            ub = torch.empty(n, device=DEV)
+            bu = torch.empty(n, d, device=DEV)
+            sd = torch.empty(n, dtype=torch.int32, device=DEV)
+            costs = torch.empty(n, M, device=DEV)
+            B.bab_rollout_split(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), ids_t(ids), n, M, seed, B.PREC_BF16,
+                                1.0, ub, sd, best_u=bu, costs=costs)
+            torch.cuda.synchronize()
+            out[v] = (costs.cpu().numpy(), ub.cpu().numpy(), bu.cpu().numpy())
+        assert B.bab_status(g.ctx) == 0
+        for a_, b_ in ((1, 2), (3, 4)):
+            for x, y in zip(out[a_], out[b_]):
+                assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+        cf, ubf, buf = out[2]
+        cl = out[4][0]
+        np.testing.assert_allclose(cf, cl, rtol=1e-4, atol=0)
+        for i in range(n):
+            for m in range(0, M, max(1, M // 8)):
+                u = np.array([oracle.sample(seed, int(ids[i]), m, j, float(lo[i, j]), float(hi[i, j])) for j in range(d)])
+                assert cf[i, m] == pytest.approx(oracle.objective(p, u), rel=1e-4)
+            assert ubf[i] == pytest.approx(oracle.objective(p, buf[i].astype(np.float64)), rel=1e-5)
+    finally:
+        g.close()
+
+
 @pytest.mark.parametrize("name,n,with_alpha", [("tiny", 300, False), ("pushing", 300, False), ("pushing", 211, True),
                                                 ("pushing", 5000, False)])
 def test_crown_tc_variants_bit_identical(name, n, with_alpha):
@@ -189,7 +227,7 @@ def test_autotune_keeps_results(oracle):
         before = g.rollout(lo, hi, ids, M=256, seed=5)
         B.bab_autotune(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), ids_t(ids), lo.shape[0], 256, alpha_steps=4)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_FP32) in (0, 1, 2)
-        assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_TC) in (1, 2)
+        assert B.bab_get_variant(g.ctx, B.KERNEL_ROLLOUT_TC) in (1, 2)  # the autotuner keeps the fused step
         assert B.bab_get_variant(g.ctx, B.KERNEL_CROWN_TC) in (0, 1, 2, 3, 4)
         assert B.bab_get_variant(g.ctx, B.KERNEL_ALPHA_FUSED) in (-2, 0, 1, 2, 3)
         after = g.rollout(lo, hi, ids, M=256, seed=5)
