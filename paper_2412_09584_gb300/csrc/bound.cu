@@ -272,11 +272,15 @@ __global__ void __launch_bounds__(NT) k_ibp(BoundArgs a)
             o.dl = dl;
             o.nrows = nlive - box0;
             o.hidden = l < L;
+            // (an output layer of 8 or 16 columns: 1 x 2 tiles, twice the threads of 1 x 4 on its K-long sums)
             if (Np >= 64)
                 ibp_dense<2, 4>(blo[cur], bhi[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, blo[cur ^ 1],
                                 bhi[cur ^ 1], o);
-            else
+            else if (Np >= 32)
                 ibp_dense<1, 4>(blo[cur], bhi[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, blo[cur ^ 1],
+                                bhi[cur ^ 1], o);
+            else
+                ibp_dense<1, 2>(blo[cur], bhi[cur], ld, img + N.fwd_w[l], img + N.fwd_b[l], Kp, Np, blo[cur ^ 1],
                                 bhi[cur ^ 1], o);
             __syncthreads();
             cur ^= 1;

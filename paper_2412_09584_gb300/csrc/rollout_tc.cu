@@ -1051,10 +1051,13 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
 // at once (one row per box: its chosen sample), the layers as register-blocked FP32 products over the tile with
 // the network image in shared memory (WSMEM) or read through L1, so that each weight read serves RR boxes.
 constexpr int kRescoreRows = 28;  // 4096 boxes make 147 CTAs: one wave on 152 SMs
+// 512 threads: a 128-wide layer of the tile is 448 register tiles of 2 rows x 4 columns, one per thread (256
+// threads took two each, 0.49 ms for 4096 boxes)
+constexpr int kRescoreThreads = 512;
 template <bool WSMEM>
-__global__ void __launch_bounds__(256) k_rescore_rows(RolloutArgs a)
+__global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
 {
-    constexpr int RR = kRescoreRows, NT = 256;
+    constexpr int RR = kRescoreRows, NT = kRescoreThreads;
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const NetDesc &N = a.net;
@@ -1151,7 +1154,7 @@ static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
     auto kern = wsmem ? k_rescore_rows<true> : k_rescore_rows<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(a.n + kRescoreRows - 1) / kRescoreRows, 256, smem, st>>>(a);
+    kern<<<(a.n + kRescoreRows - 1) / kRescoreRows, kRescoreThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
