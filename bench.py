@@ -674,6 +674,15 @@ def manip_scale(dev, reps=3):
     t_tc = timed(lambda: B.bab_bound_crown(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb, precision=B.PREC_BF16X3))
     t_32 = timed(lambda: B.bab_bound_crown(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb32))
     sound = bool((lb <= ub).all().item())
+    # the interval bounds on tensor cores (3-term BF16 split with a computed margin: sound, wider)
+    lb_f = lb.clone()
+    B.bab_set_interval_precision(ctx, B.PREC_BF16X3)
+    t_ibp_tc = timed(lambda: B.bab_bound_ibp(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb32))
+    t_tc_tc = timed(lambda: B.bab_bound_crown(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb, precision=B.PREC_BF16X3))
+    sound = sound and bool((lb <= ub).all().item())
+    # how much of the bound the wider intervals give up, relative to the bound's magnitude (median over boxes)
+    loss = float(((lb_f - lb).abs() / lb_f.abs().clamp_min(1.0)).median().item())
+    B.bab_set_interval_precision(ctx, B.PREC_FP32)
     B.bab_destroy(ctx)
     macs = sum(a * b for a, b in zip(p["dims"][1:], p["dims"][:-1]))
     bwd_flop = 2.0 * macs * H * n  # algorithmic backward products of one CROWN call (the pipe runs 3x for the split)
@@ -684,8 +693,13 @@ def manip_scale(dev, reps=3):
             "bound_bf16x3_ms": t_tc, "bound_fp32_ms": t_32,
             "subdomain_bounds_per_s_bf16x3": n / (t_tc / 1e3), "subdomain_bounds_per_s_fp32": n / (t_32 / 1e3),
             "crown_backward_tflops_bf16x3": bwd_flop / ((t_tc - t_ibp) / 1e3) / 1e12,
+            "ibp_tensor_core_ms": t_ibp_tc, "bound_bf16x3_tc_intervals_ms": t_tc_tc,
+            "subdomain_bounds_per_s_tc_intervals": n / (t_tc_tc / 1e3),
+            "tc_intervals_bound_loss_median": loss,
             "note": "bound times include the interval bounds (ibp_ms); backward TFLOP/s = algorithmic 2 x MACs x H x "
-                    "boxes over (bound - ibp) time; weights streamed through shared memory (they exceed it)",
+                    "boxes over (bound - ibp) time; weights streamed through shared memory (they exceed it); "
+                    "tc_intervals: the interval bounds on tensor cores (3-term BF16 split, computed margin), the "
+                    "bound's median loss against FP32 intervals relative to its magnitude",
             "bounds_below_sampled_ub": sound}
 
 

@@ -620,6 +620,23 @@ int bab_set_rescore_topk(bab_ctx *ctx, int k);
  */
 int bab_set_scratch_limit(bab_ctx *ctx, size_t bytes);
 
+/*
+ * Arithmetic of the interval bounds (IBP, the intermediate bounds that Lemma 1
+ * of Appendix B.1 relaxes) of every later bound call on this context.
+ * BAB_PREC_FP32 (the default): FP32 sums with directed rounding, each input's
+ * endpoint picked by the weight's sign.  BAB_PREC_BF16X3: on the tensor cores,
+ * each layer's input in centre-radius form, W c and |W| r as 3-term BF16 split
+ * products and |W| (|c| + r) as one BF16 product, the intervals widened by
+ * gamma_split(K) |W| (|c| + r) (about 5e-5 of it): sound, and containing the
+ * exact interval bounds, but wider than the FP32 ones by that margin per layer.
+ * The weights are streamed through shared memory, so the network need not fit
+ * there.  Squared-distance cost only (other costs keep the FP32 intervals).
+ * No counterpart in the paper beyond Lemma 1's input.
+ * Errors: BAB_ERR_INVALID_ARG (unknown precision), BAB_ERR_UNSUPPORTED
+ * (BF16X3 with a batch of several problems, or a width above 256).
+ */
+int bab_set_interval_precision(bab_ctx *ctx, int precision);
+
 #define BAB_KERNEL_ROLLOUT_FP32 0
 #define BAB_KERNEL_ALPHA_FUSED 1
 #define BAB_KERNEL_ROLLOUT_TC 2

@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
     L.bab_bound_crown_static.argtypes = [_I, ctypes.POINTER(_I), _P, _I, _I, _P, _P, _I, _F, _P, _P, _I, _P, _P, _P]
     L.bab_probe_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P]
     L.bab_set_scratch_limit.argtypes = [_P, ctypes.c_size_t]
+    L.bab_set_interval_precision.argtypes = [_P, ctypes.c_int]
     L.bab_load_dynamics_batch.argtypes = [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_F), _I,
                                           _I, ctypes.c_uint]
     L.bab_rollout_batch.argtypes = [_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _P, _I, _P, _I, ctypes.c_uint64, _I, _P,
@@ -261,6 +262,10 @@ def bab_set_variant(ctx, kernel, variant):
 
 def bab_set_scratch_limit(ctx, nbytes):
     _check(ctx, load().bab_set_scratch_limit(ctx, ctypes.c_size_t(int(nbytes))))
+
+
+def bab_set_interval_precision(ctx, precision):
+    _check(ctx, load().bab_set_interval_precision(ctx, int(precision)))
 
 
 def bab_set_rescore_topk(ctx, k):

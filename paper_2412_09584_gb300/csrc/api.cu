@@ -20,6 +20,8 @@ struct bab_ctx {
     NetDesc net{};
     float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
     uint8_t *d_tc = nullptr, *d_tcb = nullptr;
+    uint8_t *d_ibp = nullptr;   // the tensor-core interval image (problem 0)
+    int interval_precision = 0; // bab_set_interval_precision: BAB_PREC_FP32 (0) or BAB_PREC_BF16X3
     float *d_tc_bias = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -95,6 +97,44 @@ void build_fused_image(const NetDesc &N, const float *params, std::vector<uint8_
     }
     for (int i = 0; i < s; ++i)
         for (int kk = 0; kk < kin; ++kk) put_bf16(img, base, NF, N.tc_N[1] + i, kk, WL[(size_t)i * kin + kk]);
+}
+
+// The tensor-core interval image (see NetDesc::ibp_off): W_l as the A operand of the feature-major products
+// (rows = the layer's outputs, K = its inputs in the network's own order), BF16 hi and lo halves of W and |W|.
+void build_ibp_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &img)
+{
+    const int L = N.L;
+    bool ok = N.tc_ok && N.s <= 32 && N.dims[0] <= 128;  // the state boxes and the first layer's inputs: one block
+    for (int l = 0; l <= L; ++l) ok = ok && N.dims[l] <= 256;
+    int off = 0;
+    for (int l = 1; l <= L; ++l) {
+        N.ibp_mb[l] = (N.dims[l] + 127) / 128;
+        N.ibp_ka[l] = (pad16(N.dims[l - 1]) + 63) / 64;
+        N.ibp_off[l] = off;
+        off += N.ibp_mb[l] * N.ibp_ka[l] * 65536;
+        N.gam_ibp[l] = gamma_split(pad16(N.dims[l - 1]));
+    }
+    N.ibp_ok = ok ? 1 : 0;
+    N.ibp_bytes = ok ? off : 0;
+    img.assign((size_t)N.ibp_bytes, 0);
+    if (!ok) return;
+    for (int l = 1; l <= L; ++l) {
+        const int no = N.dims[l], ni = N.dims[l - 1];
+        const float *W = params + N.raw_w[l];
+        for (int n = 0; n < no; ++n)
+            for (int kk = 0; kk < ni; ++kk) {
+                const float w = W[(size_t)n * ni + kk], a = std::fabs(w);
+                const int mb = n / 128, row = n % 128, ka = kk / 64, within = kk % 64;
+                const size_t stage = (size_t)N.ibp_off[l] + ((size_t)mb * N.ibp_ka[l] + ka) * 65536;
+                const size_t o = (size_t)row * 128 + (size_t)((((within * 2) / 16) ^ (row % 8)) * 16) + (size_t)((within * 2) % 16);
+                const uint16_t wh = bf16_rn_host(w), wl = bf16_rn_host(w - bf16_to_f32_host(wh));
+                const uint16_t ah = bf16_rn_host(a), al = bf16_rn_host(a - bf16_to_f32_host(ah));
+                std::memcpy(&img[stage + o], &wh, 2);
+                std::memcpy(&img[stage + 16384 + o], &wl, 2);
+                std::memcpy(&img[stage + 32768 + o], &ah, 2);
+                std::memcpy(&img[stage + 49152 + o], &al, 2);
+            }
+    }
 }
 
 // Tensor-core layout of the network (see NetDesc) and its BF16 hi/lo image.
@@ -349,7 +389,9 @@ int run_ibp(bab_ctx *c, BoundArgs &a, Carver &cv, float *pre_lo, float *pre_hi, 
     a.x_hi = x_hi ? x_hi : cv.take<float>(nx);
     a.S = cv.take<float>((size_t)a.n * a.H * (N.sumh + N.s));
     a.lb_ibp = lb_ibp;
-    cudaError_t e = launch_ibp(a, c->num_sms, st);
+    a.ibp_img = c->d_ibp;
+    const bool tc = c->interval_precision == BAB_PREC_BF16X3 && a.batch.P <= 1 && a.cost.kind == 0;
+    cudaError_t e = tc ? launch_ibp_tc(a, c->num_sms, st) : launch_ibp(a, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "interval bounds kernel");
     return BAB_OK;
 }
@@ -439,14 +481,18 @@ int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *
         tc_img.insert(tc_img.end(), im.begin(), im.end());
         tc_bias.insert(tc_bias.end(), bi.begin(), bi.end());
     }
-    std::vector<uint8_t> tcb_img;
+    std::vector<uint8_t> tcb_img, ibp_img;
     build_tcb_image(N, params, tcb_img);
+    build_ibp_tc_image(N, params, ibp_img);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tc, tc_img.size());
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tcb, tcb_img.size());
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tcb, tcb_img.data(), tcb_img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ibp_img.empty()) e = cudaMalloc(&c->d_ibp, ibp_img.size());
+    if (e == cudaSuccess && !ibp_img.empty())
+        e = cudaMemcpy(c->d_ibp, ibp_img.data(), ibp_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_bias, sizeof(float) * tc_bias.size());
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tc, tc_img.data(), tc_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -626,6 +672,7 @@ int bab_destroy(bab_ctx *c)
     cudaFree(c->d_bwd);
     cudaFree(c->d_tc);
     cudaFree(c->d_tcb);
+    cudaFree(c->d_ibp);
     cudaFree(c->d_tc_bias);
     cudaFree(c->scratch);
     cudaFree(c->d_status);
@@ -1636,6 +1683,21 @@ int bab_set_variant(bab_ctx *c, int kernel, int variant)
             return fail(c, BAB_ERR_INVALID_ARG, "unknown kernel %d", kernel);
     }
     return fail(c, BAB_ERR_INVALID_ARG, "variant %d out of range for kernel %d", variant, kernel);
+}
+
+int bab_set_interval_precision(bab_ctx *c, int precision)
+{
+    if (!c) return BAB_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (precision == BAB_PREC_FP32) {
+        c->interval_precision = precision;
+        return BAB_OK;
+    }
+    if (precision != BAB_PREC_BF16X3) return fail(c, BAB_ERR_INVALID_ARG, "interval precision %d unknown", precision);
+    if (c->n_problems > 1 || !ibp_tc_supported(c->net, c->max_smem))
+        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core interval bounds need one network with every width at most 256");
+    c->interval_precision = precision;
+    return BAB_OK;
 }
 
 int bab_set_scratch_limit(bab_ctx *c, size_t bytes)

@@ -68,6 +68,13 @@ struct NetDesc {
     // gam_tc[l] = gamma_split(tcb_K[l]) for a 3-term BF16 split product
     float gam[kMaxLayers + 1];
     float gam_tc[kMaxLayers + 1];
+    // tensor-core interval image (k_ibp_tc): per layer l, per 128-row block mb of its outputs and 64-wide block
+    // ka of its inputs, one 64 KB stage [W hi | W lo | |W| hi | |W| lo], each 128 rows x 128 bytes (swizzled
+    // K-major, rows past d_l zero); ibp_mb[l], ibp_ka[l] the block counts, ibp_off[l] the layer's first stage;
+    // gam_ibp[l] = gamma_split(pad16(d_{l-1})); ibp_ok: every width at most 256
+    int ibp_ok, ibp_bytes;
+    int ibp_mb[kMaxLayers + 1], ibp_ka[kMaxLayers + 1], ibp_off[kMaxLayers + 1];
+    float gam_ibp[kMaxLayers + 1];
 };
 
 __host__ __device__ constexpr int pad16(int x) { return (x + 15) & ~15; }

@@ -123,6 +123,7 @@ struct BoundArgs {
     int stages;              // > 0: the backward image is streamed through `stages` ring buffers
     int stage_bytes;
     int stg_cols, stg_hid, stg_step;  // staged tensor-core CROWN: columns a thread takes, floats per area
+    const uint8_t *ibp_img;  // tensor-core interval image (k_ibp_tc)
     CostDesc cost;           // the state cost (kind 0: squared distance)
 };
 
@@ -346,6 +347,9 @@ void launch_emp_init(const RolloutArgs &a, cudaStream_t st);
 void launch_emp_finish(const RolloutArgs &a, cudaStream_t st);
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st);
 cudaError_t launch_ibp(const BoundArgs &a, int num_sms, cudaStream_t st);
+// interval bounds on tensor cores (split products with a computed margin; squared-distance cost, widths <= 256)
+cudaError_t launch_ibp_tc(const BoundArgs &a, int num_sms, cudaStream_t st);
+bool ibp_tc_supported(const NetDesc &N, int max_smem);
 cudaError_t launch_crown(const BoundArgs &a, int num_sms, cudaStream_t st);
 // Loads every instance launch_ibp / launch_crown may pick into the current device's context (lazy module loading
 // would otherwise load, and allocate for, each one at its first launch).

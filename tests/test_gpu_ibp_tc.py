@@ -1,0 +1,70 @@
+"""Interval bounds on tensor cores (bab_set_interval_precision(BAB_PREC_BF16X3)): W c and |W| r as 3-term BF16
+split products with a computed margin.  Checked against the FP64 oracle's interval bounds (they must contain them:
+the margin is sound), for the tiny, pushing and object-manipulation networks, ragged tiles included; the CROWN bound
+on these intervals stays sound (below the oracle's bound on exact intervals and below sampled objectives) and close
+to it at the pushing scale; the interval bound of the cost stays below the oracle's."""
+import numpy as np
+import pytest
+
+from paper_2412_09584_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("name,n,maxw", [("tiny", 64, 0.5), ("tiny", 37, 2.0), ("pushing", 19, 0.5),
+                                         ("pushing", 70, 0.05), ("manip", 5, 0.02)])
+def test_tc_intervals_contain_the_oracle(oracle, gp, name, n, maxw):
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem(name, 2)
+    d = p["k"] * p["H"]
+    lo, hi, _ = W.random_boxes(d, n, seed=4, min_width=0.0, max_width=maxw)
+    g = gp(p)
+    B.bab_set_interval_precision(g.ctx, B.PREC_BF16X3)
+    lb, pl, pu, xl, xu = g.ibp(lo, hi)
+    assert B.bab_status(g.ctx) == 0
+    lb_o, pl_o, pu_o, xl_o, xu_o = oracle.ibp(p, lo, hi)
+    assert np.all(pl <= pl_o) and np.all(pu >= pu_o)
+    assert np.all(xl <= xl_o) and np.all(xu >= xu_o)
+    assert np.all(lb <= lb_o + 1e-12 * np.abs(lb_o))
+    if name != "manip":
+        # the margin's widening: about gamma_split |W| (|c| + r) per layer, compounding over the unrolled steps
+        scale = np.maximum(np.abs(pl_o) + np.abs(pu_o), 1.0)
+        assert np.max(((pu - pl) - (pu_o - pl_o)) / scale) <= 2e-3
+
+
+@pytest.mark.parametrize("name,n,maxw", [("pushing", 21, 0.2), ("pushing", 200, 2.0), ("tiny", 64, 2.0)])
+def test_crown_on_tc_intervals(oracle, gp, name, n, maxw):
+    """The tensor-core CROWN on the tensor-core intervals: at most the oracle's bound on exact intervals, within
+    1e-4 of its scale at these depths, and below sampled objectives."""
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem(name, 3)
+    d = p["k"] * p["H"]
+    lo, hi, _ = W.random_boxes(d, n, seed=n, min_width=0.0, max_width=maxw)
+    g = gp(p)
+    B.bab_set_interval_precision(g.ctx, B.PREC_BF16X3)
+    r = g.crown(lo, hi, precision=B.PREC_BF16X3)
+    assert B.bab_status(g.ctx) == 0
+    o = oracle.crown(p, lo, hi)
+    scale = np.maximum(o["scale"], 1.0)
+    assert np.all(r["lb"] <= o["lb"] + 1e-12 * np.abs(o["lb"]))
+    assert np.all(r["lb"] + r["margin"] >= o["lb"] - 1e-4 * scale)
+    rng = np.random.default_rng(1)
+    for i in range(0, n, max(1, n // 8)):
+        us = lo[i] + rng.uniform(size=(64, d)) * (hi[i] - lo[i])
+        assert r["lb"][i] <= min(oracle.objective(p, u.astype(np.float64)) for u in us)
+
+
+def test_interval_precision_settings(gp):
+    from paper_2412_09584_gb300 import binding as B
+    g = gp(W.config_problem("tiny", 1))
+    with pytest.raises(B.BabError) as e:
+        B.bab_set_interval_precision(g.ctx, 7)
+    assert e.value.code == -1
+    B.bab_set_interval_precision(g.ctx, B.PREC_BF16X3)
+    B.bab_set_interval_precision(g.ctx, B.PREC_FP32)
