@@ -202,7 +202,7 @@ class BabState:
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
                  alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None,
-                 heuristics=None, cem=None, cost=None):
+                 heuristics=None, cem=None, cost=None, interval_prec="fp32"):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -220,6 +220,10 @@ class BabState:
         self.rprec, self.bprec = PRECISIONS[rollout_prec], PRECISIONS[bound_prec]
         self.alpha_steps, self.alpha_lr = alpha_steps, alpha_lr
         self.ctx = B.bab_load_dynamics(self.p["dims"], self.p["params"], self.p["s"], self.p["k"])
+        self.iprec = interval_prec
+        if interval_prec == "bf16x3":
+            # interval bounds on tensor cores (split products with a computed margin)
+            B.bab_set_interval_precision(self.ctx, B.PREC_BF16X3)
         if cost is not None:
             # the pushing-with-obstacles state cost (Appendix D.4) instead of the squared distance
             B.bab_set_cost(self.ctx, B.COST_PUSHING_OBSTACLES, cost["w"], cost["lam"], cost["obstacles"], cost["p0"])
@@ -445,6 +449,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     n_pick = args.boxes // 2
     st = BabState("pushing", rank_seed(rank), dev, n_pick, args.precision, args.bound_precision,
+                  interval_prec=args.interval_precision,
                   fixed_launch=not args.no_graph, autotune=not args.no_autotune)
     for _ in range(args.warmup):
         st.step()
@@ -509,7 +514,8 @@ def run_ours(args):
     roof["traffic"] = rollout_traffic(args.precision, st.nb, st.M)
     # the same iteration with the rollouts in the other arithmetics: all-FP32 (the configuration as named) and
     # plain BF16 with each box's pick re-scored in FP32 (the search precision the method's plan prescribes)
-    lines = precision_lines(dev, rank_seed(rank), n_pick, args.precision, args.bound_precision) \
+    lines = precision_lines(dev, rank_seed(rank), n_pick, args.precision, args.bound_precision,
+                            args.interval_precision) \
         if ws == 1 and not args.no_precision_lines else None
     if rank != 0:
         return
@@ -517,7 +523,9 @@ def run_ours(args):
                        f"rho=0.01, {st.nb} children bounded per iteration ({n_pick} picked, widest-dim bisection), "
                        f"{st.M} uniform rollouts per child",
            "rollout_arithmetic": ARITH[args.precision],
-           "bound_arithmetic": "outward-rounded FP32 intervals; CROWN products " +
+           "bound_arithmetic": ("interval bounds on tcgen05 (3-term BF16 split, computed margin)"
+                                if args.interval_precision == "bf16x3" else "outward-rounded FP32 intervals") +
+                               "; CROWN products " +
                                ("on tcgen05, 3-term BF16 split" if args.bound_precision == "bf16x3"
                                 else "in FP32 on CUDA cores") + ", margin-corrected",
            "boxes_per_step": st.nb, "samples_per_box": st.M, "H": st.H,
@@ -543,7 +551,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def precision_lines(dev, seed, n_pick, headline, bound_precision, steps=3):
+def precision_lines(dev, seed, n_pick, headline, bound_precision, interval_precision="fp32", steps=3):
     """The bench iteration with the rollouts in each arithmetic other than the headline's, and with the headline's
     rollouts and the other CROWN arithmetic: CUDA-graph replays of the same pushing-scale iteration, L2 flushed
     between steps, per-kernel times by CUDA events after the timed region; each with its rollout roofline (FP32
@@ -551,10 +559,14 @@ def precision_lines(dev, seed, n_pick, headline, bound_precision, steps=3):
     import torch
     out = {}
     other_bound = "fp32" if bound_precision == "bf16x3" else "bf16x3"
-    combos = [(p, bound_precision) for p in ("fp32", "bf16x3", "bf16") if p != headline] + [(headline, other_bound)]
-    for prec, bprec in combos:
+    other_int = "fp32" if interval_precision == "bf16x3" else "bf16x3"
+    combos = [(p, bound_precision, interval_precision) for p in ("fp32", "bf16x3", "bf16") if p != headline]
+    combos += [(headline, other_bound, interval_precision), (headline, bound_precision, other_int)]
+    for prec, bprec, iprec in combos:
         key = prec if bprec == bound_precision else f"{prec}, {bprec} CROWN products"
-        st = BabState("pushing", seed, dev, n_pick, prec, bprec, fixed_launch=True)
+        if iprec != interval_precision:
+            key = f"{prec}, {iprec} interval bounds"
+        st = BabState("pushing", seed, dev, n_pick, prec, bprec, fixed_launch=True, interval_prec=iprec)
         for _ in range(3):
             st.step()
             st.flush_l2()
@@ -576,7 +588,8 @@ def precision_lines(dev, seed, n_pick, headline, bound_precision, steps=3):
         torch.cuda.synchronize()
         roll = statistics.mean(e[0].elapsed_time(e[1]) for e in st.ev)
         bound = statistics.mean(e[1].elapsed_time(e[2]) for e in st.ev)
-        out[key] = {"rollout_arithmetic": ARITH[prec], "bound_arithmetic": bprec, "ms_per_step": ms,
+        out[key] = {"rollout_arithmetic": ARITH[prec], "bound_arithmetic": bprec, "interval_arithmetic": iprec,
+                    "ms_per_step": ms,
                     "subdomain_bounds_per_s": st.nb / (ms / 1e3),
                     "rollout_steps_per_s": st.nb * st.M * st.H / (ms / 1e3),
                     "kernel_ms": {"rollout": roll, "bound": bound},
@@ -1113,9 +1126,9 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
     (read back every iteration by every variant alike)."""
     import torch
 
-    def run(rprec, bprec, alpha_steps, n_iter, target=None):
+    def run(rprec, bprec, alpha_steps, n_iter, target=None, iprec="fp32"):
         st = BabState(workload, SEED, dev, n_pick, rprec, bprec, alpha_steps=alpha_steps,
-                      pool_iters=max_iters + 2, autotune=True)
+                      pool_iters=max_iters + 2, autotune=True, interval_prec=iprec)
         torch.cuda.synchronize()
         t = time.perf_counter()
         hist = []
@@ -1136,10 +1149,15 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
     if variants is None:
         variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
                     "alpha_split": ("bf16x3", "bf16x3", 5), "alpha_split_20": ("bf16x3", "bf16x3", 20),
-                    "alpha_fused": ("bf16x3", "fp32", 20), "alpha_fused_5": ("bf16x3", "fp32", 5)}
+                    "alpha_fused": ("bf16x3", "fp32", 20), "alpha_fused_5": ("bf16x3", "fp32", 5),
+                    "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
+                    "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3")}
+    def go(v, **kw):  # a variant: (rollout, CROWN products, Adam steps[, interval bounds])
+        return run(*v[:3], iprec=v[3] if len(v) > 3 else "fp32", **kw)
+
     for v in variants.values():  # load every kernel and size every scratch buffer before timing
-        run(*v, n_iter=2)
-    plain = run(*variants["plain_fp32"], n_iter=iters)
+        go(v, n_iter=2)
+    plain = go(variants["plain_fp32"], n_iter=iters)
     target = plain[-1][1]
     c = W_CONFIGS()[workload]
     dims = "-".join(str(x) for x in [c["s"] + c["k"]] + list(c["hidden"]) + [c["s"]])
@@ -1148,11 +1166,11 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
                        f"target = plain FP32 BaB's gap after {iters} iterations", "target_gap": target}
     plain_variants = run.variants
     for name, v in variants.items():
-        h = plain if name == "plain_fp32" else run(*v, n_iter=max_iters, target=target)
+        h = plain if name == "plain_fp32" else go(v, n_iter=max_iters, target=target)
         reached = h[-1][1] <= target
         out[name] = {"seconds": h[-1][0], "iterations": len(h), "reached": reached,
                      "ms_per_iteration": 1e3 * h[-1][0] / len(h), "gap_curve": [round(x[1], 6) for x in h],
-                     "rollout": v[0], "bound": v[1], "alpha_steps": v[2],
+                     "rollout": v[0], "bound": v[1], "alpha_steps": v[2], "intervals": v[3] if len(v) > 3 else "fp32",
                      "launch_variants": plain_variants if name == "plain_fp32" else run.variants}
         if name != "plain_fp32":
             out[name]["speedup_vs_plain"] = plain[-1][0] / h[-1][0] if reached else None
@@ -1168,7 +1186,9 @@ def time_to_gap_pushing(dev):
     """Time-to-gap on the pushing network (MLP 10-128-128-128-8, H = 20), 512 children per iteration."""
     variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
                 "split_fp32_bound": ("bf16x3", "fp32", 0), "alpha_fused": ("bf16x3", "fp32", 20),
-                "alpha_fused_5": ("bf16x3", "fp32", 5), "alpha_split": ("bf16x3", "bf16x3", 5)}
+                "alpha_fused_5": ("bf16x3", "fp32", 5), "alpha_split": ("bf16x3", "bf16x3", 5),
+                "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
+                "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3")}
     return time_to_gap(dev, "pushing", n_pick=256, iters=10, max_iters=30, variants=variants)
 
 
@@ -1334,6 +1354,8 @@ def main():
     ap.add_argument("--no-precision-lines", action="store_true",
                     help="skip the same iteration with the rollouts in the other arithmetics")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--interval-precision", choices=["fp32", "bf16x3"], default="fp32",
+                    help="interval bounds: fp32 (directed rounding, CUDA cores) or bf16x3 (tcgen05, computed margin)")
     ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="bf16x3",
                     help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16",
