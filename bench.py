@@ -1145,11 +1145,13 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
     # plain: FP32 rollouts and FP32 CROWN; split: 3-term BF16 tensor-core rollouts and CROWN; alpha_split: split
     # plus 5 Adam steps per iteration (alpha_split_20: 20), each a tensor-core CROWN + adjoint + Adam launch;
     # alpha_fused: 3-term BF16 rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration;
-    # alpha_fused_5: the same with 5 Adam steps (the bound gains most in the first steps)
+    # alpha_fused_5, alpha_fused_2: the same with 5 or 2 Adam steps (the bound gains most in the first steps);
+    # *_tc_intervals: the interval bounds on tensor cores as well
     if variants is None:
         variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
                     "alpha_split": ("bf16x3", "bf16x3", 5), "alpha_split_20": ("bf16x3", "bf16x3", 20),
                     "alpha_fused": ("bf16x3", "fp32", 20), "alpha_fused_5": ("bf16x3", "fp32", 5),
+                    "alpha_fused_2": ("bf16x3", "fp32", 2), "alpha_split_2": ("bf16x3", "bf16x3", 2),
                     "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
                     "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3")}
     def go(v, **kw):  # a variant: (rollout, CROWN products, Adam steps[, interval bounds])
@@ -1187,6 +1189,7 @@ def time_to_gap_pushing(dev):
     variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
                 "split_fp32_bound": ("bf16x3", "fp32", 0), "alpha_fused": ("bf16x3", "fp32", 20),
                 "alpha_fused_5": ("bf16x3", "fp32", 5), "alpha_split": ("bf16x3", "bf16x3", 5),
+                "alpha_fused_2": ("bf16x3", "fp32", 2), "alpha_split_2": ("bf16x3", "bf16x3", 2),
                 "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
                 "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3")}
     return time_to_gap(dev, "pushing", n_pick=256, iters=10, max_iters=30, variants=variants)
