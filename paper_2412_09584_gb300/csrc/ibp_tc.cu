@@ -19,8 +19,8 @@
 // a producer warp streams them one 64 KB stage (one 128-row block x 64 inputs of the four images) at a time
 // through a ring, in the MMA issuer's order; the tile's operands c (hi, lo), r (hi, lo) and |c| + r stay in shared
 // memory.  Epilogue warp (row block mb, lane quadrant q) lane `lane` owns output j = 128 mb + 32 q + lane of every
-// box of the tile, or, in a layer of one row block, output 32 q + lane of half the tile's boxes.  Squared-distance cost; the interval of the cost (lb_ibp) comes from a separate pass.  Every wait
-// is bounded in time.
+// box of the tile, or, in a layer of one row block, output 32 q + lane of half the tile's boxes.  Squared-distance
+// cost; the interval of the cost (lb_ibp) comes from a separate pass.  Every wait is bounded in time.
 #include <cuda_bf16.h>
 
 #include "bab_internal.cuh"
