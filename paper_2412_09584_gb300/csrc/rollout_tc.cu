@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
             tc::tmem_wait_st();
         }
         // ReLU and BF16 conversion of accumulator columns [c_beg, c_end) (the bias came in by its MMA) into the A
-        // region, 16 columns per TMEM round trip
+        // region, 32 columns (two loads) per TMEM round trip (16 measured 8.29 against 8.18 ms)
         auto hidden = [&](int Nl) {
             const bool split_cols = (Nl % 64 == 0);
             int c_beg = 0, c_end = Nl;
@@ -722,15 +722,19 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
             } else if (!primary) {
                 c_end = 0;
             }
-            for (int c0 = c_beg; c0 < c_end; c0 += 16) {
-                uint32_t v[16];
+            for (int c0 = c_beg; c0 < c_end; c0 += 32) {
+                uint32_t v[16], w[16];
                 tc::tmem_ld16(dcol + c0, v);
+                tc::tmem_ld16(dcol + c0 + 16, w);
                 tc::tmem_wait_ld();
-                uint32_t ph[8], pl[8];
+                uint32_t ph[8], qh[8], unused;
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    relu_split2<1>(make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])), ph[q], pl[q]);
+                for (int q = 0; q < 8; ++q) {
+                    relu_split2<1>(make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1])), ph[q], unused);
+                    relu_split2<1>(make_float2(__uint_as_float(w[2 * q]), __uint_as_float(w[2 * q + 1])), qh[q], unused);
+                }
                 tc::tmem_st8(acol + c0 / 2, ph);
+                tc::tmem_st8(acol + c0 / 2 + 8, qh);
             }
         };
         auto handoff = [&]() {
