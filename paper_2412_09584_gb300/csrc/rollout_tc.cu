@@ -712,13 +712,14 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
             tc::tmem_wait_st();
         }
         // ReLU and BF16 conversion of accumulator columns [c_beg, c_end) (the bias came in by its MMA) into the A
-        // region, 32 columns (two loads) per TMEM round trip (16 measured 8.29 against 8.18 ms)
-        auto hidden = [&](int Nl) {
+        // region, 32 columns (two loads) per TMEM round trip (16 measured 8.29 against 8.18 ms); a width that is a
+        // multiple of 64 is split between the quadrant's primary warp (the first pc columns) and its helper
+        auto hidden = [&](int Nl, int pc) {
             const bool split_cols = (Nl % 64 == 0);
             int c_beg = 0, c_end = Nl;
             if (split_cols) {
-                c_beg = primary ? 0 : Nl / 2;
-                c_end = c_beg + Nl / 2;
+                c_beg = primary ? 0 : pc;
+                c_end = primary ? pc : Nl;
             } else if (!primary) {
                 c_end = 0;
             }
@@ -813,7 +814,7 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
             if (ok) handoff();  // layer 1 of step 0 may start
             // z1_0
             if (ok && (ok = wait_d())) {
-                hidden(N1);
+                hidden(N1, N1 / 2);
                 handoff();
             }
             for (int t = 0; t < Hb && ok; ++t) {
@@ -821,7 +822,7 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
                 if (primary && more) draw_step(t + 1);  // the next step's actions, drawn while layer 2 runs
                 for (int l = 2; l <= L - 1 && ok; ++l) {
                     if (!(ok = wait_d())) break;
-                    hidden(N.tc_N[l]);
+                    hidden(N.tc_N[l], N.tc_N[l] / 2);
                     if (l == L - 1 && primary) write_row(more);  // the fused product's input row [u_{t+1} | x_t]
                     handoff();
                 }
@@ -862,7 +863,7 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
                     if (more) rho_term(cost);
                 }
                 if (more) {
-                    hidden(N1);
+                    hidden(N1, N1 / 2 >= 64 ? 32 : N1 / 2);  // the primary also ran the output stage: 32 columns
                     handoff();
                 }
             }
