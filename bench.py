@@ -293,6 +293,21 @@ class BabState:
         # prune/branch 2, rollout 4 (keys, rollout, finalize, incumbent), bound 2 (or the alpha loop)
         self.launches_per_step = 2 + 4 + (2 if not alpha_steps else (2 if fused else 3 + alpha_steps * 3))
 
+    def snapshot(self):
+        """Device copies of the BaB state (both pools, counts, incumbent), to rerun the same iterations."""
+        keys = ("counts", "inc_val", "inc_u", "n_live_dev")
+        return {"pool": [{k: v.clone() for k, v in P.items()} for P in self.pool], "cur": self.cur, "it": self.it,
+                **{k: getattr(self, k).clone() for k in keys}}
+
+    def restore(self, snap):
+        """Back to a snapshot, in place (captured graphs keep their buffers)."""
+        for P, Q in zip(self.pool, snap["pool"]):
+            for k, v in Q.items():
+                P[k].copy_(v)
+        for k in ("counts", "inc_val", "inc_u", "n_live_dev"):
+            getattr(self, k).copy_(snap[k])
+        self.cur, self.it = snap["cur"], snap["it"]
+
     def _alloc(self):
         torch = self.torch
         f = dict(device=self.dev, dtype=torch.float32)
@@ -405,8 +420,8 @@ def capture_graphs(st):
 # 1024 samples, from one ncu capture of this bench (dram__bytes_read.sum + dram__bytes_write.sum); valid only for
 # the kernel sources it was taken on, so it is reported only while their digest (comments and whitespace removed)
 # matches.
-ROLLOUT_TC_TRAFFIC = {"bytes": 1805056, "precision": "bf16", "boxes": 4096, "samples": 1024,
-                      "sources_sha1": "6459b409fdcd9e0a5dae32e54d241f831381503e"}
+ROLLOUT_TC_TRAFFIC = {"bytes": 1826048, "precision": "bf16", "boxes": 4096, "samples": 1024,
+                      "sources_sha1": "fcfea32e89c6a4b4e7c62266abc6aa47099232a9"}
 ROLLOUT_TC_SOURCES = ("rollout_tc.cu", "tc_ptx.cuh", "kernels.cuh", "bab_internal.cuh")
 
 
@@ -456,6 +471,8 @@ def run_ours(args):
         st.flush_l2()
     graphs = None if args.no_graph else capture_graphs(st)
     torch.cuda.synchronize()
+    snap = st.snapshot()  # the end-to-end run below starts from the same pool as the timed region
+    torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -484,7 +501,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     roll_ms = [e[0].elapsed_time(e[1]) for e in st.ev]
     bound_ms = [e[1].elapsed_time(e[2]) for e in st.ev]
-    # end to end through the C-ABI with host buffers; whole-job rate over the slowest rank, as the device timing
+    # end to end through the C-ABI with host buffers, from the timed region's starting pool (the pool grows every
+    # iteration, and with it the prune/branch plan); whole-job rate over the slowest rank, as the device timing
+    st.restore(snap)
+    del snap
+    torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     e2e = run_e2e(st, args.steps)
