@@ -1167,14 +1167,16 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
     # plus 5 Adam steps per iteration (alpha_split_20: 20), each a tensor-core CROWN + adjoint + Adam launch;
     # alpha_fused: 3-term BF16 rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration;
     # alpha_fused_5, alpha_fused_2: the same with 5 or 2 Adam steps (the bound gains most in the first steps);
-    # *_tc_intervals: the interval bounds on tensor cores as well
+    # *_tc_intervals: the interval bounds on tensor cores as well; headline*: the bench's own arithmetic (BF16
+    # rollouts with the picks re-scored in FP32, tensor-core CROWN), plain or with 2 tensor-core Adam steps
     if variants is None:
         variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
                     "alpha_split": ("bf16x3", "bf16x3", 5), "alpha_split_20": ("bf16x3", "bf16x3", 20),
                     "alpha_fused": ("bf16x3", "fp32", 20), "alpha_fused_5": ("bf16x3", "fp32", 5),
                     "alpha_fused_2": ("bf16x3", "fp32", 2), "alpha_split_2": ("bf16x3", "bf16x3", 2),
                     "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
-                    "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3")}
+                    "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3"),
+                    "headline": ("bf16", "bf16x3", 0), "headline_alpha_2": ("bf16", "bf16x3", 2)}
     def go(v, **kw):  # a variant: (rollout, CROWN products, Adam steps[, interval bounds])
         return run(*v[:3], iprec=v[3] if len(v) > 3 else "fp32", **kw)
 
@@ -1212,7 +1214,9 @@ def time_to_gap_pushing(dev):
                 "alpha_fused_5": ("bf16x3", "fp32", 5), "alpha_split": ("bf16x3", "bf16x3", 5),
                 "alpha_fused_2": ("bf16x3", "fp32", 2), "alpha_split_2": ("bf16x3", "bf16x3", 2),
                 "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
-                "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3")}
+                "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3"),
+                "headline": ("bf16", "bf16x3", 0), "headline_alpha_2": ("bf16", "bf16x3", 2),
+                "headline_tc_intervals": ("bf16", "bf16x3", 0, "bf16x3")}
     return time_to_gap(dev, "pushing", n_pick=256, iters=10, max_iters=30, variants=variants)
 
 
