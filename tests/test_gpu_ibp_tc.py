@@ -68,3 +68,40 @@ def test_interval_precision_settings(gp):
     assert e.value.code == -1
     B.bab_set_interval_precision(g.ctx, B.PREC_BF16X3)
     B.bab_set_interval_precision(g.ctx, B.PREC_FP32)
+    # several problems in one context: the tensor-core intervals are refused, the FP32 ones stay
+    probs, _ = W.batch_problems(3, 5, H_lo=2, H_hi=4)
+    params, _, _, _, _ = W.pack_batch(probs)
+    ctx = B.bab_load_dynamics_batch(probs[0]["dims"], params, probs[0]["s"], probs[0]["k"])
+    try:
+        with pytest.raises(B.BabError) as e:
+            B.bab_set_interval_precision(ctx, B.PREC_BF16X3)
+        assert e.value.code == -7
+        B.bab_set_interval_precision(ctx, B.PREC_FP32)
+    finally:
+        B.bab_destroy(ctx)
+
+
+def test_tc_intervals_chunked_bit_identical(gp):
+    """Under a scratch limit the boxes are bounded in chunks, each box on its own: the tensor-core intervals and the
+    CROWN bound on them equal the one-pass results bit for bit (a box's column of the products and its epilogue do
+    not depend on its neighbours in the tile)."""
+    import torch
+    from gpu_util import DEV, T
+    from paper_2412_09584_gb300 import binding as B
+    p = W.config_problem("pushing", 2)
+    g = gp(p)
+    n = 150
+    lo, hi, _ = W.random_boxes(g.d, n, seed=9, min_width=0.0, max_width=1.0)
+    B.bab_set_interval_precision(g.ctx, B.PREC_BF16X3)
+    per_box = (3 * g.H * g.sumh + 2 * (g.H + 1) * p["s"] + g.H * (g.sumh + p["s"]) + 2 * g.d + 4) * 4
+    outs = []
+    for limit in (0, 64 * 1024 + 37 * per_box):
+        B.bab_set_scratch_limit(g.ctx, limit)
+        lb, mg = torch.empty(n, device=DEV), torch.empty(n, device=DEV)
+        B.bab_bound_crown(g.ctx, g.x0, g.goal, g.H, g.rho, T(lo), T(hi), n, lb, precision=B.PREC_BF16X3, margin=mg)
+        torch.cuda.synchronize()
+        outs.append((lb.cpu().numpy().view(np.uint32).copy(), mg.cpu().numpy().view(np.uint32).copy()))
+    B.bab_set_scratch_limit(g.ctx, 0)
+    assert B.bab_status(g.ctx) == 0
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
