@@ -61,6 +61,7 @@ extern "C" {
 #define BAB_PREC_FP32 0    /* FP32 on CUDA cores (round-to-nearest FMA chains) */
 #define BAB_PREC_BF16X3 1  /* tcgen05 tensor cores, 3-term BF16 split operands, FP32 accumulate */
 #define BAB_PREC_BF16 2    /* tcgen05 tensor cores, BF16 operands, FP32 accumulate (rollouts only) */
+#define BAB_PREC_TF32X3 3  /* tcgen05 tensor cores, 3-term TF32 split operands, FP32 accumulate (CROWN and alpha only) */
 
 /* Split rules of bab_prune_branch. */
 #define BAB_SPLIT_WIDEST 0 /* bisect the widest coordinate (Section 3.1), lowest index on ties */
@@ -203,7 +204,14 @@ int bab_bound_ibp(bab_ctx *ctx, const float *x0, const float *goal, int horizon,
  *   alpha      device float[n][H][sumh] (nullable): lower slopes of unstable
  *              ReLUs, each in [0, 1]; NULL selects the adaptive slope
  *              (1 if u >= -l, else 0).
- *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3.
+ *   precision  BAB_PREC_FP32, BAB_PREC_BF16X3 or BAB_PREC_TF32X3.  The split
+ *              precisions evaluate every backward product A' W_l as
+ *              A'h Wh + A'h Wl + A'l Wh on the tensor cores (BF16 halves: about
+ *              2^-16 representation error per operand; TF32 halves: about
+ *              2^-22, at twice the operand bytes and twice the instructions),
+ *              and charge gamma_K sum |A'| |W| max|a| to the margin.
+ *              BAB_PREC_TF32X3 takes the squared-distance cost and networks
+ *              whose widths are all at most 128 (else BAB_ERR_UNSUPPORTED).
  *   lb         device float[n]; margin device float[n] (nullable).
  *   lin_coef   device float[n][d] (nullable): mu; lin_const device float[n]
  *              (nullable): the constant (before the margin).
@@ -227,7 +235,8 @@ int bab_bound_crown(bab_ctx *ctx, const float *x0, const float *goal, int horizo
  *      alpha to [0, 1].
  *   alpha, adam_m, adam_v  device float[n][H][sumh], updated in place
  *              (m, v start at 0; alpha typically at the adaptive slopes).
- *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3 (the CROWN products, as bab_bound_crown).
+ *   precision  BAB_PREC_FP32, BAB_PREC_BF16X3 or BAB_PREC_TF32X3 (the CROWN
+ *              products, as bab_bound_crown).
  *   lb         device float[n] (nullable): bound at the incoming alpha.
  *   lb_best    device float[n] (nullable): running maximum, updated.
  *   grad_alpha device float[n][H][sumh] (nullable): the gradient.
@@ -277,7 +286,7 @@ int bab_box_grad(bab_ctx *ctx, const float *x0, const float *goal, int horizon, 
  * once, and the Adam moments in context scratch.  lb_best[i] receives the
  * best bound of box i over all steps (each a valid bound, margin subtracted).
  *   steps      number of Adam steps (>= 1); lr their learning rate.
- *   precision  BAB_PREC_FP32 or BAB_PREC_BF16X3.
+ *   precision  BAB_PREC_FP32, BAB_PREC_BF16X3 or BAB_PREC_TF32X3.
  *   alpha      device float[n][H][sumh] (nullable): receives the final slopes.
  *   lb_best    device float[n].
  * All work is queued on `stream` without host synchronisation.  In FP32 the

@@ -578,6 +578,10 @@ typedef struct {
  *      3.1 * 2^-16 for the BF16 halves of both operands and the dropped
  *      lo * lo term, plus gamma_K with unit 2^-23 (an accumulator that may
  *      truncate).
+ *   2: 3-term TF32 split, the same with halves of 11 significant bits
+ *      (each operand's residual and the dropped lo * lo term at most about
+ *      2^-22 of |a| |b|) over K = d_l rounded up to a multiple of 8 terms:
+ *      3.1 * 2^-22 plus gamma_K with unit 2^-23.
  * Each other rounded coefficient operation costs at most 2^-23 (twice the
  * unit roundoff) of its magnitude times the largest magnitude of its
  * variable: the relaxation product A D of a neuron whose slope is neither 0
@@ -590,6 +594,10 @@ static double margin_gamma(int prec, int d)
     if (prec == 1) {
         double K = (double)((d + 15) / 16 * 16), u = ldexp(1.0, -23);
         return 3.1 * ldexp(1.0, -16) + K * u / (1.0 - K * u);
+    }
+    if (prec == 2) {
+        double K = (double)((d + 7) / 8 * 8), u = ldexp(1.0, -23);
+        return 3.1 * ldexp(1.0, -22) + K * u / (1.0 - K * u);
     }
     double K = (double)((d + 3) / 4 * 4), u = ldexp(1.0, -24);
     return K * u / (1.0 - K * u);
@@ -930,7 +938,7 @@ int oracle_crown_given(int L, const int *dims, const double *params, int s, int 
 
 /*
  * CROWN bound with its outward rounding margin (margin_gamma) for the
- * arithmetic `prec` (0: FP32 products, 1: 3-term BF16 split), with given
+ * arithmetic `prec` (0: FP32 products, 1: 3-term BF16 split, 2: 3-term TF32 split), with given
  * intermediate bounds (pre_lo/pre_hi [n][H][sumh], x_lo/x_hi [n][H+1][s]) or,
  * when pre_lo is NULL, the interval bounds of oracle_ibp; alpha [n][H][sumh]
  * nullable (adaptive slopes).  Outputs per box: lb (exact FP64, no margin
@@ -944,7 +952,7 @@ int oracle_crown_margin(int L, const int *dims, const double *params, int s, int
 {
     onet N;
     if (onet_init(&N, L, dims, params, s, k)) return -1;
-    if (prec != 0 && prec != 1) return -1;
+    if (prec < 0 || prec > 2) return -1;
     int d = k * H;
     size_t nh = (size_t)H * N.sumh, nx = (size_t)(H + 1) * s;
     double *pl = (double *)malloc(sizeof(double) * (nh ? nh : 1));

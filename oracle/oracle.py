@@ -13,7 +13,7 @@ citations are to arXiv 2412.09584 (BaB-ND):
 * ``rollout``       Section 3.3 (batch_search, uniform samples)
 * ``ibp``           interval intermediate bounds used by Lemma 1
 * ``crown``         Appendix B.1, Lemma 1, Theorem 1, Theorem 2 (box form)
-* ``crown_margin``  the same bound with the outward rounding margin of an FP32 / split-BF16 evaluation
+* ``crown_margin``  the same bound with the outward rounding margin of an FP32 / split-BF16 / split-TF32 evaluation
 * ``alpha_grad``    gradient of the Theorem 1/2 bound in the Lemma 1 slopes
 * ``adam_ascent``   projected Adam on the slopes
 * ``prune_branch``  Section 3 overview (Pruner), Section 3.1 (pick out, split)
@@ -279,8 +279,8 @@ def crown_given(problem, lo, hi, pre_lo, pre_hi, x_lo, x_hi, t_stop=0):
 
 
 def crown_margin(problem, lo, hi, intervals=None, alpha=None, prec=0):
-    """CROWN bound with the outward rounding margin of an FP32 (prec 0) or 3-term BF16 split (prec 1)
-    evaluation, in FP64: dict with lb (no margin subtracted), margin and scale.  `intervals` = (pre_lo, pre_hi,
+    """CROWN bound with the outward rounding margin of an FP32 (prec 0), 3-term BF16 split (prec 1) or 3-term TF32
+    split (prec 2) evaluation, in FP64: dict with lb (no margin subtracted), margin and scale.  `intervals` = (pre_lo, pre_hi,
     x_lo, x_hi) gives the intermediate bounds (else the oracle's interval bounds); alpha: lower slopes or None
     (adaptive)."""
     net, keep, (cH, crho, px0, pg) = _prob(problem)

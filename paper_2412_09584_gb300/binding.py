@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "bab.h")
 BAB_OK = 0
 ERRORS = {-1: "BAB_ERR_INVALID_ARG", -2: "BAB_ERR_SHAPE", -3: "BAB_ERR_CUDA", -4: "BAB_ERR_OOM",
           -5: "BAB_ERR_TIMEOUT", -6: "BAB_ERR_NUMERIC", -7: "BAB_ERR_UNSUPPORTED"}
-PREC_FP32, PREC_BF16X3, PREC_BF16 = 0, 1, 2
+PREC_FP32, PREC_BF16X3, PREC_BF16, PREC_TF32X3 = 0, 1, 2, 3
 SPLIT_WIDEST = 0
 PICK_LB, PICK_SOFTMAX = 0, 1
 KERNEL_ROLLOUT_FP32, KERNEL_ALPHA_FUSED, KERNEL_ROLLOUT_TC, KERNEL_CROWN_TC = 0, 1, 2, 3

@@ -21,6 +21,7 @@ struct bab_ctx {
     float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
     uint8_t *d_tc = nullptr, *d_tcb = nullptr;
     uint8_t *d_ibp = nullptr;   // the tensor-core interval image (problem 0)
+    uint8_t *d_tf = nullptr;    // the backward TF32 image (problem 0)
     int interval_precision = 0; // bab_set_interval_precision: BAB_PREC_FP32 (0) or BAB_PREC_BF16X3
     float *d_tc_bias = nullptr;
     void *scratch = nullptr;
@@ -53,6 +54,17 @@ float bf16_to_f32_host(uint16_t h)
 {
     uint32_t u = (uint32_t)h << 16;
     float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// f rounded to TF32 (10 stored mantissa bits, to nearest, ties away from zero): add half a unit of the 13th bit
+// to the magnitude, clear the 13 low bits (finite inputs)
+float tf32_rna_host(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
     std::memcpy(&f, &u, 4);
     return f;
 }
@@ -249,6 +261,37 @@ void build_tcb_image(NetDesc &N, const float *params, std::vector<uint8_t> &img)
                                    (size_t)((((within * 2) / 16) ^ (n % 8)) * 16) + (size_t)((within * 2) % 16);
                 std::memcpy(&img[N.tcb_hi[l] + off], &h, 2);
                 std::memcpy(&img[N.tcb_lo[l] + off], &lo, 2);
+            }
+    }
+}
+
+// Backward TF32 image: the operand of build_tcb_image with 32-bit elements, for 3-term TF32 split products.  Layer
+// l: K = d_l rounded up to 8 in blocks of 32 (128 bytes a row); block kb holds tcb_N[l] rows of the hi halves, then
+// as many rows of the lo halves (hi = tf32(w), lo = tf32(w - hi)), swizzled K-major.  Needs build_tcb_image first.
+void build_tf_image(NetDesc &N, const float *params, std::vector<uint8_t> &img)
+{
+    const int L = N.L;
+    int off = 0;
+    for (int l = 1; l <= L; ++l) {
+        N.tf_K[l] = pad8(N.dims[l]);
+        N.tf_off[l] = off;
+        N.gam_tf[l] = gamma_tf32(N.tf_K[l]);
+        off += ((N.tf_K[l] + 31) / 32) * 2 * N.tcb_N[l] * 128;
+    }
+    N.tf_bytes = off;
+    img.assign((size_t)off, 0);
+    for (int l = 1; l <= L; ++l) {
+        const int no = N.dims[l], ni = N.dims[l - 1], Nl = N.tcb_N[l];
+        const float *W = params + N.raw_w[l];
+        for (int n = 0; n < ni; ++n)
+            for (int kk = 0; kk < no; ++kk) {
+                const float w = W[(size_t)kk * ni + n];
+                const float h = tf32_rna_host(w), lo = tf32_rna_host(w - h);
+                const int kb = kk / 32, within = kk % 32;
+                const size_t off2 = (size_t)N.tf_off[l] + (size_t)kb * 2 * Nl * 128 + (size_t)n * 128 +
+                                    (size_t)((((within * 4) / 16) ^ (n % 8)) * 16) + (size_t)((within * 4) % 16);
+                std::memcpy(&img[off2], &h, 4);
+                std::memcpy(&img[off2 + (size_t)Nl * 128], &lo, 4);
             }
     }
 }
@@ -481,8 +524,9 @@ int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *
         tc_img.insert(tc_img.end(), im.begin(), im.end());
         tc_bias.insert(tc_bias.end(), bi.begin(), bi.end());
     }
-    std::vector<uint8_t> tcb_img, ibp_img;
+    std::vector<uint8_t> tcb_img, ibp_img, tf_img;
     build_tcb_image(N, params, tcb_img);
+    build_tf_image(N, params, tf_img);
     build_ibp_tc_image(N, params, ibp_img);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -490,6 +534,8 @@ int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tc, tc_img.size());
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tcb, tcb_img.size());
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tcb, tcb_img.data(), tcb_img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tf, tf_img.size());
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_tf, tf_img.data(), tf_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ibp_img.empty()) e = cudaMalloc(&c->d_ibp, ibp_img.size());
     if (e == cudaSuccess && !ibp_img.empty())
         e = cudaMemcpy(c->d_ibp, ibp_img.data(), ibp_img.size(), cudaMemcpyHostToDevice);
@@ -673,6 +719,7 @@ int bab_destroy(bab_ctx *c)
     cudaFree(c->d_tc);
     cudaFree(c->d_tcb);
     cudaFree(c->d_ibp);
+    cudaFree(c->d_tf);
     cudaFree(c->d_tc_bias);
     cudaFree(c->scratch);
     cudaFree(c->d_status);
@@ -1041,12 +1088,47 @@ int bab_bound_ibp(bab_ctx *c, const float *x0, const float *goal, int H, float r
     return run_ibp(c, a, cv, pre_lo, pre_hi, x_lo, x_hi, lb_ibp, (cudaStream_t)stream);
 }
 
+// The CROWN launch of a bound precision (the tensor-core ones need a.mu set by the caller).
+static cudaError_t launch_crown_prec(bab_ctx *c, BoundArgs &a, int precision, cudaStream_t st)
+{
+    if (precision == BAB_PREC_FP32) return launch_crown(a, c->num_sms, st);
+    a.tc_bias = c->d_tc_bias;
+    if (precision == BAB_PREC_TF32X3) {
+        a.tcb_img = c->d_tf;
+        return launch_crown_tf32(a, c->num_sms, st);
+    }
+    a.tcb_img = c->d_tcb;
+    return launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st);
+}
+
+// Whether `precision` is a bound precision this context can run (else fails with BAB_ERR_UNSUPPORTED).
+static int check_crown_precision(bab_ctx *c, int precision, const char *what)
+{
+    int rc;
+    if (precision == BAB_PREC_BF16X3) {
+        if ((rc = check_tc_obstacles(c, what)) != BAB_OK) return rc;
+        if (!crown_tc_supported(c->net, c->max_smem))
+            return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN needs hidden widths that are multiples of 32, "
+                                                "s <= 32, s + k <= 48 and a weight image that fits in shared memory");
+        return BAB_OK;
+    }
+    if (precision == BAB_PREC_TF32X3) {
+        if (c->cost.kind != 0) return fail(c, BAB_ERR_UNSUPPORTED, "%s in TF32x3 takes the squared-distance cost", what);
+        if (!crown_tf32_supported(c->net, c->max_smem))
+            return fail(c, BAB_ERR_UNSUPPORTED, "TF32x3 CROWN needs hidden widths that are multiples of 32 and every "
+                                                "width at most 128, s <= 32");
+        return BAB_OK;
+    }
+    if (precision != BAB_PREC_FP32) return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
+    return BAB_OK;
+}
+
 // One pass of bab_bound_crown over rows row0 .. row0 + n - 1 (pointers already offset to row0).
 static int bound_crown_pass(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo,
                             const float *hi, int n, const int *d_n, int row0, const float *alpha, int precision,
                             float *lb, float *margin, float *lin_coef, float *lin_const, void *stream)
 {
-    const bool tc = precision == BAB_PREC_BF16X3;
+    const bool tc = precision != BAB_PREC_FP32;
     int rc = ensure_scratch(c, bound_scratch_bytes(c->net, n, H, c->net.k * H, tc));
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1059,15 +1141,8 @@ static int bound_crown_pass(bab_ctx *c, const float *x0, const float *goal, int 
     a.margin = margin;
     a.lin_coef = lin_coef;
     a.lin_const = lin_const;
-    cudaError_t e;
-    if (tc) {
-        a.tcb_img = c->d_tcb;
-        a.tc_bias = c->d_tc_bias;
-        a.mu = lin_coef ? lin_coef : cv.take<float>((size_t)n * a.d);
-        e = launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st);
-    } else {
-        e = launch_crown(a, c->num_sms, st);
-    }
+    if (tc) a.mu = lin_coef ? lin_coef : cv.take<float>((size_t)n * a.d);
+    cudaError_t e = launch_crown_prec(c, a, precision, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
     return BAB_OK;
 }
@@ -1078,14 +1153,9 @@ int bab_bound_crown(bab_ctx *c, const float *x0, const float *goal, int H, float
 {
     int rc = check_problem(c, x0, goal, H, rho, lo, hi, n);
     if (rc) return rc;
-    if (precision == BAB_PREC_BF16X3 && (rc = check_tc_obstacles(c, "the tensor-core CROWN")) != BAB_OK) return rc;
     if (n > 0 && !lb) return fail(c, BAB_ERR_INVALID_ARG, "lb is required");
-    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
-        return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
-    const bool tc = precision == BAB_PREC_BF16X3;
-    if (tc && !crown_tc_supported(c->net, c->max_smem))
-        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN needs hidden widths that are multiples of 32, "
-                                            "s <= 32, s + k <= 48 and a weight image that fits in shared memory");
+    if ((rc = check_crown_precision(c, precision, "the tensor-core CROWN")) != BAB_OK) return rc;
+    const bool tc = precision != BAB_PREC_FP32;
     if (n == 0) return BAB_OK;
     const int d = c->net.k * H;
     const size_t per_row = bound_scratch_bytes(c->net, 1, H, d, tc) - 16 * 256 + (tc && !lin_coef ? (size_t)d * 4 : 0);
@@ -1142,29 +1212,15 @@ int alpha_grad_core(bab_ctx *c, BoundArgs &a, Carver &cv, int precision, const f
     a.grad_alpha = grad_alpha ? grad_alpha : cv.take<float>(nh);
     a.lb = lb ? lb : cv.take<float>(n);
     a.lb_best = lb_best;
-    cudaError_t e;
-    if (precision == BAB_PREC_BF16X3) {
-        a.tcb_img = c->d_tcb;
-        a.tc_bias = c->d_tc_bias;
-        a.mu = cv.take<float>((size_t)n * d);
-        e = launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st);
-    } else {
-        e = launch_crown(a, c->num_sms, st);
-    }
+    if (precision != BAB_PREC_FP32) a.mu = cv.take<float>((size_t)n * d);
+    cudaError_t e = launch_crown_prec(c, a, precision, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "CROWN kernel");
     e = launch_alpha_fwd(a, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha adjoint kernel");
     return BAB_OK;
 }
 
-int check_bound_precision(bab_ctx *c, int precision)
-{
-    if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3)
-        return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);
-    if (precision == BAB_PREC_BF16X3 && !crown_tc_supported(c->net, c->max_smem))
-        return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core CROWN is not available for this network");
-    return BAB_OK;
-}
+int check_bound_precision(bab_ctx *c, int precision) { return check_crown_precision(c, precision, "the alpha step"); }
 
 }  // namespace
 
@@ -1313,8 +1369,6 @@ static int alpha_optimize_pass(bab_ctx *c, const float *x0, const float *goal, i
     a.grad_alpha = cv.take<float>(nh);
     a.lb = cv.take<float>(n);
     a.mu = cv.take<float>((size_t)n * d);
-    a.tcb_img = c->d_tcb;
-    a.tc_bias = c->d_tc_bias;
     a.alpha = al;
     cudaError_t e = launch_alpha_init(a, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(m, 0, nh * sizeof(float), st);
@@ -1323,7 +1377,7 @@ static int alpha_optimize_pass(bab_ctx *c, const float *x0, const float *goal, i
     if (e != cudaSuccess) return cuda_fail(c, e, "alpha set-up");
     a.lb_best = lb_best;
     for (int step = 1; step <= steps; ++step) {
-        e = precision == BAB_PREC_BF16X3 ? launch_crown_tc(a, c->tune_crown_tc, c->num_sms, st) : launch_crown(a, c->num_sms, st);
+        e = launch_crown_prec(c, a, precision, st);
         if (e == cudaSuccess) e = launch_alpha_fwd(a, c->num_sms, st);
         const double bc1 = 1.0 - std::pow(0.9, step), bc2 = 1.0 - std::pow(0.999, step);
         if (e == cudaSuccess) e = launch_adam(al, m, v, a.grad_alpha, (long long)nh, lr, (float)bc1, (float)bc2, st);

@@ -75,9 +75,15 @@ struct NetDesc {
     int ibp_ok, ibp_bytes;
     int ibp_mb[kMaxLayers + 1], ibp_ka[kMaxLayers + 1], ibp_off[kMaxLayers + 1];
     float gam_ibp[kMaxLayers + 1];
+    // backward TF32 image (3-term TF32 split products): per layer l, K = tf_K[l] = d_l rounded up to 8, in blocks
+    // of 32 (128 bytes a row); block kb at tf_off[l] + 2 kb tcb_N[l] 128 bytes: tcb_N[l] rows of the hi halves, then
+    // as many of the lo halves (swizzled K-major); gam_tf[l] = gamma_tf32(tf_K[l])
+    int tf_K[kMaxLayers + 1], tf_off[kMaxLayers + 1], tf_bytes;
+    float gam_tf[kMaxLayers + 1];
 };
 
 __host__ __device__ constexpr int pad16(int x) { return (x + 15) & ~15; }
+__host__ __device__ constexpr int pad8(int x) { return (x + 7) & ~7; }
 
 // ---------------------------------------------------------------------------
 // Counter-based sampling: SplitMix64 output function (Steele, Lea and Flood,
@@ -209,6 +215,14 @@ __host__ __device__ __forceinline__ float gamma_split(int K)
 {
     const double u = 1.1920928955078125e-07;  // 2^-23
     return (float)(3.1 * 1.52587890625e-05 + K * u / (1.0 - K * u)) * 1.000001f;
+}
+
+// The same bound for a 3-term TF32 split (11 significant bits per half, so each operand's representation error
+// and the dropped lo x lo term are at most about 2^-22 of |a| |b| each).
+__host__ __device__ __forceinline__ float gamma_tf32(int K)
+{
+    const double u = 1.1920928955078125e-07;  // 2^-23
+    return (float)(3.1 * 2.384185791015625e-07 + K * u / (1.0 - K * u)) * 1.000001f;
 }
 
 __device__ __forceinline__ int live_count(int n, const int *d_n)

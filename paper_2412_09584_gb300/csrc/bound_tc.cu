@@ -650,11 +650,17 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
 // tensor core runs the current product.  Each thread keeps, per box, partial sums over its features of the
 // constant (rounded down) and of the rounding-error margin (rounded up); a warp shuffle and the four quadrant
 // warps reduce them per box at the end of the tile.  The state lanes (j < s) carry the coefficient of the state
-// from step to step, the action lanes (s <= j < s + k) write mu.  Squared-distance cost, resident image, every
-// width at most 128.
+// from step to step, the action lanes (s <= j < s + k) write mu.  Squared-distance cost, every width at most 128.
+// TF = false: 3-term BF16 split products, the backward image resident in shared memory.  TF = true: 3-term TF32
+// split products (kind::tf32, K = 8 per instruction), the image (twice the BF16 one) streamed by a producer warp
+// through a ring of 32-wide K blocks in the issuer's order.
 // ---------------------------------------------------------------------------------------------------------------
 constexpr int kNB = 32;   // boxes per tile: the MMA's N
-constexpr uint32_t kBopHalf = 2 * kNB * 128;  // one half (hi or lo) of the B operand: K <= 128 in two 64-wide blocks
+constexpr uint32_t kBopHalf = 2 * kNB * 128;    // one half (hi or lo) of the B operand: K <= 128 in two 64-wide blocks
+constexpr uint32_t kBopHalfTf = 4 * kNB * 128;  // the same with TF32 halves: four 32-wide blocks
+constexpr uint32_t kTfHalf = 128 * 128;         // TF32 ring stage: one 32-wide K block of the image, 128 rows of hi,
+constexpr uint32_t kTfStage = 2 * kTfHalf;      // then 128 rows of lo
+constexpr int kTfMaxStages = 6;
 
 // byte offset of element (box n, k) in the K-major 128-byte-swizzled B operand of kNB rows
 __device__ __forceinline__ uint32_t bop_off(int n, int k)
@@ -669,6 +675,26 @@ __device__ __forceinline__ void st_bf16_pair(uint8_t *bop, uint32_t off, float v
     const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
     *reinterpret_cast<__nv_bfloat16 *>(bop + off) = h;
     *reinterpret_cast<__nv_bfloat16 *>(bop + kBopHalf + off) = l;
+}
+// the TF32 operand: 32 elements of 4 bytes per 128-byte block
+__device__ __forceinline__ uint32_t bop_off_tf(int n, int k)
+{
+    const int kb = k >> 5, w = k & 31;
+    return (uint32_t)(kb * kNB * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((w >> 2) ^ (n & 7)) << 4) + ((w & 3) << 2));
+}
+// v as hi = tf32(v) and lo = tf32(v - hi) (v - hi is exact in FP32)
+__device__ __forceinline__ void st_tf32_pair(uint8_t *bop, uint32_t off, float v)
+{
+    const float h = tc::tf32_rna(v);
+    *reinterpret_cast<float *>(bop + off) = h;
+    *reinterpret_cast<float *>(bop + kBopHalfTf + off) = tc::tf32_rna(v - h);
+}
+// element (box n, k) of the split B operand in the kernel's arithmetic
+template <bool TF>
+__device__ __forceinline__ void st_split(uint8_t *bop, int n, int k, float v)
+{
+    if (TF) st_tf32_pair(bop, bop_off_tf(n, k), v);
+    else st_bf16_pair(bop, bop_off(n, k), v);
 }
 
 // Lemma 1's relaxation without branches (the lanes of a warp hold different neurons).  The upper slope of an
@@ -695,18 +721,21 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 __device__ __forceinline__ void tmem_ld_bpt(uint32_t taddr, uint32_t (&r)[16]) { tc::tmem_ld16(taddr, r); }
 __device__ __forceinline__ void tmem_ld_bpt(uint32_t taddr, uint32_t (&r)[8]) { tc::tmem_ld8(taddr, r); }
 
-template <bool ALPHA, int WQ>
-__global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
+template <bool ALPHA, int WQ, bool TF>
+__global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_tcf(BoundArgs a)
 {
     constexpr int NE = 4 * WQ, BPT = kNB / WQ;  // epilogue warps, boxes per epilogue thread
+    constexpr uint32_t kHalf = TF ? kBopHalfTf : kBopHalf;
     extern __shared__ uint8_t smem_raw[];
     const NetDesc &N = a.net;
+    // the resident image, or the TF32 ring of a.stages stages
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *bop = wimg + (((size_t)N.tcb_bytes + 1023) & ~size_t(1023));
-    float *bias = reinterpret_cast<float *>(bop + 2 * kBopHalf);
+    uint8_t *bop = wimg + (TF ? (size_t)a.stages * kTfStage : (((size_t)N.tcb_bytes + 1023) & ~size_t(1023)));
+    float *bias = reinterpret_cast<float *>(bop + 2 * kHalf);
     float *red = bias + ((N.tc_bias_floats + 3) & ~3);  // [2 tile parities][4 quadrants][kNB][2]
     float *small = red + 2 * 4 * kNB * 2;               // [WQ][32 lanes][2 step parities][3][BPT]
     __shared__ uint64_t bar_w, bar_a, bar_d, bar_r, bar_fin;
+    __shared__ uint64_t bar_full[TF ? kTfMaxStages : 1], bar_empty[TF ? kTfMaxStages : 1];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -720,6 +749,11 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
         tc::mbar_init(&bar_d, 1);
         tc::mbar_init(&bar_r, NE);
         tc::mbar_init(&bar_fin, 1);
+        if (TF)
+            for (int i = 0; i < a.stages; ++i) {
+                tc::mbar_init(&bar_full[i], 1);
+                tc::mbar_init(&bar_empty[i], 1);
+            }
         tc::mbar_init_fence();
     }
     if (warp == NE) tc::tmem_alloc(&tmem_base, 32);
@@ -727,12 +761,14 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (threadIdx.x == NE * 32) {
-        tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
-        for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
-            tc::bulk_g2s(wimg + off, a.tcb_img + off, min(32768u, (uint32_t)N.tcb_bytes - off), &bar_w);
+    if (!TF) {
+        if (threadIdx.x == NE * 32) {
+            tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
+            for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
+                tc::bulk_g2s(wimg + off, a.tcb_img + off, min(32768u, (uint32_t)N.tcb_bytes - off), &bar_w);
+        }
+        if (!wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
     }
-    if (!wwait(&bar_w, 0, abort) && lane == 0) abort_all(a.status, abort);
 
     const int nlive = live_count(a.n, a.d_n, a.row0);
     const int ntiles = (nlive + kNB - 1) / kNB;
@@ -803,17 +839,17 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
             for (int t = H - 1; t >= 0 && ok; --t) {
                 const float *sx = sm + (t & 1) * 3 * BPT;
                 // ---- output layer: B = lam (zero up to K), constant lam . b_L, margin of the product ----
-                if (q == 0 && j < N.tcb_K[L]) {
+                if (q == 0 && j < (TF ? N.tf_K[L] : N.tcb_K[L])) {
                     float bL = 0.f;
                     if (state) {
                         cp_wait<0>();
                         bL = bias[N.tc_boff[L] + j];
                     }
-                    const float gL = N.gam_tc[L];
+                    const float gL = TF ? N.gam_tf[L] : N.gam_tc[L];
 #pragma unroll
                     for (int bi = 0; bi < BPT; ++bi) {
                         const float v = state ? lam[bi] : 0.f;
-                        st_bf16_pair(bop, bop_off(BPT * h + bi, j), v);
+                        st_split<TF>(bop, BPT * h + bi, j, v);
                         if (state && box0 + bi < nlive) {
                             cp[bi] = __fmaf_rd(v, bL, cp[bi]);
                             mp[bi] = __fmaf_ru(__fmul_ru(gL, fabsf(v)), sx[bi], mp[bi]);
@@ -837,7 +873,7 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
                     tmem_ld_bpt(dcol, v);
                     tc::tmem_wait_ld();
                     if (j < N.dims[l]) {
-                        const float bj = bias[N.tc_boff[l] + j], gK = N.gam_tc[l];
+                        const float bj = bias[N.tc_boff[l] + j], gK = TF ? N.gam_tf[l] : N.gam_tc[l];
 #pragma unroll
                         for (int bi = 0; bi < BPT; ++bi) {
                             const bool vb = box0 + bi < nlive;
@@ -853,7 +889,7 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
                                 if (D != 0.f && D != 1.f)
                                     mp[bi] = __fmaf_ru(__fmul_ru(kTwoU, fabsf(Ap)), fmaxf(-pzl[bi], pzu[bi]), mp[bi]);
                             }
-                            st_bf16_pair(bop, bop_off(BPT * h + bi, j), Ap);
+                            st_split<TF>(bop, BPT * h + bi, j, Ap);
                         }
                     }
                     tc::fence_proxy_async_smem();
@@ -992,8 +1028,10 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
         long long left = cnt * H * L;
         int l = L;
         uint32_t phA = 0;
-        const uint32_t idesc = tc::idesc_bf16_f32(128, kNB);
-        const uint32_t bh = tc::desc_sw128_lo(tc::smem_u32(bop)), bl = tc::desc_sw128_lo(tc::smem_u32(bop + kBopHalf));
+        const uint32_t idesc = TF ? tc::idesc_tf32_f32(128, kNB) : tc::idesc_bf16_f32(128, kNB);
+        const uint32_t bh = tc::desc_sw128_lo(tc::smem_u32(bop)), bl = tc::desc_sw128_lo(tc::smem_u32(bop + kHalf));
+        uint32_t ring_it = 0;
+        bool ok = true;
         while (left > 0 && !*abort) {
             if (!tc::mbar_wait(&bar_a, phA, abort, kWaitNs)) {
                 abort_all(a.status, abort);
@@ -1001,17 +1039,44 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
             }
             phA ^= 1;
             tc::fence_after_sync();
-            const int nks = N.tcb_K[l] / 16, Nl = N.tcb_N[l];
-            const uint32_t ah = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_hi[l]));
-            const uint32_t al = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_lo[l]));
-            for (int ks = 0; ks < nks; ++ks) {
-                // 16-byte units: K-block ks / 4 of the operand, then 32 bytes per K = 16 step inside it
-                const uint32_t ao = (uint32_t)((ks >> 2) * Nl * 8 + (ks & 3) * 2);
-                const uint32_t bo = (uint32_t)((ks >> 2) * kNB * 8 + (ks & 3) * 2);
-                const uint64_t Ah = tc::desc_join(ah + ao), Bh = tc::desc_join(bh + bo);
-                tc::mma_ss(tb, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
-                tc::mma_ss(tb, tc::desc_join(al + ao), Bh, idesc, 1u);
-                tc::mma_ss(tb, Ah, tc::desc_join(bl + bo), idesc, 1u);
+            if (TF) {
+                // K = 8 per instruction, 32-wide blocks from the ring; each stage is released once its MMAs are done
+                const int nks = N.tf_K[l] / 8;
+                for (int kb = 0; kb < (nks + 3) / 4; ++kb, ++ring_it) {
+                    const uint32_t st = ring_it % (uint32_t)a.stages, ph = (ring_it / (uint32_t)a.stages) & 1u;
+                    if (!tc::mbar_wait(&bar_full[st], ph, abort, kWaitNs)) {
+                        abort_all(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t ah = tc::desc_sw128_lo(tc::smem_u32(wimg + (size_t)st * kTfStage));
+                    const uint32_t al = ah + (kTfHalf >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int ks = 4 * kb + kk;
+                        if (ks >= nks) break;
+                        const uint32_t bo = (uint32_t)(kb * kNB * 8 + kk * 2);
+                        const uint64_t Ah = tc::desc_join(ah + 2u * kk), Bh = tc::desc_join(bh + bo);
+                        tc::mma_ss_tf32(tb, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
+                        tc::mma_ss_tf32(tb, tc::desc_join(al + 2u * kk), Bh, idesc, 1u);
+                        tc::mma_ss_tf32(tb, Ah, tc::desc_join(bl + bo), idesc, 1u);
+                    }
+                    tc::mma_commit(&bar_empty[st]);
+                }
+                if (!ok) break;
+            } else {
+                const int nks = N.tcb_K[l] / 16, Nl = N.tcb_N[l];
+                const uint32_t ah = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_hi[l]));
+                const uint32_t al = tc::desc_sw128_lo(tc::smem_u32(wimg + N.tcb_lo[l]));
+                for (int ks = 0; ks < nks; ++ks) {
+                    // 16-byte units: K-block ks / 4 of the operand, then 32 bytes per K = 16 step inside it
+                    const uint32_t ao = (uint32_t)((ks >> 2) * Nl * 8 + (ks & 3) * 2);
+                    const uint32_t bo = (uint32_t)((ks >> 2) * kNB * 8 + (ks & 3) * 2);
+                    const uint64_t Ah = tc::desc_join(ah + ao), Bh = tc::desc_join(bh + bo);
+                    tc::mma_ss(tb, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_ss(tb, tc::desc_join(al + ao), Bh, idesc, 1u);
+                    tc::mma_ss(tb, Ah, tc::desc_join(bl + bo), idesc, 1u);
+                }
             }
             tc::mma_commit(&bar_d);
             l = (l == 1) ? L : l - 1;
@@ -1021,6 +1086,37 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
             volatile int never = 0;
             tc::mma_commit(&bar_fin);
             tc::mbar_wait(&bar_fin, 0, &never, kWaitNs);
+        }
+    } else if (TF && warp == NE + 1 && lane == 0) {
+        // ------------- producer: the TF32 image's K blocks in the issuer's order (t = H-1 .. 0, l = L .. 1) -------------
+        const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        uint32_t it = 0;
+        bool ok = true;
+        for (long long q = 0; q < cnt * H && ok && !*abort; ++q) {
+            for (int l = L; l >= 1 && ok; --l) {
+                const uint32_t rows = (uint32_t)N.tcb_N[l] * 128u;  // bytes of one half of a block
+                const int nb = (N.tf_K[l] / 8 + 3) / 4;
+                for (int kb = 0; kb < nb; ++kb, ++it) {
+                    const uint32_t st = it % (uint32_t)a.stages, ph = (it / (uint32_t)a.stages) & 1u;
+                    if (!tc::mbar_wait(&bar_empty[st], ph ^ 1u, abort, kWaitNs)) {
+                        abort_all(a.status, abort);
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *dst = wimg + (size_t)st * kTfStage;
+                    const uint8_t *src = a.tcb_img + N.tf_off[l] + (size_t)kb * 2 * rows;
+                    tc::mbar_arrive_expect_tx(&bar_full[st], 2u * rows);
+                    tc::bulk_g2s(dst, src, rows, &bar_full[st]);
+                    tc::bulk_g2s(dst + kTfHalf, src + rows, rows, &bar_full[st]);
+                }
+            }
+        }
+        // copies still in flight must land before the shared memory is released
+        volatile int never = 0;
+        const uint32_t inflight = it < (uint32_t)a.stages ? it : (uint32_t)a.stages;
+        for (uint32_t j2 = 0; j2 < inflight; ++j2) {
+            const uint32_t i2 = it - 1 - j2, st = i2 % (uint32_t)a.stages;
+            tc::mbar_wait(&bar_full[st], (i2 / (uint32_t)a.stages) & 1u, &never, kWaitNs);
         }
     }
     tc::fence_before_sync();
@@ -1032,10 +1128,49 @@ __global__ void __launch_bounds__((4 * WQ + 1) * 32, 1) k_crown_tcf(BoundArgs a)
     }
 }
 
-// shared memory of k_crown_tcf beyond the image
-static size_t crown_tcf_extra(const NetDesc &N)
+// shared memory of k_crown_tcf beyond the image (BF16) or the ring (TF32)
+static size_t crown_tcf_extra(const NetDesc &N, bool tf = false)
 {
-    return 1024 + 1024 + 2 * kBopHalf + ((size_t)((N.tc_bias_floats + 3) & ~3) + 2 * 4 * kNB * 2 + 32 * 2 * 3 * kNB) * 4;
+    return 1024 + 1024 + 2 * (size_t)(tf ? kBopHalfTf : kBopHalf) +
+           ((size_t)((N.tc_bias_floats + 3) & ~3) + 2 * 4 * kNB * 2 + 32 * 2 * 3 * kNB) * 4;
+}
+
+// ring stages of the TF32 kernel that fit beside the rest of its shared memory
+static int crown_tf32_stages(const NetDesc &N, int max_smem)
+{
+    const size_t extra = crown_tcf_extra(N, true);
+    if (extra >= (size_t)max_smem) return 0;
+    const int st = (int)(((size_t)max_smem - extra) / kTfStage);
+    return st > kTfMaxStages ? kTfMaxStages : st;
+}
+
+// 3-term TF32 split CROWN: the feature-major kernel's conditions (squared-distance cost, every width at most 128),
+// with at least two ring stages
+bool crown_tf32_supported(const NetDesc &N, int max_smem)
+{
+    for (int l = 0; l <= N.L; ++l)
+        if (N.dims[l] > 128) return false;
+    return N.tc_ok && N.L >= 2 && N.s <= 32 && N.tf_K[N.L] <= 32 && crown_tf32_stages(N, max_smem) >= 2;
+}
+
+cudaError_t launch_crown_tf32(BoundArgs a, int num_sms, cudaStream_t st)
+{
+    const NetDesc &N = a.net;
+    if (a.n <= 0) return cudaSuccess;
+    int dev, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (a.cost.kind != 0 || !crown_tf32_supported(N, max_smem)) return cudaErrorNotSupported;
+    a.stages = crown_tf32_stages(N, max_smem);
+    a.stage_bytes = (int)kTfStage;
+    const size_t smem = (size_t)a.stages * kTfStage + crown_tcf_extra(N, true);
+    const int ntiles = (a.n + kNB - 1) / kNB;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    auto kern = a.alpha ? k_crown_tcf<true, 4, true> : k_crown_tcf<false, 4, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, (4 * 4 + 2) * 32, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 // The feature-major kernel: squared-distance cost, every width at most 128 (the MMA's 128 rows), the image resident
@@ -1132,8 +1267,8 @@ cudaError_t launch_crown_tc(BoundArgs a, int variant, int num_sms, cudaStream_t 
         const int ntiles = (a.n + kNB - 1) / kNB;
         const int grid = ntiles < num_sms ? ntiles : num_sms;
         const int wq = variant == 3 ? 2 : 4;  // epilogue warps per TMEM lane quadrant
-        auto kern = wq == 2 ? (a.alpha ? k_crown_tcf<true, 2> : k_crown_tcf<false, 2>)
-                            : (a.alpha ? k_crown_tcf<true, 4> : k_crown_tcf<false, 4>);
+        auto kern = wq == 2 ? (a.alpha ? k_crown_tcf<true, 2, false> : k_crown_tcf<false, 2, false>)
+                            : (a.alpha ? k_crown_tcf<true, 4, false> : k_crown_tcf<false, 4, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, (4 * wq + 1) * 32, smem, st>>>(a);

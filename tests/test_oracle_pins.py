@@ -1094,12 +1094,31 @@ def test_obstacle_penalty_relaxation_brute_force(oracle):
 # Outward rounding margin of an FP32 / split-BF16 evaluation (oracle_crown_margin)
 # --------------------------------------------------------------------------
 
-def _fp32_chain(p, lo, hi, pl, pu, xl, xu, A_pre, order, seed=0):
+def _round_half(x, kind):
+    """x (float32 array) rounded to the high half of a split: 'bf16' to nearest even with 8 significant bits,
+    'tf32' to nearest (ties away from zero) with 11, written out on the bit patterns."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    if kind == "bf16":
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    else:
+        u = (u + 0x1000) & 0xFFFFE000
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(x))
+
+
+def _split(x, kind):
+    """(hi, lo) with hi = round(x), lo = round(x - hi): the operand halves of a 3-term split product."""
+    x = np.asarray(x, np.float32)
+    h = _round_half(x, kind)
+    return h, _round_half((x - h).astype(np.float32), kind)
+
+
+def _fp32_chain(p, lo, hi, pl, pu, xl, xu, A_pre, order, seed=0, split=None):
     """The coefficient chain of the CROWN bound evaluated in FP32 (numpy float32, one rounding per multiply and
     per add, products summed in `order`: 'fwd', 'rev' or 'perm'), with the oracle's relaxation choices (lower line
     where the oracle's pre-relaxation coefficient is >= 0) and every constant term and the concretization taken
-    in FP64 from the FP32 coefficients.  Returns the bound per box; its distance from the FP64 bound is the
-    rounding the margin has to cover."""
+    in FP64 from the FP32 coefficients.  split = 'bf16' or 'tf32': every product A W is the 3-term split product
+    A_hi W_hi + A_hi W_lo + A_lo W_hi instead, its terms accumulated in FP32.  Returns the bound per box; its
+    distance from the FP64 bound is the rounding the margin has to cover."""
     f32 = np.float32
     layers = W.unpack_params(p)
     L, s, k, H, rho = len(layers), p["s"], p["k"], p["H"], float(p["rho"])
@@ -1115,8 +1134,14 @@ def _fp32_chain(p, lo, hi, pl, pu, xl, xu, A_pre, order, seed=0):
         idx = np.arange(K) if order == "fwd" else (np.arange(K)[::-1] if order == "rev" else rng.permutation(K))
         acc = np.zeros((A.shape[0], Wl.shape[1]), f32)
         W32 = Wl.astype(f32)
+        if split is None:
+            terms = [(A, W32)]
+        else:
+            (Ah, Al), (Wh, Wlo) = _split(A, split), _split(W32, split)
+            terms = [(Ah, Wh), (Ah, Wlo), (Al, Wh)]
         for kk in idx:
-            acc = (acc + (A[:, kk:kk + 1] * W32[kk][None, :]).astype(f32)).astype(f32)
+            for a_, w_ in terms:
+                acc = (acc + (a_[:, kk:kk + 1] * w_[kk][None, :]).astype(f32)).astype(f32)
         return acc
 
     out = np.zeros(n)
@@ -1183,6 +1208,43 @@ def test_margin_covers_fp32_evaluations(oracle, s, k, hidden, H, rho, wscale, ma
     # the split-BF16 margin charges 3.1 * 2^-16 per product term on top of its FP32 accumulation: larger
     r1 = oracle.crown_margin(p, lo, hi, prec=1)
     assert np.all(r1["margin"] > 10 * r["margin"])
+    # the split-TF32 margin charges 3.1 * 2^-22 and accumulation at unit 2^-23: between the two
+    r2 = oracle.crown_margin(p, lo, hi, prec=2)
+    assert np.all(r2["margin"] > r["margin"]) and np.all(r2["margin"] < r1["margin"])
+
+
+@pytest.mark.parametrize("prec,split", [(1, "bf16"), (2, "tf32")])
+@pytest.mark.parametrize("s,k,hidden,H,rho,wscale,maxw", [(4, 2, [32, 32], 5, 0.0, 0.3, 1.0),
+                                                          (8, 2, [128, 128], 3, 0.01, 0.3, 1.0)])
+def test_margin_covers_split_evaluations(oracle, prec, split, s, k, hidden, H, rho, wscale, maxw):
+    """The margin of a 3-term split evaluation covers the chain with every product evaluated as
+    A_hi W_hi + A_hi W_lo + A_lo W_hi from BF16 or TF32 halves (accumulated in FP32, in two orders), and the
+    chain does differ from the exact bound by more than the FP32 chain's rounding alone."""
+    p = W.make_problem(s, k, hidden, H, rho, seed=33, weight_scale=wscale)
+    lo, hi, _ = W.random_boxes(k * H, 5, seed=34, min_width=0.1, max_width=maxw)
+    _, pl, pu, xl, xu = oracle.ibp(p, lo, hi)
+    o = oracle.crown(p, lo, hi)
+    r = oracle.crown_margin(p, lo, hi, prec=prec)
+    np.testing.assert_allclose(r["lb"], o["lb"], rtol=1e-14, atol=1e-12)
+    worst = 0.0
+    for order in ("fwd", "rev"):
+        v = _fp32_chain(p, lo, hi, pl, pu, xl, xu, o["A_pre"], order, split=split)
+        assert np.all(v - r["margin"] <= r["lb"] + 1e-12 * np.abs(r["lb"])), order
+        worst = max(worst, float(np.max(np.abs(v - r["lb"]) / r["margin"])))
+    assert worst > 0
+
+
+def test_split_halves_representation_error():
+    """The halves the split margins assume: |x - hi| <= 2^-(p) |x| and |x - hi - lo| <= 2^-(2p) |x| with p = 8
+    (BF16) and 11 (TF32) significant bits, hi and lo exactly representable in the half format (low bits zero)."""
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal(20000) * np.exp2(rng.integers(-30, 30, 20000))).astype(np.float32)
+    for kind, pbits, low in (("bf16", 8, 0xFFFF), ("tf32", 11, 0x1FFF)):
+        h, l = _split(x, kind)
+        xd, hd, ld = x.astype(np.float64), h.astype(np.float64), l.astype(np.float64)
+        assert np.all(np.abs(xd - hd) <= 2.0 ** -pbits * np.abs(xd))
+        assert np.all(np.abs(xd - hd - ld) <= 2.0 ** (-2 * pbits) * np.abs(xd))
+        assert np.all((h.view(np.uint32) & low) == 0) and np.all((l.view(np.uint32) & low) == 0)
 
 
 def test_margin_single_step_linear_closed_form(oracle):
@@ -1211,6 +1273,10 @@ def test_margin_single_step_linear_closed_form(oracle):
     got = oracle.crown_margin(p, lo, hi)["margin"][0]
     assert got == pytest.approx(expect, rel=1e-12)
     assert r_.shape == (s,)
+    # 3-term TF32 split: 3.1 * 2^-22 plus gamma_8 with unit 2^-23 (3 terms rounded up to a multiple of 8)
+    g8 = 3.1 * 2.0 ** -22 + 8 * 2.0 ** -23 / (1 - 8 * 2.0 ** -23)
+    expect2 = g8 * np.abs(lam) @ np.abs(Wm) @ amax + 2.0 ** -23 * (np.abs(lam) + np.abs(lam @ Wm[:, :s])) @ np.abs(x0)
+    assert oracle.crown_margin(p, lo, hi, prec=2)["margin"][0] == pytest.approx(expect2, rel=1e-12)
 
 
 def test_margin_scales_with_square_of_homogeneous_scaling(oracle):
