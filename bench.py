@@ -39,8 +39,10 @@ sys.path.insert(0, ROOT)
 SEED = 2024
 METRIC = "CROWN subdomain-bounds/s & rollout-steps/s at H=20"
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+BOUND_PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 3}
 ARITH = {"fp32": "FP32 CUDA cores", "bf16x3": "tcgen05, 3-term BF16 split, FP32 accumulate",
-         "bf16": "tcgen05, BF16 operands, FP32 accumulate, FP32 re-score of each box's pick"}
+         "bf16": "tcgen05, BF16 operands, FP32 accumulate, FP32 re-score of each box's pick",
+         "tf32x3": "tcgen05, 3-term TF32 split, FP32 accumulate"}
 
 
 def dist_env():
@@ -217,7 +219,7 @@ class BabState:
         self.n_pick = n_pick
         self.nb = 2 * n_pick
         self.seed = seed
-        self.rprec, self.bprec = PRECISIONS[rollout_prec], PRECISIONS[bound_prec]
+        self.rprec, self.bprec = PRECISIONS[rollout_prec], BOUND_PRECISIONS[bound_prec]
         self.alpha_steps, self.alpha_lr = alpha_steps, alpha_lr
         self.ctx = B.bab_load_dynamics(self.p["dims"], self.p["params"], self.p["s"], self.p["k"])
         self.iprec = interval_prec
@@ -547,8 +549,8 @@ def run_ours(args):
            "bound_arithmetic": ("interval bounds on tcgen05 (3-term BF16 split, computed margin)"
                                 if args.interval_precision == "bf16x3" else "outward-rounded FP32 intervals") +
                                "; CROWN products " +
-                               ("on tcgen05, 3-term BF16 split" if args.bound_precision == "bf16x3"
-                                else "in FP32 on CUDA cores") + ", margin-corrected",
+                               {"bf16x3": "on tcgen05, 3-term BF16 split", "tf32x3": "on tcgen05, 3-term TF32 split",
+                                "fp32": "in FP32 on CUDA cores"}[args.bound_precision] + ", margin-corrected",
            "boxes_per_step": st.nb, "samples_per_box": st.M, "H": st.H,
            "initial_pool": f"{st.nb}-box grid over [-1,1]^{st.d}", "l2": "flushed between steps (256 MiB write)",
            "timed_region": "CUDA-graph replays of the whole iteration" if graphs is not None else "eager launches",
@@ -583,6 +585,8 @@ def precision_lines(dev, seed, n_pick, headline, bound_precision, interval_preci
     other_int = "fp32" if interval_precision == "bf16x3" else "bf16x3"
     combos = [(p, bound_precision, interval_precision) for p in ("fp32", "bf16x3", "bf16") if p != headline]
     combos += [(headline, other_bound, interval_precision), (headline, bound_precision, other_int)]
+    if bound_precision != "tf32x3":
+        combos.append((headline, "tf32x3", interval_precision))
     for prec, bprec, iprec in combos:
         key = prec if bprec == bound_precision else f"{prec}, {bprec} CROWN products"
         if iprec != interval_precision:
@@ -1384,8 +1388,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--interval-precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="interval bounds: fp32 (directed rounding, CUDA cores) or bf16x3 (tcgen05, computed margin)")
-    ap.add_argument("--bound-precision", choices=["fp32", "bf16x3"], default="bf16x3",
-                    help="CROWN products: fp32 (CUDA cores) or bf16x3 (tcgen05, 3-term split, margin-corrected)")
+    ap.add_argument("--bound-precision", choices=sorted(BOUND_PRECISIONS), default="bf16x3",
+                    help="CROWN products: fp32 (CUDA cores), bf16x3 or tf32x3 (tcgen05, 3-term split, "
+                         "margin-corrected)")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="bf16",
                     help="rollout arithmetic: fp32 (CUDA cores), bf16x3 (tcgen05, 3-term split), bf16 (tcgen05)")
     ap.add_argument("--boxes", type=int, default=4096,
