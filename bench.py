@@ -1073,7 +1073,8 @@ def obstacle_bab(dev, iters=30):
     """Algorithm 2 with the pushing-with-obstacles cost (Appendix D.4: weighted norm to the target, w_t = t / H,
     plus lambda = 10 times the obstacle penalties of the pusher and the 4 keypoints; 3 obstacles) on the pushing
     network: 512 children per iteration, 1024 BF16x3 rollouts each (uniform, or the warm-started cross-entropy
-    search 4 x 256 in FP32), sound FP32 interval + CROWN bounds, or alpha-CROWN (20 Adam steps per iteration)."""
+    search 4 x 256 in FP32), sound FP32 interval + CROWN bounds, or alpha-CROWN (20 Adam steps per iteration); and
+    the headline arithmetic (BF16 rollouts with the picks re-scored in FP32, CROWN on tensor cores)."""
     import torch
     from paper_2412_09584_gb300 import workloads as W
     p = W.config_problem("pushing", SEED)
@@ -1083,11 +1084,13 @@ def obstacle_bab(dev, iters=30):
            "obstacles": [[round(v, 4) for v in o] for o in cost["obstacles"]]}
     variants = (("uniform_bf16x3", dict(rollout_prec="bf16x3")),
                 ("cem_fp32_4x256", dict(rollout_prec="fp32", cem={"iters": 4, "elites": 10, "jitter": 1e-3})),
-                ("uniform_bf16x3_alpha20", dict(rollout_prec="bf16x3", alpha_steps=20)))
+                ("uniform_bf16x3_alpha20", dict(rollout_prec="bf16x3", alpha_steps=20)),
+                ("uniform_bf16_tc_crown", dict(rollout_prec="bf16", bound_prec="bf16x3")))
     # one untimed pass first, so that no variant is timed while the clocks ramp up
     for name, kw in (("warm-up", variants[0][1]),) + variants:
         for warm in (True, False):
-            st = BabState("pushing", SEED, dev, 256, bound_prec="fp32", pool_iters=iters + 2, cost=cost, **kw)
+            kw2 = dict(bound_prec="fp32", **kw) if "bound_prec" not in kw else kw
+            st = BabState("pushing", SEED, dev, 256, pool_iters=iters + 2, cost=cost, **kw2)
             torch.cuda.synchronize()
             t = time.perf_counter()
             inc, gaps = [], []

@@ -402,14 +402,15 @@ int bab_rollout_split(bab_ctx *ctx, const float *x0, const float *goal, int hori
  * obstacles [n_obs][3] (x, y, size), n_obs <= 8, p0 [2].  The context keeps a
  * device copy; kind BAB_COST_SQUARED clears it.
  *
- * Paths that support the obstacle cost: bab_rollout (FP32, and BF16X3 for
- * s <= 8), bab_rollout_cem (FP32), bab_update_incumbent, bab_bound_ibp,
- * bab_bound_crown (FP32, adaptive or given slopes), bab_alpha_init and the
- * FP32 alpha calls (bab_alpha_grad, bab_alpha_step, bab_alpha_optimize; the
- * optimisation then runs as separate launches or in the shared-memory tiles,
- * not as the warp-per-box loop); the other bound paths (tensor-core CROWN and
- * alpha, early stop, batched problems, the static entry point, the box
- * gradient) and BF16 rollouts return BAB_ERR_UNSUPPORTED.
+ * Paths that support the obstacle cost: bab_rollout (FP32; BF16X3 and BF16
+ * for s <= 8, BF16 with each box's pick re-scored in FP32 under this cost),
+ * bab_rollout_cem (FP32), bab_update_incumbent, bab_bound_ibp (FP32
+ * intervals, whatever bab_set_interval_precision selects), bab_bound_crown
+ * (FP32, adaptive or given slopes; BF16X3 when the backward image fits in
+ * shared memory), bab_alpha_init and the alpha calls (bab_alpha_grad,
+ * bab_alpha_step, bab_alpha_optimize, in the same precisions); the other
+ * paths (TF32X3, the tensor-core cross-entropy search, early stop, batched
+ * problems, the box gradient, the autotuner) return BAB_ERR_UNSUPPORTED.
  * Sound as for the squared cost: interval minima per term rounded down; in
  * CROWN the norm by its tangent plane at the box centre (w ||y|| >= w ghat . y,
  * |ghat| <= 1), each penalty by an affine function below the concave

@@ -776,8 +776,8 @@ int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rh
     if (precision != BAB_PREC_FP32 && precision != BAB_PREC_BF16X3 && precision != BAB_PREC_BF16)
         return fail(c, BAB_ERR_INVALID_ARG, "unknown precision %d", precision);
     const int split = precision == BAB_PREC_BF16X3 ? 3 : 1;
-    if (c->cost.kind != 0 && (precision == BAB_PREC_BF16 || (precision == BAB_PREC_BF16X3 && c->net.s > 8)))
-        return refuse_obstacles(c, "BF16 rollouts (and tensor-core rollouts with more than 8 states)");
+    if (c->cost.kind != 0 && precision != BAB_PREC_FP32 && c->net.s > 8)
+        return refuse_obstacles(c, "tensor-core rollouts with more than 8 states");
     if (precision != BAB_PREC_FP32 && !rollout_tc_supported(c->net, split, c->max_smem))
         return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout needs hidden widths that are multiples of 32, "
                                             "s <= 32, s + k <= 64 and a weight image that fits in shared memory");

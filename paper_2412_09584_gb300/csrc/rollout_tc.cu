@@ -1016,6 +1016,7 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
     for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = x0[i];
     if (threadIdx.x == 0) f_sh = 0.f;
+    float px = a.cost.p0x, py = a.cost.p0y;  // pusher position (obstacle cost; thread 0)
     __syncthreads();
     for (int t = 0; t < Hb; ++t) {
         for (int c = threadIdx.x; c < s + k; c += blockDim.x)
@@ -1040,6 +1041,8 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
             for (int j = 0; j < k; ++j) {
                 const float u = draw_sample(hb, m, (uint32_t)(t * k + j), blo[t * k + j], bhi[t * k + j]);
                 f = fmaf(rho * u, u, f);
+                if (a.cost.kind == 1 && j == 0) px = __fadd_rn(px, u);
+                if (a.cost.kind == 1 && j == 1) py = __fadd_rn(py, u);
             }
             float c = 0.f;
             for (int i = 0; i < s; ++i) {
@@ -1047,6 +1050,7 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
                 const float e = xs[i] - goal[i];
                 c = fmaf(e, e, c);
             }
+            if (a.cost.kind == 1) c = obstacle_cost_f32(a.cost, t + 1, s, xs, goal, px, py);
             f_sh = f + c;
         }
         __syncthreads();
@@ -1061,6 +1065,7 @@ constexpr int kRescoreRows = 28;  // 4096 boxes make 147 CTAs: one wave on 152 S
 // 512 threads: a 128-wide layer of the tile is 448 register tiles of 2 rows x 4 columns, one per thread (256
 // threads took two each, 0.49 ms for 4096 boxes)
 constexpr int kRescoreThreads = 512;
+static_assert(kRescoreRows <= kRescoreThreads, "one thread per row keeps that row's pusher position");
 template <bool WSMEM>
 __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
 {
@@ -1095,6 +1100,7 @@ __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
         fsum[r] = 0.f;
     }
     for (int i = threadIdx.x; i < RR * s; i += NT) xs[(i / s) * s4 + i % s] = a.x0[i % s];
+    float px = a.cost.p0x, py = a.cost.p0y;  // pusher position of row threadIdx.x (obstacle cost; NT >= RR)
     __syncthreads();
     for (int t = 0; t < a.H; ++t) {
         for (int i = threadIdx.x; i < RR * Kp1; i += NT) {
@@ -1133,6 +1139,11 @@ __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
                 xs[r * s4 + i] = x;
                 const float e = x - a.goal[i];
                 c = fmaf(e, e, c);
+            }
+            if (a.cost.kind == 1) {
+                px = __fadd_rn(px, us[r * pad4(k)]);
+                py = __fadd_rn(py, us[r * pad4(k) + 1]);
+                c = obstacle_cost_f32(a.cost, t + 1, s, xs + r * s4, a.goal, px, py);
             }
             fsum[r] = f + c;
         }
@@ -1317,9 +1328,10 @@ cudaError_t launch_rollout_tc(RolloutArgs a, int split, int nslot_pref, int num_
     cudaError_t e;
     // state registers: 8, 16 or 32 (the output layer is 16 wide up to 16 states, else 32)
     if (a.cost.kind == 1) {
-        // the obstacle cost: 3-term split, uniform samples, at most 8 states
-        if (split != 3 || a.cem_mu || N.s > 8) return cudaErrorInvalidValue;
-        e = launch_tc_shape<3, 8, false, true>(a, nslot, stream, grid, smem, st);
+        // the obstacle cost: uniform samples, at most 8 states
+        if (a.cem_mu || N.s > 8) return cudaErrorInvalidValue;
+        e = split == 3 ? launch_tc_shape<3, 8, false, true>(a, nslot, stream, grid, smem, st)
+                       : launch_tc_shape<1, 8, false, true>(a, nslot, stream, grid, smem, st);
     } else if (a.cem_mu) {
         // the cross-entropy search runs the 3-term split only
         if (split != 3) return cudaErrorInvalidValue;
