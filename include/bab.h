@@ -211,7 +211,7 @@ int bab_bound_ibp(bab_ctx *ctx, const float *x0, const float *goal, int horizon,
  *              2^-22, at twice the operand bytes and twice the instructions),
  *              and charge gamma_K sum |A'| |W| max|a| to the margin.
  *              BAB_PREC_TF32X3 takes the squared-distance cost and networks
- *              whose widths are all at most 128 (else BAB_ERR_UNSUPPORTED).
+ *              whose widths are all at most 256 (else BAB_ERR_UNSUPPORTED).
  *   lb         device float[n]; margin device float[n] (nullable).
  *   lin_coef   device float[n][d] (nullable): mu; lin_const device float[n]
  *              (nullable): the constant (before the margin).
@@ -585,8 +585,11 @@ int bab_prune_branch_batch(bab_ctx *ctx, int d_stride, const int *horizon, int m
  *                            per CTA, layer by layer in every case.
  *   BAB_KERNEL_CROWN_TC      3 or 4: feature-major products (the layer's
  *                            features on the MMA's 128 rows, 32 boxes on its
- *                            columns) with 8 or 16 epilogue warps; squared-
- *                            distance cost and widths <= 128 only, 0 otherwise
+ *                            columns) with 8 or 16 epilogue warps; with
+ *                            widths between 129 and 256 (either value) two
+ *                            128-row feature blocks, 16 boxes a tile and the
+ *                            image streamed through shared memory; squared-
+ *                            distance cost and widths <= 256 only, 0 otherwise
  *                            (4 is the default where it applies);
  *                            0: box-major, one tile of up to 32 boxes per CTA,
  *                            each epilogue thread staging its next layer's

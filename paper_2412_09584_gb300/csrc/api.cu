@@ -1116,7 +1116,7 @@ static int check_crown_precision(bab_ctx *c, int precision, const char *what)
         if (c->cost.kind != 0) return fail(c, BAB_ERR_UNSUPPORTED, "%s in TF32x3 takes the squared-distance cost", what);
         if (!crown_tf32_supported(c->net, c->max_smem))
             return fail(c, BAB_ERR_UNSUPPORTED, "TF32x3 CROWN needs hidden widths that are multiples of 32 and every "
-                                                "width at most 128, s <= 32");
+                                                "width at most 256, s <= 32");
         return BAB_OK;
     }
     if (precision != BAB_PREC_FP32) return fail(c, BAB_ERR_UNSUPPORTED, "bound precision %d not available", precision);

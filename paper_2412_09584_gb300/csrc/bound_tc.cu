@@ -655,46 +655,50 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
 // split products (kind::tf32, K = 8 per instruction), the image (twice the BF16 one) streamed by a producer warp
 // through a ring of 32-wide K blocks in the issuer's order.
 // ---------------------------------------------------------------------------------------------------------------
-constexpr int kNB = 32;   // boxes per tile: the MMA's N
-constexpr uint32_t kBopHalf = 2 * kNB * 128;    // one half (hi or lo) of the B operand: K <= 128 in two 64-wide blocks
-constexpr uint32_t kBopHalfTf = 4 * kNB * 128;  // the same with TF32 halves: four 32-wide blocks
-constexpr uint32_t kTfHalf = 128 * 128;         // TF32 ring stage: one 32-wide K block of the image, 128 rows of hi,
-constexpr uint32_t kTfStage = 2 * kTfHalf;      // then 128 rows of lo
-constexpr int kTfMaxStages = 6;
+constexpr int kNB = 32;  // boxes per tile (the MMA's N) of the one-block kernels: 128 features at most
+// Tile shape of k_crown_tcf with MB 128-row feature blocks: 32 / MB boxes, K up to 128 MB, the B operand's halves.
+template <int MB>
+struct TcfShape {
+    static constexpr int KNB = 32 / MB;                      // boxes per tile
+    static constexpr uint32_t kHalfBf = 2 * MB * KNB * 128;  // BF16 half of the B operand: 64-wide K blocks
+    static constexpr uint32_t kHalfTf = 4 * MB * KNB * 128;  // TF32 half: 32-wide K blocks
+    static constexpr uint32_t kRingHalf = MB * 128 * 128;    // ring stage: one K block of the image, MB x 128 rows
+    static constexpr uint32_t kRingStage = 2 * kRingHalf;    // of the hi halves, then as many of the lo halves
+};
+constexpr int kRingMaxStages = 6;
 
-// byte offset of element (box n, k) in the K-major 128-byte-swizzled B operand of kNB rows
+// byte offset of element (box n, k) in the K-major 128-byte-swizzled B operand of KNB rows: BF16 (64 elements per
+// 128-byte block) or TF32 (32 per block)
+template <int KNB>
 __device__ __forceinline__ uint32_t bop_off(int n, int k)
 {
     const int kb = k >> 6, w = k & 63;
-    return (uint32_t)(kb * kNB * 128 + (n >> 3) * 1024 + (n & 7) * 128 + ((((w * 2) >> 4) ^ (n & 7)) << 4) +
+    return (uint32_t)(kb * KNB * 128 + (n >> 3) * 1024 + (n & 7) * 128 + ((((w * 2) >> 4) ^ (n & 7)) << 4) +
                       ((w * 2) & 15));
 }
-__device__ __forceinline__ void st_bf16_pair(uint8_t *bop, uint32_t off, float v)
-{
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    *reinterpret_cast<__nv_bfloat16 *>(bop + off) = h;
-    *reinterpret_cast<__nv_bfloat16 *>(bop + kBopHalf + off) = l;
-}
-// the TF32 operand: 32 elements of 4 bytes per 128-byte block
+template <int KNB>
 __device__ __forceinline__ uint32_t bop_off_tf(int n, int k)
 {
     const int kb = k >> 5, w = k & 31;
-    return (uint32_t)(kb * kNB * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((w >> 2) ^ (n & 7)) << 4) + ((w & 3) << 2));
+    return (uint32_t)(kb * KNB * 128 + (n >> 3) * 1024 + (n & 7) * 128 + (((w >> 2) ^ (n & 7)) << 4) + ((w & 3) << 2));
 }
-// v as hi = tf32(v) and lo = tf32(v - hi) (v - hi is exact in FP32)
-__device__ __forceinline__ void st_tf32_pair(uint8_t *bop, uint32_t off, float v)
+// element (box n, k) of the split B operand in the kernel's arithmetic: BF16 hi = bf16(v), lo = bf16(v - hi), or TF32
+// hi = tf32(v), lo = tf32(v - hi) (v - hi is exact in FP32); the lo halves `half` bytes after the hi halves
+template <bool TF, int KNB>
+__device__ __forceinline__ void st_split(uint8_t *bop, uint32_t half, int n, int k, float v)
 {
-    const float h = tc::tf32_rna(v);
-    *reinterpret_cast<float *>(bop + off) = h;
-    *reinterpret_cast<float *>(bop + kBopHalfTf + off) = tc::tf32_rna(v - h);
-}
-// element (box n, k) of the split B operand in the kernel's arithmetic
-template <bool TF>
-__device__ __forceinline__ void st_split(uint8_t *bop, int n, int k, float v)
-{
-    if (TF) st_tf32_pair(bop, bop_off_tf(n, k), v);
-    else st_bf16_pair(bop, bop_off(n, k), v);
+    if (TF) {
+        const uint32_t off = bop_off_tf<KNB>(n, k);
+        const float h = tc::tf32_rna(v);
+        *reinterpret_cast<float *>(bop + off) = h;
+        *reinterpret_cast<float *>(bop + half + off) = tc::tf32_rna(v - h);
+    } else {
+        const uint32_t off = bop_off<KNB>(n, k);
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        *reinterpret_cast<__nv_bfloat16 *>(bop + off) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(bop + half + off) = l;
+    }
 }
 
 // Lemma 1's relaxation without branches (the lanes of a warp hold different neurons).  The upper slope of an
@@ -721,21 +725,24 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 __device__ __forceinline__ void tmem_ld_bpt(uint32_t taddr, uint32_t (&r)[16]) { tc::tmem_ld16(taddr, r); }
 __device__ __forceinline__ void tmem_ld_bpt(uint32_t taddr, uint32_t (&r)[8]) { tc::tmem_ld8(taddr, r); }
 
-template <bool ALPHA, int WQ, bool TF>
-__global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_tcf(BoundArgs a)
+template <bool ALPHA, int WQ, bool TF, int MB>
+__global__ void __launch_bounds__((4 * WQ * MB + 1 + (TF || MB == 2 ? 1 : 0)) * 32, 1) k_crown_tcf(BoundArgs a)
 {
-    constexpr int NE = 4 * WQ, BPT = kNB / WQ;  // epilogue warps, boxes per epilogue thread
-    constexpr uint32_t kHalf = TF ? kBopHalfTf : kBopHalf;
+    using S = TcfShape<MB>;
+    constexpr int KNB = S::KNB;                           // boxes per tile
+    constexpr int NE = 4 * WQ * MB, BPT = KNB / WQ;       // epilogue warps, boxes per epilogue thread
+    constexpr bool STRM = TF || MB == 2;                  // the image streamed through a ring (else resident)
+    constexpr uint32_t kHalf = TF ? S::kHalfTf : S::kHalfBf;
     extern __shared__ uint8_t smem_raw[];
     const NetDesc &N = a.net;
-    // the resident image, or the TF32 ring of a.stages stages
+    // the resident image, or the ring of a.stages stages
     uint8_t *wimg = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *bop = wimg + (TF ? (size_t)a.stages * kTfStage : (((size_t)N.tcb_bytes + 1023) & ~size_t(1023)));
+    uint8_t *bop = wimg + (STRM ? (size_t)a.stages * S::kRingStage : (((size_t)N.tcb_bytes + 1023) & ~size_t(1023)));
     float *bias = reinterpret_cast<float *>(bop + 2 * kHalf);
-    float *red = bias + ((N.tc_bias_floats + 3) & ~3);  // [2 tile parities][4 quadrants][kNB][2]
-    float *small = red + 2 * 4 * kNB * 2;               // [WQ][32 lanes][2 step parities][3][BPT]
+    float *red = bias + ((N.tc_bias_floats + 3) & ~3);  // [2 tile parities][4 MB quadrants][KNB][2]
+    float *small = red + 2 * 4 * MB * KNB * 2;          // [WQ][32 lanes][2 step parities][3][BPT]
     __shared__ uint64_t bar_w, bar_a, bar_d, bar_r, bar_fin;
-    __shared__ uint64_t bar_full[TF ? kTfMaxStages : 1], bar_empty[TF ? kTfMaxStages : 1];
+    __shared__ uint64_t bar_full[STRM ? kRingMaxStages : 1], bar_empty[STRM ? kRingMaxStages : 1];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -749,7 +756,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
         tc::mbar_init(&bar_d, 1);
         tc::mbar_init(&bar_r, NE);
         tc::mbar_init(&bar_fin, 1);
-        if (TF)
+        if (STRM)
             for (int i = 0; i < a.stages; ++i) {
                 tc::mbar_init(&bar_full[i], 1);
                 tc::mbar_init(&bar_empty[i], 1);
@@ -761,7 +768,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (!TF) {
+    if (!STRM) {
         if (threadIdx.x == NE * 32) {
             tc::mbar_arrive_expect_tx(&bar_w, (uint32_t)N.tcb_bytes);
             for (uint32_t off = 0; off < (uint32_t)N.tcb_bytes; off += 32768u)
@@ -771,18 +778,20 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
     }
 
     const int nlive = live_count(a.n, a.d_n, a.row0);
-    const int ntiles = (nlive + kNB - 1) / kNB;
+    const int ntiles = (nlive + KNB - 1) / KNB;
     const uint32_t tb = tmem_base;
 
     if (warp < NE) {
-        const int q = warp & 3, h = warp >> 2, j = 32 * q + lane;  // h: the warp's share of the tile's boxes
-        const uint32_t dcol = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(BPT * h);
+        // lane quadrant q, feature block mb, share h of the tile's boxes: feature j of boxes BPT h .. BPT h + BPT - 1
+        const int q = warp & 3, mb = MB == 2 ? (warp >> 2) & 1 : 0, h = warp >> (MB == 2 ? 3 : 2);
+        const int j = 128 * mb + 32 * q + lane, qd = 4 * mb + q;
+        const uint32_t dcol = tb + ((uint32_t)(32 * q) << 16) + (uint32_t)(KNB * mb + BPT * h);
         float *sm = small + (size_t)(h * 32 + lane) * (2 * 3 * BPT);
         const bool state = j < s;
         uint32_t phD = 0, phR = 0;
         int par = 0;
         for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, par ^= 1) {
-            const int box0 = tile * kNB + BPT * h;
+            const int box0 = tile * KNB + BPT * h;
             float lam[BPT], cp[BPT], mp[BPT];
             float pzl[BPT], pzu[BPT], pS[BPT], pal[BPT];
             bool ok = true;
@@ -849,7 +858,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
 #pragma unroll
                     for (int bi = 0; bi < BPT; ++bi) {
                         const float v = state ? lam[bi] : 0.f;
-                        st_split<TF>(bop, BPT * h + bi, j, v);
+                        st_split<TF, KNB>(bop, kHalf, BPT * h + bi, j, v);
                         if (state && box0 + bi < nlive) {
                             cp[bi] = __fmaf_rd(v, bL, cp[bi]);
                             mp[bi] = __fmaf_ru(__fmul_ru(gL, fabsf(v)), sx[bi], mp[bi]);
@@ -889,7 +898,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
                                 if (D != 0.f && D != 1.f)
                                     mp[bi] = __fmaf_ru(__fmul_ru(kTwoU, fabsf(Ap)), fmaxf(-pzl[bi], pzu[bi]), mp[bi]);
                             }
-                            st_split<TF>(bop, BPT * h + bi, j, Ap);
+                            st_split<TF, KNB>(bop, kHalf, BPT * h + bi, j, Ap);
                         }
                     }
                     tc::fence_proxy_async_smem();
@@ -952,7 +961,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
                     mp[bi] = __fadd_ru(mp[bi], __shfl_xor_sync(0xFFFFFFFFu, mp[bi], o));
                 }
             }
-            float *rp = red + (size_t)par * 4 * kNB * 2 + ((size_t)q * kNB + BPT * h) * 2;
+            float *rp = red + (size_t)par * 4 * MB * KNB * 2 + ((size_t)qd * KNB + BPT * h) * 2;
             if (lane == 0)
 #pragma unroll
                 for (int bi = 0; bi < BPT; ++bi) {
@@ -968,13 +977,13 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
                 break;
             }
             phR ^= 1;
-            const int box = tile * kNB + lane;
-            if (box < nlive) {
-            const float *rr = red + (size_t)par * 4 * kNB * 2 + (size_t)lane * 2;
+            const int box = tile * KNB + lane;
+            if (lane < KNB && box < nlive) {
+            const float *rr = red + (size_t)par * 4 * MB * KNB * 2 + (size_t)lane * 2;
             float c = rr[0], mg = rr[1];
-            for (int q2 = 1; q2 < 4; ++q2) {
-                c = __fadd_rd(c, rr[(size_t)q2 * kNB * 2]);
-                mg = __fadd_ru(mg, rr[(size_t)q2 * kNB * 2 + 1]);
+            for (int q2 = 1; q2 < 4 * MB; ++q2) {
+                c = __fadd_rd(c, rr[(size_t)q2 * KNB * 2]);
+                mg = __fadd_ru(mg, rr[(size_t)q2 * KNB * 2 + 1]);
             }
             float vsum = 0.f, e = 0.f;
             for (int j0 = 0; j0 < d; j0 += 8) {
@@ -1028,7 +1037,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
         long long left = cnt * H * L;
         int l = L;
         uint32_t phA = 0;
-        const uint32_t idesc = TF ? tc::idesc_tf32_f32(128, kNB) : tc::idesc_bf16_f32(128, kNB);
+        const uint32_t idesc = TF ? tc::idesc_tf32_f32(128, KNB) : tc::idesc_bf16_f32(128, KNB);
         const uint32_t bh = tc::desc_sw128_lo(tc::smem_u32(bop)), bl = tc::desc_sw128_lo(tc::smem_u32(bop + kHalf));
         uint32_t ring_it = 0;
         bool ok = true;
@@ -1039,9 +1048,12 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
             }
             phA ^= 1;
             tc::fence_after_sync();
-            if (TF) {
-                // K = 8 per instruction, 32-wide blocks from the ring; each stage is released once its MMAs are done
-                const int nks = N.tf_K[l] / 8;
+            if (STRM) {
+                // K = 16 (BF16) or 8 (TF32) per instruction, four instructions per 128-byte K block from the ring,
+                // for each feature block that has rows (the layer's inputs beyond 128 need the second); each stage
+                // is released once its MMAs are done
+                const int nks = TF ? N.tf_K[l] / 8 : N.tcb_K[l] / 16;
+                const int mbl = (MB == 2 && N.dims[l - 1] > 128) ? 2 : 1;
                 for (int kb = 0; kb < (nks + 3) / 4; ++kb, ++ring_it) {
                     const uint32_t st = ring_it % (uint32_t)a.stages, ph = (ring_it / (uint32_t)a.stages) & 1u;
                     if (!tc::mbar_wait(&bar_full[st], ph, abort, kWaitNs)) {
@@ -1049,17 +1061,30 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
                         ok = false;
                         break;
                     }
-                    const uint32_t ah = tc::desc_sw128_lo(tc::smem_u32(wimg + (size_t)st * kTfStage));
-                    const uint32_t al = ah + (kTfHalf >> 4);
+                    const uint32_t a0 = tc::desc_sw128_lo(tc::smem_u32(wimg + (size_t)st * S::kRingStage));
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const int ks = 4 * kb + kk;
                         if (ks >= nks) break;
-                        const uint32_t bo = (uint32_t)(kb * kNB * 8 + kk * 2);
-                        const uint64_t Ah = tc::desc_join(ah + 2u * kk), Bh = tc::desc_join(bh + bo);
-                        tc::mma_ss_tf32(tb, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
-                        tc::mma_ss_tf32(tb, tc::desc_join(al + 2u * kk), Bh, idesc, 1u);
-                        tc::mma_ss_tf32(tb, Ah, tc::desc_join(bl + bo), idesc, 1u);
+                        const uint32_t bo = (uint32_t)(kb * KNB * 8 + kk * 2);
+                        const uint64_t Bh = tc::desc_join(bh + bo), Bl = tc::desc_join(bl + bo);
+#pragma unroll
+                        for (int m = 0; m < MB; ++m) {
+                            if (m >= mbl) break;
+                            // feature block m: rows 128 m .. 128 m + 127 of the stage's hi and lo halves
+                            const uint32_t ah = a0 + (uint32_t)m * (128u * 128u >> 4) + 2u * kk;
+                            const uint64_t Ah = tc::desc_join(ah), Al = tc::desc_join(ah + (S::kRingHalf >> 4));
+                            const uint32_t dm = tb + (uint32_t)(m * KNB);
+                            if (TF) {
+                                tc::mma_ss_tf32(dm, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
+                                tc::mma_ss_tf32(dm, Al, Bh, idesc, 1u);
+                                tc::mma_ss_tf32(dm, Ah, Bl, idesc, 1u);
+                            } else {
+                                tc::mma_ss(dm, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
+                                tc::mma_ss(dm, Al, Bh, idesc, 1u);
+                                tc::mma_ss(dm, Ah, Bl, idesc, 1u);
+                            }
+                        }
                     }
                     tc::mma_commit(&bar_empty[st]);
                 }
@@ -1071,7 +1096,7 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
                 for (int ks = 0; ks < nks; ++ks) {
                     // 16-byte units: K-block ks / 4 of the operand, then 32 bytes per K = 16 step inside it
                     const uint32_t ao = (uint32_t)((ks >> 2) * Nl * 8 + (ks & 3) * 2);
-                    const uint32_t bo = (uint32_t)((ks >> 2) * kNB * 8 + (ks & 3) * 2);
+                    const uint32_t bo = (uint32_t)((ks >> 2) * KNB * 8 + (ks & 3) * 2);
                     const uint64_t Ah = tc::desc_join(ah + ao), Bh = tc::desc_join(bh + bo);
                     tc::mma_ss(tb, Ah, Bh, idesc, ks > 0 ? 1u : 0u);
                     tc::mma_ss(tb, tc::desc_join(al + ao), Bh, idesc, 1u);
@@ -1087,15 +1112,17 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
             tc::mma_commit(&bar_fin);
             tc::mbar_wait(&bar_fin, 0, &never, kWaitNs);
         }
-    } else if (TF && warp == NE + 1 && lane == 0) {
-        // ------------- producer: the TF32 image's K blocks in the issuer's order (t = H-1 .. 0, l = L .. 1) -------------
+    } else if (STRM && warp == NE + 1 && lane == 0) {
+        // ---------- producer: the image's K blocks in the issuer's order (t = H-1 .. 0, l = L .. 1) ----------
+        // BF16: block kb of layer l's hi rows at tcb_hi[l] + kb rows, its lo rows at tcb_lo[l] + kb rows; TF32: the
+        // two halves of block kb back to back at tf_off[l] + 2 kb rows (rows = the layer's tcb_N[l] x 128 bytes)
         const long long cnt = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         uint32_t it = 0;
         bool ok = true;
         for (long long q = 0; q < cnt * H && ok && !*abort; ++q) {
             for (int l = L; l >= 1 && ok; --l) {
                 const uint32_t rows = (uint32_t)N.tcb_N[l] * 128u;  // bytes of one half of a block
-                const int nb = (N.tf_K[l] / 8 + 3) / 4;
+                const int nb = TF ? (N.tf_K[l] / 8 + 3) / 4 : (N.tcb_K[l] / 16 + 3) / 4;
                 for (int kb = 0; kb < nb; ++kb, ++it) {
                     const uint32_t st = it % (uint32_t)a.stages, ph = (it / (uint32_t)a.stages) & 1u;
                     if (!tc::mbar_wait(&bar_empty[st], ph ^ 1u, abort, kWaitNs)) {
@@ -1103,11 +1130,13 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
                         ok = false;
                         break;
                     }
-                    uint8_t *dst = wimg + (size_t)st * kTfStage;
-                    const uint8_t *src = a.tcb_img + N.tf_off[l] + (size_t)kb * 2 * rows;
+                    uint8_t *dst = wimg + (size_t)st * S::kRingStage;
+                    const uint8_t *src_h = TF ? a.tcb_img + N.tf_off[l] + (size_t)kb * 2 * rows
+                                              : a.tcb_img + N.tcb_hi[l] + (size_t)kb * rows;
+                    const uint8_t *src_l = TF ? src_h + rows : a.tcb_img + N.tcb_lo[l] + (size_t)kb * rows;
                     tc::mbar_arrive_expect_tx(&bar_full[st], 2u * rows);
-                    tc::bulk_g2s(dst, src, rows, &bar_full[st]);
-                    tc::bulk_g2s(dst + kTfHalf, src + rows, rows, &bar_full[st]);
+                    tc::bulk_g2s(dst, src_h, rows, &bar_full[st]);
+                    tc::bulk_g2s(dst + S::kRingHalf, src_l, rows, &bar_full[st]);
                 }
             }
         }
@@ -1128,49 +1157,72 @@ __global__ void __launch_bounds__((4 * WQ + 1 + (TF ? 1 : 0)) * 32, 1) k_crown_t
     }
 }
 
-// shared memory of k_crown_tcf beyond the image (BF16) or the ring (TF32)
-static size_t crown_tcf_extra(const NetDesc &N, bool tf = false)
+// shared memory of k_crown_tcf beyond the resident image or the ring: mb feature blocks, BF16 or TF32 halves
+static size_t crown_tcf_extra(const NetDesc &N, bool tf = false, int mb = 1)
 {
-    return 1024 + 1024 + 2 * (size_t)(tf ? kBopHalfTf : kBopHalf) +
-           ((size_t)((N.tc_bias_floats + 3) & ~3) + 2 * 4 * kNB * 2 + 32 * 2 * 3 * kNB) * 4;
+    const size_t knb = (size_t)(32 / mb), half = (tf ? 4 : 2) * (size_t)mb * knb * 128;
+    return 1024 + 1024 + 2 * half + ((size_t)((N.tc_bias_floats + 3) & ~3) + 2 * 4 * (size_t)mb * knb * 2 + 32 * 2 * 3 * knb) * 4;
 }
 
-// ring stages of the TF32 kernel that fit beside the rest of its shared memory
-static int crown_tf32_stages(const NetDesc &N, int max_smem)
+// feature blocks of 128 rows the feature-major kernel needs: 1 (every width <= 128), 2 (<= 256), else 0
+static int crown_tcf_blocks(const NetDesc &N)
 {
-    const size_t extra = crown_tcf_extra(N, true);
+    int w = 0;
+    for (int l = 0; l <= N.L; ++l) w = N.dims[l] > w ? N.dims[l] : w;
+    return w <= 128 ? 1 : (w <= 256 ? 2 : 0);
+}
+
+// ring stages of a streamed feature-major kernel that fit beside the rest of its shared memory
+static int crown_ring_stages(const NetDesc &N, bool tf, int mb, int max_smem)
+{
+    const size_t extra = crown_tcf_extra(N, tf, mb), stage = 2 * (size_t)mb * 128 * 128;
     if (extra >= (size_t)max_smem) return 0;
-    const int st = (int)(((size_t)max_smem - extra) / kTfStage);
-    return st > kTfMaxStages ? kTfMaxStages : st;
+    const int st = (int)(((size_t)max_smem - extra) / stage);
+    return st > kRingMaxStages ? kRingMaxStages : st;
 }
 
-// 3-term TF32 split CROWN: the feature-major kernel's conditions (squared-distance cost, every width at most 128),
-// with at least two ring stages
-bool crown_tf32_supported(const NetDesc &N, int max_smem)
+// the streamed feature-major kernels (TF32 halves, or BF16 halves with two feature blocks): squared-distance cost,
+// hidden widths multiples of 32, every width at most 256, s <= 32, at least two ring stages
+static bool crown_tcf_streamed_ok(const NetDesc &N, bool tf, int max_smem)
 {
-    for (int l = 0; l <= N.L; ++l)
-        if (N.dims[l] > 128) return false;
-    return N.tc_ok && N.L >= 2 && N.s <= 32 && N.tf_K[N.L] <= 32 && crown_tf32_stages(N, max_smem) >= 2;
+    const int mb = crown_tcf_blocks(N);
+    return mb >= 1 && N.tc_ok && N.L >= 2 && N.s <= 32 && (tf ? N.tf_K[N.L] : N.tcb_K[N.L]) <= 32 &&
+           crown_ring_stages(N, tf, mb, max_smem) >= 2;
+}
+
+// 3-term TF32 split CROWN
+bool crown_tf32_supported(const NetDesc &N, int max_smem) { return crown_tcf_streamed_ok(N, true, max_smem); }
+
+// A streamed feature-major launch: TF32 halves (one or two feature blocks) or BF16 halves with two feature blocks;
+// 16 epilogue warps and 8 boxes a thread either way (4 warps per quadrant with one block, 2 with two).
+static cudaError_t launch_crown_tcf_streamed(BoundArgs a, bool tf, int num_sms, int max_smem, cudaStream_t st)
+{
+    const NetDesc &N = a.net;
+    const int mb = crown_tcf_blocks(N);
+    a.stages = crown_ring_stages(N, tf, mb, max_smem);
+    a.stage_bytes = 2 * mb * 128 * 128;
+    const size_t smem = (size_t)a.stages * a.stage_bytes + crown_tcf_extra(N, tf, mb);
+    const int knb = 32 / mb;
+    const int ntiles = (a.n + knb - 1) / knb;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    void (*kern)(BoundArgs);
+    if (mb == 1) kern = a.alpha ? k_crown_tcf<true, 4, true, 1> : k_crown_tcf<false, 4, true, 1>;
+    else if (tf) kern = a.alpha ? k_crown_tcf<true, 2, true, 2> : k_crown_tcf<false, 2, true, 2>;
+    else kern = a.alpha ? k_crown_tcf<true, 2, false, 2> : k_crown_tcf<false, 2, false, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 18 * 32, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_crown_tf32(BoundArgs a, int num_sms, cudaStream_t st)
 {
-    const NetDesc &N = a.net;
     if (a.n <= 0) return cudaSuccess;
     int dev, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (a.cost.kind != 0 || !crown_tf32_supported(N, max_smem)) return cudaErrorNotSupported;
-    a.stages = crown_tf32_stages(N, max_smem);
-    a.stage_bytes = (int)kTfStage;
-    const size_t smem = (size_t)a.stages * kTfStage + crown_tcf_extra(N, true);
-    const int ntiles = (a.n + kNB - 1) / kNB;
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
-    auto kern = a.alpha ? k_crown_tcf<true, 4, true> : k_crown_tcf<false, 4, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, (4 * 4 + 2) * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    if (a.cost.kind != 0 || !crown_tf32_supported(a.net, max_smem)) return cudaErrorNotSupported;
+    return launch_crown_tcf_streamed(a, true, num_sms, max_smem, st);
 }
 
 // The feature-major kernel: squared-distance cost, every width at most 128 (the MMA's 128 rows), the image resident
@@ -1252,7 +1304,8 @@ static cudaError_t launch_shape(const BoundArgs &a, int nslot, bool stream, bool
                       : launch_variant<1, SP, false, false, false>(a, grid, smem, st);
 }
 
-// variant: 3 or 4 feature-major with 8 or 16 epilogue warps (fall back to 0 where it does not apply), 0 staged (one slot, a multiple of 4 up to
+// variant: 3 or 4 feature-major with 8 or 16 epilogue warps (widths up to 256: the streamed two-block kernel for
+// either; fall back to 0 where it does not apply), 0 staged (one slot, a multiple of 4 up to
 // 32 boxes per tile, the fewest that spread the batch over the SMs; falls back to 1 when the areas do not fit),
 // 1 or 2 unstaged tiles per CTA, -1 the first of 4, 0, 1 that applies
 cudaError_t launch_crown_tc(BoundArgs a, int variant, int num_sms, cudaStream_t st)
@@ -1262,13 +1315,16 @@ cudaError_t launch_crown_tc(BoundArgs a, int variant, int num_sms, cudaStream_t 
     int dev, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((variant == -1 || variant == 3 || variant == 4) && a.cost.kind == 0 && crown_tcf_blocks(N) == 2 &&
+        crown_tcf_streamed_ok(N, false, max_smem))
+        return launch_crown_tcf_streamed(a, false, num_sms, max_smem, st);
     if ((variant == -1 || variant == 3 || variant == 4) && a.cost.kind == 0 && crown_tcf_supported(N, max_smem)) {
         const size_t smem = (size_t)N.tcb_bytes + crown_tcf_extra(N);
         const int ntiles = (a.n + kNB - 1) / kNB;
         const int grid = ntiles < num_sms ? ntiles : num_sms;
         const int wq = variant == 3 ? 2 : 4;  // epilogue warps per TMEM lane quadrant
-        auto kern = wq == 2 ? (a.alpha ? k_crown_tcf<true, 2, false> : k_crown_tcf<false, 2, false>)
-                            : (a.alpha ? k_crown_tcf<true, 4, false> : k_crown_tcf<false, 4, false>);
+        auto kern = wq == 2 ? (a.alpha ? k_crown_tcf<true, 2, false, 1> : k_crown_tcf<false, 2, false, 1>)
+                            : (a.alpha ? k_crown_tcf<true, 4, false, 1> : k_crown_tcf<false, 4, false, 1>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, (4 * wq + 1) * 32, smem, st>>>(a);

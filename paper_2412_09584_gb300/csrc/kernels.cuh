@@ -357,7 +357,7 @@ cudaError_t preload_ibp_crown();
 cudaError_t launch_crown_tc(BoundArgs a, int nslot_pref, int num_sms, cudaStream_t st);
 bool crown_tc_supported(const NetDesc &N, int max_smem);
 bool crown_tc_obstacles_supported(const NetDesc &N, int max_smem);
-// CROWN with 3-term TF32 split products (a.tcb_img = the backward TF32 image; squared-distance cost, widths <= 128)
+// CROWN with 3-term TF32 split products (a.tcb_img = the backward TF32 image; squared-distance cost, widths <= 256)
 cudaError_t launch_crown_tf32(BoundArgs a, int num_sms, cudaStream_t st);
 bool crown_tf32_supported(const NetDesc &N, int max_smem);
 cudaError_t launch_alpha_fwd(const BoundArgs &a, int num_sms, cudaStream_t st);

@@ -23,11 +23,11 @@ def _setup(seed=12, n=24):
     return p, lo, hi, g, T(lo), T(hi)
 
 
-@pytest.mark.parametrize("prec_name,tol", [("fp32", 1e-4), ("bf16x3", 1e-3)])
+@pytest.mark.parametrize("prec_name,tol", [("fp32", 1e-4), ("bf16x3", 1e-3), ("tf32x3", 1e-4)])
 def test_autograd_gradient_matches_oracle(oracle, prec_name, tol):
     from paper_2412_09584_gb300 import binding as B
     from paper_2412_09584_gb300.autograd import CrownProblem, crown_bound
-    prec = {"fp32": B.PREC_FP32, "bf16x3": B.PREC_BF16X3}[prec_name]
+    prec = {"fp32": B.PREC_FP32, "bf16x3": B.PREC_BF16X3, "tf32x3": B.PREC_TF32X3}[prec_name]
     p, lo, hi, g, tlo, thi = _setup()
     try:
         a0 = oracle.adaptive_alpha(p, lo, hi)
@@ -77,11 +77,11 @@ def test_autograd_adam_raises_sound_bounds(oracle):
         g.close()
 
 
-@pytest.mark.parametrize("prec_name", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec_name", ["fp32", "bf16x3", "tf32x3"])
 def test_alpha_optimize_matches_oracle(oracle, prec_name):
     """bab_alpha_optimize (interval bounds once, 20 Adam steps on the device) against the oracle's 20 steps."""
     from paper_2412_09584_gb300 import binding as B
-    prec = {"fp32": B.PREC_FP32, "bf16x3": B.PREC_BF16X3}[prec_name]
+    prec = {"fp32": B.PREC_FP32, "bf16x3": B.PREC_BF16X3, "tf32x3": B.PREC_TF32X3}[prec_name]
     p, lo, hi, g, tlo, thi = _setup(seed=40, n=32)
     try:
         n = lo.shape[0]

@@ -1,6 +1,6 @@
 """Bounding under a scratch limit (bab_set_scratch_limit): the boxes go through in chunks whose working set fits,
 each chunk's interval bounds recomputed instead of held for every box, and every output is bit-identical to the
-one-pass call (each box is bounded on its own).  Covers the CROWN bound in both precisions, the box gradient, the
+one-pass call (each box is bounded on its own).  Covers the CROWN bound in its three precisions, the box gradient, the
 whole alpha optimisation (the adjoint's stored coefficients are the largest per-box state), a device-side live
 count, and the object-manipulation configuration with alpha-CROWN at its full 16384 boxes."""
 import numpy as np
@@ -32,7 +32,8 @@ def _limit_for(g, rows):
     return 32 * 256 + rows * per
 
 
-@pytest.mark.parametrize("name,n,prec", [("pushing", 200, 0), ("pushing", 130, 1), ("tiny", 300, 0)])
+@pytest.mark.parametrize("name,n,prec", [("pushing", 200, 0), ("pushing", 130, 1), ("tiny", 300, 0),
+                                         ("pushing", 150, 3)])
 def test_crown_chunked_bit_identical(gp, name, n, prec):
     from gpu_util import DEV, T
     from paper_2412_09584_gb300 import binding as B

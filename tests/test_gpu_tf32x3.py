@@ -7,7 +7,9 @@ bits each) and FP32 accumulation, the backward image streamed through shared mem
   oracle's, the margin within 1e-3 of the oracle's FP64 evaluation of the TF32-split margin formula.
 * Tighter than the BF16 split: a smaller margin on every box.
 * alpha-CROWN through it: each Adam step's bound and gradient against the oracle's at the GPU's own slopes.
-* Refusals: the obstacle cost and widths above 128 (BAB_ERR_UNSUPPORTED).
+* Networks wider than 128 (two 128-row feature blocks per product): against the oracle on a small wide network,
+  and at the object-manipulation scale against the oracle's CROWN on the GPU's own interval bounds.
+* Refusals: the obstacle cost and hidden widths that are not multiples of 32 (BAB_ERR_UNSUPPORTED).
 """
 import numpy as np
 import pytest
@@ -121,8 +123,8 @@ def test_tf32x3_alpha_optimize_matches_steps(gp):
 def test_tf32x3_refusals(gp):
     from gpu_util import DEV, T
     from paper_2412_09584_gb300 import binding as B
-    # widths above 128
-    q = W.config_problem("manip", 0)
+    # hidden widths that are not multiples of 32
+    q = W.make_problem(8, 2, [48, 48], 3, 0.01, seed=2)
     g = gp(q)
     lo, hi, _ = W.random_boxes(q["k"] * q["H"], 4, seed=1, min_width=0.01, max_width=0.1)
     lb = torch.empty(4, device=DEV)
@@ -140,3 +142,77 @@ def test_tf32x3_refusals(gp):
     B.bab_set_cost(g2.ctx, B.COST_SQUARED)   # back to the default: the same call now runs
     B.bab_bound_crown(g2.ctx, g2.x0, g2.goal, g2.H, g2.rho, T(lo), T(hi), 4, lb, precision=B.PREC_TF32X3)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec_name,oprec,tol", [("bf16x3", 1, 5e-5), ("tf32x3", 2, 1e-5)])
+def test_wide_feature_major_matches_oracle(oracle, gp, prec_name, oprec, tol):
+    """Hidden widths 160 and 192 (two feature blocks, 16-box tiles, the image streamed).  The GPU's outward-rounded
+    interval bounds drift from the oracle's FP64 ones on this network (about 4e-5 of the bound's scale in every
+    precision, the FP32 CROWN included), so CROWN is checked on the GPU's own intervals: the raw bound within the
+    split's band of the oracle's CROWN (Theorems 1-2) on them, the margin equal to the oracle's formula, never above
+    the oracle's bound; with given slopes too.  The bound on the oracle's own intervals stays at least the GPU's."""
+    from paper_2412_09584_gb300 import binding as B
+    prec = {"bf16x3": B.PREC_BF16X3, "tf32x3": B.PREC_TF32X3}[prec_name]
+    p = W.make_problem(8, 2, [160, 192], 4, 0.01, seed=21, weight_scale=0.5)
+    d = p["k"] * p["H"]
+    g = gp(p)
+
+    def check(lo, hi, alpha=None):
+        _, pl, pu, xl, xu = g.ibp(lo, hi)
+        r = g.crown(lo, hi, alpha=alpha, precision=prec)
+        a64 = None if alpha is None else alpha.astype(np.float64)
+        o = oracle.crown_margin(p, lo, hi, intervals=(pl, pu, xl, xu), alpha=a64, prec=oprec)
+        scale = np.maximum(o["scale"], 1.0)
+        np.testing.assert_allclose(r["margin"], o["margin"], rtol=MARGIN_REL, atol=0)
+        err = np.abs(r["lb"].astype(np.float64) + r["margin"] - o["lb"]) / scale
+        assert np.all(err <= tol), err.max()
+        assert np.all(r["lb"] <= o["lb"] + 1e-12 * np.abs(o["lb"]))
+        own = oracle.crown_margin(p, lo, hi, alpha=a64, prec=oprec)
+        assert np.all(r["lb"] <= own["lb"] + 1e-12 * np.abs(own["lb"]))
+
+    for n, maxw, seed in ((53, 1.0, 3), (16, 0.05, 4)):
+        lo, hi, _ = W.random_boxes(d, n, seed=seed, min_width=0.0, max_width=maxw)
+        check(lo, hi)
+    check(lo, hi, np.random.default_rng(5).uniform(0, 1, size=(16, p["H"], 352)).astype(np.float32))
+
+
+def test_wide_feature_major_against_box_major(gp):
+    """The two-block feature-major kernel (the default at widths up to 256) and the box-major one (variant 1) agree
+    within the BF16 split's rounding: the feature-major constant is summed per feature first."""
+    from paper_2412_09584_gb300 import binding as B
+    p = W.make_problem(8, 2, [160, 192], 4, 0.01, seed=22, weight_scale=0.5)
+    g = gp(p)
+    lo, hi, _ = W.random_boxes(p["k"] * p["H"], 70, seed=6, min_width=0.0, max_width=1.0)
+    rf = g.crown(lo, hi, precision=B.PREC_BF16X3)
+    B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, 1)
+    rb = g.crown(lo, hi, precision=B.PREC_BF16X3)
+    B.bab_set_variant(g.ctx, B.KERNEL_CROWN_TC, -1)
+    band = 2e-5 * np.maximum(np.abs(rb["lb"]), 1.0) + rb["margin"] + rf["margin"]
+    assert np.all(np.abs(rf["lb"] - rb["lb"]) <= band)
+
+
+@pytest.fixture(scope="module")
+def manip():
+    from gpu_util import GpuProblem
+    p = W.config_problem("manip", 0)
+    g = GpuProblem(p)
+    yield p, g
+    g.close()
+
+
+def test_tf32x3_manip_on_gpu_intervals(oracle, manip):
+    """The object-manipulation scale (MLP 36-256x4-32, H = 40) in TF32x3: the oracle's CROWN on the GPU's own
+    interval bounds against the GPU's raw bound, within max(1e-5 x scale, the GPU's margin), the margin equal to the
+    oracle's TF32-split formula, never above the oracle's bound."""
+    p, g = manip
+    lo, hi, _ = W.random_boxes(160, 6, seed=21, min_width=0.002, max_width=0.02)
+    _, pl, pu, xl, xu = g.ibp(lo, hi)
+    from paper_2412_09584_gb300 import binding as B
+    r = g.crown(lo, hi, precision=B.PREC_TF32X3)
+    o = oracle.crown_margin(p, lo, hi, intervals=(pl, pu, xl, xu), prec=2)
+    scale = np.maximum(o["scale"], 1.0)
+    err = np.abs(r["lb"] + r["margin"] - o["lb"]) / scale
+    band = np.maximum(REL, r["margin"] / scale)
+    assert np.all(err <= band), (err / band).max()
+    assert np.all(r["lb"] <= o["lb"] + 1e-12 * np.abs(o["lb"]))
+    np.testing.assert_allclose(r["margin"], o["margin"], rtol=MARGIN_REL, atol=0)
