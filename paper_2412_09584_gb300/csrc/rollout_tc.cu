@@ -989,6 +989,7 @@ __global__ void __launch_bounds__(1024) k_topk_select(RolloutArgs a)
 
 // BF16 mode: the chosen sample of a box is re-scored in FP32 on CUDA cores (one
 // CTA per box), for every box or for the topk of smallest BF16 ub.
+template <bool OBST>
 __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
 {
     const NetDesc &N = a.net;
@@ -1016,7 +1017,7 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
     for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = x0[i];
     if (threadIdx.x == 0) f_sh = 0.f;
-    float px = a.cost.p0x, py = a.cost.p0y;  // pusher position (obstacle cost; thread 0)
+    float px = OBST ? a.cost.p0x : 0.f, py = OBST ? a.cost.p0y : 0.f;  // pusher position (thread 0)
     __syncthreads();
     for (int t = 0; t < Hb; ++t) {
         for (int c = threadIdx.x; c < s + k; c += blockDim.x)
@@ -1041,8 +1042,8 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
             for (int j = 0; j < k; ++j) {
                 const float u = draw_sample(hb, m, (uint32_t)(t * k + j), blo[t * k + j], bhi[t * k + j]);
                 f = fmaf(rho * u, u, f);
-                if (a.cost.kind == 1 && j == 0) px = __fadd_rn(px, u);
-                if (a.cost.kind == 1 && j == 1) py = __fadd_rn(py, u);
+                if (OBST && j == 0) px = __fadd_rn(px, u);
+                if (OBST && j == 1) py = __fadd_rn(py, u);
             }
             float c = 0.f;
             for (int i = 0; i < s; ++i) {
@@ -1050,7 +1051,7 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
                 const float e = xs[i] - goal[i];
                 c = fmaf(e, e, c);
             }
-            if (a.cost.kind == 1) c = obstacle_cost_f32(a.cost, t + 1, s, xs, goal, px, py);
+            if (OBST) c = obstacle_cost_f32(a.cost, t + 1, s, xs, goal, px, py);
             f_sh = f + c;
         }
         __syncthreads();
@@ -1066,7 +1067,7 @@ constexpr int kRescoreRows = 28;  // 4096 boxes make 147 CTAs: one wave on 152 S
 // threads took two each, 0.49 ms for 4096 boxes)
 constexpr int kRescoreThreads = 512;
 static_assert(kRescoreRows <= kRescoreThreads, "one thread per row keeps that row's pusher position");
-template <bool WSMEM>
+template <bool WSMEM, bool OBST>
 __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
 {
     constexpr int RR = kRescoreRows, NT = kRescoreThreads;
@@ -1100,7 +1101,7 @@ __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
         fsum[r] = 0.f;
     }
     for (int i = threadIdx.x; i < RR * s; i += NT) xs[(i / s) * s4 + i % s] = a.x0[i % s];
-    float px = a.cost.p0x, py = a.cost.p0y;  // pusher position of row threadIdx.x (obstacle cost; NT >= RR)
+    float px = OBST ? a.cost.p0x : 0.f, py = OBST ? a.cost.p0y : 0.f;  // pusher position of row threadIdx.x
     __syncthreads();
     for (int t = 0; t < a.H; ++t) {
         for (int i = threadIdx.x; i < RR * Kp1; i += NT) {
@@ -1140,7 +1141,7 @@ __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
                 const float e = x - a.goal[i];
                 c = fmaf(e, e, c);
             }
-            if (a.cost.kind == 1) {
+            if (OBST) {
                 px = __fadd_rn(px, us[r * pad4(k)]);
                 py = __fadd_rn(py, us[r * pad4(k) + 1]);
                 c = obstacle_cost_f32(a.cost, t + 1, s, xs + r * s4, a.goal, px, py);
@@ -1158,7 +1159,8 @@ static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
     const NetDesc &N = a.net;
     if (a.batch.P > 1 || a.topk > 0) {
         // each box reads its own problem's image; with a top-k selection all but k boxes return at once
-        k_rescore_fp32<<<a.n, 256, 0, st>>>(a);
+        if (a.cost.kind == 1) k_rescore_fp32<true><<<a.n, 256, 0, st>>>(a);
+        else k_rescore_fp32<false><<<a.n, 256, 0, st>>>(a);
         return cudaGetLastError();
     }
     int dev, budget = 0;
@@ -1169,7 +1171,8 @@ static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
     const size_t img = (size_t)N.img_floats * 4;
     const bool wsmem = img + rest + 1024 <= (size_t)budget;
     const size_t smem = (wsmem ? img : 0) + rest;
-    auto kern = wsmem ? k_rescore_rows<true> : k_rescore_rows<false>;
+    auto kern = a.cost.kind == 1 ? (wsmem ? k_rescore_rows<true, true> : k_rescore_rows<false, true>)
+                                 : (wsmem ? k_rescore_rows<true, false> : k_rescore_rows<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(a.n + kRescoreRows - 1) / kRescoreRows, kRescoreThreads, smem, st>>>(a);
