@@ -987,28 +987,30 @@ __global__ void __launch_bounds__(1024) k_topk_select(RolloutArgs a)
     }
 }
 
-// BF16 mode: the chosen sample of a box is re-scored in FP32 on CUDA cores (one
-// CTA per box), for every box or for the topk of smallest BF16 ub.
+// BF16 mode: the chosen sample of a box is re-scored in FP32 on CUDA cores (a
+// CTA per box at a time), for every box or for the topk of smallest BF16 ub.
 template <bool OBST>
 __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
 {
     const NetDesc &N = a.net;
-    const int box = blockIdx.x;
-    if (box >= live_count(a.n, a.d_n)) return;
+    const int nlive = live_count(a.n, a.d_n);
+    Thresh T;
     if (a.topk > 0) {
-        Thresh T;
         T.key = (uint32_t)a.topk_t[0];
         T.id = a.topk_t[1];
         T.none = a.topk_t[2] != 0;
-        if (!le_thresh(float_order(a.ub[box]), a.id[box], T)) return;
     }
     __shared__ float act[2][kMaxWidth + 4];
     __shared__ float xs[kMaxWidth];
     __shared__ float f_sh;
+    const int s = N.s, k = N.k, d = a.d;
+    // boxes blockIdx.x, blockIdx.x + gridDim.x, ...: the grid is sized to the SMs, so that a top-k selection does
+    // not pay for one CTA per box
+    for (int box = blockIdx.x; box < nlive; box += gridDim.x) {
+    if (a.topk > 0 && !le_thresh(float_order(a.ub[box]), a.id[box], T)) continue;
     const unsigned long long key = a.keys[box];
     const uint32_t m = (uint32_t)(key & 0xFFFFFFFFu);
     const uint64_t hb = box_hash(a.seed, a.id[box]);
-    const int s = N.s, k = N.k, d = a.d;
     const int pb = row_problem(a.batch, box);
     const float *fwd = a.fwd + (size_t)pb * N.img_floats;
     const float *x0 = a.x0 + (size_t)pb * s, *goal = a.goal + (size_t)pb * s;
@@ -1031,7 +1033,15 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
             const float *b = fwd + N.fwd_b[l];
             for (int q = threadIdx.x; q < no; q += blockDim.x) {
                 float acc = b[q];
-                for (int c = 0; c < ni; ++c) acc = fmaf(Wt[(size_t)c * Np + q], act[cur][c], acc);
+                // 16 inputs' weights loaded before their multiply-adds (which run in input order)
+                for (int c0 = 0; c0 < ni; c0 += 16) {
+                    float w[16];
+#pragma unroll
+                    for (int cc = 0; cc < 16; ++cc) w[cc] = c0 + cc < ni ? __ldg(Wt + (size_t)(c0 + cc) * Np + q) : 0.f;
+#pragma unroll
+                    for (int cc = 0; cc < 16; ++cc)
+                        if (c0 + cc < ni) acc = fmaf(w[cc], act[cur][c0 + cc], acc);
+                }
                 act[cur ^ 1][q] = (l < N.L) ? fmaxf(acc, 0.f) : acc;
             }
             __syncthreads();
@@ -1057,6 +1067,8 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
         __syncthreads();
     }
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
+    __syncthreads();  // before the next box reuses the shared arrays
+    }
 }
 
 // BF16 mode, one problem, every box re-scored: the same FP32 re-score as k_rescore_fp32 for a tile of RR boxes
@@ -1159,8 +1171,12 @@ static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
     const NetDesc &N = a.net;
     if (a.batch.P > 1 || a.topk > 0) {
         // each box reads its own problem's image; with a top-k selection all but k boxes return at once
-        if (a.cost.kind == 1) k_rescore_fp32<true><<<a.n, 256, 0, st>>>(a);
-        else k_rescore_fp32<false><<<a.n, 256, 0, st>>>(a);
+        int dev, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = a.n < 2 * sms ? a.n : 2 * sms;
+        if (a.cost.kind == 1) k_rescore_fp32<true><<<grid, 256, 0, st>>>(a);
+        else k_rescore_fp32<false><<<grid, 256, 0, st>>>(a);
         return cudaGetLastError();
     }
     int dev, budget = 0;
