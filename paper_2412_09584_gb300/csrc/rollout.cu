@@ -9,6 +9,8 @@
 // tile, adds the residual, and reduces the per-row cost with warp shuffles.
 // A tile's best (f, m) is folded into its box with a 64-bit atomicMin on
 // (order(f) << 32 | m), which keeps the lowest m among equal values.
+#include <cooperative_groups.h>
+
 #include "bab_internal.cuh"
 #include "kernels.cuh"
 
@@ -204,14 +206,25 @@ __global__ void k_rollout_finalize(RolloutArgs a)
             j < db ? draw_sample(hb, m, (uint32_t)j, a.lo[(size_t)box * a.d + j], a.hi[(size_t)box * a.d + j]) : 0.f;
 }
 
-// Incumbent update: the box with the smallest ub (lowest index on ties) has its
-// best_u re-evaluated in FP64; if the value beats *inc_val, it becomes the incumbent.
+// Incumbent update: the box with the smallest ub (lowest index on ties) has its best_u re-evaluated in FP64; if the
+// value beats *inc_val, it becomes the incumbent.  The FP64 rate of one SM (about one multiply-add per clock) sets
+// the pace of a one-CTA evaluation, so a large network's row is evaluated by a cluster of kIncCTAs CTAs (a small
+// one's by a cluster of one, which leaves the other SMs to the bounds that run beside it): every CTA keeps the whole
+// layer input in its shared memory, computes its share of each layer's outputs (each output's sum split over ks
+// lanes, strided over the inputs, and added across them by shuffles) and writes them into every CTA's shared memory
+// (distributed shared memory); a cluster barrier closes each layer and each step's cost.  The control flow depends
+// only on values every CTA of the cluster computes alike, so all of them reach the same barriers.
+constexpr int kIncCTAs = 8;
+
 __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), ncta = (int)cluster.num_blocks();
     const NetDesc &N = a.net;
     const int nlive = live_count(a.n, a.d_n);
-    // one CTA per problem: its rows, weights, start, goal, horizon, rho and incumbent
-    const int pb = blockIdx.x;
+    // one cluster per problem: its rows, weights, start, goal, horizon, rho and incumbent
+    const int pb = blockIdx.x / ncta;
     const float *raw = a.raw + (size_t)pb * N.raw_floats;
     const float *x0 = a.x0 + (size_t)pb * N.s, *goal = a.goal + (size_t)pb * N.s;
     const int Hb = problem_H(a.batch, pb, a.H);
@@ -223,13 +236,14 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
     __shared__ double xs[kMaxWidth];
     __shared__ double f_sh;
     __shared__ int row_sh;
+    const int lane = threadIdx.x & 31;
     unsigned long long best = ~0ull;
     for (int i = threadIdx.x; i < nlive; i += blockDim.x)
         if (row_problem(a.batch, i) == pb)
             best = umin64(best, ((unsigned long long)float_order(a.ub[i]) << 32) | (unsigned)i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = umin64(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    if (lane == 0) red[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long b = red[0];
@@ -239,7 +253,7 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
     }
     __syncthreads();
     const int row = row_sh;
-    if (row < 0) return;
+    if (row < 0) return;  // the same in every CTA of the cluster
     const float *u = a.best_u + (size_t)row * a.d;
     const int s = N.s, k = N.k;
     double px = (double)a.cost.p0x, py = (double)a.cost.p0y;  // pusher position (obstacle cost; thread 0)
@@ -254,12 +268,24 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
             const int no = N.dims[l], ni = N.dims[l - 1];
             const float *W = raw + N.raw_w[l];
             const float *b = raw + N.raw_b[l];
-            for (int q = threadIdx.x; q < no; q += blockDim.x) {
-                double acc = (double)b[q];
-                for (int c = 0; c < ni; ++c) acc = fma((double)W[(size_t)q * ni + c], act[cur][c], acc);
-                act[cur ^ 1][q] = (l < N.L && acc < 0.0) ? 0.0 : acc;
+            // this CTA's outputs q0 .. q0 + chunk - 1 (chunk <= 256, the widest layer): cp >= chunk slots of ks
+            // lanes each (ks a power of two, at most 32, cp ks <= 256 threads)
+            const int chunk = (no + ncta - 1) / ncta, q0 = rank * chunk;
+            int cp = 1;
+            while (cp < chunk) cp *= 2;
+            const int ks = 256 / cp > 32 ? 32 : 256 / cp;
+            const int ql = (int)threadIdx.x / ks, sl = (int)threadIdx.x % ks, q = q0 + ql;
+            const bool mine = ql < chunk && q < no;
+            double part = 0.0;
+            if (mine)
+                for (int c = sl; c < ni; c += ks) part = fma((double)W[(size_t)q * ni + c], act[cur][c], part);
+            for (int o = ks / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+            if (mine && sl == 0) {
+                double v = (double)b[q] + part;
+                if (l < N.L && v < 0.0) v = 0.0;
+                for (int r2 = 0; r2 < ncta; ++r2) cluster.map_shared_rank(&act[cur ^ 1][0], r2)[q] = v;
             }
-            __syncthreads();
+            cluster.sync();  // every CTA's copy of the layer output complete
             cur ^= 1;
         }
         if (threadIdx.x == 0) {
@@ -281,8 +307,9 @@ __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
             }
             f_sh = f;
         }
-        __syncthreads();
+        cluster.sync();  // the output read before the next step's first layer overwrites it
     }
+    if (rank != 0) return;
     if (threadIdx.x == 0) row_sh = (f_sh < *inc_val) ? 1 : 0;
     __syncthreads();
     if (row_sh) {
@@ -412,7 +439,26 @@ void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st)
 
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st)
 {
-    if (a.n > 0) k_incumbent_fp64<<<a.batch.P > 1 ? a.batch.P : 1, 256, 0, st>>>(a);
+    if (a.n <= 0) return;
+    // a cluster of kIncCTAs for rows of more than 2 M multiply-adds (at about one FP64 multiply-add per clock, a
+    // millisecond on one SM), else one CTA per problem
+    const NetDesc &N = a.net;
+    long long macs = 0;
+    for (int l = 1; l <= N.L; ++l) macs += (long long)N.dims[l] * N.dims[l - 1];
+    const int ncta = macs * a.H > 2000000 ? kIncCTAs : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ncta * (a.batch.P > 1 ? a.batch.P : 1)));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_incumbent_fp64, a);
 }
 
 }  // namespace bab
