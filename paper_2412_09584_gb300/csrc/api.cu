@@ -748,6 +748,10 @@ namespace {
 int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rho, const float *lo, const float *hi,
                  const uint64_t *id, int n, const int *d_n, int samples, uint64_t seed, int precision, float *ub,
                  float *best_u, double *inc_val, float *inc_u, float *costs, void *stream);
+// the head of a rollout call's scratch: the per-box keys, the top-k list, the selection words
+size_t rollout_keys_bytes(int n) { return ((size_t)n * sizeof(unsigned long long) + 255) & ~size_t(255); }
+size_t rollout_list_bytes(int n) { return ((size_t)n * sizeof(int) + 255) & ~size_t(255); }
+size_t rollout_head_bytes(int n) { return rollout_keys_bytes(n) + rollout_list_bytes(n) + 512; }
 }  // namespace
 
 extern "C" {
@@ -782,13 +786,14 @@ int rollout_impl(bab_ctx *c, const float *x0, const float *goal, int H, float rh
         return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core rollout needs hidden widths that are multiples of 32, "
                                             "s <= 32, s + k <= 64 and a weight image that fits in shared memory");
     if (n == 0) return BAB_OK;
-    const size_t key_bytes = ((size_t)n * sizeof(unsigned long long) + 255) & ~size_t(255);
-    rc = ensure_scratch(c, key_bytes + 512);
+    const size_t key_bytes = rollout_keys_bytes(n);
+    rc = ensure_scratch(c, rollout_head_bytes(n));
     if (rc) return rc;
     RolloutArgs a{};
     a.cost = c->cost;
     a.topk = precision == BAB_PREC_BF16 ? c->rescore_topk : 0;
-    a.topk_t = reinterpret_cast<unsigned long long *>(static_cast<char *>(c->scratch) + key_bytes);
+    a.topk_list = reinterpret_cast<int *>(static_cast<char *>(c->scratch) + key_bytes);
+    a.topk_t = reinterpret_cast<unsigned long long *>(static_cast<char *>(c->scratch) + key_bytes + rollout_list_bytes(n));
     a.net = c->net;
     a.batch.P = 1;
     a.batch.Hmax = H;
@@ -851,11 +856,10 @@ int bab_rollout_split(bab_ctx *c, const float *x0, const float *goal, int H, flo
     if (top_k > samples) top_k = samples;
     float *cst = costs;
     if (!cst && n > 0) {
-        // costs in the scratch after the rollout's own keys
-        const size_t key_bytes = ((size_t)n * sizeof(unsigned long long) + 255) & ~size_t(255);
-        int rc = ensure_scratch(c, key_bytes + 512 + (size_t)n * samples * sizeof(float) + 256);
+        // costs in the scratch after the rollout's own keys, top-k list and threshold
+        int rc = ensure_scratch(c, rollout_head_bytes(n) + (size_t)n * samples * sizeof(float) + 256);
         if (rc) return rc;
-        cst = reinterpret_cast<float *>(static_cast<char *>(c->scratch) + key_bytes + 512);
+        cst = reinterpret_cast<float *>(static_cast<char *>(c->scratch) + rollout_head_bytes(n));
     }
     int rc = rollout_impl(c, x0, goal, H, rho, lo, hi, id, n, d_n, samples, seed, precision, ub, best_u, inc_val, inc_u,
                           cst, stream);

@@ -66,7 +66,8 @@ struct RolloutArgs {
     float *costs;        // [n][M] (nullable): every sample's objective as the search computed it
     // BF16 rollouts: re-score in FP32 only the topk boxes of smallest BF16 ub (0: every box)
     int topk;
-    unsigned long long *topk_t;  // [3] scratch: the selection threshold
+    unsigned long long *topk_t;  // [4] scratch: the selection threshold, then the number of boxes it picked
+    int *topk_list;              // [n] scratch: the boxes the top-k selection picked (any order)
     // cross-entropy search (nullable): samples are cem_sample(.., cem_it, m, j, cem_mu[j], cem_sigma[j], ..) of
     // each box's [n][d] mean and spread instead of uniform draws
     const float *cem_mu, *cem_sigma;

@@ -31,6 +31,7 @@
 // Every mbarrier wait is bounded in time; on a time-out the kernel records
 // BAB_ERR_TIMEOUT, stops issuing work, waits (bounded) for its MMAs, frees
 // its TMEM and returns.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "bab_internal.cuh"
@@ -969,13 +970,14 @@ __global__ void __launch_bounds__(NSLOT * (kEpiWarps + 1) * 32, 1) k_rollout_tcf
     }
 }
 
-// BF16 mode: the threshold (order(ub), id) of the topk smallest BF16 upper bounds.
+// BF16 mode: the threshold (order(ub), id) of the topk smallest BF16 upper bounds, and the list of the boxes it
+// picks (in no particular order; each is re-scored on its own)
 __global__ void __launch_bounds__(1024) k_topk_select(RolloutArgs a)
 {
     __shared__ unsigned hist[256];
     __shared__ uint32_t sh_pk;
     __shared__ uint64_t sh_pid;
-    __shared__ int sh_rem, sh_done;
+    __shared__ int sh_rem, sh_done, sh_cnt;
     const int n = live_count(a.n, a.d_n);
     const int K = a.topk < n ? a.topk : n;
     const Thresh T = radix_select(n, a.ub, a.id, [](int) { return true; }, K, hist, &sh_pk, &sh_pid, &sh_rem,
@@ -984,7 +986,14 @@ __global__ void __launch_bounds__(1024) k_topk_select(RolloutArgs a)
         a.topk_t[0] = T.key;
         a.topk_t[1] = T.id;
         a.topk_t[2] = T.none ? 1ull : 0ull;
+        sh_cnt = 0;
     }
+    __syncthreads();
+    if (!T.none)
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (le_thresh(float_order(a.ub[i]), a.id[i], T)) a.topk_list[atomicAdd(&sh_cnt, 1)] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) a.topk_t[3] = (unsigned long long)sh_cnt;
 }
 
 // BF16 mode: the chosen sample of a box is re-scored in FP32 on CUDA cores (a
@@ -1068,6 +1077,88 @@ __global__ void __launch_bounds__(256) k_rescore_fp32(RolloutArgs a)
     }
     if (threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
     __syncthreads();  // before the next box reuses the shared arrays
+    }
+}
+
+// BF16 mode, one problem, top-k re-score of a large network: the boxes of the top-k list, one per thread-block
+// cluster at a time.  Each of the cluster's CTAs stages its share of each layer's columns of W_l^T (at most 32) in
+// shared memory, computes those outputs one per thread (the same sums, in the same order, as k_rescore_fp32 and
+// k_rescore_rows: from the bias over the inputs in order) and writes them into every CTA's shared memory
+// (distributed shared memory); a cluster barrier closes each layer and each step's cost.  The list and its count
+// are the same for every CTA, so all of them reach the same barriers.
+constexpr int kRescoreCTAs = 8;
+template <bool OBST>
+__global__ void __launch_bounds__(256) k_rescore_cl(RolloutArgs a)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), ncta = (int)cluster.num_blocks();
+    const int cl = (int)blockIdx.x / ncta, ncl = (int)gridDim.x / ncta;
+    extern __shared__ float wsl[];  // [inputs][32]: this CTA's columns of W_l^T
+    __shared__ float act[2][kMaxWidth + 4];
+    __shared__ float xs[kMaxWidth];
+    __shared__ float f_sh;
+    const NetDesc &N = a.net;
+    const int s = N.s, k = N.k, d = a.d;
+    const int count = (int)a.topk_t[3];
+    const float *fwd = a.fwd;
+    const float *x0 = a.x0, *goal = a.goal;
+    const float rho = a.rho;
+    for (int e = cl; e < count; e += ncl) {
+        const int box = a.topk_list[e];
+        const unsigned long long key = a.keys[box];
+        const uint32_t m = (uint32_t)(key & 0xFFFFFFFFu);
+        const uint64_t hb = box_hash(a.seed, a.id[box]);
+        const float *blo = a.lo + (size_t)box * d, *bhi = a.hi + (size_t)box * d;
+        for (int i = threadIdx.x; i < s; i += blockDim.x) xs[i] = x0[i];
+        if (threadIdx.x == 0) f_sh = 0.f;
+        float px = OBST ? a.cost.p0x : 0.f, py = OBST ? a.cost.p0y : 0.f;  // pusher position (thread 0)
+        __syncthreads();
+        for (int t = 0; t < a.H; ++t) {
+            for (int c = threadIdx.x; c < s + k; c += blockDim.x)
+                act[0][c] = c < s ? xs[c]
+                                  : draw_sample(hb, m, (uint32_t)(t * k + c - s), blo[t * k + c - s], bhi[t * k + c - s]);
+            __syncthreads();
+            int cur = 0;
+            for (int l = 1; l <= N.L; ++l) {
+                const int no = N.dims[l], ni = N.dims[l - 1], Np = pad4(no);
+                const int chunk = (no + ncta - 1) / ncta, q0 = rank * chunk;  // chunk <= 32: widths <= 256
+                const float *Wt = fwd + N.fwd_w[l];
+                for (int i = threadIdx.x; i < ni * 32; i += blockDim.x) {
+                    const int c = i >> 5, j = i & 31;
+                    wsl[i] = (j < chunk && q0 + j < no) ? __ldg(Wt + (size_t)c * Np + q0 + j) : 0.f;
+                }
+                __syncthreads();
+                const int q = q0 + (int)threadIdx.x;
+                if ((int)threadIdx.x < chunk && q < no) {
+                    float acc = fwd[N.fwd_b[l] + q];
+                    for (int c = 0; c < ni; ++c) acc = fmaf(wsl[c * 32 + threadIdx.x], act[cur][c], acc);
+                    const float v = (l < N.L) ? fmaxf(acc, 0.f) : acc;
+                    for (int r2 = 0; r2 < ncta; ++r2) cluster.map_shared_rank(&act[cur ^ 1][0], r2)[q] = v;
+                }
+                cluster.sync();  // every CTA's copy of the layer output complete, the staged columns free again
+                cur ^= 1;
+            }
+            if (threadIdx.x == 0) {
+                float f = f_sh;
+                for (int j = 0; j < k; ++j) {
+                    const float u = draw_sample(hb, m, (uint32_t)(t * k + j), blo[t * k + j], bhi[t * k + j]);
+                    f = fmaf(rho * u, u, f);
+                    if (OBST && j == 0) px = __fadd_rn(px, u);
+                    if (OBST && j == 1) py = __fadd_rn(py, u);
+                }
+                float c = 0.f;
+                for (int i = 0; i < s; ++i) {
+                    xs[i] = xs[i] + act[cur][i];
+                    const float ee = xs[i] - goal[i];
+                    c = fmaf(ee, ee, c);
+                }
+                if (OBST) c = obstacle_cost_f32(a.cost, t + 1, s, xs, goal, px, py);
+                f_sh = f + c;
+            }
+            cluster.sync();  // the output read before the next step's first layer overwrites it
+        }
+        if (rank == 0 && threadIdx.x == 0) a.ub[box] = f_sh;  // best_u was written by the finalize kernel
     }
 }
 
@@ -1169,6 +1260,26 @@ __global__ void __launch_bounds__(kRescoreThreads) k_rescore_rows(RolloutArgs a)
 static cudaError_t launch_rescore(const RolloutArgs &a, cudaStream_t st)
 {
     const NetDesc &N = a.net;
+    long long macs = 0;
+    for (int l = 1; l <= N.L; ++l) macs += (long long)N.dims[l] * N.dims[l - 1];
+    if (a.batch.P <= 1 && a.topk > 0 && macs * a.H > 2000000) {
+        // a large network's top k: a cluster of kRescoreCTAs per listed box
+        cudaLaunchConfig_t cfg = {};
+        const int ncl = a.topk < 64 ? a.topk : 64;
+        cfg.gridDim = dim3((unsigned)(kRescoreCTAs * ncl));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = (size_t)N.maxw_p * 32 * sizeof(float);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kRescoreCTAs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return a.cost.kind == 1 ? cudaLaunchKernelEx(&cfg, k_rescore_cl<true>, a)
+                                : cudaLaunchKernelEx(&cfg, k_rescore_cl<false>, a);
+    }
     if (a.batch.P > 1 || a.topk > 0) {
         // each box reads its own problem's image; with a top-k selection all but k boxes return at once
         int dev, sms = 1;

@@ -156,3 +156,27 @@ def test_manip_full_batch_sampled(oracle, manip):
     assert np.all(np.abs(c["lb"][rows] + c["margin"][rows] - oc["lb"]) <= drift_tol(p) * scale)
     # a lower bound never exceeds a sampled objective value (up to the FP32 rounding of the rollout)
     assert np.all(c["lb"] <= r["ub"] * (1 + REL))
+
+
+def test_manip_topk_rescore_cluster(oracle, manip):
+    """The configuration's top-k FP32 re-score on this network runs on thread-block clusters (a box per cluster,
+    each CTA a share of every layer's outputs): the picked boxes get exactly the every-box re-score's values (the
+    same sums in the same order), the rest keep their BF16 values, and the re-scored values are the FP32 objective
+    of the picked samples."""
+    from paper_2412_09584_gb300 import binding as B
+    p, g = manip
+    n = 600
+    lo, hi, ids = W.random_boxes(160, n, seed=31, min_width=0.01, max_width=0.3)
+    r_all = g.rollout(lo, hi, ids, M=4, seed=5, precision=B.PREC_BF16)
+    B.bab_set_rescore_topk(g.ctx, 40)
+    try:
+        r = g.rollout(lo, hi, ids, M=4, seed=5, precision=B.PREC_BF16, incumbent=True)
+    finally:
+        B.bab_set_rescore_topk(g.ctx, 0)
+    np.testing.assert_array_equal(r["best_u"], r_all["best_u"])
+    same = r["ub"] == r_all["ub"]
+    assert same.sum() >= 40
+    rows = np.flatnonzero(same)[:6]
+    f = np.array([oracle.objective(p, r["best_u"][i].astype(np.float64)) for i in rows])
+    np.testing.assert_allclose(r["ub"][rows], f, rtol=REL)
+    assert r["inc_val"] == pytest.approx(oracle.objective(p, r["inc_u"].astype(np.float64)), rel=1e-10)
