@@ -204,7 +204,7 @@ class BabState:
 
     def __init__(self, workload, seed, device, n_pick, rollout_prec="bf16x3", bound_prec="fp32", alpha_steps=0,
                  alpha_lr=0.1, samples=None, fixed_launch=False, pool_iters=64, autotune=False, search_stop=None,
-                 heuristics=None, cem=None, cost=None, interval_prec="fp32"):
+                 heuristics=None, cem=None, cost=None, interval_prec="fp32", rescore_topk=0):
         import torch
         from paper_2412_09584_gb300 import binding as B
         from paper_2412_09584_gb300 import workloads as W
@@ -226,6 +226,9 @@ class BabState:
         if interval_prec == "bf16x3":
             # interval bounds on tensor cores (split products with a computed margin)
             B.bab_set_interval_precision(self.ctx, B.PREC_BF16X3)
+        if rescore_topk:
+            # BF16 rollouts: re-score only the boxes of the rescore_topk smallest BF16 upper bounds in FP32
+            B.bab_set_rescore_topk(self.ctx, rescore_topk)
         if cost is not None:
             # the pushing-with-obstacles state cost (Appendix D.4) instead of the squared distance
             B.bab_set_cost(self.ctx, B.COST_PUSHING_OBSTACLES, cost["w"], cost["lam"], cost["obstacles"], cost["p0"])
@@ -738,7 +741,39 @@ def manip_scale(dev, reps=3):
                     "boxes over (bound - ibp) time; weights streamed through shared memory (they exceed it); "
                     "tc_intervals: the interval bounds on tensor cores (3-term BF16 split, computed margin), the "
                     "bound's median loss against FP32 intervals relative to its magnitude",
-            "bounds_below_sampled_ub": sound}
+            "bounds_below_sampled_ub": sound,
+            "iteration": manip_iteration(dev)}
+
+
+def manip_iteration(dev, steps=4):
+    """The object-manipulation configuration as whole BaB iterations: prune + pick-out + bisect of the pool (8192
+    picked, 16384 children), 4 BF16 rollouts per child with the top 64 re-scored in FP32 and the FP64 incumbent on a
+    side stream, interval bounds + 3-term BF16 CROWN; CUDA-graph replays, CUDA events, the pool and its intervals
+    far beyond L2.  With FP32 intervals, then with the intervals on tensor cores."""
+    import torch
+    out = {"workload": "MLP 36-256x4-32, H=40, rho=0.01, 16384 children per iteration (8192 picked, widest-dim "
+                       "bisection), 4 BF16 rollouts each, top 64 re-scored in FP32, FP64 incumbent, CROWN on tcgen05 "
+                       "(3-term BF16 split)"}
+    for iprec in ("fp32", "bf16x3"):
+        st = BabState("manip", SEED, dev, 8192, "bf16", "bf16x3", fixed_launch=True, pool_iters=steps + 10,
+                      interval_prec=iprec, rescore_topk=64)
+        graphs = capture_graphs(st)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(steps):
+            graphs[st.cur].replay()
+            st.cur ^= 1
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / steps
+        out["fp32_intervals" if iprec == "fp32" else "tensor_core_intervals"] = {
+            "ms_per_iteration": ms, "subdomain_bounds_per_s": st.nb / (ms / 1e3),
+            "rollout_steps_per_s": st.nb * st.M * st.H / (ms / 1e3), "steps": steps,
+            "status": st.B.bab_status(st.ctx)}
+        del graphs
+        st.close()
+    return out
 
 
 
