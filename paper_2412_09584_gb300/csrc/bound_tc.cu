@@ -650,10 +650,14 @@ __global__ void __launch_bounds__((NSLOT * (kEpi + 1) + (STREAM ? 1 : 0)) * 32, 
 // tensor core runs the current product.  Each thread keeps, per box, partial sums over its features of the
 // constant (rounded down) and of the rounding-error margin (rounded up); a warp shuffle and the four quadrant
 // warps reduce them per box at the end of the tile.  The state lanes (j < s) carry the coefficient of the state
-// from step to step, the action lanes (s <= j < s + k) write mu.  Squared-distance cost, every width at most 128.
-// TF = false: 3-term BF16 split products, the backward image resident in shared memory.  TF = true: 3-term TF32
-// split products (kind::tf32, K = 8 per instruction), the image (twice the BF16 one) streamed by a producer warp
-// through a ring of 32-wide K blocks in the issuer's order.
+// from step to step, the action lanes (s <= j < s + k) write mu.  Squared-distance cost.
+// TF = false: 3-term BF16 split products; TF = true: 3-term TF32 split products (kind::tf32, K = 8 per
+// instruction, twice the operand bytes).  MB = 1: every width at most 128, tiles of 32 boxes; MB = 2: widths up
+// to 256 as two 128-row feature blocks (two M = 128 products per K step into two accumulators, the second skipped
+// for layers with at most 128 inputs), tiles of 16 boxes, warp (quadrant q, block mb, share h) owning feature
+// j = 128 mb + 32 q + lane.  The backward image stays resident in shared memory for BF16 with one block; otherwise
+// a producer warp streams it through a ring of K blocks (64-wide BF16 or 32-wide TF32, each with the rows of every
+// feature block, hi then lo) in the issuer's order.
 // ---------------------------------------------------------------------------------------------------------------
 constexpr int kNB = 32;  // boxes per tile (the MMA's N) of the one-block kernels: 128 features at most
 // Tile shape of k_crown_tcf with MB 128-row feature blocks: 32 / MB boxes, K up to 128 MB, the B operand's halves.
