@@ -214,7 +214,7 @@ __global__ void k_rollout_finalize(RolloutArgs a)
 // lanes, strided over the inputs, and added across them by shuffles) and writes them into every CTA's shared memory
 // (distributed shared memory); a cluster barrier closes each layer and each step's cost.  The control flow depends
 // only on values every CTA of the cluster computes alike, so all of them reach the same barriers.
-constexpr int kIncCTAs = 8;
+constexpr int kIncCTAs = 16;  // a non-portable cluster size; 8 where the GPU cannot place 16
 
 __global__ void __launch_bounds__(256) k_incumbent_fp64(RolloutArgs a)
 {
@@ -440,12 +440,34 @@ void launch_rollout_finalize(const RolloutArgs &a, cudaStream_t st)
 void launch_incumbent(const RolloutArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return;
-    // a cluster of kIncCTAs for rows of more than 2 M multiply-adds (at about one FP64 multiply-add per clock, a
-    // millisecond on one SM), else one CTA per problem
+    // a cluster of kIncCTAs (else 8) for rows of more than 2 M multiply-adds (at about one FP64 multiply-add per
+    // clock, a millisecond on one SM), else one CTA per problem
     const NetDesc &N = a.net;
     long long macs = 0;
     for (int l = 1; l <= N.L; ++l) macs += (long long)N.dims[l] * N.dims[l - 1];
-    const int ncta = macs * a.H > 2000000 ? kIncCTAs : 1;
+    int ncta = macs * a.H > 2000000 ? kIncCTAs : 1;
+    // whether this GPU places a 16-CTA cluster of the kernel (non-portable size): decided at the first large launch,
+    // which runs eagerly before any graph capture, and kept (one device per process)
+    static int big_ok = -1;
+    if (ncta > 8 && big_ok < 0) {
+        big_ok = 0;
+        if (cudaFuncSetAttribute(k_incumbent_fp64, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3((unsigned)ncta);
+            q.blockDim = dim3(256);
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = (unsigned)ncta;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int nclusters = 0;
+            big_ok = cudaOccupancyMaxActiveClusters(&nclusters, k_incumbent_fp64, &q) == cudaSuccess && nclusters >= 1;
+        }
+        cudaGetLastError();
+    }
+    if (ncta > 8 && !big_ok) ncta = 8;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(ncta * (a.batch.P > 1 ? a.batch.P : 1)));
     cfg.blockDim = dim3(256);
