@@ -62,3 +62,27 @@ def test_static_bound_refuses_sizes_beyond_its_array_on_the_host(lib):
                                       fake, 1, fake, None, None) == -2
     assert lib.bab_bound_crown_static(4, dims, fake, 8, 2, fake, fake, 20, ctypes.c_float(-1.0), fake, fake, 1,
                                       fake, None, None) == -1
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define of include/bab.h that the binding mirrors (BAB_<NAME> as <NAME>, the error codes in
+    ERRORS) has the same value on both sides."""
+    import os
+    import re
+    from paper_2412_09584_gb300 import binding
+    text = open(binding.HEADER).read()
+    defines = {}
+    for name, val in re.findall(r"^#define (BAB_[A-Z0-9_]+)\s+\(?(-?\d+)u?\)?", text, flags=re.M):
+        defines[name] = int(val)
+    assert defines["BAB_PREC_TF32X3"] == 3 and defines["BAB_ERR_UNSUPPORTED"] == -7
+    mirrored = 0
+    for name, val in defines.items():
+        short = name[len("BAB_"):]
+        if hasattr(binding, short):
+            assert getattr(binding, short) == val, name
+            mirrored += 1
+        if name.startswith("BAB_ERR_"):
+            assert binding.ERRORS[val] == name
+    assert defines["BAB_OK"] == binding.BAB_OK
+    assert mirrored >= 12
+    assert os.path.exists(binding.HEADER)
