@@ -295,8 +295,11 @@ class BabState:
         # Algorithm 2 starts by searching and bounding the starting pool
         self.search_and_bound(P, n0, None)
         fused = alpha_steps and self.bprec == B.PREC_FP32 and (self.variants or {}).get("alpha_fused", -1) != -2
-        # prune/branch 2, rollout 4 (keys, rollout, finalize, incumbent), bound 2 (or the alpha loop)
-        self.launches_per_step = 2 + 4 + (2 if not alpha_steps else (2 if fused else 3 + alpha_steps * 3))
+        # prune/branch 2, rollout 4 (keys, rollout, finalize, incumbent) plus the FP32 re-score of BF16 rollouts (and
+        # the top-k selection before it), bound 2 (or the alpha loop)
+        bf16 = self.rprec == PRECISIONS["bf16"]
+        roll = 4 + (1 if bf16 else 0) + (1 if bf16 and rescore_topk else 0)
+        self.launches_per_step = 2 + roll + (2 if not alpha_steps else (2 if fused else 3 + alpha_steps * 3))
 
     def snapshot(self):
         """Device copies of the BaB state (both pools, counts, incumbent), to rerun the same iterations."""
