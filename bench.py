@@ -223,9 +223,9 @@ class BabState:
         self.alpha_steps, self.alpha_lr = alpha_steps, alpha_lr
         self.ctx = B.bab_load_dynamics(self.p["dims"], self.p["params"], self.p["s"], self.p["k"])
         self.iprec = interval_prec
-        if interval_prec == "bf16x3":
-            # interval bounds on tensor cores (split products with a computed margin)
-            B.bab_set_interval_precision(self.ctx, B.PREC_BF16X3)
+        if interval_prec != "fp32":
+            # interval bounds on tensor cores (3-term BF16 or TF32 split products with a computed margin)
+            B.bab_set_interval_precision(self.ctx, BOUND_PRECISIONS[interval_prec])
         if rescore_topk:
             # BF16 rollouts: re-score only the boxes of the rescore_topk smallest BF16 upper bounds in FP32
             B.bab_set_rescore_topk(self.ctx, rescore_topk)
@@ -552,8 +552,9 @@ def run_ours(args):
                        f"rho=0.01, {st.nb} children bounded per iteration ({n_pick} picked, widest-dim bisection), "
                        f"{st.M} uniform rollouts per child",
            "rollout_arithmetic": ARITH[args.precision],
-           "bound_arithmetic": ("interval bounds on tcgen05 (3-term BF16 split, computed margin)"
-                                if args.interval_precision == "bf16x3" else "outward-rounded FP32 intervals") +
+           "bound_arithmetic": {"bf16x3": "interval bounds on tcgen05 (3-term BF16 split, computed margin)",
+                                "tf32x3": "interval bounds on tcgen05 (3-term TF32 split, computed margin)",
+                                "fp32": "outward-rounded FP32 intervals"}[args.interval_precision] +
                                "; CROWN products " +
                                {"bf16x3": "on tcgen05, 3-term BF16 split", "tf32x3": "on tcgen05, 3-term TF32 split",
                                 "fp32": "in FP32 on CUDA cores"}[args.bound_precision] + ", margin-corrected",
@@ -726,6 +727,12 @@ def manip_scale(dev, reps=3):
     sound = sound and bool((lb <= ub).all().item())
     # how much of the bound the wider intervals give up, relative to the bound's magnitude (median over boxes)
     loss = float(((lb_f - lb).abs() / lb_f.abs().clamp_min(1.0)).median().item())
+    # the same with TF32 halves (a smaller margin per layer)
+    B.bab_set_interval_precision(ctx, B.PREC_TF32X3)
+    t_ibp_tf = timed(lambda: B.bab_bound_ibp(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb32))
+    t_tc_tf = timed(lambda: B.bab_bound_crown(ctx, x0, goal, H, p["rho"], tlo, thi, n, lb, precision=B.PREC_BF16X3))
+    sound = sound and bool((lb <= ub).all().item())
+    loss_tf = float(((lb_f - lb).abs() / lb_f.abs().clamp_min(1.0)).median().item())
     B.bab_set_interval_precision(ctx, B.PREC_FP32)
     B.bab_destroy(ctx)
     macs = sum(a * b for a, b in zip(p["dims"][1:], p["dims"][:-1]))
@@ -740,10 +747,14 @@ def manip_scale(dev, reps=3):
             "ibp_tensor_core_ms": t_ibp_tc, "bound_bf16x3_tc_intervals_ms": t_tc_tc,
             "subdomain_bounds_per_s_tc_intervals": n / (t_tc_tc / 1e3),
             "tc_intervals_bound_loss_median": loss,
+            "ibp_tensor_core_tf32_ms": t_ibp_tf, "bound_bf16x3_tf32_intervals_ms": t_tc_tf,
+            "subdomain_bounds_per_s_tf32_intervals": n / (t_tc_tf / 1e3),
+            "tf32_intervals_bound_loss_median": loss_tf,
             "note": "bound times include the interval bounds (ibp_ms); backward TFLOP/s = algorithmic 2 x MACs x H x "
                     "boxes over (bound - ibp) time; weights streamed through shared memory (they exceed it); "
                     "tc_intervals: the interval bounds on tensor cores (3-term BF16 split, computed margin), the "
-                    "bound's median loss against FP32 intervals relative to its magnitude",
+                    "bound's median loss against FP32 intervals relative to its magnitude; tf32_intervals: the same "
+                    "with 3-term TF32 halves",
             "bounds_below_sampled_ub": sound,
             "iteration": manip_iteration(dev)}
 
@@ -752,12 +763,13 @@ def manip_iteration(dev, steps=4):
     """The object-manipulation configuration as whole BaB iterations: prune + pick-out + bisect of the pool (8192
     picked, 16384 children), 4 BF16 rollouts per child with the top 64 re-scored in FP32 and the FP64 incumbent on a
     side stream, interval bounds + 3-term BF16 CROWN; CUDA-graph replays, CUDA events, the pool and its intervals
-    far beyond L2.  With FP32 intervals, then with the intervals on tensor cores."""
+    far beyond L2.  With FP32 intervals, then with the intervals on tensor cores (BF16, then TF32 halves)."""
     import torch
     out = {"workload": "MLP 36-256x4-32, H=40, rho=0.01, 16384 children per iteration (8192 picked, widest-dim "
                        "bisection), 4 BF16 rollouts each, top 64 re-scored in FP32, FP64 incumbent, CROWN on tcgen05 "
                        "(3-term BF16 split)"}
-    for iprec in ("fp32", "bf16x3"):
+    keys = {"fp32": "fp32_intervals", "bf16x3": "tensor_core_intervals", "tf32x3": "tensor_core_tf32_intervals"}
+    for iprec in ("fp32", "bf16x3", "tf32x3"):
         st = BabState("manip", SEED, dev, 8192, "bf16", "bf16x3", fixed_launch=True, pool_iters=steps + 10,
                       interval_prec=iprec, rescore_topk=64)
         graphs = capture_graphs(st)
@@ -770,7 +782,7 @@ def manip_iteration(dev, steps=4):
         t1.record()
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1) / steps
-        out["fp32_intervals" if iprec == "fp32" else "tensor_core_intervals"] = {
+        out[keys[iprec]] = {
             "ms_per_iteration": ms, "subdomain_bounds_per_s": st.nb / (ms / 1e3),
             "rollout_steps_per_s": st.nb * st.M * st.H / (ms / 1e3), "steps": steps,
             "status": st.B.bab_status(st.ctx)}
@@ -1212,8 +1224,9 @@ def time_to_gap(dev, workload="alpha", n_pick=2048, iters=20, max_iters=60, vari
     # plus 5 Adam steps per iteration (alpha_split_20: 20), each a tensor-core CROWN + adjoint + Adam launch;
     # alpha_fused: 3-term BF16 rollouts plus the 20-step alpha-CROWN loop in one FP32 launch per iteration;
     # alpha_fused_5, alpha_fused_2: the same with 5 or 2 Adam steps (the bound gains most in the first steps);
-    # *_tc_intervals: the interval bounds on tensor cores as well; headline*: the bench's own arithmetic (BF16
-    # rollouts with the picks re-scored in FP32, tensor-core CROWN), plain or with 2 tensor-core Adam steps
+    # *_tc_intervals (*_tf32_intervals): the interval bounds on tensor cores as well, BF16 (TF32) halves;
+    # headline*: the bench's own arithmetic (BF16 rollouts with the picks re-scored in FP32, tensor-core CROWN),
+    # plain or with 2 tensor-core Adam steps
     if variants is None:
         variants = {"plain_fp32": ("fp32", "fp32", 0), "split": ("bf16x3", "bf16x3", 0),
                     "alpha_split": ("bf16x3", "bf16x3", 5), "alpha_split_20": ("bf16x3", "bf16x3", 20),
@@ -1261,7 +1274,8 @@ def time_to_gap_pushing(dev):
                 "split_tc_intervals": ("bf16x3", "bf16x3", 0, "bf16x3"),
                 "alpha_split_tc_intervals": ("bf16x3", "bf16x3", 5, "bf16x3"),
                 "headline": ("bf16", "bf16x3", 0), "headline_alpha_2": ("bf16", "bf16x3", 2),
-                "headline_tc_intervals": ("bf16", "bf16x3", 0, "bf16x3")}
+                "headline_tc_intervals": ("bf16", "bf16x3", 0, "bf16x3"),
+                "headline_tf32_intervals": ("bf16", "bf16x3", 0, "tf32x3")}
     return time_to_gap(dev, "pushing", n_pick=256, iters=10, max_iters=30, variants=variants)
 
 
@@ -1427,8 +1441,9 @@ def main():
     ap.add_argument("--no-precision-lines", action="store_true",
                     help="skip the same iteration with the rollouts in the other arithmetics")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--interval-precision", choices=["fp32", "bf16x3"], default="fp32",
-                    help="interval bounds: fp32 (directed rounding, CUDA cores) or bf16x3 (tcgen05, computed margin)")
+    ap.add_argument("--interval-precision", choices=["fp32", "bf16x3", "tf32x3"], default="fp32",
+                    help="interval bounds: fp32 (directed rounding, CUDA cores), bf16x3 or tf32x3 (tcgen05, 3-term "
+                         "split, computed margin)")
     ap.add_argument("--bound-precision", choices=sorted(BOUND_PRECISIONS), default="bf16x3",
                     help="CROWN products: fp32 (CUDA cores), bf16x3 or tf32x3 (tcgen05, 3-term split, "
                          "margin-corrected)")

@@ -61,7 +61,7 @@ extern "C" {
 #define BAB_PREC_FP32 0    /* FP32 on CUDA cores (round-to-nearest FMA chains) */
 #define BAB_PREC_BF16X3 1  /* tcgen05 tensor cores, 3-term BF16 split operands, FP32 accumulate */
 #define BAB_PREC_BF16 2    /* tcgen05 tensor cores, BF16 operands, FP32 accumulate (rollouts only) */
-#define BAB_PREC_TF32X3 3  /* tcgen05 tensor cores, 3-term TF32 split operands, FP32 accumulate (CROWN and alpha only) */
+#define BAB_PREC_TF32X3 3  /* tcgen05 tensor cores, 3-term TF32 split operands, FP32 accumulate (CROWN, alpha, intervals) */
 
 /* Split rules of bab_prune_branch. */
 #define BAB_SPLIT_WIDEST 0 /* bisect the widest coordinate (Section 3.1), lowest index on ties */
@@ -642,11 +642,15 @@ int bab_set_scratch_limit(bab_ctx *ctx, size_t bytes);
  * products and |W| (|c| + r) as one BF16 product, the intervals widened by
  * gamma_split(K) |W| (|c| + r) (about 5e-5 of it): sound, and containing the
  * exact interval bounds, but wider than the FP32 ones by that margin per layer.
+ * BAB_PREC_TF32X3: the same products from TF32 halves (16 boxes a tile), the
+ * widening gamma_tf32(K) |W| (|c| + r) = (3.1 * 2^-22 + K 2^-23 / (1 - K 2^-23))
+ * |W| (|c| + r), K the layer's inputs rounded up to 8: about a quarter of the
+ * BF16 split's at K = 128, the accumulation term then dominating.
  * The weights are streamed through shared memory, so the network need not fit
  * there.  Squared-distance cost only (other costs keep the FP32 intervals).
  * No counterpart in the paper beyond Lemma 1's input.
  * Errors: BAB_ERR_INVALID_ARG (unknown precision), BAB_ERR_UNSUPPORTED
- * (BF16X3 with a batch of several problems, or a width above 256).
+ * (BF16X3 or TF32X3 with a batch of several problems, or a width above 256).
  */
 int bab_set_interval_precision(bab_ctx *ctx, int precision);
 

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "bab_internal.cuh"
+#include "ibp_tc.cuh"
 #include "kernels.cuh"
 
 using namespace bab;
@@ -20,9 +21,10 @@ struct bab_ctx {
     NetDesc net{};
     float *d_raw = nullptr, *d_fwd = nullptr, *d_bwd = nullptr;
     uint8_t *d_tc = nullptr, *d_tcb = nullptr;
-    uint8_t *d_ibp = nullptr;   // the tensor-core interval image (problem 0)
-    uint8_t *d_tf = nullptr;    // the backward TF32 image (problem 0)
-    int interval_precision = 0; // bab_set_interval_precision: BAB_PREC_FP32 (0) or BAB_PREC_BF16X3
+    uint8_t *d_ibp = nullptr;    // the tensor-core interval image, BF16 halves (problem 0)
+    uint8_t *d_ibp_tf = nullptr; // the tensor-core interval image, TF32 halves (problem 0)
+    uint8_t *d_tf = nullptr;     // the backward TF32 image (problem 0)
+    int interval_precision = 0;  // bab_set_interval_precision: BAB_PREC_FP32 (0), BAB_PREC_BF16X3 or BAB_PREC_TF32X3
     float *d_tc_bias = nullptr;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -145,6 +147,34 @@ void build_ibp_tc_image(NetDesc &N, const float *params, std::vector<uint8_t> &i
                 std::memcpy(&img[stage + 16384 + o], &wl, 2);
                 std::memcpy(&img[stage + 32768 + o], &ah, 2);
                 std::memcpy(&img[stage + 49152 + o], &al, 2);
+            }
+    }
+}
+
+// The TF32 interval image (layout in ibp_tc.cuh): the same four A operands as the BF16 one, as TF32 halves (each
+// rounded to nearest, ties away), 32 inputs a 128-byte row.  Empty unless the BF16 one is built (N.ibp_ok).
+void build_ibp_tf_image(const NetDesc &N, const float *params, std::vector<uint8_t> &img)
+{
+    img.clear();
+    if (!N.ibp_ok) return;
+    std::vector<size_t> off(N.L + 2, 0);
+    for (int l = 1; l <= N.L; ++l) off[l + 1] = off[l] + (size_t)N.ibp_mb[l] * ibp_tf_ka(N.dims[l - 1]) * 65536;
+    img.assign(off[N.L + 1], 0);
+    for (int l = 1; l <= N.L; ++l) {
+        const int no = N.dims[l], ni = N.dims[l - 1], nka = ibp_tf_ka(ni);
+        const float *W = params + N.raw_w[l];
+        for (int n = 0; n < no; ++n)
+            for (int kk = 0; kk < ni; ++kk) {
+                const float w = W[(size_t)n * ni + kk], a = std::fabs(w);
+                const int mb = n / 128, row = n % 128, ka = kk / 32, within = kk % 32;
+                const size_t stage = off[l] + ((size_t)mb * nka + ka) * 65536;
+                const size_t o = (size_t)row * 128 + (size_t)((((within * 4) / 16) ^ (row % 8)) * 16) + (size_t)((within * 4) % 16);
+                const float wh = tf32_rna_host(w), wl = tf32_rna_host(w - wh);
+                const float ah = tf32_rna_host(a), al = tf32_rna_host(a - ah);
+                std::memcpy(&img[stage + o], &wh, 4);
+                std::memcpy(&img[stage + 16384 + o], &wl, 4);
+                std::memcpy(&img[stage + 32768 + o], &ah, 4);
+                std::memcpy(&img[stage + 49152 + o], &al, 4);
             }
     }
 }
@@ -432,9 +462,11 @@ int run_ibp(bab_ctx *c, BoundArgs &a, Carver &cv, float *pre_lo, float *pre_hi, 
     a.x_hi = x_hi ? x_hi : cv.take<float>(nx);
     a.S = cv.take<float>((size_t)a.n * a.H * (N.sumh + N.s));
     a.lb_ibp = lb_ibp;
-    a.ibp_img = c->d_ibp;
-    const bool tc = c->interval_precision == BAB_PREC_BF16X3 && a.batch.P <= 1 && a.cost.kind == 0;
-    cudaError_t e = tc ? launch_ibp_tc(a, c->num_sms, st) : launch_ibp(a, c->num_sms, st);
+    const bool tc = c->interval_precision != BAB_PREC_FP32 && a.batch.P <= 1 && a.cost.kind == 0;
+    const bool tf = c->interval_precision == BAB_PREC_TF32X3;
+    a.ibp_img = tf ? c->d_ibp_tf : c->d_ibp;
+    cudaError_t e = !tc ? launch_ibp(a, c->num_sms, st)
+                        : (tf ? launch_ibp_tc_tf32(a, c->num_sms, st) : launch_ibp_tc(a, c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "interval bounds kernel");
     return BAB_OK;
 }
@@ -524,10 +556,11 @@ int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *
         tc_img.insert(tc_img.end(), im.begin(), im.end());
         tc_bias.insert(tc_bias.end(), bi.begin(), bi.end());
     }
-    std::vector<uint8_t> tcb_img, ibp_img, tf_img;
+    std::vector<uint8_t> tcb_img, ibp_img, ibp_tf_img, tf_img;
     build_tcb_image(N, params, tcb_img);
     build_tf_image(N, params, tf_img);
     build_ibp_tc_image(N, params, ibp_img);
+    build_ibp_tf_image(N, params, ibp_tf_img);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -539,6 +572,9 @@ int load_impl(bab_ctx **out, int P, int n_layers, const int *dims, const float *
     if (e == cudaSuccess && !ibp_img.empty()) e = cudaMalloc(&c->d_ibp, ibp_img.size());
     if (e == cudaSuccess && !ibp_img.empty())
         e = cudaMemcpy(c->d_ibp, ibp_img.data(), ibp_img.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ibp_tf_img.empty()) e = cudaMalloc(&c->d_ibp_tf, ibp_tf_img.size());
+    if (e == cudaSuccess && !ibp_tf_img.empty())
+        e = cudaMemcpy(c->d_ibp_tf, ibp_tf_img.data(), ibp_tf_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_bias, sizeof(float) * tc_bias.size());
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tc, tc_img.data(), tc_img.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -719,6 +755,7 @@ int bab_destroy(bab_ctx *c)
     cudaFree(c->d_tc);
     cudaFree(c->d_tcb);
     cudaFree(c->d_ibp);
+    cudaFree(c->d_ibp_tf);
     cudaFree(c->d_tf);
     cudaFree(c->d_tc_bias);
     cudaFree(c->scratch);
@@ -1751,7 +1788,8 @@ int bab_set_interval_precision(bab_ctx *c, int precision)
         c->interval_precision = precision;
         return BAB_OK;
     }
-    if (precision != BAB_PREC_BF16X3) return fail(c, BAB_ERR_INVALID_ARG, "interval precision %d unknown", precision);
+    if (precision != BAB_PREC_BF16X3 && precision != BAB_PREC_TF32X3)
+        return fail(c, BAB_ERR_INVALID_ARG, "interval precision %d unknown", precision);
     if (c->n_problems > 1 || !ibp_tc_supported(c->net, c->max_smem))
         return fail(c, BAB_ERR_UNSUPPORTED, "tensor-core interval bounds need one network with every width at most 256");
     c->interval_precision = precision;
