@@ -594,6 +594,8 @@ def precision_lines(dev, seed, n_pick, headline, bound_precision, interval_preci
     combos += [(headline, other_bound, interval_precision), (headline, bound_precision, other_int)]
     if bound_precision != "tf32x3":
         combos.append((headline, "tf32x3", interval_precision))
+    if interval_precision != "tf32x3":
+        combos.append((headline, bound_precision, "tf32x3"))
     for prec, bprec, iprec in combos:
         key = prec if bprec == bound_precision else f"{prec}, {bprec} CROWN products"
         if iprec != interval_precision:
