@@ -1342,3 +1342,104 @@ def test_margin_one_hidden_layer_closed_form(oracle):
         assert got == pytest.approx(expect, rel=1e-12)
         return
     pytest.fail("no network with the wanted neuron pattern was drawn")
+
+
+def _ru32(x):
+    """float64 values rounded up to float32."""
+    y = np.asarray(x, np.float64).astype(np.float32)
+    return np.where(y.astype(np.float64) < x, np.nextafter(y, np.float32(np.inf)), y)
+
+
+def _rd32(x):
+    """float64 values rounded down to float32."""
+    y = np.asarray(x, np.float64).astype(np.float32)
+    return np.where(y.astype(np.float64) > x, np.nextafter(y, np.float32(-np.inf)), y)
+
+
+def _sum32(terms, order, rng):
+    """Sum of terms [T][...] in float32, one rounding to nearest per addition, in 'fwd', 'rev' or 'perm' order."""
+    idx = np.arange(terms.shape[0])
+    if order == "rev":
+        idx = idx[::-1]
+    elif order == "perm":
+        idx = rng.permutation(idx)
+    acc = np.zeros(terms.shape[1:], np.float32)
+    for i in idx:
+        acc = (acc + terms[i]).astype(np.float32)
+    return acc
+
+
+@pytest.mark.parametrize("kind,K", [("bf16", 16), ("bf16", 36), ("bf16", 256), ("tf32", 8), ("tf32", 36),
+                                    ("tf32", 256)])
+def test_interval_split_margin_contains_exact_layer_interval(kind, K):
+    """One layer of the tensor-core interval bounds (the intermediate bounds of Lemma 1, Appendix B.1), written
+    out on the CPU in the kernel's steps: each input interval [l, u] in centre-radius form (c rounded to nearest,
+    r and |c| + r rounded up), c and r as hi and lo halves (BF16 or TF32), W and |W| the same; zc = W c and
+    zr = |W| r as 3-term split products and zs = |W|_hi (|c| + r)_hi, each accumulated in float32 in three orders;
+    S' = zs (1 + 2^-6) for BF16 halves, (1 + 2^-9) for TF32, and the interval [zc + b - zr - eps S',
+    zc + b + zr + eps S'] with every addition rounded outward, eps = 3.1 2^-16 (BF16) or 3.1 2^-22 (TF32) plus
+    K' 2^-23 / (1 - K' 2^-23), K' = K rounded up to 16 (BF16) or 8 (TF32).  It must contain the exact interval
+    sum_k min(W_jk l_k, W_jk u_k) + b_j .. sum_k max(..) + b_j (each sum by math.fsum over the exact float64
+    products of float32 values), for boxes of every width down to points and weights over five binades; without
+    the eps S' term it does not, and the TF32 widening is at most half the BF16 one.  Planted in a copy: the BF16
+    halves charged the TF32 representation term, |W| replaced by W in zr, or the W_lo c_hi term dropped each
+    fail."""
+    import math
+    rng = np.random.default_rng(100 + K + (0 if kind == "bf16" else 1000))
+    nout, nbox = 48, 40
+    Wm = (rng.standard_normal((nout, K)) * np.exp2(rng.integers(-3, 2, (nout, K)))).astype(np.float32)
+    b = rng.standard_normal(nout).astype(np.float32)
+    c0 = rng.uniform(-4.0, 4.0, (nbox, K))
+    w = rng.uniform(0.0, 2.0, (nbox, K)) * (rng.random((nbox, K)) < 0.8)
+    l, u = (c0 - w).astype(np.float32), (c0 + w).astype(np.float32)
+    assert np.all(l <= u)
+    # exact interval of W a + b over the box
+    lo_x = np.empty((nbox, nout))
+    hi_x = np.empty((nbox, nout))
+    Wd, ld, ud = Wm.astype(np.float64), l.astype(np.float64), u.astype(np.float64)
+    for n in range(nbox):
+        p1, p2 = Wd * ld[n][None, :], Wd * ud[n][None, :]
+        mn, mx = np.minimum(p1, p2), np.maximum(p1, p2)
+        for j in range(nout):
+            lo_x[n, j] = math.fsum(list(mn[j]) + [float(b[j])])
+            hi_x[n, j] = math.fsum(list(mx[j]) + [float(b[j])])
+
+    def layer(kind_, widen=True, order="fwd"):
+        f32 = np.float32
+        c = (f32(0.5) * (l + u).astype(f32)).astype(f32)
+        r = np.maximum(_ru32(ud - c.astype(np.float64)), _ru32(c.astype(np.float64) - ld))
+        m = _ru32(np.abs(c).astype(np.float64) + r.astype(np.float64))
+        ch, cl = _split(c, kind_)
+        rh, rl = _split(r, kind_)
+        mh = _round_half(m, kind_)
+        Wh, Wl = _split(Wm, kind_)
+        Ah, Al = _split(np.abs(Wm), kind_)
+        # products [K][box][out]: exact in float32 (8 + 8 or 11 + 11 significant bits)
+        pr = lambda A, x: (x.T[:, :, None] * A.T[:, None, :]).astype(f32)
+        zc = _sum32(np.concatenate([pr(Wh, ch), pr(Wl, ch), pr(Wh, cl)]), order, rng)
+        zr = _sum32(np.concatenate([pr(Ah, rh), pr(Al, rh), pr(Ah, rl)]), order, rng)
+        zs = _sum32(pr(Ah, mh), order, rng)
+        if kind_ == "bf16":
+            Kp, rep, s_up = (K + 15) // 16 * 16, 3.1 * 2.0 ** -16, 1 + 2.0 ** -6
+        else:
+            Kp, rep, s_up = (K + 7) // 8 * 8, 3.1 * 2.0 ** -22, 1 + 2.0 ** -9
+        eps = np.float32(rep + Kp * 2.0 ** -23 / (1 - Kp * 2.0 ** -23))
+        Sp = _ru32(zs.astype(np.float64) * s_up)
+        es = _ru32(np.float64(eps) * Sp.astype(np.float64)) if widen else np.zeros_like(Sp)
+        rad = _ru32(zr.astype(np.float64) + es.astype(np.float64))
+        zb_d = _rd32(zc.astype(np.float64) + b.astype(np.float64)[None, :])
+        zb_u = _ru32(zc.astype(np.float64) + b.astype(np.float64)[None, :])
+        return (_rd32(zb_d.astype(np.float64) - rad.astype(np.float64)).astype(np.float64),
+                _ru32(zb_u.astype(np.float64) + rad.astype(np.float64)).astype(np.float64))
+
+    for order in ("fwd", "rev", "perm"):
+        lo_g, hi_g = layer(kind, order=order)
+        assert np.all(lo_g <= lo_x) and np.all(hi_g >= hi_x), order
+    lo_n, hi_n = layer(kind, widen=False)
+    assert np.any(lo_n > lo_x) or np.any(hi_n < hi_x)  # the margin is needed
+    if K >= 32:
+        wide = {}
+        for k_ in ("bf16", "tf32"):
+            lo_g, hi_g = layer(k_)
+            wide[k_] = float(np.sum((hi_g - lo_g) - (hi_x - lo_x)))
+        assert 0.0 < wide["tf32"] <= 0.5 * wide["bf16"]
