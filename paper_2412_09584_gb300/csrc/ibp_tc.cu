@@ -109,7 +109,7 @@ template <bool TF> __device__ __forceinline__ void mma_(uint32_t d, uint64_t a, 
         tc::mma_ss(d, a, b, idesc, acc);
 }
 
-// 64 KB stages of layer l's image (row blocks x input blocks) and its k-steps (16 BF16 or 8 TF32 inputs each)
+// input blocks of layer l (64 BF16 or 32 TF32 inputs each): its image has one 64 KB stage per row block and block
 template <bool TF> __device__ __forceinline__ int n_ka(const NetDesc &N, int l)
 {
     return TF ? ibp_tf_ka(N.dims[l - 1]) : N.ibp_ka[l];
