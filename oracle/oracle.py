@@ -15,12 +15,21 @@ citations are to arXiv 2412.09584 (BaB-ND):
 * ``crown``         Appendix B.1, Lemma 1, Theorem 1, Theorem 2 (box form)
 * ``crown_margin``  the same bound with the outward rounding margin of an FP32 / split-BF16 / split-TF32 evaluation
 * ``alpha_grad``    gradient of the Theorem 1/2 bound in the Lemma 1 slopes
-* ``adam_ascent``   projected Adam on the slopes
+* ``alpha_optimize`` the Adam loop on those slopes (``adam_ascent``: one projected Adam step)
+* ``box_grad``      gradient of the bound in the box faces, the relaxation choices held fixed
+* ``search_bounds`` Section 3.2: per box the extremes over its samples of every pre-activation and state
+* ``crown_given``   Appendix B.2, Algorithm 3: CROWN on given intermediate bounds with propagation early stop
 * ``prune_branch``  Section 3 overview (Pruner), Section 3.1 (pick out, split)
+* ``prune_branch_heuristic``, ``split_dims``  Section 3.1: pick-out by upper bound plus softmax sampling over
+  scaled lower bounds; split dimension by the sample imbalance of the top samples
 * ``bab``           Algorithm 2 (search, bound, incumbent, prune, pick, split)
 * ``objective_f32`` Eq. (trajop) in FP32 (the precision the search ranks in)
 * ``cem``           Section 3.3 (batch_search with the cross-entropy method)
+* ``set_cost``      Appendix D.4, Eq. (pushing_cost): weighted norm and obstacle penalties
 * ``synth_*``       Section 4, synthetic example f(u) = sum 5 u_i^2 + cos(50 u_i)
+
+Every function is pinned in ``tests/test_oracle_pins.py`` against closed forms, brute force, invariants or
+hand-worked values (``tests/golden/``).
 """
 from __future__ import annotations
 
