@@ -707,14 +707,17 @@ __device__ __forceinline__ void st_split(uint8_t *bop, uint32_t half, int n, int
 
 // Lemma 1's relaxation without branches (the lanes of a warp hold different neurons).  The upper slope of an
 // unstable neuron is a fast quotient bounded upward: any slope at least u / (u - l) gives a valid upper line
-// through (l, 0), and the quotient of __fdividef (2 ulp) over the denominator rounded down, scaled up by
-// 2^-20 and capped at 1, is one; slope 1 where the quotient could be inexact (huge denominator, tiny numerator).
+// through (l, 0), and the quotient of __fdividef over the denominator rounded down (den in [1e-30, 1e36], so
+// within 2 ulp wherever the quotient is a normal number), scaled up by 2^-20, raised to at least 2^-99 and capped
+// at 1, is one: a quotient below 2^-126, whose rounding the bound does not cover, means a chord below 2^-126.
+// Slope 1 where the quotient could be inexact otherwise (huge denominator, tiny numerator).
 __device__ __forceinline__ void relax_nb(float zl, float zu, float A, float alpha_j, bool has_alpha, float &D, float &c)
 {
     const bool on = zl >= 0.f, off = zu <= 0.f;
     const float den = __fsub_rd(zu, zl);
     const bool fast = den < 1e36f && zu > 1e-30f;
-    const float du = fast ? fminf(__fmul_ru(__fdividef(zu, den), 1.00000095367431640625f), 1.f) : 1.f;
+    const float du =
+        fast ? fminf(fmaxf(__fmul_ru(__fdividef(zu, den), 1.00000095367431640625f), 0x1p-99f), 1.f) : 1.f;
     const float lower = has_alpha ? alpha_j : (zu >= -zl ? 1.f : 0.f);
     const bool up = !on && !off && A < 0.f;
     D = on ? 1.f : (off ? 0.f : (up ? du : lower));

@@ -1443,3 +1443,48 @@ def test_interval_split_margin_contains_exact_layer_interval(kind, K):
             lo_g, hi_g = layer(k_)
             wide[k_] = float(np.sum((hi_g - lo_g) - (hi_x - lo_x)))
         assert 0.0 < wide["tf32"] <= 0.5 * wide["bf16"]
+
+
+def test_fast_upper_slope_is_at_least_the_chord():
+    """Reading of Lemma 1's upper line in the feature-major CROWN: any slope at least the chord u / (u - l) gives
+    an upper line through (l, 0).  The kernel's slope: den = u - l rounded down, a quotient u / den from a fast
+    division modelled at the low end of its documented 2-ulp range for normal results and as 0 below 2^-126
+    (flushed), times 1 + 2^-20 rounded up, raised to at least 2^-99, capped at 1; slope 1 outside
+    den < 1e36, u > 1e-30.  Checked exactly (rationals) over neurons whose chord spans 2^-140 .. 1; without the
+    2^-99 floor a flushed quotient gives slope 0, below the chord."""
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    f32 = np.float32
+
+    def slope(zl, zu, floor=True):
+        den = _rd32(np.float64(zu) - np.float64(zl))
+        if not (den < f32(1e36) and zu > f32(1e-30)):
+            return f32(1.0)
+        q = Fraction(float(zu)) / Fraction(float(den))
+        if q < Fraction(2) ** -126:
+            qf = f32(0.0)
+        else:
+            qf = _rd32(float(q))
+            for _ in range(2):  # two units in the last place below
+                qf = np.nextafter(qf, f32(-np.inf))
+        s = _ru32(np.float64(qf) * (1 + 2.0 ** -20))
+        if floor:
+            s = max(s, f32(2.0 ** -99))
+        return min(s, f32(1.0))
+
+    cases = []
+    for _ in range(3000):
+        zu = f32(np.exp2(rng.uniform(-99.5, 20)))
+        zl = -f32(np.exp2(rng.uniform(-99.5, 120)))
+        cases.append((zl, zu))
+    cases += [(f32(-1e20), f32(1e-20)), (f32(-1e35), f32(2e-30)), (f32(-3.0), f32(1e-29)), (f32(-1.0), f32(1.0))]
+    flushed = 0
+    for zl, zu in cases:
+        chord = Fraction(float(zu)) / (Fraction(float(zu)) - Fraction(float(zl)))
+        s = slope(zl, zu)
+        assert Fraction(float(s)) >= chord, (zl, zu)
+        den = _rd32(np.float64(zu) - np.float64(zl))
+        if den < f32(1e36) and zu > f32(1e-30) and Fraction(float(zu)) / Fraction(float(den)) < Fraction(2) ** -126:
+            flushed += 1
+            assert Fraction(float(slope(zl, zu, floor=False))) < chord  # the floor is what keeps it valid
+    assert flushed > 0
